@@ -1,0 +1,300 @@
+"""Plain FP64 reference for the method of "Optimized Processing of Localized
+Collisions in Projective Dynamics" (Wang et al., SCA 2020).
+
+TEST INFRASTRUCTURE ONLY -- see the package docstring.  Written with numpy and
+scipy in float64, with no blocking, fusion or reordering beyond what the paper
+states, so that each function can be read against the section it cites.
+
+Where the paper is silent or garbled, these readings are taken:
+  * lambda is accepted and ignored: the energy is mu*||F - R||^2 only (Eq. 1,
+    the paper sets lambda = 0 in Section 2.2).
+  * The collision force is -W^T C (W x - t) (it follows from E_col in Eq. 7;
+    the printed total force in Section 3.1 has "+ t", a sign typo).
+  * The collision-prone nodes x_2 are given; E_beta is the set of tets whose
+    four vertices all lie in x_2 (so that beta touches only x_2, Section 3.4).
+  * Step 5 of Algorithm 1 is the full backward substitution of Step 3 in
+    Section 3.2: u_1 = L_1^-T (y_1 - L_1^-1 A_12 U_2), with U_2 the sum of the
+    inner-loop corrections.
+  * Local step on inverted elements: R = U diag(1, 1, det(U V^T)) V^T with the
+    singular values in descending order (the closest rotation in SO(3)).
+  * Backward Euler (Section 2.2 says it carries over but does not show it):
+    lumped mass m_i = rho * sum_{e ni i} Vol_e / 4, inertia target
+    y = x_n + dt * v_n, v_{n+1} = (x_{n+1} - x_n) / dt, no gravity; the x_1
+    inertia belongs to the alpha part, the x_2 inertia to the beta part.
+  * Dirichlet nodes are eliminated; their prescribed positions enter the
+    right-hand side only.
+
+Parity status: every function below is pinned by tests against closed forms,
+invariants, finite differences or brute force, except the multi-step
+trajectory, which the paper gives no numbers for ("parity unpinned" beyond the
+per-step pins).
+"""
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+__all__ = [
+    "element_precompute", "shape_gradients", "deformation_gradients",
+    "polar_rotations", "pd_energy", "elastic_forces", "stiffness_matrix",
+    "lumped_mass", "projection_rhs", "contact_matrix", "contact_forces",
+    "contact_energy", "Partition", "partition", "global_solve",
+    "OracleSolver", "schur_complement",
+]
+
+# The constant 4x3 matrix that maps tet vertex positions (as a 3x4 matrix
+# [x0 x1 x2 x3]) to the edge matrix Ds = [x1-x0, x2-x0, x3-x0].
+_S = np.array([[-1.0, -1.0, -1.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
+
+
+def element_precompute(X, tets):
+    """Rest shape data of linear tets (Section 2.2, linear elements).
+
+    Dm = [X1-X0, X2-X0, X3-X0]; Vol = |det Dm| / 6.  Returns (Dm_inv [E,3,3],
+    vol [E]).  Raises ValueError on a degenerate tet."""
+    P = X[tets]                               # [E, 4, 3]
+    Dm = np.stack([P[:, 1] - P[:, 0], P[:, 2] - P[:, 0], P[:, 3] - P[:, 0]], axis=2)
+    det = np.linalg.det(Dm)
+    if np.any(np.abs(det) <= 1e-300) or not np.all(np.isfinite(det)):
+        raise ValueError("degenerate rest tet")
+    return np.linalg.inv(Dm), np.abs(det) / 6.0
+
+
+def shape_gradients(Dm_inv):
+    """G_e = S Dm^-1 (4x3): F_e = [x0 x1 x2 x3] G_e."""
+    return np.einsum("ab,ebc->eac", _S, Dm_inv)
+
+
+def deformation_gradients(x, tets, Dm_inv):
+    """F_e = Ds Dm^-1 (Section 2.2)."""
+    P = x[tets]
+    Ds = np.stack([P[:, 1] - P[:, 0], P[:, 2] - P[:, 0], P[:, 3] - P[:, 0]], axis=2)
+    return Ds @ Dm_inv
+
+
+def polar_rotations(F):
+    """Local step (Section 2.2): the rotation minimising ||F - R||_F over SO(3),
+    R = U V^T from the SVD F = U Sigma V^T (orthogonal Procrustes), with the
+    smallest singular direction negated when det(U V^T) < 0."""
+    U, s, Vt = np.linalg.svd(F)
+    d = np.sign(np.linalg.det(U @ Vt))
+    d[d == 0] = 1.0
+    D = np.ones(F.shape[:-2] + (3,))
+    D[..., 2] = d
+    return (U * D[..., None, :]) @ Vt
+
+
+def pd_energy(x, R, tets, Dm_inv, vol, mu, elems=None):
+    """E_hat(x, R) = sum_e Vol_e * mu * ||F_e(x) - R_e||_F^2 (Eqs. 2-3)."""
+    if elems is not None:
+        tets, Dm_inv, vol, R = tets[elems], Dm_inv[elems], vol[elems], R[elems] if len(R) != len(elems) else R
+    F = deformation_gradients(x, tets, Dm_inv)
+    return float(np.sum(vol * mu * np.sum((F - R) ** 2, axis=(1, 2))))
+
+
+def elastic_forces(x, R, tets, Dm_inv, vol, mu, n=None):
+    """f = -dE_hat/dx with R fixed (Section 2.2): P = 2 mu (F - R) and
+    f_e = -Vol_e P G_e^T, scattered to the four vertices.  Returns [n, 3]."""
+    n = len(x) if n is None else n
+    F = deformation_gradients(x, tets, Dm_inv)
+    P = 2.0 * mu * (F - R)
+    G = shape_gradients(Dm_inv)
+    fe = -vol[:, None, None] * np.einsum("eij,eaj->eai", P, G)   # [E, 4, 3]
+    f = np.zeros((n, 3))
+    for a in range(4):
+        np.add.at(f, tets[:, a], fe[:, a])
+    return f
+
+
+def stiffness_matrix(tets, Dm_inv, vol, mu, n):
+    """Scalar PD matrix K = sum_e 2 mu Vol_e G_e G_e^T (n x n); the 3n x 3n
+    Hessian of E_hat is K (x) I_3 (Section 2.2, block-diagonal per coordinate)."""
+    G = shape_gradients(Dm_inv)
+    Ke = 2.0 * mu * vol[:, None, None] * np.einsum("eai,ebi->eab", G, G)
+    rows = np.repeat(tets, 4, axis=1).ravel()
+    cols = np.tile(tets, (1, 4)).ravel()
+    return sp.csr_matrix((Ke.ravel(), (rows, cols)), shape=(n, n))
+
+
+def lumped_mass(tets, vol, density, n):
+    """m_i = density * sum over incident tets of Vol_e / 4 (backward Euler)."""
+    m = np.zeros(n)
+    for a in range(4):
+        np.add.at(m, tets[:, a], density * vol / 4.0)
+    return m
+
+
+def projection_rhs(R, tets, Dm_inv, vol, mu, n):
+    """b = sum_e 2 mu Vol_e G_e R_e^T scattered, so that E_hat(x) for fixed R
+    equals sum_v (1/2 x_v^T K x_v - b_v^T x_v) + const.  Returns [n, 3]."""
+    G = shape_gradients(Dm_inv)
+    be = 2.0 * mu * vol[:, None, None] * np.einsum("eaj,eij->eai", G, R)   # [E, 4, 3]
+    b = np.zeros((n, 3))
+    for a in range(4):
+        np.add.at(b, tets[:, a], be[:, a])
+    return b
+
+
+def _contact_W(contacts, n):
+    k = contacts.k
+    rows = np.repeat(np.arange(k), 4)
+    cols = contacts.nodes.ravel()
+    vals = contacts.w.ravel()
+    keep = cols >= 0
+    return sp.csr_matrix((vals[keep], (rows[keep], cols[keep])), shape=(k, n))
+
+
+def contact_matrix(contacts, n):
+    """C_22 = W^T C W over all nodes (Eq. 8), C = diag(c_j) of active springs."""
+    W = _contact_W(contacts, n)
+    return (W.T @ sp.diags(contacts.stiffness) @ W).tocsr()
+
+
+def contact_forces(contacts, x):
+    """f_col = -W^T C (W x - t) (Section 3.1, sign as derived from Eq. 7)."""
+    W = _contact_W(contacts, len(x))
+    r = W @ x - contacts.target
+    return -(W.T @ (contacts.stiffness[:, None] * r))
+
+
+def contact_energy(contacts, x):
+    """E_col = sum_j c_j / 2 ||p_j - t_j||^2 over active springs (Section 2.3)."""
+    W = _contact_W(contacts, len(x))
+    r = W @ x - contacts.target
+    return float(0.5 * np.sum(contacts.stiffness[:, None] * r * r))
+
+
+class Partition:
+    """Node and element split of Section 3.4 / Figure 2."""
+
+    def __init__(self, n, tets, dirichlet, region):
+        self.n = n
+        self.dirichlet = np.asarray(dirichlet, dtype=np.int64)
+        self.region = np.asarray(region, dtype=np.int64)
+        is_d = np.zeros(n, bool)
+        is_d[self.dirichlet] = True
+        is_r = np.zeros(n, bool)
+        is_r[self.region] = True
+        if np.any(is_d & is_r):
+            raise ValueError("region and Dirichlet sets overlap")
+        self.free = np.nonzero(~is_d)[0]
+        self.x1 = np.nonzero(~is_d & ~is_r)[0]
+        self.beta = np.nonzero(is_r[tets].all(axis=1))[0]
+        self.alpha = np.nonzero(~is_r[tets].all(axis=1))[0]
+
+
+def partition(n, tets, dirichlet, region):
+    return Partition(n, tets, dirichlet, region)
+
+
+def global_solve(K, b, free, fixed, x_fixed, extra_diag=None, extra_rhs=None, C=None, Ct=None):
+    """Minimise the quadratic sum_v 1/2 x_v^T (K + C) x_v - rhs_v^T x_v over the
+    free nodes with the fixed nodes held at x_fixed (the PD global step,
+    Section 2.2, with the penalty terms of Section 2.3 folded in).
+    K: n x n sparse; b: [n, 3]; C: optional n x n sparse contact matrix with
+    Ct = W^T C t [n, 3]; extra_diag / extra_rhs: inertia terms.  Solves the
+    free block directly (sparse LU, all three coordinates at once)."""
+    M = K if C is None else (K + C)
+    rhs = b.copy()
+    if Ct is not None:
+        rhs = rhs + Ct
+    if extra_diag is not None:
+        M = M + sp.diags(extra_diag)
+        rhs = rhs + extra_rhs
+    M = M.tocsr()
+    Mff = M[free][:, free].tocsc()
+    r = rhs[free] - M[free][:, fixed] @ x_fixed
+    lu = spla.splu(Mff, permc_spec="MMD_AT_PLUS_A")
+    return lu.solve(r)
+
+
+def schur_complement(A, idx1, idx2):
+    """Sigma = A_22 - A_21 A_11^-1 A_12 (Eq. 10), dense, from a sparse A."""
+    A = A.tocsr()
+    A11 = A[idx1][:, idx1].tocsc()
+    A12 = A[idx1][:, idx2].toarray()
+    A22 = A[idx2][:, idx2].toarray()
+    Z = spla.splu(A11, permc_spec="MMD_AT_PLUS_A").solve(A12)
+    return A22 - A12.T @ Z
+
+
+class OracleSolver:
+    """Algorithm 1 (Section 3.4), computed without the Schur split.
+
+    Each inner iteration solves the full free-node system with R_alpha from the
+    start of the outer iteration, R_beta and the contacts of this inner
+    iteration, and keeps only x_2 from that solve; x_1 is taken from the last
+    such solve when the inner loop ends.  This equals the Schur-complement
+    form because minimising over x_1 first leaves the reduced energy
+    E~_alpha(x_2) the paper's inner loop descends (Eq. 12)."""
+
+    def __init__(self, X, tets, dirichlet, region, mu, density=0.0, dt=0.0):
+        self.X = np.asarray(X, dtype=np.float64)
+        self.tets = np.asarray(tets, dtype=np.int64)
+        self.n = len(X)
+        self.mu = float(mu)
+        self.dt = float(dt)
+        self.Dm_inv, self.vol = element_precompute(self.X, self.tets)
+        self.part = Partition(self.n, self.tets, dirichlet, region)
+        self.K = stiffness_matrix(self.tets, self.Dm_inv, self.vol, self.mu, self.n)
+        self.mass = lumped_mass(self.tets, self.vol, density, self.n) if dt > 0 else None
+        self.x = self.X.copy()
+        self.v = np.zeros_like(self.X)
+        self.stats = {"solves": 0}
+
+    def set_dirichlet(self, pos):
+        self.x[self.part.dirichlet] = pos
+
+    def rotations(self, x, elems):
+        F = deformation_gradients(x, self.tets[elems], self.Dm_inv[elems])
+        return polar_rotations(F)
+
+    def full_solve(self, x, R, contacts, y=None):
+        """Argmin over free x of E_hat(x; R) + E_col (+ inertia), Dirichlet fixed."""
+        b = projection_rhs(R, self.tets, self.Dm_inv, self.vol, self.mu, self.n)
+        C = Ct = None
+        if contacts is not None and contacts.k > 0:
+            C = contact_matrix(contacts, self.n)
+            W = _contact_W(contacts, self.n)
+            Ct = W.T @ (contacts.stiffness[:, None] * contacts.target)
+        ed = er = None
+        if self.mass is not None:
+            ed = self.mass / self.dt ** 2
+            er = ed[:, None] * y
+        p = self.part
+        xf = global_solve(self.K, b, p.free, p.dirichlet, x[p.dirichlet], ed, er, C, Ct)
+        out = x.copy()
+        out[p.free] = xf
+        self.stats["solves"] += 1
+        return out
+
+    def step(self, outer_iters, inner_iters, contacts_fn=None, dirichlet_pos=None):
+        """One time step (quasistatic if dt == 0): Algorithm 1 repeated
+        outer_iters times.  contacts_fn(x) -> Contacts is called once per inner
+        iteration with the current x_2 (the detection step 4.1)."""
+        p = self.part
+        if dirichlet_pos is not None:
+            self.set_dirichlet(dirichlet_pos)
+        x_n = self.x.copy()
+        y = (x_n + self.dt * self.v) if self.mass is not None else None
+        R = np.zeros((len(self.tets), 3, 3))
+        for _ in range(outer_iters):
+            R[p.alpha] = self.rotations(self.x, p.alpha)          # step 1
+            virt = None
+            for _ in range(inner_iters):
+                contacts = contacts_fn(self.x) if contacts_fn is not None else None   # 4.1
+                R[p.beta] = self.rotations(self.x, p.beta)        # 4.2
+                virt = self.full_solve(self.x, R, contacts, y)    # 4.3-4.5
+                self.x[p.region] = virt[p.region]                 # 4.6
+            self.x[p.x1] = virt[p.x1]                             # 5
+        if self.mass is not None:
+            self.v = (self.x - x_n) / self.dt
+        return self.x
+
+    def energy(self, x, R, contacts=None, y=None):
+        """E_hat + E_col (+ inertia) at x for fixed R and contacts."""
+        e = pd_energy(x, R, self.tets, self.Dm_inv, self.vol, self.mu)
+        if contacts is not None and contacts.k > 0:
+            e += contact_energy(contacts, x)
+        if self.mass is not None and y is not None:
+            e += float(0.5 * np.sum(self.mass[:, None] / self.dt ** 2 * (x - y) ** 2))
+        return e
