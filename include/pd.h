@@ -1,0 +1,204 @@
+/*
+ * pd.h -- C ABI of the localized-collision Projective Dynamics library
+ * (Wang, Tao, Brandt, Cutting, Sifakis, "Optimized Processing of Localized
+ * Collisions in Projective Dynamics", SCA 2020).
+ *
+ * One solver handle owns one scene on one CUDA device.  Every entry point
+ * returns a pd_status; the library never aborts or exits.  On any error the
+ * handle stays usable, the solver state is left as it was before the call,
+ * and pd_last_error() describes what happened.
+ *
+ * Conventions
+ *   - Host pointers are read (or written) during the call only; the caller
+ *     keeps ownership.  Entry points ending in _dev take device pointers that
+ *     must stay valid until the call returns on the solver's stream.
+ *   - Node ids and element indices are int32 and 0-based; sizes are int64.
+ *   - Positions are [n][3] row-major float64 in the caller's node order.
+ *   - The solver owns all device memory it allocates and frees it in
+ *     pd_destroy().
+ */
+#ifndef PD_H
+#define PD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PD_OK = 0,
+    PD_ERR_INVALID_ARG = 1,            /* null pointer, negative size, bad option   */
+    PD_ERR_BAD_MESH = 2,               /* degenerate rest tet or node id out of range */
+    PD_ERR_REGION = 3,                 /* region empty, overlaps Dirichlet, or too large */
+    PD_ERR_CONTACT_OUTSIDE_REGION = 4, /* a contact names a node outside x_2        */
+    PD_ERR_NOT_SPD = 5,                /* a Cholesky pivot was not positive         */
+    PD_ERR_NO_CONVERGENCE = 6,         /* refinement / PCG missed tol in max_refine */
+    PD_ERR_TIMEOUT = 7,                /* a bounded device wait gave up             */
+    PD_ERR_CUDA = 8,                   /* a CUDA runtime call failed                */
+    PD_ERR_OOM = 9                     /* device or host allocation failed          */
+} pd_status;
+
+/* Precision of the collision-region solve H u_2 = g (Algorithm 1, step 4.5). */
+enum {
+    PD_FP64 = 0,      /* FP64 blocked Cholesky of H and FP64 triangular solves      */
+    PD_FP32_IR = 1,   /* FP32 factor, FP64-residual iterative refinement            */
+    PD_TF32_IR = 2,   /* TF32 tensor-core trailing updates, FP64-residual refinement */
+    PD_BF16_IR = 3,   /* BF16 tensor-core trailing updates, FP64-residual refinement */
+    PD_PCG_WARM = 4   /* PCG on H preconditioned by the contact-free factor of Sigma,
+                         started from a caller-supplied (e.g. learned) guess        */
+};
+
+typedef struct {
+    int64_t n_nodes;
+    const double* rest_pos;   /* [n_nodes][3] */
+    int64_t n_tets;
+    const int32_t* tets;      /* [n_tets][4], either orientation */
+} pd_mesh;
+
+typedef struct {
+    double mu;        /* Lame mu of the PD energy mu ||F - R||_F^2 (Eq. 2)       */
+    double lambda;    /* accepted and ignored: the method sets lambda = 0 (Sec 2.2) */
+    double density;   /* used for the lumped mass when dt > 0                    */
+} pd_material;
+
+typedef struct {
+    int precision;     /* PD_FP64, PD_FP32_IR, ... (default PD_FP64)            */
+    double tol;        /* relative residual ||g - H u|| / ||g|| for the refined forms (1e-10) */
+    int max_refine;    /* refinement / PCG iteration cap (default 50)           */
+    int inner_iters;   /* inner iterations per outer iteration (Algorithm 1, step 4) */
+    void* cuda_stream; /* cudaStream_t to run on; NULL = the library's own stream */
+    int timing;        /* nonzero: record CUDA events per phase (pd_get_stats)  */
+} pd_options;
+
+typedef struct {
+    int64_t n_nodes, n_tets, n_free, n1, m;   /* sizes after partitioning            */
+    int64_t n_alpha, n_beta;                  /* |E_alpha|, |E_beta|                 */
+    int64_t n_supernodes, n_levels, nnz_L;    /* interior factor L_1 and L_21        */
+    int64_t contacts;                         /* active springs in the last inner iteration */
+    int64_t outer_done, inner_done;           /* iterations run by the last pd_step  */
+    int refine_iters;                         /* refinement / PCG iterations, last solve */
+    double residual;                          /* ||g - H u|| / ||g|| of the last solve */
+    double setup_ms;                          /* wall time of pd_setup               */
+    /* per-phase device time of the last pd_step (timing != 0), milliseconds:      */
+    double ms_local_alpha;    /* a1: alpha polar + forces + gather                  */
+    double ms_forward;        /* a2: sparse forward substitution                    */
+    double ms_contact_update; /* a3: H = Sigma_0 + C_22                             */
+    double ms_local_beta;     /* a4: beta polar + forces + RHS g                    */
+    double ms_factor_solve;   /* a5: refactor + solve (incl. refinement)            */
+    double ms_bookkeeping;    /* a6: x_2 += u_2, f~_2 -= Sigma_alpha u_2             */
+    double ms_backward;       /* a7: sparse backward substitution                   */
+    double ms_step;           /* whole pd_step                                      */
+} pd_stats;
+
+typedef struct pd_solver pd_solver;
+
+/* Called once per inner iteration (Algorithm 1, step 4.1, DetectCollisions)
+ * with the current collision-prone positions x2 [m][3] (host, region order).
+ * It may call pd_set_contacts() on the solver; a non-PD_OK return aborts the
+ * step (state rolled back) and is returned by pd_step. */
+typedef pd_status (*pd_contact_cb)(void* user, const double* x2, pd_solver* s);
+
+/* Build a solver (Algorithm 1, "preliminary"): element rest data, the node
+ * split into x_1 / x_2 and E_alpha / E_beta (Section 3.4, Figure 2), the
+ * interior ordering (nested dissection, x_2 last: Section 3.2), the partial
+ * Cholesky A = [L_1 0; A_21 L_1^-T I] diag(I, Sigma_alpha) [...]^T of the
+ * alpha matrix (Eq. 9) and Sigma_0 = Sigma_alpha + A_22^beta (+ M_2/dt^2).
+ *   mesh, mat     : rest mesh and material (copied)
+ *   dt            : time step; 0 = quasistatic (Eq. 4), > 0 = backward Euler
+ *   region, m     : the m collision-prone node ids x_2 (any order; row i of
+ *                   Sigma is region[i]); 1 <= m <= 16384
+ *   dirichlet, nd : fixed node ids; must not meet the region
+ *   opts          : may be NULL for defaults
+ *   out           : receives the handle; NULL on failure
+ * Errors: INVALID_ARG, BAD_MESH, REGION, NOT_SPD (a free component without a
+ * Dirichlet node in quasistatic mode), CUDA, OOM. */
+pd_status pd_setup(const pd_mesh* mesh, const pd_material* mat, double dt,
+                   const int32_t* region, int64_t m,
+                   const int32_t* dirichlet, int64_t nd,
+                   const pd_options* opts, pd_solver** out);
+
+/* Prescribe the Dirichlet positions [nd][3] (order of pd_setup's list);
+ * they take effect at the next pd_step.  Errors: INVALID_ARG. */
+pd_status pd_set_dirichlet(pd_solver* s, const double* pos);
+
+/* Replace the active penalty springs (Section 2.3, Eqs. 6-8): spring j pulls
+ * the proxy p_j = sum_a w[j][a] x[nodes[j][a]] toward target[j] with stiffness
+ * stiffness[j]; unused slots have nodes = -1 and w = 0.  Every named node must
+ * lie in x_2.  k = 0 clears all springs.  Errors: INVALID_ARG,
+ * CONTACT_OUTSIDE_REGION (state unchanged), CUDA, OOM. */
+pd_status pd_set_contacts(pd_solver* s, int64_t k, const int32_t* nodes /*[k][4]*/,
+                          const double* w /*[k][4]*/, const double* target /*[k][3]*/,
+                          const double* stiffness /*[k]*/);
+
+/* One time step: outer_iters passes of Algorithm 1 (Section 3.4).  If cb is
+ * not NULL it is called at every inner iteration before the local beta step;
+ * otherwise the springs last set stay active.  Errors: NOT_SPD,
+ * NO_CONVERGENCE, TIMEOUT, CUDA, or the callback's status; on error the
+ * positions and velocities are those from before the call. */
+pd_status pd_step(pd_solver* s, int outer_iters, pd_contact_cb cb, void* user);
+
+/* Current positions [n][3] (host). */
+pd_status pd_get_positions(const pd_solver* s, double* out);
+
+/* Current positions into a caller-owned device buffer [n][3]. */
+pd_status pd_get_positions_dev(const pd_solver* s, double* out_dev);
+
+/* Checkpoint / restore: positions and velocities [n][3] (host); v may be NULL
+ * (quasistatic). */
+pd_status pd_get_state(const pd_solver* s, double* x, double* v);
+pd_status pd_set_state(pd_solver* s, const double* x, const double* v);
+
+/* Counters and per-phase timings of the last pd_step. */
+pd_status pd_get_stats(const pd_solver* s, pd_stats* out);
+
+/* Text of the last error on this handle ("" if none).  Valid until the next
+ * call on the handle.  s may be NULL for errors of pd_setup. */
+const char* pd_last_error(const pd_solver* s);
+
+/* Free the handle and every device buffer it owns.  NULL is ignored. */
+void pd_destroy(pd_solver* s);
+
+/* ------------------------------------------------------------------------
+ * Kernel-level entry points (used by the parity tests and the benchmark).
+ * ------------------------------------------------------------------------ */
+
+/* Local step on all elements (Section 2.2): for each tet e, R_e = polar(F_e)
+ * in SO(3) with F_e = Ds Dm^-1 at positions x [n][3] (host), and the elastic
+ * forces f = -dE_hat/dx, f_e = -Vol_e 2 mu (F_e - R_e) G_e^T, summed per node.
+ *   R_out : [n_tets][3][3] row-major (host), may be NULL
+ *   f_out : [n][3] (host), may be NULL; Dirichlet nodes receive their sums too */
+pd_status pd_local_step(pd_solver* s, const double* x, double* R_out, double* f_out);
+
+/* Sigma_0 = Sigma_alpha + A_22^beta (+ M_2/dt^2), dense [m][m] row-major,
+ * region order (host). */
+pd_status pd_get_schur(const pd_solver* s, double* out);
+
+/* Schur refactor + solve (Algorithm 1, steps 4.3 and 4.5, Section 3.3): form
+ * H = Sigma_0 + C_22 from the springs last set with pd_set_contacts, factor
+ * it in the solver's precision and solve H u = g for three right-hand sides.
+ *   g : [m][3] host (region order);  u : [m][3] host output
+ *   u0: [m][3] host initial guess for PD_PCG_WARM, may be NULL (zero)
+ * Errors: NOT_SPD, NO_CONVERGENCE, CUDA. */
+pd_status pd_schur_solve(pd_solver* s, const double* g, const double* u0, double* u);
+
+/* Same on device buffers (g_dev, u_dev [m][3]; u0_dev may be NULL). */
+pd_status pd_schur_solve_dev(pd_solver* s, const double* g_dev, const double* u0_dev, double* u_dev);
+
+/* Host-only partial Cholesky (no device needed): runs the setup of pd_setup
+ * on the CPU and returns Sigma_0 (dense [m][m] row-major, region order) and
+ * a one-line summary of the factorisation in info (may be NULL; at most
+ * info_len bytes including the terminating zero).  Same arguments and errors
+ * as pd_setup (Algorithm 1 "preliminary", Eq. 9). */
+pd_status pd_host_schur(const pd_mesh* mesh, const pd_material* mat, double dt,
+                        const int32_t* region, int64_t m,
+                        const int32_t* dirichlet, int64_t nd,
+                        double* sigma_out, char* info, int64_t info_len);
+
+/* Change the precision of the collision-region solve on an existing handle. */
+pd_status pd_set_precision(pd_solver* s, int precision);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PD_H */

@@ -1,0 +1,328 @@
+// Dense collision-region kernels (Section 3.3; Algorithm 1 steps 4.3-4.7):
+// the additive contact update of the Schur complement, the blocked FP64
+// Cholesky refactorisation with 64 x 64 tiles, the blocked triangular solves
+// for three right-hand sides, and the Sigma matrix-vector products.
+// H is stored column-major with leading dimension mp (a multiple of 64); rows
+// and columns m..mp-1 hold an identity block, so every tile is full.
+#include "kernels.h"
+
+namespace pdk {
+namespace {
+
+constexpr int TB = 64;
+
+__global__ void k_copy_sigma(const double* __restrict__ S, int64_t m, double* __restrict__ H, int64_t mp) {
+  int ti = blockIdx.x, tj = blockIdx.y;
+  if (ti < tj) return;
+  for (int idx = threadIdx.x; idx < TB * TB; idx += blockDim.x) {
+    int r = idx % TB, c = idx / TB;
+    int64_t i = (int64_t)ti * TB + r, j = (int64_t)tj * TB + c;
+    double v;
+    if (i < m && j < m) v = S[i + j * m];
+    else v = (i == j) ? 1.0 : 0.0;
+    H[i + j * mp] = v;
+  }
+}
+
+__global__ void k_contact_scatter(int64_t k, const int32_t* __restrict__ cidx, const double* __restrict__ cw,
+                                  const double* __restrict__ cs, double* __restrict__ H, int64_t mp) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= 16 * k) return;
+  int64_t j = t >> 4;
+  int a = (t >> 2) & 3, b = t & 3;
+  int ra = cidx[4 * j + a], rb = cidx[4 * j + b];
+  if (ra < 0 || rb < 0 || ra < rb) return;
+  atomicAdd(H + ra + (int64_t)rb * mp, cs[j] * cw[4 * j + a] * cw[4 * j + b]);
+}
+
+__global__ void k_contact_forces(int64_t k, const int32_t* __restrict__ cidx, const double* __restrict__ cw,
+                                 const double* __restrict__ ct, const double* __restrict__ cs,
+                                 const int32_t* __restrict__ region, const double* __restrict__ x,
+                                 double* __restrict__ g) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= k) return;
+  double p[3] = {0, 0, 0};
+  for (int a = 0; a < 4; ++a) {
+    int r = cidx[4 * j + a];
+    if (r < 0) continue;
+    const double* xv = x + 3 * (int64_t)region[r];
+    double w = cw[4 * j + a];
+    p[0] += w * xv[0]; p[1] += w * xv[1]; p[2] += w * xv[2];
+  }
+  double c = cs[j];
+  double q[3] = {c * (p[0] - ct[3 * j]), c * (p[1] - ct[3 * j + 1]), c * (p[2] - ct[3 * j + 2])};
+  for (int a = 0; a < 4; ++a) {
+    int r = cidx[4 * j + a];
+    if (r < 0) continue;
+    double w = cw[4 * j + a];
+    atomicAdd(g + 3 * (int64_t)r, -w * q[0]);
+    atomicAdd(g + 3 * (int64_t)r + 1, -w * q[1]);
+    atomicAdd(g + 3 * (int64_t)r + 2, -w * q[2]);
+  }
+}
+
+// Factor the diagonal tile (kt, kt) in shared memory and form its inverse.
+__global__ void __launch_bounds__(256) k_chol_diag(double* __restrict__ H, int64_t mp, int kt,
+                                                   double* __restrict__ Linv, int* __restrict__ status) {
+  extern __shared__ double sm[];
+  double* A = sm;             // column-major A[c*TB + r]
+  double* Z = sm + TB * TB;   // inverse, column-major
+  __shared__ double piv;
+  const int tid = threadIdx.x;
+  double* Ht = H + (int64_t)kt * TB + (int64_t)kt * TB * mp;
+  for (int idx = tid; idx < TB * TB; idx += 256) A[idx] = Ht[(idx % TB) + (int64_t)(idx / TB) * mp];
+  __syncthreads();
+  for (int j = 0; j < TB; ++j) {
+    if (tid == 0) {
+      double d = A[j * TB + j];
+      if (!(d > 0.0) || !isfinite(d)) {
+        if (status[0] == 0) status[0] = kt * TB + j + 1;
+        d = 1.0;
+      }
+      piv = sqrt(d);
+      A[j * TB + j] = piv;
+    }
+    __syncthreads();
+    double ip = 1.0 / piv;
+    if (tid > j && tid < TB) A[j * TB + tid] *= ip;
+    __syncthreads();
+    int r = tid % TB;
+    for (int c = j + 1 + tid / TB; c < TB; c += 256 / TB)
+      if (r >= c) A[c * TB + r] -= A[j * TB + r] * A[j * TB + c];
+    __syncthreads();
+  }
+  // inverse of the lower-triangular tile: thread c solves L z = e_c
+  if (tid < TB) {
+    int c = tid;
+    for (int i = 0; i < c; ++i) Z[c * TB + i] = 0.0;
+    Z[c * TB + c] = 1.0 / A[c * TB + c];
+    for (int i = c + 1; i < TB; ++i) {
+      double s = 0.0;
+      for (int q = c; q < i; ++q) s += A[q * TB + i] * Z[c * TB + q];
+      Z[c * TB + i] = -s / A[i * TB + i];
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < TB * TB; idx += 256) {
+    int r = idx % TB, c = idx / TB;
+    if (r >= c) Ht[r + (int64_t)c * mp] = A[idx];
+    Linv[(int64_t)kt * TB * TB + idx] = Z[idx];
+  }
+}
+
+// 64x64x64 FP64 product in shared memory: acc[a][b] = sum_t As[t][r_a] * Bs[t][c_b],
+// r_a = tr + 16a, c_b = tc + 16b.
+__device__ __forceinline__ void tile_mma(const double* As, const double* Bs, int tr, int tc, double acc[4][4]) {
+#pragma unroll 8
+  for (int t = 0; t < TB; ++t) {
+    double a[4], b[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { a[q] = As[t * TB + tr + 16 * q]; b[q] = Bs[t * TB + tc + 16 * q]; }
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[p][q] = fma(a[p], b[q], acc[p][q]);
+  }
+}
+
+// L_ik = A_ik Linv_kk^T for tiles i > kt
+__global__ void __launch_bounds__(256) k_chol_trsm(double* __restrict__ H, int64_t mp, int kt,
+                                                   const double* __restrict__ Linv) {
+  extern __shared__ double sm[];
+  double* As = sm;            // As[t][r] = A_ik(r, t)
+  double* Bs = sm + TB * TB;  // Bs[t][c] = Linv(c, t)
+  const int tid = threadIdx.x;
+  const int64_t it = kt + 1 + blockIdx.x;
+  double* Ai = H + it * TB + (int64_t)kt * TB * mp;
+  const double* Li = Linv + (int64_t)kt * TB * TB;
+  for (int idx = tid; idx < TB * TB; idx += 256) {
+    int r = idx % TB, t = idx / TB;
+    As[idx] = Ai[r + (int64_t)t * mp];
+    Bs[idx] = Li[r + t * TB];   // (c = r, t)
+  }
+  __syncthreads();
+  int tr = tid % 16, tc = tid / 16;
+  double acc[4][4] = {};
+  tile_mma(As, Bs, tr, tc, acc);
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Ai[(tr + 16 * p) + (int64_t)(tc + 16 * q) * mp] = acc[p][q];
+}
+
+// A_ij -= L_ik L_jk^T for kt < j <= i
+__global__ void __launch_bounds__(256) k_chol_update(double* __restrict__ H, int64_t mp, int kt, int T) {
+  extern __shared__ double sm[];
+  double* As = sm;
+  double* Bs = sm + TB * TB;
+  const int tid = threadIdx.x;
+  int64_t idx = blockIdx.x;
+  int64_t ii = (int64_t)((sqrt(8.0 * (double)idx + 1.0) - 1.0) * 0.5);
+  while ((ii + 1) * (ii + 2) / 2 <= idx) ++ii;
+  while (ii * (ii + 1) / 2 > idx) --ii;
+  int64_t jj = idx - ii * (ii + 1) / 2;
+  const int64_t it = kt + 1 + ii, jt = kt + 1 + jj;
+  const double* Li = H + it * TB + (int64_t)kt * TB * mp;
+  const double* Lj = H + jt * TB + (int64_t)kt * TB * mp;
+  for (int q = tid; q < TB * TB; q += 256) {
+    int r = q % TB, t = q / TB;
+    As[q] = Li[r + (int64_t)t * mp];
+    Bs[q] = Lj[r + (int64_t)t * mp];
+  }
+  __syncthreads();
+  int tr = tid % 16, tc = tid / 16;
+  double acc[4][4] = {};
+  tile_mma(As, Bs, tr, tc, acc);
+  double* Aij = H + it * TB + jt * TB * mp;
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Aij[(tr + 16 * p) + (int64_t)(tc + 16 * q) * mp] -= acc[p][q];
+}
+
+// Forward step kt: y_k = Linv_kk w_k (block 0 stores it), w_i -= L_ik y_k for i = kt + blockIdx.x
+__global__ void __launch_bounds__(192) k_trsv_fwd(const double* __restrict__ H, int64_t mp, int kt,
+                                                  const double* __restrict__ Linv, double* __restrict__ w,
+                                                  double* __restrict__ y) {
+  __shared__ double yk[TB * 3];
+  const int tid = threadIdx.x, r = tid / 3, v = tid % 3;
+  const double* Lk = Linv + (int64_t)kt * TB * TB;
+  const double* wk = w + (int64_t)kt * TB * 3;
+  double s = 0.0;
+  for (int c = 0; c <= r; ++c) s += Lk[r + c * TB] * wk[3 * c + v];
+  yk[tid] = s;
+  __syncthreads();
+  if (blockIdx.x == 0) {
+    y[(int64_t)kt * TB * 3 + tid] = s;
+    return;
+  }
+  const int64_t it = kt + blockIdx.x;
+  const double* Lik = H + it * TB + (int64_t)kt * TB * mp;
+  double acc = 0.0;
+  for (int c = 0; c < TB; ++c) acc += Lik[r + (int64_t)c * mp] * yk[3 * c + v];
+  w[it * TB * 3 + tid] -= acc;
+}
+
+// Backward step kt: u_k = Linv_kk^T w_k (block 0 stores it), w_j -= L_kj^T u_k for j = blockIdx.x - 1
+__global__ void __launch_bounds__(192) k_trsv_bwd(const double* __restrict__ H, int64_t mp, int kt,
+                                                  const double* __restrict__ Linv, double* __restrict__ w,
+                                                  double* __restrict__ u) {
+  __shared__ double uk[TB * 3];
+  const int tid = threadIdx.x, r = tid / 3, v = tid % 3;
+  const double* Lk = Linv + (int64_t)kt * TB * TB;
+  const double* wk = w + (int64_t)kt * TB * 3;
+  double s = 0.0;
+  for (int c = r; c < TB; ++c) s += Lk[c + r * TB] * wk[3 * c + v];
+  uk[tid] = s;
+  __syncthreads();
+  if (blockIdx.x == 0) {
+    u[(int64_t)kt * TB * 3 + tid] = s;
+    return;
+  }
+  const int64_t jt = blockIdx.x - 1;
+  const double* Lkj = H + (int64_t)kt * TB + jt * TB * mp;
+  double acc = 0.0;
+  for (int c = 0; c < TB; ++c) acc += Lkj[c + (int64_t)r * mp] * uk[3 * c + v];
+  w[jt * TB * 3 + tid] -= acc;
+}
+
+__global__ void k_pad_rhs(const double* g, int64_t m, int64_t mp, double* w) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < 3 * mp) w[i] = i < 3 * m ? g[i] : 0.0;
+}
+
+__global__ void k_symv3(const double* __restrict__ S, int64_t m, const double* __restrict__ v,
+                        double* __restrict__ out) {
+  int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (i >= m) return;
+  const double* row = S + i * m;
+  double a0 = 0, a1 = 0, a2 = 0;
+  for (int64_t j = lane; j < m; j += 32) {
+    double s = row[j];
+    a0 += s * v[3 * j]; a1 += s * v[3 * j + 1]; a2 += s * v[3 * j + 2];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+  }
+  if (lane == 0) { out[3 * i] = a0; out[3 * i + 1] = a1; out[3 * i + 2] = a2; }
+}
+
+__global__ void k_spmv3(int64_t m, const int64_t* __restrict__ ptr, const int32_t* __restrict__ row,
+                        const double* __restrict__ val, const double* __restrict__ v, double alpha,
+                        double* __restrict__ out) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  double a0 = 0, a1 = 0, a2 = 0;
+  for (int64_t q = ptr[i]; q < ptr[i + 1]; ++q) {
+    double s = val[q];
+    int64_t j = row[q];
+    a0 += s * v[3 * j]; a1 += s * v[3 * j + 1]; a2 += s * v[3 * j + 2];
+  }
+  out[3 * i] += alpha * a0; out[3 * i + 1] += alpha * a1; out[3 * i + 2] += alpha * a2;
+}
+
+inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+void copy_sigma(const double* S, int64_t m, double* H, int64_t mp, cudaStream_t st) {
+  dim3 grid((unsigned)(mp / TB), (unsigned)(mp / TB));
+  k_copy_sigma<<<grid, 256, 0, st>>>(S, m, H, mp);
+}
+
+void contact_scatter(int64_t k, const int32_t* cidx, const double* cw, const double* cs, double* H,
+                     int64_t mp, cudaStream_t st) {
+  if (k > 0) k_contact_scatter<<<nblk(16 * k, 256), 256, 0, st>>>(k, cidx, cw, cs, H, mp);
+}
+
+void contact_forces(int64_t k, const int32_t* cidx, const double* cw, const double* ct, const double* cs,
+                    const int32_t* region, const double* x, double* g, cudaStream_t st) {
+  if (k > 0) k_contact_forces<<<nblk(k, 128), 128, 0, st>>>(k, cidx, cw, ct, cs, region, x, g);
+}
+
+void cholesky_fp64(double* H, int64_t mp, double* Linv, int* status, cudaStream_t st) {
+  static bool attr = false;
+  const int smem = 2 * TB * TB * sizeof(double);
+  if (!attr) {
+    cudaFuncSetAttribute(k_chol_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_chol_update, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_chol_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr = true;
+  }
+  const int T = (int)(mp / TB);
+  for (int k = 0; k < T; ++k) {
+    k_chol_diag<<<1, 256, smem, st>>>(H, mp, k, Linv, status);
+    int n = T - k - 1;
+    if (n <= 0) break;
+    k_chol_trsm<<<n, 256, smem, st>>>(H, mp, k, Linv);
+    k_chol_update<<<(unsigned)((int64_t)n * (n + 1) / 2), 256, smem, st>>>(H, mp, k, T);
+  }
+}
+
+void chol_solve_fp64(const double* H, int64_t mp, const double* Linv, const double* g, double* u, int64_t m,
+                     double* work, cudaStream_t st) {
+  const int T = (int)(mp / TB);
+  double* w = work;
+  double* y = work + 3 * mp;
+  k_pad_rhs<<<nblk(3 * mp, 256), 256, 0, st>>>(g, m, mp, w);
+  for (int k = 0; k < T; ++k) k_trsv_fwd<<<T - k, 192, 0, st>>>(H, mp, k, Linv, w, y);
+  // backward on y (copied into w as the running right-hand side)
+  cudaMemcpyAsync(w, y, sizeof(double) * 3 * mp, cudaMemcpyDeviceToDevice, st);
+  for (int k = T - 1; k >= 0; --k) k_trsv_bwd<<<k + 1, 192, 0, st>>>(H, mp, k, Linv, w, y);
+  cudaMemcpyAsync(u, y, sizeof(double) * 3 * m, cudaMemcpyDeviceToDevice, st);
+}
+
+void symv3(const double* S, int64_t m, const double* v, double* out, cudaStream_t st) {
+  if (m > 0) k_symv3<<<nblk(32 * m, 256), 256, 0, st>>>(S, m, v, out);
+}
+
+void spmv3(int64_t m, const int64_t* ptr, const int32_t* row, const double* val, const double* v, double alpha,
+           double* out, cudaStream_t st) {
+  if (m > 0) k_spmv3<<<nblk(m, 256), 256, 0, st>>>(m, ptr, row, val, v, alpha, out);
+}
+
+}  // namespace pdk

@@ -1,0 +1,282 @@
+// Local step kernels: batched FP64 polar decomposition of the deformation
+// gradients and the elemental forces (Section 2.2), plus the deterministic
+// per-node gather and small vector kernels.
+#include "kernels.h"
+
+namespace pdk {
+namespace {
+
+// X^-T = cof(X) / det(X); row-major 3x3.
+__device__ __forceinline__ double cofactor(const double* X, double* C) {
+  C[0] = X[4] * X[8] - X[5] * X[7];
+  C[1] = X[5] * X[6] - X[3] * X[8];
+  C[2] = X[3] * X[7] - X[4] * X[6];
+  C[3] = X[2] * X[7] - X[1] * X[8];
+  C[4] = X[0] * X[8] - X[2] * X[6];
+  C[5] = X[1] * X[6] - X[0] * X[7];
+  C[6] = X[1] * X[5] - X[2] * X[4];
+  C[7] = X[2] * X[3] - X[0] * X[5];
+  C[8] = X[0] * X[4] - X[1] * X[3];
+  return X[0] * C[0] + X[1] * C[1] + X[2] * C[2];
+}
+
+// Scaled Newton iteration for the orthogonal polar factor (Higham):
+// X <- (g X + X^-T / g) / 2, Frobenius scaling g = sqrt(||X^-1|| / ||X||)
+// until the update is small, then unscaled.  Valid for det F > 0, where the
+// polar factor is the closest rotation.  Returns false if it cannot be used.
+__device__ bool polar_newton(const double* F, double* R) {
+  double X[9], C[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) X[i] = F[i];
+  double nx = 0.0;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) nx += X[i] * X[i];
+  bool scaled = true;
+  for (int it = 0; it < 40; ++it) {
+    double det = cofactor(X, C);
+    if (!(det > 1e-12 * nx * sqrt(nx))) return false;
+    double g = 1.0;
+    if (scaled) {
+      double nc = 0.0;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) nc += C[i] * C[i];
+      g = sqrt(sqrt(nc / nx) / det);
+    }
+    double a = 0.5 * g, b = 0.5 / (g * det), d2 = 0.0, nn = 0.0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      double v = a * X[i] + b * C[i];
+      double dv = v - X[i];
+      d2 += dv * dv;
+      nn += v * v;
+      X[i] = v;
+    }
+    nx = nn;
+    if (d2 < 1e-4) scaled = false;
+    if (d2 < 1e-20) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) R[i] = X[i];
+      return true;
+    }
+  }
+  return false;
+}
+
+// Closest rotation through the eigen-decomposition of F^T F (cyclic Jacobi):
+// R = [u1 u2 u1 x u2] [v1 v2 v1 x v2]^T with u_i = F v_i / sigma_i.  Used for
+// inverted, degenerate or badly conditioned F, where the smallest singular
+// direction is the one that gets flipped.
+__device__ void polar_jacobi(const double* F, double* R) {
+  double S[3][3], V[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      S[i][j] = F[0 * 3 + i] * F[0 * 3 + j] + F[1 * 3 + i] * F[1 * 3 + j] + F[2 * 3 + i] * F[2 * 3 + j];
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    double off = S[0][1] * S[0][1] + S[0][2] * S[0][2] + S[1][2] * S[1][2];
+    double dia = S[0][0] * S[0][0] + S[1][1] * S[1][1] + S[2][2] * S[2][2];
+    if (off <= 1e-34 * dia || off == 0.0) break;
+    for (int pq = 0; pq < 3; ++pq) {
+      int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
+      double apq = S[p][q];
+      if (apq == 0.0) continue;
+      double theta = (S[q][q] - S[p][p]) / (2.0 * apq);
+      double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+      double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+      for (int k = 0; k < 3; ++k) {  // S <- J^T S J, J = rotation in (p,q)
+        double skp = S[k][p], skq = S[k][q];
+        S[k][p] = c * skp - s * skq;
+        S[k][q] = s * skp + c * skq;
+      }
+      for (int k = 0; k < 3; ++k) {
+        double spk = S[p][k], sqk = S[q][k];
+        S[p][k] = c * spk - s * sqk;
+        S[q][k] = s * spk + c * sqk;
+      }
+      for (int k = 0; k < 3; ++k) {
+        double vkp = V[k][p], vkq = V[k][q];
+        V[k][p] = c * vkp - s * vkq;
+        V[k][q] = s * vkp + c * vkq;
+      }
+    }
+  }
+  // sort eigenvalues descending
+  int o[3] = {0, 1, 2};
+  double lam[3] = {S[0][0], S[1][1], S[2][2]};
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2 - i; ++j)
+      if (lam[o[j]] < lam[o[j + 1]]) { int t = o[j]; o[j] = o[j + 1]; o[j + 1] = t; }
+  double v1[3] = {V[0][o[0]], V[1][o[0]], V[2][o[0]]};
+  double v2[3] = {V[0][o[1]], V[1][o[1]], V[2][o[1]]};
+  double u1[3], u2[3];
+  for (int i = 0; i < 3; ++i) {
+    u1[i] = F[3 * i] * v1[0] + F[3 * i + 1] * v1[1] + F[3 * i + 2] * v1[2];
+    u2[i] = F[3 * i] * v2[0] + F[3 * i + 1] * v2[1] + F[3 * i + 2] * v2[2];
+  }
+  double n1 = sqrt(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
+  if (!(n1 > 1e-300)) {
+    for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0) ? 1.0 : 0.0;
+    return;
+  }
+  for (int i = 0; i < 3; ++i) u1[i] /= n1;
+  double d = u1[0] * u2[0] + u1[1] * u2[1] + u1[2] * u2[2];
+  for (int i = 0; i < 3; ++i) u2[i] -= d * u1[i];
+  double n2 = sqrt(u2[0] * u2[0] + u2[1] * u2[1] + u2[2] * u2[2]);
+  if (!(n2 > 1e-14 * n1)) {  // rank one: any unit vector orthogonal to u1
+    double e[3] = {0, 0, 0};
+    int k = fabs(u1[0]) < fabs(u1[1]) ? (fabs(u1[0]) < fabs(u1[2]) ? 0 : 2) : (fabs(u1[1]) < fabs(u1[2]) ? 1 : 2);
+    e[k] = 1.0;
+    double dd = u1[k];
+    for (int i = 0; i < 3; ++i) u2[i] = e[i] - dd * u1[i];
+    n2 = sqrt(u2[0] * u2[0] + u2[1] * u2[1] + u2[2] * u2[2]);
+  }
+  for (int i = 0; i < 3; ++i) u2[i] /= n2;
+  double u3[3] = {u1[1] * u2[2] - u1[2] * u2[1], u1[2] * u2[0] - u1[0] * u2[2], u1[0] * u2[1] - u1[1] * u2[0]};
+  double v3[3] = {v1[1] * v2[2] - v1[2] * v2[1], v1[2] * v2[0] - v1[0] * v2[2], v1[0] * v2[1] - v1[1] * v2[0]};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) R[3 * i + j] = u1[i] * v1[j] + u2[i] * v2[j] + u3[i] * v3[j];
+}
+
+__global__ void k_polar_forces(int64_t count, const int4* __restrict__ tets,
+                               const double* __restrict__ Dm, const double* __restrict__ w,
+                               const double* __restrict__ x, double* __restrict__ fe,
+                               double* __restrict__ Rout) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= count) return;
+  int4 t = tets[e];
+  double p0[3], D[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) p0[i] = __ldg(x + 3 * (int64_t)t.x + i);
+  const int vid[3] = {t.y, t.z, t.w};
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) D[3 * i + c] = __ldg(x + 3 * (int64_t)vid[c] + i) - p0[i];
+  double Mi[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) Mi[i] = __ldg(Dm + i * count + e);
+  double F[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) F[3 * i + j] = D[3 * i] * Mi[j] + D[3 * i + 1] * Mi[3 + j] + D[3 * i + 2] * Mi[6 + j];
+  double R[9];
+  if (!polar_newton(F, R)) polar_jacobi(F, R);
+  double we = __ldg(w + e);
+  double f[4][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    double P0 = F[3 * i] - R[3 * i], P1 = F[3 * i + 1] - R[3 * i + 1], P2 = F[3 * i + 2] - R[3 * i + 2];
+#pragma unroll
+    for (int a = 1; a < 4; ++a)
+      f[a][i] = -we * (P0 * Mi[3 * (a - 1)] + P1 * Mi[3 * (a - 1) + 1] + P2 * Mi[3 * (a - 1) + 2]);
+    f[0][i] = -(f[1][i] + f[2][i] + f[3][i]);
+  }
+  double* o = fe + 12 * e;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) o[3 * a + i] = f[a][i];
+  if (Rout) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Rout[9 * e + i] = R[i];
+  }
+}
+
+__global__ void k_gather(int64_t nt, const int64_t* __restrict__ ptr, const int32_t* __restrict__ slot,
+                         const double* __restrict__ fe, double* __restrict__ out,
+                         const double* __restrict__ add, const double* __restrict__ mass_h2,
+                         const double* __restrict__ x, const double* __restrict__ y,
+                         const int32_t* __restrict__ node, int64_t lim) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  double s0 = 0, s1 = 0, s2 = 0;
+  for (int64_t q = ptr[t]; q < ptr[t + 1]; ++q) {
+    const double* p = fe + 3 * (int64_t)slot[q];
+    s0 += p[0]; s1 += p[1]; s2 += p[2];
+  }
+  if (add) { s0 += add[3 * t]; s1 += add[3 * t + 1]; s2 += add[3 * t + 2]; }
+  if (mass_h2 && t < lim) {
+    int64_t v = node[t];
+    double mh = mass_h2[t];
+    s0 -= mh * (x[3 * v] - y[3 * t]);
+    s1 -= mh * (x[3 * v + 1] - y[3 * t + 1]);
+    s2 -= mh * (x[3 * v + 2] - y[3 * t + 2]);
+  }
+  out[3 * t] = s0; out[3 * t + 1] = s1; out[3 * t + 2] = s2;
+}
+
+__global__ void k_gather_rows(int64_t cnt, const int32_t* idx, const double* x, double* out) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= cnt) return;
+  int64_t v = idx[i];
+  out[3 * i] = x[3 * v]; out[3 * i + 1] = x[3 * v + 1]; out[3 * i + 2] = x[3 * v + 2];
+}
+
+__global__ void k_scatter_rows(int64_t cnt, const int32_t* idx, const double* v, double* x) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= cnt) return;
+  int64_t r = idx[i];
+  x[3 * r] = v[3 * i]; x[3 * r + 1] = v[3 * i + 1]; x[3 * r + 2] = v[3 * i + 2];
+}
+
+__global__ void k_axpby(int64_t n, double a, const double* x, double b, double* y) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = a * x[i] + b * y[i];
+}
+
+__global__ void k_inner_update(int64_t m, const double* u2, const double* Sau, const int32_t* region,
+                               double* x, double* U2, double* ft2) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  int64_t v = region[i];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    double du = u2[3 * i + c];
+    x[3 * v + c] += du;
+    U2[3 * i + c] += du;
+    ft2[3 * i + c] -= Sau[3 * i + c];
+  }
+}
+
+__global__ void k_apply_interior(int64_t n1, const double* u, const int32_t* node, double* x) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n1) return;
+  int64_t v = node[p];
+  x[3 * v] += u[3 * p]; x[3 * v + 1] += u[3 * p + 1]; x[3 * v + 2] += u[3 * p + 2];
+}
+
+inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+void polar_forces(int64_t count, const int4* tets, const double* Dm, const double* w, const double* x,
+                  double* fe, double* R_out, cudaStream_t st) {
+  if (count <= 0) return;
+  k_polar_forces<<<nblk(count, 128), 128, 0, st>>>(count, tets, Dm, w, x, fe, R_out);
+}
+
+void gather_forces(int64_t nt, const int64_t* ptr, const int32_t* slot, const double* fe, double* out,
+                   const double* add, const double* mass_h2, const double* x, const double* y,
+                   const int32_t* node, int64_t lim, cudaStream_t st) {
+  if (nt <= 0) return;
+  k_gather<<<nblk(nt, 256), 256, 0, st>>>(nt, ptr, slot, fe, out, add, mass_h2, x, y, node, lim);
+}
+
+void gather_rows(int64_t cnt, const int32_t* idx, const double* x, double* out, cudaStream_t st) {
+  if (cnt > 0) k_gather_rows<<<nblk(cnt, 256), 256, 0, st>>>(cnt, idx, x, out);
+}
+void scatter_rows(int64_t cnt, const int32_t* idx, const double* v, double* x, cudaStream_t st) {
+  if (cnt > 0) k_scatter_rows<<<nblk(cnt, 256), 256, 0, st>>>(cnt, idx, v, x);
+}
+void axpby(int64_t n, double a, const double* x, double b, double* y, cudaStream_t st) {
+  if (n > 0) k_axpby<<<nblk(n, 256), 256, 0, st>>>(n, a, x, b, y);
+}
+void inner_update(int64_t m, const double* u2, const double* Sau, const int32_t* region, double* x,
+                  double* U2, double* ft2, cudaStream_t st) {
+  if (m > 0) k_inner_update<<<nblk(m, 256), 256, 0, st>>>(m, u2, Sau, region, x, U2, ft2);
+}
+void apply_interior(int64_t n1, const double* u, const int32_t* node, double* x, cudaStream_t st) {
+  if (n1 > 0) k_apply_interior<<<nblk(n1, 256), 256, 0, st>>>(n1, u, node, x);
+}
+
+}  // namespace pdk

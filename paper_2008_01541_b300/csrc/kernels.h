@@ -1,0 +1,75 @@
+// Launch wrappers of the CUDA kernels (plain pointers, one stream each).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pdk {
+
+// ---- local step (Section 2.2) -------------------------------------------
+// For each element e of a set: F = Ds Dm^-1, R = polar(F) in SO(3),
+// fe[e][a][:] = forces on its four vertices, f_a = -w_e (F - R) G_a^T
+// (w_e = 2 mu Vol_e).  R_out (optional) receives R row-major [count][9].
+void polar_forces(int64_t count, const int4* tets, const double* DminvSoA, const double* w,
+                  const double* x, double* fe, double* R_out, cudaStream_t st);
+
+// out[t][:] = sum over the slots of target t of fe[slot][:]  (+ inertia if
+// mass_h2 != null and t < inertia_limit: - mass_h2[t] (x[node(t)] - y[t]))
+void gather_forces(int64_t ntarget, const int64_t* ptr, const int32_t* slot, const double* fe,
+                   double* out, const double* add /*[ntarget][3] or null*/,
+                   const double* mass_h2, const double* x, const double* y, const int32_t* node_of_t,
+                   int64_t inertia_limit, cudaStream_t st);
+
+// ---- supernodal triangular solves with L_1 / L_21 (Section 3.2, Steps 1 and 3)
+struct SparseFactor {
+  int64_t n1 = 0, nfree = 0, nsn = 0, nlevels = 0;
+  const int32_t* col0 = nullptr;     // [nsn+1]
+  const int64_t* rowptr = nullptr;   // [nsn+1]
+  const int32_t* rows = nullptr;
+  const int64_t* valptr = nullptr;   // [nsn+1]
+  const double* L = nullptr;
+  // per-level work lists (host offsets, device items)
+  const int64_t* lvl_col_ptr = nullptr;  // host [nlevels+1] into col items
+  const int64_t* lvl_row_ptr = nullptr;  // host [nlevels+1] into row items
+  const int32_t* col_sn = nullptr;  const int32_t* col_i = nullptr;   // device items: (supernode, column)
+  const int32_t* row_sn = nullptr;  const int32_t* row_r = nullptr;   // device items: (supernode, off-diag row)
+};
+// b [nfree][3] in: forces (factor order).  Out: y[0..n1) = L_1^-1 b_1 and
+// b[n1..nfree) = b_2 - L_21 y_1.
+void sparse_forward(const SparseFactor& f, double* b, double* y, cudaStream_t st);
+// u[n1..nfree) must hold U_2.  Out: u[0..n1) = L_1^-T (y_1 - L_21^T U_2).
+void sparse_backward(const SparseFactor& f, const double* y, double* u, double* z, cudaStream_t st);
+
+// ---- dense collision-region block (Section 3.3) ---------------------------
+// H (mp x mp, column-major, lower) = Sigma0 (m x m) padded with identity.
+void copy_sigma(const double* Sigma0, int64_t m, double* H, int64_t mp, cudaStream_t st);
+// H[ra][rb] += c_j w_a w_b for the k springs (region indices, -1 = unused)
+void contact_scatter(int64_t k, const int32_t* cidx, const double* cw, const double* cs,
+                     double* H, int64_t mp, cudaStream_t st);
+// g[r][:] += -w_a c_j (p_j - t_j) with p_j = sum_a w_a x[region[r_a]]
+void contact_forces(int64_t k, const int32_t* cidx, const double* cw, const double* ct,
+                    const double* cs, const int32_t* region, const double* x, double* g,
+                    cudaStream_t st);
+// Blocked right-looking FP64 Cholesky of the padded H (tile 64). Linv receives
+// the inverses of the diagonal tiles; status[0] = first failing column + 1.
+void cholesky_fp64(double* H, int64_t mp, double* Linv, int* status, cudaStream_t st);
+// Solve (L L^T) u = g for 3 right-hand sides, g/u [m][3] (padded internally).
+void chol_solve_fp64(const double* H, int64_t mp, const double* Linv, const double* g, double* u,
+                     int64_t m, double* work /*[mp][3] x 2*/, cudaStream_t st);
+// out[i][:] = sum_j S[i][j] v[j][:]  (S symmetric m x m, full storage), FP64
+void symv3(const double* S, int64_t m, const double* v, double* out, cudaStream_t st);
+// out[i][:] += alpha * sum_j B[i][j] v[j][:]  (CSC of a symmetric pattern)
+void spmv3(int64_t m, const int64_t* ptr, const int32_t* row, const double* val, const double* v,
+           double alpha, double* out, cudaStream_t st);
+// Algorithm 1, 4.6-4.7: x2 += u2, U2 += u2, ft2 -= (Su - Bu)   (Bu already in Su: Su holds Sigma_alpha u)
+void inner_update(int64_t m, const double* u2, const double* Sau, const int32_t* region, double* x,
+                  double* U2, double* ft2, cudaStream_t st);
+// x[node_of_pos[p]] += u[p] for p < n1
+void apply_interior(int64_t n1, const double* u, const int32_t* node_of_pos, double* x, cudaStream_t st);
+// out[i] = x[idx[i]]  (3 doubles each)
+void gather_rows(int64_t cnt, const int32_t* idx, const double* x, double* out, cudaStream_t st);
+// x[idx[i]] = v[i]
+void scatter_rows(int64_t cnt, const int32_t* idx, const double* v, double* x, cudaStream_t st);
+// y = a*x + b*y elementwise over n doubles
+void axpby(int64_t n, double a, const double* x, double b, double* y, cudaStream_t st);
+
+}  // namespace pdk

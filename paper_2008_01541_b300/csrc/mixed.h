@@ -1,0 +1,8 @@
+// Mixed-precision and PCG forms of the collision-region solve H u = g.
+#pragma once
+#include "pd.h"
+struct pd_solver;
+namespace pdm {
+pd_status mixed_solve(pd_solver* s, const double* g, const double* u0, double* u);
+void mixed_free(pd_solver* s);
+}  // namespace pdm

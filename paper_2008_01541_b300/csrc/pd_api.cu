@@ -1,0 +1,626 @@
+// The C ABI (include/pd.h): solver state on the device and the orchestration
+// of Algorithm 1 (Section 3.4) over the kernels of k_local.cu, k_sparse.cu,
+// k_dense.cu and k_mixed.cu.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "host_setup.h"
+#include "kernels.h"
+#include "mixed.h"
+#include "pd.h"
+#include "solver.h"
+
+using pdk::SparseFactor;
+
+namespace {
+
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------- helpers
+#define CK(call)                                                           \
+  do {                                                                     \
+    cudaError_t e_ = (call);                                               \
+    if (e_ != cudaSuccess) {                                               \
+      s->err = std::string(#call) + ": " + cudaGetErrorString(e_);          \
+      return e_ == cudaErrorMemoryAllocation ? PD_ERR_OOM : PD_ERR_CUDA;   \
+    }                                                                      \
+  } while (0)
+
+template <class T>
+static cudaError_t dalloc(pd_solver* s, T** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+  if (e == cudaSuccess) s->allocs.push_back((void*)*p);
+  return e;
+}
+
+template <class T>
+static cudaError_t dupload(pd_solver* s, T** p, const T* h, size_t n) {
+  cudaError_t e = dalloc(s, p, n);
+  if (e != cudaSuccess) return e;
+  if (n) e = cudaMemcpy(*p, h, n * sizeof(T), cudaMemcpyHostToDevice);
+  return e;
+}
+
+static pd_status build_elemset(pd_solver* s, const pdh::Setup& h, const int32_t* tets,
+                               const std::vector<int32_t>& elems, ElemSet& es) {
+  const int64_t c = (int64_t)elems.size();
+  es.count = c;
+  std::vector<int4> t(c);
+  std::vector<double> Dm(9 * c), w(c);
+  for (int64_t i = 0; i < c; ++i) {
+    int32_t e = elems[i];
+    t[i] = make_int4(tets[4 * e], tets[4 * e + 1], tets[4 * e + 2], tets[4 * e + 3]);
+    for (int q = 0; q < 9; ++q) Dm[q * c + i] = h.Dminv[9 * (int64_t)e + q];
+    w[i] = 2.0 * s->mu * h.vol[e];
+  }
+  CK(dupload(s, &es.tets, t.data(), c));
+  CK(dupload(s, &es.Dm, Dm.data(), 9 * c));
+  CK(dupload(s, &es.w, w.data(), c));
+  CK(dalloc(s, &es.fe, 12 * c));
+  return PD_OK;
+}
+
+static pd_status upload_gather(pd_solver* s, ElemSet& es, int64_t nt, const std::vector<int64_t>& ptr,
+                               const std::vector<int32_t>& slot) {
+  es.nt = nt;
+  CK(dupload(s, &es.gptr, ptr.data(), ptr.size()));
+  CK(dupload(s, &es.gslot, slot.data(), slot.size()));
+  return PD_OK;
+}
+
+// ----------------------------------------------------------------- timing
+void pd_solver::tbegin(int phase) {
+  if (!opt.timing) return;
+  if (ev_used + 2 > (int)events.size()) {
+    for (int i = 0; i < 64; ++i) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      events.push_back(e);
+    }
+  }
+  cudaEventRecord(events[ev_used], stream);
+  marks.push_back({phase, ev_used});
+  ev_used += 2;
+}
+
+void pd_solver::tend() {
+  if (!opt.timing || marks.empty()) return;
+  cudaEventRecord(events[marks.back().second + 1], stream);
+}
+
+void pd_solver::tcollect(double* out /*[8]*/) {
+  for (int i = 0; i < 8; ++i) out[i] = 0.0;
+  if (!opt.timing) return;
+  cudaStreamSynchronize(stream);
+  for (auto& mk : marks) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, events[mk.second], events[mk.second + 1]);
+    out[mk.first] += ms;
+  }
+  marks.clear();
+  ev_used = 0;
+}
+
+// ----------------------------------------------------------------- the region solve
+// H = Sigma_0 + C_22; factor; solve H u = g (Algorithm 1, 4.3 and 4.5).
+pd_status pd_solver::region_solve(const double* g_dev, const double* u0_dev, double* u_dev) {
+  if (precision == PD_FP64) {
+    tbegin(2);
+    pdk::copy_sigma(Sigma0, m, H, mp, stream);
+    pdk::contact_scatter(k, c_idx, c_w, c_s, H, mp, stream);
+    tend();
+    tbegin(4);
+    pdk::cholesky_fp64(H, mp, Linv, status, stream);
+    pdk::chol_solve_fp64(H, mp, Linv, g_dev, u_dev, m, work, stream);
+    tend();
+    last_refine = 0;
+    return PD_OK;
+  }
+  return pdm::mixed_solve(this, g_dev, u0_dev, u_dev);
+}
+
+// ----------------------------------------------------------------- C ABI
+extern "C" {
+
+static thread_local std::string g_setup_error;
+
+pd_status pd_setup(const pd_mesh* mesh, const pd_material* mat, double dt, const int32_t* region, int64_t m,
+                   const int32_t* dirichlet, int64_t nd, const pd_options* opts, pd_solver** out) {
+  double t0 = now_ms();
+  if (out) *out = nullptr;
+  g_setup_error.clear();
+  if (!mesh || !mat || !out || !mesh->rest_pos || !mesh->tets || (!region && m > 0) || (!dirichlet && nd > 0) ||
+      nd < 0 || m < 0 || !(dt >= 0) || !std::isfinite(dt)) {
+    g_setup_error = "invalid argument";
+    return PD_ERR_INVALID_ARG;
+  }
+  pd_solver* s = nullptr;
+  try {
+    s = new pd_solver();
+  } catch (...) {
+    g_setup_error = "host allocation failed";
+    return PD_ERR_OOM;
+  }
+  if (opts) s->opt = *opts;
+  if (s->opt.tol <= 0) s->opt.tol = 1e-10;
+  if (s->opt.max_refine <= 0) s->opt.max_refine = 50;
+  if (s->opt.inner_iters <= 0) s->opt.inner_iters = 1;
+  if (s->opt.precision < PD_FP64 || s->opt.precision > PD_PCG_WARM) {
+    g_setup_error = "unknown precision";
+    delete s;
+    return PD_ERR_INVALID_ARG;
+  }
+  s->precision = s->opt.precision;
+  s->mu = mat->mu; s->density = mat->density; s->dt = dt;
+  pdh::Input in;
+  in.n = mesh->n_nodes; in.E = mesh->n_tets; in.X = mesh->rest_pos; in.tets = mesh->tets;
+  in.mu = mat->mu; in.density = mat->density; in.dt = dt;
+  in.region = region; in.m = m; in.dirichlet = dirichlet; in.nd = nd;
+  pdh::Setup h;
+  std::string err;
+  int st;
+  try {
+    st = pdh::build(in, h, &err);
+  } catch (...) {
+    st = PD_ERR_OOM;
+    err = "host allocation failed during setup";
+  }
+  if (st) {
+    g_setup_error = err;
+    delete s;
+    return (pd_status)st;
+  }
+  pd_status rs = s->upload(h, in);
+  if (rs != PD_OK) {
+    g_setup_error = s->err;
+    pd_destroy(s);
+    return rs;
+  }
+  s->stats.setup_ms = now_ms() - t0;
+  s->setup_log = h.log;
+  *out = s;
+  return PD_OK;
+}
+
+pd_status pd_set_dirichlet(pd_solver* s, const double* pos) {
+  if (!s) return PD_ERR_INVALID_ARG;
+  if (!pos && s->nd > 0) { s->err = "pos is NULL"; return PD_ERR_INVALID_ARG; }
+  for (int64_t i = 0; i < 3 * s->nd; ++i)
+    if (!std::isfinite(pos[i])) { s->err = "non-finite Dirichlet position"; return PD_ERR_INVALID_ARG; }
+  if (s->nd > 0) CK(cudaMemcpyAsync(s->dpos, pos, sizeof(double) * 3 * s->nd, cudaMemcpyHostToDevice, s->stream));
+  s->dirichlet_pending = true;
+  return PD_OK;
+}
+
+pd_status pd_set_contacts(pd_solver* s, int64_t k, const int32_t* nodes, const double* w, const double* target,
+                          const double* stiffness) {
+  if (!s) return PD_ERR_INVALID_ARG;
+  if (k < 0 || (k > 0 && (!nodes || !w || !target || !stiffness))) { s->err = "invalid contact arrays"; return PD_ERR_INVALID_ARG; }
+  std::vector<int32_t> idx(4 * k);
+  for (int64_t j = 0; j < k; ++j) {
+    if (!std::isfinite(stiffness[j])) { s->err = "non-finite stiffness"; return PD_ERR_INVALID_ARG; }
+    for (int a = 0; a < 3; ++a)
+      if (!std::isfinite(target[3 * j + a])) { s->err = "non-finite target"; return PD_ERR_INVALID_ARG; }
+    for (int a = 0; a < 4; ++a) {
+      int32_t v = nodes[4 * j + a];
+      if (v < 0) {
+        if (w[4 * j + a] != 0.0) { s->err = "unused contact slot with nonzero weight"; return PD_ERR_INVALID_ARG; }
+        idx[4 * j + a] = -1;
+        continue;
+      }
+      if (v >= s->n || s->region_index[v] < 0) {
+        s->err = "contact " + std::to_string(j) + " names node " + std::to_string(v) + " outside the region";
+        return PD_ERR_CONTACT_OUTSIDE_REGION;
+      }
+      if (!std::isfinite(w[4 * j + a])) { s->err = "non-finite weight"; return PD_ERR_INVALID_ARG; }
+      idx[4 * j + a] = s->region_index[v];
+    }
+  }
+  if (k > s->kcap) {
+    int64_t cap = std::max<int64_t>(k, 2 * s->kcap);
+    int32_t* ni; double *nw, *nt, *ns;
+    CK(cudaMalloc(&ni, sizeof(int32_t) * 4 * cap));
+    CK(cudaMalloc(&nw, sizeof(double) * 4 * cap));
+    CK(cudaMalloc(&nt, sizeof(double) * 3 * cap));
+    CK(cudaMalloc(&ns, sizeof(double) * cap));
+    cudaFree(s->c_idx); cudaFree(s->c_w); cudaFree(s->c_t); cudaFree(s->c_s);
+    s->c_idx = ni; s->c_w = nw; s->c_t = nt; s->c_s = ns;
+    s->kcap = cap;
+  }
+  if (k > 0) {
+    CK(cudaMemcpyAsync(s->c_idx, idx.data(), sizeof(int32_t) * 4 * k, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->c_w, w, sizeof(double) * 4 * k, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->c_t, target, sizeof(double) * 3 * k, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->c_s, stiffness, sizeof(double) * k, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));  // host arrays may be freed by the caller on return
+  }
+  s->k = k;
+  return PD_OK;
+}
+
+pd_status pd_step(pd_solver* s, int outer_iters, pd_contact_cb cb, void* user) {
+  if (!s || outer_iters < 0) return PD_ERR_INVALID_ARG;
+  return s->step(outer_iters, cb, user);
+}
+
+pd_status pd_get_positions(const pd_solver* cs, double* out) {
+  pd_solver* s = const_cast<pd_solver*>(cs);
+  if (!s || !out) return PD_ERR_INVALID_ARG;
+  CK(cudaMemcpyAsync(out, s->x, sizeof(double) * 3 * s->n, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  return PD_OK;
+}
+
+pd_status pd_get_positions_dev(const pd_solver* cs, double* out) {
+  pd_solver* s = const_cast<pd_solver*>(cs);
+  if (!s || !out) return PD_ERR_INVALID_ARG;
+  CK(cudaMemcpyAsync(out, s->x, sizeof(double) * 3 * s->n, cudaMemcpyDeviceToDevice, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  return PD_OK;
+}
+
+pd_status pd_get_state(const pd_solver* cs, double* x, double* v) {
+  pd_solver* s = const_cast<pd_solver*>(cs);
+  if (!s || !x) return PD_ERR_INVALID_ARG;
+  CK(cudaMemcpyAsync(x, s->x, sizeof(double) * 3 * s->n, cudaMemcpyDeviceToHost, s->stream));
+  if (v) CK(cudaMemcpyAsync(v, s->v, sizeof(double) * 3 * s->n, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  return PD_OK;
+}
+
+pd_status pd_set_state(pd_solver* s, const double* x, const double* v) {
+  if (!s || !x) return PD_ERR_INVALID_ARG;
+  for (int64_t i = 0; i < 3 * s->n; ++i)
+    if (!std::isfinite(x[i]) || (v && !std::isfinite(v[i]))) { s->err = "non-finite state"; return PD_ERR_INVALID_ARG; }
+  CK(cudaMemcpyAsync(s->x, x, sizeof(double) * 3 * s->n, cudaMemcpyHostToDevice, s->stream));
+  if (v) CK(cudaMemcpyAsync(s->v, v, sizeof(double) * 3 * s->n, cudaMemcpyHostToDevice, s->stream));
+  else CK(cudaMemsetAsync(s->v, 0, sizeof(double) * 3 * s->n, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  return PD_OK;
+}
+
+pd_status pd_get_stats(const pd_solver* s, pd_stats* out) {
+  if (!s || !out) return PD_ERR_INVALID_ARG;
+  *out = s->stats;
+  return PD_OK;
+}
+
+const char* pd_last_error(const pd_solver* s) {
+  if (!s) return g_setup_error.c_str();
+  return s->err.c_str();
+}
+
+void pd_destroy(pd_solver* s) {
+  if (!s) return;
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  for (void* p : s->allocs) cudaFree(p);
+  cudaFree(s->c_idx); cudaFree(s->c_w); cudaFree(s->c_t); cudaFree(s->c_s);
+  if (s->x2_host) cudaFreeHost(s->x2_host);
+  if (s->status_h) cudaFreeHost(s->status_h);
+  pdm::mixed_free(s);
+  for (auto e : s->events) cudaEventDestroy(e);
+  if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+  delete s;
+}
+
+pd_status pd_local_step(pd_solver* s, const double* x, double* R_out, double* f_out) {
+  if (!s || !x) return PD_ERR_INVALID_ARG;
+  pd_status r = s->ensure_all_elements();
+  if (r != PD_OK) return r;
+  double *xd = nullptr, *Rd = nullptr, *fd = nullptr;
+  CK(cudaMalloc(&xd, sizeof(double) * 3 * s->n));
+  CK(cudaMalloc(&fd, sizeof(double) * 3 * s->n));
+  if (R_out) CK(cudaMalloc(&Rd, sizeof(double) * 9 * s->E));
+  CK(cudaMemcpyAsync(xd, x, sizeof(double) * 3 * s->n, cudaMemcpyHostToDevice, s->stream));
+  pdk::polar_forces(s->all.count, s->all.tets, s->all.Dm, s->all.w, xd, s->all.fe, Rd, s->stream);
+  pdk::gather_forces(s->n, s->all.gptr, s->all.gslot, s->all.fe, fd, nullptr, nullptr, nullptr, nullptr,
+                     nullptr, 0, s->stream);
+  CK(cudaGetLastError());
+  if (f_out) CK(cudaMemcpyAsync(f_out, fd, sizeof(double) * 3 * s->n, cudaMemcpyDeviceToHost, s->stream));
+  if (R_out) CK(cudaMemcpyAsync(R_out, Rd, sizeof(double) * 9 * s->E, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  cudaFree(xd); cudaFree(fd); if (Rd) cudaFree(Rd);
+  return PD_OK;
+}
+
+pd_status pd_get_schur(const pd_solver* cs, double* out) {
+  pd_solver* s = const_cast<pd_solver*>(cs);
+  if (!s || !out) return PD_ERR_INVALID_ARG;
+  CK(cudaMemcpyAsync(out, s->Sigma0, sizeof(double) * s->m * s->m, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  return PD_OK;
+}
+
+pd_status pd_schur_solve_dev(pd_solver* s, const double* g_dev, const double* u0_dev, double* u_dev) {
+  if (!s || !g_dev || !u_dev) return PD_ERR_INVALID_ARG;
+  CK(cudaMemsetAsync(s->status, 0, sizeof(int) * 4, s->stream));
+  pd_status r = s->region_solve(g_dev, u0_dev, u_dev);
+  if (r != PD_OK) return r;
+  CK(cudaGetLastError());
+  return s->check_status();
+}
+
+pd_status pd_schur_solve(pd_solver* s, const double* g, const double* u0, double* u) {
+  if (!s || !g || !u) return PD_ERR_INVALID_ARG;
+  CK(cudaMemcpyAsync(s->g, g, sizeof(double) * 3 * s->m, cudaMemcpyHostToDevice, s->stream));
+  if (u0) CK(cudaMemcpyAsync(s->u0, u0, sizeof(double) * 3 * s->m, cudaMemcpyHostToDevice, s->stream));
+  pd_status r = pd_schur_solve_dev(s, s->g, u0 ? s->u0 : nullptr, s->u2);
+  double ph[8];
+  s->tcollect(ph);
+  s->stats.ms_contact_update = ph[2];
+  s->stats.ms_factor_solve = ph[4];
+  if (r != PD_OK) return r;
+  CK(cudaMemcpyAsync(u, s->u2, sizeof(double) * 3 * s->m, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  return PD_OK;
+}
+
+pd_status pd_set_precision(pd_solver* s, int precision) {
+  if (!s || precision < PD_FP64 || precision > PD_PCG_WARM) return PD_ERR_INVALID_ARG;
+  s->precision = precision;
+  return PD_OK;
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------------- solver methods
+pd_status pd_solver::check_status() {
+  pd_solver* s = this;
+  CK(cudaMemcpyAsync(status_h, status, sizeof(int) * 4, cudaMemcpyDeviceToHost, stream));
+  CK(cudaStreamSynchronize(stream));
+  if (status_h[0] != 0) {
+    err = "Cholesky pivot " + std::to_string(status_h[0] - 1) + " of the collision-region matrix is not positive";
+    return PD_ERR_NOT_SPD;
+  }
+  if (status_h[1] != 0) {
+    err = "a bounded device wait gave up (code " + std::to_string(status_h[1]) + ")";
+    return PD_ERR_TIMEOUT;
+  }
+  if (status_h[2] != 0) {
+    err = "refinement did not reach tol within max_refine";
+    return PD_ERR_NO_CONVERGENCE;
+  }
+  return PD_OK;
+}
+
+pd_status pd_solver::ensure_all_elements() {
+  if (all.count > 0) return PD_OK;
+  std::vector<int32_t> elems(E);
+  for (int64_t e = 0; e < E; ++e) elems[e] = (int32_t)e;
+  pd_status r = build_elemset(this, *hostdata, tets_h.data(), elems, all);
+  if (r != PD_OK) return r;
+  return upload_gather(this, all, n, hostdata->gall_ptr, hostdata->gall_slot);
+}
+
+pd_status pd_solver::upload(const pdh::Setup& h, const pdh::Input& in) {
+  pd_solver* s = this;
+  n = in.n; E = in.E; m = in.m; nd = in.nd; n1 = h.n1; nfree = h.nfree;
+  mp = ((m + 63) / 64) * 64;
+  CK(cudaGetDevice(&device));
+  if (opt.cuda_stream) {
+    stream = (cudaStream_t)opt.cuda_stream;
+    own_stream = false;
+  } else {
+    CK(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+    own_stream = true;
+  }
+  tets_h.assign(in.tets, in.tets + 4 * E);
+  region_h.assign(in.region, in.region + m);
+  region_index.assign(n, -1);
+  for (int64_t i = 0; i < m; ++i) region_index[in.region[i]] = (int32_t)i;
+  hostdata.reset(new pdh::Setup());
+  hostdata->Dminv = h.Dminv;
+  hostdata->vol = h.vol;
+  hostdata->gall_ptr = h.gall_ptr;
+  hostdata->gall_slot = h.gall_slot;
+  // state
+  CK(dupload(s, &x, in.X, 3 * n));
+  CK(dalloc(s, &v, 3 * n));
+  CK(cudaMemset(v, 0, sizeof(double) * 3 * n));
+  CK(dalloc(s, &x_save, 3 * n));
+  CK(dalloc(s, &v_save, 3 * n));
+  CK(dalloc(s, &x_n, 3 * n));
+  CK(dalloc(s, &dpos, 3 * std::max<int64_t>(nd, 1)));
+  CK(dupload(s, &d_dirichlet, in.dirichlet, nd));
+  CK(dupload(s, &d_region, in.region, m));
+  CK(dupload(s, &d_node_of_pos, h.node_of_pos.data(), nfree));
+  if (nd > 0) {
+    std::vector<double> dp(3 * nd);
+    for (int64_t i = 0; i < nd; ++i)
+      for (int a = 0; a < 3; ++a) dp[3 * i + a] = in.X[3 * in.dirichlet[i] + a];
+    CK(cudaMemcpy(dpos, dp.data(), sizeof(double) * 3 * nd, cudaMemcpyHostToDevice));
+  }
+  if (dt > 0) {
+    std::vector<double> mh(nfree);
+    for (int64_t p = 0; p < nfree; ++p) mh[p] = h.mass[h.node_of_pos[p]] / (dt * dt);
+    CK(dupload(s, &mass_h2, mh.data(), nfree));
+    CK(dalloc(s, &y_in, 3 * nfree));
+    CK(dalloc(s, &tmp3, 3 * nfree));
+  }
+  // elements
+  pd_status r = build_elemset(s, h, in.tets, h.alpha, alpha);
+  if (r != PD_OK) return r;
+  r = upload_gather(s, alpha, nfree, h.ga_ptr, h.ga_slot);
+  if (r != PD_OK) return r;
+  r = build_elemset(s, h, in.tets, h.beta, beta);
+  if (r != PD_OK) return r;
+  r = upload_gather(s, beta, m, h.gb_ptr, h.gb_slot);
+  if (r != PD_OK) return r;
+  // sparse factor and per-level work lists
+  CK(dupload(s, &sn_col0, h.sn_col0.data(), h.sn_col0.size()));
+  CK(dupload(s, &sn_rowptr, h.sn_rowptr.data(), h.sn_rowptr.size()));
+  CK(dupload(s, &rows, h.rows.data(), h.rows.size()));
+  CK(dupload(s, &sn_valptr, h.sn_valptr.data(), h.sn_valptr.size()));
+  CK(dupload(s, &Lval, h.Lval.data(), h.Lval.size()));
+  {
+    int64_t nl = h.nlevels;
+    std::vector<std::vector<int32_t>> bylevel(nl);
+    for (int64_t k2 = 0; k2 < h.nsn; ++k2) bylevel[h.sn_level[k2]].push_back((int32_t)k2);
+    std::vector<int32_t> csn, ci, rsn, rr;
+    lvl_col_ptr.assign(nl + 1, 0);
+    lvl_row_ptr.assign(nl + 1, 0);
+    for (int64_t l = 0; l < nl; ++l) {
+      for (int32_t sn : bylevel[l]) {
+        int32_t nc = h.sn_col0[sn + 1] - h.sn_col0[sn];
+        int64_t nr = h.sn_rowptr[sn + 1] - h.sn_rowptr[sn];
+        for (int32_t i = 0; i < nc; ++i) { csn.push_back(sn); ci.push_back(i); }
+        for (int64_t q = 0; q < nr; ++q) { rsn.push_back(sn); rr.push_back((int32_t)q); }
+      }
+      lvl_col_ptr[l + 1] = (int64_t)csn.size();
+      lvl_row_ptr[l + 1] = (int64_t)rsn.size();
+    }
+    CK(dupload(s, &col_sn, csn.data(), csn.size()));
+    CK(dupload(s, &col_i, ci.data(), ci.size()));
+    CK(dupload(s, &row_sn, rsn.data(), rsn.size()));
+    CK(dupload(s, &row_r, rr.data(), rr.size()));
+    sf.n1 = n1; sf.nfree = nfree; sf.nsn = h.nsn; sf.nlevels = nl;
+    sf.col0 = sn_col0; sf.rowptr = sn_rowptr; sf.rows = rows; sf.valptr = sn_valptr; sf.L = Lval;
+    sf.lvl_col_ptr = lvl_col_ptr.data(); sf.lvl_row_ptr = lvl_row_ptr.data();
+    sf.col_sn = col_sn; sf.col_i = col_i; sf.row_sn = row_sn; sf.row_r = rr.empty() ? nullptr : row_r;
+    sf.row_r = row_r;
+  }
+  CK(dalloc(s, &b, 3 * nfree));
+  CK(dalloc(s, &yv, 3 * nfree));
+  CK(dalloc(s, &u, 3 * nfree));
+  CK(dalloc(s, &z, 3 * nfree));
+  // dense block
+  CK(dupload(s, &Sigma0, h.Sigma0.data(), (size_t)m * m));
+  CK(dupload(s, &b22_ptr, h.B22.colptr.data(), h.B22.colptr.size()));
+  CK(dupload(s, &b22_row, h.B22.row.data(), h.B22.row.size()));
+  CK(dupload(s, &b22_val, h.B22.val.data(), h.B22.val.size()));
+  CK(dalloc(s, &H, (size_t)mp * mp));
+  CK(dalloc(s, &Linv, (size_t)mp * 64));
+  CK(dalloc(s, &g, 3 * m));
+  CK(dalloc(s, &u0, 3 * m));
+  CK(dalloc(s, &u2, 3 * m));
+  CK(dalloc(s, &Sau, 3 * m));
+  CK(dalloc(s, &U2, 3 * m));
+  CK(dalloc(s, &work, 6 * mp));
+  CK(dalloc(s, &status, 4));
+  CK(cudaMemset(status, 0, sizeof(int) * 4));
+  CK(cudaMallocHost(&status_h, sizeof(int) * 4));
+  CK(cudaMallocHost(&x2_host, sizeof(double) * 3 * m));
+  CK(dalloc(s, &x2_dev, 3 * m));
+  stats.n_nodes = n; stats.n_tets = E; stats.n_free = nfree; stats.n1 = n1; stats.m = m;
+  stats.n_alpha = alpha.count; stats.n_beta = beta.count;
+  stats.n_supernodes = h.nsn; stats.n_levels = h.nlevels; stats.nnz_L = h.nnzL;
+  CK(cudaDeviceSynchronize());
+  return PD_OK;
+}
+
+// Algorithm 1 for one time step.
+pd_status pd_solver::step(int outer_iters, pd_contact_cb cb, void* user) {
+  pd_solver* s = this;
+  double t0 = now_ms();
+  marks.clear();
+  ev_used = 0;
+  CK(cudaMemsetAsync(status, 0, sizeof(int) * 4, stream));
+  CK(cudaMemcpyAsync(x_save, x, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, stream));
+  CK(cudaMemcpyAsync(v_save, v, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, stream));
+  if (dirichlet_pending) {
+    pdk::scatter_rows(nd, d_dirichlet, dpos, x, stream);
+    dirichlet_pending = false;
+  }
+  if (dt > 0) {
+    CK(cudaMemcpyAsync(x_n, x_save, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, stream));
+    // inertia target y = x_n + dt v_n, in factor order
+    pdk::gather_rows(nfree, d_node_of_pos, x_save, y_in, stream);
+    pdk::gather_rows(nfree, d_node_of_pos, v, tmp3, stream);
+    pdk::axpby(3 * nfree, dt, tmp3, 1.0, y_in, stream);
+  }
+  pd_status result = PD_OK;
+  int64_t inner_total = 0;
+  for (int it = 0; it < outer_iters && result == PD_OK; ++it) {
+    // 1-2: R_alpha and the alpha forces f_1, f_2^(alpha) (+ x_1 inertia)
+    tbegin(0);
+    pdk::polar_forces(alpha.count, alpha.tets, alpha.Dm, alpha.w, x, alpha.fe, nullptr, stream);
+    pdk::gather_forces(nfree, alpha.gptr, alpha.gslot, alpha.fe, b, nullptr, mass_h2, x, y_in,
+                       d_node_of_pos, n1, stream);
+    tend();
+    // 3: forward substitution; b[n1..] becomes f~_2 = y_2
+    tbegin(1);
+    pdk::sparse_forward(sf, b, yv, stream);
+    tend();
+    double* ft2 = b + 3 * n1;
+    CK(cudaMemsetAsync(U2, 0, sizeof(double) * 3 * m, stream));
+    for (int j = 0; j < opt.inner_iters; ++j) {
+      // 4.1 detection (host callback)
+      if (cb) {
+        pdk::gather_rows(m, d_region, x, x2_dev, stream);
+        CK(cudaMemcpyAsync(x2_host, x2_dev, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, stream));
+        CK(cudaStreamSynchronize(stream));
+        pd_status cr = cb(user, x2_host, this);
+        if (cr != PD_OK) {
+          if (err.empty()) err = "contact callback returned an error";
+          result = cr;
+          break;
+        }
+      }
+      // 4.2, 4.4: R_beta, g = f~_2 + f_2^(beta) (+ x_2 inertia) + f_2^(col)
+      tbegin(3);
+      pdk::polar_forces(beta.count, beta.tets, beta.Dm, beta.w, x, beta.fe, nullptr, stream);
+      pdk::gather_forces(m, beta.gptr, beta.gslot, beta.fe, g, ft2, mass_h2 ? mass_h2 + n1 : nullptr, x,
+                         y_in ? y_in + 3 * n1 : nullptr, d_region, m, stream);
+      pdk::contact_forces(k, c_idx, c_w, c_t, c_s, d_region, x, g, stream);
+      tend();
+      // 4.3, 4.5: H = Sigma_alpha + A22^beta + C22; solve H u2 = g
+      pd_status r = region_solve(g, nullptr, u2);
+      if (r != PD_OK) { result = r; break; }
+      // 4.6, 4.7: x2 += u2; f~_2 -= Sigma_alpha u2 (= Sigma_0 u2 - A22^beta u2 - M2/dt^2 u2)
+      tbegin(5);
+      pdk::symv3(Sigma0, m, u2, Sau, stream);
+      pdk::spmv3(m, b22_ptr, b22_row, b22_val, u2, -1.0, Sau, stream);
+      pdk::inner_update(m, u2, Sau, d_region, x, U2, ft2, stream);
+      tend();
+      ++inner_total;
+    }
+    if (result != PD_OK) break;
+    // 5: backward substitution u_1 = L_1^-T (y_1 - L_21^T U_2); x_1 += u_1
+    tbegin(6);
+    CK(cudaMemcpyAsync(u + 3 * n1, U2, sizeof(double) * 3 * m, cudaMemcpyDeviceToDevice, stream));
+    pdk::sparse_backward(sf, yv, u, z, stream);
+    pdk::apply_interior(n1, u, d_node_of_pos, x, stream);
+    tend();
+    stats.outer_done = it + 1;
+  }
+  cudaError_t ce = cudaGetLastError();
+  if (ce != cudaSuccess && result == PD_OK) {
+    err = std::string("kernel launch: ") + cudaGetErrorString(ce);
+    result = PD_ERR_CUDA;
+  }
+  if (result == PD_OK) result = check_status();
+  if (result == PD_OK && dt > 0) {
+    pdk::axpby(3 * n, 1.0 / dt, x, 0.0, v, stream);
+    pdk::axpby(3 * n, -1.0 / dt, x_n, 1.0, v, stream);
+  }
+  if (result != PD_OK) {  // roll back to the state before the call
+    cudaMemcpyAsync(x, x_save, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, stream);
+    cudaMemcpyAsync(v, v_save, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, stream);
+    cudaStreamSynchronize(stream);
+    return result;
+  }
+  double ph[8];
+  tcollect(ph);
+  stats.ms_local_alpha = ph[0]; stats.ms_forward = ph[1]; stats.ms_contact_update = ph[2];
+  stats.ms_local_beta = ph[3]; stats.ms_factor_solve = ph[4]; stats.ms_bookkeeping = ph[5];
+  stats.ms_backward = ph[6];
+  CK(cudaStreamSynchronize(stream));
+  stats.ms_step = now_ms() - t0;
+  stats.inner_done = inner_total;
+  stats.contacts = k;
+  stats.refine_iters = last_refine;
+  stats.residual = last_residual;
+  return PD_OK;
+}

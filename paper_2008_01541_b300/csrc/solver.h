@@ -1,0 +1,89 @@
+// Internal solver state behind the opaque pd_solver handle.
+#pragma once
+#include <cstdint>
+#include <memory>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "host_setup.h"
+#include "kernels.h"
+#include "pd.h"
+
+struct ElemSet {
+  int64_t count = 0;
+  int4* tets = nullptr;
+  double* Dm = nullptr;   // SoA [9][count]
+  double* w = nullptr;    // 2 mu Vol
+  double* fe = nullptr;   // [count][4][3]
+  int64_t nt = 0;
+  int64_t* gptr = nullptr;
+  int32_t* gslot = nullptr;
+};
+
+namespace pdm { struct MixedState; }
+
+struct pd_solver {
+  // configuration
+  pd_options opt{};
+  int precision = PD_FP64;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  double mu = 0, density = 0, dt = 0;
+  int64_t n = 0, E = 0, m = 0, nd = 0, n1 = 0, nfree = 0, mp = 0;
+  std::vector<int32_t> tets_h, region_h, region_index;
+  std::unique_ptr<pdh::Setup> hostdata;  // element data kept for pd_local_step
+  std::string setup_log;
+  // device state
+  std::vector<void*> allocs;
+  double *x = nullptr, *v = nullptr, *x_save = nullptr, *v_save = nullptr, *x_n = nullptr;
+  double *dpos = nullptr, *mass_h2 = nullptr, *y_in = nullptr, *tmp3 = nullptr;
+  int32_t *d_dirichlet = nullptr, *d_region = nullptr, *d_node_of_pos = nullptr;
+  bool dirichlet_pending = false;
+  ElemSet alpha, beta, all;
+  // interior factor
+  int32_t* sn_col0 = nullptr;
+  int64_t* sn_rowptr = nullptr;
+  int32_t* rows = nullptr;
+  int64_t* sn_valptr = nullptr;
+  double* Lval = nullptr;
+  std::vector<int64_t> lvl_col_ptr, lvl_row_ptr;
+  int32_t *col_sn = nullptr, *col_i = nullptr, *row_sn = nullptr, *row_r = nullptr;
+  pdk::SparseFactor sf;
+  double *b = nullptr, *yv = nullptr, *u = nullptr, *z = nullptr;
+  // collision-region block
+  double* Sigma0 = nullptr;
+  int64_t* b22_ptr = nullptr;
+  int32_t* b22_row = nullptr;
+  double* b22_val = nullptr;
+  double *H = nullptr, *Linv = nullptr, *g = nullptr, *u0 = nullptr, *u2 = nullptr, *Sau = nullptr;
+  double *U2 = nullptr, *work = nullptr, *x2_dev = nullptr;
+  double* x2_host = nullptr;
+  int* status = nullptr;      // [0] non-SPD column+1, [1] timeout code, [2] no convergence
+  int* status_h = nullptr;
+  pdm::MixedState* mixed = nullptr;
+  int last_refine = 0;
+  double last_residual = 0.0;
+  // contacts (region indices)
+  int64_t k = 0, kcap = 0;
+  int32_t* c_idx = nullptr;
+  double *c_w = nullptr, *c_t = nullptr, *c_s = nullptr;
+  // bookkeeping
+  pd_stats stats{};
+  std::string err;
+  std::vector<cudaEvent_t> events;
+  std::vector<std::pair<int, int>> marks;
+  int ev_used = 0;
+
+  pd_status upload(const pdh::Setup& h, const pdh::Input& in);
+  pd_status step(int outer_iters, pd_contact_cb cb, void* user);
+  pd_status region_solve(const double* g_dev, const double* u0_dev, double* u_dev);
+  pd_status check_status();
+  pd_status ensure_all_elements();
+  void tbegin(int phase);
+  void tend();
+  void tcollect(double* out);
+};

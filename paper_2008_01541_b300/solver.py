@@ -1,0 +1,170 @@
+"""Thin Python wrapper over the C ABI: numpy (host) or torch (device) buffers in,
+status codes turned into exceptions.  No arithmetic of the method happens here."""
+import ctypes
+import numpy as np
+
+from . import _lib
+from ._lib import lib, PDError
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None and a.size else None
+
+
+def _dptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _mesh(X, tets):
+    X = _c(X, np.float64)
+    tets = _c(tets, np.int32)
+    return _lib.Mesh(len(X), X.ctypes.data, len(tets), tets.ctypes.data), (X, tets)
+
+
+def host_schur(X, tets, region, dirichlet, mu, density=0.0, dt=0.0):
+    """Sigma_0 from the library's host partial Cholesky (no GPU needed)."""
+    mesh, keep = _mesh(X, tets)
+    region = _c(region, np.int32)
+    dirichlet = _c(dirichlet, np.int32)
+    mat = _lib.Material(mu, 0.0, density)
+    out = np.zeros((len(region), len(region)))
+    info = ctypes.create_string_buffer(1024)
+    st = lib.pd_host_schur(ctypes.byref(mesh), ctypes.byref(mat), dt, _ptr(region), len(region),
+                           _ptr(dirichlet), len(dirichlet), _ptr(out), info, 1024)
+    if st:
+        raise PDError(st, info.value.decode())
+    return out, info.value.decode()
+
+
+class Solver:
+    """One scene on the current CUDA device (pd_setup ... pd_destroy)."""
+
+    def __init__(self, X, tets, region, dirichlet, mu, lam=0.0, density=0.0, dt=0.0,
+                 precision=_lib.FP64, inner_iters=1, tol=1e-10, max_refine=50, stream=None, timing=False):
+        mesh, keep = _mesh(X, tets)
+        self.n = len(keep[0])
+        self.E = len(keep[1])
+        self.region = _c(region, np.int32)
+        self.dirichlet = _c(dirichlet, np.int32)
+        self.m = len(self.region)
+        self.nd = len(self.dirichlet)
+        mat = _lib.Material(mu, lam, density)
+        opt = _lib.Options(precision, tol, max_refine, inner_iters,
+                           ctypes.c_void_p(stream) if stream else None, 1 if timing else 0)
+        h = ctypes.c_void_p()
+        st = lib.pd_setup(ctypes.byref(mesh), ctypes.byref(mat), dt, _ptr(self.region), self.m,
+                          _ptr(self.dirichlet), self.nd, ctypes.byref(opt), ctypes.byref(h))
+        if st:
+            raise PDError(st, lib.pd_last_error(None).decode())
+        self.h = h
+        self._cb_keep = None
+
+    def _check(self, st):
+        if st:
+            raise PDError(st, lib.pd_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.pd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_dirichlet(self, pos):
+        pos = _c(pos, np.float64).reshape(self.nd, 3)
+        self._check(lib.pd_set_dirichlet(self.h, _ptr(pos)))
+
+    def set_contacts(self, nodes, w, target, stiffness):
+        nodes = _c(nodes, np.int32).reshape(-1, 4)
+        k = len(nodes)
+        w = _c(w, np.float64).reshape(k, 4)
+        target = _c(target, np.float64).reshape(k, 3)
+        stiffness = _c(stiffness, np.float64).reshape(k)
+        self._check(lib.pd_set_contacts(self.h, k, _ptr(nodes), _ptr(w), _ptr(target), _ptr(stiffness)))
+
+    def step(self, outer_iters, contacts_fn=None):
+        """contacts_fn(x2 [m,3] numpy) -> (nodes, w, target, stiffness) or None."""
+        if contacts_fn is None:
+            self._check(lib.pd_step(self.h, outer_iters, _lib.CB(), None))
+            return
+        m = self.m
+        err = []
+
+        def cb(user, x2p, handle):
+            try:
+                x2 = np.ctypeslib.as_array(x2p, shape=(m, 3)).copy()
+                c = contacts_fn(x2)
+                if c is not None:
+                    self.set_contacts(*c)
+                return 0
+            except PDError as e:
+                err.append(e)
+                return e.code
+            except Exception as e:  # pragma: no cover - surfaced below
+                err.append(e)
+                return 1
+
+        fn = _lib.CB(cb)
+        st = lib.pd_step(self.h, outer_iters, fn, None)
+        if err:
+            raise err[0]
+        self._check(st)
+
+    def positions(self):
+        out = np.empty((self.n, 3))
+        self._check(lib.pd_get_positions(self.h, _ptr(out)))
+        return out
+
+    def positions_dev(self, out):
+        self._check(lib.pd_get_positions_dev(self.h, _dptr(out)))
+        return out
+
+    def get_state(self):
+        x = np.empty((self.n, 3))
+        v = np.empty((self.n, 3))
+        self._check(lib.pd_get_state(self.h, _ptr(x), _ptr(v)))
+        return x, v
+
+    def set_state(self, x, v=None):
+        x = _c(x, np.float64)
+        v = None if v is None else _c(v, np.float64)
+        self._check(lib.pd_set_state(self.h, _ptr(x), _ptr(v) if v is not None else None))
+
+    def stats(self):
+        st = _lib.Stats()
+        self._check(lib.pd_get_stats(self.h, ctypes.byref(st)))
+        return st.as_dict()
+
+    def local_step(self, x, want_R=True):
+        x = _c(x, np.float64)
+        R = np.empty((self.E, 3, 3)) if want_R else None
+        f = np.empty((self.n, 3))
+        self._check(lib.pd_local_step(self.h, _ptr(x), _ptr(R) if want_R else None, _ptr(f)))
+        return R, f
+
+    def schur(self):
+        out = np.empty((self.m, self.m))
+        self._check(lib.pd_get_schur(self.h, _ptr(out)))
+        return out
+
+    def schur_solve(self, g, u0=None):
+        g = _c(g, np.float64).reshape(self.m, 3)
+        u = np.empty((self.m, 3))
+        u0 = None if u0 is None else _c(u0, np.float64).reshape(self.m, 3)
+        self._check(lib.pd_schur_solve(self.h, _ptr(g), _ptr(u0) if u0 is not None else None, _ptr(u)))
+        return u
+
+    def schur_solve_dev(self, g, u, u0=None):
+        self._check(lib.pd_schur_solve_dev(self.h, _dptr(g), _dptr(u0), _dptr(u)))
+        return u
+
+    def set_precision(self, p):
+        self._check(lib.pd_set_precision(self.h, p))
