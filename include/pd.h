@@ -89,6 +89,7 @@ typedef struct {
     double ms_bookkeeping;    /* a6: x_2 += u_2, f~_2 -= Sigma_alpha u_2             */
     double ms_backward;       /* a7: sparse backward substitution                   */
     double ms_step;           /* whole pd_step                                      */
+    int64_t kernel_launches;  /* kernels this library launched during the last pd_step */
 } pd_stats;
 
 typedef struct pd_solver pd_solver;

@@ -272,16 +272,23 @@ inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 void copy_sigma(const double* S, int64_t m, double* H, int64_t mp, cudaStream_t st) {
   dim3 grid((unsigned)(mp / TB), (unsigned)(mp / TB));
   k_copy_sigma<<<grid, 256, 0, st>>>(S, m, H, mp);
+  ++g_launches;
 }
 
 void contact_scatter(int64_t k, const int32_t* cidx, const double* cw, const double* cs, double* H,
                      int64_t mp, cudaStream_t st) {
-  if (k > 0) k_contact_scatter<<<nblk(16 * k, 256), 256, 0, st>>>(k, cidx, cw, cs, H, mp);
+  if (k > 0) {
+    k_contact_scatter<<<nblk(16 * k, 256), 256, 0, st>>>(k, cidx, cw, cs, H, mp);
+    ++g_launches;
+  }
 }
 
 void contact_forces(int64_t k, const int32_t* cidx, const double* cw, const double* ct, const double* cs,
                     const int32_t* region, const double* x, double* g, cudaStream_t st) {
-  if (k > 0) k_contact_forces<<<nblk(k, 128), 128, 0, st>>>(k, cidx, cw, ct, cs, region, x, g);
+  if (k > 0) {
+    k_contact_forces<<<nblk(k, 128), 128, 0, st>>>(k, cidx, cw, ct, cs, region, x, g);
+    ++g_launches;
+  }
 }
 
 void cholesky_fp64(double* H, int64_t mp, double* Linv, int* status, cudaStream_t st) {
@@ -296,10 +303,13 @@ void cholesky_fp64(double* H, int64_t mp, double* Linv, int* status, cudaStream_
   const int T = (int)(mp / TB);
   for (int k = 0; k < T; ++k) {
     k_chol_diag<<<1, 256, smem, st>>>(H, mp, k, Linv, status);
+    ++g_launches;
     int n = T - k - 1;
     if (n <= 0) break;
     k_chol_trsm<<<n, 256, smem, st>>>(H, mp, k, Linv);
+    ++g_launches;
     k_chol_update<<<(unsigned)((int64_t)n * (n + 1) / 2), 256, smem, st>>>(H, mp, k, T);
+    ++g_launches;
   }
 }
 
@@ -309,20 +319,33 @@ void chol_solve_fp64(const double* H, int64_t mp, const double* Linv, const doub
   double* w = work;
   double* y = work + 3 * mp;
   k_pad_rhs<<<nblk(3 * mp, 256), 256, 0, st>>>(g, m, mp, w);
-  for (int k = 0; k < T; ++k) k_trsv_fwd<<<T - k, 192, 0, st>>>(H, mp, k, Linv, w, y);
+  ++g_launches;
+  for (int k = 0; k < T; ++k) {
+    k_trsv_fwd<<<T - k, 192, 0, st>>>(H, mp, k, Linv, w, y);
+    ++g_launches;
+  }
   // backward on y (copied into w as the running right-hand side)
   cudaMemcpyAsync(w, y, sizeof(double) * 3 * mp, cudaMemcpyDeviceToDevice, st);
-  for (int k = T - 1; k >= 0; --k) k_trsv_bwd<<<k + 1, 192, 0, st>>>(H, mp, k, Linv, w, y);
+  for (int k = T - 1; k >= 0; --k) {
+    k_trsv_bwd<<<k + 1, 192, 0, st>>>(H, mp, k, Linv, w, y);
+    ++g_launches;
+  }
   cudaMemcpyAsync(u, y, sizeof(double) * 3 * m, cudaMemcpyDeviceToDevice, st);
 }
 
 void symv3(const double* S, int64_t m, const double* v, double* out, cudaStream_t st) {
-  if (m > 0) k_symv3<<<nblk(32 * m, 256), 256, 0, st>>>(S, m, v, out);
+  if (m > 0) {
+    k_symv3<<<nblk(32 * m, 256), 256, 0, st>>>(S, m, v, out);
+    ++g_launches;
+  }
 }
 
 void spmv3(int64_t m, const int64_t* ptr, const int32_t* row, const double* val, const double* v, double alpha,
            double* out, cudaStream_t st) {
-  if (m > 0) k_spmv3<<<nblk(m, 256), 256, 0, st>>>(m, ptr, row, val, v, alpha, out);
+  if (m > 0) {
+    k_spmv3<<<nblk(m, 256), 256, 0, st>>>(m, ptr, row, val, v, alpha, out);
+    ++g_launches;
+  }
 }
 
 }  // namespace pdk

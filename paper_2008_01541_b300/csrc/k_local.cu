@@ -4,6 +4,9 @@
 #include "kernels.h"
 
 namespace pdk {
+
+int64_t g_launches = 0;
+
 namespace {
 
 // X^-T = cof(X) / det(X); row-major 3x3.
@@ -253,6 +256,7 @@ void polar_forces(int64_t count, const int4* tets, const double* Dm, const doubl
                   double* fe, double* R_out, cudaStream_t st) {
   if (count <= 0) return;
   k_polar_forces<<<nblk(count, 128), 128, 0, st>>>(count, tets, Dm, w, x, fe, R_out);
+  ++g_launches;
 }
 
 void gather_forces(int64_t nt, const int64_t* ptr, const int32_t* slot, const double* fe, double* out,
@@ -260,23 +264,39 @@ void gather_forces(int64_t nt, const int64_t* ptr, const int32_t* slot, const do
                    const int32_t* node, int64_t lim, cudaStream_t st) {
   if (nt <= 0) return;
   k_gather<<<nblk(nt, 256), 256, 0, st>>>(nt, ptr, slot, fe, out, add, mass_h2, x, y, node, lim);
+  ++g_launches;
 }
 
 void gather_rows(int64_t cnt, const int32_t* idx, const double* x, double* out, cudaStream_t st) {
-  if (cnt > 0) k_gather_rows<<<nblk(cnt, 256), 256, 0, st>>>(cnt, idx, x, out);
+  if (cnt > 0) {
+    k_gather_rows<<<nblk(cnt, 256), 256, 0, st>>>(cnt, idx, x, out);
+    ++g_launches;
+  }
 }
 void scatter_rows(int64_t cnt, const int32_t* idx, const double* v, double* x, cudaStream_t st) {
-  if (cnt > 0) k_scatter_rows<<<nblk(cnt, 256), 256, 0, st>>>(cnt, idx, v, x);
+  if (cnt > 0) {
+    k_scatter_rows<<<nblk(cnt, 256), 256, 0, st>>>(cnt, idx, v, x);
+    ++g_launches;
+  }
 }
 void axpby(int64_t n, double a, const double* x, double b, double* y, cudaStream_t st) {
-  if (n > 0) k_axpby<<<nblk(n, 256), 256, 0, st>>>(n, a, x, b, y);
+  if (n > 0) {
+    k_axpby<<<nblk(n, 256), 256, 0, st>>>(n, a, x, b, y);
+    ++g_launches;
+  }
 }
 void inner_update(int64_t m, const double* u2, const double* Sau, const int32_t* region, double* x,
                   double* U2, double* ft2, cudaStream_t st) {
-  if (m > 0) k_inner_update<<<nblk(m, 256), 256, 0, st>>>(m, u2, Sau, region, x, U2, ft2);
+  if (m > 0) {
+    k_inner_update<<<nblk(m, 256), 256, 0, st>>>(m, u2, Sau, region, x, U2, ft2);
+    ++g_launches;
+  }
 }
 void apply_interior(int64_t n1, const double* u, const int32_t* node, double* x, cudaStream_t st) {
-  if (n1 > 0) k_apply_interior<<<nblk(n1, 256), 256, 0, st>>>(n1, u, node, x);
+  if (n1 > 0) {
+    k_apply_interior<<<nblk(n1, 256), 256, 0, st>>>(n1, u, node, x);
+    ++g_launches;
+  }
 }
 
 }  // namespace pdk

@@ -120,12 +120,16 @@ void sparse_forward(const SparseFactor& f, double* b, double* y, cudaStream_t st
   for (int64_t l = 0; l < f.nlevels; ++l) {
     int64_t c0 = f.lvl_col_ptr[l], c1 = f.lvl_col_ptr[l + 1];
     int64_t r0 = f.lvl_row_ptr[l], r1 = f.lvl_row_ptr[l + 1];
-    if (c1 > c0)
+    if (c1 > c0) {
       k_fwd_diag<<<nblk(c1 - c0, 128), 128, 0, st>>>(c1 - c0, f.col_sn + c0, f.col_i + c0, f.col0,
                                                      f.rowptr, f.valptr, f.L, b, y);
-    if (r1 > r0)
+      ++g_launches;
+    }
+    if (r1 > r0) {
       k_fwd_off<<<nblk(r1 - r0, 128), 128, 0, st>>>(r1 - r0, f.row_sn + r0, f.row_r + r0, f.col0, f.rowptr,
                                                     f.rows, f.valptr, f.L, y, b);
+      ++g_launches;
+    }
   }
 }
 
@@ -135,8 +139,10 @@ void sparse_backward(const SparseFactor& f, const double* y, double* u, double* 
     if (c1 <= c0) continue;
     k_bwd_off<<<nblk((c1 - c0) * 32, 256), 256, 0, st>>>(c1 - c0, f.col_sn + c0, f.col_i + c0, f.col0,
                                                         f.rowptr, f.rows, f.valptr, f.L, y, u, z);
+    ++g_launches;
     k_bwd_diag<<<nblk((c1 - c0) * 32, 256), 256, 0, st>>>(c1 - c0, f.col_sn + c0, f.col_i + c0, f.col0,
                                                          f.rowptr, f.valptr, f.L, z, u);
+    ++g_launches;
   }
 }
 

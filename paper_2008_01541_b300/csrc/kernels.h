@@ -5,6 +5,9 @@
 
 namespace pdk {
 
+// Number of kernels launched by this library so far (host-side counter).
+extern int64_t g_launches;
+
 // ---- local step (Section 2.2) -------------------------------------------
 // For each element e of a set: F = Ds Dm^-1, R = polar(F) in SO(3),
 // fe[e][a][:] = forces on its four vertices, f_a = -w_e (F - R) G_a^T

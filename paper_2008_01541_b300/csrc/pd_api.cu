@@ -524,6 +524,7 @@ pd_status pd_solver::upload(const pdh::Setup& h, const pdh::Input& in) {
 pd_status pd_solver::step(int outer_iters, pd_contact_cb cb, void* user) {
   pd_solver* s = this;
   double t0 = now_ms();
+  const int64_t launches0 = pdk::g_launches;
   marks.clear();
   ev_used = 0;
   CK(cudaMemsetAsync(status, 0, sizeof(int) * 4, stream));
@@ -619,6 +620,7 @@ pd_status pd_solver::step(int outer_iters, pd_contact_cb cb, void* user) {
   CK(cudaStreamSynchronize(stream));
   stats.ms_step = now_ms() - t0;
   stats.inner_done = inner_total;
+  stats.kernel_launches = pdk::g_launches - launches0;
   stats.contacts = k;
   stats.refine_iters = last_refine;
   stats.residual = last_residual;
