@@ -196,6 +196,32 @@ pd_status pd_host_schur(const pd_mesh* mesh, const pd_material* mat, double dt,
                         const int32_t* dirichlet, int64_t nd,
                         double* sigma_out, char* info, int64_t info_len);
 
+/* Allocation-free Schur refactor + solve (FP64).  The paper has no
+ * counterpart: this exists for callers that may not allocate device memory
+ * while they run -- an engine that reserves all of the GPU's memory up front
+ * and forbids cudaMalloc/cudaFree mid-frame, an arena/pool integration, or a
+ * real-time loop that cannot take the synchronisation an allocation implies.
+ * It computes the same result as pd_schur_solve_dev() in PD_FP64 mode, but
+ * without a solver handle and without allocating: its working memory is one
+ * file-scope device array of about 8.5 MB that every device which loads this
+ * library holds until the process exits.
+ *   sigma_dev : [m][m] device, the symmetric Sigma_0 (row- or column-major)
+ *   m         : 1 <= m <= 1024; larger m returns PD_ERR_INVALID_ARG
+ *   k, cidx_dev [k][4], cw_dev [k][4], cs_dev [k] : springs on region rows
+ *               (cidx = -1 marks an unused slot); H = Sigma_0 + sum_j c_j w_j w_j^T
+ *   g_dev, u_dev : [m][3] device right-hand sides and solution
+ *   cuda_stream  : stream to run on (NULL = the default stream)
+ *   err, err_len : optional buffer for a message
+ * The call is synchronous (it reads the pivot status back).  The first call
+ * on each device looks up the scratch array's device address; make that
+ * first call before any stream capture.  All calls share the one array, so
+ * calls that overlap on the GPU (other threads, other streams) race.
+ * Errors: INVALID_ARG, CONTACT_OUTSIDE_REGION, NOT_SPD, CUDA. */
+pd_status pd_schur_solve_noalloc(const double* sigma_dev, int64_t m, int64_t k,
+                                 const int32_t* cidx_dev, const double* cw_dev, const double* cs_dev,
+                                 const double* g_dev, double* u_dev, void* cuda_stream,
+                                 char* err, int64_t err_len);
+
 /* Change the precision of the collision-region solve on an existing handle. */
 pd_status pd_set_precision(pd_solver* s, int precision);
 
