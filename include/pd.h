@@ -222,6 +222,15 @@ pd_status pd_schur_solve_noalloc(const double* sigma_dev, int64_t m, int64_t k,
                                  const double* g_dev, double* u_dev, void* cuda_stream,
                                  char* err, int64_t err_len);
 
+/* Tensor-core rank-K update, exposed for diagnostics: C -= A B^T with A [M][K],
+ * B [N][K], C [M][N] row-major float32 device buffers, M and N multiples of 128,
+ * K = 128.  mode 0 = TF32, 1 = split TF32 (three products, ~FP32 accuracy),
+ * 2 = BF16 (operands rounded to bfloat16); accumulation is FP32 in tensor
+ * memory.  This is the trailing-update kernel of the low-precision Cholesky
+ * (Section 3.3 dense refactorisation).  Errors: INVALID_ARG, OOM, CUDA, TIMEOUT. */
+pd_status pd_tc_rank_k(int mode, const float* A, const float* B, float* C, int64_t M, int64_t N, int64_t K,
+                       void* cuda_stream);
+
 /* Change the precision of the collision-region solve on an existing handle. */
 pd_status pd_set_precision(pd_solver* s, int precision);
 

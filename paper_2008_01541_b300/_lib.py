@@ -72,6 +72,7 @@ _sigs = {
     "pd_schur_solve": (ctypes.c_int, [P, P, P, P]),
     "pd_schur_solve_dev": (ctypes.c_int, [P, P, P, P]),
     "pd_set_precision": (ctypes.c_int, [P, ctypes.c_int]),
+    "pd_tc_rank_k": (ctypes.c_int, [ctypes.c_int, P, P, P, I64, I64, I64, P]),
     "pd_schur_solve_noalloc": (ctypes.c_int, [P, I64, I64, P, P, P, P, P, P, ctypes.c_char_p, I64]),
     "pd_host_schur": (ctypes.c_int, [ctypes.POINTER(Mesh), ctypes.POINTER(Material), D, P, I64, P, I64,
                                      P, ctypes.c_char_p, I64]),
