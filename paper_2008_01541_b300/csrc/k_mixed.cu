@@ -1,12 +1,580 @@
-// Mixed-precision forms of the collision-region solve (placeholder until the
-// low-precision factorisations are wired in).
+// Mixed-precision forms of the collision-region solve H u = g (Algorithm 1,
+// step 4.5; Section 3.3).  H = Sigma_0 + C_22 is equilibrated by
+// D = diag(H)^-1/2 and factored in low precision with a blocked right-looking
+// Cholesky (128 x 128 tiles): FP32 diagonal-tile factorisation and inversion,
+// FP32 panel solve, and tcgen05 trailing updates in TF32, split TF32 (three
+// products, ~FP32 accuracy) or BF16, all accumulated in FP32.  Accuracy is
+// recovered with FP64 residuals r = g - H u: plain iterative refinement for
+// the split-TF32 factor, and refinement accelerated by preconditioned CG for
+// TF32 and BF16.  PD_PCG_WARM runs PCG on H with the contact-free factor of
+// Sigma_0 (computed once) as the preconditioner, started from a given guess.
+#include <cooperative_groups.h>
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <string>
+
+#include "kernels.h"
 #include "mixed.h"
 #include "solver.h"
+#include "tc.h"
 
 namespace pdm {
-pd_status mixed_solve(pd_solver* s, const double*, const double*, double*) {
-  s->err = "precision mode not available in this build";
-  return PD_ERR_INVALID_ARG;
+
+constexpr int NB = 128;      // tile of the low-precision factor
+constexpr int PADW = NB + 1; // padded shared-memory row
+
+struct Factor {
+  float* L = nullptr;         // [mq][mq] row-major, lower tiles hold the factor
+  float* Dinv = nullptr;      // [T][128][128] row-major inverses of the diagonal tiles
+  __nv_bfloat16* Pb = nullptr;  // [mq][128] BF16 copy of the current panel
+  double* d = nullptr;        // [mq] equilibration D
+  CUtensorMap mapL{}, mapP{};
+  bool valid = false;
+};
+
+struct MixedState {
+  int64_t mq = 0, T = 0;
+  Factor f, f0;               // per-solve factor, contact-free factor (PCG_WARM)
+  double *hdiag = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *u = nullptr;
+  double* sc = nullptr;       // device scalars: [0] r.r  [1] r.z  [2] p.q  [3] r.z old  [4] g.g
+  double* sc_h = nullptr;     // pinned copy
+  float *w = nullptr, *y = nullptr, *uo = nullptr;   // [mq][3] triangular-solve vectors
+  unsigned* bar = nullptr;    // grid-barrier counter
+  int coop_grid = 0;
+};
+
+namespace {
+
+// ---------------------------------------------------------------- small kernels
+__global__ void k_hdiag(const double* S, int64_t m, double* hd) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < m) hd[i] = S[i * m + i];
 }
-void mixed_free(pd_solver*) {}
+__global__ void k_contact_diag(int64_t k, const int32_t* cidx, const double* cw, const double* cs, double* hd) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= 16 * k) return;
+  int64_t j = t >> 4;
+  int a = (t >> 2) & 3, b = t & 3;
+  int ra = cidx[4 * j + a], rb = cidx[4 * j + b];
+  if (ra < 0 || ra != rb) return;
+  atomicAdd(hd + ra, cs[j] * cw[4 * j + a] * cw[4 * j + b]);
+}
+__global__ void k_dscale(const double* hd, int64_t m, int64_t mq, double* d, int* status) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= mq) return;
+  if (i < m) {
+    double h = hd[i];
+    if (!(h > 0.0)) { atomicCAS(status, 0, (int)i + 1); h = 1.0; }
+    d[i] = 1.0 / sqrt(h);
+  } else {
+    d[i] = 1.0;
+  }
+}
+// L = D Sigma_0 D in FP32 (lower tiles), identity padding.
+__global__ void k_cast_eq(const double* __restrict__ S, int64_t m, const double* __restrict__ d,
+                          float* __restrict__ L, int64_t mq) {
+  int ti = blockIdx.x, tj = blockIdx.y;
+  if (ti < tj) return;
+  for (int q = threadIdx.x; q < NB * NB; q += blockDim.x) {
+    int r = q / NB, c = q % NB;
+    int64_t i = (int64_t)ti * NB + r, j = (int64_t)tj * NB + c;
+    float v;
+    if (i < m && j < m) v = (float)(S[i * m + j] * d[i] * d[j]);
+    else v = (i == j) ? 1.f : 0.f;
+    L[i * mq + j] = v;
+  }
+}
+__global__ void k_contact_scatter_f32(int64_t k, const int32_t* cidx, const double* cw, const double* cs,
+                                      const double* d, float* L, int64_t mq) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= 16 * k) return;
+  int64_t j = t >> 4;
+  int a = (t >> 2) & 3, b = t & 3;
+  int ra = cidx[4 * j + a], rb = cidx[4 * j + b];
+  if (ra < 0 || rb < 0 || ra < rb) return;
+  atomicAdd(L + (int64_t)ra * mq + rb, (float)(cs[j] * cw[4 * j + a] * cw[4 * j + b] * d[ra] * d[rb]));
+}
+
+// Factor the diagonal tile (kt, kt) in FP32 and invert it.
+__global__ void __launch_bounds__(512) k_diag_f32(float* __restrict__ L, int64_t mq, int kt,
+                                                  float* __restrict__ Dinv, int* __restrict__ status) {
+  extern __shared__ float sm[];
+  float* A = sm;                // A[r*PADW + c]
+  float* Z = sm + NB * PADW;    // inverse
+  __shared__ float piv;
+  const int tid = threadIdx.x;
+  float* Lt = L + (int64_t)kt * NB * mq + (int64_t)kt * NB;
+  for (int q = tid; q < NB * NB; q += 512) {
+    int r = q / NB, c = q % NB;
+    A[r * PADW + c] = Lt[(int64_t)r * mq + c];
+    Z[r * PADW + c] = (r == c) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  for (int j = 0; j < NB; ++j) {
+    if (tid == 0) {
+      float dj = A[j * PADW + j];
+      if (!(dj > 0.f) || !isfinite(dj)) {
+        atomicCAS(status, 0, kt * NB + j + 1);
+        dj = 1.f;
+      }
+      piv = sqrtf(dj);
+      A[j * PADW + j] = piv;
+    }
+    __syncthreads();
+    const float ip = 1.f / piv;
+    if (tid > j && tid < NB) A[tid * PADW + j] *= ip;
+    __syncthreads();
+    const int r = tid % NB;
+    for (int c = j + 1 + tid / NB; c < NB; c += 512 / NB)
+      if (r >= c) A[r * PADW + c] -= A[r * PADW + j] * A[c * PADW + j];
+    __syncthreads();
+  }
+  // Z = L^-1: row j scaled, then eliminated from the rows below
+  for (int j = 0; j < NB; ++j) {
+    const float ip = 1.f / A[j * PADW + j];
+    if (tid <= j) Z[j * PADW + tid] *= ip;
+    __syncthreads();
+    const int c = tid % NB;
+    if (c <= j)
+      for (int r = j + 1 + tid / NB; r < NB; r += 512 / NB) Z[r * PADW + c] -= A[r * PADW + j] * Z[j * PADW + c];
+    __syncthreads();
+  }
+  float* Di = Dinv + (int64_t)kt * NB * NB;
+  for (int q = tid; q < NB * NB; q += 512) {
+    int r = q / NB, c = q % NB;
+    if (c <= r) Lt[(int64_t)r * mq + c] = A[r * PADW + c];
+    Di[q] = (c <= r) ? Z[r * PADW + c] : 0.f;
+  }
+}
+
+// Panel solve: L_ik = A_ik Dinv_k^T for the 64-row slab blockIdx.x below tile kt.
+__global__ void __launch_bounds__(256) k_trsm_f32(float* __restrict__ L, int64_t mq, int kt,
+                                                  const float* __restrict__ Dinv, __nv_bfloat16* __restrict__ Pb) {
+  extern __shared__ float sm[];
+  float* As = sm;               // [64][PADW]
+  float* Ds = sm + 64 * PADW;   // [128][PADW]
+  const int tid = threadIdx.x;
+  const int64_t r0 = (int64_t)(kt + 1) * NB + (int64_t)blockIdx.x * 64;
+  float* Ab = L + r0 * mq + (int64_t)kt * NB;
+  const float* Di = Dinv + (int64_t)kt * NB * NB;
+  for (int q = tid; q < 64 * NB; q += 256) As[(q / NB) * PADW + q % NB] = Ab[(int64_t)(q / NB) * mq + q % NB];
+  for (int q = tid; q < NB * NB; q += 256) Ds[(q / NB) * PADW + q % NB] = Di[q];
+  __syncthreads();
+  const int tr = tid % 16, tc = tid / 16;
+  float acc[4][8] = {};
+  for (int t = 0; t < NB; ++t) {
+    float a[4], b[8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = As[(tr + 16 * i) * PADW + t];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) b[j] = Ds[(tc + 16 * j) * PADW + t];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      int rr = tr + 16 * i, cc = tc + 16 * j;
+      Ab[(int64_t)rr * mq + cc] = acc[i][j];
+      if (Pb) Pb[(r0 + rr) * NB + cc] = __float2bfloat16_rn(acc[i][j]);
+    }
+}
+
+// Bounded grid barrier for the cooperative launch; false = gave up.
+__device__ bool grid_barrier(unsigned* ctr, unsigned target, int* status) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    __threadfence();
+    atomicAdd(ctr, 1u);
+    unsigned it = 0;
+    while (*(volatile unsigned*)ctr < target) {
+      if (++it > (1u << 26)) { ok = 0; atomicExch(status + 1, 200); break; }
+      if (it > 64) __nanosleep(64);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// z = D L^-T L^-1 D r  for 3 right-hand sides, one cooperative launch.
+__global__ void __launch_bounds__(256) k_precond(const float* __restrict__ L, const float* __restrict__ Dinv,
+                                                 int64_t mq, int64_t m, const double* __restrict__ d,
+                                                 const double* __restrict__ r, double* __restrict__ z, float* w,
+                                                 float* y, float* uo, unsigned* bar, int* status) {
+  __shared__ float vk[NB * 3];
+  __shared__ float ok_s[NB * 3];
+  const int T = (int)(mq / NB);
+  const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
+  unsigned nb = 0;
+  for (int64_t i = (int64_t)b * 256 + tid; i < mq; i += (int64_t)G * 256)
+    for (int v = 0; v < 3; ++v) w[3 * i + v] = i < m ? (float)(d[i] * r[3 * i + v]) : 0.f;
+  if (!grid_barrier(bar, (unsigned)G * ++nb, status)) return;
+  // forward: y_k = Dinv_k w_k; w_i -= L_ik y_k (i > k)
+  for (int k = 0; k < T; ++k) {
+    const float* Di = Dinv + (int64_t)k * NB * NB;
+    for (int q = tid; q < NB * 3; q += 256) {
+      int rr = q / 3, v = q % 3;
+      float s = 0.f;
+      for (int c = 0; c <= rr; ++c) s = fmaf(Di[rr * NB + c], w[3 * ((int64_t)k * NB + c) + v], s);
+      vk[q] = s;
+    }
+    __syncthreads();
+    if (b == 0)
+      for (int q = tid; q < NB * 3; q += 256) y[3 * (int64_t)k * NB + q] = vk[q];
+    const int64_t lo = (int64_t)(k + 1) * NB, n = mq - lo;
+    const int64_t per = (n + G - 1) / G;
+    for (int64_t i = lo + b * per + tid; i < lo + (b + 1) * per && i < mq; i += 256) {
+      const float* Li = L + i * mq + (int64_t)k * NB;
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+      for (int c = 0; c < NB; c += 4) {
+        float4 l4 = *reinterpret_cast<const float4*>(Li + c);
+        a0 = fmaf(l4.x, vk[3 * c], a0); a1 = fmaf(l4.x, vk[3 * c + 1], a1); a2 = fmaf(l4.x, vk[3 * c + 2], a2);
+        a0 = fmaf(l4.y, vk[3 * c + 3], a0); a1 = fmaf(l4.y, vk[3 * c + 4], a1); a2 = fmaf(l4.y, vk[3 * c + 5], a2);
+        a0 = fmaf(l4.z, vk[3 * c + 6], a0); a1 = fmaf(l4.z, vk[3 * c + 7], a1); a2 = fmaf(l4.z, vk[3 * c + 8], a2);
+        a0 = fmaf(l4.w, vk[3 * c + 9], a0); a1 = fmaf(l4.w, vk[3 * c + 10], a1); a2 = fmaf(l4.w, vk[3 * c + 11], a2);
+      }
+      w[3 * i] -= a0; w[3 * i + 1] -= a1; w[3 * i + 2] -= a2;
+    }
+    if (!grid_barrier(bar, (unsigned)G * ++nb, status)) return;
+  }
+  // backward on y: u_k = Dinv_k^T y_k; y_j -= L_kj^T u_k (j < k)
+  for (int k = T - 1; k >= 0; --k) {
+    const float* Di = Dinv + (int64_t)k * NB * NB;
+    for (int q = tid; q < NB * 3; q += 256) {
+      int cc = q / 3, v = q % 3;
+      float s = 0.f;
+      for (int rr = cc; rr < NB; ++rr) s = fmaf(Di[rr * NB + cc], y[3 * ((int64_t)k * NB + rr) + v], s);
+      ok_s[q] = s;
+    }
+    __syncthreads();
+    if (b == 0)
+      for (int q = tid; q < NB * 3; q += 256) uo[3 * (int64_t)k * NB + q] = ok_s[q];
+    const int64_t n = (int64_t)k * NB;
+    const int64_t per = (n + G - 1) / G;
+    const float* Lk = L + (int64_t)k * NB * mq;
+    for (int64_t j = b * per + tid; j < (b + 1) * per && j < n; j += 256) {
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+      for (int rr = 0; rr < NB; ++rr) {
+        float l = Lk[(int64_t)rr * mq + j];
+        a0 = fmaf(l, ok_s[3 * rr], a0); a1 = fmaf(l, ok_s[3 * rr + 1], a1); a2 = fmaf(l, ok_s[3 * rr + 2], a2);
+      }
+      y[3 * j] -= a0; y[3 * j + 1] -= a1; y[3 * j + 2] -= a2;
+    }
+    if (!grid_barrier(bar, (unsigned)G * ++nb, status)) return;
+  }
+  for (int64_t i = (int64_t)b * 256 + tid; i < m; i += (int64_t)G * 256)
+    for (int v = 0; v < 3; ++v) z[3 * i + v] = d[i] * (double)uo[3 * i + v];
+}
+
+__global__ void k_contact_matvec(int64_t k, const int32_t* cidx, const double* cw, const double* cs,
+                                 const double* p, double* q) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= k) return;
+  double s0 = 0, s1 = 0, s2 = 0;
+  for (int a = 0; a < 4; ++a) {
+    int ra = cidx[4 * j + a];
+    if (ra < 0) continue;
+    double wa = cw[4 * j + a];
+    s0 += wa * p[3 * ra]; s1 += wa * p[3 * ra + 1]; s2 += wa * p[3 * ra + 2];
+  }
+  double c = cs[j];
+  for (int a = 0; a < 4; ++a) {
+    int ra = cidx[4 * j + a];
+    if (ra < 0) continue;
+    double f = c * cw[4 * j + a];
+    atomicAdd(q + 3 * ra, f * s0); atomicAdd(q + 3 * ra + 1, f * s1); atomicAdd(q + 3 * ra + 2, f * s2);
+  }
+}
+
+// out[slot] += sum x*y over n doubles
+__global__ void k_dot(const double* __restrict__ x, const double* __restrict__ y, int64_t n, double* out) {
+  __shared__ double red[8];
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s += x[i] * y[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    atomicAdd(out, t);
+  }
+}
+__global__ void k_sub(const double* a, const double* b, double* out, int64_t n) {   // out = a - b
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a[i] - b[i];
+}
+__global__ void k_add(double* u, const double* z, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) u[i] += z[i];
+}
+// u += alpha p, r -= alpha q with alpha = sc[1] / sc[2]
+__global__ void k_cg_step(double* u, double* r, const double* p, const double* q, const double* sc, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double alpha = sc[1] / sc[2];
+  u[i] += alpha * p[i];
+  r[i] -= alpha * q[i];
+}
+// p = z + beta p with beta = sc[1] / sc[3]
+__global__ void k_cg_dir(double* p, const double* z, const double* sc, int64_t n, int first) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  p[i] = first ? z[i] : z[i] + (sc[1] / sc[3]) * p[i];
+}
+
+inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+// ------------------------------------------------------------------ host side
+static pd_status ensure_state(pd_solver* s) {
+  if (s->mixed) return PD_OK;
+  MixedState* M = new MixedState();
+  s->mixed = M;
+  M->mq = ((s->m + NB - 1) / NB) * NB;
+  M->T = M->mq / NB;
+  auto A = [&](void** p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 1);
+    if (e == cudaSuccess) s->allocs.push_back(*p);
+    return e;
+  };
+  const int64_t mq = M->mq, m = s->m;
+  for (Factor* f : {&M->f, &M->f0}) {
+    if (A((void**)&f->L, sizeof(float) * mq * mq) || A((void**)&f->Dinv, sizeof(float) * mq * NB) ||
+        A((void**)&f->Pb, sizeof(__nv_bfloat16) * mq * NB) || A((void**)&f->d, sizeof(double) * mq)) {
+      s->err = "device allocation for the mixed-precision factor failed";
+      return PD_ERR_OOM;
+    }
+    if (!pdtc::make_map(&f->mapL, f->L, 4, mq, mq, mq, 32) || !pdtc::make_map(&f->mapP, f->Pb, 2, mq, NB, NB, 64)) {
+      s->err = "cuTensorMapEncodeTiled failed";
+      return PD_ERR_CUDA;
+    }
+  }
+  if (A((void**)&M->hdiag, sizeof(double) * m) || A((void**)&M->r, sizeof(double) * 3 * m) ||
+      A((void**)&M->z, sizeof(double) * 3 * m) || A((void**)&M->p, sizeof(double) * 3 * m) ||
+      A((void**)&M->q, sizeof(double) * 3 * m) || A((void**)&M->u, sizeof(double) * 3 * m) ||
+      A((void**)&M->sc, sizeof(double) * 8) || A((void**)&M->w, sizeof(float) * 3 * mq) ||
+      A((void**)&M->y, sizeof(float) * 3 * mq) || A((void**)&M->uo, sizeof(float) * 3 * mq) ||
+      A((void**)&M->bar, sizeof(unsigned) * 4)) {
+    s->err = "device allocation for the mixed-precision vectors failed";
+    return PD_ERR_OOM;
+  }
+  if (cudaMallocHost(&M->sc_h, sizeof(double) * 8) != cudaSuccess) return PD_ERR_OOM;
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_precond, 256, 0);
+  M->coop_grid = nsm * (per > 0 ? 1 : 0);
+  if (M->coop_grid <= 0) {
+    s->err = "cooperative triangular-solve kernel cannot be resident";
+    return PD_ERR_CUDA;
+  }
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_diag_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * NB * PADW * 4);
+    cudaFuncSetAttribute(k_trsm_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (64 + NB) * PADW * 4);
+    attr = true;
+  }
+  return PD_OK;
+}
+
+// Equilibrate Sigma_0 (+ C_22 if with_contacts) into f (Algorithm 1, 4.3).
+static void factor_cast(pd_solver* s, Factor& f, bool with_contacts) {
+  MixedState* M = s->mixed;
+  const int64_t m = s->m, mq = M->mq, T = M->T;
+  cudaStream_t st = s->stream;
+  const int64_t k = with_contacts ? s->k : 0;
+  k_hdiag<<<nblk(m, 256), 256, 0, st>>>(s->Sigma0, m, M->hdiag); ++pdk::g_launches;
+  if (k > 0) { k_contact_diag<<<nblk(16 * k, 256), 256, 0, st>>>(k, s->c_idx, s->c_w, s->c_s, M->hdiag); ++pdk::g_launches; }
+  k_dscale<<<nblk(mq, 256), 256, 0, st>>>(M->hdiag, m, mq, f.d, s->status); ++pdk::g_launches;
+  k_cast_eq<<<dim3((unsigned)T, (unsigned)T), 256, 0, st>>>(s->Sigma0, m, f.d, f.L, mq); ++pdk::g_launches;
+  if (k > 0) {
+    k_contact_scatter_f32<<<nblk(16 * k, 256), 256, 0, st>>>(k, s->c_idx, s->c_w, s->c_s, f.d, f.L, mq);
+    ++pdk::g_launches;
+  }
+}
+
+// Blocked low-precision Cholesky of f.L in place.
+static void factor_panels(pd_solver* s, Factor& f, pdtc::Mode mode) {
+  MixedState* M = s->mixed;
+  const int64_t mq = M->mq, T = M->T;
+  cudaStream_t st = s->stream;
+  for (int kt = 0; kt < T; ++kt) {
+    k_diag_f32<<<1, 512, 2 * NB * PADW * 4, st>>>(f.L, mq, kt, f.Dinv, s->status); ++pdk::g_launches;
+    const int n = (int)(T - kt - 1);
+    if (n <= 0) break;
+    k_trsm_f32<<<(unsigned)(2 * n), 256, (64 + NB) * PADW * 4, st>>>(f.L, mq, kt, f.Dinv,
+                                                                    mode == pdtc::BF16 ? f.Pb : nullptr);
+    ++pdk::g_launches;
+    if (mode == pdtc::BF16)
+      pdtc::rank_k_update(mode, &f.mapP, &f.mapP, 0, 2, f.L, mq, kt + 1, kt + 1, n, n, 1, s->status, st);
+    else
+      pdtc::rank_k_update(mode, &f.mapL, &f.mapL, kt * NB, 4, f.L, mq, kt + 1, kt + 1, n, n, 1, s->status, st);
+  }
+  f.valid = true;
+}
+
+static cudaError_t precond(pd_solver* s, const Factor& f, const double* r, double* z) {
+  MixedState* M = s->mixed;
+  cudaMemsetAsync(M->bar, 0, sizeof(unsigned), s->stream);
+  const float* L = f.L;
+  const float* Di = f.Dinv;
+  int64_t mq = M->mq, m = s->m;
+  const double* d = f.d;
+  float *w = M->w, *y = M->y, *uo = M->uo;
+  unsigned* bar = M->bar;
+  int* status = s->status;
+  void* args[] = {(void*)&L, (void*)&Di, (void*)&mq, (void*)&m, (void*)&d, (void*)&r, (void*)&z,
+                  (void*)&w, (void*)&y, (void*)&uo, (void*)&bar, (void*)&status};
+  ++pdk::g_launches;
+  return cudaLaunchCooperativeKernel((void*)k_precond, dim3(M->coop_grid), dim3(256), args, 0, s->stream);
+}
+
+// q = H p = Sigma_0 p + C_22 p  (FP64)
+static void hmatvec(pd_solver* s, const double* p, double* q) {
+  pdk::symv3(s->Sigma0, s->m, p, q, s->stream);
+  if (s->k > 0) {
+    k_contact_matvec<<<nblk(s->k, 128), 128, 0, s->stream>>>(s->k, s->c_idx, s->c_w, s->c_s, p, q);
+    ++pdk::g_launches;
+  }
+}
+
+static void dot(pd_solver* s, const double* x, const double* y, int slot) {
+  MixedState* M = s->mixed;
+  cudaMemsetAsync(M->sc + slot, 0, sizeof(double), s->stream);
+  k_dot<<<148, 256, 0, s->stream>>>(x, y, 3 * s->m, M->sc + slot);
+  ++pdk::g_launches;
+}
+
+static double read_slot(pd_solver* s, int slot) {
+  MixedState* M = s->mixed;
+  cudaMemcpyAsync(M->sc_h + slot, M->sc + slot, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  cudaStreamSynchronize(s->stream);
+  return M->sc_h[slot];
+}
+
+pd_status mixed_solve(pd_solver* s, const double* g, const double* u0, double* u) {
+  pd_status rs = ensure_state(s);
+  if (rs != PD_OK) return rs;
+  MixedState* M = s->mixed;
+  cudaStream_t st = s->stream;
+  const int64_t n3 = 3 * s->m;
+  const bool warm = s->precision == PD_PCG_WARM;
+  const pdtc::Mode mode = s->precision == PD_FP32_IR ? pdtc::TF32X3
+                          : s->precision == PD_TF32_IR ? pdtc::TF32
+                          : s->precision == PD_BF16_IR ? pdtc::BF16 : pdtc::TF32X3;
+  // 4.3: contact update + low-precision refactorisation (not needed for the warm PCG form)
+  Factor* f = &M->f;
+  if (warm) {
+    f = &M->f0;
+    if (!f->valid) {
+      factor_cast(s, *f, false);
+      factor_panels(s, *f, pdtc::TF32X3);
+    }
+    s->tbegin(4);
+  } else {
+    s->tbegin(2);
+    factor_cast(s, *f, true);
+    s->tend();
+    s->tbegin(4);
+    factor_panels(s, *f, mode);
+  }
+  // u = u0 (or 0); r = g - H u
+  if (u0) cudaMemcpyAsync(u, u0, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st);
+  else cudaMemsetAsync(u, 0, sizeof(double) * n3, st);
+  hmatvec(s, u, M->q);
+  k_sub<<<nblk(n3, 256), 256, 0, st>>>(g, M->q, M->r, n3); ++pdk::g_launches;
+  dot(s, g, g, 4);
+  dot(s, M->r, M->r, 0);
+  const double gg = read_slot(s, 4);
+  const double tol2 = s->opt.tol * s->opt.tol * (gg > 0 ? gg : 1.0);
+  double rr = read_slot(s, 0);
+  int it = 0;
+  bool ok = rr <= tol2;
+  const bool use_cg = warm || mode != pdtc::TF32X3;
+  cudaError_t ce = cudaSuccess;
+  if (!ok && !use_cg) {
+    // classic refinement: u += M^-1 r; r = g - H u (FP64)
+    for (it = 1; it <= s->opt.max_refine; ++it) {
+      ce = precond(s, *f, M->r, M->z);
+      if (ce != cudaSuccess) break;
+      k_add<<<nblk(n3, 256), 256, 0, st>>>(u, M->z, n3); ++pdk::g_launches;
+      hmatvec(s, u, M->q);
+      k_sub<<<nblk(n3, 256), 256, 0, st>>>(g, M->q, M->r, n3); ++pdk::g_launches;
+      dot(s, M->r, M->r, 0);
+      rr = read_slot(s, 0);
+      if (rr <= tol2 || !std::isfinite(rr)) break;
+    }
+    ok = rr <= tol2;
+  } else if (!ok) {
+    // refinement accelerated by preconditioned CG (FP64 vectors, true residual checked at the end)
+    ce = precond(s, *f, M->r, M->z);
+    dot(s, M->r, M->z, 1);
+    k_cg_dir<<<nblk(n3, 256), 256, 0, st>>>(M->p, M->z, M->sc, n3, 1); ++pdk::g_launches;
+    for (it = 1; it <= s->opt.max_refine && ce == cudaSuccess; ++it) {
+      hmatvec(s, M->p, M->q);
+      dot(s, M->p, M->q, 2);
+      k_cg_step<<<nblk(n3, 256), 256, 0, st>>>(u, M->r, M->p, M->q, M->sc, n3); ++pdk::g_launches;
+      dot(s, M->r, M->r, 0);
+      rr = read_slot(s, 0);
+      if (!std::isfinite(rr)) break;
+      if (rr <= tol2) {   // confirm with the true residual
+        hmatvec(s, u, M->q);
+        k_sub<<<nblk(n3, 256), 256, 0, st>>>(g, M->q, M->r, n3); ++pdk::g_launches;
+        dot(s, M->r, M->r, 0);
+        rr = read_slot(s, 0);
+        if (rr <= tol2) break;
+      }
+      cudaMemcpyAsync(M->sc + 3, M->sc + 1, sizeof(double), cudaMemcpyDeviceToDevice, st);
+      ce = precond(s, *f, M->r, M->z);
+      dot(s, M->r, M->z, 1);
+      k_cg_dir<<<nblk(n3, 256), 256, 0, st>>>(M->p, M->z, M->sc, n3, 0); ++pdk::g_launches;
+    }
+    ok = rr <= tol2;
+  }
+  s->tend();
+  s->last_refine = it;
+  s->last_residual = std::sqrt(rr / (gg > 0 ? gg : 1.0));
+  if (ce != cudaSuccess) {
+    s->err = std::string("cooperative launch failed: ") + cudaGetErrorString(ce);
+    return PD_ERR_CUDA;
+  }
+  if (!ok) {
+    int h[4] = {0, 0, 0, 0};
+    cudaMemcpy(h, s->status, sizeof h, cudaMemcpyDeviceToHost);
+    if (h[0]) {
+      s->err = "low-precision Cholesky pivot " + std::to_string(h[0] - 1) + " is not positive";
+      return PD_ERR_NOT_SPD;
+    }
+    if (h[1]) {
+      s->err = "a bounded device wait gave up (code " + std::to_string(h[1]) + ")";
+      return PD_ERR_TIMEOUT;
+    }
+    s->err = "refinement reached relative residual " + std::to_string(s->last_residual) + " after " +
+             std::to_string(it) + " iterations (tol " + std::to_string(s->opt.tol) + ")";
+    return PD_ERR_NO_CONVERGENCE;
+  }
+  return PD_OK;
+}
+
+void mixed_free(pd_solver* s) {
+  if (!s->mixed) return;
+  if (s->mixed->sc_h) cudaFreeHost(s->mixed->sc_h);
+  delete s->mixed;   // device buffers are in s->allocs
+  s->mixed = nullptr;
+}
+
+void mixed_invalidate(pd_solver* s) {
+  if (s->mixed) s->mixed->f0.valid = false;
+}
+
 }  // namespace pdm

@@ -5,4 +5,5 @@ struct pd_solver;
 namespace pdm {
 pd_status mixed_solve(pd_solver* s, const double* g, const double* u0, double* u);
 void mixed_free(pd_solver* s);
+void mixed_invalidate(pd_solver* s);
 }  // namespace pdm

@@ -347,6 +347,8 @@ pd_status pd_schur_solve_dev(pd_solver* s, const double* g_dev, const double* u0
   if (!s || !g_dev || !u_dev) return PD_ERR_INVALID_ARG;
   CK(cudaMemsetAsync(s->status, 0, sizeof(int) * 4, s->stream));
   pd_status r = s->region_solve(g_dev, u0_dev, u_dev);
+  s->stats.refine_iters = s->last_refine;
+  s->stats.residual = s->last_residual;
   if (r != PD_OK) return r;
   CK(cudaGetLastError());
   return s->check_status();

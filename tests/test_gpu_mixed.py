@@ -1,0 +1,83 @@
+"""Mixed-precision and PCG forms of the region solve vs the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+from gpu_util import need_gpu, rng, contact_tuple, region_callback, oracle_callback
+from test_gpu_parity import _oracle_H, _solver
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def pd():
+    need_gpu()
+    import paper_2008_01541_b300 as pd
+    return pd
+
+
+def _scene(name):
+    if name == "config1":
+        s = scenes.config1(pre_indent=0.8)
+        return s, s.contacts(0, s.X)
+    s = scenes.small_elbow() if name == "small_elbow" else scenes.small_elbow(h=1.0)
+    c = s.contacts(58, s.X)
+    if c.k == 0:
+        c = scenes.sphere_contacts(s.proxies, s.X, s.X[s.proxies].mean(0), 3.0, 1e6)
+    return s, c
+
+
+PRECS = ["FP32_IR", "TF32_IR", "BF16_IR", "PCG_WARM"]
+
+
+@pytest.mark.parametrize("name", ["config1", "small_elbow", "medium_elbow"])
+def test_mixed_forms_reach_1e10_residual(pd, name):
+    s, c = _scene(name)
+    S0, H = _oracle_H(s, c)
+    sol = _solver(pd, s, max_refine=500)
+    sol.set_contacts(*contact_tuple(c))
+    g = rng(3).normal(size=(s.m, 3)) * 1e3
+    uo = np.linalg.solve(H, g)
+    for p in PRECS:
+        sol.set_precision(getattr(pd, p))
+        u = sol.schur_solve(g)
+        res = np.linalg.norm(g - H @ u) / np.linalg.norm(g)
+        st = sol.stats()
+        assert res <= TOL, (p, res, st["refine_iters"])
+        assert np.linalg.norm(u - uo) / np.linalg.norm(uo) <= 1e3 * TOL, p
+        assert st["refine_iters"] >= 1
+        assert st["residual"] <= TOL
+
+
+def test_warm_start_cuts_pcg_iterations(pd):
+    s, c = _scene("small_elbow")
+    S0, H = _oracle_H(s, c)
+    sol = _solver(pd, s, max_refine=500, precision=pd.PCG_WARM)
+    sol.set_contacts(*contact_tuple(c))
+    g = rng(4).normal(size=(s.m, 3)) * 1e3
+    sol.schur_solve(g)
+    cold = sol.stats()["refine_iters"]
+    uo = np.linalg.solve(H, g)
+    u = sol.schur_solve(g, u0=uo * (1 + 1e-6 * rng(5).normal(size=uo.shape)))
+    warm = sol.stats()["refine_iters"]
+    assert np.linalg.norm(g - H @ u) / np.linalg.norm(g) <= TOL
+    assert warm < cold
+
+
+@pytest.mark.parametrize("prec", ["FP32_IR", "BF16_IR"])
+def test_outer_iteration_mixed_matches_oracle(pd, prec):
+    s = scenes.config1(pre_indent=0.6)
+    x0 = s.X.copy()
+    free = np.setdiff1d(np.arange(s.n), s.dirichlet)
+    x0[free] += 0.05 * rng(6).normal(size=(len(free), 3))
+    sol = _solver(pd, s, inner_iters=2, precision=getattr(pd, prec), max_refine=200)
+    sol.set_state(x0)
+    sol.set_dirichlet(s.dirichlet_positions(0))
+    sol.step(1, region_callback(s, 0, x0))
+    o = oracle.OracleSolver(s.X, s.tets, s.dirichlet, s.region, s.mu, s.density, s.dt)
+    o.x = x0.copy()
+    xo = o.step(1, 2, oracle_callback(s, 0), s.dirichlet_positions(0))
+    err = np.linalg.norm(sol.positions() - xo) / np.linalg.norm(xo - x0)
+    assert err <= 1e-8, err
