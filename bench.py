@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "tf32", "bf16", "pcg"])
     ap.add_argument("--h", type=float, default=0.585, help="elbow voxel spacing (0.585 -> ~598K tets)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip timing the other precision forms")
     return ap.parse_args()
 
 
@@ -100,6 +101,41 @@ class ClockSampler:
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+def time_forms(pd, sol, stream, args, fp64_ms, torch):
+    """Every precision form of the region solve on the same scene and state:
+    device-timed ms per step, PD iters/s, speedup over the FP64 form, the
+    Schur refactor+solve time and the refinement iterations it took to reach
+    the 1e-10 relative residual."""
+    out = {}
+    state = sol.get_state()
+    for name, prec in (("fp32_ir (split-TF32 tcgen05)", pd.FP32_IR), ("tf32_ir (TF32 tcgen05, CG-refined)", pd.TF32_IR),
+                       ("bf16_ir (BF16 tcgen05, CG-refined)", pd.BF16_IR), ("pcg (contact-free preconditioner, cold start)", pd.PCG_WARM)):
+        sol.set_state(*state)
+        sol.set_precision(prec)
+        for _ in range(3):
+            sol.step(1)
+        schur = iters = res = 0.0
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            sol.step(1)
+            st = sol.stats()
+            schur += st["ms_contact_update"] + st["ms_factor_solve"]
+            iters += st["refine_iters"]
+            res = max(res, st["residual"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        out[name] = {"ms_per_step": ms, "value": 1e3 / ms, "unit": UNIT, "speedup_vs_fp64": fp64_ms / ms,
+                     "schur_refactor_solve_ms": schur / args.steps, "refine_iters": iters / args.steps,
+                     "max_rel_residual": res}
+    sol.set_precision(pd.FP64)
+    sol.set_state(*state)
+    return out
 
 
 def cpu_baseline(scene, x_state):
@@ -170,7 +206,7 @@ def main():
     stream = torch.cuda.Stream()
     t_setup = time.perf_counter()
     sol = pd.Solver(s.X, s.tets, s.region, s.dirichlet, s.mu, 0.0, 0.0, 0.0, precision=prec,
-                    inner_iters=1, stream=stream.cuda_stream, timing=True)
+                    inner_iters=1, stream=stream.cuda_stream, timing=True, max_refine=500)
     setup_s = time.perf_counter() - t_setup
     rest = s.info["rest_step"]
     con = s.contacts(CONTACT_STEP, s.X)
@@ -264,6 +300,8 @@ def main():
         "clocks": clk,
         "setup_s": setup_s,
     }
+    if not args.no_forms:
+        line["forms"] = time_forms(pd, sol, stream, args, ms / args.steps, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         x_now = sol.positions()
         line["cpu_baseline"] = cpu_baseline(s, x_now)

@@ -27,6 +27,8 @@ constexpr int PADW = NB + 1; // padded shared-memory row
 struct Factor {
   float* L = nullptr;         // [mq][mq] row-major, lower tiles hold the factor
   float* Dinv = nullptr;      // [T][128][128] row-major inverses of the diagonal tiles
+  float* E = nullptr;         // [T][128][128] Dinv^T Dinv per diagonal tile
+  float* Lh = nullptr;        // [mq][mq] row-major, Lh_ik = L_ik Dinv_k (i > k)
   __nv_bfloat16* Pb = nullptr;  // [mq][128] BF16 copy of the current panel
   double* d = nullptr;        // [mq] equilibration D
   CUtensorMap mapL{}, mapP{};
@@ -39,7 +41,7 @@ struct MixedState {
   double *hdiag = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *u = nullptr;
   double* sc = nullptr;       // device scalars: [0] r.r  [1] r.z  [2] p.q  [3] r.z old  [4] g.g
   double* sc_h = nullptr;     // pinned copy
-  float *w = nullptr, *y = nullptr, *uo = nullptr;   // [mq][3] triangular-solve vectors
+  float *w = nullptr, *uo = nullptr;   // [mq][3] triangular-solve vectors
   unsigned* bar = nullptr;    // grid-barrier counter
   int coop_grid = 0;
 };
@@ -96,60 +98,128 @@ __global__ void k_contact_scatter_f32(int64_t k, const int32_t* cidx, const doub
   atomicAdd(L + (int64_t)ra * mq + rb, (float)(cs[j] * cw[4 * j + a] * cw[4 * j + b] * d[ra] * d[rb]));
 }
 
-// Factor the diagonal tile (kt, kt) in FP32 and invert it.
+// Factor the diagonal tile (kt, kt) in FP32, invert it, and form
+// E = Dinv^T Dinv.  Blocked in shared memory with 32-wide sub-blocks: warp 0
+// factors and inverts each 32 x 32 diagonal sub-block, all warps solve the
+// sub-panel below it and update the trailing sub-matrix; the off-diagonal
+// blocks of the inverse follow by block forward substitution.
 __global__ void __launch_bounds__(512) k_diag_f32(float* __restrict__ L, int64_t mq, int kt,
-                                                  float* __restrict__ Dinv, int* __restrict__ status) {
+                                                  float* __restrict__ Dinv, float* __restrict__ Eout,
+                                                  int* __restrict__ status) {
   extern __shared__ float sm[];
-  float* A = sm;                // A[r*PADW + c]
-  float* Z = sm + NB * PADW;    // inverse
-  __shared__ float piv;
-  const int tid = threadIdx.x;
+  float* A = sm;                   // [128][PADW]
+  float* Z = sm + NB * PADW;       // [128][PADW] inverse
+  float* S = sm + 2 * NB * PADW;   // [3][32][33] scratch
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   float* Lt = L + (int64_t)kt * NB * mq + (int64_t)kt * NB;
   for (int q = tid; q < NB * NB; q += 512) {
     int r = q / NB, c = q % NB;
     A[r * PADW + c] = Lt[(int64_t)r * mq + c];
-    Z[r * PADW + c] = (r == c) ? 1.f : 0.f;
+    Z[r * PADW + c] = 0.f;
   }
   __syncthreads();
-  for (int j = 0; j < NB; ++j) {
-    if (tid == 0) {
-      float dj = A[j * PADW + j];
-      if (!(dj > 0.f) || !isfinite(dj)) {
-        atomicCAS(status, 0, kt * NB + j + 1);
-        dj = 1.f;
+  for (int p = 0; p < 4; ++p) {
+    const int c0 = 32 * p;
+    float* Ap = A + c0 * PADW + c0;
+    float* Zp = Z + c0 * PADW + c0;
+    if (warp == 0) {
+      for (int j = 0; j < 32; ++j) {
+        if (lane == j) {
+          float d = Ap[j * PADW + j];
+          if (!(d > 0.f) || !isfinite(d)) {
+            atomicCAS(status, 0, kt * NB + c0 + j + 1);
+            d = 1.f;
+          }
+          Ap[j * PADW + j] = sqrtf(d);
+        }
+        __syncwarp();
+        const float pj = Ap[j * PADW + j];
+        if (lane > j) Ap[lane * PADW + j] /= pj;
+        __syncwarp();
+        if (lane > j) {
+          const float lij = Ap[lane * PADW + j];
+          for (int c = j + 1; c <= lane; ++c) Ap[lane * PADW + c] -= lij * Ap[c * PADW + j];
+        }
+        __syncwarp();
       }
-      piv = sqrtf(dj);
-      A[j * PADW + j] = piv;
+      // inverse of the 32 x 32 block, lane = column
+      for (int i = 0; i < 32; ++i) Zp[i * PADW + lane] = (i == lane) ? 1.f : 0.f;
+      __syncwarp();
+      for (int j = 0; j < 32; ++j) {
+        if (lane <= j) Zp[j * PADW + lane] /= Ap[j * PADW + j];
+        __syncwarp();
+        if (lane <= j) {
+          const float zj = Zp[j * PADW + lane];
+          for (int i = j + 1; i < 32; ++i) Zp[i * PADW + lane] -= Ap[i * PADW + j] * zj;
+        }
+        __syncwarp();
+      }
     }
     __syncthreads();
-    const float ip = 1.f / piv;
-    if (tid > j && tid < NB) A[tid * PADW + j] *= ip;
+    // sub-panel below: row r of L = A[r, c0:c0+32] inv(L_D)^T
+    const int nbelow = NB - c0 - 32;
+    float val[6];
+    int cnt = 0;
+    for (int q = tid; q < nbelow * 32; q += 512) {
+      const int r = c0 + 32 + q / 32, j = q % 32;
+      float acc = 0.f;
+      for (int t = 0; t <= j; ++t) acc = fmaf(A[r * PADW + c0 + t], Zp[j * PADW + t], acc);
+      val[cnt++] = acc;
+    }
     __syncthreads();
-    const int r = tid % NB;
-    for (int c = j + 1 + tid / NB; c < NB; c += 512 / NB)
-      if (r >= c) A[r * PADW + c] -= A[r * PADW + j] * A[c * PADW + j];
+    cnt = 0;
+    for (int q = tid; q < nbelow * 32; q += 512) {
+      const int r = c0 + 32 + q / 32, j = q % 32;
+      A[r * PADW + c0 + j] = val[cnt++];
+    }
+    __syncthreads();
+    // trailing update of the lower part below and right of the sub-panel
+    for (int q = tid; q < nbelow * nbelow; q += 512) {
+      const int r = c0 + 32 + q / nbelow, c = c0 + 32 + q % nbelow;
+      if (c > r) continue;
+      float acc = 0.f;
+#pragma unroll 8
+      for (int t = 0; t < 32; ++t) acc = fmaf(A[r * PADW + c0 + t], A[c * PADW + c0 + t], acc);
+      A[r * PADW + c] -= acc;
+    }
     __syncthreads();
   }
-  // Z = L^-1: row j scaled, then eliminated from the rows below
-  for (int j = 0; j < NB; ++j) {
-    const float ip = 1.f / A[j * PADW + j];
-    if (tid <= j) Z[j * PADW + tid] *= ip;
+  // off-diagonal 32 x 32 blocks of the inverse: Z_ij = -Z_ii sum_{t=j}^{i-1} L_it Z_tj
+  for (int d = 1; d < 4; ++d) {
+    const int npairs = 4 - d;
+    for (int q = tid; q < npairs * 1024; q += 512) {
+      const int pr = q / 1024, r = (q % 1024) / 32, c = q % 32;
+      const int j = pr, i = pr + d;
+      float acc = 0.f;
+      for (int t = 32 * j; t < 32 * i; ++t) acc = fmaf(A[(32 * i + r) * PADW + t], Z[t * PADW + 32 * j + c], acc);
+      S[pr * 32 * 33 + r * 33 + c] = acc;
+    }
     __syncthreads();
-    const int c = tid % NB;
-    if (c <= j)
-      for (int r = j + 1 + tid / NB; r < NB; r += 512 / NB) Z[r * PADW + c] -= A[r * PADW + j] * Z[j * PADW + c];
+    for (int q = tid; q < npairs * 1024; q += 512) {
+      const int pr = q / 1024, r = (q % 1024) / 32, c = q % 32;
+      const int j = pr, i = pr + d;
+      float acc = 0.f;
+      for (int t = 0; t <= r; ++t) acc = fmaf(Z[(32 * i + r) * PADW + 32 * i + t], S[pr * 32 * 33 + t * 33 + c], acc);
+      Z[(32 * i + r) * PADW + 32 * j + c] = -acc;
+    }
     __syncthreads();
   }
   float* Di = Dinv + (int64_t)kt * NB * NB;
+  float* Ek = Eout + (int64_t)kt * NB * NB;
   for (int q = tid; q < NB * NB; q += 512) {
-    int r = q / NB, c = q % NB;
+    const int r = q / NB, c = q % NB;
     if (c <= r) Lt[(int64_t)r * mq + c] = A[r * PADW + c];
     Di[q] = (c <= r) ? Z[r * PADW + c] : 0.f;
+    // E = Z^T Z (symmetric): E[r][c] = sum_{t >= max(r,c)} Z[t][r] Z[t][c]
+    float e = 0.f;
+    for (int t = (r > c ? r : c); t < NB; ++t) e = fmaf(Z[t * PADW + r], Z[t * PADW + c], e);
+    Ek[q] = e;
   }
 }
 
-// Panel solve: L_ik = A_ik Dinv_k^T for the 64-row slab blockIdx.x below tile kt.
-__global__ void __launch_bounds__(256) k_trsm_f32(float* __restrict__ L, int64_t mq, int kt,
+// Panel solve for the 64-row slab blockIdx.x below tile kt: L_ik = A_ik Dinv_k^T,
+// and the pre-multiplied copy Lh_ik = L_ik Dinv_k used by the preconditioner.
+__global__ void __launch_bounds__(256) k_trsm_f32(float* __restrict__ L, float* __restrict__ Lh, int64_t mq, int kt,
                                                   const float* __restrict__ Dinv, __nv_bfloat16* __restrict__ Pb) {
   extern __shared__ float sm[];
   float* As = sm;               // [64][PADW]
@@ -157,6 +227,7 @@ __global__ void __launch_bounds__(256) k_trsm_f32(float* __restrict__ L, int64_t
   const int tid = threadIdx.x;
   const int64_t r0 = (int64_t)(kt + 1) * NB + (int64_t)blockIdx.x * 64;
   float* Ab = L + r0 * mq + (int64_t)kt * NB;
+  float* Hb = Lh + r0 * mq + (int64_t)kt * NB;
   const float* Di = Dinv + (int64_t)kt * NB * NB;
   for (int q = tid; q < 64 * NB; q += 256) As[(q / NB) * PADW + q % NB] = Ab[(int64_t)(q / NB) * mq + q % NB];
   for (int q = tid; q < NB * NB; q += 256) Ds[(q / NB) * PADW + q % NB] = Di[q];
@@ -174,14 +245,33 @@ __global__ void __launch_bounds__(256) k_trsm_f32(float* __restrict__ L, int64_t
 #pragma unroll
       for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
   }
+  __syncthreads();
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       int rr = tr + 16 * i, cc = tc + 16 * j;
       Ab[(int64_t)rr * mq + cc] = acc[i][j];
+      As[rr * PADW + cc] = acc[i][j];
       if (Pb) Pb[(r0 + rr) * NB + cc] = __float2bfloat16_rn(acc[i][j]);
     }
+  __syncthreads();
+  float h[4][8] = {};
+  for (int t = 0; t < NB; ++t) {
+    float a[4], b[8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = As[(tr + 16 * i) * PADW + t];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) b[j] = Ds[t * PADW + tc + 16 * j];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) h[i][j] = fmaf(a[i], b[j], h[i][j]);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) Hb[(int64_t)(tr + 16 * i) * mq + tc + 16 * j] = h[i][j];
 }
 
 // Bounded grid barrier for the cooperative launch; false = gave up.
@@ -203,36 +293,33 @@ __device__ bool grid_barrier(unsigned* ctr, unsigned target, int* status) {
   return ok != 0;
 }
 
-// z = D L^-T L^-1 D r  for 3 right-hand sides, one cooperative launch.
-__global__ void __launch_bounds__(256) k_precond(const float* __restrict__ L, const float* __restrict__ Dinv,
+// z = D L^-T L^-1 D r for 3 right-hand sides in one cooperative launch.
+// With Lh_ik = L_ik Dinv_k and E_k = Dinv_k^T Dinv_k the block substitutions
+// need no dense diagonal solve inside the sequential loops:
+//   forward : w_i -= Lh_ik w_k for i > k            (k ascending)
+//   middle  : u_k = E_k w_k                          (all k at once)
+//   backward: u_k -= sum_{i > k} Lh_ik^T u_i         (k descending)
+__global__ void __launch_bounds__(256) k_precond(const float* __restrict__ Lh, const float* __restrict__ E,
                                                  int64_t mq, int64_t m, const double* __restrict__ d,
                                                  const double* __restrict__ r, double* __restrict__ z, float* w,
-                                                 float* y, float* uo, unsigned* bar, int* status) {
+                                                 float* uo, unsigned* bar, int* status) {
   __shared__ float vk[NB * 3];
-  __shared__ float ok_s[NB * 3];
+  __shared__ float part[2][NB * 3];
   const int T = (int)(mq / NB);
   const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
   unsigned nb = 0;
   for (int64_t i = (int64_t)b * 256 + tid; i < mq; i += (int64_t)G * 256)
     for (int v = 0; v < 3; ++v) w[3 * i + v] = i < m ? (float)(d[i] * r[3 * i + v]) : 0.f;
   if (!grid_barrier(bar, (unsigned)G * ++nb, status)) return;
-  // forward: y_k = Dinv_k w_k; w_i -= L_ik y_k (i > k)
-  for (int k = 0; k < T; ++k) {
-    const float* Di = Dinv + (int64_t)k * NB * NB;
-    for (int q = tid; q < NB * 3; q += 256) {
-      int rr = q / 3, v = q % 3;
-      float s = 0.f;
-      for (int c = 0; c <= rr; ++c) s = fmaf(Di[rr * NB + c], w[3 * ((int64_t)k * NB + c) + v], s);
-      vk[q] = s;
-    }
+  for (int k = 0; k + 1 < T; ++k) {
+    for (int q = tid; q < NB * 3; q += 256) vk[q] = w[3 * (int64_t)k * NB + q];
     __syncthreads();
-    if (b == 0)
-      for (int q = tid; q < NB * 3; q += 256) y[3 * (int64_t)k * NB + q] = vk[q];
     const int64_t lo = (int64_t)(k + 1) * NB, n = mq - lo;
     const int64_t per = (n + G - 1) / G;
     for (int64_t i = lo + b * per + tid; i < lo + (b + 1) * per && i < mq; i += 256) {
-      const float* Li = L + i * mq + (int64_t)k * NB;
+      const float* Li = Lh + i * mq + (int64_t)k * NB;
       float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll 4
       for (int c = 0; c < NB; c += 4) {
         float4 l4 = *reinterpret_cast<const float4*>(Li + c);
         a0 = fmaf(l4.x, vk[3 * c], a0); a1 = fmaf(l4.x, vk[3 * c + 1], a1); a2 = fmaf(l4.x, vk[3 * c + 2], a2);
@@ -244,28 +331,35 @@ __global__ void __launch_bounds__(256) k_precond(const float* __restrict__ L, co
     }
     if (!grid_barrier(bar, (unsigned)G * ++nb, status)) return;
   }
-  // backward on y: u_k = Dinv_k^T y_k; y_j -= L_kj^T u_k (j < k)
-  for (int k = T - 1; k >= 0; --k) {
-    const float* Di = Dinv + (int64_t)k * NB * NB;
+  for (int k = b; k < T; k += G) {
+    const float* Ek = E + (int64_t)k * NB * NB;
+    for (int q = tid; q < NB * 3; q += 256) vk[q] = w[3 * (int64_t)k * NB + q];
+    __syncthreads();
     for (int q = tid; q < NB * 3; q += 256) {
-      int cc = q / 3, v = q % 3;
+      const int rr = q / 3, v = q % 3;
       float s = 0.f;
-      for (int rr = cc; rr < NB; ++rr) s = fmaf(Di[rr * NB + cc], y[3 * ((int64_t)k * NB + rr) + v], s);
-      ok_s[q] = s;
+      for (int c = 0; c < NB; ++c) s = fmaf(Ek[rr * NB + c], vk[3 * c + v], s);
+      uo[3 * (int64_t)k * NB + q] = s;
     }
     __syncthreads();
-    if (b == 0)
-      for (int q = tid; q < NB * 3; q += 256) uo[3 * (int64_t)k * NB + q] = ok_s[q];
-    const int64_t n = (int64_t)k * NB;
+  }
+  if (!grid_barrier(bar, (unsigned)G * ++nb, status)) return;
+  for (int k = T - 2; k >= 0; --k) {
+    const int64_t lo = (int64_t)(k + 1) * NB, n = mq - lo;
     const int64_t per = (n + G - 1) / G;
-    const float* Lk = L + (int64_t)k * NB * mq;
-    for (int64_t j = b * per + tid; j < (b + 1) * per && j < n; j += 256) {
-      float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-      for (int rr = 0; rr < NB; ++rr) {
-        float l = Lk[(int64_t)rr * mq + j];
-        a0 = fmaf(l, ok_s[3 * rr], a0); a1 = fmaf(l, ok_s[3 * rr + 1], a1); a2 = fmaf(l, ok_s[3 * rr + 2], a2);
+    const int c = tid % NB, half = tid / NB;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    for (int64_t i = lo + b * per + half; i < lo + (b + 1) * per && i < mq; i += 2) {
+      const float l = Lh[i * mq + (int64_t)k * NB + c];
+      a0 = fmaf(l, uo[3 * i], a0); a1 = fmaf(l, uo[3 * i + 1], a1); a2 = fmaf(l, uo[3 * i + 2], a2);
+    }
+    part[half][3 * c] = a0; part[half][3 * c + 1] = a1; part[half][3 * c + 2] = a2;
+    __syncthreads();
+    if (tid < NB * 3 / 2 * 2 && tid < NB) {
+      for (int v = 0; v < 3; ++v) {
+        const float t = part[0][3 * tid + v] + part[1][3 * tid + v];
+        if (t != 0.f) atomicAdd(uo + 3 * ((int64_t)k * NB + tid) + v, -t);
       }
-      y[3 * j] -= a0; y[3 * j + 1] -= a1; y[3 * j + 2] -= a2;
     }
     if (!grid_barrier(bar, (unsigned)G * ++nb, status)) return;
   }
@@ -350,6 +444,7 @@ static pd_status ensure_state(pd_solver* s) {
   const int64_t mq = M->mq, m = s->m;
   for (Factor* f : {&M->f, &M->f0}) {
     if (A((void**)&f->L, sizeof(float) * mq * mq) || A((void**)&f->Dinv, sizeof(float) * mq * NB) ||
+        A((void**)&f->E, sizeof(float) * mq * NB) || A((void**)&f->Lh, sizeof(float) * mq * mq) ||
         A((void**)&f->Pb, sizeof(__nv_bfloat16) * mq * NB) || A((void**)&f->d, sizeof(double) * mq)) {
       s->err = "device allocation for the mixed-precision factor failed";
       return PD_ERR_OOM;
@@ -363,7 +458,7 @@ static pd_status ensure_state(pd_solver* s) {
       A((void**)&M->z, sizeof(double) * 3 * m) || A((void**)&M->p, sizeof(double) * 3 * m) ||
       A((void**)&M->q, sizeof(double) * 3 * m) || A((void**)&M->u, sizeof(double) * 3 * m) ||
       A((void**)&M->sc, sizeof(double) * 8) || A((void**)&M->w, sizeof(float) * 3 * mq) ||
-      A((void**)&M->y, sizeof(float) * 3 * mq) || A((void**)&M->uo, sizeof(float) * 3 * mq) ||
+      A((void**)&M->uo, sizeof(float) * 3 * mq) ||
       A((void**)&M->bar, sizeof(unsigned) * 4)) {
     s->err = "device allocation for the mixed-precision vectors failed";
     return PD_ERR_OOM;
@@ -380,7 +475,7 @@ static pd_status ensure_state(pd_solver* s) {
   }
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_diag_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * NB * PADW * 4);
+    cudaFuncSetAttribute(k_diag_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (2 * NB * PADW + 3 * 32 * 33) * 4);
     cudaFuncSetAttribute(k_trsm_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (64 + NB) * PADW * 4);
     attr = true;
   }
@@ -409,10 +504,11 @@ static void factor_panels(pd_solver* s, Factor& f, pdtc::Mode mode) {
   const int64_t mq = M->mq, T = M->T;
   cudaStream_t st = s->stream;
   for (int kt = 0; kt < T; ++kt) {
-    k_diag_f32<<<1, 512, 2 * NB * PADW * 4, st>>>(f.L, mq, kt, f.Dinv, s->status); ++pdk::g_launches;
+    k_diag_f32<<<1, 512, (2 * NB * PADW + 3 * 32 * 33) * 4, st>>>(f.L, mq, kt, f.Dinv, f.E, s->status);
+    ++pdk::g_launches;
     const int n = (int)(T - kt - 1);
     if (n <= 0) break;
-    k_trsm_f32<<<(unsigned)(2 * n), 256, (64 + NB) * PADW * 4, st>>>(f.L, mq, kt, f.Dinv,
+    k_trsm_f32<<<(unsigned)(2 * n), 256, (64 + NB) * PADW * 4, st>>>(f.L, f.Lh, mq, kt, f.Dinv,
                                                                     mode == pdtc::BF16 ? f.Pb : nullptr);
     ++pdk::g_launches;
     if (mode == pdtc::BF16)
@@ -426,15 +522,15 @@ static void factor_panels(pd_solver* s, Factor& f, pdtc::Mode mode) {
 static cudaError_t precond(pd_solver* s, const Factor& f, const double* r, double* z) {
   MixedState* M = s->mixed;
   cudaMemsetAsync(M->bar, 0, sizeof(unsigned), s->stream);
-  const float* L = f.L;
-  const float* Di = f.Dinv;
+  const float* Lh = f.Lh;
+  const float* E = f.E;
   int64_t mq = M->mq, m = s->m;
   const double* d = f.d;
-  float *w = M->w, *y = M->y, *uo = M->uo;
+  float *w = M->w, *uo = M->uo;
   unsigned* bar = M->bar;
   int* status = s->status;
-  void* args[] = {(void*)&L, (void*)&Di, (void*)&mq, (void*)&m, (void*)&d, (void*)&r, (void*)&z,
-                  (void*)&w, (void*)&y, (void*)&uo, (void*)&bar, (void*)&status};
+  void* args[] = {(void*)&Lh, (void*)&E, (void*)&mq, (void*)&m, (void*)&d, (void*)&r, (void*)&z,
+                  (void*)&w, (void*)&uo, (void*)&bar, (void*)&status};
   ++pdk::g_launches;
   return cudaLaunchCooperativeKernel((void*)k_precond, dim3(M->coop_grid), dim3(256), args, 0, s->stream);
 }

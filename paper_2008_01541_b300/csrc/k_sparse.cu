@@ -4,145 +4,144 @@
 // (nc + nr) x nc column-major: the first nc rows hold the inverse of the
 // diagonal block (lower), the next nr rows the off-diagonal block whose row
 // positions are rows[rowptr[s]..].  Rows >= n1 are x_2 rows (the L_21 part).
+//
 // Supernodes are processed level by level (height in the supernodal
-// elimination tree), all supernodes of a level in parallel.
+// elimination tree).  Within a level the work is cut into 64 x 64 tiles of
+// the panels; one CTA per tile accumulates its partial products into the
+// destination vector with FP64 atomics, so a large separator is spread over
+// many SMs instead of a few long per-row loops.
 #include "kernels.h"
 
 namespace pdk {
 namespace {
 
-// y_s = Dinv_s b_s  (one thread per column item of the level)
-__global__ void k_fwd_diag(int64_t n_items, const int32_t* __restrict__ isn, const int32_t* __restrict__ ii,
-                           const int32_t* __restrict__ col0, const int64_t* __restrict__ rowptr,
-                           const int64_t* __restrict__ valptr, const double* __restrict__ L,
-                           const double* __restrict__ b, double* __restrict__ y) {
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= n_items) return;
-  int s = isn[t], i = ii[t];
-  int64_t c0 = col0[s], nc = col0[s + 1] - c0, ld = nc + (rowptr[s + 1] - rowptr[s]);
-  const double* P = L + valptr[s];
+constexpr int TT = 64;
+
+// Forward tile: dst[...] += sign * sum_c P[row + c*ld] src[c0 + c]
+// diag tiles: rows/cols within the diagonal block, c <= row, dst = y[c0 + row], sign +1
+// off  tiles: rows within the off-diagonal block, dst = b[rows[r]], sign -1
+__global__ void __launch_bounds__(256) k_fwd_tiles(const int4* __restrict__ tasks, int diag,
+                                                   const int32_t* __restrict__ col0, const int64_t* __restrict__ rowptr,
+                                                   const int32_t* __restrict__ rows, const int64_t* __restrict__ valptr,
+                                                   const double* __restrict__ L, const double* __restrict__ src,
+                                                   double* __restrict__ dst) {
+  __shared__ double part[4][TT][3];
+  const int4 tk = tasks[blockIdx.x];
+  const int s = tk.x, rb = tk.y, cb = tk.z;
+  const int64_t c0 = col0[s], nc = col0[s + 1] - c0, nr = rowptr[s + 1] - rowptr[s], ld = nc + nr;
+  const int tid = threadIdx.x, rloc = tid % TT, chunk = tid / TT;
+  const int64_t r = rb + rloc;                       // row within the diag or off block
+  const int64_t nrows = diag ? nc : nr;
+  const double* P = L + valptr[s] + (diag ? 0 : nc);
   double a0 = 0, a1 = 0, a2 = 0;
-  for (int64_t j = 0; j <= i; ++j) {
-    double d = P[i + j * ld];
-    const double* bj = b + 3 * (c0 + j);
-    a0 += d * bj[0]; a1 += d * bj[1]; a2 += d * bj[2];
+  if (r < nrows) {
+    const int64_t cend = min((int64_t)cb + TT, nc);
+    for (int64_t c = cb + chunk * 16; c < cb + chunk * 16 + 16 && c < cend; ++c) {
+      if (diag && c > r) break;
+      const double l = P[r + c * ld];
+      const double* x = src + 3 * (c0 + c);
+      a0 = fma(l, x[0], a0); a1 = fma(l, x[1], a1); a2 = fma(l, x[2], a2);
+    }
   }
-  double* yi = y + 3 * (c0 + i);
-  yi[0] = a0; yi[1] = a1; yi[2] = a2;
+  part[chunk][rloc][0] = a0; part[chunk][rloc][1] = a1; part[chunk][rloc][2] = a2;
+  __syncthreads();
+  if (chunk == 0 && r < nrows) {
+    for (int q = 1; q < 4; ++q) { a0 += part[q][rloc][0]; a1 += part[q][rloc][1]; a2 += part[q][rloc][2]; }
+    if (diag) {
+      double* d = dst + 3 * (c0 + r);
+      atomicAdd(d, a0); atomicAdd(d + 1, a1); atomicAdd(d + 2, a2);
+    } else {
+      double* d = dst + 3 * (int64_t)rows[rowptr[s] + r];
+      atomicAdd(d, -a0); atomicAdd(d + 1, -a1); atomicAdd(d + 2, -a2);
+    }
+  }
 }
 
-// b[rows[r]] -= L_rs y_s  (one thread per off-diagonal row item)
-__global__ void k_fwd_off(int64_t n_items, const int32_t* __restrict__ isn, const int32_t* __restrict__ ir,
-                          const int32_t* __restrict__ col0, const int64_t* __restrict__ rowptr,
-                          const int32_t* __restrict__ rows, const int64_t* __restrict__ valptr,
-                          const double* __restrict__ L, const double* __restrict__ y, double* __restrict__ b) {
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= n_items) return;
-  int s = isn[t], r = ir[t];
-  int64_t c0 = col0[s], nc = col0[s + 1] - c0, ld = nc + (rowptr[s + 1] - rowptr[s]);
-  const double* P = L + valptr[s] + nc + r;
-  double a0 = 0, a1 = 0, a2 = 0;
-  for (int64_t j = 0; j < nc; ++j) {
-    double l = P[j * ld];
-    const double* yj = y + 3 * (c0 + j);
-    a0 += l * yj[0]; a1 += l * yj[1]; a2 += l * yj[2];
-  }
-  double* br = b + 3 * (int64_t)rows[rowptr[s] + r];
-  atomicAdd(br, -a0); atomicAdd(br + 1, -a1); atomicAdd(br + 2, -a2);
-}
-
-// z_j = y_j - sum_r L_rj u_{rows[r]}  (one warp per column item)
-__global__ void k_bwd_off(int64_t n_items, const int32_t* __restrict__ isn, const int32_t* __restrict__ ii,
-                          const int32_t* __restrict__ col0, const int64_t* __restrict__ rowptr,
-                          const int32_t* __restrict__ rows, const int64_t* __restrict__ valptr,
-                          const double* __restrict__ L, const double* __restrict__ y,
-                          const double* __restrict__ u, double* __restrict__ z) {
-  int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (t >= n_items) return;
-  int s = isn[t], j = ii[t];
-  int64_t c0 = col0[s], nc = col0[s + 1] - c0, nr = rowptr[s + 1] - rowptr[s], ld = nc + nr;
-  const double* P = L + valptr[s] + nc + j * ld;
+// Backward tile (transposed), staged through shared memory so that the
+// global loads stay coalesced along the panel's columns:
+// off : z[c0 + j] -= sum_r P[r + j*ld] u[rows[r]]
+// diag: u[c0 + j] += sum_{r >= j} Dinv[r + j*ld] z[c0 + r]
+__global__ void __launch_bounds__(256) k_bwd_tiles(const int4* __restrict__ tasks, int diag,
+                                                   const int32_t* __restrict__ col0, const int64_t* __restrict__ rowptr,
+                                                   const int32_t* __restrict__ rows, const int64_t* __restrict__ valptr,
+                                                   const double* __restrict__ L, const double* __restrict__ src,
+                                                   double* __restrict__ dst) {
+  __shared__ double tile[TT][TT + 1];
+  __shared__ double xs[TT][3];
+  __shared__ double part[4][TT][3];
+  const int4 tk = tasks[blockIdx.x];
+  const int s = tk.x, rb = tk.y, cb = tk.z;
+  const int64_t c0 = col0[s], nc = col0[s + 1] - c0, nr = rowptr[s + 1] - rowptr[s], ld = nc + nr;
+  const int64_t nrows = diag ? nc : nr;
+  const double* P = L + valptr[s] + (diag ? 0 : nc);
   const int32_t* R = rows + rowptr[s];
+  const int tid = threadIdx.x;
+  for (int q = tid; q < TT * TT; q += 256) {
+    const int r = q % TT, j = q / TT;
+    const int64_t gr = rb + r, gj = cb + j;
+    double v = 0.0;
+    if (gr < nrows && gj < nc && !(diag && gr < gj)) v = P[gr + gj * ld];
+    tile[r][j] = v;
+  }
+  if (tid < TT) {
+    const int64_t gr = rb + tid;
+    if (gr < nrows) {
+      const double* x = diag ? src + 3 * (c0 + gr) : src + 3 * (int64_t)R[gr];
+      xs[tid][0] = x[0]; xs[tid][1] = x[1]; xs[tid][2] = x[2];
+    } else {
+      xs[tid][0] = xs[tid][1] = xs[tid][2] = 0.0;
+    }
+  }
+  __syncthreads();
+  const int j = tid % TT, rc = tid / TT;
   double a0 = 0, a1 = 0, a2 = 0;
-  for (int64_t r = lane; r < nr; r += 32) {
-    double l = P[r];
-    const double* ur = u + 3 * (int64_t)R[r];
-    a0 += l * ur[0]; a1 += l * ur[1]; a2 += l * ur[2];
+#pragma unroll 4
+  for (int r = rc * 16; r < rc * 16 + 16; ++r) {
+    const double l = tile[r][j];
+    a0 = fma(l, xs[r][0], a0); a1 = fma(l, xs[r][1], a1); a2 = fma(l, xs[r][2], a2);
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-    a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-  }
-  if (lane == 0) {
-    const double* yj = y + 3 * (c0 + j);
-    double* zj = z + 3 * (c0 + j);
-    zj[0] = yj[0] - a0; zj[1] = yj[1] - a1; zj[2] = yj[2] - a2;
+  part[rc][j][0] = a0; part[rc][j][1] = a1; part[rc][j][2] = a2;
+  __syncthreads();
+  if (rc == 0 && cb + j < nc) {
+    for (int q = 1; q < 4; ++q) { a0 += part[q][j][0]; a1 += part[q][j][1]; a2 += part[q][j][2]; }
+    double* d = dst + 3 * (c0 + cb + j);
+    const double sg = diag ? 1.0 : -1.0;
+    atomicAdd(d, sg * a0); atomicAdd(d + 1, sg * a1); atomicAdd(d + 2, sg * a2);
   }
 }
-
-// u_i = sum_{j >= i} Dinv_ji z_j  (one warp per column item)
-__global__ void k_bwd_diag(int64_t n_items, const int32_t* __restrict__ isn, const int32_t* __restrict__ ii,
-                           const int32_t* __restrict__ col0, const int64_t* __restrict__ rowptr,
-                           const int64_t* __restrict__ valptr, const double* __restrict__ L,
-                           const double* __restrict__ z, double* __restrict__ u) {
-  int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (t >= n_items) return;
-  int s = isn[t], i = ii[t];
-  int64_t c0 = col0[s], nc = col0[s + 1] - c0, ld = nc + (rowptr[s + 1] - rowptr[s]);
-  const double* P = L + valptr[s] + i * ld;
-  double a0 = 0, a1 = 0, a2 = 0;
-  for (int64_t j = i + lane; j < nc; j += 32) {
-    double d = P[j];
-    const double* zj = z + 3 * (c0 + j);
-    a0 += d * zj[0]; a1 += d * zj[1]; a2 += d * zj[2];
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-    a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-  }
-  if (lane == 0) {
-    double* ui = u + 3 * (c0 + i);
-    ui[0] = a0; ui[1] = a1; ui[2] = a2;
-  }
-}
-
-inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 }  // namespace
 
 void sparse_forward(const SparseFactor& f, double* b, double* y, cudaStream_t st) {
+  cudaMemsetAsync(y, 0, sizeof(double) * 3 * f.n1, st);
   for (int64_t l = 0; l < f.nlevels; ++l) {
-    int64_t c0 = f.lvl_col_ptr[l], c1 = f.lvl_col_ptr[l + 1];
-    int64_t r0 = f.lvl_row_ptr[l], r1 = f.lvl_row_ptr[l + 1];
-    if (c1 > c0) {
-      k_fwd_diag<<<nblk(c1 - c0, 128), 128, 0, st>>>(c1 - c0, f.col_sn + c0, f.col_i + c0, f.col0,
-                                                     f.rowptr, f.valptr, f.L, b, y);
+    int64_t d0 = f.lvl_diag_ptr[l], d1 = f.lvl_diag_ptr[l + 1];
+    int64_t o0 = f.lvl_off_ptr[l], o1 = f.lvl_off_ptr[l + 1];
+    if (d1 > d0) {
+      k_fwd_tiles<<<(unsigned)(d1 - d0), 256, 0, st>>>(f.diag_tasks + d0, 1, f.col0, f.rowptr, f.rows, f.valptr, f.L, b, y);
       ++g_launches;
     }
-    if (r1 > r0) {
-      k_fwd_off<<<nblk(r1 - r0, 128), 128, 0, st>>>(r1 - r0, f.row_sn + r0, f.row_r + r0, f.col0, f.rowptr,
-                                                    f.rows, f.valptr, f.L, y, b);
+    if (o1 > o0) {
+      k_fwd_tiles<<<(unsigned)(o1 - o0), 256, 0, st>>>(f.off_tasks + o0, 0, f.col0, f.rowptr, f.rows, f.valptr, f.L, y, b);
       ++g_launches;
     }
   }
 }
 
 void sparse_backward(const SparseFactor& f, const double* y, double* u, double* z, cudaStream_t st) {
+  cudaMemcpyAsync(z, y, sizeof(double) * 3 * f.n1, cudaMemcpyDeviceToDevice, st);
+  cudaMemsetAsync(u, 0, sizeof(double) * 3 * f.n1, st);
   for (int64_t l = f.nlevels - 1; l >= 0; --l) {
-    int64_t c0 = f.lvl_col_ptr[l], c1 = f.lvl_col_ptr[l + 1];
-    if (c1 <= c0) continue;
-    k_bwd_off<<<nblk((c1 - c0) * 32, 256), 256, 0, st>>>(c1 - c0, f.col_sn + c0, f.col_i + c0, f.col0,
-                                                        f.rowptr, f.rows, f.valptr, f.L, y, u, z);
-    ++g_launches;
-    k_bwd_diag<<<nblk((c1 - c0) * 32, 256), 256, 0, st>>>(c1 - c0, f.col_sn + c0, f.col_i + c0, f.col0,
-                                                         f.rowptr, f.valptr, f.L, z, u);
-    ++g_launches;
+    int64_t d0 = f.lvl_diag_ptr[l], d1 = f.lvl_diag_ptr[l + 1];
+    int64_t o0 = f.lvl_off_ptr[l], o1 = f.lvl_off_ptr[l + 1];
+    if (o1 > o0) {
+      k_bwd_tiles<<<(unsigned)(o1 - o0), 256, 0, st>>>(f.off_tasks + o0, 0, f.col0, f.rowptr, f.rows, f.valptr, f.L, u, z);
+      ++g_launches;
+    }
+    if (d1 > d0) {
+      k_bwd_tiles<<<(unsigned)(d1 - d0), 256, 0, st>>>(f.diag_tasks + d0, 1, f.col0, f.rowptr, f.rows, f.valptr, f.L, z, u);
+      ++g_launches;
+    }
   }
 }
 

@@ -30,11 +30,11 @@ struct SparseFactor {
   const int32_t* rows = nullptr;
   const int64_t* valptr = nullptr;   // [nsn+1]
   const double* L = nullptr;
-  // per-level work lists (host offsets, device items)
-  const int64_t* lvl_col_ptr = nullptr;  // host [nlevels+1] into col items
-  const int64_t* lvl_row_ptr = nullptr;  // host [nlevels+1] into row items
-  const int32_t* col_sn = nullptr;  const int32_t* col_i = nullptr;   // device items: (supernode, column)
-  const int32_t* row_sn = nullptr;  const int32_t* row_r = nullptr;   // device items: (supernode, off-diag row)
+  // per-level 64 x 64 tile tasks {supernode, row offset, col offset, 0}
+  const int64_t* lvl_diag_ptr = nullptr;  // host [nlevels+1] into diag_tasks
+  const int64_t* lvl_off_ptr = nullptr;   // host [nlevels+1] into off_tasks
+  const int4* diag_tasks = nullptr;       // device: tiles of the diagonal blocks (col <= row tile)
+  const int4* off_tasks = nullptr;        // device: tiles of the off-diagonal blocks
 };
 // b [nfree][3] in: forces (factor order).  Out: y[0..n1) = L_1^-1 b_1 and
 // b[n1..nfree) = b_2 - L_21 y_1.

@@ -470,28 +470,27 @@ pd_status pd_solver::upload(const pdh::Setup& h, const pdh::Input& in) {
     int64_t nl = h.nlevels;
     std::vector<std::vector<int32_t>> bylevel(nl);
     for (int64_t k2 = 0; k2 < h.nsn; ++k2) bylevel[h.sn_level[k2]].push_back((int32_t)k2);
-    std::vector<int32_t> csn, ci, rsn, rr;
-    lvl_col_ptr.assign(nl + 1, 0);
-    lvl_row_ptr.assign(nl + 1, 0);
+    std::vector<int4> dt, ot;
+    lvl_diag_ptr.assign(nl + 1, 0);
+    lvl_off_ptr.assign(nl + 1, 0);
     for (int64_t l = 0; l < nl; ++l) {
       for (int32_t sn : bylevel[l]) {
         int32_t nc = h.sn_col0[sn + 1] - h.sn_col0[sn];
-        int64_t nr = h.sn_rowptr[sn + 1] - h.sn_rowptr[sn];
-        for (int32_t i = 0; i < nc; ++i) { csn.push_back(sn); ci.push_back(i); }
-        for (int64_t q = 0; q < nr; ++q) { rsn.push_back(sn); rr.push_back((int32_t)q); }
+        int32_t nr = (int32_t)(h.sn_rowptr[sn + 1] - h.sn_rowptr[sn]);
+        for (int32_t rb = 0; rb < nc; rb += 64)
+          for (int32_t cb = 0; cb <= rb; cb += 64) dt.push_back(make_int4(sn, rb, cb, 0));
+        for (int32_t rb = 0; rb < nr; rb += 64)
+          for (int32_t cb = 0; cb < nc; cb += 64) ot.push_back(make_int4(sn, rb, cb, 0));
       }
-      lvl_col_ptr[l + 1] = (int64_t)csn.size();
-      lvl_row_ptr[l + 1] = (int64_t)rsn.size();
+      lvl_diag_ptr[l + 1] = (int64_t)dt.size();
+      lvl_off_ptr[l + 1] = (int64_t)ot.size();
     }
-    CK(dupload(s, &col_sn, csn.data(), csn.size()));
-    CK(dupload(s, &col_i, ci.data(), ci.size()));
-    CK(dupload(s, &row_sn, rsn.data(), rsn.size()));
-    CK(dupload(s, &row_r, rr.data(), rr.size()));
+    CK(dupload(s, &diag_tasks, dt.data(), dt.size()));
+    CK(dupload(s, &off_tasks, ot.data(), ot.size()));
     sf.n1 = n1; sf.nfree = nfree; sf.nsn = h.nsn; sf.nlevels = nl;
     sf.col0 = sn_col0; sf.rowptr = sn_rowptr; sf.rows = rows; sf.valptr = sn_valptr; sf.L = Lval;
-    sf.lvl_col_ptr = lvl_col_ptr.data(); sf.lvl_row_ptr = lvl_row_ptr.data();
-    sf.col_sn = col_sn; sf.col_i = col_i; sf.row_sn = row_sn; sf.row_r = rr.empty() ? nullptr : row_r;
-    sf.row_r = row_r;
+    sf.lvl_diag_ptr = lvl_diag_ptr.data(); sf.lvl_off_ptr = lvl_off_ptr.data();
+    sf.diag_tasks = diag_tasks; sf.off_tasks = off_tasks;
   }
   CK(dalloc(s, &b, 3 * nfree));
   CK(dalloc(s, &yv, 3 * nfree));

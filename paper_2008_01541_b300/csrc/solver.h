@@ -50,8 +50,8 @@ struct pd_solver {
   int32_t* rows = nullptr;
   int64_t* sn_valptr = nullptr;
   double* Lval = nullptr;
-  std::vector<int64_t> lvl_col_ptr, lvl_row_ptr;
-  int32_t *col_sn = nullptr, *col_i = nullptr, *row_sn = nullptr, *row_r = nullptr;
+  std::vector<int64_t> lvl_diag_ptr, lvl_off_ptr;
+  int4 *diag_tasks = nullptr, *off_tasks = nullptr;
   pdk::SparseFactor sf;
   double *b = nullptr, *yv = nullptr, *u = nullptr, *z = nullptr;
   // collision-region block
