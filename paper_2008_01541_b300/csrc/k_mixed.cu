@@ -13,6 +13,7 @@
 
 #include <cmath>
 #include <string>
+#include <vector>
 
 #include "kernels.h"
 #include "mixed.h"
@@ -29,9 +30,9 @@ struct Factor {
   float* Dinv = nullptr;      // [T][128][128] row-major inverses of the diagonal tiles
   float* E = nullptr;         // [T][128][128] Dinv^T Dinv per diagonal tile
   float* Lh = nullptr;        // [mq][mq] row-major, Lh_ik = L_ik Dinv_k (i > k)
-  __nv_bfloat16* Pb = nullptr;  // [mq][128] BF16 copy of the current panel
+  __nv_bfloat16* Pb[2] = {nullptr, nullptr};  // [mq][128] BF16 copies of the panel, by panel parity
   double* d = nullptr;        // [mq] equilibration D
-  CUtensorMap mapL{}, mapP{};
+  CUtensorMap mapL{}, mapP[2]{};
   bool valid = false;
 };
 
@@ -43,6 +44,8 @@ struct MixedState {
   double* sc_h = nullptr;     // pinned copy
   float *w = nullptr, *uo = nullptr;   // [mq][3] triangular-solve vectors
   unsigned* bar = nullptr;    // grid-barrier counter
+  cudaStream_t side = nullptr;              // low-priority stream for the bulk trailing updates
+  std::vector<cudaEvent_t> ev_panel, ev_rest;
   int coop_grid = 0;
 };
 
@@ -98,83 +101,100 @@ __global__ void k_contact_scatter_f32(int64_t k, const int32_t* cidx, const doub
   atomicAdd(L + (int64_t)ra * mq + rb, (float)(cs[j] * cw[4 * j + a] * cw[4 * j + b] * d[ra] * d[rb]));
 }
 
-// Factor the diagonal tile (kt, kt) in FP32, invert it, and form
-// E = Dinv^T Dinv.  Blocked in shared memory with 32-wide sub-blocks: warp 0
+// One warp factors the 32 x 32 block at Ap (row stride PADW) in registers
+// (lane i holds row i) and writes L back to Ap.
+__device__ __noinline__ void warp_chol32(float* Ap, int* status, int code0) {
+  const int lane = threadIdx.x & 31;
+  float a[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) a[c] = Ap[lane * PADW + c];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    float djj = __shfl_sync(0xffffffffu, a[j], j);
+    if (!(djj > 0.f) || !isfinite(djj)) {
+      if (lane == 0) atomicCAS(status, 0, code0 + j + 1);
+      djj = 1.f;
+    }
+    const float piv = sqrtf(djj);
+    if (lane == j) a[j] = piv;
+    if (lane > j) a[j] *= 1.f / piv;
+#pragma unroll
+    for (int c = j + 1; c < 32; ++c) {
+      const float lcj = __shfl_sync(0xffffffffu, a[j], c);
+      if (lane >= c) a[c] = fmaf(-a[j], lcj, a[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 32; ++c)
+    if (c <= lane) Ap[lane * PADW + c] = a[c];
+}
+
+// One warp inverts the lower-triangular 32 x 32 block at Ap into Zp.
+__device__ __noinline__ void warp_inv32(const float* Ap, float* Zp) {
+  const int lane = threadIdx.x & 31;
+  float a[32], z[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) { a[c] = (c <= lane) ? Ap[lane * PADW + c] : 0.f; z[c] = (c == lane) ? 1.f : 0.f; }
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    if (lane == j) {
+      const float ip = 1.f / a[j];
+#pragma unroll
+      for (int c = 0; c <= j; ++c) z[c] *= ip;
+    }
+#pragma unroll
+    for (int c = 0; c <= j; ++c) {
+      const float zjc = __shfl_sync(0xffffffffu, z[c], j);
+      if (lane > j) z[c] = fmaf(-a[j], zjc, z[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 32; ++c) Zp[lane * PADW + c] = z[c];
+}
+
+// Factor the diagonal tile (kt, kt) in FP32 and invert it.  Blocked in shared memory with 32-wide sub-blocks: warp 0
 // factors and inverts each 32 x 32 diagonal sub-block, all warps solve the
 // sub-panel below it and update the trailing sub-matrix; the off-diagonal
 // blocks of the inverse follow by block forward substitution.
-__global__ void __launch_bounds__(512) k_diag_f32(float* __restrict__ L, int64_t mq, int kt,
-                                                  float* __restrict__ Dinv, float* __restrict__ Eout,
-                                                  int* __restrict__ status) {
+__global__ void __launch_bounds__(256) k_diag_f32(float* __restrict__ L, int64_t mq, int kt,
+                                                  float* __restrict__ Dinv, int* __restrict__ status) {
   extern __shared__ float sm[];
   float* A = sm;                   // [128][PADW]
   float* Z = sm + NB * PADW;       // [128][PADW] inverse
   float* S = sm + 2 * NB * PADW;   // [3][32][33] scratch
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   float* Lt = L + (int64_t)kt * NB * mq + (int64_t)kt * NB;
-  for (int q = tid; q < NB * NB; q += 512) {
+  for (int q = tid; q < NB * NB; q += 256) {
     int r = q / NB, c = q % NB;
     A[r * PADW + c] = Lt[(int64_t)r * mq + c];
     Z[r * PADW + c] = 0.f;
   }
   __syncthreads();
+#pragma unroll 1
   for (int p = 0; p < 4; ++p) {
     const int c0 = 32 * p;
     float* Ap = A + c0 * PADW + c0;
     float* Zp = Z + c0 * PADW + c0;
-    if (warp == 0) {
-      for (int j = 0; j < 32; ++j) {
-        if (lane == j) {
-          float d = Ap[j * PADW + j];
-          if (!(d > 0.f) || !isfinite(d)) {
-            atomicCAS(status, 0, kt * NB + c0 + j + 1);
-            d = 1.f;
-          }
-          Ap[j * PADW + j] = sqrtf(d);
-        }
-        __syncwarp();
-        const float pj = Ap[j * PADW + j];
-        if (lane > j) Ap[lane * PADW + j] /= pj;
-        __syncwarp();
-        if (lane > j) {
-          const float lij = Ap[lane * PADW + j];
-          for (int c = j + 1; c <= lane; ++c) Ap[lane * PADW + c] -= lij * Ap[c * PADW + j];
-        }
-        __syncwarp();
-      }
-      // inverse of the 32 x 32 block, lane = column
-      for (int i = 0; i < 32; ++i) Zp[i * PADW + lane] = (i == lane) ? 1.f : 0.f;
-      __syncwarp();
-      for (int j = 0; j < 32; ++j) {
-        if (lane <= j) Zp[j * PADW + lane] /= Ap[j * PADW + j];
-        __syncwarp();
-        if (lane <= j) {
-          const float zj = Zp[j * PADW + lane];
-          for (int i = j + 1; i < 32; ++i) Zp[i * PADW + lane] -= Ap[i * PADW + j] * zj;
-        }
-        __syncwarp();
-      }
-    }
+    if (warp == 0) warp_chol32(Ap, status, kt * NB + c0);
     __syncthreads();
-    // sub-panel below: row r of L = A[r, c0:c0+32] inv(L_D)^T
+    // sub-panel below: row r solves x L_D^T = A[r, c0:c0+32] by substitution (one thread per row)
     const int nbelow = NB - c0 - 32;
-    float val[6];
-    int cnt = 0;
-    for (int q = tid; q < nbelow * 32; q += 512) {
-      const int r = c0 + 32 + q / 32, j = q % 32;
-      float acc = 0.f;
-      for (int t = 0; t <= j; ++t) acc = fmaf(A[r * PADW + c0 + t], Zp[j * PADW + t], acc);
-      val[cnt++] = acc;
-    }
-    __syncthreads();
-    cnt = 0;
-    for (int q = tid; q < nbelow * 32; q += 512) {
-      const int r = c0 + 32 + q / 32, j = q % 32;
-      A[r * PADW + c0 + j] = val[cnt++];
+    if (tid < nbelow) {
+      float* row = A + (c0 + 32 + tid) * PADW + c0;
+      float x[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        float acc = row[j];
+#pragma unroll
+        for (int t = 0; t < j; ++t) acc = fmaf(-x[t], Ap[j * PADW + t], acc);
+        x[j] = acc / Ap[j * PADW + j];
+      }
+#pragma unroll
+      for (int j = 0; j < 32; ++j) row[j] = x[j];
     }
     __syncthreads();
     // trailing update of the lower part below and right of the sub-panel
-    for (int q = tid; q < nbelow * nbelow; q += 512) {
+    for (int q = tid; q < nbelow * nbelow; q += 256) {
       const int r = c0 + 32 + q / nbelow, c = c0 + 32 + q % nbelow;
       if (c > r) continue;
       float acc = 0.f;
@@ -184,10 +204,12 @@ __global__ void __launch_bounds__(512) k_diag_f32(float* __restrict__ L, int64_t
     }
     __syncthreads();
   }
+  if (warp < 4) warp_inv32(A + 32 * warp * PADW + 32 * warp, Z + 32 * warp * PADW + 32 * warp);
+  __syncthreads();
   // off-diagonal 32 x 32 blocks of the inverse: Z_ij = -Z_ii sum_{t=j}^{i-1} L_it Z_tj
   for (int d = 1; d < 4; ++d) {
     const int npairs = 4 - d;
-    for (int q = tid; q < npairs * 1024; q += 512) {
+    for (int q = tid; q < npairs * 1024; q += 256) {
       const int pr = q / 1024, r = (q % 1024) / 32, c = q % 32;
       const int j = pr, i = pr + d;
       float acc = 0.f;
@@ -195,7 +217,7 @@ __global__ void __launch_bounds__(512) k_diag_f32(float* __restrict__ L, int64_t
       S[pr * 32 * 33 + r * 33 + c] = acc;
     }
     __syncthreads();
-    for (int q = tid; q < npairs * 1024; q += 512) {
+    for (int q = tid; q < npairs * 1024; q += 256) {
       const int pr = q / 1024, r = (q % 1024) / 32, c = q % 32;
       const int j = pr, i = pr + d;
       float acc = 0.f;
@@ -205,14 +227,25 @@ __global__ void __launch_bounds__(512) k_diag_f32(float* __restrict__ L, int64_t
     __syncthreads();
   }
   float* Di = Dinv + (int64_t)kt * NB * NB;
-  float* Ek = Eout + (int64_t)kt * NB * NB;
-  for (int q = tid; q < NB * NB; q += 512) {
+  for (int q = tid; q < NB * NB; q += 256) {
     const int r = q / NB, c = q % NB;
     if (c <= r) Lt[(int64_t)r * mq + c] = A[r * PADW + c];
     Di[q] = (c <= r) ? Z[r * PADW + c] : 0.f;
-    // E = Z^T Z (symmetric): E[r][c] = sum_{t >= max(r,c)} Z[t][r] Z[t][c]
+  }
+}
+
+// E_k = Dinv_k^T Dinv_k for every diagonal tile (one CTA per tile, off the
+// factorisation's critical path).
+__global__ void __launch_bounds__(512) k_gram(const float* __restrict__ Dinv, float* __restrict__ E) {
+  extern __shared__ float sm[];
+  const float* Di = Dinv + (int64_t)blockIdx.x * NB * NB;
+  float* Ek = E + (int64_t)blockIdx.x * NB * NB;
+  for (int q = threadIdx.x; q < NB * NB; q += 512) sm[(q / NB) * PADW + q % NB] = Di[q];
+  __syncthreads();
+  for (int q = threadIdx.x; q < NB * NB; q += 512) {
+    const int r = q / NB, c = q % NB;
     float e = 0.f;
-    for (int t = (r > c ? r : c); t < NB; ++t) e = fmaf(Z[t * PADW + r], Z[t * PADW + c], e);
+    for (int t = (r > c ? r : c); t < NB; ++t) e = fmaf(sm[t * PADW + r], sm[t * PADW + c], e);
     Ek[q] = e;
   }
 }
@@ -445,11 +478,13 @@ static pd_status ensure_state(pd_solver* s) {
   for (Factor* f : {&M->f, &M->f0}) {
     if (A((void**)&f->L, sizeof(float) * mq * mq) || A((void**)&f->Dinv, sizeof(float) * mq * NB) ||
         A((void**)&f->E, sizeof(float) * mq * NB) || A((void**)&f->Lh, sizeof(float) * mq * mq) ||
-        A((void**)&f->Pb, sizeof(__nv_bfloat16) * mq * NB) || A((void**)&f->d, sizeof(double) * mq)) {
+        A((void**)&f->Pb[0], sizeof(__nv_bfloat16) * mq * NB) || A((void**)&f->Pb[1], sizeof(__nv_bfloat16) * mq * NB) ||
+        A((void**)&f->d, sizeof(double) * mq)) {
       s->err = "device allocation for the mixed-precision factor failed";
       return PD_ERR_OOM;
     }
-    if (!pdtc::make_map(&f->mapL, f->L, 4, mq, mq, mq, 32) || !pdtc::make_map(&f->mapP, f->Pb, 2, mq, NB, NB, 64)) {
+    if (!pdtc::make_map(&f->mapL, f->L, 4, mq, mq, mq, 32) || !pdtc::make_map(&f->mapP[0], f->Pb[0], 2, mq, NB, NB, 64) ||
+        !pdtc::make_map(&f->mapP[1], f->Pb[1], 2, mq, NB, NB, 64)) {
       s->err = "cuTensorMapEncodeTiled failed";
       return PD_ERR_CUDA;
     }
@@ -464,6 +499,15 @@ static pd_status ensure_state(pd_solver* s) {
     return PD_ERR_OOM;
   }
   if (cudaMallocHost(&M->sc_h, sizeof(double) * 8) != cudaSuccess) return PD_ERR_OOM;
+  int lo_prio = 0, hi_prio = 0;
+  cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+  if (cudaStreamCreateWithPriority(&M->side, cudaStreamNonBlocking, lo_prio) != cudaSuccess) return PD_ERR_CUDA;
+  M->ev_panel.resize(M->T);
+  M->ev_rest.resize(M->T);
+  for (int64_t i = 0; i < M->T; ++i) {
+    cudaEventCreateWithFlags(&M->ev_panel[i], cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&M->ev_rest[i], cudaEventDisableTiming);
+  }
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -477,6 +521,7 @@ static pd_status ensure_state(pd_solver* s) {
   if (!attr) {
     cudaFuncSetAttribute(k_diag_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (2 * NB * PADW + 3 * 32 * 33) * 4);
     cudaFuncSetAttribute(k_trsm_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (64 + NB) * PADW * 4);
+    cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, NB * PADW * 4);
     attr = true;
   }
   return PD_OK;
@@ -503,19 +548,30 @@ static void factor_panels(pd_solver* s, Factor& f, pdtc::Mode mode) {
   MixedState* M = s->mixed;
   const int64_t mq = M->mq, T = M->T;
   cudaStream_t st = s->stream;
+  // Depth-1 look-ahead: the main stream factors tile kt, solves panel kt and
+  // updates only block column kt+1; the low-priority side stream applies
+  // panel kt to the rest of the trailing matrix meanwhile.
+  cudaStream_t sb = M->side;
   for (int kt = 0; kt < T; ++kt) {
-    k_diag_f32<<<1, 512, (2 * NB * PADW + 3 * 32 * 33) * 4, st>>>(f.L, mq, kt, f.Dinv, f.E, s->status);
+    k_diag_f32<<<1, 256, (2 * NB * PADW + 3 * 32 * 33) * 4, st>>>(f.L, mq, kt, f.Dinv, s->status);
     ++pdk::g_launches;
     const int n = (int)(T - kt - 1);
     if (n <= 0) break;
-    k_trsm_f32<<<(unsigned)(2 * n), 256, (64 + NB) * PADW * 4, st>>>(f.L, f.Lh, mq, kt, f.Dinv,
-                                                                    mode == pdtc::BF16 ? f.Pb : nullptr);
+    __nv_bfloat16* pb = mode == pdtc::BF16 ? f.Pb[kt & 1] : nullptr;
+    k_trsm_f32<<<(unsigned)(2 * n), 256, (64 + NB) * PADW * 4, st>>>(f.L, f.Lh, mq, kt, f.Dinv, pb);
     ++pdk::g_launches;
-    if (mode == pdtc::BF16)
-      pdtc::rank_k_update(mode, &f.mapP, &f.mapP, 0, 2, f.L, mq, kt + 1, kt + 1, n, n, 1, s->status, st);
-    else
-      pdtc::rank_k_update(mode, &f.mapL, &f.mapL, kt * NB, 4, f.L, mq, kt + 1, kt + 1, n, n, 1, s->status, st);
+    cudaEventRecord(M->ev_panel[kt], st);
+    if (kt > 0) cudaStreamWaitEvent(st, M->ev_rest[kt - 1], 0);
+    const CUtensorMap* map = mode == pdtc::BF16 ? &f.mapP[kt & 1] : &f.mapL;
+    const int kx = mode == pdtc::BF16 ? 0 : kt * NB, kch = mode == pdtc::BF16 ? 2 : 4;
+    pdtc::rank_k_update(mode, map, map, kx, kch, f.L, mq, kt + 1, kt + 1, n, 1, 0, s->status, st);
+    cudaStreamWaitEvent(sb, M->ev_panel[kt], 0);
+    if (n > 1) pdtc::rank_k_update(mode, map, map, kx, kch, f.L, mq, kt + 2, kt + 2, n - 1, n - 1, 1, s->status, sb);
+    cudaEventRecord(M->ev_rest[kt], sb);
   }
+  if (T > 1) cudaStreamWaitEvent(st, M->ev_rest[T - 2], 0);
+  k_gram<<<(unsigned)T, 512, NB * PADW * 4, st>>>(f.Dinv, f.E);
+  ++pdk::g_launches;
   f.valid = true;
 }
 
@@ -665,6 +721,9 @@ pd_status mixed_solve(pd_solver* s, const double* g, const double* u0, double* u
 void mixed_free(pd_solver* s) {
   if (!s->mixed) return;
   if (s->mixed->sc_h) cudaFreeHost(s->mixed->sc_h);
+  for (auto e : s->mixed->ev_panel) cudaEventDestroy(e);
+  for (auto e : s->mixed->ev_rest) cudaEventDestroy(e);
+  if (s->mixed->side) cudaStreamDestroy(s->mixed->side);
   delete s->mixed;   // device buffers are in s->allocs
   s->mixed = nullptr;
 }
