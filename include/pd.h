@@ -77,7 +77,9 @@ typedef struct {
     int64_t n_supernodes, n_levels, nnz_L;    /* interior factor L_1 and L_21        */
     int64_t contacts;                         /* active springs in the last inner iteration */
     int64_t outer_done, inner_done;           /* iterations run by the last pd_step  */
-    int refine_iters;                         /* refinement / PCG iterations, last solve */
+    int refine_iters;                         /* refinement / PCG iterations: summed over the
+                                                 solves of the last pd_step, or of the last
+                                                 pd_schur_solve */
     double residual;                          /* ||g - H u|| / ||g|| of the last solve */
     double setup_ms;                          /* wall time of pd_setup               */
     /* per-phase device time of the last pd_step (timing != 0), milliseconds:      */
@@ -230,6 +232,53 @@ pd_status pd_schur_solve_noalloc(const double* sigma_dev, int64_t m, int64_t k,
  * (Section 3.3 dense refactorisation).  Errors: INVALID_ARG, OOM, CUDA, TIMEOUT. */
 pd_status pd_tc_rank_k(int mode, const float* A, const float* B, float* C, int64_t M, int64_t N, int64_t K,
                        void* cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Learned warm start for PD_PCG_WARM (beyond the paper: a small network that
+ * predicts the collision-region solution u_2 of H u_2 = g, used only as the
+ * starting point of PCG; the refined answer still has to meet tol).
+ * The start is u0 = z0 + s * N(features), where z0 = M0^-1 g is the
+ * response of the contact-free factor M0 of Sigma_0 (one preconditioner
+ * application) and the network N predicts the contact correction u - z0.
+ * Per region node, 14 inputs -- g_i / rms(g), z0_i / s, |g_i| / rms(g),
+ * |z0_i| / s, contact flag, log(1 + contact stiffness / mean diag Sigma_0),
+ * spring direction (3), normalised rest height -- then 256-256-256 ReLU
+ * layers and 3 outputs; s = rms(g) / mean(diag Sigma_0).  BF16 weights and
+ * activations, FP32 accumulation, all products on the tensor cores.
+ * Parameter vector (float32, logical layout, 136195 values):
+ *   W1 [256][14] b1 [256] W2 [256][256] b2 [256] W3 [256][256] b3 [256] W4 [3][256] b4 [3]
+ * ------------------------------------------------------------------------ */
+#define PD_MLP_NPARAMS 136195
+
+/* Starting point of PD_PCG_WARM solves inside pd_step: 0 = zero, 1 = the
+ * previous region solution, 2 = the network's prediction z0 + s N (needs
+ * parameters), 3 = z0 alone (the contact-free response, no network). */
+pd_status pd_set_warm_start(pd_solver* s, int source);
+
+/* Set / read the network parameters (n must be PD_MLP_NPARAMS); setting them
+ * resets the optimiser state. */
+pd_status pd_mlp_set_params(pd_solver* s, const float* params, int64_t n);
+pd_status pd_mlp_get_params(pd_solver* s, float* params, int64_t n);
+
+/* Record (features, solution) pairs of the next max_solves region solves run
+ * by pd_step / pd_schur_solve, on the device (the training set is generated
+ * by the method itself).  0 stops recording.  Recording restarts the set. */
+pd_status pd_mlp_record(pd_solver* s, int64_t max_solves);
+
+/* Adam (lr, beta 0.9/0.999) on mean-squared error over `steps` minibatches
+ * of `batch` recorded node rows (multiple of 128, <= 8192) drawn with a
+ * counter-based generator from `seed`.  *loss = mean loss of the last steps. */
+pd_status pd_mlp_train(pd_solver* s, int64_t steps, int64_t batch, double lr, uint64_t seed, double* loss);
+
+/* Mean squared error on every recorded row of the network's correction,
+ * against the true u - z0, and that of the zero correction (the z0 start),
+ * in the scaled units: 1 - mse_net / mse_zero is the part of the remaining
+ * error after the contact-free response that the network predicts. */
+pd_status pd_mlp_eval(pd_solver* s, double* mse_net, double* mse_zero);
+
+/* Loss and gradient (logical layout) at the current parameters for a host
+ * batch X [B][14], T [B][3] (for checking the hand-written backward pass). */
+pd_status pd_mlp_loss_grad(pd_solver* s, const float* X, const float* T, int64_t B, double* loss, float* grad);
 
 /* Change the precision of the collision-region solve on an existing handle. */
 pd_status pd_set_precision(pd_solver* s, int precision);

@@ -72,6 +72,13 @@ _sigs = {
     "pd_schur_solve": (ctypes.c_int, [P, P, P, P]),
     "pd_schur_solve_dev": (ctypes.c_int, [P, P, P, P]),
     "pd_set_precision": (ctypes.c_int, [P, ctypes.c_int]),
+    "pd_set_warm_start": (ctypes.c_int, [P, ctypes.c_int]),
+    "pd_mlp_set_params": (ctypes.c_int, [P, P, I64]),
+    "pd_mlp_get_params": (ctypes.c_int, [P, P, I64]),
+    "pd_mlp_record": (ctypes.c_int, [P, I64]),
+    "pd_mlp_train": (ctypes.c_int, [P, I64, I64, D, ctypes.c_uint64, ctypes.POINTER(D)]),
+    "pd_mlp_eval": (ctypes.c_int, [P, ctypes.POINTER(D), ctypes.POINTER(D)]),
+    "pd_mlp_loss_grad": (ctypes.c_int, [P, P, P, I64, ctypes.POINTER(D), P]),
     "pd_tc_rank_k": (ctypes.c_int, [ctypes.c_int, P, P, P, I64, I64, I64, P]),
     "pd_schur_solve_noalloc": (ctypes.c_int, [P, I64, I64, P, P, P, P, P, P, ctypes.c_char_p, I64]),
     "pd_host_schur": (ctypes.c_int, [ctypes.POINTER(Mesh), ctypes.POINTER(Material), D, P, I64, P, I64,
@@ -83,3 +90,4 @@ for _name, (_res, _args) in _sigs.items():
     _f.argtypes = _args
 
 EXPORTED = sorted(_sigs)
+MLP_NPARAMS = 136195

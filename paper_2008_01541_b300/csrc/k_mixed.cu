@@ -718,6 +718,23 @@ pd_status mixed_solve(pd_solver* s, const double* g, const double* u0, double* u
   return PD_OK;
 }
 
+// z = M0^-1 r with the contact-free factor of Sigma_0 (computed on first use).
+pd_status apply_free(pd_solver* s, const double* r, double* z) {
+  pd_status rs = ensure_state(s);
+  if (rs != PD_OK) return rs;
+  MixedState* M = s->mixed;
+  if (!M->f0.valid) {
+    factor_cast(s, M->f0, false);
+    factor_panels(s, M->f0, pdtc::TF32X3);
+  }
+  cudaError_t ce = precond(s, M->f0, r, z);
+  if (ce != cudaSuccess) {
+    s->err = std::string("cooperative launch failed: ") + cudaGetErrorString(ce);
+    return PD_ERR_CUDA;
+  }
+  return PD_OK;
+}
+
 void mixed_free(pd_solver* s) {
   if (!s->mixed) return;
   if (s->mixed->sc_h) cudaFreeHost(s->mixed->sc_h);

@@ -5,5 +5,7 @@ struct pd_solver;
 namespace pdm {
 pd_status mixed_solve(pd_solver* s, const double* g, const double* u0, double* u);
 void mixed_free(pd_solver* s);
+// z = M0^-1 r with the contact-free low-precision factor of Sigma_0.
+pd_status apply_free(pd_solver* s, const double* r, double* z);
 void mixed_invalidate(pd_solver* s);
 }  // namespace pdm

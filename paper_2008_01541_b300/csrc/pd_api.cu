@@ -13,6 +13,7 @@
 #include "host_setup.h"
 #include "kernels.h"
 #include "mixed.h"
+#include "mlp.h"
 #include "pd.h"
 #include "solver.h"
 
@@ -102,12 +103,13 @@ void pd_solver::tend() {
 
 void pd_solver::tcollect(double* out /*[8]*/) {
   for (int i = 0; i < 8; ++i) out[i] = 0.0;
+  // phase 7 (network inference) is reported inside phase 4
   if (!opt.timing) return;
   cudaStreamSynchronize(stream);
   for (auto& mk : marks) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, events[mk.second], events[mk.second + 1]);
-    out[mk.first] += ms;
+    out[mk.first == 7 ? 4 : mk.first] += ms;
   }
   marks.clear();
   ev_used = 0;
@@ -116,6 +118,39 @@ void pd_solver::tcollect(double* out /*[8]*/) {
 // ----------------------------------------------------------------- the region solve
 // H = Sigma_0 + C_22; factor; solve H u = g (Algorithm 1, 4.3 and 4.5).
 pd_status pd_solver::region_solve(const double* g_dev, const double* u0_dev, double* u_dev) {
+  pd_status r = region_solve_core(g_dev, u0_dev, u_dev);
+  if (r != PD_OK) return r;
+  if (net) {
+    r = pdn::after_solve(this, u_dev);
+    if (r != PD_OK) return r;
+  }
+  cudaMemcpyAsync(u_last, u_dev, sizeof(double) * 3 * m, cudaMemcpyDeviceToDevice, stream);
+  return PD_OK;
+}
+
+pd_status pd_solver::region_solve_core(const double* g_dev, const double* u0_dev, double* u_dev) {
+  // warm start of the PCG form (Section 3.3 solve with a learned or previous guess)
+  if (precision == PD_PCG_WARM && !u0_dev && warm_source != 0) {
+    if (warm_source == 2 && net) {
+      tbegin(7);
+      pd_status r = pdn::before_solve(this, g_dev, u0);
+      tend();
+      if (r != PD_OK) return r;
+      u0_dev = u0;
+    } else if (warm_source == 1) {
+      cudaMemcpyAsync(u0, u_last, sizeof(double) * 3 * m, cudaMemcpyDeviceToDevice, stream);
+      u0_dev = u0;
+    } else if (warm_source == 3) {
+      tbegin(7);
+      pd_status r = pdm::apply_free(this, g_dev, u0);
+      tend();
+      if (r != PD_OK) return r;
+      u0_dev = u0;
+    }
+  } else if (net && mlp_recording) {
+    pd_status r = pdn::before_solve(this, g_dev, nullptr);
+    if (r != PD_OK) return r;
+  }
   if (precision == PD_FP64) {
     tbegin(2);
     pdk::copy_sigma(Sigma0, m, H, mp, stream);
@@ -310,6 +345,7 @@ void pd_destroy(pd_solver* s) {
   if (s->x2_host) cudaFreeHost(s->x2_host);
   if (s->status_h) cudaFreeHost(s->status_h);
   pdm::mixed_free(s);
+  pdn::free_net(s);
   for (auto e : s->events) cudaEventDestroy(e);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
   delete s;
@@ -367,6 +403,45 @@ pd_status pd_schur_solve(pd_solver* s, const double* g, const double* u0, double
   CK(cudaMemcpyAsync(u, s->u2, sizeof(double) * 3 * s->m, cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
   return PD_OK;
+}
+
+pd_status pd_set_warm_start(pd_solver* s, int source) {
+  if (!s || source < 0 || source > 3) return PD_ERR_INVALID_ARG;
+  s->warm_source = source;
+  return PD_OK;
+}
+
+pd_status pd_mlp_set_params(pd_solver* s, const float* params, int64_t n) {
+  if (!s || !params || n != pdn::NPARAMS) {
+    if (s) s->err = "expected " + std::to_string(pdn::NPARAMS) + " parameters";
+    return PD_ERR_INVALID_ARG;
+  }
+  return pdn::set_params(s, params);
+}
+
+pd_status pd_mlp_get_params(pd_solver* s, float* params, int64_t n) {
+  if (!s || !params || n != pdn::NPARAMS) return PD_ERR_INVALID_ARG;
+  return pdn::get_params(s, params);
+}
+
+pd_status pd_mlp_record(pd_solver* s, int64_t max_solves) {
+  if (!s || max_solves < 0) return PD_ERR_INVALID_ARG;
+  return pdn::record(s, max_solves);
+}
+
+pd_status pd_mlp_train(pd_solver* s, int64_t steps, int64_t batch, double lr, uint64_t seed, double* loss) {
+  if (!s || steps < 0 || !(lr > 0)) return PD_ERR_INVALID_ARG;
+  return pdn::train(s, steps, batch, lr, seed, loss);
+}
+
+pd_status pd_mlp_eval(pd_solver* s, double* mse_net, double* mse_zero) {
+  if (!s) return PD_ERR_INVALID_ARG;
+  return pdn::eval(s, mse_net, mse_zero);
+}
+
+pd_status pd_mlp_loss_grad(pd_solver* s, const float* X, const float* T, int64_t B, double* loss, float* grad) {
+  if (!s || !X || !T || B < 1) return PD_ERR_INVALID_ARG;
+  return pdn::loss_grad(s, X, T, B, loss, grad);
 }
 
 pd_status pd_set_precision(pd_solver* s, int precision) {
@@ -508,6 +583,9 @@ pd_status pd_solver::upload(const pdh::Setup& h, const pdh::Input& in) {
   CK(dalloc(s, &u2, 3 * m));
   CK(dalloc(s, &Sau, 3 * m));
   CK(dalloc(s, &U2, 3 * m));
+  CK(dalloc(s, &u_last, 3 * m));
+  CK(cudaMemset(u_last, 0, sizeof(double) * 3 * m));
+  X_rest_h.assign(in.X, in.X + 3 * n);
   CK(dalloc(s, &work, 6 * mp));
   CK(dalloc(s, &status, 4));
   CK(cudaMemset(status, 0, sizeof(int) * 4));
@@ -543,7 +621,7 @@ pd_status pd_solver::step(int outer_iters, pd_contact_cb cb, void* user) {
     pdk::axpby(3 * nfree, dt, tmp3, 1.0, y_in, stream);
   }
   pd_status result = PD_OK;
-  int64_t inner_total = 0;
+  int64_t inner_total = 0, refine_total = 0;
   for (int it = 0; it < outer_iters && result == PD_OK; ++it) {
     // 1-2: R_alpha and the alpha forces f_1, f_2^(alpha) (+ x_1 inertia)
     tbegin(0);
@@ -580,6 +658,7 @@ pd_status pd_solver::step(int outer_iters, pd_contact_cb cb, void* user) {
       // 4.3, 4.5: H = Sigma_alpha + A22^beta + C22; solve H u2 = g
       pd_status r = region_solve(g, nullptr, u2);
       if (r != PD_OK) { result = r; break; }
+      refine_total += last_refine;
       // 4.6, 4.7: x2 += u2; f~_2 -= Sigma_alpha u2 (= Sigma_0 u2 - A22^beta u2 - M2/dt^2 u2)
       tbegin(5);
       pdk::symv3(Sigma0, m, u2, Sau, stream);
@@ -623,7 +702,7 @@ pd_status pd_solver::step(int outer_iters, pd_contact_cb cb, void* user) {
   stats.inner_done = inner_total;
   stats.kernel_launches = pdk::g_launches - launches0;
   stats.contacts = k;
-  stats.refine_iters = last_refine;
+  stats.refine_iters = (int)refine_total;
   stats.residual = last_residual;
   return PD_OK;
 }

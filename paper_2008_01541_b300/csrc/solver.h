@@ -24,6 +24,7 @@ struct ElemSet {
 };
 
 namespace pdm { struct MixedState; }
+namespace pdn { struct Net; }
 
 struct pd_solver {
   // configuration
@@ -65,6 +66,11 @@ struct pd_solver {
   int* status = nullptr;      // [0] non-SPD column+1, [1] timeout code, [2] no convergence
   int* status_h = nullptr;
   pdm::MixedState* mixed = nullptr;
+  pdn::Net* net = nullptr;       // learned warm start
+  bool mlp_recording = false;
+  int warm_source = 0;           // PD_PCG_WARM start: 0 zero, 1 previous solution, 2 network
+  double* u_last = nullptr;      // [m][3] solution of the previous region solve
+  std::vector<double> X_rest_h;  // rest positions (host)
   int last_refine = 0;
   double last_residual = 0.0;
   // contacts (region indices)
@@ -81,6 +87,7 @@ struct pd_solver {
   pd_status upload(const pdh::Setup& h, const pdh::Input& in);
   pd_status step(int outer_iters, pd_contact_cb cb, void* user);
   pd_status region_solve(const double* g_dev, const double* u0_dev, double* u_dev);
+  pd_status region_solve_core(const double* g_dev, const double* u0_dev, double* u_dev);
   pd_status check_status();
   pd_status ensure_all_elements();
   void tbegin(int phase);

@@ -168,3 +168,39 @@ class Solver:
 
     def set_precision(self, p):
         self._check(lib.pd_set_precision(self.h, p))
+
+    # ---- learned warm start (PD_PCG_WARM) ----
+    def set_warm_start(self, source):
+        """0 = zero, 1 = previous region solution, 2 = network prediction."""
+        self._check(lib.pd_set_warm_start(self.h, int(source)))
+
+    def mlp_set_params(self, params):
+        p = _c(params, np.float32).ravel()
+        self._check(lib.pd_mlp_set_params(self.h, _ptr(p), len(p)))
+
+    def mlp_get_params(self):
+        p = np.empty(_lib.MLP_NPARAMS, np.float32)
+        self._check(lib.pd_mlp_get_params(self.h, _ptr(p), len(p)))
+        return p
+
+    def mlp_record(self, max_solves):
+        self._check(lib.pd_mlp_record(self.h, int(max_solves)))
+
+    def mlp_train(self, steps, batch=1024, lr=1e-3, seed=0):
+        loss = ctypes.c_double()
+        self._check(lib.pd_mlp_train(self.h, int(steps), int(batch), float(lr), int(seed), ctypes.byref(loss)))
+        return loss.value
+
+    def mlp_loss_grad(self, X, T):
+        X = _c(X, np.float32)
+        T = _c(T, np.float32)
+        grad = np.empty(_lib.MLP_NPARAMS, np.float32)
+        loss = ctypes.c_double()
+        self._check(lib.pd_mlp_loss_grad(self.h, _ptr(X), _ptr(T), len(X), ctypes.byref(loss), _ptr(grad)))
+        return loss.value, grad
+
+    def mlp_eval(self):
+        """(mse of the network, mse of the zero prediction) over the recorded rows."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        self._check(lib.pd_mlp_eval(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value

@@ -1,0 +1,56 @@
+"""Driving the learned warm start: generate training solves with the method
+itself along seeded random indenter paths, train the network on the device,
+and compare PCG iteration counts by starting point.  Host orchestration only;
+every solve, feature and gradient is computed by libpd.so."""
+import numpy as np
+
+from . import _lib
+from ._lib import PDError  # noqa: F401
+
+
+def he_init(seed):
+    """He-normal weights, zero biases, in the library's logical layout."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = []
+    for n, k in [(256, 14), (256, 256), (256, 256), (3, 256)]:
+        parts += [rng.normal(0.0, np.sqrt(2.0 / k), size=n * k), np.zeros(n)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def indenter_path(scene, seed, steps, radius=None, step_len=None):
+    """Seeded random walk of a rigid sphere over the collision-prone surface.
+    Returns a list of sphere centres (one per time step)."""
+    import scenes
+    rng = np.random.Generator(np.random.PCG64(seed))
+    P = scene.X[scene.proxies]
+    h = scene.info.get("h", 1.0)
+    radius = radius if radius is not None else 4.0 * h
+    step_len = step_len if step_len is not None else 0.5 * h
+    c = P[rng.integers(len(P))].copy()
+    out = []
+    for _ in range(steps):
+        c = c + step_len * rng.normal(size=3)
+        near = P[np.argmin(np.linalg.norm(P - c, axis=1))]
+        c = 0.7 * c + 0.3 * near          # stay close to the surface
+        out.append(c.copy())
+    return out, radius
+
+
+def run_path(solver, scene, centres, radius, outer=1, depth=0.3):
+    """One pd_step per centre; contacts from the sphere pushed `depth*radius`
+    into the surface, detected at every inner iteration."""
+    import scenes
+    x_ref = scene.X.copy()
+    iters = []
+    for c in centres:
+        ctr = np.asarray(c)
+
+        def cb(x2, ctr=ctr):
+            x = x_ref.copy()
+            x[scene.region] = x2
+            con = scenes.sphere_contacts(scene.proxies, x, ctr, radius * (1.0 + depth), scene.stiffness)
+            return (con.nodes, con.w, con.target, con.stiffness)
+
+        solver.step(outer, cb)
+        iters.append(solver.stats()["refine_iters"])
+    return iters
