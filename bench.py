@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--h", type=float, default=0.585, help="elbow voxel spacing (0.585 -> ~598K tets)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip timing the other precision forms")
+    ap.add_argument("--train-solves", type=int, default=200, help="solves recorded to train the warm start")
+    ap.add_argument("--train-steps", type=int, default=1000)
     return ap.parse_args()
 
 
@@ -133,9 +135,72 @@ def time_forms(pd, sol, stream, args, fp64_ms, torch):
         out[name] = {"ms_per_step": ms, "value": 1e3 / ms, "unit": UNIT, "speedup_vs_fp64": fp64_ms / ms,
                      "schur_refactor_solve_ms": schur / args.steps, "refine_iters": iters / args.steps,
                      "max_rel_residual": res}
+    out.update(time_learned(pd, sol, stream, args, fp64_ms, torch, state))
     sol.set_precision(pd.FP64)
+    sol.set_warm_start(0)
     sol.set_state(*state)
     return out
+
+
+def time_learned(pd, sol, stream, args, fp64_ms, torch, state):
+    """The learned warm start on this scene: record region solves along seeded
+    random indenter paths (split-TF32 form), train the network on the device,
+    then time the PCG form started from the network's prediction and report
+    PCG iterations by starting point.  A bounded sample of the 20K-solve
+    training run (see the training recipe in the package's warmstart module)."""
+    from paper_2008_01541_b300 import warmstart as ws
+    import scenes
+    s = sol._scene
+    t0 = time.perf_counter()
+    sol.set_precision(pd.FP32_IR)
+    sol.mlp_set_params(ws.he_init(0))
+    sol.mlp_record(args.train_solves + 8)
+    centres, radius = ws.indenter_path(s, seed=1, steps=args.train_solves)
+    sol.set_state(*state)
+    ws.run_path(sol, s, centres, radius)
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    loss = sol.mlp_train(args.train_steps, batch=4096, lr=1e-3, seed=2)
+    train_s = time.perf_counter() - t0
+    sol.mlp_record(40)
+    held, radius = ws.indenter_path(s, seed=99, steps=12)
+    sol.set_state(*state)
+    ws.run_path(sol, s, held, radius)
+    mse_net, mse_zero = sol.mlp_eval()
+    sol.mlp_record(0)
+    sol.set_precision(pd.PCG_WARM)
+    iters = {}
+    for name, src in (("zero", 0), ("z0", 3), ("network", 2)):
+        sol.set_state(*state)
+        sol.set_warm_start(src)
+        iters[name] = float(np.mean(ws.run_path(sol, s, held, radius)))
+    sol.set_state(*state)
+    sol.set_warm_start(2)
+    c = s.contacts(CONTACT_STEP, s.X)
+    sol.set_contacts(c.nodes, c.w, c.target, c.stiffness)
+    for _ in range(3):
+        sol.step(1)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    schur = it = res = 0.0
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        sol.step(1)
+        st = sol.stats()
+        schur += st["ms_contact_update"] + st["ms_factor_solve"]
+        it += st["refine_iters"]
+        res = max(res, st["residual"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    return {"pcg_learned (network warm start)": {
+        "ms_per_step": ms, "value": 1e3 / ms, "unit": UNIT, "speedup_vs_fp64": fp64_ms / ms,
+        "schur_refactor_solve_ms": schur / args.steps, "refine_iters": it / args.steps, "max_rel_residual": res,
+        "train_solves": args.train_solves, "train_steps": args.train_steps, "train_loss": loss,
+        "generate_s": gen_s, "train_s": train_s,
+        "heldout_err_vs_z0_start": mse_net / mse_zero if mse_zero > 0 else None,
+        "heldout_pcg_iters_by_start": iters}}
 
 
 def cpu_baseline(scene, x_state):
@@ -208,6 +273,7 @@ def main():
     sol = pd.Solver(s.X, s.tets, s.region, s.dirichlet, s.mu, 0.0, 0.0, 0.0, precision=prec,
                     inner_iters=1, stream=stream.cuda_stream, timing=True, max_refine=500)
     setup_s = time.perf_counter() - t_setup
+    sol._scene = s
     rest = s.info["rest_step"]
     con = s.contacts(CONTACT_STEP, s.X)
     sol.set_dirichlet(s.dirichlet_positions(rest))
