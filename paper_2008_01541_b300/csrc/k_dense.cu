@@ -150,18 +150,26 @@ __global__ void __launch_bounds__(256) k_chol_trsm(double* __restrict__ H, int64
     for (int q = 0; q < 4; ++q) Ai[(tr + 16 * p) + (int64_t)(tc + 16 * q) * mp] = acc[p][q];
 }
 
-// A_ij -= L_ik L_jk^T for kt < j <= i
-__global__ void __launch_bounds__(256) k_chol_update(double* __restrict__ H, int64_t mp, int kt, int T) {
+// A_ij -= L_ik L_jk^T for the tiles selected by the launch: lower != 0 ->
+// tiles it0 + ii, jt0 + jj with jj <= ii (triangular numbering); else an
+// n_i x n_j rectangle starting at (it0, jt0).
+__global__ void __launch_bounds__(256) k_chol_update(double* __restrict__ H, int64_t mp, int kt, int it0, int jt0,
+                                                     int n_j, int lower) {
   extern __shared__ double sm[];
   double* As = sm;
   double* Bs = sm + TB * TB;
   const int tid = threadIdx.x;
-  int64_t idx = blockIdx.x;
-  int64_t ii = (int64_t)((sqrt(8.0 * (double)idx + 1.0) - 1.0) * 0.5);
-  while ((ii + 1) * (ii + 2) / 2 <= idx) ++ii;
-  while (ii * (ii + 1) / 2 > idx) --ii;
-  int64_t jj = idx - ii * (ii + 1) / 2;
-  const int64_t it = kt + 1 + ii, jt = kt + 1 + jj;
+  int64_t idx = blockIdx.x, ii, jj;
+  if (lower) {
+    ii = (int64_t)((sqrt(8.0 * (double)idx + 1.0) - 1.0) * 0.5);
+    while ((ii + 1) * (ii + 2) / 2 <= idx) ++ii;
+    while (ii * (ii + 1) / 2 > idx) --ii;
+    jj = idx - ii * (ii + 1) / 2;
+  } else {
+    ii = idx / n_j;
+    jj = idx % n_j;
+  }
+  const int64_t it = it0 + ii, jt = jt0 + jj;
   const double* Li = H + it * TB + (int64_t)kt * TB * mp;
   const double* Lj = H + jt * TB + (int64_t)kt * TB * mp;
   for (int q = tid; q < TB * TB; q += 256) {
@@ -291,7 +299,7 @@ void contact_forces(int64_t k, const int32_t* cidx, const double* cw, const doub
   }
 }
 
-void cholesky_fp64(double* H, int64_t mp, double* Linv, int* status, cudaStream_t st) {
+void cholesky_fp64(double* H, int64_t mp, double* Linv, int* status, cudaStream_t st, const LookAhead* la) {
   static bool attr = false;
   const int smem = 2 * TB * TB * sizeof(double);
   if (!attr) {
@@ -301,6 +309,22 @@ void cholesky_fp64(double* H, int64_t mp, double* Linv, int* status, cudaStream_
     attr = true;
   }
   const int T = (int)(mp / TB);
+  if (!la || (int64_t)la->ev_panel.size() < T) {   // plain right-looking order on one stream
+    for (int k = 0; k < T; ++k) {
+      k_chol_diag<<<1, 256, smem, st>>>(H, mp, k, Linv, status);
+      ++g_launches;
+      int n = T - k - 1;
+      if (n <= 0) break;
+      k_chol_trsm<<<n, 256, smem, st>>>(H, mp, k, Linv);
+      ++g_launches;
+      k_chol_update<<<(unsigned)((int64_t)n * (n + 1) / 2), 256, smem, st>>>(H, mp, k, k + 1, k + 1, 0, 1);
+      ++g_launches;
+    }
+    return;
+  }
+  // Depth-1 look-ahead: the main stream factors tile k, solves panel k and
+  // updates only block column k+1; the low-priority side stream applies panel
+  // k to the rest of the trailing matrix while tile k+1 is being factored.
   for (int k = 0; k < T; ++k) {
     k_chol_diag<<<1, 256, smem, st>>>(H, mp, k, Linv, status);
     ++g_launches;
@@ -308,9 +332,18 @@ void cholesky_fp64(double* H, int64_t mp, double* Linv, int* status, cudaStream_
     if (n <= 0) break;
     k_chol_trsm<<<n, 256, smem, st>>>(H, mp, k, Linv);
     ++g_launches;
-    k_chol_update<<<(unsigned)((int64_t)n * (n + 1) / 2), 256, smem, st>>>(H, mp, k, T);
+    cudaEventRecord(la->ev_panel[k], st);
+    if (k > 0) cudaStreamWaitEvent(st, la->ev_rest[k - 1], 0);
+    k_chol_update<<<(unsigned)n, 256, smem, st>>>(H, mp, k, k + 1, k + 1, 1, 0);
     ++g_launches;
+    cudaStreamWaitEvent(la->side, la->ev_panel[k], 0);
+    if (n > 1) {
+      k_chol_update<<<(unsigned)((int64_t)(n - 1) * n / 2), 256, smem, la->side>>>(H, mp, k, k + 2, k + 2, 0, 1);
+      ++g_launches;
+    }
+    cudaEventRecord(la->ev_rest[k], la->side);
   }
+  if (T > 1) cudaStreamWaitEvent(st, la->ev_rest[T - 2], 0);
 }
 
 void chol_solve_fp64(const double* H, int64_t mp, const double* Linv, const double* g, double* u, int64_t m,

@@ -1,6 +1,7 @@
 // Launch wrappers of the CUDA kernels (plain pointers, one stream each).
 #pragma once
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 namespace pdk {
@@ -52,9 +53,17 @@ void contact_scatter(int64_t k, const int32_t* cidx, const double* cw, const dou
 void contact_forces(int64_t k, const int32_t* cidx, const double* cw, const double* ct,
                     const double* cs, const int32_t* region, const double* x, double* g,
                     cudaStream_t st);
+// Side stream and events for the look-ahead factorisation order.
+struct LookAhead {
+  cudaStream_t side = nullptr;
+  std::vector<cudaEvent_t> ev_panel, ev_rest;   // one per tile step
+};
 // Blocked right-looking FP64 Cholesky of the padded H (tile 64). Linv receives
 // the inverses of the diagonal tiles; status[0] = first failing column + 1.
-void cholesky_fp64(double* H, int64_t mp, double* Linv, int* status, cudaStream_t st);
+// With la (events for mp/64 steps) the trailing update is split between st
+// and la->side (depth-1 look-ahead); without it everything runs on st.
+void cholesky_fp64(double* H, int64_t mp, double* Linv, int* status, cudaStream_t st,
+                   const LookAhead* la = nullptr);
 // Solve (L L^T) u = g for 3 right-hand sides, g/u [m][3] (padded internally).
 void chol_solve_fp64(const double* H, int64_t mp, const double* Linv, const double* g, double* u,
                      int64_t m, double* work /*[mp][3] x 2*/, cudaStream_t st);

@@ -157,7 +157,7 @@ pd_status pd_solver::region_solve_core(const double* g_dev, const double* u0_dev
     pdk::contact_scatter(k, c_idx, c_w, c_s, H, mp, stream);
     tend();
     tbegin(4);
-    pdk::cholesky_fp64(H, mp, Linv, status, stream);
+    pdk::cholesky_fp64(H, mp, Linv, status, stream, &la);
     pdk::chol_solve_fp64(H, mp, Linv, g_dev, u_dev, m, work, stream);
     tend();
     last_refine = 0;
@@ -346,6 +346,9 @@ void pd_destroy(pd_solver* s) {
   if (s->status_h) cudaFreeHost(s->status_h);
   pdm::mixed_free(s);
   pdn::free_net(s);
+  for (auto e : s->la.ev_panel) cudaEventDestroy(e);
+  for (auto e : s->la.ev_rest) cudaEventDestroy(e);
+  if (s->la.side) cudaStreamDestroy(s->la.side);
   for (auto e : s->events) cudaEventDestroy(e);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
   delete s;
@@ -577,6 +580,17 @@ pd_status pd_solver::upload(const pdh::Setup& h, const pdh::Input& in) {
   CK(dupload(s, &b22_row, h.B22.row.data(), h.B22.row.size()));
   CK(dupload(s, &b22_val, h.B22.val.data(), h.B22.val.size()));
   CK(dalloc(s, &H, (size_t)mp * mp));
+  {
+    int lo_prio = 0, hi_prio = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
+    CK(cudaStreamCreateWithPriority(&la.side, cudaStreamNonBlocking, lo_prio));
+    la.ev_panel.resize(mp / 64);
+    la.ev_rest.resize(mp / 64);
+    for (size_t i = 0; i < la.ev_panel.size(); ++i) {
+      CK(cudaEventCreateWithFlags(&la.ev_panel[i], cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&la.ev_rest[i], cudaEventDisableTiming));
+    }
+  }
   CK(dalloc(s, &Linv, (size_t)mp * 64));
   CK(dalloc(s, &g, 3 * m));
   CK(dalloc(s, &u0, 3 * m));

@@ -65,6 +65,7 @@ struct pd_solver {
   double* x2_host = nullptr;
   int* status = nullptr;      // [0] non-SPD column+1, [1] timeout code, [2] no convergence
   int* status_h = nullptr;
+  pdk::LookAhead la;             // side stream + events of the FP64 factorisation
   pdm::MixedState* mixed = nullptr;
   pdn::Net* net = nullptr;       // learned warm start
   bool mlp_recording = false;
