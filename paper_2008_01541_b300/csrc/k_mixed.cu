@@ -40,6 +40,8 @@ struct MixedState {
   int64_t mq = 0, T = 0;
   Factor f, f0;               // per-solve factor, contact-free factor (PCG_WARM)
   double *hdiag = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *u = nullptr;
+  float *Shi = nullptr, *Slo = nullptr;   // Sigma_0 = Shi + Slo (FP32 pair, ~48-bit)
+  float *vhi = nullptr, *vlo = nullptr;   // [m][3] split of the vector being multiplied
   double* sc = nullptr;       // device scalars: [0] r.r  [1] r.z  [2] p.q  [3] r.z old  [4] g.g
   double* sc_h = nullptr;     // pinned copy
   float *w = nullptr, *uo = nullptr;   // [mq][3] triangular-solve vectors
@@ -115,9 +117,9 @@ __device__ __noinline__ void warp_chol32(float* Ap, int* status, int code0) {
       if (lane == 0) atomicCAS(status, 0, code0 + j + 1);
       djj = 1.f;
     }
-    const float piv = sqrtf(djj);
-    if (lane == j) a[j] = piv;
-    if (lane > j) a[j] *= 1.f / piv;
+    const float rs = rsqrtf(djj);        // hardware reciprocal square root (MUFU)
+    if (lane == j) a[j] = djj * rs;
+    if (lane > j) a[j] *= rs;
 #pragma unroll
     for (int c = j + 1; c < 32; ++c) {
       const float lcj = __shfl_sync(0xffffffffu, a[j], c);
@@ -138,7 +140,7 @@ __device__ __noinline__ void warp_inv32(const float* Ap, float* Zp) {
 #pragma unroll
   for (int j = 0; j < 32; ++j) {
     if (lane == j) {
-      const float ip = 1.f / a[j];
+      const float ip = __frcp_rn(a[j]);
 #pragma unroll
       for (int c = 0; c <= j; ++c) z[c] *= ip;
     }
@@ -187,7 +189,7 @@ __global__ void __launch_bounds__(256) k_diag_f32(float* __restrict__ L, int64_t
         float acc = row[j];
 #pragma unroll
         for (int t = 0; t < j; ++t) acc = fmaf(-x[t], Ap[j * PADW + t], acc);
-        x[j] = acc / Ap[j * PADW + j];
+        x[j] = acc * __frcp_rn(Ap[j * PADW + j]);
       }
 #pragma unroll
       for (int j = 0; j < 32; ++j) row[j] = x[j];
@@ -400,6 +402,53 @@ __global__ void __launch_bounds__(256) k_precond(const float* __restrict__ Lh, c
     for (int v = 0; v < 3; ++v) z[3 * i + v] = d[i] * (double)uo[3 * i + v];
 }
 
+// Double-float products: a double split into an FP32 head and an FP32 tail.
+__global__ void k_split(const double* __restrict__ x, int64_t n, float* __restrict__ hi, float* __restrict__ lo) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = x[i];
+  const float h = (float)v;
+  hi[i] = h;
+  lo[i] = (float)(v - (double)h);
+}
+// out = Sigma_0 v for 3 right-hand sides in double-float arithmetic on the
+// FP32 pipes: exact head products (FMA remainder), cross terms, and a
+// compensated (two-sum) accumulation per lane; lanes are combined in FP64.
+__global__ void k_symv_df(const float* __restrict__ Shi, const float* __restrict__ Slo, int64_t m,
+                          const float* __restrict__ vhi, const float* __restrict__ vlo, double* __restrict__ out) {
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= m) return;
+  float ah[3] = {0.f, 0.f, 0.f}, al[3] = {0.f, 0.f, 0.f};
+  const float* rh = Shi + i * m;
+  const float* rl = Slo + i * m;
+  for (int64_t j = lane; j < m; j += 32) {
+    const float a = rh[j], b = rl[j];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float x = vhi[3 * j + c], y = vlo[3 * j + c];
+      const float p = a * x;
+      float e = fmaf(a, x, -p);
+      e = fmaf(a, y, e);
+      e = fmaf(b, x, e);
+      const float s = ah[c] + p;
+      const float bb = s - ah[c];
+      float t = (ah[c] - (s - bb)) + (p - bb);
+      t += e + al[c];
+      ah[c] = s + t;
+      al[c] = t - (ah[c] - s);
+    }
+  }
+  double r[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    r[c] = (double)ah[c] + (double)al[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r[c] += __shfl_xor_sync(0xffffffffu, r[c], o);
+  }
+  if (lane == 0) { out[3 * i] = r[0]; out[3 * i + 1] = r[1]; out[3 * i + 2] = r[2]; }
+}
+
 __global__ void k_contact_matvec(int64_t k, const int32_t* cidx, const double* cw, const double* cs,
                                  const double* p, double* q) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -493,12 +542,16 @@ static pd_status ensure_state(pd_solver* s) {
       A((void**)&M->z, sizeof(double) * 3 * m) || A((void**)&M->p, sizeof(double) * 3 * m) ||
       A((void**)&M->q, sizeof(double) * 3 * m) || A((void**)&M->u, sizeof(double) * 3 * m) ||
       A((void**)&M->sc, sizeof(double) * 8) || A((void**)&M->w, sizeof(float) * 3 * mq) ||
-      A((void**)&M->uo, sizeof(float) * 3 * mq) ||
+      A((void**)&M->uo, sizeof(float) * 3 * mq) || A((void**)&M->Shi, sizeof(float) * m * m) ||
+      A((void**)&M->Slo, sizeof(float) * m * m) || A((void**)&M->vhi, sizeof(float) * 3 * m) ||
+      A((void**)&M->vlo, sizeof(float) * 3 * m) ||
       A((void**)&M->bar, sizeof(unsigned) * 4)) {
     s->err = "device allocation for the mixed-precision vectors failed";
     return PD_ERR_OOM;
   }
   if (cudaMallocHost(&M->sc_h, sizeof(double) * 8) != cudaSuccess) return PD_ERR_OOM;
+  k_split<<<nblk(m * m, 256), 256, 0, s->stream>>>(s->Sigma0, m * m, M->Shi, M->Slo);
+  ++pdk::g_launches;
   int lo_prio = 0, hi_prio = 0;
   cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
   if (cudaStreamCreateWithPriority(&M->side, cudaStreamNonBlocking, lo_prio) != cudaSuccess) return PD_ERR_CUDA;
@@ -591,9 +644,12 @@ static cudaError_t precond(pd_solver* s, const Factor& f, const double* r, doubl
   return cudaLaunchCooperativeKernel((void*)k_precond, dim3(M->coop_grid), dim3(256), args, 0, s->stream);
 }
 
-// q = H p = Sigma_0 p + C_22 p  (FP64)
+// q = H p = Sigma_0 p + C_22 p  (double-float Sigma_0 product, FP64 contact term)
 static void hmatvec(pd_solver* s, const double* p, double* q) {
-  pdk::symv3(s->Sigma0, s->m, p, q, s->stream);
+  MixedState* M = s->mixed;
+  k_split<<<nblk(3 * s->m, 256), 256, 0, s->stream>>>(p, 3 * s->m, M->vhi, M->vlo);
+  k_symv_df<<<nblk(32 * s->m, 256), 256, 0, s->stream>>>(M->Shi, M->Slo, s->m, M->vhi, M->vlo, q);
+  pdk::g_launches += 2;
   if (s->k > 0) {
     k_contact_matvec<<<nblk(s->k, 128), 128, 0, s->stream>>>(s->k, s->c_idx, s->c_w, s->c_s, p, q);
     ++pdk::g_launches;

@@ -21,10 +21,10 @@ using namespace dev;
 
 // MODE: 0 = TF32, 1 = 3xTF32 (hi*hi + hi*lo + lo*hi), 2 = BF16.
 template <int MODE>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(128, 3)
     k_rank_k(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int kx0, int kchunks,
              float* __restrict__ C, int64_t ldc, int ti0, int tj0, int n_j, int lower, int* __restrict__ status) {
-  constexpr int NST = (MODE == 1) ? 2 : 4;                 // stages resident in shared memory
+  constexpr int NST = (MODE == 1) ? 1 : 2;                 // stages resident in shared memory (3 CTAs/SM)
   constexpr int STAGE = (MODE == 1) ? 4 * kChunkBytes : 2 * kChunkBytes;  // A, B (+ A_lo, B_lo)
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t full[NST], done[NST];
@@ -165,7 +165,7 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 
 template <int MODE>
 constexpr int smem_bytes() {
-  return ((MODE == 1) ? 2 * 4 * kChunkBytes : 4 * 2 * kChunkBytes) + 1024;
+  return ((MODE == 1) ? 1 * 4 * kChunkBytes : 2 * 2 * kChunkBytes) + 1024;
 }
 
 }  // namespace
