@@ -19,8 +19,10 @@
 #include "mixed.h"
 #include "solver.h"
 #include "tc.h"
+#include "grid_sync.cuh"
 
 namespace pdm {
+using pdk::grid_barrier;
 
 constexpr int NB = 128;      // tile of the low-precision factor
 constexpr int PADW = NB + 1; // padded shared-memory row
@@ -307,25 +309,6 @@ __global__ void __launch_bounds__(256) k_trsm_f32(float* __restrict__ L, float* 
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 8; ++j) Hb[(int64_t)(tr + 16 * i) * mq + tc + 16 * j] = h[i][j];
-}
-
-// Bounded grid barrier for the cooperative launch; false = gave up.
-__device__ bool grid_barrier(unsigned* ctr, unsigned target, int* status) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    ok = 1;
-    __threadfence();
-    atomicAdd(ctr, 1u);
-    unsigned it = 0;
-    while (*(volatile unsigned*)ctr < target) {
-      if (++it > (1u << 26)) { ok = 0; atomicExch(status + 1, 200); break; }
-      if (it > 64) __nanosleep(64);
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  return ok != 0;
 }
 
 // z = D L^-T L^-1 D r for 3 right-hand sides in one cooperative launch.
