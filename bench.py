@@ -56,6 +56,19 @@ def dist_env():
     return rank, world, local
 
 
+def aggregate_replicas(local_ms, steps, world, dist=None, device="cpu"):
+    """Replicas only: every rank ran `steps` steps of its own scene; the job's
+    time is the slowest rank's (max over ranks) and the job's throughput is
+    all ranks' steps over that time.  Returns (max_ms, PD iterations/s)."""
+    import torch
+    ms = float(local_ms)
+    if dist is not None and world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * steps / (ms / 1e3)
+
+
 def workload_name(s, precision):
     return (f"elbow (two r=8 L=60 cylinders + joint ball, voxel h={s.info['h']}): {s.E} tets, {s.n} nodes, "
             f"m={s.m} collision-prone nodes ({100.0 * s.m / s.n:.1f}%), quasistatic, {precision} region solve, "
@@ -304,13 +317,9 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
+    ms, value = aggregate_replicas(e0.elapsed_time(e1), args.steps, world, dist, "cuda")
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
-    value = world * args.steps / (ms / 1e3)
     st = sol.stats()
 
     # ---- end to end through the C ABI with host buffers
@@ -331,12 +340,7 @@ def main():
         sol.step(1)
         xbuf[:] = sol.positions()
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = world * args.steps / e2e_s
+    e2e_ms, e2e = aggregate_replicas(1e3 * (time.perf_counter() - t0), args.steps, world, dist, "cuda")
 
     # ---- roofline of the dominant kernel group: the dense refactor + solve (a5)
     m = s.m

@@ -280,6 +280,12 @@ pd_status pd_mlp_eval(pd_solver* s, double* mse_net, double* mse_zero);
  * batch X [B][14], T [B][3] (for checking the hand-written backward pass). */
 pd_status pd_mlp_loss_grad(pd_solver* s, const float* X, const float* T, int64_t B, double* loss, float* grad);
 
+/* Failure-detection check (no counterpart in the paper): launches a kernel
+ * whose bounded wait on a flag that nothing sets gives up after a short poll
+ * limit (~20 ms), and reports it the way every bounded device wait in the
+ * library does.  Returns PD_ERR_TIMEOUT with the handle still usable. */
+pd_status pd_debug_wait_timeout(pd_solver* s);
+
 /* Change the precision of the collision-region solve on an existing handle. */
 pd_status pd_set_precision(pd_solver* s, int precision);
 

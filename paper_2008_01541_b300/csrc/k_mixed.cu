@@ -774,6 +774,33 @@ pd_status apply_free(pd_solver* s, const double* r, double* z) {
   return PD_OK;
 }
 
+// Diagnostic: a grid barrier that can never complete (the target exceeds the
+// grid), with a short poll limit, to exercise the timeout path.
+__global__ void k_wait_probe(unsigned* ctr, unsigned limit, int* status) {
+  if (threadIdx.x == 0) {
+    atomicAdd(ctr, 1u);
+    unsigned it = 0;
+    while (*(volatile unsigned*)ctr < gridDim.x + 1u) {   // nothing ever adds the last arrival
+      if (++it > limit) { atomicExch(status + 1, 201); break; }
+      __nanosleep(256);
+    }
+  }
+}
+
+}  // namespace pdm
+
+extern "C" pd_status pd_debug_wait_timeout(pd_solver* s) {
+  if (!s) return PD_ERR_INVALID_ARG;
+  cudaMemsetAsync(s->status, 0, sizeof(int) * 4, s->stream);
+  cudaMemsetAsync(s->status + 3, 0, sizeof(int), s->stream);
+  pdm::k_wait_probe<<<4, 32, 0, s->stream>>>(reinterpret_cast<unsigned*>(s->status + 3), 1u << 16, s->status);
+  ++pdk::g_launches;
+  if (cudaGetLastError() != cudaSuccess) return PD_ERR_CUDA;
+  return s->check_status();
+}
+
+namespace pdm {
+
 void mixed_free(pd_solver* s) {
   if (!s->mixed) return;
   if (s->mixed->sc_h) cudaFreeHost(s->mixed->sc_h);

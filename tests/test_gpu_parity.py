@@ -187,3 +187,14 @@ def test_state_roundtrip_and_empty_contacts(pd):
     np.testing.assert_array_equal(v2, v)
     sol.step(2)     # no contacts ever set
     assert sol.stats()["outer_done"] == 2
+
+
+def test_bounded_wait_times_out_and_handle_survives(pd):
+    # a device wait on a flag nothing sets gives up and reports PD_ERR_TIMEOUT
+    s = scenes.config1(nx=3, ny=3, nz=5)
+    sol = _solver(pd, s)
+    st = pd.lib.pd_debug_wait_timeout(sol.h)
+    assert pd._lib.STATUS[st] == "PD_ERR_TIMEOUT"
+    assert b"gave up" in pd.lib.pd_last_error(sol.h)
+    sol.step(1)                       # the context is still usable
+    assert np.all(np.isfinite(sol.positions()))
