@@ -168,10 +168,11 @@ __global__ void __launch_bounds__(256) k_diag_f32(float* __restrict__ L, int64_t
   float* S = sm + 2 * NB * PADW;   // [3][32][33] scratch
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   float* Lt = L + (int64_t)kt * NB * mq + (int64_t)kt * NB;
-  for (int q = tid; q < NB * NB; q += 256) {
-    int r = q / NB, c = q % NB;
-    A[r * PADW + c] = Lt[(int64_t)r * mq + c];
-    Z[r * PADW + c] = 0.f;
+  for (int q = tid; q < NB * NB / 4; q += 256) {
+    const int r = q / (NB / 4), c = 4 * (q % (NB / 4));
+    const float4 v = *reinterpret_cast<const float4*>(Lt + (int64_t)r * mq + c);
+    A[r * PADW + c] = v.x; A[r * PADW + c + 1] = v.y; A[r * PADW + c + 2] = v.z; A[r * PADW + c + 3] = v.w;
+    Z[r * PADW + c] = 0.f; Z[r * PADW + c + 1] = 0.f; Z[r * PADW + c + 2] = 0.f; Z[r * PADW + c + 3] = 0.f;
   }
   __syncthreads();
 #pragma unroll 1
@@ -197,36 +198,62 @@ __global__ void __launch_bounds__(256) k_diag_f32(float* __restrict__ L, int64_t
       for (int j = 0; j < 32; ++j) row[j] = x[j];
     }
     __syncthreads();
-    // trailing update of the lower part below and right of the sub-panel
-    for (int q = tid; q < nbelow * nbelow; q += 256) {
-      const int r = c0 + 32 + q / nbelow, c = c0 + 32 + q % nbelow;
-      if (c > r) continue;
-      float acc = 0.f;
+    // trailing update of the lower part below and right of the sub-panel,
+    // 2 x 2 outputs per thread (blocks on or below the diagonal)
+    {
+      const int nb2 = nbelow / 2;
+      for (int q = tid; q < nb2 * nb2; q += 256) {
+        const int bi = q / nb2, bj = q % nb2;
+        if (bj > bi) continue;
+        const int r = c0 + 32 + 2 * bi, c = c0 + 32 + 2 * bj;
+        float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f;
 #pragma unroll 8
-      for (int t = 0; t < 32; ++t) acc = fmaf(A[r * PADW + c0 + t], A[c * PADW + c0 + t], acc);
-      A[r * PADW + c] -= acc;
+        for (int t = 0; t < 32; ++t) {
+          const float a0 = A[r * PADW + c0 + t], a1 = A[(r + 1) * PADW + c0 + t];
+          const float b0 = A[c * PADW + c0 + t], b1 = A[(c + 1) * PADW + c0 + t];
+          s00 = fmaf(a0, b0, s00); s01 = fmaf(a0, b1, s01); s10 = fmaf(a1, b0, s10); s11 = fmaf(a1, b1, s11);
+        }
+        A[r * PADW + c] -= s00;
+        A[(r + 1) * PADW + c] -= s10;
+        A[(r + 1) * PADW + c + 1] -= s11;
+        if (c + 1 <= r) A[r * PADW + c + 1] -= s01;
+      }
     }
     __syncthreads();
   }
   if (warp < 4) warp_inv32(A + 32 * warp * PADW + 32 * warp, Z + 32 * warp * PADW + 32 * warp);
   __syncthreads();
-  // off-diagonal 32 x 32 blocks of the inverse: Z_ij = -Z_ii sum_{t=j}^{i-1} L_it Z_tj
+  // off-diagonal 32 x 32 blocks of the inverse: Z_ij = -Z_ii sum_{t=j}^{i-1} L_it Z_tj,
+  // 2 x 2 outputs per thread
   for (int d = 1; d < 4; ++d) {
     const int npairs = 4 - d;
-    for (int q = tid; q < npairs * 1024; q += 256) {
-      const int pr = q / 1024, r = (q % 1024) / 32, c = q % 32;
+    for (int q = tid; q < npairs * 256; q += 256) {
+      const int pr = q / 256, r = 2 * ((q % 256) / 16), c = 2 * (q % 16);
       const int j = pr, i = pr + d;
-      float acc = 0.f;
-      for (int t = 32 * j; t < 32 * i; ++t) acc = fmaf(A[(32 * i + r) * PADW + t], Z[t * PADW + 32 * j + c], acc);
-      S[pr * 32 * 33 + r * 33 + c] = acc;
+      float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f;
+      for (int t = 32 * j; t < 32 * i; ++t) {
+        const float a0 = A[(32 * i + r) * PADW + t], a1 = A[(32 * i + r + 1) * PADW + t];
+        const float b0 = Z[t * PADW + 32 * j + c], b1 = Z[t * PADW + 32 * j + c + 1];
+        s00 = fmaf(a0, b0, s00); s01 = fmaf(a0, b1, s01); s10 = fmaf(a1, b0, s10); s11 = fmaf(a1, b1, s11);
+      }
+      float* Sp = S + pr * 32 * 33;
+      Sp[r * 33 + c] = s00; Sp[r * 33 + c + 1] = s01; Sp[(r + 1) * 33 + c] = s10; Sp[(r + 1) * 33 + c + 1] = s11;
     }
     __syncthreads();
-    for (int q = tid; q < npairs * 1024; q += 256) {
-      const int pr = q / 1024, r = (q % 1024) / 32, c = q % 32;
+    for (int q = tid; q < npairs * 256; q += 256) {
+      const int pr = q / 256, r = 2 * ((q % 256) / 16), c = 2 * (q % 16);
       const int j = pr, i = pr + d;
-      float acc = 0.f;
-      for (int t = 0; t <= r; ++t) acc = fmaf(Z[(32 * i + r) * PADW + 32 * i + t], S[pr * 32 * 33 + t * 33 + c], acc);
-      Z[(32 * i + r) * PADW + 32 * j + c] = -acc;
+      const float* Sp = S + pr * 32 * 33;
+      float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f;
+      for (int t = 0; t <= r + 1; ++t) {
+        const float z0 = Z[(32 * i + r) * PADW + 32 * i + t], z1 = Z[(32 * i + r + 1) * PADW + 32 * i + t];
+        const float b0 = Sp[t * 33 + c], b1 = Sp[t * 33 + c + 1];
+        s00 = fmaf(z0, b0, s00); s01 = fmaf(z0, b1, s01); s10 = fmaf(z1, b0, s10); s11 = fmaf(z1, b1, s11);
+      }
+      Z[(32 * i + r) * PADW + 32 * j + c] = -s00;
+      Z[(32 * i + r) * PADW + 32 * j + c + 1] = -s01;
+      Z[(32 * i + r + 1) * PADW + 32 * j + c] = -s10;
+      Z[(32 * i + r + 1) * PADW + 32 * j + c + 1] = -s11;
     }
     __syncthreads();
   }
