@@ -44,6 +44,9 @@ struct MixedState {
   double *hdiag = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *u = nullptr;
   float *Shi = nullptr, *Slo = nullptr;   // Sigma_0 = Shi + Slo (FP32 pair, ~48-bit)
   float *vhi = nullptr, *vlo = nullptr;   // [m][3] split of the vector being multiplied
+  float* Minv0 = nullptr;     // [m][m] explicit inverse of the contact-free factor (PCG form), built once
+  float* r32 = nullptr;       // [m][3] float copy of a right-hand side
+  bool minv_valid = false;
   double* sc = nullptr;       // device scalars: [0] r.r  [1] r.z  [2] p.q  [3] r.z old  [4] g.g
   double* sc_h = nullptr;     // pinned copy
   float *w = nullptr, *uo = nullptr;   // [mq][3] triangular-solve vectors
@@ -412,6 +415,44 @@ __global__ void __launch_bounds__(256) k_precond(const float* __restrict__ Lh, c
     for (int v = 0; v < 3; ++v) z[3 * i + v] = d[i] * (double)uo[3 * i + v];
 }
 
+// z = Minv0 r (FP32 dense symmetric inverse, 3 right-hand sides), one warp per row.
+__global__ void k_minv_apply(const float* __restrict__ Mi, int64_t m, const float* __restrict__ r,
+                             double* __restrict__ z) {
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= m) return;
+  const float* row = Mi + i * m;
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+  for (int64_t j = lane; j < m; j += 32) {
+    const float v = row[j];
+    a0 = fmaf(v, r[3 * j], a0); a1 = fmaf(v, r[3 * j + 1], a1); a2 = fmaf(v, r[3 * j + 2], a2);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+  }
+  if (lane == 0) { z[3 * i] = a0; z[3 * i + 1] = a1; z[3 * i + 2] = a2; }
+}
+__global__ void k_to_f32(const double* __restrict__ x, int64_t n, float* __restrict__ y) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (float)x[i];
+}
+// three unit right-hand sides e_{3q}, e_{3q+1}, e_{3q+2} as the columns of r [m][3]
+__global__ void k_unit3(double* r, int64_t m, int64_t q) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  for (int v = 0; v < 3; ++v) r[3 * i + v] = (i == 3 * q + v) ? 1.0 : 0.0;
+}
+// rows 3q..3q+2 of the inverse from z [m][3] (the inverse is symmetric)
+__global__ void k_store_cols(const double* z, int64_t m, int64_t q, float* Mi) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  for (int v = 0; v < 3; ++v)
+    if (3 * q + v < m) Mi[(3 * q + v) * m + i] = (float)z[3 * i + v];
+}
+
 // Double-float products: a double split into an FP32 head and an FP32 tail.
 __global__ void k_split(const double* __restrict__ x, int64_t n, float* __restrict__ hi, float* __restrict__ lo) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -554,7 +595,7 @@ static pd_status ensure_state(pd_solver* s) {
       A((void**)&M->sc, sizeof(double) * 8) || A((void**)&M->w, sizeof(float) * 3 * mq) ||
       A((void**)&M->uo, sizeof(float) * 3 * mq) || A((void**)&M->Shi, sizeof(float) * m * m) ||
       A((void**)&M->Slo, sizeof(float) * m * m) || A((void**)&M->vhi, sizeof(float) * 3 * m) ||
-      A((void**)&M->vlo, sizeof(float) * 3 * m) ||
+      A((void**)&M->vlo, sizeof(float) * 3 * m) || A((void**)&M->r32, sizeof(float) * 3 * m) ||
       A((void**)&M->bar, sizeof(unsigned) * 4)) {
     s->err = "device allocation for the mixed-precision vectors failed";
     return PD_ERR_OOM;
@@ -654,6 +695,40 @@ static cudaError_t precond(pd_solver* s, const Factor& f, const double* r, doubl
   return cudaLaunchCooperativeKernel((void*)k_precond, dim3(M->coop_grid), dim3(256), args, 0, s->stream);
 }
 
+// Explicit inverse of the contact-free factor, built once from m/3 solves with
+// three unit right-hand sides each; afterwards the preconditioner of the PCG
+// form is one dense FP32 matrix-vector product.
+static pd_status build_minv(pd_solver* s) {
+  MixedState* M = s->mixed;
+  if (M->minv_valid) return PD_OK;
+  if (!M->Minv0) {
+    cudaError_t e = cudaMalloc(&M->Minv0, sizeof(float) * s->m * s->m);
+    if (e != cudaSuccess) { s->err = "device allocation of the explicit inverse failed"; return PD_ERR_OOM; }
+    s->allocs.push_back(M->Minv0);
+  }
+  if (!M->f0.valid) {
+    factor_cast(s, M->f0, false);
+    factor_panels(s, M->f0, pdtc::TF32X3);
+  }
+  const int64_t m = s->m;
+  for (int64_t q = 0; 3 * q < m; ++q) {
+    k_unit3<<<nblk(m, 256), 256, 0, s->stream>>>(M->p, m, q);
+    cudaError_t ce = precond(s, M->f0, M->p, M->z);
+    if (ce != cudaSuccess) { s->err = cudaGetErrorString(ce); return PD_ERR_CUDA; }
+    k_store_cols<<<nblk(m, 256), 256, 0, s->stream>>>(M->z, m, q, M->Minv0);
+    pdk::g_launches += 2;
+  }
+  M->minv_valid = true;
+  return PD_OK;
+}
+
+static void apply_minv(pd_solver* s, const double* r, double* z) {
+  MixedState* M = s->mixed;
+  k_to_f32<<<nblk(3 * s->m, 256), 256, 0, s->stream>>>(r, 3 * s->m, M->r32);
+  k_minv_apply<<<nblk(32 * s->m, 256), 256, 0, s->stream>>>(M->Minv0, s->m, M->r32, z);
+  pdk::g_launches += 2;
+}
+
 // q = H p = Sigma_0 p + C_22 p  (double-float Sigma_0 product, FP64 contact term)
 static void hmatvec(pd_solver* s, const double* p, double* q) {
   MixedState* M = s->mixed;
@@ -694,10 +769,8 @@ pd_status mixed_solve(pd_solver* s, const double* g, const double* u0, double* u
   Factor* f = &M->f;
   if (warm) {
     f = &M->f0;
-    if (!f->valid) {
-      factor_cast(s, *f, false);
-      factor_panels(s, *f, pdtc::TF32X3);
-    }
+    pd_status rb = build_minv(s);
+    if (rb != PD_OK) return rb;
     s->tbegin(4);
   } else {
     s->tbegin(2);
@@ -735,7 +808,8 @@ pd_status mixed_solve(pd_solver* s, const double* g, const double* u0, double* u
     ok = rr <= tol2;
   } else if (!ok) {
     // refinement accelerated by preconditioned CG (FP64 vectors, true residual checked at the end)
-    ce = precond(s, *f, M->r, M->z);
+    if (warm) apply_minv(s, M->r, M->z);
+    else ce = precond(s, *f, M->r, M->z);
     dot(s, M->r, M->z, 1);
     k_cg_dir<<<nblk(n3, 256), 256, 0, st>>>(M->p, M->z, M->sc, n3, 1); ++pdk::g_launches;
     for (it = 1; it <= s->opt.max_refine && ce == cudaSuccess; ++it) {
@@ -753,7 +827,8 @@ pd_status mixed_solve(pd_solver* s, const double* g, const double* u0, double* u
         if (rr <= tol2) break;
       }
       cudaMemcpyAsync(M->sc + 3, M->sc + 1, sizeof(double), cudaMemcpyDeviceToDevice, st);
-      ce = precond(s, *f, M->r, M->z);
+      if (warm) apply_minv(s, M->r, M->z);
+      else ce = precond(s, *f, M->r, M->z);
       dot(s, M->r, M->z, 1);
       k_cg_dir<<<nblk(n3, 256), 256, 0, st>>>(M->p, M->z, M->sc, n3, 0); ++pdk::g_launches;
     }
@@ -788,16 +863,9 @@ pd_status mixed_solve(pd_solver* s, const double* g, const double* u0, double* u
 pd_status apply_free(pd_solver* s, const double* r, double* z) {
   pd_status rs = ensure_state(s);
   if (rs != PD_OK) return rs;
-  MixedState* M = s->mixed;
-  if (!M->f0.valid) {
-    factor_cast(s, M->f0, false);
-    factor_panels(s, M->f0, pdtc::TF32X3);
-  }
-  cudaError_t ce = precond(s, M->f0, r, z);
-  if (ce != cudaSuccess) {
-    s->err = std::string("cooperative launch failed: ") + cudaGetErrorString(ce);
-    return PD_ERR_CUDA;
-  }
+  rs = build_minv(s);
+  if (rs != PD_OK) return rs;
+  apply_minv(s, r, z);
   return PD_OK;
 }
 
