@@ -81,3 +81,31 @@ def test_outer_iteration_mixed_matches_oracle(pd, prec):
     xo = o.step(1, 2, oracle_callback(s, 0), s.dirichlet_positions(0))
     err = np.linalg.norm(sol.positions() - xo) / np.linalg.norm(xo - x0)
     assert err <= 1e-8, err
+
+
+def test_resampled_contacts_per_step_error_vs_oracle(pd):
+    # config-3 style: a seeded indenter path resamples the contact set every
+    # step; the split-TF32 and BF16 forms stay within 1e-8 of the FP64 oracle
+    from paper_2008_01541_b300 import warmstart as ws
+    s = scenes.small_elbow(h=1.5)
+    centres, radius = ws.indenter_path(s, seed=5, steps=4)
+    for prec in ("FP32_IR", "BF16_IR"):
+        sol = _solver(pd, s, precision=getattr(pd, prec), max_refine=200)
+        o = oracle.OracleSolver(s.X, s.tets, s.dirichlet, s.region, s.mu)
+        errs = []
+        for st, ctr in enumerate(centres):
+            x_ref = sol.positions()
+            con_fn = lambda x, ctr=ctr: scenes.sphere_contacts(s.proxies, x, ctr, 1.3 * radius, 1e6)
+
+            def cb(x2, ctr=ctr):
+                x = x_ref.copy()
+                x[s.region] = x2
+                c = con_fn(x)
+                return contact_tuple(c)
+
+            sol.step(2, cb)
+            o.step(2, 1, con_fn)
+            errs.append(np.linalg.norm(sol.positions() - o.x) / np.linalg.norm(o.x - s.X))
+        print(prec, "per-step relative error vs oracle:", ["%.1e" % e for e in errs])
+        assert max(errs) <= 1e-8, (prec, errs)
+        sol.close()
