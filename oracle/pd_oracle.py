@@ -136,7 +136,7 @@ def projection_rhs(R, tets, Dm_inv, vol, mu, n):
 
 def _contact_W(contacts, n):
     k = contacts.k
-    rows = np.repeat(np.arange(k), 4)
+    rows = np.repeat(np.arange(k), contacts.nodes.shape[1])
     cols = contacts.nodes.ravel()
     vals = contacts.w.ravel()
     keep = cols >= 0

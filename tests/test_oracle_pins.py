@@ -343,3 +343,24 @@ def test_paper_dense_flop_estimate_reading():
     # Section 3.3 quotes ~8/3 GFLOP for a Cholesky at m = 2000: that is m^3 / 3
     m = 2000
     assert abs(m ** 3 / 3 / 1e9 - 8.0 / 3.0) < 1e-12
+
+
+def test_two_sided_spring_force_and_closed_form():
+    # an 8-slot spring on x_a - x_b: forces are equal and opposite, and a lone
+    # pair of free nodes ends at the target separation (Sherman-Morrison form)
+    X, tets = _small_mesh(5)
+    rng_ = _rng(12)
+    x = X + 0.1 * rng_.normal(size=X.shape)
+    nodes = np.full((1, 8), -1, np.int32)
+    w = np.zeros((1, 8))
+    nodes[0, 0], nodes[0, 4] = 3, 7
+    w[0, 0], w[0, 4] = 1.0, -1.0
+    t = np.array([[0.3, -0.2, 0.5]])
+    c = scenes.Contacts(nodes, w, t, np.array([5.0]))
+    f = oracle.contact_forces(c, x)
+    np.testing.assert_allclose(f[3], -f[7], atol=1e-14)
+    np.testing.assert_allclose(f[3], -5.0 * ((x[3] - x[7]) - t[0]), atol=1e-13)
+    d = rng_.normal(size=x.shape)
+    eps = 1e-4
+    fd = -(oracle.contact_energy(c, x + eps * d) - oracle.contact_energy(c, x - eps * d)) / (2 * eps)
+    assert abs(fd - np.sum(f * d)) < 1e-8 * max(1, abs(fd))
