@@ -134,6 +134,18 @@ pd_status pd_set_contacts(pd_solver* s, int64_t k, const int32_t* nodes /*[k][4]
                           const double* w /*[k][4]*/, const double* target /*[k][3]*/,
                           const double* stiffness /*[k]*/);
 
+/* Two-sided springs between two proxies (self-collision, Section 2.3 with
+ * the spring between p_a and p_b; the paper notes that W is re-sent for
+ * self-collision, Section 3.3): spring j acts on the difference
+ * d_j = sum_{a<8} w[j][a] x[nodes[j][a]] -- typically slots 0..3 hold one
+ * proxy's barycentric weights and slots 4..7 the other's, negated -- with
+ * energy stiffness[j]/2 ||d_j - target[j]||^2 (target = the separation to
+ * keep, frozen for the iteration).  Same ownership and errors as
+ * pd_set_contacts; replaces all springs. */
+pd_status pd_set_contact_pairs(pd_solver* s, int64_t k, const int32_t* nodes /*[k][8]*/,
+                               const double* w /*[k][8]*/, const double* target /*[k][3]*/,
+                               const double* stiffness /*[k]*/);
+
 /* One time step: outer_iters passes of Algorithm 1 (Section 3.4).  If cb is
  * not NULL it is called at every inner iteration before the local beta step;
  * otherwise the springs last set stay active.  Errors: NOT_SPD,

@@ -59,6 +59,7 @@ _sigs = {
                                 ctypes.POINTER(Options), ctypes.POINTER(P)]),
     "pd_set_dirichlet": (ctypes.c_int, [P, P]),
     "pd_set_contacts": (ctypes.c_int, [P, I64, P, P, P, P]),
+    "pd_set_contact_pairs": (ctypes.c_int, [P, I64, P, P, P, P]),
     "pd_step": (ctypes.c_int, [P, ctypes.c_int, CB, P]),
     "pd_get_positions": (ctypes.c_int, [P, P]),
     "pd_get_positions_dev": (ctypes.c_int, [P, P]),

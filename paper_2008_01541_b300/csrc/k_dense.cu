@@ -24,37 +24,37 @@ __global__ void k_copy_sigma(const double* __restrict__ S, int64_t m, double* __
   }
 }
 
-__global__ void k_contact_scatter(int64_t k, const int32_t* __restrict__ cidx, const double* __restrict__ cw,
+__global__ void k_contact_scatter(int64_t k, int ns, const int32_t* __restrict__ cidx, const double* __restrict__ cw,
                                   const double* __restrict__ cs, double* __restrict__ H, int64_t mp) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= 16 * k) return;
-  int64_t j = t >> 4;
-  int a = (t >> 2) & 3, b = t & 3;
-  int ra = cidx[4 * j + a], rb = cidx[4 * j + b];
+  if (t >= (int64_t)ns * ns * k) return;
+  int64_t j = t / (ns * ns);
+  int a = (int)((t / ns) % ns), b = (int)(t % ns);
+  int ra = cidx[ns * j + a], rb = cidx[ns * j + b];
   if (ra < 0 || rb < 0 || ra < rb) return;
-  atomicAdd(H + ra + (int64_t)rb * mp, cs[j] * cw[4 * j + a] * cw[4 * j + b]);
+  atomicAdd(H + ra + (int64_t)rb * mp, cs[j] * cw[ns * j + a] * cw[ns * j + b]);
 }
 
-__global__ void k_contact_forces(int64_t k, const int32_t* __restrict__ cidx, const double* __restrict__ cw,
+__global__ void k_contact_forces(int64_t k, int ns, const int32_t* __restrict__ cidx, const double* __restrict__ cw,
                                  const double* __restrict__ ct, const double* __restrict__ cs,
                                  const int32_t* __restrict__ region, const double* __restrict__ x,
                                  double* __restrict__ g) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= k) return;
   double p[3] = {0, 0, 0};
-  for (int a = 0; a < 4; ++a) {
-    int r = cidx[4 * j + a];
+  for (int a = 0; a < ns; ++a) {
+    int r = cidx[ns * j + a];
     if (r < 0) continue;
     const double* xv = x + 3 * (int64_t)region[r];
-    double w = cw[4 * j + a];
+    double w = cw[ns * j + a];
     p[0] += w * xv[0]; p[1] += w * xv[1]; p[2] += w * xv[2];
   }
   double c = cs[j];
   double q[3] = {c * (p[0] - ct[3 * j]), c * (p[1] - ct[3 * j + 1]), c * (p[2] - ct[3 * j + 2])};
-  for (int a = 0; a < 4; ++a) {
-    int r = cidx[4 * j + a];
+  for (int a = 0; a < ns; ++a) {
+    int r = cidx[ns * j + a];
     if (r < 0) continue;
-    double w = cw[4 * j + a];
+    double w = cw[ns * j + a];
     atomicAdd(g + 3 * (int64_t)r, -w * q[0]);
     atomicAdd(g + 3 * (int64_t)r + 1, -w * q[1]);
     atomicAdd(g + 3 * (int64_t)r + 2, -w * q[2]);
@@ -284,17 +284,17 @@ void copy_sigma(const double* S, int64_t m, double* H, int64_t mp, cudaStream_t 
 }
 
 void contact_scatter(int64_t k, const int32_t* cidx, const double* cw, const double* cs, double* H,
-                     int64_t mp, cudaStream_t st) {
+                     int64_t mp, cudaStream_t st, int ns) {
   if (k > 0) {
-    k_contact_scatter<<<nblk(16 * k, 256), 256, 0, st>>>(k, cidx, cw, cs, H, mp);
+    k_contact_scatter<<<nblk((int64_t)ns * ns * k, 256), 256, 0, st>>>(k, ns, cidx, cw, cs, H, mp);
     ++g_launches;
   }
 }
 
 void contact_forces(int64_t k, const int32_t* cidx, const double* cw, const double* ct, const double* cs,
-                    const int32_t* region, const double* x, double* g, cudaStream_t st) {
+                    const int32_t* region, const double* x, double* g, cudaStream_t st, int ns) {
   if (k > 0) {
-    k_contact_forces<<<nblk(k, 128), 128, 0, st>>>(k, cidx, cw, ct, cs, region, x, g);
+    k_contact_forces<<<nblk(k, 128), 128, 0, st>>>(k, ns, cidx, cw, ct, cs, region, x, g);
     ++g_launches;
   }
 }

@@ -65,12 +65,13 @@ __global__ void k_hdiag(const double* S, int64_t m, double* hd) {
 }
 __global__ void k_contact_diag(int64_t k, const int32_t* cidx, const double* cw, const double* cs, double* hd) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= 16 * k) return;
-  int64_t j = t >> 4;
-  int a = (t >> 2) & 3, b = t & 3;
-  int ra = cidx[4 * j + a], rb = cidx[4 * j + b];
+  constexpr int NS = pdk::CSLOTS;
+  if (t >= (int64_t)NS * NS * k) return;
+  int64_t j = t / (NS * NS);
+  int a = (int)((t / NS) % NS), b = (int)(t % NS);
+  int ra = cidx[NS * j + a], rb = cidx[NS * j + b];
   if (ra < 0 || ra != rb) return;
-  atomicAdd(hd + ra, cs[j] * cw[4 * j + a] * cw[4 * j + b]);
+  atomicAdd(hd + ra, cs[j] * cw[NS * j + a] * cw[NS * j + b]);
 }
 __global__ void k_dscale(const double* hd, int64_t m, int64_t mq, double* d, int* status) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -100,12 +101,13 @@ __global__ void k_cast_eq(const double* __restrict__ S, int64_t m, const double*
 __global__ void k_contact_scatter_f32(int64_t k, const int32_t* cidx, const double* cw, const double* cs,
                                       const double* d, float* L, int64_t mq) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= 16 * k) return;
-  int64_t j = t >> 4;
-  int a = (t >> 2) & 3, b = t & 3;
-  int ra = cidx[4 * j + a], rb = cidx[4 * j + b];
+  constexpr int NS = pdk::CSLOTS;
+  if (t >= (int64_t)NS * NS * k) return;
+  int64_t j = t / (NS * NS);
+  int a = (int)((t / NS) % NS), b = (int)(t % NS);
+  int ra = cidx[NS * j + a], rb = cidx[NS * j + b];
   if (ra < 0 || rb < 0 || ra < rb) return;
-  atomicAdd(L + (int64_t)ra * mq + rb, (float)(cs[j] * cw[4 * j + a] * cw[4 * j + b] * d[ra] * d[rb]));
+  atomicAdd(L + (int64_t)ra * mq + rb, (float)(cs[j] * cw[NS * j + a] * cw[NS * j + b] * d[ra] * d[rb]));
 }
 
 // One warp factors the 32 x 32 block at Ap (row stride PADW) in registers
@@ -504,18 +506,19 @@ __global__ void k_contact_matvec(int64_t k, const int32_t* cidx, const double* c
                                  const double* p, double* q) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= k) return;
+  constexpr int NS = pdk::CSLOTS;
   double s0 = 0, s1 = 0, s2 = 0;
-  for (int a = 0; a < 4; ++a) {
-    int ra = cidx[4 * j + a];
+  for (int a = 0; a < NS; ++a) {
+    int ra = cidx[NS * j + a];
     if (ra < 0) continue;
-    double wa = cw[4 * j + a];
+    double wa = cw[NS * j + a];
     s0 += wa * p[3 * ra]; s1 += wa * p[3 * ra + 1]; s2 += wa * p[3 * ra + 2];
   }
   double c = cs[j];
-  for (int a = 0; a < 4; ++a) {
-    int ra = cidx[4 * j + a];
+  for (int a = 0; a < NS; ++a) {
+    int ra = cidx[NS * j + a];
     if (ra < 0) continue;
-    double f = c * cw[4 * j + a];
+    double f = c * cw[NS * j + a];
     atomicAdd(q + 3 * ra, f * s0); atomicAdd(q + 3 * ra + 1, f * s1); atomicAdd(q + 3 * ra + 2, f * s2);
   }
 }
@@ -638,11 +641,11 @@ static void factor_cast(pd_solver* s, Factor& f, bool with_contacts) {
   cudaStream_t st = s->stream;
   const int64_t k = with_contacts ? s->k : 0;
   k_hdiag<<<nblk(m, 256), 256, 0, st>>>(s->Sigma0, m, M->hdiag); ++pdk::g_launches;
-  if (k > 0) { k_contact_diag<<<nblk(16 * k, 256), 256, 0, st>>>(k, s->c_idx, s->c_w, s->c_s, M->hdiag); ++pdk::g_launches; }
+  if (k > 0) { k_contact_diag<<<nblk((int64_t)pdk::CSLOTS * pdk::CSLOTS * k, 256), 256, 0, st>>>(k, s->c_idx, s->c_w, s->c_s, M->hdiag); ++pdk::g_launches; }
   k_dscale<<<nblk(mq, 256), 256, 0, st>>>(M->hdiag, m, mq, f.d, s->status); ++pdk::g_launches;
   k_cast_eq<<<dim3((unsigned)T, (unsigned)T), 256, 0, st>>>(s->Sigma0, m, f.d, f.L, mq); ++pdk::g_launches;
   if (k > 0) {
-    k_contact_scatter_f32<<<nblk(16 * k, 256), 256, 0, st>>>(k, s->c_idx, s->c_w, s->c_s, f.d, f.L, mq);
+    k_contact_scatter_f32<<<nblk((int64_t)pdk::CSLOTS * pdk::CSLOTS * k, 256), 256, 0, st>>>(k, s->c_idx, s->c_w, s->c_s, f.d, f.L, mq);
     ++pdk::g_launches;
   }
 }

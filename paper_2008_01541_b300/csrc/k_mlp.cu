@@ -215,23 +215,24 @@ __global__ void k_contact_feat(int64_t k, const int32_t* cidx, const double* cw,
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= k) return;
   const double cs_j = cs[j];
+  constexpr int NS = pdk::CSLOTS;
   double p[3] = {0, 0, 0};
-  for (int a = 0; a < 4; ++a) {
-    int r = cidx[4 * j + a];
+  for (int a = 0; a < NS; ++a) {
+    int r = cidx[NS * j + a];
     if (r < 0) continue;
     const double* xv = x + 3 * (int64_t)region[r];
-    double w = cw[4 * j + a];
+    double w = cw[NS * j + a];
     p[0] += w * xv[0]; p[1] += w * xv[1]; p[2] += w * xv[2];
   }
   const double d[3] = {ct[3 * j] - p[0], ct[3 * j + 1] - p[1], ct[3 * j + 2] - p[2]};
-  for (int a = 0; a < 4; ++a) {
-    int r = cidx[4 * j + a];
+  for (int a = 0; a < NS; ++a) {
+    int r = cidx[NS * j + a];
     if (r < 0) continue;
-    float w = (float)cw[4 * j + a];
+    float w = (float)cw[NS * j + a];
     atomicAdd(cacc + 4 * r, w * (float)d[0]);
     atomicAdd(cacc + 4 * r + 1, w * (float)d[1]);
     atomicAdd(cacc + 4 * r + 2, w * (float)d[2]);
-    atomicAdd(cacc + 4 * r + 3, (float)(cs_j * cw[4 * j + a] * cw[4 * j + a]));
+    atomicAdd(cacc + 4 * r + 3, (float)(cs_j * cw[NS * j + a] * cw[NS * j + a]));
   }
 }
 // Features of region node i, linear in g where they are vectors:

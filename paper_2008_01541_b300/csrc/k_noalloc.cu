@@ -100,7 +100,7 @@ extern "C" pd_status pd_schur_solve_noalloc(const double* sigma_dev, int64_t m, 
     return PD_ERR_CUDA;
   }
   pdk::copy_sigma(sigma_dev, m, H, mp, st);
-  pdk::contact_scatter(k, cidx_dev, cw_dev, cs_dev, H, mp, st);
+  pdk::contact_scatter(k, cidx_dev, cw_dev, cs_dev, H, mp, st, 4);
   pdk::cholesky_fp64(H, mp, Linv, status, st);
   pdk::chol_solve_fp64(H, mp, Linv, g_dev, u_dev, m, work, st);
   int status_h[4] = {0, 0, 0, 0};

@@ -46,13 +46,16 @@ void sparse_backward(const SparseFactor& f, const double* y, double* u, double* 
 // ---- dense collision-region block (Section 3.3) ---------------------------
 // H (mp x mp, column-major, lower) = Sigma0 (m x m) padded with identity.
 void copy_sigma(const double* Sigma0, int64_t m, double* H, int64_t mp, cudaStream_t st);
-// H[ra][rb] += c_j w_a w_b for the k springs (region indices, -1 = unused)
+// Springs store ns node slots each (region indices, -1 = unused): 4 for a
+// proxy embedded in one tet, 8 for a two-sided spring between two proxies.
+constexpr int CSLOTS = 8;
+// H[ra][rb] += c_j w_a w_b for the k springs
 void contact_scatter(int64_t k, const int32_t* cidx, const double* cw, const double* cs,
-                     double* H, int64_t mp, cudaStream_t st);
+                     double* H, int64_t mp, cudaStream_t st, int ns = CSLOTS);
 // g[r][:] += -w_a c_j (p_j - t_j) with p_j = sum_a w_a x[region[r_a]]
 void contact_forces(int64_t k, const int32_t* cidx, const double* cw, const double* ct,
                     const double* cs, const int32_t* region, const double* x, double* g,
-                    cudaStream_t st);
+                    cudaStream_t st, int ns = CSLOTS);
 // Side stream and events for the look-ahead factorisation order.
 struct LookAhead {
   cudaStream_t side = nullptr;

@@ -239,50 +239,64 @@ pd_status pd_set_dirichlet(pd_solver* s, const double* pos) {
   return PD_OK;
 }
 
-pd_status pd_set_contacts(pd_solver* s, int64_t k, const int32_t* nodes, const double* w, const double* target,
-                          const double* stiffness) {
+// Springs are stored with pdk::CSLOTS node slots; `ns` is the caller's slot count.
+static pd_status set_contacts_slots(pd_solver* s, int64_t k, int ns, const int32_t* nodes, const double* w,
+                                    const double* target, const double* stiffness) {
   if (!s) return PD_ERR_INVALID_ARG;
   if (k < 0 || (k > 0 && (!nodes || !w || !target || !stiffness))) { s->err = "invalid contact arrays"; return PD_ERR_INVALID_ARG; }
-  std::vector<int32_t> idx(4 * k);
+  constexpr int NS = pdk::CSLOTS;
+  std::vector<int32_t> idx((size_t)NS * k, -1);
+  std::vector<double> ww((size_t)NS * k, 0.0);
   for (int64_t j = 0; j < k; ++j) {
     if (!std::isfinite(stiffness[j])) { s->err = "non-finite stiffness"; return PD_ERR_INVALID_ARG; }
     for (int a = 0; a < 3; ++a)
       if (!std::isfinite(target[3 * j + a])) { s->err = "non-finite target"; return PD_ERR_INVALID_ARG; }
-    for (int a = 0; a < 4; ++a) {
-      int32_t v = nodes[4 * j + a];
+    for (int a = 0; a < ns; ++a) {
+      int32_t v = nodes[(int64_t)ns * j + a];
+      const double wa = w[(int64_t)ns * j + a];
       if (v < 0) {
-        if (w[4 * j + a] != 0.0) { s->err = "unused contact slot with nonzero weight"; return PD_ERR_INVALID_ARG; }
-        idx[4 * j + a] = -1;
+        if (wa != 0.0) { s->err = "unused contact slot with nonzero weight"; return PD_ERR_INVALID_ARG; }
         continue;
       }
       if (v >= s->n || s->region_index[v] < 0) {
         s->err = "contact " + std::to_string(j) + " names node " + std::to_string(v) + " outside the region";
         return PD_ERR_CONTACT_OUTSIDE_REGION;
       }
-      if (!std::isfinite(w[4 * j + a])) { s->err = "non-finite weight"; return PD_ERR_INVALID_ARG; }
-      idx[4 * j + a] = s->region_index[v];
+      if (!std::isfinite(wa)) { s->err = "non-finite weight"; return PD_ERR_INVALID_ARG; }
+      idx[(size_t)NS * j + a] = s->region_index[v];
+      ww[(size_t)NS * j + a] = wa;
     }
   }
   if (k > s->kcap) {
     int64_t cap = std::max<int64_t>(k, 2 * s->kcap);
-    int32_t* ni; double *nw, *nt, *ns;
-    CK(cudaMalloc(&ni, sizeof(int32_t) * 4 * cap));
-    CK(cudaMalloc(&nw, sizeof(double) * 4 * cap));
+    int32_t* ni; double *nw, *nt, *nsf;
+    CK(cudaMalloc(&ni, sizeof(int32_t) * NS * cap));
+    CK(cudaMalloc(&nw, sizeof(double) * NS * cap));
     CK(cudaMalloc(&nt, sizeof(double) * 3 * cap));
-    CK(cudaMalloc(&ns, sizeof(double) * cap));
+    CK(cudaMalloc(&nsf, sizeof(double) * cap));
     cudaFree(s->c_idx); cudaFree(s->c_w); cudaFree(s->c_t); cudaFree(s->c_s);
-    s->c_idx = ni; s->c_w = nw; s->c_t = nt; s->c_s = ns;
+    s->c_idx = ni; s->c_w = nw; s->c_t = nt; s->c_s = nsf;
     s->kcap = cap;
   }
   if (k > 0) {
-    CK(cudaMemcpyAsync(s->c_idx, idx.data(), sizeof(int32_t) * 4 * k, cudaMemcpyHostToDevice, s->stream));
-    CK(cudaMemcpyAsync(s->c_w, w, sizeof(double) * 4 * k, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->c_idx, idx.data(), sizeof(int32_t) * NS * k, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->c_w, ww.data(), sizeof(double) * NS * k, cudaMemcpyHostToDevice, s->stream));
     CK(cudaMemcpyAsync(s->c_t, target, sizeof(double) * 3 * k, cudaMemcpyHostToDevice, s->stream));
     CK(cudaMemcpyAsync(s->c_s, stiffness, sizeof(double) * k, cudaMemcpyHostToDevice, s->stream));
     CK(cudaStreamSynchronize(s->stream));  // host arrays may be freed by the caller on return
   }
   s->k = k;
   return PD_OK;
+}
+
+pd_status pd_set_contacts(pd_solver* s, int64_t k, const int32_t* nodes, const double* w, const double* target,
+                          const double* stiffness) {
+  return set_contacts_slots(s, k, 4, nodes, w, target, stiffness);
+}
+
+pd_status pd_set_contact_pairs(pd_solver* s, int64_t k, const int32_t* nodes, const double* w, const double* target,
+                               const double* stiffness) {
+  return set_contacts_slots(s, k, 8, nodes, w, target, stiffness);
 }
 
 pd_status pd_step(pd_solver* s, int outer_iters, pd_contact_cb cb, void* user) {

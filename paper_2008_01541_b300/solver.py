@@ -83,12 +83,16 @@ class Solver:
         self._check(lib.pd_set_dirichlet(self.h, _ptr(pos)))
 
     def set_contacts(self, nodes, w, target, stiffness):
-        nodes = _c(nodes, np.int32).reshape(-1, 4)
+        """Springs with 4 node slots (one proxy) or 8 (two-sided, pd_set_contact_pairs)."""
+        nodes = np.asarray(nodes)
+        slots = 8 if nodes.ndim == 2 and nodes.shape[1] == 8 else 4
+        nodes = _c(nodes, np.int32).reshape(-1, slots)
         k = len(nodes)
-        w = _c(w, np.float64).reshape(k, 4)
+        w = _c(w, np.float64).reshape(k, slots)
         target = _c(target, np.float64).reshape(k, 3)
         stiffness = _c(stiffness, np.float64).reshape(k)
-        self._check(lib.pd_set_contacts(self.h, k, _ptr(nodes), _ptr(w), _ptr(target), _ptr(stiffness)))
+        fn = lib.pd_set_contact_pairs if slots == 8 else lib.pd_set_contacts
+        self._check(fn(self.h, k, _ptr(nodes), _ptr(w), _ptr(target), _ptr(stiffness)))
 
     def step(self, outer_iters, contacts_fn=None):
         """contacts_fn(x2 [m,3] numpy) -> (nodes, w, target, stiffness) or None."""

@@ -111,6 +111,28 @@ def cylinder_contacts(nodes, x, origin, axis, radius, length, stiffness):
     return _node_contacts(nodes[act], t, stiffness)
 
 
+def pair_contacts(side_a, side_b, x, gap, stiffness):
+    """Two-sided springs between surface nodes of opposite sides closer than
+    `gap`: spring on d = x_a - x_b with frozen target gap * (x_a - x_b)/|x_a - x_b|,
+    i.e. the pair is pushed apart to distance `gap` (8-slot rows: +1 on a, -1 on b)."""
+    if len(side_a) == 0 or len(side_b) == 0:
+        return Contacts(np.zeros((0, 8), np.int32), np.zeros((0, 8)), np.zeros((0, 3)), np.zeros(0))
+    pa, pb = x[side_a], x[side_b]
+    d2 = ((pa[:, None, :] - pb[None, :, :]) ** 2).sum(-1)
+    j = np.argmin(d2, axis=1)
+    dist = np.sqrt(d2[np.arange(len(side_a)), j])
+    act = (dist < gap) & (dist > 1e-12)
+    ia, ib = side_a[act], side_b[j[act]]
+    k = len(ia)
+    nodes = np.full((k, 8), -1, np.int32)
+    w = np.zeros((k, 8))
+    nodes[:, 0], nodes[:, 4] = ia, ib
+    w[:, 0], w[:, 4] = 1.0, -1.0
+    d = x[ia] - x[ib]
+    target = gap * d / np.linalg.norm(d, axis=1, keepdims=True)
+    return Contacts(nodes, w, target, np.full(k, float(stiffness)))
+
+
 def _cat(*cs):
     cs = [c for c in cs if c.k > 0]
     if not cs:
@@ -250,10 +272,16 @@ def elbow(h=0.585, seed=0, region_fraction=0.05, inner_iters=1, contact_mode="se
         cb = cylinder_contacts(side_a, x, np.zeros(3), axis_b, _R, _L, stiffness)
         return _cat(ca, cb)
 
+    all_a = proxies[(X[proxies, 0] + X[proxies, 1]) < 0.0]
+    all_b = proxies[(X[proxies, 0] + X[proxies, 1]) >= 0.0]
+
+    def self_pairs(x, gap=None):
+        return pair_contacts(all_a, all_b, x, 2.0 * h if gap is None else gap, stiffness)
+
     return Scene("elbow", X, tets, dirichlet, region, proxies, mu=1e4, lam=0.0,
                  density=1000.0, dt=0.0, outer_iters=10, inner_iters=inner_iters, steps=60,
                  stiffness=stiffness, dirichlet_positions=dirichlet_positions,
-                 contacts=contacts, info={"h": h, "theta": theta, "rest_step": 45})
+                 contacts=contacts, info={"h": h, "theta": theta, "rest_step": 45, "self_pairs": self_pairs})
 
 
 def small_elbow(h=2.0, seed=0, region_fraction=0.05, inner_iters=1):

@@ -198,3 +198,32 @@ def test_bounded_wait_times_out_and_handle_survives(pd):
     assert b"gave up" in pd.lib.pd_last_error(sol.h)
     sol.step(1)                       # the context is still usable
     assert np.all(np.isfinite(sol.positions()))
+
+
+def test_two_sided_springs_match_oracle(pd):
+    # self-collision springs between two proxies (8-slot W rows)
+    s = scenes.small_elbow(h=1.5)
+    x0 = s.X.copy()
+    pairs = s.info["self_pairs"](x0, gap=6.0)
+    assert pairs.k > 5 and pairs.nodes.shape[1] == 8
+    S0, H = _oracle_H(s, pairs)
+    sol = _solver(pd, s)
+    sol.set_contacts(*contact_tuple(pairs))
+    g = rng(31).normal(size=(s.m, 3)) * 1e3
+    u = sol.schur_solve(g)
+    assert np.linalg.norm(g - H @ u) / np.linalg.norm(g) <= TOL
+    # one outer iteration with the pairs re-detected at every inner iteration
+    sol.set_state(x0)
+    sol.set_dirichlet(s.dirichlet_positions(50))
+
+    def cb(x2):
+        x = x0.copy()
+        x[s.region] = x2
+        return contact_tuple(s.info["self_pairs"](x, gap=6.0))
+
+    sol.step(1, cb)
+    o = oracle.OracleSolver(s.X, s.tets, s.dirichlet, s.region, s.mu)
+    o.x = x0.copy()
+    xo = o.step(1, 1, lambda x: s.info["self_pairs"](x, gap=6.0), s.dirichlet_positions(50))
+    err = np.linalg.norm(sol.positions() - xo) / np.linalg.norm(xo - x0)
+    assert err <= TOL, err
