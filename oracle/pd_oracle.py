@@ -23,6 +23,13 @@ Where the paper is silent or garbled, these readings are taken:
     inertia belongs to the alpha part, the x_2 inertia to the beta part.
   * Dirichlet nodes are eliminated; their prescribed positions enter the
     right-hand side only.
+  * Bi-phasic strain limiting (Section 5): the open set S of matrices with
+    singular values strictly between sigma_min and sigma_max is taken with
+    its closure, so the minimiser exists; it is Q = U clamp(Sigma) V^T from
+    the SVD with non-negative singular values (an inverted F keeps its
+    reflection in Q).  The mu' term is present for every element, so the
+    system matrix carries mu + mu' and the target of element e is
+    (mu R_e + mu' Q_e) / (mu + mu').
 
 Parity status: every function below is pinned by tests against closed forms,
 invariants, finite differences or brute force, except the multi-step
@@ -35,7 +42,7 @@ import scipy.sparse.linalg as spla
 
 __all__ = [
     "element_precompute", "shape_gradients", "deformation_gradients",
-    "polar_rotations", "pd_energy", "elastic_forces", "stiffness_matrix",
+    "polar_rotations", "strain_limit_projection", "biphasic_energy", "pd_energy", "elastic_forces", "stiffness_matrix",
     "lumped_mass", "projection_rhs", "contact_matrix", "contact_forces",
     "contact_energy", "Partition", "partition", "global_solve",
     "OracleSolver", "schur_complement",
@@ -81,6 +88,22 @@ def polar_rotations(F):
     D = np.ones(F.shape[:-2] + (3,))
     D[..., 2] = d
     return (U * D[..., None, :]) @ Vt
+
+
+def strain_limit_projection(F, sigma_min, sigma_max):
+    """Local step of the bi-phasic term (Section 5): the matrix with singular
+    values in [sigma_min, sigma_max] closest to F in the Frobenius norm,
+    Q = U clamp(Sigma, sigma_min, sigma_max) V^T from the SVD F = U Sigma V^T."""
+    U, s, Vt = np.linalg.svd(F)
+    return (U * np.clip(s, sigma_min, sigma_max)[..., None, :]) @ Vt
+
+
+def biphasic_energy(x, R, Q, tets, Dm_inv, vol, mu, mu_prime):
+    """E_hat'(x, R, Q) = sum_e Vol_e (mu' ||F_e - Q_e||^2 + mu ||F_e - R_e||^2)
+    (Section 5)."""
+    F = deformation_gradients(x, tets, Dm_inv)
+    return float(np.sum(vol * (mu_prime * np.sum((F - Q) ** 2, axis=(1, 2))
+                               + mu * np.sum((F - R) ** 2, axis=(1, 2)))))
 
 
 def pd_energy(x, R, tets, Dm_inv, vol, mu, elems=None):
@@ -227,15 +250,19 @@ class OracleSolver:
     form because minimising over x_1 first leaves the reduced energy
     E~_alpha(x_2) the paper's inner loop descends (Eq. 12)."""
 
-    def __init__(self, X, tets, dirichlet, region, mu, density=0.0, dt=0.0):
+    def __init__(self, X, tets, dirichlet, region, mu, density=0.0, dt=0.0, mu_prime=0.0,
+                 sigma_min=0.0, sigma_max=np.inf):
         self.X = np.asarray(X, dtype=np.float64)
         self.tets = np.asarray(tets, dtype=np.int64)
         self.n = len(X)
         self.mu = float(mu)
         self.dt = float(dt)
+        # bi-phasic strain limiting (Section 5); mu_prime = 0 turns it off
+        self.mu_prime = float(mu_prime)
+        self.sigma = (float(sigma_min), float(sigma_max))
         self.Dm_inv, self.vol = element_precompute(self.X, self.tets)
         self.part = Partition(self.n, self.tets, dirichlet, region)
-        self.K = stiffness_matrix(self.tets, self.Dm_inv, self.vol, self.mu, self.n)
+        self.K = stiffness_matrix(self.tets, self.Dm_inv, self.vol, self.mu + self.mu_prime, self.n)
         self.mass = lumped_mass(self.tets, self.vol, density, self.n) if dt > 0 else None
         self.x = self.X.copy()
         self.v = np.zeros_like(self.X)
@@ -248,9 +275,17 @@ class OracleSolver:
         F = deformation_gradients(x, self.tets[elems], self.Dm_inv[elems])
         return polar_rotations(F)
 
-    def full_solve(self, x, R, contacts, y=None):
-        """Argmin over free x of E_hat(x; R) + E_col (+ inertia), Dirichlet fixed."""
+    def projections(self, x, elems):
+        """Q_e of the bi-phasic term (Section 5) for the given elements."""
+        F = deformation_gradients(x, self.tets[elems], self.Dm_inv[elems])
+        return strain_limit_projection(F, *self.sigma)
+
+    def full_solve(self, x, R, contacts, y=None, Q=None):
+        """Argmin over free x of E_hat(x; R) (or E_hat'(x; R, Q)) + E_col
+        (+ inertia), Dirichlet fixed."""
         b = projection_rhs(R, self.tets, self.Dm_inv, self.vol, self.mu, self.n)
+        if self.mu_prime > 0:
+            b = b + projection_rhs(Q, self.tets, self.Dm_inv, self.vol, self.mu_prime, self.n)
         C = Ct = None
         if contacts is not None and contacts.k > 0:
             C = contact_matrix(contacts, self.n)
@@ -277,22 +312,31 @@ class OracleSolver:
         x_n = self.x.copy()
         y = (x_n + self.dt * self.v) if self.mass is not None else None
         R = np.zeros((len(self.tets), 3, 3))
+        Q = np.zeros((len(self.tets), 3, 3)) if self.mu_prime > 0 else None
         for _ in range(outer_iters):
             R[p.alpha] = self.rotations(self.x, p.alpha)          # step 1
+            if Q is not None:
+                Q[p.alpha] = self.projections(self.x, p.alpha)
             virt = None
             for _ in range(inner_iters):
                 contacts = contacts_fn(self.x) if contacts_fn is not None else None   # 4.1
                 R[p.beta] = self.rotations(self.x, p.beta)        # 4.2
-                virt = self.full_solve(self.x, R, contacts, y)    # 4.3-4.5
+                if Q is not None:
+                    Q[p.beta] = self.projections(self.x, p.beta)
+                virt = self.full_solve(self.x, R, contacts, y, Q)  # 4.3-4.5
                 self.x[p.region] = virt[p.region]                 # 4.6
             self.x[p.x1] = virt[p.x1]                             # 5
         if self.mass is not None:
             self.v = (self.x - x_n) / self.dt
         return self.x
 
-    def energy(self, x, R, contacts=None, y=None):
-        """E_hat + E_col (+ inertia) at x for fixed R and contacts."""
-        e = pd_energy(x, R, self.tets, self.Dm_inv, self.vol, self.mu)
+    def energy(self, x, R, contacts=None, y=None, Q=None):
+        """E_hat (or E_hat' with Q) + E_col (+ inertia) at x for fixed R, Q
+        and contacts."""
+        if self.mu_prime > 0:
+            e = biphasic_energy(x, R, Q, self.tets, self.Dm_inv, self.vol, self.mu, self.mu_prime)
+        else:
+            e = pd_energy(x, R, self.tets, self.Dm_inv, self.vol, self.mu)
         if contacts is not None and contacts.k > 0:
             e += contact_energy(contacts, x)
         if self.mass is not None and y is not None:
