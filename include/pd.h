@@ -146,6 +146,27 @@ pd_status pd_set_contact_pairs(pd_solver* s, int64_t k, const int32_t* nodes /*[
                                const double* w /*[k][8]*/, const double* target /*[k][3]*/,
                                const double* stiffness /*[k]*/);
 
+/* Collision detection on the device (Algorithm 1, step 4.1, run at every
+ * inner iteration when pd_step gets no callback).  Each proxy (or side-A
+ * proxy) owns one spring slot; inactive proxies contribute nothing.
+ * Spheres: proxies [np] (node ids in x_2) inside a rigid sphere spheres[q] =
+ * {cx, cy, cz, r} get a zero-rest-length spring of stiffness `stiffness` to
+ * their projection on the deepest sphere's surface.
+ * Pairs: each side-A node within `gap` of its nearest side-B node gets a
+ * two-sided spring on x_a - x_b toward separation `gap` (self-collision).
+ * While a detector is set, pd_step without a callback re-detects at every
+ * inner iteration and so replaces springs given by pd_set_contacts; with a
+ * callback the callback's springs are used.  pd_clear_detector removes the
+ * detector and all springs.  The detector's arrays are copied; the caller
+ * keeps ownership of its buffers.
+ * Errors: INVALID_ARG (negative counts, null arrays, non-finite values,
+ * gap <= 0), CONTACT_OUTSIDE_REGION (a node not in x_2), CUDA. */
+pd_status pd_set_detector_spheres(pd_solver* s, const int32_t* proxies, int64_t np, int nsph,
+                                  const double* spheres /*[nsph][4]*/, double stiffness);
+pd_status pd_set_detector_pairs(pd_solver* s, const int32_t* side_a, int64_t na, const int32_t* side_b,
+                                int64_t nb, double gap, double stiffness);
+pd_status pd_clear_detector(pd_solver* s);
+
 /* One time step: outer_iters passes of Algorithm 1 (Section 3.4).  If cb is
  * not NULL it is called at every inner iteration before the local beta step;
  * otherwise the springs last set stay active.  Errors: NOT_SPD,

@@ -75,6 +75,14 @@ void symv3(const double* S, int64_t m, const double* v, double* out, cudaStream_
 // out[i][:] += alpha * sum_j B[i][j] v[j][:]  (CSC of a symmetric pattern)
 void spmv3(int64_t m, const int64_t* ptr, const int32_t* row, const double* val, const double* v,
            double alpha, double* out, cudaStream_t st);
+// Device collision detection (one spring slot per proxy / side-A proxy).
+// sph: [nsph][4] centre + radius.  Region indices for the proxies.
+void detect_spheres(int64_t np, const int32_t* prox_r, const int32_t* region, const double* x, int nsph,
+                    const double* sph, double stiffness, int32_t* cidx, double* cw, double* ct, double* cs,
+                    cudaStream_t st);
+void detect_pairs(int64_t na, const int32_t* ra, int64_t nb, const int32_t* rb, const int32_t* region,
+                  const double* x, double gap, double stiffness, int32_t* cidx, double* cw, double* ct, double* cs,
+                  cudaStream_t st);
 // Algorithm 1, 4.6-4.7: x2 += u2, U2 += u2, ft2 -= (Su - Bu)   (Bu already in Su: Su holds Sigma_alpha u)
 void inner_update(int64_t m, const double* u2, const double* Sau, const int32_t* region, double* x,
                   double* U2, double* ft2, cudaStream_t st);

@@ -356,6 +356,7 @@ void pd_destroy(pd_solver* s) {
   if (s->stream) cudaStreamSynchronize(s->stream);
   for (void* p : s->allocs) cudaFree(p);
   cudaFree(s->c_idx); cudaFree(s->c_w); cudaFree(s->c_t); cudaFree(s->c_s);
+  cudaFree(s->det_a); cudaFree(s->det_b); cudaFree(s->det_sph);
   if (s->x2_host) cudaFreeHost(s->x2_host);
   if (s->status_h) cudaFreeHost(s->status_h);
   pdm::mixed_free(s);
@@ -419,6 +420,83 @@ pd_status pd_schur_solve(pd_solver* s, const double* g, const double* u0, double
   if (r != PD_OK) return r;
   CK(cudaMemcpyAsync(u, s->u2, sizeof(double) * 3 * s->m, cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
+  return PD_OK;
+}
+
+static pd_status detector_buffers(pd_solver* s, int64_t nslots) {
+  if (nslots > s->kcap) {
+    constexpr int NS = pdk::CSLOTS;
+    int32_t* ni; double *nw, *nt, *nsf;
+    CK(cudaMalloc(&ni, sizeof(int32_t) * NS * nslots));
+    CK(cudaMalloc(&nw, sizeof(double) * NS * nslots));
+    CK(cudaMalloc(&nt, sizeof(double) * 3 * nslots));
+    CK(cudaMalloc(&nsf, sizeof(double) * nslots));
+    cudaFree(s->c_idx); cudaFree(s->c_w); cudaFree(s->c_t); cudaFree(s->c_s);
+    s->c_idx = ni; s->c_w = nw; s->c_t = nt; s->c_s = nsf;
+    s->kcap = nslots;
+  }
+  return PD_OK;
+}
+
+static pd_status region_list(pd_solver* s, const int32_t* nodes, int64_t n, int32_t** dev) {
+  std::vector<int32_t> r(n);
+  for (int64_t i = 0; i < n; ++i) {
+    if (nodes[i] < 0 || nodes[i] >= s->n || s->region_index[nodes[i]] < 0) {
+      s->err = "detector node " + std::to_string(nodes[i]) + " is not in the region";
+      return PD_ERR_CONTACT_OUTSIDE_REGION;
+    }
+    r[i] = s->region_index[nodes[i]];
+  }
+  cudaFree(*dev);
+  *dev = nullptr;
+  CK(cudaMalloc(dev, sizeof(int32_t) * std::max<int64_t>(n, 1)));
+  if (n) CK(cudaMemcpy(*dev, r.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+  return PD_OK;
+}
+
+pd_status pd_set_detector_spheres(pd_solver* s, const int32_t* proxies, int64_t np, int nsph, const double* spheres,
+                                  double stiffness) {
+  if (!s || np < 0 || nsph < 0 || (np > 0 && !proxies) || (nsph > 0 && !spheres) || !std::isfinite(stiffness))
+    return PD_ERR_INVALID_ARG;
+  for (int q = 0; q < 4 * nsph; ++q)
+    if (!std::isfinite(spheres[q])) { s->err = "non-finite sphere"; return PD_ERR_INVALID_ARG; }
+  pd_status r = region_list(s, proxies, np, &s->det_a);
+  if (r != PD_OK) return r;
+  r = detector_buffers(s, np);
+  if (r != PD_OK) return r;
+  cudaFree(s->det_sph);
+  s->det_sph = nullptr;
+  CK(cudaMalloc(&s->det_sph, sizeof(double) * 4 * std::max(nsph, 1)));
+  if (nsph) CK(cudaMemcpy(s->det_sph, spheres, sizeof(double) * 4 * nsph, cudaMemcpyHostToDevice));
+  s->nsph = nsph;
+  s->det_n = np;
+  s->det_stiffness = stiffness;
+  s->detector = 1;
+  return PD_OK;
+}
+
+pd_status pd_set_detector_pairs(pd_solver* s, const int32_t* side_a, int64_t na, const int32_t* side_b, int64_t nb,
+                                double gap, double stiffness) {
+  if (!s || na < 0 || nb < 0 || (na > 0 && !side_a) || (nb > 0 && !side_b) || !(gap > 0) || !std::isfinite(stiffness))
+    return PD_ERR_INVALID_ARG;
+  pd_status r = region_list(s, side_a, na, &s->det_a);
+  if (r != PD_OK) return r;
+  r = region_list(s, side_b, nb, &s->det_b);
+  if (r != PD_OK) return r;
+  r = detector_buffers(s, na);
+  if (r != PD_OK) return r;
+  s->det_n = na;
+  s->det_nb = nb;
+  s->det_gap = gap;
+  s->det_stiffness = stiffness;
+  s->detector = 2;
+  return PD_OK;
+}
+
+pd_status pd_clear_detector(pd_solver* s) {
+  if (!s) return PD_ERR_INVALID_ARG;
+  s->detector = 0;
+  s->k = 0;
   return PD_OK;
 }
 
@@ -664,7 +742,17 @@ pd_status pd_solver::step(int outer_iters, pd_contact_cb cb, void* user) {
     double* ft2 = b + 3 * n1;
     CK(cudaMemsetAsync(U2, 0, sizeof(double) * 3 * m, stream));
     for (int j = 0; j < opt.inner_iters; ++j) {
-      // 4.1 detection (host callback)
+      // 4.1 detection: on the device, or through the host callback
+      if (!cb && detector) {
+        tbegin(3);
+        if (detector == 1)
+          pdk::detect_spheres(det_n, det_a, d_region, x, nsph, det_sph, det_stiffness, c_idx, c_w, c_t, c_s, stream);
+        else
+          pdk::detect_pairs(det_n, det_a, det_nb, det_b, d_region, x, det_gap, det_stiffness, c_idx, c_w, c_t, c_s,
+                            stream);
+        tend();
+        k = det_n;
+      }
       if (cb) {
         pdk::gather_rows(m, d_region, x, x2_dev, stream);
         CK(cudaMemcpyAsync(x2_host, x2_dev, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, stream));

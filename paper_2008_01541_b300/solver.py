@@ -94,6 +94,20 @@ class Solver:
         fn = lib.pd_set_contact_pairs if slots == 8 else lib.pd_set_contacts
         self._check(fn(self.h, k, _ptr(nodes), _ptr(w), _ptr(target), _ptr(stiffness)))
 
+    def set_detector_spheres(self, proxies, spheres, stiffness):
+        proxies = _c(proxies, np.int32)
+        spheres = _c(spheres, np.float64).reshape(-1, 4)
+        self._check(lib.pd_set_detector_spheres(self.h, _ptr(proxies), len(proxies), len(spheres), _ptr(spheres),
+                                                float(stiffness)))
+
+    def set_detector_pairs(self, side_a, side_b, gap, stiffness):
+        a = _c(side_a, np.int32)
+        b = _c(side_b, np.int32)
+        self._check(lib.pd_set_detector_pairs(self.h, _ptr(a), len(a), _ptr(b), len(b), float(gap), float(stiffness)))
+
+    def clear_detector(self):
+        self._check(lib.pd_clear_detector(self.h))
+
     def step(self, outer_iters, contacts_fn=None):
         """contacts_fn(x2 [m,3] numpy) -> (nodes, w, target, stiffness) or None."""
         if contacts_fn is None:

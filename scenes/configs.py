@@ -281,7 +281,9 @@ def elbow(h=0.585, seed=0, region_fraction=0.05, inner_iters=1, contact_mode="se
     return Scene("elbow", X, tets, dirichlet, region, proxies, mu=1e4, lam=0.0,
                  density=1000.0, dt=0.0, outer_iters=10, inner_iters=inner_iters, steps=60,
                  stiffness=stiffness, dirichlet_positions=dirichlet_positions,
-                 contacts=contacts, info={"h": h, "theta": theta, "rest_step": 45, "self_pairs": self_pairs})
+                 contacts=contacts,
+                 info={"h": h, "theta": theta, "rest_step": 45, "self_pairs": self_pairs,
+                       "pair_sides": (all_a, all_b)})
 
 
 def small_elbow(h=2.0, seed=0, region_fraction=0.05, inner_iters=1):
