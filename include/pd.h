@@ -60,6 +60,14 @@ typedef struct {
     double mu;        /* Lame mu of the PD energy mu ||F - R||_F^2 (Eq. 2)       */
     double lambda;    /* accepted and ignored: the method sets lambda = 0 (Sec 2.2) */
     double density;   /* used for the lumped mass when dt > 0                    */
+    /* Bi-phasic strain limiting (Section 5): the energy density gains
+     * mu_prime * min_{Q in S} ||F - Q||_F^2, S = the matrices whose singular
+     * values lie in [sigma_min, sigma_max] (the paper's open set, taken with
+     * its closure).  mu_prime = 0 (zero-initialised struct) turns it off;
+     * otherwise 0 <= sigma_min <= sigma_max (sigma_max may be +inf).  The
+     * system matrix then carries mu + mu_prime for every element.           */
+    double mu_prime;
+    double sigma_min, sigma_max;
 } pd_material;
 
 typedef struct {
@@ -201,7 +209,8 @@ void pd_destroy(pd_solver* s);
 
 /* Local step on all elements (Section 2.2): for each tet e, R_e = polar(F_e)
  * in SO(3) with F_e = Ds Dm^-1 at positions x [n][3] (host), and the elastic
- * forces f = -dE_hat/dx, f_e = -Vol_e 2 mu (F_e - R_e) G_e^T, summed per node.
+ * forces f = -dE_hat/dx, f_e = -Vol_e 2 mu (F_e - R_e) G_e^T, summed per node;
+ * with strain limiting f_e gains -Vol_e 2 mu' (F_e - Q_e) G_e^T (Section 5).
  *   R_out : [n_tets][3][3] row-major (host), may be NULL
  *   f_out : [n][3] (host), may be NULL; Dirichlet nodes receive their sums too */
 pd_status pd_local_step(pd_solver* s, const double* x, double* R_out, double* f_out);

@@ -13,7 +13,7 @@ struct Input {
   int64_t n = 0, E = 0;
   const double* X = nullptr;      // [n][3]
   const int32_t* tets = nullptr;  // [E][4]
-  double mu = 0, density = 0, dt = 0;
+  double mu = 0, mu_prime = 0, density = 0, dt = 0;   // mu_prime: bi-phasic term (Section 5)
   const int32_t* region = nullptr;
   int64_t m = 0;
   const int32_t* dirichlet = nullptr;

@@ -69,11 +69,11 @@ __device__ bool polar_newton(const double* F, double* R) {
 // R = [u1 u2 u1 x u2] [v1 v2 v1 x v2]^T with u_i = F v_i / sigma_i.  Used for
 // inverted, degenerate or badly conditioned F, where the smallest singular
 // direction is the one that gets flipped.
-__device__ void polar_jacobi(const double* F, double* R) {
-  double S[3][3], V[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+// Cyclic Jacobi eigen-decomposition of a symmetric 3x3 matrix in place:
+// on return S is diagonal (the eigenvalues) and S_in = V S_out V^T.
+__device__ void jacobi_eig3(double S[3][3], double V[3][3]) {
   for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j)
-      S[i][j] = F[0 * 3 + i] * F[0 * 3 + j] + F[1 * 3 + i] * F[1 * 3 + j] + F[2 * 3 + i] * F[2 * 3 + j];
+    for (int j = 0; j < 3; ++j) V[i][j] = i == j ? 1.0 : 0.0;
   for (int sweep = 0; sweep < 30; ++sweep) {
     double off = S[0][1] * S[0][1] + S[0][2] * S[0][2] + S[1][2] * S[1][2];
     double dia = S[0][0] * S[0][0] + S[1][1] * S[1][1] + S[2][2] * S[2][2];
@@ -102,6 +102,14 @@ __device__ void polar_jacobi(const double* F, double* R) {
       }
     }
   }
+}
+
+__device__ void polar_jacobi(const double* F, double* R) {
+  double S[3][3], V[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      S[i][j] = F[0 * 3 + i] * F[0 * 3 + j] + F[1 * 3 + i] * F[1 * 3 + j] + F[2 * 3 + i] * F[2 * 3 + j];
+  jacobi_eig3(S, V);
   // sort eigenvalues descending
   int o[3] = {0, 1, 2};
   double lam[3] = {S[0][0], S[1][1], S[2][2]};
@@ -139,10 +147,47 @@ __device__ void polar_jacobi(const double* F, double* R) {
     for (int j = 0; j < 3; ++j) R[3 * i + j] = u1[i] * v1[j] + u2[i] * v2[j] + u3[i] * v3[j];
 }
 
+// Bi-phasic strain limiting (Section 5): with F = R S the polar split and
+// S = V diag(lambda) V^T (signed: an inverted F has one negative lambda, its
+// singular values are |lambda|), the closest matrix with singular values in
+// [lo, hi] is Q = R V diag(sign(lambda) clamp(|lambda|)) V^T.  Returns
+// D = F - Q = -R V diag(c - lambda) V^T, which is exactly zero when every
+// singular value is inside the bounds.
+__device__ void strain_limit_residual(const double* F, const double* R, double lo, double hi, double* D) {
+  double S[3][3], V[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      const double a = R[i] * F[j] + R[3 + i] * F[3 + j] + R[6 + i] * F[6 + j];   // (R^T F)_ij
+      const double b = R[j] * F[i] + R[3 + j] * F[3 + i] + R[6 + j] * F[6 + i];   // (R^T F)_ji
+      S[i][j] = 0.5 * (a + b);
+    }
+  jacobi_eig3(S, V);
+  double dl[3];
+  bool any = false;
+  for (int q = 0; q < 3; ++q) {
+    const double l = S[q][q], al = fabs(l), c = fmin(fmax(al, lo), hi);
+    dl[q] = (l < 0.0 ? -c : c) - l;
+    any |= dl[q] != 0.0;
+  }
+  if (!any) {
+    for (int i = 0; i < 9; ++i) D[i] = 0.0;
+    return;
+  }
+  double M[3][3];   // V diag(dl) V^T
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) M[i][j] = V[i][0] * dl[0] * V[j][0] + V[i][1] * dl[1] * V[j][1] + V[i][2] * dl[2] * V[j][2];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) D[3 * i + j] = -(R[3 * i] * M[0][j] + R[3 * i + 1] * M[1][j] + R[3 * i + 2] * M[2][j]);
+}
+
+// Elemental forces f_e = -Vol_e G_e-weighted (2 mu (F - R) + 2 mu' (F - Q));
+// w = 2 (mu + mu') Vol and frac = mu' / (mu + mu') (frac = 0 without the
+// bi-phasic term, SL = false compiles it out).
+template <bool SL>
 __global__ void k_polar_forces(int64_t count, const int4* __restrict__ tets,
                                const double* __restrict__ Dm, const double* __restrict__ w,
                                const double* __restrict__ x, double* __restrict__ fe,
-                               double* __restrict__ Rout) {
+                               double* __restrict__ Rout, double frac, double lo, double hi) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= count) return;
   int4 t = tets[e];
@@ -165,10 +210,19 @@ __global__ void k_polar_forces(int64_t count, const int4* __restrict__ tets,
   double R[9];
   if (!polar_newton(F, R)) polar_jacobi(F, R);
   double we = __ldg(w + e);
+  double P[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) P[i] = F[i] - R[i];
+  if (SL) {
+    double D[9];
+    strain_limit_residual(F, R, lo, hi, D);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) P[i] = (1.0 - frac) * P[i] + frac * D[i];
+  }
   double f[4][3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    double P0 = F[3 * i] - R[3 * i], P1 = F[3 * i + 1] - R[3 * i + 1], P2 = F[3 * i + 2] - R[3 * i + 2];
+    double P0 = P[3 * i], P1 = P[3 * i + 1], P2 = P[3 * i + 2];
 #pragma unroll
     for (int a = 1; a < 4; ++a)
       f[a][i] = -we * (P0 * Mi[3 * (a - 1)] + P1 * Mi[3 * (a - 1) + 1] + P2 * Mi[3 * (a - 1) + 2]);
@@ -253,9 +307,12 @@ inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 }  // namespace
 
 void polar_forces(int64_t count, const int4* tets, const double* Dm, const double* w, const double* x,
-                  double* fe, double* R_out, cudaStream_t st) {
+                  double* fe, double* R_out, cudaStream_t st, const StrainLimit* sl) {
   if (count <= 0) return;
-  k_polar_forces<<<nblk(count, 128), 128, 0, st>>>(count, tets, Dm, w, x, fe, R_out);
+  if (sl && sl->frac > 0.0)
+    k_polar_forces<true><<<nblk(count, 128), 128, 0, st>>>(count, tets, Dm, w, x, fe, R_out, sl->frac, sl->lo, sl->hi);
+  else
+    k_polar_forces<false><<<nblk(count, 128), 128, 0, st>>>(count, tets, Dm, w, x, fe, R_out, 0.0, 0.0, 0.0);
   ++g_launches;
 }
 

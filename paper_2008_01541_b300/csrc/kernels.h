@@ -10,11 +10,18 @@ namespace pdk {
 extern int64_t g_launches;
 
 // ---- local step (Section 2.2) -------------------------------------------
+// Bi-phasic strain limiting (Section 5): frac = mu' / (mu + mu'), singular
+// value bounds [lo, hi].
+struct StrainLimit {
+  double frac = 0.0, lo = 0.0, hi = 0.0;
+};
+
 // For each element e of a set: F = Ds Dm^-1, R = polar(F) in SO(3),
-// fe[e][a][:] = forces on its four vertices, f_a = -w_e (F - R) G_a^T
-// (w_e = 2 mu Vol_e).  R_out (optional) receives R row-major [count][9].
+// fe[e][a][:] = forces on its four vertices, f_a = -w_e (F - T) G_a^T with
+// T = R, or with strain limiting T = (1 - frac) R + frac Q
+// (w_e = 2 (mu + mu') Vol_e).  R_out (optional) receives R row-major [count][9].
 void polar_forces(int64_t count, const int4* tets, const double* DminvSoA, const double* w,
-                  const double* x, double* fe, double* R_out, cudaStream_t st);
+                  const double* x, double* fe, double* R_out, cudaStream_t st, const StrainLimit* sl = nullptr);
 
 // out[t][:] = sum over the slots of target t of fe[slot][:]  (+ inertia if
 // mass_h2 != null and t < inertia_limit: - mass_h2[t] (x[node(t)] - y[t]))

@@ -64,7 +64,7 @@ static pd_status build_elemset(pd_solver* s, const pdh::Setup& h, const int32_t*
     int32_t e = elems[i];
     t[i] = make_int4(tets[4 * e], tets[4 * e + 1], tets[4 * e + 2], tets[4 * e + 3]);
     for (int q = 0; q < 9; ++q) Dm[q * c + i] = h.Dminv[9 * (int64_t)e + q];
-    w[i] = 2.0 * s->mu * h.vol[e];
+    w[i] = 2.0 * (s->mu + s->mu_prime) * h.vol[e];
   }
   CK(dupload(s, &es.tets, t.data(), c));
   CK(dupload(s, &es.Dm, Dm.data(), 9 * c));
@@ -199,9 +199,22 @@ pd_status pd_setup(const pd_mesh* mesh, const pd_material* mat, double dt, const
   }
   s->precision = s->opt.precision;
   s->mu = mat->mu; s->density = mat->density; s->dt = dt;
+  if (!(mat->mu_prime >= 0) || !std::isfinite(mat->mu_prime) ||
+      (mat->mu_prime > 0 && (!(mat->sigma_min >= 0) || !(mat->sigma_max >= mat->sigma_min) ||
+                             !std::isfinite(mat->sigma_min)))) {
+    g_setup_error = "strain limit needs mu_prime >= 0 and 0 <= sigma_min <= sigma_max";
+    delete s;
+    return PD_ERR_INVALID_ARG;
+  }
+  s->mu_prime = mat->mu_prime;
+  if (mat->mu_prime > 0) {
+    s->sl.frac = mat->mu_prime / (mat->mu + mat->mu_prime);
+    s->sl.lo = mat->sigma_min;
+    s->sl.hi = mat->sigma_max;
+  }
   pdh::Input in;
   in.n = mesh->n_nodes; in.E = mesh->n_tets; in.X = mesh->rest_pos; in.tets = mesh->tets;
-  in.mu = mat->mu; in.density = mat->density; in.dt = dt;
+  in.mu = mat->mu; in.mu_prime = mat->mu_prime; in.density = mat->density; in.dt = dt;
   in.region = region; in.m = m; in.dirichlet = dirichlet; in.nd = nd;
   pdh::Setup h;
   std::string err;
@@ -378,7 +391,7 @@ pd_status pd_local_step(pd_solver* s, const double* x, double* R_out, double* f_
   CK(cudaMalloc(&fd, sizeof(double) * 3 * s->n));
   if (R_out) CK(cudaMalloc(&Rd, sizeof(double) * 9 * s->E));
   CK(cudaMemcpyAsync(xd, x, sizeof(double) * 3 * s->n, cudaMemcpyHostToDevice, s->stream));
-  pdk::polar_forces(s->all.count, s->all.tets, s->all.Dm, s->all.w, xd, s->all.fe, Rd, s->stream);
+  pdk::polar_forces(s->all.count, s->all.tets, s->all.Dm, s->all.w, xd, s->all.fe, Rd, s->stream, &s->sl);
   pdk::gather_forces(s->n, s->all.gptr, s->all.gslot, s->all.fe, fd, nullptr, nullptr, nullptr, nullptr,
                      nullptr, 0, s->stream);
   CK(cudaGetLastError());
@@ -731,7 +744,7 @@ pd_status pd_solver::step(int outer_iters, pd_contact_cb cb, void* user) {
   for (int it = 0; it < outer_iters && result == PD_OK; ++it) {
     // 1-2: R_alpha and the alpha forces f_1, f_2^(alpha) (+ x_1 inertia)
     tbegin(0);
-    pdk::polar_forces(alpha.count, alpha.tets, alpha.Dm, alpha.w, x, alpha.fe, nullptr, stream);
+    pdk::polar_forces(alpha.count, alpha.tets, alpha.Dm, alpha.w, x, alpha.fe, nullptr, stream, &sl);
     pdk::gather_forces(nfree, alpha.gptr, alpha.gslot, alpha.fe, b, nullptr, mass_h2, x, y_in,
                        d_node_of_pos, n1, stream);
     tend();
@@ -766,7 +779,7 @@ pd_status pd_solver::step(int outer_iters, pd_contact_cb cb, void* user) {
       }
       // 4.2, 4.4: R_beta, g = f~_2 + f_2^(beta) (+ x_2 inertia) + f_2^(col)
       tbegin(3);
-      pdk::polar_forces(beta.count, beta.tets, beta.Dm, beta.w, x, beta.fe, nullptr, stream);
+      pdk::polar_forces(beta.count, beta.tets, beta.Dm, beta.w, x, beta.fe, nullptr, stream, &sl);
       pdk::gather_forces(m, beta.gptr, beta.gslot, beta.fe, g, ft2, mass_h2 ? mass_h2 + n1 : nullptr, x,
                          y_in ? y_in + 3 * n1 : nullptr, d_region, m, stream);
       pdk::contact_forces(k, c_idx, c_w, c_t, c_s, d_region, x, g, stream);
