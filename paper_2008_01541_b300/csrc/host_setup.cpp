@@ -523,8 +523,8 @@ int build(const Input& in, Setup& s, std::string* err) {
       while (j + 1 < n1 && parent[j] == j + 1) {
         int64_t zeros = cnt[j + 1] + 1 - cnt[j];
         int64_t width = j - j0 + 1;
-        bool fundamental = zeros == 0 && width < 512;
-        bool relaxed = zeros <= 2 + cnt[j] / 8 && width < 32;
+        bool fundamental = zeros == 0 && width < 1024;
+        bool relaxed = zeros <= 4 + cnt[j] / 4 && width < 256;
         if (!(fundamental || relaxed)) break;
         ++j;
       }

@@ -286,62 +286,103 @@ __global__ void __launch_bounds__(512) k_gram(const float* __restrict__ Dinv, fl
   }
 }
 
-// Panel solve for the 64-row slab blockIdx.x below tile kt: L_ik = A_ik Dinv_k^T,
-// and the pre-multiplied copy Lh_ik = L_ik Dinv_k used by the preconditioner.
-__global__ void __launch_bounds__(256) k_trsm_f32(float* __restrict__ L, float* __restrict__ Lh, int64_t mq, int kt,
-                                                  const float* __restrict__ Dinv, __nv_bfloat16* __restrict__ Pb) {
-  extern __shared__ float sm[];
-  float* As = sm;               // [64][PADW]
-  float* Ds = sm + 64 * PADW;   // [128][PADW]
-  const int tid = threadIdx.x;
-  const int64_t r0 = (int64_t)(kt + 1) * NB + (int64_t)blockIdx.x * 64;
+// Panel solve for the 32-row slab blockIdx.x below tile kt: L_ik = A_ik Dinv_k^T
+// and Lh_ik = L_ik Dinv_k.  128 threads, 4 x 8 outputs each; operands are held
+// k-major in shared memory so every inner step is three 16-byte loads.
+constexpr int RB = 32, AP = RB + 4, DP = NB + 4;
+__global__ void __launch_bounds__(128) k_trsm_f32(float* __restrict__ L, float* __restrict__ Lh, int64_t mq, int kt,
+                                               const float* __restrict__ Dinv, __nv_bfloat16* __restrict__ Pb) {
+  extern __shared__ float4 sm4[];
+  float* AT = reinterpret_cast<float*>(sm4);   // [NB][AP]  A^T, later L^T
+  float* DT = AT + NB * AP;                     // [NB][DP]  Dinv^T, later Dinv
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int64_t r0 = (int64_t)(kt + 1) * NB + (int64_t)blockIdx.x * RB;
   float* Ab = L + r0 * mq + (int64_t)kt * NB;
   float* Hb = Lh + r0 * mq + (int64_t)kt * NB;
   const float* Di = Dinv + (int64_t)kt * NB * NB;
-  for (int q = tid; q < 64 * NB; q += 256) As[(q / NB) * PADW + q % NB] = Ab[(int64_t)(q / NB) * mq + q % NB];
-  for (int q = tid; q < NB * NB; q += 256) Ds[(q / NB) * PADW + q % NB] = Di[q];
-  __syncthreads();
-  const int tr = tid % 16, tc = tid / 16;
-  float acc[4][8] = {};
-  for (int t = 0; t < NB; ++t) {
-    float a[4], b[8];
+  {
+    float4 va[8];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) a[i] = As[(tr + 16 * i) * PADW + t];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) b[j] = Ds[(tc + 16 * j) * PADW + t];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-  }
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      int rr = tr + 16 * i, cc = tc + 16 * j;
-      Ab[(int64_t)rr * mq + cc] = acc[i][j];
-      As[rr * PADW + cc] = acc[i][j];
-      if (Pb) Pb[(r0 + rr) * NB + cc] = __float2bfloat16_rn(acc[i][j]);
+    for (int k = 0; k < 8; ++k) {   // A slab: 32 rows x 32 float4
+      const int q = tid + 128 * k, r = q >> 5, c = 4 * (q & 31);
+      va[k] = __ldcg(reinterpret_cast<const float4*>(Ab + (int64_t)r * mq + c));
     }
-  __syncthreads();
-  float h[4][8] = {};
-  for (int t = 0; t < NB; ++t) {
-    float a[4], b[8];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) a[i] = As[(tr + 16 * i) * PADW + t];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) b[j] = Ds[t * PADW + tc + 16 * j];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 8; ++j) h[i][j] = fmaf(a[i], b[j], h[i][j]);
+    for (int k = 0; k < 8; ++k) {
+      const int q = tid + 128 * k, r = q >> 5, c = 4 * (q & 31);
+      AT[(c + 0) * AP + r] = va[k].x; AT[(c + 1) * AP + r] = va[k].y; AT[(c + 2) * AP + r] = va[k].z; AT[(c + 3) * AP + r] = va[k].w;
+    }
+#pragma unroll 4
+    for (int k = 0; k < 32; ++k) {  // Dinv: 128 rows x 32 float4, stored transposed
+      const int q = tid + 128 * k, r = q >> 5, c = 4 * (q & 31);
+      const float4 v = __ldcg(reinterpret_cast<const float4*>(Di + r * NB + c));
+      DT[(c + 0) * DP + r] = v.x; DT[(c + 1) * DP + r] = v.y; DT[(c + 2) * DP + r] = v.z; DT[(c + 3) * DP + r] = v.w;
+    }
   }
+  __syncthreads();
+  float acc[4][8];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) Hb[(int64_t)(tr + 16 * i) * mq + tc + 16 * j] = h[i][j];
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+#pragma unroll 4
+  for (int t = 0; t < NB; ++t) {
+    const float4 a = *reinterpret_cast<const float4*>(AT + t * AP + 4 * ty);
+    const float4 b0 = *reinterpret_cast<const float4*>(DT + t * DP + 8 * tx);
+    const float4 b1 = *reinterpret_cast<const float4*>(DT + t * DP + 8 * tx + 4);
+    const float av[4] = {a.x, a.y, a.z, a.w}, bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+  }
+  __syncthreads();
+  // L to global (and its BF16 copy), L^T into AT; Dinv (row-major) into DT
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int rr = 4 * ty + i;
+    float* dst = Ab + (int64_t)rr * mq + 8 * tx;
+    *reinterpret_cast<float4*>(dst) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+    *reinterpret_cast<float4*>(dst + 4) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+    if (Pb) {
+      __nv_bfloat16 hb[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) hb[j] = __float2bfloat16_rn(acc[i][j]);
+      *reinterpret_cast<uint4*>(Pb + (r0 + rr) * NB + 8 * tx) = *reinterpret_cast<const uint4*>(hb);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    *reinterpret_cast<float4*>(AT + (8 * tx + j) * AP + 4 * ty) = make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
+#pragma unroll 4
+  for (int k = 0; k < 32; ++k) {
+    const int q = tid + 128 * k, r = q >> 5, c = 4 * (q & 31);
+    *reinterpret_cast<float4*>(DT + r * DP + c) = __ldcg(reinterpret_cast<const float4*>(Di + r * NB + c));
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+#pragma unroll 4
+  for (int t = 0; t < NB; ++t) {
+    const float4 a = *reinterpret_cast<const float4*>(AT + t * AP + 4 * ty);
+    const float4 b0 = *reinterpret_cast<const float4*>(DT + t * DP + 8 * tx);
+    const float4 b1 = *reinterpret_cast<const float4*>(DT + t * DP + 8 * tx + 4);
+    const float av[4] = {a.x, a.y, a.z, a.w}, bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float* dst = Hb + (int64_t)(4 * ty + i) * mq + 8 * tx;
+    *reinterpret_cast<float4*>(dst) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+    *reinterpret_cast<float4*>(dst + 4) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+  }
 }
+
 
 // z = D L^-T L^-1 D r for 3 right-hand sides in one cooperative launch.
 // With Lh_ik = L_ik Dinv_k and E_k = Dinv_k^T Dinv_k the block substitutions
@@ -627,7 +668,7 @@ static pd_status ensure_state(pd_solver* s) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_diag_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (2 * NB * PADW + 3 * 32 * 33) * 4);
-    cudaFuncSetAttribute(k_trsm_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (64 + NB) * PADW * 4);
+    cudaFuncSetAttribute(k_trsm_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (NB * AP + NB * DP) * 4);
     cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, NB * PADW * 4);
     attr = true;
   }
@@ -665,7 +706,7 @@ static void factor_panels(pd_solver* s, Factor& f, pdtc::Mode mode) {
     const int n = (int)(T - kt - 1);
     if (n <= 0) break;
     __nv_bfloat16* pb = mode == pdtc::BF16 ? f.Pb[kt & 1] : nullptr;
-    k_trsm_f32<<<(unsigned)(2 * n), 256, (64 + NB) * PADW * 4, st>>>(f.L, f.Lh, mq, kt, f.Dinv, pb);
+    k_trsm_f32<<<(unsigned)(n * (NB / RB)), 128, (NB * AP + NB * DP) * 4, st>>>(f.L, f.Lh, mq, kt, f.Dinv, pb);
     ++pdk::g_launches;
     cudaEventRecord(M->ev_panel[kt], st);
     if (kt > 0) cudaStreamWaitEvent(st, M->ev_rest[kt - 1], 0);

@@ -38,12 +38,22 @@ struct SparseFactor {
   const int32_t* rows = nullptr;
   const int64_t* valptr = nullptr;   // [nsn+1]
   const double* L = nullptr;
-  // per-level 64 x 64 tile tasks {supernode, row offset, col offset, 0}
-  const int64_t* lvl_diag_ptr = nullptr;  // host [nlevels+1] into diag_tasks
-  const int64_t* lvl_off_ptr = nullptr;   // host [nlevels+1] into off_tasks
-  const int4* diag_tasks = nullptr;       // device: tiles of the diagonal blocks (col <= row tile)
-  const int4* off_tasks = nullptr;        // device: tiles of the off-diagonal blocks
+  // Tasks {s | kind << 29, row offset, col offset, target-list index} in
+  // forward / backward topological order; kind 0 = 64 x 64 tile of a
+  // diagonal block, 1 = tile of an off-diagonal block, 2 = a whole small
+  // supernode.
+  int64_t n_ftasks = 0, n_btasks = 0;
+  const int4* ftasks = nullptr;
+  const int4* btasks = nullptr;
+  const int64_t* tgt_ptr = nullptr;       // target lists: distinct supernodes owning a task's off-diagonal rows
+  const int32_t* tgt = nullptr;
+  int* cnt = nullptr;                     // counters, reset from cnt_init before each solve
+  const int* cnt_init = nullptr;
+  int64_t cnt_fin = 0, cnt_ydone = 0, cnt_next_f = 0, cnt_zpend = 0, cnt_udone = 0, cnt_next_b = 0;
+  int grid = 0;
+  int* status = nullptr;                  // status[1] <- 300 if a wait gave up
 };
+int sparse_grid();
 // b [nfree][3] in: forces (factor order).  Out: y[0..n1) = L_1^-1 b_1 and
 // b[n1..nfree) = b_2 - L_21 y_1.
 void sparse_forward(const SparseFactor& f, double* b, double* y, cudaStream_t st);

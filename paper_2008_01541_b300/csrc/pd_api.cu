@@ -653,27 +653,92 @@ pd_status pd_solver::upload(const pdh::Setup& h, const pdh::Input& in) {
     int64_t nl = h.nlevels;
     std::vector<std::vector<int32_t>> bylevel(nl);
     for (int64_t k2 = 0; k2 < h.nsn; ++k2) bylevel[h.sn_level[k2]].push_back((int32_t)k2);
-    std::vector<int4> dt, ot;
-    lvl_diag_ptr.assign(nl + 1, 0);
-    lvl_off_ptr.assign(nl + 1, 0);
-    for (int64_t l = 0; l < nl; ++l) {
-      for (int32_t sn : bylevel[l]) {
-        int32_t nc = h.sn_col0[sn + 1] - h.sn_col0[sn];
-        int32_t nr = (int32_t)(h.sn_rowptr[sn + 1] - h.sn_rowptr[sn]);
-        for (int32_t rb = 0; rb < nc; rb += 64)
-          for (int32_t cb = 0; cb <= rb; cb += 64) dt.push_back(make_int4(sn, rb, cb, 0));
-        for (int32_t rb = 0; rb < nr; rb += 64)
-          for (int32_t cb = 0; cb < nc; cb += 64) ot.push_back(make_int4(sn, rb, cb, 0));
+    // dependency-counter task lists (Section 3.2 substitutions without level
+    // barriers): a supernode of at most 64 columns and 128 off-diagonal rows
+    // is one fused task (its diagonal block and all its rows); larger ones
+    // are split into 64 x 64 tile tasks that run in parallel.
+    {
+      const int64_t nsn = h.nsn;
+      std::vector<int32_t> col2sn(n1, -1);
+      for (int64_t k2 = 0; k2 < nsn; ++k2)
+        for (int32_t c = h.sn_col0[k2]; c < h.sn_col0[k2 + 1]; ++c) col2sn[c] = (int32_t)k2;
+      std::vector<int64_t> tptr(1, 0);
+      std::vector<int32_t> tg;
+      std::vector<int> init(4 * nsn + 2, 0);
+      const int64_t FIN = 0, YD = nsn, NF = 2 * nsn, ZP = 2 * nsn + 1, UD = 3 * nsn + 1, NB2 = 4 * nsn + 1;
+      auto ncol = [&](int32_t sn) { return h.sn_col0[sn + 1] - h.sn_col0[sn]; };
+      auto nrow = [&](int32_t sn) { return (int32_t)(h.sn_rowptr[sn + 1] - h.sn_rowptr[sn]); };
+      // distinct supernodes owning rows [r0, r1) of sn's off-diagonal block
+      // (each of the `mult` tasks sharing the list signals every target once)
+      auto targets = [&](int32_t sn, int32_t r0, int32_t r1, int mult) {
+        int32_t last = -1;
+        for (int32_t r = r0; r < r1; ++r) {
+          const int32_t row = h.rows[h.sn_rowptr[sn] + r];
+          if (row >= n1) break;                 // rows ascend; x_2 rows need no signal
+          const int32_t a = col2sn[row];
+          if (a != last) { tg.push_back(a); init[FIN + a] += mult; last = a; }
+        }
+        tptr.push_back((int64_t)tg.size());
+        return (int)(tptr.size() - 2);
+      };
+      constexpr int KD = 0, KO = 1 << 29, KF = 2 << 29;
+      std::vector<int4> fd, fo, ff;   // per level: diag tiles, off tiles, fused
+      std::vector<int4> ft, bt;
+      for (int64_t l = 0; l < nl; ++l) {
+        fd.clear(); fo.clear(); ff.clear();
+        for (int32_t sn : bylevel[l]) {
+          const int32_t nc = ncol(sn), nr = nrow(sn);
+          if (nc <= 64 && nr <= 128) {
+            ff.push_back(make_int4(sn | KF, 0, 0, targets(sn, 0, nr, 1)));
+            init[UD + sn] = 1;
+            continue;
+          }
+          for (int32_t rb = 0; rb < nc; rb += 64)
+            for (int32_t cb = 0; cb <= rb; cb += 64) {
+              fd.push_back(make_int4(sn | KD, rb, cb, 0));
+              init[YD + sn]++; init[UD + sn]++;
+            }
+          for (int32_t rb = 0; rb < nr; rb += 64) {
+            const int ti = targets(sn, rb, std::min(nr, rb + 64), (nc + 63) / 64);
+            for (int32_t cb = 0; cb < nc; cb += 64) {
+              fo.push_back(make_int4(sn | KO, rb, cb, ti));
+              init[ZP + sn]++;
+            }
+          }
+        }
+        ft.insert(ft.end(), fd.begin(), fd.end());
+        ft.insert(ft.end(), ff.begin(), ff.end());
+        ft.insert(ft.end(), fo.begin(), fo.end());
       }
-      lvl_diag_ptr[l + 1] = (int64_t)dt.size();
-      lvl_off_ptr[l + 1] = (int64_t)ot.size();
+      // backward: the same tasks, levels descending; off tiles, fused, diag tiles
+      {
+        std::vector<std::vector<int4>> lo(nl), lf(nl), ld(nl);
+        for (const int4& t : ft) {
+          const int32_t sn = t.x & 0x1fffffff, kind = t.x & (3 << 29);
+          const int32_t l = h.sn_level[sn];
+          (kind == KO ? lo : kind == KF ? lf : ld)[l].push_back(t);
+        }
+        for (int64_t l = nl - 1; l >= 0; --l) {
+          bt.insert(bt.end(), lo[l].begin(), lo[l].end());
+          bt.insert(bt.end(), lf[l].begin(), lf[l].end());
+          bt.insert(bt.end(), ld[l].begin(), ld[l].end());
+        }
+      }
+      init[NF] = 0; init[NB2] = 0;
+      CK(dupload(s, &sf_ftasks, ft.data(), ft.size()));
+      CK(dupload(s, &sf_btasks, bt.data(), bt.size()));
+      CK(dupload(s, &sf_tptr, tptr.data(), tptr.size()));
+      CK(dupload(s, &sf_tgt, tg.data(), std::max<size_t>(tg.size(), 1)));
+      CK(dupload(s, &sf_cnt_init, init.data(), init.size()));
+      CK(dupload(s, &sf_cnt, init.data(), init.size()));
+      sf.n_ftasks = (int64_t)ft.size(); sf.n_btasks = (int64_t)bt.size();
+      sf.ftasks = sf_ftasks; sf.btasks = sf_btasks; sf.tgt_ptr = sf_tptr; sf.tgt = sf_tgt;
+      sf.cnt = sf_cnt; sf.cnt_init = sf_cnt_init;
+      sf.cnt_fin = FIN; sf.cnt_ydone = YD; sf.cnt_next_f = NF; sf.cnt_zpend = ZP; sf.cnt_udone = UD; sf.cnt_next_b = NB2;
+      sf.grid = pdk::sparse_grid();
     }
-    CK(dupload(s, &diag_tasks, dt.data(), dt.size()));
-    CK(dupload(s, &off_tasks, ot.data(), ot.size()));
     sf.n1 = n1; sf.nfree = nfree; sf.nsn = h.nsn; sf.nlevels = nl;
     sf.col0 = sn_col0; sf.rowptr = sn_rowptr; sf.rows = rows; sf.valptr = sn_valptr; sf.L = Lval;
-    sf.lvl_diag_ptr = lvl_diag_ptr.data(); sf.lvl_off_ptr = lvl_off_ptr.data();
-    sf.diag_tasks = diag_tasks; sf.off_tasks = off_tasks;
   }
   CK(dalloc(s, &b, 3 * nfree));
   CK(dalloc(s, &yv, 3 * nfree));
@@ -707,6 +772,7 @@ pd_status pd_solver::upload(const pdh::Setup& h, const pdh::Input& in) {
   X_rest_h.assign(in.X, in.X + 3 * n);
   CK(dalloc(s, &work, 6 * mp));
   CK(dalloc(s, &status, 4));
+  sf.status = status;
   CK(cudaMemset(status, 0, sizeof(int) * 4));
   CK(cudaMallocHost(&status_h, sizeof(int) * 4));
   CK(cudaMallocHost(&x2_host, sizeof(double) * 3 * m));

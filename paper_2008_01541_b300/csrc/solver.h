@@ -53,8 +53,10 @@ struct pd_solver {
   int32_t* rows = nullptr;
   int64_t* sn_valptr = nullptr;
   double* Lval = nullptr;
-  std::vector<int64_t> lvl_diag_ptr, lvl_off_ptr;
-  int4 *diag_tasks = nullptr, *off_tasks = nullptr;
+  int4 *sf_ftasks = nullptr, *sf_btasks = nullptr;
+  int64_t* sf_tptr = nullptr;
+  int32_t* sf_tgt = nullptr;
+  int *sf_cnt = nullptr, *sf_cnt_init = nullptr;
   pdk::SparseFactor sf;
   double *b = nullptr, *yv = nullptr, *u = nullptr, *z = nullptr;
   // collision-region block
