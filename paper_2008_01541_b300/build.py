@@ -13,7 +13,7 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU = ["k_local.cu", "k_sparse.cu", "k_dense.cu", "k_mixed.cu", "pd_api.cu", "k_noalloc.cu", "k_tc.cu", "k_mlp.cu", "k_detect.cu"]
 CPP = ["host_setup.cpp", "pd_host.cpp"]
-HEADERS = ["kernels.h", "host_setup.h", "solver.h", "mixed.h", "tc.h", "tc_dev.cuh", "mlp.h", "grid_sync.cuh"]
+HEADERS = ["kernels.h", "host_setup.h", "solver.h", "mixed.h", "tc.h", "tc_dev.cuh", "mlp.h"]
 
 
 def _newer(target, deps):

@@ -8,9 +8,9 @@
 // the split-TF32 factor, and refinement accelerated by preconditioned CG for
 // TF32 and BF16.  PD_PCG_WARM runs PCG on H with the contact-free factor of
 // Sigma_0 (computed once) as the preconditioner, started from a given guess.
-#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -19,10 +19,8 @@
 #include "mixed.h"
 #include "solver.h"
 #include "tc.h"
-#include "grid_sync.cuh"
 
 namespace pdm {
-using pdk::grid_barrier;
 
 constexpr int NB = 128;      // tile of the low-precision factor
 constexpr int PADW = NB + 1; // padded shared-memory row
@@ -50,10 +48,10 @@ struct MixedState {
   double* sc = nullptr;       // device scalars: [0] r.r  [1] r.z  [2] p.q  [3] r.z old  [4] g.g
   double* sc_h = nullptr;     // pinned copy
   float *w = nullptr, *uo = nullptr;   // [mq][3] triangular-solve vectors
-  unsigned* bar = nullptr;    // grid-barrier counter
+  int* pcnt = nullptr;        // preconditioner task counters [1 + 2T]
+  int pc_grid = 0;            // persistent grid of the preconditioner
   cudaStream_t side = nullptr;              // low-priority stream for the bulk trailing updates
   std::vector<cudaEvent_t> ev_panel, ev_rest;
-  int coop_grid = 0;
 };
 
 namespace {
@@ -384,78 +382,159 @@ __global__ void __launch_bounds__(128) k_trsm_f32(float* __restrict__ L, float* 
 }
 
 
-// z = D L^-T L^-1 D r for 3 right-hand sides in one cooperative launch.
-// With Lh_ik = L_ik Dinv_k and E_k = Dinv_k^T Dinv_k the block substitutions
-// need no dense diagonal solve inside the sequential loops:
-//   forward : w_i -= Lh_ik w_k for i > k            (k ascending)
-//   middle  : u_k = E_k w_k                          (all k at once)
-//   backward: u_k -= sum_{i > k} Lh_ik^T u_i         (k descending)
+// z = D L^-T L^-1 D r for 3 right-hand sides.  With Lh_ik = L_ik Dinv_k and
+// E_k = Dinv_k^T Dinv_k the block substitutions need no dense diagonal solve:
+//   forward : w_i = D r_i - sum_{k < i} Lh_ik w_k
+//   backward: u_k = E_k w_k - sum_{i > k} Lh_ik^T u_i
+// Tasks are 32-row slices of a block row (forward, i ascending) and 32-column
+// slices of a block column (backward, k descending), claimed in that order
+// from an atomic counter by a persistent grid.  A task waits, per block it
+// needs, for the four slices of that block to be done (counters cnt[1 + k]
+// forward, cnt[1 + T + k] backward); every wait is on an earlier task, so the
+// grid cannot stall, and every wait is bounded (code 301 in status[1]).
+constexpr int PS = 32;                 // rows / columns per task
+constexpr int NSL = NB / PS;           // slices per block
+
+__device__ __forceinline__ unsigned long long ptimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void wait_at_least(const int* c, int target, int* status, unsigned long long t0) {
+  unsigned it = 0;
+  while (*(volatile const int*)c < target) {
+    if (*(volatile int*)(status + 1) != 0) return;
+    if (++it > 32) __nanosleep(64);
+    if ((it & 1023u) == 0 && ptimer() - t0 > 1000000000ull) {
+      atomicCAS(status + 1, 0, 301);
+      return;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256) k_precond(const float* __restrict__ Lh, const float* __restrict__ E,
                                                  int64_t mq, int64_t m, const double* __restrict__ d,
                                                  const double* __restrict__ r, double* __restrict__ z, float* w,
-                                                 float* uo, unsigned* bar, int* status) {
+                                                 float* uo, int* cnt, int* status) {
   __shared__ float vk[NB * 3];
-  __shared__ float part[2][NB * 3];
-  const int T = (int)(mq / NB);
-  const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
-  unsigned nb = 0;
-  for (int64_t i = (int64_t)b * 256 + tid; i < mq; i += (int64_t)G * 256)
-    for (int v = 0; v < 3; ++v) w[3 * i + v] = i < m ? (float)(d[i] * r[3 * i + v]) : 0.f;
-  if (!grid_barrier(bar, (unsigned)G * ++nb, status)) return;
-  for (int k = 0; k + 1 < T; ++k) {
-    for (int q = tid; q < NB * 3; q += 256) vk[q] = w[3 * (int64_t)k * NB + q];
+  __shared__ float red[8][PS][3];
+  __shared__ int cur;
+  const int T = (int)(mq / NB), ntask = 2 * T * NSL, tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) cur = atomicAdd(cnt, 1);
     __syncthreads();
-    const int64_t lo = (int64_t)(k + 1) * NB, n = mq - lo;
-    const int64_t per = (n + G - 1) / G;
-    for (int64_t i = lo + b * per + tid; i < lo + (b + 1) * per && i < mq; i += 256) {
-      const float* Li = Lh + i * mq + (int64_t)k * NB;
+    const int t = cur;
+    if (t >= ntask) break;
+    if (t < T * NSL) {
+      // ---- forward slice: rows R0 .. R0 + 31 of block row i
+      const int i = t / NSL;
+      const int64_t R0 = (int64_t)i * NB + (int64_t)(t % NSL) * PS;
+      const int rr = tid >> 3, cc = tid & 7;           // row, 16-column chunk
+      const float* Lrow = Lh + (R0 + rr) * mq + cc * 16;
       float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-#pragma unroll 4
-      for (int c = 0; c < NB; c += 4) {
-        float4 l4 = *reinterpret_cast<const float4*>(Li + c);
-        a0 = fmaf(l4.x, vk[3 * c], a0); a1 = fmaf(l4.x, vk[3 * c + 1], a1); a2 = fmaf(l4.x, vk[3 * c + 2], a2);
-        a0 = fmaf(l4.y, vk[3 * c + 3], a0); a1 = fmaf(l4.y, vk[3 * c + 4], a1); a2 = fmaf(l4.y, vk[3 * c + 5], a2);
-        a0 = fmaf(l4.z, vk[3 * c + 6], a0); a1 = fmaf(l4.z, vk[3 * c + 7], a1); a2 = fmaf(l4.z, vk[3 * c + 8], a2);
-        a0 = fmaf(l4.w, vk[3 * c + 9], a0); a1 = fmaf(l4.w, vk[3 * c + 10], a1); a2 = fmaf(l4.w, vk[3 * c + 11], a2);
+      for (int k = 0; k < i; ++k) {
+        float4 l[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) l[q] = __ldg(reinterpret_cast<const float4*>(Lrow + (int64_t)k * NB) + q);
+        if (tid == 0) {
+          wait_at_least(cnt + 1 + k, NSL, status, ptimer());
+          __threadfence();
+        }
+        __syncthreads();
+        for (int q = tid; q < NB * 3; q += 256) vk[q] = __ldcg(w + 3 * (int64_t)k * NB + q);
+        __syncthreads();
+        const float* v = vk + 3 * cc * 16;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float lv[4] = {l[q].x, l[q].y, l[q].z, l[q].w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int c = 4 * q + e;
+            a0 = fmaf(lv[e], v[3 * c], a0); a1 = fmaf(lv[e], v[3 * c + 1], a1); a2 = fmaf(lv[e], v[3 * c + 2], a2);
+          }
+        }
       }
-      w[3 * i] -= a0; w[3 * i + 1] -= a1; w[3 * i + 2] -= a2;
-    }
-    if (!grid_barrier(bar, (unsigned)G * ++nb, status)) return;
-  }
-  for (int k = b; k < T; k += G) {
-    const float* Ek = E + (int64_t)k * NB * NB;
-    for (int q = tid; q < NB * 3; q += 256) vk[q] = w[3 * (int64_t)k * NB + q];
-    __syncthreads();
-    for (int q = tid; q < NB * 3; q += 256) {
-      const int rr = q / 3, v = q % 3;
-      float s = 0.f;
-      for (int c = 0; c < NB; ++c) s = fmaf(Ek[rr * NB + c], vk[3 * c + v], s);
-      uo[3 * (int64_t)k * NB + q] = s;
-    }
-    __syncthreads();
-  }
-  if (!grid_barrier(bar, (unsigned)G * ++nb, status)) return;
-  for (int k = T - 2; k >= 0; --k) {
-    const int64_t lo = (int64_t)(k + 1) * NB, n = mq - lo;
-    const int64_t per = (n + G - 1) / G;
-    const int c = tid % NB, half = tid / NB;
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-    for (int64_t i = lo + b * per + half; i < lo + (b + 1) * per && i < mq; i += 2) {
-      const float l = Lh[i * mq + (int64_t)k * NB + c];
-      a0 = fmaf(l, uo[3 * i], a0); a1 = fmaf(l, uo[3 * i + 1], a1); a2 = fmaf(l, uo[3 * i + 2], a2);
-    }
-    part[half][3 * c] = a0; part[half][3 * c + 1] = a1; part[half][3 * c + 2] = a2;
-    __syncthreads();
-    if (tid < NB * 3 / 2 * 2 && tid < NB) {
-      for (int v = 0; v < 3; ++v) {
-        const float t = part[0][3 * tid + v] + part[1][3 * tid + v];
-        if (t != 0.f) atomicAdd(uo + 3 * ((int64_t)k * NB + tid) + v, -t);
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
       }
+      if (cc == 0) {
+        const int64_t row = R0 + rr;
+        float* wr = w + 3 * row;
+        if (row < m) {
+          const double dr = d[row];
+          wr[0] = (float)(dr * r[3 * row]) - a0;
+          wr[1] = (float)(dr * r[3 * row + 1]) - a1;
+          wr[2] = (float)(dr * r[3 * row + 2]) - a2;
+        } else {
+          wr[0] = -a0; wr[1] = -a1; wr[2] = -a2;
+        }
+        __threadfence();
+      }
+      __syncthreads();
+      if (tid == 0) atomicAdd(cnt + 1 + i, 1);
+    } else {
+      // ---- backward slice: columns C0 .. C0 + 31 of block column k
+      const int tb = t - T * NSL, k = T - 1 - tb / NSL, sl = tb % NSL;
+      const int64_t C0 = (int64_t)k * NB + (int64_t)sl * PS;
+      const int cc = tid & 31, rc = tid >> 5;          // column, 16-row chunk
+      float e[16];
+      const float* Ek = E + (int64_t)k * NB * NB + (int64_t)(rc * 16) * NB + sl * PS + cc;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) e[q] = __ldg(Ek + (int64_t)q * NB);   // E_k symmetric: row c = column c
+      if (tid == 0) {
+        wait_at_least(cnt + 1 + k, NSL, status, ptimer());
+        __threadfence();
+      }
+      __syncthreads();
+      for (int q = tid; q < NB * 3; q += 256) vk[q] = __ldcg(w + 3 * (int64_t)k * NB + q);
+      __syncthreads();
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const float* v = vk + 3 * (rc * 16 + q);
+        a0 = fmaf(e[q], v[0], a0); a1 = fmaf(e[q], v[1], a1); a2 = fmaf(e[q], v[2], a2);
+      }
+      for (int i = T - 1; i > k; --i) {
+        float l[16];
+        const float* Lc = Lh + ((int64_t)i * NB + rc * 16) * mq + C0 + cc;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) l[q] = __ldg(Lc + (int64_t)q * mq);
+        if (tid == 0) {
+          wait_at_least(cnt + 1 + T + i, NSL, status, ptimer());
+          __threadfence();
+        }
+        __syncthreads();
+        for (int q = tid; q < NB * 3; q += 256) vk[q] = __ldcg(uo + 3 * (int64_t)i * NB + q);
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const float* v = vk + 3 * (rc * 16 + q);
+          a0 = fmaf(-l[q], v[0], a0); a1 = fmaf(-l[q], v[1], a1); a2 = fmaf(-l[q], v[2], a2);
+        }
+      }
+      red[rc][cc][0] = a0; red[rc][cc][1] = a1; red[rc][cc][2] = a2;
+      __syncthreads();
+      if (tid < PS) {
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) { s0 += red[q][tid][0]; s1 += red[q][tid][1]; s2 += red[q][tid][2]; }
+        const int64_t col = C0 + tid;
+        float* uc = uo + 3 * col;
+        uc[0] = s0; uc[1] = s1; uc[2] = s2;
+        if (col < m) {
+          const double dc = d[col];
+          z[3 * col] = dc * (double)s0; z[3 * col + 1] = dc * (double)s1; z[3 * col + 2] = dc * (double)s2;
+        }
+        __threadfence();
+      }
+      __syncthreads();
+      if (tid == 0) atomicAdd(cnt + 1 + T + k, 1);
     }
-    if (!grid_barrier(bar, (unsigned)G * ++nb, status)) return;
   }
-  for (int64_t i = (int64_t)b * 256 + tid; i < m; i += (int64_t)G * 256)
-    for (int v = 0; v < 3; ++v) z[3 * i + v] = d[i] * (double)uo[3 * i + v];
 }
 
 // z = Minv0 r (FP32 dense symmetric inverse, 3 right-hand sides), one warp per row.
@@ -640,7 +719,7 @@ static pd_status ensure_state(pd_solver* s) {
       A((void**)&M->uo, sizeof(float) * 3 * mq) || A((void**)&M->Shi, sizeof(float) * m * m) ||
       A((void**)&M->Slo, sizeof(float) * m * m) || A((void**)&M->vhi, sizeof(float) * 3 * m) ||
       A((void**)&M->vlo, sizeof(float) * 3 * m) || A((void**)&M->r32, sizeof(float) * 3 * m) ||
-      A((void**)&M->bar, sizeof(unsigned) * 4)) {
+      A((void**)&M->pcnt, sizeof(int) * (1 + 2 * M->T))) {
     s->err = "device allocation for the mixed-precision vectors failed";
     return PD_ERR_OOM;
   }
@@ -660,11 +739,7 @@ static pd_status ensure_state(pd_solver* s) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_precond, 256, 0);
-  M->coop_grid = nsm * (per > 0 ? 1 : 0);
-  if (M->coop_grid <= 0) {
-    s->err = "cooperative triangular-solve kernel cannot be resident";
-    return PD_ERR_CUDA;
-  }
+  M->pc_grid = std::max(1, nsm * std::max(1, per));
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_diag_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (2 * NB * PADW + 3 * 32 * 33) * 4);
@@ -725,18 +800,13 @@ static void factor_panels(pd_solver* s, Factor& f, pdtc::Mode mode) {
 
 static cudaError_t precond(pd_solver* s, const Factor& f, const double* r, double* z) {
   MixedState* M = s->mixed;
-  cudaMemsetAsync(M->bar, 0, sizeof(unsigned), s->stream);
-  const float* Lh = f.Lh;
-  const float* E = f.E;
-  int64_t mq = M->mq, m = s->m;
-  const double* d = f.d;
-  float *w = M->w, *uo = M->uo;
-  unsigned* bar = M->bar;
-  int* status = s->status;
-  void* args[] = {(void*)&Lh, (void*)&E, (void*)&mq, (void*)&m, (void*)&d, (void*)&r, (void*)&z,
-                  (void*)&w, (void*)&uo, (void*)&bar, (void*)&status};
+  const int64_t T = M->T;
+  cudaMemsetAsync(M->pcnt, 0, sizeof(int) * (1 + 2 * T), s->stream);
+  const int ntask = (int)(2 * T * NSL);
+  k_precond<<<(unsigned)std::min(ntask, M->pc_grid), 256, 0, s->stream>>>(f.Lh, f.E, M->mq, s->m, f.d, r, z, M->w, M->uo,
+                                                                         M->pcnt, s->status);
   ++pdk::g_launches;
-  return cudaLaunchCooperativeKernel((void*)k_precond, dim3(M->coop_grid), dim3(256), args, 0, s->stream);
+  return cudaGetLastError();
 }
 
 // Explicit inverse of the contact-free factor, built once from m/3 solves with
@@ -882,7 +952,7 @@ pd_status mixed_solve(pd_solver* s, const double* g, const double* u0, double* u
   s->last_refine = it;
   s->last_residual = std::sqrt(rr / (gg > 0 ? gg : 1.0));
   if (ce != cudaSuccess) {
-    s->err = std::string("cooperative launch failed: ") + cudaGetErrorString(ce);
+    s->err = std::string("preconditioner launch failed: ") + cudaGetErrorString(ce);
     return PD_ERR_CUDA;
   }
   if (!ok) {
