@@ -109,31 +109,44 @@ __global__ void k_contact_scatter_f32(int64_t k, const int32_t* cidx, const doub
 }
 
 // One warp factors the 32 x 32 block at Ap (row stride PADW) in registers
-// (lane i holds row i) and writes L back to Ap.
+// (lane i holds row i) and writes L back to Ap.  Each scaled column goes
+// through shared memory once and is read back with 16-byte broadcasts; a
+// non-positive pivot is replaced by 1 and reported in *status (first bad
+// column + 1, offset by code0).
 __device__ __noinline__ void warp_chol32(float* Ap, int* status, int code0) {
   const int lane = threadIdx.x & 31;
   float a[32];
 #pragma unroll
   for (int c = 0; c < 32; ++c) a[c] = Ap[lane * PADW + c];
+  __shared__ __align__(16) float col[32];
+  unsigned bad = 0;
 #pragma unroll
   for (int j = 0; j < 32; ++j) {
     float djj = __shfl_sync(0xffffffffu, a[j], j);
-    if (!(djj > 0.f) || !isfinite(djj)) {
-      if (lane == 0) atomicCAS(status, 0, code0 + j + 1);
-      djj = 1.f;
-    }
-    const float rs = rsqrtf(djj);        // hardware reciprocal square root (MUFU)
+    const bool b = !(djj > 0.f) || !isfinite(djj);
+    bad |= (unsigned)b << j;
+    djj = b ? 1.f : djj;
+    const float rs = rsqrtf(djj);
     if (lane == j) a[j] = djj * rs;
     if (lane > j) a[j] *= rs;
+    col[lane] = a[j];
+    __syncwarp();
+    const float4* c4 = reinterpret_cast<const float4*>(col);
 #pragma unroll
-    for (int c = j + 1; c < 32; ++c) {
-      const float lcj = __shfl_sync(0xffffffffu, a[j], c);
-      if (lane >= c) a[c] = fmaf(-a[j], lcj, a[c]);
+    for (int q = (j + 1) / 4; q < 8; ++q) {
+      const float4 v = c4[q];
+      const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int c = 4 * q + e;
+        if (c > j && lane >= c) a[c] = fmaf(-a[j], vv[e], a[c]);
+      }
     }
+    __syncwarp();
   }
+  if (bad && lane == 0) atomicCAS(status, 0, code0 + __ffs(bad));
 #pragma unroll
-  for (int c = 0; c < 32; ++c)
-    if (c <= lane) Ap[lane * PADW + c] = a[c];
+  for (int c = 0; c < 32; ++c) if (c <= lane) Ap[lane * PADW + c] = a[c];
 }
 
 // One warp inverts the lower-triangular 32 x 32 block at Ap into Zp.
@@ -159,61 +172,97 @@ __device__ __noinline__ void warp_inv32(const float* Ap, float* Zp) {
   for (int c = 0; c < 32; ++c) Zp[lane * PADW + c] = z[c];
 }
 
-// Factor the diagonal tile (kt, kt) in FP32 and invert it.  Blocked in shared memory with 32-wide sub-blocks: warp 0
-// factors and inverts each 32 x 32 diagonal sub-block, all warps solve the
-// sub-panel below it and update the trailing sub-matrix; the off-diagonal
-// blocks of the inverse follow by block forward substitution.
+// Up to three 32 x 32 block products O_w = sg_w X_w Y_w (acc: O_w += ...), all
+// blocks with leading dimension PADW; threads [t0, t0 + nthr) take 2 x 2
+// outputs each.
+__device__ __forceinline__ void blk_prods(int np, int acc, int t0, int nthr,
+                                          const float* X0, const float* Y0, float* O0, float g0,
+                                          const float* X1 = nullptr, const float* Y1 = nullptr, float* O1 = nullptr,
+                                          float g1 = 0.f, const float* X2 = nullptr, const float* Y2 = nullptr,
+                                          float* O2 = nullptr, float g2 = 0.f) {
+  const int me = threadIdx.x - t0;
+  if (me < 0 || me >= nthr) return;
+  for (int q = me; q < np * 256; q += nthr) {
+    const int w = q >> 8;
+    const float* X = w == 0 ? X0 : (w == 1 ? X1 : X2);
+    const float* Y = w == 0 ? Y0 : (w == 1 ? Y1 : Y2);
+    float* O = w == 0 ? O0 : (w == 1 ? O1 : O2);
+    const float g = w == 0 ? g0 : (w == 1 ? g1 : g2);
+    const int r = 2 * ((q & 255) >> 4), c = 2 * (q & 15);
+    float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f;
+#pragma unroll 8
+    for (int t = 0; t < 32; ++t) {
+      const float x0 = X[r * PADW + t], x1 = X[(r + 1) * PADW + t];
+      const float y0 = Y[t * PADW + c], y1 = Y[t * PADW + c + 1];
+      s00 = fmaf(x0, y0, s00); s01 = fmaf(x0, y1, s01); s10 = fmaf(x1, y0, s10); s11 = fmaf(x1, y1, s11);
+    }
+    float* o = O + r * PADW + c;
+    if (acc) {
+      o[0] += g * s00; o[1] += g * s01; o[PADW] += g * s10; o[PADW + 1] += g * s11;
+    } else {
+      o[0] = g * s00; o[1] = g * s01; o[PADW] = g * s10; o[PADW + 1] = g * s11;
+    }
+  }
+}
+
+// Factor the diagonal tile (kt, kt) in FP32 and invert it (L_kk and
+// Dinv_k = L_kk^-1), blocked in shared memory with 32-wide sub-blocks and a
+// look-ahead inside the tile: while warp 0 factors sub-block p, warps 1-6
+// apply the rest of panel p-1's trailing update and warp 7 inverts
+// sub-block p-1.  The panel below sub-block p is solved one thread per row;
+// the off-diagonal blocks of the inverse, Z_ij = -Z_ii sum_t L_it Z_tj, are
+// formed in the phases where threads are idle, their partial sums S_ij kept
+// in the unused blocks above the diagonal of Z.
 __global__ void __launch_bounds__(256) k_diag_f32(float* __restrict__ L, int64_t mq, int kt,
                                                   float* __restrict__ Dinv, int* __restrict__ status) {
   extern __shared__ float sm[];
   float* A = sm;                   // [128][PADW]
   float* Z = sm + NB * PADW;       // [128][PADW] inverse
-  float* S = sm + 2 * NB * PADW;   // [3][32][33] scratch
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5;
+#define LB(i, j) (A + (32 * (i)) * PADW + 32 * (j))
+#define ZB(i, j) (Z + (32 * (i)) * PADW + 32 * (j))
+// the six S_ij live in the (zero, unused) blocks above the diagonal of Z
+#define SB(k) ((k) == 0 ? ZB(0, 1) : (k) == 1 ? ZB(0, 2) : (k) == 2 ? ZB(0, 3) : (k) == 3 ? ZB(1, 2) : (k) == 4 ? ZB(1, 3) : ZB(2, 3))
   float* Lt = L + (int64_t)kt * NB * mq + (int64_t)kt * NB;
-  for (int q = tid; q < NB * NB / 4; q += 256) {
-    const int r = q / (NB / 4), c = 4 * (q % (NB / 4));
-    const float4 v = *reinterpret_cast<const float4*>(Lt + (int64_t)r * mq + c);
-    A[r * PADW + c] = v.x; A[r * PADW + c + 1] = v.y; A[r * PADW + c + 2] = v.z; A[r * PADW + c + 3] = v.w;
-    Z[r * PADW + c] = 0.f; Z[r * PADW + c + 1] = 0.f; Z[r * PADW + c + 2] = 0.f; Z[r * PADW + c + 3] = 0.f;
+  {
+    float4 v[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int q = tid + 256 * k, r = q >> 5, c = 4 * (q & 31);
+      v[k] = __ldcg(reinterpret_cast<const float4*>(Lt + (int64_t)r * mq + c));
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int q = tid + 256 * k, r = q >> 5, c = 4 * (q & 31);
+      A[r * PADW + c] = v[k].x; A[r * PADW + c + 1] = v[k].y; A[r * PADW + c + 2] = v[k].z; A[r * PADW + c + 3] = v[k].w;
+      Z[r * PADW + c] = 0.f; Z[r * PADW + c + 1] = 0.f; Z[r * PADW + c + 2] = 0.f; Z[r * PADW + c + 3] = 0.f;
+    }
   }
   __syncthreads();
 #pragma unroll 1
-  for (int p = 0; p < 4; ++p) {
+  for (int p = 0; p <= 4; ++p) {
     const int c0 = 32 * p;
-    float* Ap = A + c0 * PADW + c0;
-    float* Zp = Z + c0 * PADW + c0;
-    if (warp == 0) warp_chol32(Ap, status, kt * NB + c0);
-    __syncthreads();
-    // sub-panel below: row r solves x L_D^T = A[r, c0:c0+32] by substitution (one thread per row)
-    const int nbelow = NB - c0 - 32;
-    if (tid < nbelow) {
-      float* row = A + (c0 + 32 + tid) * PADW + c0;
-      float x[32];
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        float acc = row[j];
-#pragma unroll
-        for (int t = 0; t < j; ++t) acc = fmaf(-x[t], Ap[j * PADW + t], acc);
-        x[j] = acc * __frcp_rn(Ap[j * PADW + j]);
-      }
-#pragma unroll
-      for (int j = 0; j < 32; ++j) row[j] = x[j];
-    }
-    __syncthreads();
-    // trailing update of the lower part below and right of the sub-panel,
-    // 2 x 2 outputs per thread (blocks on or below the diagonal)
-    {
-      const int nb2 = nbelow / 2;
-      for (int q = tid; q < nb2 * nb2; q += 256) {
-        const int bi = q / nb2, bj = q % nb2;
-        if (bj > bi) continue;
-        const int r = c0 + 32 + 2 * bi, c = c0 + 32 + 2 * bj;
+    // ---- phase 1: factor block p | rest of panel p-1's update | invert block p-1
+    if (warp == 0) {
+      if (p < 4) warp_chol32(A + c0 * PADW + c0, status, kt * NB + c0);
+    } else if (warp == 7) {
+      if (p > 0) warp_inv32(A + (c0 - 32) * PADW + (c0 - 32), Z + (c0 - 32) * PADW + (c0 - 32));
+    } else if (p == 3) {
+      // S20 += L21 Z10, S30 += L31 Z10 (warps 1-6; no trailing rows are left)
+      blk_prods(2, 1, 32, 192, LB(2, 1), ZB(1, 0), SB(0), 1.f, LB(3, 1), ZB(1, 0), SB(1), 1.f);
+    } else if (p > 0 && p < 4) {
+      // rows >= c0 + 32, columns c0 .. row (sub-block p itself was updated in phase 3)
+      const int pc = c0 - 32;                      // panel columns pc .. pc + 31
+      const int nbr = (NB - c0 - 32) / 2, nbc = (NB - c0) / 2;
+      for (int q = tid - 32; q < nbr * nbc; q += 192) {
+        const int bi = q / nbc, bj = q % nbc;
+        const int r = c0 + 32 + 2 * bi, c = c0 + 2 * bj;
+        if (c > r) continue;
         float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f;
 #pragma unroll 8
         for (int t = 0; t < 32; ++t) {
-          const float a0 = A[r * PADW + c0 + t], a1 = A[(r + 1) * PADW + c0 + t];
-          const float b0 = A[c * PADW + c0 + t], b1 = A[(c + 1) * PADW + c0 + t];
+          const float a0 = A[r * PADW + pc + t], a1 = A[(r + 1) * PADW + pc + t];
+          const float b0 = A[c * PADW + pc + t], b1 = A[(c + 1) * PADW + pc + t];
           s00 = fmaf(a0, b0, s00); s01 = fmaf(a0, b1, s01); s10 = fmaf(a1, b0, s10); s11 = fmaf(a1, b1, s11);
         }
         A[r * PADW + c] -= s00;
@@ -223,50 +272,83 @@ __global__ void __launch_bounds__(256) k_diag_f32(float* __restrict__ L, int64_t
       }
     }
     __syncthreads();
+    if (p == 4) break;
+    // ---- phase 2: panel below block p by substitution (one thread per row)
+    float* Ap = A + c0 * PADW + c0;
+    const int nbelow = NB - c0 - 32;
+    if (tid < nbelow) {
+      // right-looking: x_j is final after its own scaling, then eliminated
+      // from the later entries (independent FMAs instead of a dot-product chain)
+      float* row = A + (c0 + 32 + tid) * PADW + c0;
+      float x[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) x[j] = row[j];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        x[j] *= __frcp_rn(Ap[j * PADW + j]);
+#pragma unroll
+        for (int t = j + 1; t < 32; ++t) x[t] = fmaf(-x[j], Ap[t * PADW + j], x[t]);
+      }
+#pragma unroll
+      for (int j = 0; j < 32; ++j) row[j] = x[j];
+    }
+    // blocks of the inverse whose inputs are ready, on the threads the panel leaves idle
+    if (p == 1) {
+      blk_prods(3, 0, 64, 192, LB(1, 0), ZB(0, 0), SB(2), 1.f, LB(2, 0), ZB(0, 0), SB(0), 1.f, LB(3, 0), ZB(0, 0),
+                SB(1), 1.f);
+    } else if (p == 2) {
+      blk_prods(3, 0, 32, 224, ZB(1, 1), SB(2), ZB(1, 0), -1.f, LB(2, 1), ZB(1, 1), SB(3), 1.f, LB(3, 1), ZB(1, 1),
+                SB(4), 1.f);
+    } else if (p == 3) {
+      blk_prods(3, 0, 0, 256, ZB(2, 2), SB(0), ZB(2, 0), -1.f, ZB(2, 2), SB(3), ZB(2, 1), -1.f, LB(3, 2), ZB(2, 2),
+                SB(5), 1.f);
+    }
+    __syncthreads();
+    // ---- phase 3: update of the next diagonal block with panel p
+    if (p == 3) {
+      // S30 += L32 Z20, S31 += L32 Z21
+      blk_prods(2, 1, 0, 256, LB(3, 2), ZB(2, 0), SB(1), 1.f, LB(3, 2), ZB(2, 1), SB(4), 1.f);
+      __syncthreads();
+    }
+    if (p < 3) {
+      const int b0 = c0 + 32;
+      for (int q = tid; q < 16 * 16; q += 256) {
+        const int bi = q / 16, bj = q % 16;
+        if (bj > bi) continue;
+        const int r = b0 + 2 * bi, c = b0 + 2 * bj;
+        float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f;
+#pragma unroll 8
+        for (int t = 0; t < 32; ++t) {
+          const float a0 = A[r * PADW + c0 + t], a1 = A[(r + 1) * PADW + c0 + t];
+          const float e0 = A[c * PADW + c0 + t], e1 = A[(c + 1) * PADW + c0 + t];
+          s00 = fmaf(a0, e0, s00); s01 = fmaf(a0, e1, s01); s10 = fmaf(a1, e0, s10); s11 = fmaf(a1, e1, s11);
+        }
+        A[r * PADW + c] -= s00;
+        A[(r + 1) * PADW + c] -= s10;
+        A[(r + 1) * PADW + c + 1] -= s11;
+        if (c + 1 <= r) A[r * PADW + c + 1] -= s01;
+      }
+      __syncthreads();
+    }
   }
-  if (warp < 4) warp_inv32(A + 32 * warp * PADW + 32 * warp, Z + 32 * warp * PADW + 32 * warp);
+  {
+    // Z3j = -Z33 S3j
+    blk_prods(3, 0, 0, 256, ZB(3, 3), SB(1), ZB(3, 0), -1.f, ZB(3, 3), SB(4), ZB(3, 1), -1.f, ZB(3, 3), SB(5),
+              ZB(3, 2), -1.f);
+  }
   __syncthreads();
-  // off-diagonal 32 x 32 blocks of the inverse: Z_ij = -Z_ii sum_{t=j}^{i-1} L_it Z_tj,
-  // 2 x 2 outputs per thread
-  for (int d = 1; d < 4; ++d) {
-    const int npairs = 4 - d;
-    for (int q = tid; q < npairs * 256; q += 256) {
-      const int pr = q / 256, r = 2 * ((q % 256) / 16), c = 2 * (q % 16);
-      const int j = pr, i = pr + d;
-      float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f;
-      for (int t = 32 * j; t < 32 * i; ++t) {
-        const float a0 = A[(32 * i + r) * PADW + t], a1 = A[(32 * i + r + 1) * PADW + t];
-        const float b0 = Z[t * PADW + 32 * j + c], b1 = Z[t * PADW + 32 * j + c + 1];
-        s00 = fmaf(a0, b0, s00); s01 = fmaf(a0, b1, s01); s10 = fmaf(a1, b0, s10); s11 = fmaf(a1, b1, s11);
-      }
-      float* Sp = S + pr * 32 * 33;
-      Sp[r * 33 + c] = s00; Sp[r * 33 + c + 1] = s01; Sp[(r + 1) * 33 + c] = s10; Sp[(r + 1) * 33 + c + 1] = s11;
-    }
-    __syncthreads();
-    for (int q = tid; q < npairs * 256; q += 256) {
-      const int pr = q / 256, r = 2 * ((q % 256) / 16), c = 2 * (q % 16);
-      const int j = pr, i = pr + d;
-      const float* Sp = S + pr * 32 * 33;
-      float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f;
-      for (int t = 0; t <= r + 1; ++t) {
-        const float z0 = Z[(32 * i + r) * PADW + 32 * i + t], z1 = Z[(32 * i + r + 1) * PADW + 32 * i + t];
-        const float b0 = Sp[t * 33 + c], b1 = Sp[t * 33 + c + 1];
-        s00 = fmaf(z0, b0, s00); s01 = fmaf(z0, b1, s01); s10 = fmaf(z1, b0, s10); s11 = fmaf(z1, b1, s11);
-      }
-      Z[(32 * i + r) * PADW + 32 * j + c] = -s00;
-      Z[(32 * i + r) * PADW + 32 * j + c + 1] = -s01;
-      Z[(32 * i + r + 1) * PADW + 32 * j + c] = -s10;
-      Z[(32 * i + r + 1) * PADW + 32 * j + c + 1] = -s11;
-    }
-    __syncthreads();
-  }
   float* Di = Dinv + (int64_t)kt * NB * NB;
   for (int q = tid; q < NB * NB; q += 256) {
     const int r = q / NB, c = q % NB;
     if (c <= r) Lt[(int64_t)r * mq + c] = A[r * PADW + c];
     Di[q] = (c <= r) ? Z[r * PADW + c] : 0.f;
   }
+#undef LB
+#undef ZB
+#undef SB
 }
+
+
 
 // E_k = Dinv_k^T Dinv_k for every diagonal tile (one CTA per tile, off the
 // factorisation's critical path).
@@ -742,7 +824,7 @@ static pd_status ensure_state(pd_solver* s) {
   M->pc_grid = std::max(1, nsm * std::max(1, per));
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_diag_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (2 * NB * PADW + 3 * 32 * 33) * 4);
+    cudaFuncSetAttribute(k_diag_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * NB * PADW * 4);
     cudaFuncSetAttribute(k_trsm_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (NB * AP + NB * DP) * 4);
     cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, NB * PADW * 4);
     attr = true;
@@ -776,7 +858,7 @@ static void factor_panels(pd_solver* s, Factor& f, pdtc::Mode mode) {
   // panel kt to the rest of the trailing matrix meanwhile.
   cudaStream_t sb = M->side;
   for (int kt = 0; kt < T; ++kt) {
-    k_diag_f32<<<1, 256, (2 * NB * PADW + 3 * 32 * 33) * 4, st>>>(f.L, mq, kt, f.Dinv, s->status);
+    k_diag_f32<<<1, 256, 2 * NB * PADW * 4, st>>>(f.L, mq, kt, f.Dinv, s->status);
     ++pdk::g_launches;
     const int n = (int)(T - kt - 1);
     if (n <= 0) break;
