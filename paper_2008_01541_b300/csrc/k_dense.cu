@@ -4,6 +4,8 @@
 // for three right-hand sides, and the Sigma matrix-vector products.
 // H is stored column-major with leading dimension mp (a multiple of 64); rows
 // and columns m..mp-1 hold an identity block, so every tile is full.
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace pdk {
@@ -273,6 +275,110 @@ __global__ void k_spmv3(int64_t m, const int64_t* __restrict__ ptr, const int32_
   out[3 * i] += alpha * a0; out[3 * i + 1] += alpha * a1; out[3 * i + 2] += alpha * a2;
 }
 
+
+// ---- triangular solves of L L^T u = g as dependency-counter tasks ---------
+// Forward, for i = 0 .. T-1: task D(i) waits for the i updates into w_i,
+// then y_i = Linv_ii w_i; tasks U(i, j), j > i, wait for D(i), then
+// w_j -= L_ji y_i.  Backward mirrors it with u_i = Linv_ii^T z_i and
+// z_j -= L_ij^T u_i, j < i.  Tasks are numbered block row by block row
+// (D(i) first) and claimed in that order by a persistent grid, so every wait
+// is on an earlier, already claimed task.  Counters: cnt[0] claim,
+// cnt[1 + i] updates received by block i, cnt[1 + T + i] block i solved.
+// Waits are bounded (code 302 in status[1]).
+__device__ __forceinline__ unsigned long long dtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void wait_ge(const int* c, int target, int* status) {
+  const unsigned long long t0 = dtimer();
+  unsigned it = 0;
+  while (*(volatile const int*)c < target) {
+    if (*(volatile int*)(status + 1) != 0) return;
+    if (++it > 32) __nanosleep(64);
+    if ((it & 1023u) == 0 && dtimer() - t0 > 1000000000ull) {
+      atomicCAS(status + 1, 0, 302);
+      return;
+    }
+  }
+}
+
+template <bool FWD>
+__global__ void __launch_bounds__(256) k_trsv_tasks(const double* __restrict__ H, int64_t mp,
+                                                    const double* __restrict__ Linv, double* w, double* y, int* cnt,
+                                                    int* status) {
+  __shared__ double tile[TB][TB + 1];
+  __shared__ double vec[TB][3];
+  __shared__ int cur_i, cur_j;
+  const int T = (int)(mp / TB), tid = threadIdx.x;
+  const int ntask = T * (T + 1) / 2;
+  const int r = tid / 3, v = tid % 3;          // output row / component (tid < 192)
+  for (;;) {
+    if (tid == 0) {
+      int t = atomicAdd(cnt, 1), i = -1, j = -1;
+      if (t < ntask) {
+        // block row b (in solve order) holds T - b tasks: D first, then the updates
+        int b = 0;
+        while (t >= T - b) { t -= T - b; ++b; }
+        i = FWD ? b : T - 1 - b;
+        j = t == 0 ? i : (FWD ? i + t : i - t);
+      }
+      cur_i = i; cur_j = j;
+    }
+    __syncthreads();
+    const int i = cur_i, j = cur_j;
+    if (i < 0) break;
+    const bool diag = i == j;
+    if (tid == 0) {
+      if (diag) wait_ge(cnt + 1 + i, FWD ? i : T - 1 - i, status);
+      else wait_ge(cnt + 1 + T + i, 1, status);
+      __threadfence();
+    }
+    __syncthreads();
+    // stage the 64 x 64 operand: diag -> Linv_ii (column-major, lower);
+    // forward update -> L_ji; backward update -> L_ij (both column-major in H)
+    const double* src = diag ? Linv + (int64_t)i * TB * TB
+                             : (FWD ? H + (int64_t)j * TB + (int64_t)i * TB * mp : H + (int64_t)i * TB + (int64_t)j * TB * mp);
+    const int64_t ld = diag ? TB : mp;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int q = tid + 256 * k, rr = q % TB, cc = q / TB;
+      tile[rr][cc] = __ldg(src + rr + (int64_t)cc * ld);
+    }
+    if (tid < TB * 3) {
+      // forward: diag contracts w_i, update contracts y_i; backward: z_i / u_i
+      const double* x = (diag ? w : y) + 3 * ((int64_t)i * TB) + tid;
+      (&vec[0][0])[tid] = __ldcg(x);
+    }
+    __syncthreads();
+    if (tid < TB * 3) {
+      double acc = 0.0;
+      if (FWD) {
+        // out[r] = sum_c tile[r][c] vec[c]  (diag: c <= r)
+        const int c1 = diag ? r + 1 : TB;
+#pragma unroll 8
+        for (int c = 0; c < c1; ++c) acc = fma(tile[r][c], vec[c][v], acc);
+      } else {
+        // out[r] = sum_c tile[c][r] vec[c]  (diag: c >= r)
+        const int c0 = diag ? r : 0;
+#pragma unroll 8
+        for (int c = c0; c < TB; ++c) acc = fma(tile[c][r], vec[c][v], acc);
+      }
+      if (diag) {
+        y[3 * ((int64_t)i * TB) + tid] = acc;
+      } else {
+        atomicAdd(w + 3 * ((int64_t)j * TB) + tid, -acc);
+      }
+      __threadfence();
+    }
+    __syncthreads();
+    if (tid == 0) {
+      if (diag) atomicAdd(cnt + 1 + T + i, 1);
+      else atomicAdd(cnt + 1 + j, 1);
+    }
+  }
+}
+
 inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 }  // namespace
@@ -344,6 +450,33 @@ void cholesky_fp64(double* H, int64_t mp, double* Linv, int* status, cudaStream_
     cudaEventRecord(la->ev_rest[k], la->side);
   }
   if (T > 1) cudaStreamWaitEvent(st, la->ev_rest[T - 2], 0);
+}
+
+void chol_solve_fp64_tasks(const double* H, int64_t mp, const double* Linv, const double* g, double* u,
+                           int64_t m, double* work, int* cnt, int* status, cudaStream_t st) {
+  static int grid = 0;
+  if (grid == 0) {
+    int dev = 0, nsm = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trsv_tasks<true>, 256, 0);
+    grid = std::max(1, nsm * std::max(1, per));
+  }
+  const int T = (int)(mp / TB);
+  const int ntask = T * (T + 1) / 2;
+  double* w = work;
+  double* y = work + 3 * mp;
+  k_pad_rhs<<<nblk(3 * mp, 256), 256, 0, st>>>(g, m, mp, w);
+  ++g_launches;
+  cudaMemsetAsync(cnt, 0, sizeof(int) * (1 + 2 * T), st);
+  k_trsv_tasks<true><<<(unsigned)std::min(grid, ntask), 256, 0, st>>>(H, mp, Linv, w, y, cnt, status);
+  ++g_launches;
+  // backward on y (copied into w as the running right-hand side)
+  cudaMemcpyAsync(w, y, sizeof(double) * 3 * mp, cudaMemcpyDeviceToDevice, st);
+  cudaMemsetAsync(cnt, 0, sizeof(int) * (1 + 2 * T), st);
+  k_trsv_tasks<false><<<(unsigned)std::min(grid, ntask), 256, 0, st>>>(H, mp, Linv, w, y, cnt, status);
+  ++g_launches;
+  cudaMemcpyAsync(u, y, sizeof(double) * 3 * m, cudaMemcpyDeviceToDevice, st);
 }
 
 void chol_solve_fp64(const double* H, int64_t mp, const double* Linv, const double* g, double* u, int64_t m,

@@ -84,9 +84,14 @@ struct LookAhead {
 // and la->side (depth-1 look-ahead); without it everything runs on st.
 void cholesky_fp64(double* H, int64_t mp, double* Linv, int* status, cudaStream_t st,
                    const LookAhead* la = nullptr);
-// Solve (L L^T) u = g for 3 right-hand sides, g/u [m][3] (padded internally).
+// Solve (L L^T) u = g for 3 right-hand sides, g/u [m][3] (padded internally),
+// one launch per block step.
 void chol_solve_fp64(const double* H, int64_t mp, const double* Linv, const double* g, double* u,
                      int64_t m, double* work /*[mp][3] x 2*/, cudaStream_t st);
+// The same solve as two persistent launches of dependency-counter tasks;
+// cnt: [1 + 2 mp/64] ints of scratch, status[1] <- 302 if a wait gave up.
+void chol_solve_fp64_tasks(const double* H, int64_t mp, const double* Linv, const double* g, double* u,
+                           int64_t m, double* work /*[mp][3] x 2*/, int* cnt, int* status, cudaStream_t st);
 // out[i][:] = sum_j S[i][j] v[j][:]  (S symmetric m x m, full storage), FP64
 void symv3(const double* S, int64_t m, const double* v, double* out, cudaStream_t st);
 // out[i][:] += alpha * sum_j B[i][j] v[j][:]  (CSC of a symmetric pattern)

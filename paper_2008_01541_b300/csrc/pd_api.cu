@@ -158,7 +158,7 @@ pd_status pd_solver::region_solve_core(const double* g_dev, const double* u0_dev
     tend();
     tbegin(4);
     pdk::cholesky_fp64(H, mp, Linv, status, stream, &la);
-    pdk::chol_solve_fp64(H, mp, Linv, g_dev, u_dev, m, work, stream);
+    pdk::chol_solve_fp64_tasks(H, mp, Linv, g_dev, u_dev, m, work, trsv_cnt, status, stream);
     tend();
     last_refine = 0;
     return PD_OK;
@@ -771,6 +771,7 @@ pd_status pd_solver::upload(const pdh::Setup& h, const pdh::Input& in) {
   CK(cudaMemset(u_last, 0, sizeof(double) * 3 * m));
   X_rest_h.assign(in.X, in.X + 3 * n);
   CK(dalloc(s, &work, 6 * mp));
+  CK(dalloc(s, &trsv_cnt, 1 + 2 * (mp / 64)));
   CK(dalloc(s, &status, 4));
   sf.status = status;
   CK(cudaMemset(status, 0, sizeof(int) * 4));

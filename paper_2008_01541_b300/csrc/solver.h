@@ -68,6 +68,7 @@ struct pd_solver {
   double *U2 = nullptr, *work = nullptr, *x2_dev = nullptr;
   double* x2_host = nullptr;
   int* status = nullptr;      // [0] non-SPD column+1, [1] timeout code, [2] no convergence
+  int* trsv_cnt = nullptr;    // task counters of the FP64 Schur solve
   int* status_h = nullptr;
   pdk::LookAhead la;             // side stream + events of the FP64 factorisation
   pdm::MixedState* mixed = nullptr;
