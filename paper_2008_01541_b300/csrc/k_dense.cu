@@ -63,53 +63,127 @@ __global__ void k_contact_forces(int64_t k, int ns, const int32_t* __restrict__ 
   }
 }
 
-// Factor the diagonal tile (kt, kt) in shared memory and form its inverse.
+// Factor the diagonal tile (kt, kt) in shared memory (FP64), blocked by 16
+// columns: one warp factors each 16 x 16 diagonal block in registers (lane =
+// row), one thread per row solves the panel below it, all threads apply the
+// 16-column trailing update.  Only L_kk is formed here; its inverse is built
+// for all tiles at once after the factorisation (k_chol_inv), off the
+// sequential chain.  On B300 one SM retires 2 FP64 FMAs per clock, so this
+// tile (64^3/6 FMAs) costs at least ~11 us.
+constexpr int LDA = TB + 1;   // padded column stride of a shared 64 x 64 tile
 __global__ void __launch_bounds__(256) k_chol_diag(double* __restrict__ H, int64_t mp, int kt,
-                                                   double* __restrict__ Linv, int* __restrict__ status) {
-  extern __shared__ double sm[];
-  double* A = sm;             // column-major A[c*TB + r]
-  double* Z = sm + TB * TB;   // inverse, column-major
-  __shared__ double piv;
-  const int tid = threadIdx.x;
+                                                   int* __restrict__ status) {
+  __shared__ double A[TB * LDA];   // column-major, A[c * LDA + r]
+  __shared__ double rinv[TB];
+  const int tid = threadIdx.x, lane = tid & 31;
   double* Ht = H + (int64_t)kt * TB + (int64_t)kt * TB * mp;
-  for (int idx = tid; idx < TB * TB; idx += 256) A[idx] = Ht[(idx % TB) + (int64_t)(idx / TB) * mp];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int idx = tid + 256 * k, r = idx % TB, c = idx / TB;
+    A[c * LDA + r] = Ht[r + (int64_t)c * mp];
+  }
   __syncthreads();
-  for (int j = 0; j < TB; ++j) {
-    if (tid == 0) {
-      double d = A[j * TB + j];
-      if (!(d > 0.0) || !isfinite(d)) {
-        if (status[0] == 0) status[0] = kt * TB + j + 1;
-        d = 1.0;
+#pragma unroll 1
+  for (int p = 0; p < 4; ++p) {
+    const int c0 = 16 * p;
+    if (tid < 32) {
+      // 16 x 16 diagonal block; lanes >= 16 shadow lane - 16 (no stores)
+      const int i = lane & 15;
+      double a[16];
+#pragma unroll
+      for (int t = 0; t < 16; ++t) a[t] = A[(c0 + t) * LDA + c0 + i];
+      unsigned bad = 0;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        double djj = __shfl_sync(0xffffffffu, a[j], j);
+        const bool b = !(djj > 0.0) || !isfinite(djj);
+        bad |= (unsigned)b << j;
+        djj = b ? 1.0 : djj;
+        const double rs = rsqrt(djj);
+        if (i == j) a[j] = djj * rs;
+        if (i > j) a[j] *= rs;
+#pragma unroll
+        for (int c = j + 1; c < 16; ++c) {
+          const double lcj = __shfl_sync(0xffffffffu, a[j], c);
+          if (i >= c) a[c] = fma(-a[j], lcj, a[c]);
+        }
       }
-      piv = sqrt(d);
-      A[j * TB + j] = piv;
+      if (lane < 16) {
+#pragma unroll
+        for (int t = 0; t < 16; ++t)
+          if (t <= i) A[(c0 + t) * LDA + c0 + i] = a[t];
+        rinv[c0 + i] = 1.0 / a[i];
+      }
+      if (bad && lane == 0) atomicCAS(status, 0, kt * TB + c0 + __ffs(bad));
     }
     __syncthreads();
-    double ip = 1.0 / piv;
-    if (tid > j && tid < TB) A[j * TB + tid] *= ip;
+    const int nb = TB - c0 - 16;
+    if (tid < nb) {
+      // panel row c0 + 16 + tid: x L_D^T = a, right-looking
+      const int row = c0 + 16 + tid;
+      double x[16];
+#pragma unroll
+      for (int t = 0; t < 16; ++t) x[t] = A[(c0 + t) * LDA + row];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        x[j] *= rinv[c0 + j];
+#pragma unroll
+        for (int t = j + 1; t < 16; ++t) x[t] = fma(-x[j], A[(c0 + j) * LDA + c0 + t], x[t]);
+      }
+#pragma unroll
+      for (int t = 0; t < 16; ++t) A[(c0 + t) * LDA + row] = x[t];
+    }
     __syncthreads();
-    int r = tid % TB;
-    for (int c = j + 1 + tid / TB; c < TB; c += 256 / TB)
-      if (r >= c) A[c * TB + r] -= A[j * TB + r] * A[j * TB + c];
+    // trailing update of rows / columns >= c0 + 16 (lower part)
+    for (int q = tid; q < nb * nb; q += 256) {
+      const int r = c0 + 16 + q % nb, c = c0 + 16 + q / nb;
+      if (r < c) continue;
+      double acc = 0.0;
+#pragma unroll
+      for (int t = 0; t < 16; ++t) acc = fma(A[(c0 + t) * LDA + r], A[(c0 + t) * LDA + c], acc);
+      A[c * LDA + r] -= acc;
+    }
     __syncthreads();
   }
-  // inverse of the lower-triangular tile: thread c solves L z = e_c
-  if (tid < TB) {
-    int c = tid;
-    for (int i = 0; i < c; ++i) Z[c * TB + i] = 0.0;
-    Z[c * TB + c] = 1.0 / A[c * TB + c];
-    for (int i = c + 1; i < TB; ++i) {
-      double s = 0.0;
-      for (int q = c; q < i; ++q) s += A[q * TB + i] * Z[c * TB + q];
-      Z[c * TB + i] = -s / A[i * TB + i];
-    }
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int idx = tid + 256 * k, r = idx % TB, c = idx / TB;
+    if (r >= c) Ht[r + (int64_t)c * mp] = A[c * LDA + r];
+  }
+}
+
+// Linv_kk = L_kk^-1 for every diagonal tile (blockIdx.x = k), column-major;
+// thread c solves L z = e_c with precomputed reciprocals of the diagonal.
+__global__ void __launch_bounds__(64) k_chol_inv(const double* __restrict__ H, int64_t mp,
+                                                 double* __restrict__ Linv) {
+  __shared__ double A[TB * LDA];
+  __shared__ double rinv[TB];
+  const int kt = blockIdx.x, c = threadIdx.x;
+  const double* Ht = H + (int64_t)kt * TB + (int64_t)kt * TB * mp;
+  for (int idx = c; idx < TB * TB; idx += TB) {
+    const int r = idx % TB, cc = idx / TB;
+    A[cc * LDA + r] = r >= cc ? Ht[r + (int64_t)cc * mp] : 0.0;
   }
   __syncthreads();
-  for (int idx = tid; idx < TB * TB; idx += 256) {
-    int r = idx % TB, c = idx / TB;
-    if (r >= c) Ht[r + (int64_t)c * mp] = A[idx];
-    Linv[(int64_t)kt * TB * TB + idx] = Z[idx];
+  rinv[c] = 1.0 / A[c * LDA + c];
+  __syncthreads();
+  double* Z = Linv + (int64_t)kt * TB * TB + (int64_t)c * TB;   // column c
+  for (int i = 0; i < c; ++i) Z[i] = 0.0;
+  // right-looking: z_i final after scaling, then eliminated from rows below
+  double z[TB];
+#pragma unroll
+  for (int i = 0; i < TB; ++i) z[i] = (i == c) ? 1.0 : 0.0;
+#pragma unroll
+  for (int i = 0; i < TB; ++i) {
+    if (i >= c) {
+      z[i] *= rinv[i];
+#pragma unroll
+      for (int t = i + 1; t < TB; ++t) z[t] = fma(-z[i], A[i * LDA + t], z[t]);
+    }
   }
+#pragma unroll
+  for (int i = 0; i < TB; ++i)
+    if (i >= c) Z[i] = z[i];
 }
 
 // 64x64x64 FP64 product in shared memory: acc[a][b] = sum_t As[t][r_a] * Bs[t][c_b],
@@ -127,29 +201,74 @@ __device__ __forceinline__ void tile_mma(const double* As, const double* Bs, int
   }
 }
 
-// L_ik = A_ik Linv_kk^T for tiles i > kt
-__global__ void __launch_bounds__(256) k_chol_trsm(double* __restrict__ H, int64_t mp, int kt,
-                                                   const double* __restrict__ Linv) {
-  extern __shared__ double sm[];
-  double* As = sm;            // As[t][r] = A_ik(r, t)
-  double* Bs = sm + TB * TB;  // Bs[t][c] = Linv(c, t)
-  const int tid = threadIdx.x;
-  const int64_t it = kt + 1 + blockIdx.x;
-  double* Ai = H + it * TB + (int64_t)kt * TB * mp;
-  const double* Li = Linv + (int64_t)kt * TB * TB;
-  for (int idx = tid; idx < TB * TB; idx += 256) {
-    int r = idx % TB, t = idx / TB;
-    As[idx] = Ai[r + (int64_t)t * mp];
-    Bs[idx] = Li[r + t * TB];   // (c = r, t)
+// L_ik = A_ik L_kk^-T for tiles i > kt by forward substitution: CTA
+// (blockIdx.x / 4) takes tile i = kt + 1 + blockIdx.x / 4, rows
+// 16 * (blockIdx.x % 4) .. + 15; four threads per row, each owning the columns
+// t = q (mod 4), the owner of column j broadcasting x_j at step j.
+__global__ void __launch_bounds__(64) k_chol_trsm(double* __restrict__ H, int64_t mp, int kt) {
+  __shared__ double Lk[TB * LDA];   // L_kk, column-major
+  __shared__ double rinv[TB];
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int r = tid >> 2, q = tid & 3;   // row within the slice, column class
+  const double* Lt = H + (int64_t)kt * TB + (int64_t)kt * TB * mp;
+  for (int idx = tid; idx < TB * TB; idx += 64) {
+    const int rr = idx % TB, cc = idx / TB;
+    Lk[cc * LDA + rr] = Lt[rr + (int64_t)cc * mp];
   }
   __syncthreads();
-  int tr = tid % 16, tc = tid / 16;
-  double acc[4][4] = {};
-  tile_mma(As, Bs, tr, tc, acc);
+  rinv[tid] = 1.0 / Lk[tid * LDA + tid];
+  __syncthreads();
+  const int64_t it = kt + 1 + blockIdx.x / 4;
+  double* Ai = H + it * TB + 16 * (blockIdx.x % 4) + r + (int64_t)kt * TB * mp;   // row of the slice
+  double x[16];
 #pragma unroll
-  for (int p = 0; p < 4; ++p)
+  for (int m = 0; m < 16; ++m) x[m] = Ai[(int64_t)(4 * m + q) * mp];
+#pragma unroll 1
+  for (int j = 0; j < TB; ++j) {
+    // owner of column j: thread q == j % 4 of this row, register m == j / 4
+    double xj = 0.0;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) Ai[(tr + 16 * p) + (int64_t)(tc + 16 * q) * mp] = acc[p][q];
+    for (int m = 0; m < 16; ++m)
+      if (4 * m + q == j) { x[m] *= rinv[j]; xj = x[m]; }
+    xj = __shfl_sync(0xffffffffu, xj, (lane & ~3) | (j & 3));
+#pragma unroll
+    for (int m = 0; m < 16; ++m)
+      if (4 * m + q > j) x[m] = fma(-xj, Lk[j * LDA + 4 * m + q], x[m]);
+  }
+#pragma unroll
+  for (int m = 0; m < 16; ++m) Ai[(int64_t)(4 * m + q) * mp] = x[m];
+}
+
+// Column update of the look-ahead: rows 16 * (blockIdx.x % 4) .. + 15 of tile
+// (kt + 1 + blockIdx.x / 4, kt + 1) -= L_ik L_(kt+1)k^T.
+__global__ void __launch_bounds__(256) k_chol_colupd(double* __restrict__ H, int64_t mp, int kt) {
+  __shared__ double As[TB * 17];   // As[t * 17 + r]: the 16 rows of L_ik
+  __shared__ double Bs[TB * LDA];  // Bs[t * LDA + c]: L_(kt+1)k
+  const int tid = threadIdx.x;
+  const int64_t it = kt + 1 + blockIdx.x / 4, jt = kt + 1;
+  const int r0 = 16 * (blockIdx.x % 4);
+  const double* Li = H + it * TB + r0 + (int64_t)kt * TB * mp;
+  const double* Lj = H + jt * TB + (int64_t)kt * TB * mp;
+  for (int idx = tid; idx < 16 * TB; idx += 256) {
+    const int rr = idx % 16, t = idx / 16;
+    As[t * 17 + rr] = Li[rr + (int64_t)t * mp];
+  }
+  for (int idx = tid; idx < TB * TB; idx += 256) {
+    const int cc = idx % TB, t = idx / TB;
+    Bs[t * LDA + cc] = Lj[cc + (int64_t)t * mp];
+  }
+  __syncthreads();
+  const int rr = tid % 16, cg = tid / 16;   // row, column group (columns cg + 16 e)
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 8
+  for (int t = 0; t < TB; ++t) {
+    const double a = As[t * 17 + rr];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc[e] = fma(a, Bs[t * LDA + cg + 16 * e], acc[e]);
+  }
+  double* Aij = H + it * TB + r0 + rr + jt * TB * mp;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) Aij[(int64_t)(cg + 16 * e) * mp] -= acc[e];
 }
 
 // A_ij -= L_ik L_jk^T for the tiles selected by the launch: lower != 0 ->
@@ -409,47 +528,48 @@ void cholesky_fp64(double* H, int64_t mp, double* Linv, int* status, cudaStream_
   static bool attr = false;
   const int smem = 2 * TB * TB * sizeof(double);
   if (!attr) {
-    cudaFuncSetAttribute(k_chol_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(k_chol_update, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(k_chol_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     attr = true;
   }
   const int T = (int)(mp / TB);
   if (!la || (int64_t)la->ev_panel.size() < T) {   // plain right-looking order on one stream
     for (int k = 0; k < T; ++k) {
-      k_chol_diag<<<1, 256, smem, st>>>(H, mp, k, Linv, status);
+      k_chol_diag<<<1, 256, 0, st>>>(H, mp, k, status);
       ++g_launches;
       int n = T - k - 1;
       if (n <= 0) break;
-      k_chol_trsm<<<n, 256, smem, st>>>(H, mp, k, Linv);
+      k_chol_trsm<<<4 * n, 64, 0, st>>>(H, mp, k);
       ++g_launches;
       k_chol_update<<<(unsigned)((int64_t)n * (n + 1) / 2), 256, smem, st>>>(H, mp, k, k + 1, k + 1, 0, 1);
       ++g_launches;
     }
-    return;
-  }
-  // Depth-1 look-ahead: the main stream factors tile k, solves panel k and
-  // updates only block column k+1; the low-priority side stream applies panel
-  // k to the rest of the trailing matrix while tile k+1 is being factored.
-  for (int k = 0; k < T; ++k) {
-    k_chol_diag<<<1, 256, smem, st>>>(H, mp, k, Linv, status);
-    ++g_launches;
-    int n = T - k - 1;
-    if (n <= 0) break;
-    k_chol_trsm<<<n, 256, smem, st>>>(H, mp, k, Linv);
-    ++g_launches;
-    cudaEventRecord(la->ev_panel[k], st);
-    if (k > 0) cudaStreamWaitEvent(st, la->ev_rest[k - 1], 0);
-    k_chol_update<<<(unsigned)n, 256, smem, st>>>(H, mp, k, k + 1, k + 1, 1, 0);
-    ++g_launches;
-    cudaStreamWaitEvent(la->side, la->ev_panel[k], 0);
-    if (n > 1) {
-      k_chol_update<<<(unsigned)((int64_t)(n - 1) * n / 2), 256, smem, la->side>>>(H, mp, k, k + 2, k + 2, 0, 1);
+  } else {
+    // Depth-1 look-ahead: the main stream factors tile k, solves panel k and
+    // updates only block column k+1 (in 16-row slices, to keep this chain
+    // short); the low-priority side stream applies panel k to the rest of
+    // the trailing matrix while tile k+1 is being factored.
+    for (int k = 0; k < T; ++k) {
+      k_chol_diag<<<1, 256, 0, st>>>(H, mp, k, status);
       ++g_launches;
+      int n = T - k - 1;
+      if (n <= 0) break;
+      k_chol_trsm<<<4 * n, 64, 0, st>>>(H, mp, k);
+      ++g_launches;
+      cudaEventRecord(la->ev_panel[k], st);
+      if (k > 0) cudaStreamWaitEvent(st, la->ev_rest[k - 1], 0);
+      k_chol_colupd<<<4 * n, 256, 0, st>>>(H, mp, k);
+      ++g_launches;
+      cudaStreamWaitEvent(la->side, la->ev_panel[k], 0);
+      if (n > 1) {
+        k_chol_update<<<(unsigned)((int64_t)(n - 1) * n / 2), 256, smem, la->side>>>(H, mp, k, k + 2, k + 2, 0, 1);
+        ++g_launches;
+      }
+      cudaEventRecord(la->ev_rest[k], la->side);
     }
-    cudaEventRecord(la->ev_rest[k], la->side);
+    if (T > 1) cudaStreamWaitEvent(st, la->ev_rest[T - 2], 0);
   }
-  if (T > 1) cudaStreamWaitEvent(st, la->ev_rest[T - 2], 0);
+  k_chol_inv<<<(unsigned)T, 64, 0, st>>>(H, mp, Linv);
+  ++g_launches;
 }
 
 void chol_solve_fp64_tasks(const double* H, int64_t mp, const double* Linv, const double* g, double* u,
