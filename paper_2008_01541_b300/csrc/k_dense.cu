@@ -86,34 +86,33 @@ __global__ void __launch_bounds__(256) k_chol_diag(double* __restrict__ H, int64
 #pragma unroll 1
   for (int p = 0; p < 4; ++p) {
     const int c0 = 16 * p;
-    if (tid < 32) {
-      // 16 x 16 diagonal block; lanes >= 16 shadow lane - 16 (no stores)
-      const int i = lane & 15;
+    if (tid < 16) {
+      // 16 x 16 diagonal block on a half warp, lane = row
+      const int i = lane;
       double a[16];
 #pragma unroll
       for (int t = 0; t < 16; ++t) a[t] = A[(c0 + t) * LDA + c0 + i];
       unsigned bad = 0;
+      double my_rinv = 1.0;
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
-        double djj = __shfl_sync(0xffffffffu, a[j], j);
+        double djj = __shfl_sync(0x0000ffffu, a[j], j, 16);
         const bool b = !(djj > 0.0) || !isfinite(djj);
         bad |= (unsigned)b << j;
         djj = b ? 1.0 : djj;
-        const double rs = rsqrt(djj);
-        if (i == j) a[j] = djj * rs;
+        const double rs = rsqrt(djj);      // 1 / L_jj
+        if (i == j) { a[j] = djj * rs; my_rinv = rs; }
         if (i > j) a[j] *= rs;
 #pragma unroll
         for (int c = j + 1; c < 16; ++c) {
-          const double lcj = __shfl_sync(0xffffffffu, a[j], c);
+          const double lcj = __shfl_sync(0x0000ffffu, a[j], c, 16);
           if (i >= c) a[c] = fma(-a[j], lcj, a[c]);
         }
       }
-      if (lane < 16) {
 #pragma unroll
-        for (int t = 0; t < 16; ++t)
-          if (t <= i) A[(c0 + t) * LDA + c0 + i] = a[t];
-        rinv[c0 + i] = 1.0 / a[i];
-      }
+      for (int t = 0; t < 16; ++t)
+        if (t <= i) A[(c0 + t) * LDA + c0 + i] = a[t];
+      rinv[c0 + i] = my_rinv;
       if (bad && lane == 0) atomicCAS(status, 0, kt * TB + c0 + __ffs(bad));
     }
     __syncthreads();
@@ -134,14 +133,17 @@ __global__ void __launch_bounds__(256) k_chol_diag(double* __restrict__ H, int64
       for (int t = 0; t < 16; ++t) A[(c0 + t) * LDA + row] = x[t];
     }
     __syncthreads();
-    // trailing update of rows / columns >= c0 + 16 (lower part)
-    for (int q = tid; q < nb * nb; q += 256) {
-      const int r = c0 + 16 + q % nb, c = c0 + 16 + q / nb;
-      if (r < c) continue;
+    // trailing update of rows / columns >= c0 + 16 (lower part), one entry
+    // per thread step: q runs over the nb (nb + 1) / 2 lower entries
+    for (int q = tid; q < nb * (nb + 1) / 2; q += 256) {
+      int c = (int)((sqrtf((float)(8 * q + 1)) - 1.f) * 0.5f);   // row of the triangle (entry q)
+      while (c * (c + 1) / 2 > q) --c;
+      while ((c + 1) * (c + 2) / 2 <= q) ++c;
+      const int r = c0 + 16 + c, cc = c0 + 16 + (q - c * (c + 1) / 2);
       double acc = 0.0;
 #pragma unroll
-      for (int t = 0; t < 16; ++t) acc = fma(A[(c0 + t) * LDA + r], A[(c0 + t) * LDA + c], acc);
-      A[c * LDA + r] -= acc;
+      for (int t = 0; t < 16; ++t) acc = fma(A[(c0 + t) * LDA + r], A[(c0 + t) * LDA + cc], acc);
+      A[cc * LDA + r] -= acc;
     }
     __syncthreads();
   }
@@ -203,40 +205,45 @@ __device__ __forceinline__ void tile_mma(const double* As, const double* Bs, int
 
 // L_ik = A_ik L_kk^-T for tiles i > kt by forward substitution: CTA
 // (blockIdx.x / 4) takes tile i = kt + 1 + blockIdx.x / 4, rows
-// 16 * (blockIdx.x % 4) .. + 15; four threads per row, each owning the columns
-// t = q (mod 4), the owner of column j broadcasting x_j at step j.
+// 16 * (blockIdx.x % 4) .. + 15, held in shared memory; four threads per row.
+// At step j the first thread of the row scales x_j, then the four threads
+// eliminate it from the columns t > j, t = j + 1 + q (mod 4) -- no predicated
+// FP64 work, which matters on a part that retires 2 FP64 FMAs per SM clock.
 __global__ void __launch_bounds__(64) k_chol_trsm(double* __restrict__ H, int64_t mp, int kt) {
   __shared__ double Lk[TB * LDA];   // L_kk, column-major
+  __shared__ double X[16 * LDA];    // the 16 rows, X[r * LDA + t]
   __shared__ double rinv[TB];
-  const int tid = threadIdx.x, lane = tid & 31;
-  const int r = tid >> 2, q = tid & 3;   // row within the slice, column class
+  const int tid = threadIdx.x;
+  const int r = tid >> 2, q = tid & 3;
   const double* Lt = H + (int64_t)kt * TB + (int64_t)kt * TB * mp;
+  const int64_t it = kt + 1 + blockIdx.x / 4;
+  double* Ai = H + it * TB + 16 * (blockIdx.x % 4) + (int64_t)kt * TB * mp;   // slice, column-major
   for (int idx = tid; idx < TB * TB; idx += 64) {
     const int rr = idx % TB, cc = idx / TB;
     Lk[cc * LDA + rr] = Lt[rr + (int64_t)cc * mp];
   }
+  for (int idx = tid; idx < 16 * TB; idx += 64) {
+    const int rr = idx % 16, cc = idx / 16;
+    X[rr * LDA + cc] = Ai[rr + (int64_t)cc * mp];
+  }
   __syncthreads();
   rinv[tid] = 1.0 / Lk[tid * LDA + tid];
   __syncthreads();
-  const int64_t it = kt + 1 + blockIdx.x / 4;
-  double* Ai = H + it * TB + 16 * (blockIdx.x % 4) + r + (int64_t)kt * TB * mp;   // row of the slice
-  double x[16];
-#pragma unroll
-  for (int m = 0; m < 16; ++m) x[m] = Ai[(int64_t)(4 * m + q) * mp];
+  double* x = X + r * LDA;
 #pragma unroll 1
   for (int j = 0; j < TB; ++j) {
-    // owner of column j: thread q == j % 4 of this row, register m == j / 4
-    double xj = 0.0;
-#pragma unroll
-    for (int m = 0; m < 16; ++m)
-      if (4 * m + q == j) { x[m] *= rinv[j]; xj = x[m]; }
-    xj = __shfl_sync(0xffffffffu, xj, (lane & ~3) | (j & 3));
-#pragma unroll
-    for (int m = 0; m < 16; ++m)
-      if (4 * m + q > j) x[m] = fma(-xj, Lk[j * LDA + 4 * m + q], x[m]);
+    if (q == 0) x[j] *= rinv[j];
+    __syncwarp();
+    const double xj = x[j];
+    const double* Lj = Lk + j * LDA;
+    for (int t = j + 1 + q; t < TB; t += 4) x[t] = fma(-xj, Lj[t], x[t]);
+    __syncwarp();
   }
-#pragma unroll
-  for (int m = 0; m < 16; ++m) Ai[(int64_t)(4 * m + q) * mp] = x[m];
+  __syncthreads();
+  for (int idx = tid; idx < 16 * TB; idx += 64) {
+    const int rr = idx % 16, cc = idx / 16;
+    Ai[rr + (int64_t)cc * mp] = X[rr * LDA + cc];
+  }
 }
 
 // Column update of the look-ahead: rows 16 * (blockIdx.x % 4) .. + 15 of tile
