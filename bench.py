@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--no-forms", action="store_true", help="skip timing the other precision forms")
     ap.add_argument("--train-solves", type=int, default=200, help="solves recorded to train the warm start")
     ap.add_argument("--train-steps", type=int, default=1000)
+    ap.add_argument("--sweep", action="store_true",
+                    help="also measure inner = 3 and 5, the Schur refactor+solve median / p90 over repeated "
+                         "solves, and the two-slab lips scene at 2.5 / 5 / 10%% region (adds a 'sweep' key)")
     ap.add_argument("--profile-step", action="store_true",
                     help="after warm-up run one step between cudaProfilerStart/Stop (for ncu --profile-from-start off) "
                          "and exit; prints no measurement")
@@ -155,6 +158,80 @@ def time_forms(pd, sol, stream, args, fp64_ms, torch):
     sol.set_precision(pd.FP64)
     sol.set_warm_start(0)
     sol.set_state(*state)
+    return out
+
+
+def schur_stats(sol, g, n):
+    """Median and p90 of the Schur contact update + refactor + solve (device
+    time, CUDA events inside the library) over n region solves."""
+    t = []
+    for _ in range(n):
+        sol.schur_solve(g)
+        st = sol.stats()
+        t.append(st["ms_contact_update"] + st["ms_factor_solve"])
+    t = np.sort(np.asarray(t))
+    return {"median_ms": float(np.median(t)), "p90_ms": float(t[min(len(t) - 1, int(0.9 * len(t)))]),
+            "solves": n, "max_rel_residual": float(sol.stats()["residual"])}
+
+
+def step_rate(sol, stream, torch, steps):
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    sol.step(1)
+    e0.record(stream)
+    for _ in range(steps):
+        sol.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"ms_per_step": ms, "value": 1e3 / ms, "unit": UNIT}
+
+
+def sweep(pd, sol, stream, torch, args):
+    """Measurements beyond the headline line: inner = 3 and 5 on the elbow,
+    Schur refactor+solve median / p90 over repeated solves, and the two-slab
+    lips scene at 2.5 / 5 / 10% collision-prone nodes."""
+    import scenes
+    out = {"elbow": {}, "lips": {}}
+    state = sol.get_state()
+    g = np.random.Generator(np.random.PCG64(5)).normal(size=(sol.m, 3)) * 1e3
+    for name, prec in (("fp64", pd.FP64), ("fp32_ir", pd.FP32_IR)):
+        sol.set_precision(prec)
+        row = {"schur_refactor_solve": schur_stats(sol, g, 50 if prec != pd.FP64 else 20)}
+        for inner in (1, 3, 5):
+            sol.set_state(*state)
+            sol.set_inner_iters(inner)
+            row[f"inner{inner}"] = step_rate(sol, stream, torch, 3)
+        sol.set_inner_iters(1)
+        out["elbow"][name] = row
+    sol.set_precision(pd.FP64)
+    sol.set_state(*state)
+    for m in (3125, 6250, 12500):
+        s = scenes.slabs(m=m)
+        t0 = time.perf_counter()
+        ls = pd.Solver(s.X, s.tets, s.region, s.dirichlet, s.mu, 0.0, 0.0, 0.0, inner_iters=1,
+                       stream=stream.cuda_stream, timing=True, max_refine=500)
+        setup_s = time.perf_counter() - t0
+        # about 500 penalty springs on the facing proxies, pressed 0.1 past the gap mid-plane
+        prox = s.proxies[:: max(1, len(s.proxies) // 500)][:500]
+        nodes = np.full((len(prox), 4), -1, np.int32)
+        nodes[:, 0] = prox
+        w = np.zeros((len(prox), 4))
+        w[:, 0] = 1.0
+        tgt = s.X[prox] + np.where(s.X[prox, 2:3] < 9.25, 0.1, -0.1) * np.array([0.0, 0.0, 1.0])
+        ls.set_dirichlet(s.dirichlet_positions(30))
+        ls.set_contacts(nodes, w, tgt, np.full(len(prox), 1e6))
+        gl = np.random.Generator(np.random.PCG64(6)).normal(size=(m, 3)) * 1e3
+        row = {"tets": s.E, "nodes": s.n, "m": m, "region_fraction": m / s.n, "springs": len(prox),
+               "setup_s": setup_s}
+        for name, prec in (("fp64", pd.FP64), ("fp32_ir", pd.FP32_IR)):
+            ls.set_precision(prec)
+            r = step_rate(ls, stream, torch, 3)
+            r["schur_refactor_solve"] = schur_stats(ls, gl, 10 if prec == pd.FP64 else 30)
+            row[name] = r
+        ls.close()
+        out["lips"][f"m{m}"] = row
     return out
 
 
@@ -387,6 +464,8 @@ def main():
     }
     if not args.no_forms:
         line["forms"] = time_forms(pd, sol, stream, args, ms / args.steps, torch)
+    if args.sweep:
+        line["sweep"] = sweep(pd, sol, stream, torch, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         x_now = sol.positions()
         line["cpu_baseline"] = cpu_baseline(s, x_now)

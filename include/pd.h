@@ -330,6 +330,9 @@ pd_status pd_debug_wait_timeout(pd_solver* s);
 
 /* Change the precision of the collision-region solve on an existing handle. */
 pd_status pd_set_precision(pd_solver* s, int precision);
+/* Inner iterations per outer iteration (Algorithm 1, step 4), from the next
+ * pd_step on.  Errors: INVALID_ARG (inner_iters < 1). */
+pd_status pd_set_inner_iters(pd_solver* s, int inner_iters);
 
 #ifdef __cplusplus
 }

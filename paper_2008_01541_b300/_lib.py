@@ -77,6 +77,7 @@ _sigs = {
     "pd_schur_solve": (ctypes.c_int, [P, P, P, P]),
     "pd_schur_solve_dev": (ctypes.c_int, [P, P, P, P]),
     "pd_set_precision": (ctypes.c_int, [P, ctypes.c_int]),
+    "pd_set_inner_iters": (ctypes.c_int, [P, ctypes.c_int]),
     "pd_debug_wait_timeout": (ctypes.c_int, [P]),
     "pd_set_warm_start": (ctypes.c_int, [P, ctypes.c_int]),
     "pd_mlp_set_params": (ctypes.c_int, [P, P, I64]),

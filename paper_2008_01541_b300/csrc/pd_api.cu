@@ -552,6 +552,12 @@ pd_status pd_mlp_loss_grad(pd_solver* s, const float* X, const float* T, int64_t
   return pdn::loss_grad(s, X, T, B, loss, grad);
 }
 
+pd_status pd_set_inner_iters(pd_solver* s, int inner_iters) {
+  if (!s || inner_iters < 1) return PD_ERR_INVALID_ARG;
+  s->opt.inner_iters = inner_iters;
+  return PD_OK;
+}
+
 pd_status pd_set_precision(pd_solver* s, int precision) {
   if (!s || precision < PD_FP64 || precision > PD_PCG_WARM) return PD_ERR_INVALID_ARG;
   s->precision = precision;

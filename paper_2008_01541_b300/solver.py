@@ -188,6 +188,9 @@ class Solver:
     def set_precision(self, p):
         self._check(lib.pd_set_precision(self.h, p))
 
+    def set_inner_iters(self, n):
+        self._check(lib.pd_set_inner_iters(self.h, int(n)))
+
     # ---- learned warm start (PD_PCG_WARM) ----
     def set_warm_start(self, source):
         """0 = zero, 1 = previous region solution, 2 = network prediction."""
