@@ -19,7 +19,9 @@ Where the paper is silent or garbled, these readings are taken:
     singular values in descending order (the closest rotation in SO(3)).
   * Backward Euler (Section 2.2 says it carries over but does not show it):
     lumped mass m_i = rho * sum_{e ni i} Vol_e / 4, inertia target
-    y = x_n + dt * v_n, v_{n+1} = (x_{n+1} - x_n) / dt, no gravity; the x_1
+    y = x_n + dt * v_n, v_{n+1} = (x_{n+1} - x_n) / dt for every node with
+    x_n the positions at the end of the previous step (a prescribed node gets
+    the velocity of its prescribed motion), no gravity; the x_1
     inertia belongs to the alpha part, the x_2 inertia to the beta part.
   * Dirichlet nodes are eliminated; their prescribed positions enter the
     right-hand side only.
@@ -307,9 +309,9 @@ class OracleSolver:
         outer_iters times.  contacts_fn(x) -> Contacts is called once per inner
         iteration with the current x_2 (the detection step 4.1)."""
         p = self.part
+        x_n = self.x.copy()       # positions at the end of the previous step
         if dirichlet_pos is not None:
             self.set_dirichlet(dirichlet_pos)
-        x_n = self.x.copy()
         y = (x_n + self.dt * self.v) if self.mass is not None else None
         R = np.zeros((len(self.tets), 3, 3))
         Q = np.zeros((len(self.tets), 3, 3)) if self.mu_prime > 0 else None

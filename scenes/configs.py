@@ -325,7 +325,7 @@ def slabs(nx=120, ny=60, nz=9, gap=0.5, m=6250, seed=0):
         return math.radians(15.0 * min(step + 1, steps) / steps)
 
     def dirichlet_positions(step):
-        R = rotation_x(ang(step))
+        R = rotation_x(-ang(step))   # front (y = 0) of the lower slab moves up, closing the gap
         return np.concatenate([Xt, (Xb - hinge) @ R.T + hinge])
 
     in_region = np.zeros(n, bool)
