@@ -381,22 +381,24 @@ __global__ void __launch_bounds__(128) k_trsm_f32(float* __restrict__ L, float* 
   float* Hb = Lh + r0 * mq + (int64_t)kt * NB;
   const float* Di = Dinv + (int64_t)kt * NB * NB;
   {
+    // consecutive threads take consecutive rows, so the transposed shared
+    // stores hit consecutive banks
     float4 va[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {   // A slab: 32 rows x 32 float4
-      const int q = tid + 128 * k, r = q >> 5, c = 4 * (q & 31);
+      const int q = tid + 128 * k, r = q & 31, c = 4 * (q >> 5);
       va[k] = __ldcg(reinterpret_cast<const float4*>(Ab + (int64_t)r * mq + c));
     }
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      const int q = tid + 128 * k, r = q >> 5, c = 4 * (q & 31);
+      const int q = tid + 128 * k, r = q & 31, c = 4 * (q >> 5);
       AT[(c + 0) * AP + r] = va[k].x; AT[(c + 1) * AP + r] = va[k].y; AT[(c + 2) * AP + r] = va[k].z; AT[(c + 3) * AP + r] = va[k].w;
     }
 #pragma unroll 4
-    for (int k = 0; k < 32; ++k) {  // Dinv: 128 rows x 32 float4, stored transposed
-      const int q = tid + 128 * k, r = q >> 5, c = 4 * (q & 31);
-      const float4 v = __ldcg(reinterpret_cast<const float4*>(Di + r * NB + c));
-      DT[(c + 0) * DP + r] = v.x; DT[(c + 1) * DP + r] = v.y; DT[(c + 2) * DP + r] = v.z; DT[(c + 3) * DP + r] = v.w;
+    for (int k = 0; k < 32; ++k) {  // Dinv: row tid, float4 k, stored transposed
+      const float4 v = __ldcg(reinterpret_cast<const float4*>(Di + tid * NB + 4 * k));
+      DT[(4 * k + 0) * DP + tid] = v.x; DT[(4 * k + 1) * DP + tid] = v.y;
+      DT[(4 * k + 2) * DP + tid] = v.z; DT[(4 * k + 3) * DP + tid] = v.w;
     }
   }
   __syncthreads();
@@ -431,9 +433,12 @@ __global__ void __launch_bounds__(128) k_trsm_f32(float* __restrict__ L, float* 
       *reinterpret_cast<uint4*>(Pb + (r0 + rr) * NB + 8 * tx) = *reinterpret_cast<const uint4*>(hb);
     }
   }
+  float* LS = AT;   // L row-major [RB][DP], reusing the A^T buffer
 #pragma unroll
-  for (int j = 0; j < 8; ++j)
-    *reinterpret_cast<float4*>(AT + (8 * tx + j) * AP + 4 * ty) = make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
+  for (int i = 0; i < 4; ++i) {
+    *reinterpret_cast<float4*>(LS + (4 * ty + i) * DP + 8 * tx) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+    *reinterpret_cast<float4*>(LS + (4 * ty + i) * DP + 8 * tx + 4) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+  }
 #pragma unroll 4
   for (int k = 0; k < 32; ++k) {
     const int q = tid + 128 * k, r = q >> 5, c = 4 * (q & 31);
@@ -446,10 +451,11 @@ __global__ void __launch_bounds__(128) k_trsm_f32(float* __restrict__ L, float* 
     for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
 #pragma unroll 4
   for (int t = 0; t < NB; ++t) {
-    const float4 a = *reinterpret_cast<const float4*>(AT + t * AP + 4 * ty);
+    const float av[4] = {LS[(4 * ty) * DP + t], LS[(4 * ty + 1) * DP + t], LS[(4 * ty + 2) * DP + t],
+                         LS[(4 * ty + 3) * DP + t]};
     const float4 b0 = *reinterpret_cast<const float4*>(DT + t * DP + 8 * tx);
     const float4 b1 = *reinterpret_cast<const float4*>(DT + t * DP + 8 * tx + 4);
-    const float av[4] = {a.x, a.y, a.z, a.w}, bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
