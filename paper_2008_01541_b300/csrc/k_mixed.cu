@@ -957,30 +957,46 @@ static double read_slot(pd_solver* s, int slot) {
   return M->sc_h[slot];
 }
 
+static pdtc::Mode form_mode(const pd_solver* s) {
+  return s->precision == PD_FP32_IR ? pdtc::TF32X3
+         : s->precision == PD_TF32_IR ? pdtc::TF32
+         : s->precision == PD_BF16_IR ? pdtc::BF16 : pdtc::TF32X3;
+}
+
+// 4.3: contact update + low-precision refactorisation on s->stream (the warm
+// PCG form has no per-solve factor; its fixed preconditioner is built once).
+pd_status mixed_factor(pd_solver* s) {
+  pd_status rs = ensure_state(s);
+  if (rs != PD_OK) return rs;
+  MixedState* M = s->mixed;
+  if (s->precision == PD_PCG_WARM) return build_minv(s);
+  s->tbegin(2);
+  factor_cast(s, M->f, true);
+  s->tend();
+  s->tbegin(4);
+  factor_panels(s, M->f, form_mode(s));
+  s->tend();
+  return PD_OK;
+}
+
 pd_status mixed_solve(pd_solver* s, const double* g, const double* u0, double* u) {
+  pd_status r = mixed_factor(s);
+  if (r != PD_OK) return r;
+  return mixed_iterate(s, g, u0, u);
+}
+
+// 4.5 with the factor of the last mixed_factor: refinement (split-TF32) or
+// factor-preconditioned CG (TF32, BF16, warm PCG) to the relative residual tol.
+pd_status mixed_iterate(pd_solver* s, const double* g, const double* u0, double* u) {
   pd_status rs = ensure_state(s);
   if (rs != PD_OK) return rs;
   MixedState* M = s->mixed;
   cudaStream_t st = s->stream;
   const int64_t n3 = 3 * s->m;
   const bool warm = s->precision == PD_PCG_WARM;
-  const pdtc::Mode mode = s->precision == PD_FP32_IR ? pdtc::TF32X3
-                          : s->precision == PD_TF32_IR ? pdtc::TF32
-                          : s->precision == PD_BF16_IR ? pdtc::BF16 : pdtc::TF32X3;
-  // 4.3: contact update + low-precision refactorisation (not needed for the warm PCG form)
-  Factor* f = &M->f;
-  if (warm) {
-    f = &M->f0;
-    pd_status rb = build_minv(s);
-    if (rb != PD_OK) return rb;
-    s->tbegin(4);
-  } else {
-    s->tbegin(2);
-    factor_cast(s, *f, true);
-    s->tend();
-    s->tbegin(4);
-    factor_panels(s, *f, mode);
-  }
+  const pdtc::Mode mode = form_mode(s);
+  Factor* f = warm ? &M->f0 : &M->f;
+  s->tbegin(4);
   // u = u0 (or 0); r = g - H u
   if (u0) cudaMemcpyAsync(u, u0, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st);
   else cudaMemsetAsync(u, 0, sizeof(double) * n3, st);

@@ -4,6 +4,10 @@
 struct pd_solver;
 namespace pdm {
 pd_status mixed_solve(pd_solver* s, const double* g, const double* u0, double* u);
+// The two halves of mixed_solve: the refactorisation for the current contacts
+// (on s->stream) and the refined solve with that factor.
+pd_status mixed_factor(pd_solver* s);
+pd_status mixed_iterate(pd_solver* s, const double* g, const double* u0, double* u);
 void mixed_free(pd_solver* s);
 // z = M0^-1 r with the contact-free low-precision factor of Sigma_0.
 pd_status apply_free(pd_solver* s, const double* r, double* z);

@@ -129,6 +129,7 @@ pd_status pd_solver::region_solve(const double* g_dev, const double* u0_dev, dou
 }
 
 pd_status pd_solver::region_solve_core(const double* g_dev, const double* u0_dev, double* u_dev) {
+  pd_solver* s = this;
   // warm start of the PCG form (Section 3.3 solve with a learned or previous guess)
   if (precision == PD_PCG_WARM && !u0_dev && warm_source != 0) {
     if (warm_source == 2 && net) {
@@ -151,6 +152,35 @@ pd_status pd_solver::region_solve_core(const double* g_dev, const double* u0_dev
     pd_status r = pdn::before_solve(this, g_dev, nullptr);
     if (r != PD_OK) return r;
   }
+  if (!prefactored) {
+    pd_status r = refactor();
+    if (r != PD_OK) return r;
+  }
+  prefactored = false;
+  CK(cudaStreamWaitEvent(stream, ev_fac, 0));
+  if (precision == PD_FP64) {
+    tbegin(4);
+    pdk::chol_solve_fp64_tasks(H, mp, Linv, g_dev, u_dev, m, work, trsv_cnt, status, stream);
+    tend();
+    last_refine = 0;
+    return PD_OK;
+  }
+  return pdm::mixed_iterate(this, g_dev, u0_dev, u_dev);
+}
+
+// Algorithm 1, 4.3: H = Sigma_0 + C_22 for the current springs, and its
+// factorisation, issued on the factor stream once everything issued so far on
+// the solver stream (springs, positions, the previous solve's use of the
+// factor) is done.  The solve waits for ev_fac, so the factorisation of the
+// first inner iteration can run during the alpha local step and the forward
+// substitution, which it does not depend on.
+pd_status pd_solver::refactor() {
+  pd_solver* s = this;
+  CK(cudaEventRecord(ev_in, stream));
+  CK(cudaStreamWaitEvent(fstream, ev_in, 0));
+  cudaStream_t main_stream = stream;
+  stream = fstream;   // the factor kernels and their timing marks go to the factor stream
+  pd_status r = PD_OK;
   if (precision == PD_FP64) {
     tbegin(2);
     pdk::copy_sigma(Sigma0, m, H, mp, stream);
@@ -158,12 +188,17 @@ pd_status pd_solver::region_solve_core(const double* g_dev, const double* u0_dev
     tend();
     tbegin(4);
     pdk::cholesky_fp64(H, mp, Linv, status, stream, &la);
-    pdk::chol_solve_fp64_tasks(H, mp, Linv, g_dev, u_dev, m, work, trsv_cnt, status, stream);
     tend();
-    last_refine = 0;
-    return PD_OK;
+  } else {
+    r = pdm::mixed_factor(this);
   }
-  return pdm::mixed_solve(this, g_dev, u0_dev, u_dev);
+  stream = main_stream;
+  cudaError_t e = cudaEventRecord(ev_fac, fstream);
+  if (r == PD_OK && e != cudaSuccess) {
+    err = std::string("CUDA: ") + cudaGetErrorString(e);
+    r = PD_ERR_CUDA;
+  }
+  return r;
 }
 
 // ----------------------------------------------------------------- C ABI
@@ -367,6 +402,8 @@ const char* pd_last_error(const pd_solver* s) {
 void pd_destroy(pd_solver* s) {
   if (!s) return;
   if (s->stream) cudaStreamSynchronize(s->stream);
+  if (s->fstream) cudaStreamSynchronize(s->fstream);
+  if (s->la.side) cudaStreamSynchronize(s->la.side);
   for (void* p : s->allocs) cudaFree(p);
   cudaFree(s->c_idx); cudaFree(s->c_w); cudaFree(s->c_t); cudaFree(s->c_s);
   cudaFree(s->det_a); cudaFree(s->det_b); cudaFree(s->det_sph);
@@ -377,6 +414,9 @@ void pd_destroy(pd_solver* s) {
   for (auto e : s->la.ev_panel) cudaEventDestroy(e);
   for (auto e : s->la.ev_rest) cudaEventDestroy(e);
   if (s->la.side) cudaStreamDestroy(s->la.side);
+  if (s->fstream) cudaStreamDestroy(s->fstream);
+  if (s->ev_in) cudaEventDestroy(s->ev_in);
+  if (s->ev_fac) cudaEventDestroy(s->ev_fac);
   for (auto e : s->events) cudaEventDestroy(e);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
   delete s;
@@ -760,6 +800,9 @@ pd_status pd_solver::upload(const pdh::Setup& h, const pdh::Input& in) {
     int lo_prio = 0, hi_prio = 0;
     CK(cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
     CK(cudaStreamCreateWithPriority(&la.side, cudaStreamNonBlocking, lo_prio));
+    CK(cudaStreamCreateWithPriority(&fstream, cudaStreamNonBlocking, hi_prio));
+    CK(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ev_fac, cudaEventDisableTiming));
     la.ev_panel.resize(mp / 64);
     la.ev_rest.resize(mp / 64);
     for (size_t i = 0; i < la.ev_panel.size(); ++i) {
@@ -794,6 +837,7 @@ pd_status pd_solver::upload(const pdh::Setup& h, const pdh::Input& in) {
 // Algorithm 1 for one time step.
 pd_status pd_solver::step(int outer_iters, pd_contact_cb cb, void* user) {
   pd_solver* s = this;
+  prefactored = false;
   double t0 = now_ms();
   const int64_t launches0 = pdk::g_launches;
   marks.clear();
@@ -814,7 +858,39 @@ pd_status pd_solver::step(int outer_iters, pd_contact_cb cb, void* user) {
   }
   pd_status result = PD_OK;
   int64_t inner_total = 0, refine_total = 0;
+  // 4.1 detection: on the device, or through the host callback
+  auto detect = [&]() -> pd_status {
+    if (!cb && detector) {
+      tbegin(3);
+      if (detector == 1)
+        pdk::detect_spheres(det_n, det_a, d_region, x, nsph, det_sph, det_stiffness, c_idx, c_w, c_t, c_s, stream);
+      else
+        pdk::detect_pairs(det_n, det_a, det_nb, det_b, d_region, x, det_gap, det_stiffness, c_idx, c_w, c_t, c_s,
+                          stream);
+      tend();
+      k = det_n;
+    }
+    if (cb) {
+      pdk::gather_rows(m, d_region, x, x2_dev, stream);
+      CK(cudaMemcpyAsync(x2_host, x2_dev, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, stream));
+      CK(cudaStreamSynchronize(stream));
+      pd_status cr = cb(user, x2_host, this);
+      if (cr != PD_OK) {
+        if (err.empty()) err = "contact callback returned an error";
+        return cr;
+      }
+    }
+    return PD_OK;
+  };
   for (int it = 0; it < outer_iters && result == PD_OK; ++it) {
+    // the first inner iteration's detection and refactorisation read only x_2
+    // and the springs, so they are issued before steps 1-3 and the factor
+    // stream overlaps the alpha local step and the forward substitution
+    result = detect();
+    if (result != PD_OK) break;
+    result = refactor();
+    if (result != PD_OK) break;
+    prefactored = true;
     // 1-2: R_alpha and the alpha forces f_1, f_2^(alpha) (+ x_1 inertia)
     tbegin(0);
     pdk::polar_forces(alpha.count, alpha.tets, alpha.Dm, alpha.w, x, alpha.fe, nullptr, stream, &sl);
@@ -828,27 +904,9 @@ pd_status pd_solver::step(int outer_iters, pd_contact_cb cb, void* user) {
     double* ft2 = b + 3 * n1;
     CK(cudaMemsetAsync(U2, 0, sizeof(double) * 3 * m, stream));
     for (int j = 0; j < opt.inner_iters; ++j) {
-      // 4.1 detection: on the device, or through the host callback
-      if (!cb && detector) {
-        tbegin(3);
-        if (detector == 1)
-          pdk::detect_spheres(det_n, det_a, d_region, x, nsph, det_sph, det_stiffness, c_idx, c_w, c_t, c_s, stream);
-        else
-          pdk::detect_pairs(det_n, det_a, det_nb, det_b, d_region, x, det_gap, det_stiffness, c_idx, c_w, c_t, c_s,
-                            stream);
-        tend();
-        k = det_n;
-      }
-      if (cb) {
-        pdk::gather_rows(m, d_region, x, x2_dev, stream);
-        CK(cudaMemcpyAsync(x2_host, x2_dev, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, stream));
-        CK(cudaStreamSynchronize(stream));
-        pd_status cr = cb(user, x2_host, this);
-        if (cr != PD_OK) {
-          if (err.empty()) err = "contact callback returned an error";
-          result = cr;
-          break;
-        }
+      if (j > 0) {
+        pd_status dr = detect();
+        if (dr != PD_OK) { result = dr; break; }
       }
       // 4.2, 4.4: R_beta, g = f~_2 + f_2^(beta) (+ x_2 inertia) + f_2^(col)
       tbegin(3);
@@ -883,18 +941,22 @@ pd_status pd_solver::step(int outer_iters, pd_contact_cb cb, void* user) {
     err = std::string("kernel launch: ") + cudaGetErrorString(ce);
     result = PD_ERR_CUDA;
   }
+  // no factor-stream work of this step may outlive it (error paths included)
+  cudaStreamWaitEvent(stream, ev_fac, 0);
   if (result == PD_OK) result = check_status();
   if (result == PD_OK && dt > 0) {
     pdk::axpby(3 * n, 1.0 / dt, x, 0.0, v, stream);
     pdk::axpby(3 * n, -1.0 / dt, x_n, 1.0, v, stream);
   }
   if (result != PD_OK) {  // roll back to the state before the call
+    prefactored = false;
     cudaMemcpyAsync(x, x_save, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, stream);
     cudaMemcpyAsync(v, v_save, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, stream);
     cudaStreamSynchronize(stream);
     return result;
   }
   double ph[8];
+  prefactored = false;
   tcollect(ph);
   stats.ms_local_alpha = ph[0]; stats.ms_forward = ph[1]; stats.ms_contact_update = ph[2];
   stats.ms_local_beta = ph[3]; stats.ms_factor_solve = ph[4]; stats.ms_bookkeeping = ph[5];

@@ -71,6 +71,9 @@ struct pd_solver {
   int* trsv_cnt = nullptr;    // task counters of the FP64 Schur solve
   int* status_h = nullptr;
   pdk::LookAhead la;             // side stream + events of the FP64 factorisation
+  cudaStream_t fstream = nullptr;   // factor stream: 4.3 overlaps steps 1-3 of the outer iteration
+  cudaEvent_t ev_in = nullptr, ev_fac = nullptr;
+  bool prefactored = false;         // the factor for the current springs is issued (ev_fac)
   pdm::MixedState* mixed = nullptr;
   pdn::Net* net = nullptr;       // learned warm start
   bool mlp_recording = false;
@@ -101,6 +104,7 @@ struct pd_solver {
   pd_status step(int outer_iters, pd_contact_cb cb, void* user);
   pd_status region_solve(const double* g_dev, const double* u0_dev, double* u_dev);
   pd_status region_solve_core(const double* g_dev, const double* u0_dev, double* u_dev);
+  pd_status refactor();
   pd_status check_status();
   pd_status ensure_all_elements();
   void tbegin(int phase);
