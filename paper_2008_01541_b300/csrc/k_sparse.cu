@@ -103,7 +103,7 @@ __device__ __forceinline__ void load3(double (*dst)[3], int i, const double* x) 
 constexpr int KIND_DIAG = 0, KIND_OFF = 1, KIND_FUSED = 2;
 
 template <bool FWD>
-__global__ void __launch_bounds__(256) k_sf_solve(SparseFactor f, int64_t ntasks, const int4* __restrict__ tasks,
+__global__ void __launch_bounds__(256, 4) k_sf_solve(SparseFactor f, int64_t ntasks, const int4* __restrict__ tasks,
                                                   int* cnt, double* __restrict__ v0, double* __restrict__ v1) {
   // FWD : v0 = b (right-hand side, reduced in place by off-diagonal rows), v1 = y
   // !FWD: v0 = u (x_2 rows preset, the rest zero),                       v1 = z (= y on entry)
