@@ -532,12 +532,9 @@ void contact_forces(int64_t k, const int32_t* cidx, const double* cw, const doub
 }
 
 void cholesky_fp64(double* H, int64_t mp, double* Linv, int* status, cudaStream_t st, const LookAhead* la) {
-  static bool attr = false;
+  static std::atomic<unsigned long long> attr{0};
   const int smem = 2 * TB * TB * sizeof(double);
-  if (!attr) {
-    cudaFuncSetAttribute(k_chol_update, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    attr = true;
-  }
+  if (first_on_device(attr)) cudaFuncSetAttribute(k_chol_update, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   const int T = (int)(mp / TB);
   if (!la || (int64_t)la->ev_panel.size() < T) {   // plain right-looking order on one stream
     for (int k = 0; k < T; ++k) {
@@ -581,14 +578,11 @@ void cholesky_fp64(double* H, int64_t mp, double* Linv, int* status, cudaStream_
 
 void chol_solve_fp64_tasks(const double* H, int64_t mp, const double* Linv, const double* g, double* u,
                            int64_t m, double* work, int* cnt, int* status, cudaStream_t st) {
-  static int grid = 0;
-  if (grid == 0) {
-    int dev = 0, nsm = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trsv_tasks<true>, 256, 0);
-    grid = std::max(1, nsm * std::max(1, per));
-  }
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trsv_tasks<true>, 256, 0);
+  const int grid = std::max(1, nsm * std::max(1, per));
   const int T = (int)(mp / TB);
   const int ntask = T * (T + 1) / 2;
   double* w = work;

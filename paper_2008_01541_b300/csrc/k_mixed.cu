@@ -828,12 +828,11 @@ static pd_status ensure_state(pd_solver* s) {
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_precond, 256, 0);
   M->pc_grid = std::max(1, nsm * std::max(1, per));
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<unsigned long long> attr{0};
+  if (pdk::first_on_device(attr)) {
     cudaFuncSetAttribute(k_diag_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * NB * PADW * 4);
     cudaFuncSetAttribute(k_trsm_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (NB * AP + NB * DP) * 4);
     cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, NB * PADW * 4);
-    attr = true;
   }
   return PD_OK;
 }

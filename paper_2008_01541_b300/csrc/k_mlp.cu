@@ -390,11 +390,8 @@ bool map_bf16(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int6
 template <int EPI>
 void gemm(pd_solver* s, const CUtensorMap& a, const CUtensorMap& b, int64_t M, int64_t N, int64_t K,
           const EpiArgs& ep) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_gemm<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  if (pdk::first_on_device(attr)) cudaFuncSetAttribute(k_gemm<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
   const int n_tj = (int)(N / 128);
   k_gemm<EPI><<<(unsigned)((M / 128) * n_tj), 128, kGemmSmem, s->stream>>>(a, b, (int)(K / 64), n_tj, ep, s->status);
   ++pdk::g_launches;

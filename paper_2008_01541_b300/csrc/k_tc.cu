@@ -186,20 +186,20 @@ bool make_map(CUtensorMap* map, const void* base, int esize, uint64_t rows, uint
 
 void rank_k_update(Mode mode, const CUtensorMap* a, const CUtensorMap* b, int kx0, int kchunks, float* C,
                    int64_t ldc, int ti0, int tj0, int n_i, int n_j, int lower, int* status, cudaStream_t st) {
-  static bool attr[3] = {false, false, false};
+  static std::atomic<unsigned long long> attr[3];
   unsigned grid = lower ? (unsigned)((int64_t)n_i * (n_i + 1) / 2) : (unsigned)(n_i * n_j);
   if (grid == 0 || kchunks <= 0) return;
   switch (mode) {
     case TF32:
-      if (!attr[0]) { cudaFuncSetAttribute(k_rank_k<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<0>()); attr[0] = true; }
+      if (pdk::first_on_device(attr[0])) cudaFuncSetAttribute(k_rank_k<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<0>());
       k_rank_k<0><<<grid, 128, smem_bytes<0>(), st>>>(*a, *b, kx0, kchunks, C, ldc, ti0, tj0, n_j, lower, status);
       break;
     case TF32X3:
-      if (!attr[1]) { cudaFuncSetAttribute(k_rank_k<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<1>()); attr[1] = true; }
+      if (pdk::first_on_device(attr[1])) cudaFuncSetAttribute(k_rank_k<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<1>());
       k_rank_k<1><<<grid, 128, smem_bytes<1>(), st>>>(*a, *b, kx0, kchunks, C, ldc, ti0, tj0, n_j, lower, status);
       break;
     default:
-      if (!attr[2]) { cudaFuncSetAttribute(k_rank_k<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<2>()); attr[2] = true; }
+      if (pdk::first_on_device(attr[2])) cudaFuncSetAttribute(k_rank_k<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<2>());
       k_rank_k<2><<<grid, 128, smem_bytes<2>(), st>>>(*a, *b, kx0, kchunks, C, ldc, ti0, tj0, n_j, lower, status);
       break;
   }

@@ -2,9 +2,21 @@
 #pragma once
 #include <cstdint>
 #include <vector>
+#include <atomic>
 #include <cuda_runtime.h>
 
 namespace pdk {
+
+// True the first time it is called with this mask on the current device (one
+// bit per device): kernel attributes such as the dynamic shared-memory limit
+// are set per device, so a process driving several GPUs sets them on each.
+inline bool first_on_device(std::atomic<unsigned long long>& mask) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ull << (dev & 63);
+  return (mask.fetch_or(bit) & bit) == 0;
+}
+
 
 // Number of kernels launched by this library so far (host-side counter).
 extern int64_t g_launches;
