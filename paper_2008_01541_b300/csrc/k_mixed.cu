@@ -240,17 +240,17 @@ __global__ void __launch_bounds__(256) k_diag_f32(float* __restrict__ L, int64_t
   }
   __syncthreads();
 #pragma unroll 1
-  for (int p = 0; p <= 4; ++p) {
+  for (int p = 0; p < 4; ++p) {
     const int c0 = 32 * p;
     // ---- phase 1: factor block p | rest of panel p-1's update | invert block p-1
     if (warp == 0) {
-      if (p < 4) warp_chol32(A + c0 * PADW + c0, status, kt * NB + c0);
+      warp_chol32(A + c0 * PADW + c0, status, kt * NB + c0);
     } else if (warp == 7) {
       if (p > 0) warp_inv32(A + (c0 - 32) * PADW + (c0 - 32), Z + (c0 - 32) * PADW + (c0 - 32));
     } else if (p == 3) {
       // S20 += L21 Z10, S30 += L31 Z10 (warps 1-6; no trailing rows are left)
       blk_prods(2, 1, 32, 192, LB(2, 1), ZB(1, 0), SB(0), 1.f, LB(3, 1), ZB(1, 0), SB(1), 1.f);
-    } else if (p > 0 && p < 4) {
+    } else if (p > 0) {
       // rows >= c0 + 32, columns c0 .. row (sub-block p itself was updated in phase 3)
       const int pc = c0 - 32;                      // panel columns pc .. pc + 31
       const int nbr = (NB - c0 - 32) / 2, nbc = (NB - c0) / 2;
@@ -272,7 +272,6 @@ __global__ void __launch_bounds__(256) k_diag_f32(float* __restrict__ L, int64_t
       }
     }
     __syncthreads();
-    if (p == 4) break;
     // ---- phase 2: panel below block p by substitution (one thread per row)
     float* Ap = A + c0 * PADW + c0;
     const int nbelow = NB - c0 - 32;
@@ -300,7 +299,10 @@ __global__ void __launch_bounds__(256) k_diag_f32(float* __restrict__ L, int64_t
       blk_prods(3, 0, 32, 224, ZB(1, 1), SB(2), ZB(1, 0), -1.f, LB(2, 1), ZB(1, 1), SB(3), 1.f, LB(3, 1), ZB(1, 1),
                 SB(4), 1.f);
     } else if (p == 3) {
-      blk_prods(3, 0, 0, 256, ZB(2, 2), SB(0), ZB(2, 0), -1.f, ZB(2, 2), SB(3), ZB(2, 1), -1.f, LB(3, 2), ZB(2, 2),
+      // no panel below the last sub-block: warp 7 inverts it, the others form
+      // Z20 = -Z22 S20, Z21 = -Z22 S21 and S32 = L32 Z22
+      if (warp == 7) warp_inv32(A + 96 * PADW + 96, Z + 96 * PADW + 96);
+      blk_prods(3, 0, 0, 224, ZB(2, 2), SB(0), ZB(2, 0), -1.f, ZB(2, 2), SB(3), ZB(2, 1), -1.f, LB(3, 2), ZB(2, 2),
                 SB(5), 1.f);
     }
     __syncthreads();
