@@ -175,6 +175,20 @@ pd_status pd_set_detector_pairs(pd_solver* s, const int32_t* side_a, int64_t na,
                                 int64_t nb, double gap, double stiffness);
 pd_status pd_clear_detector(pd_solver* s);
 
+/* Declare the region nodes that springs may touch (FP64 form).  H = Sigma_0
+ * + C_22 has C_22 = 0 outside those rows and columns, so the region is
+ * ordered with the other nodes first, the partial Cholesky of those leading
+ * rows (in whole 64-row tiles) is computed once here, and every
+ * refactorisation (Algorithm 1, 4.3-4.5) factors only the trailing block
+ * S_p + C_pp, S_p being the Schur complement of the fixed rows; the solve is
+ * the same H u = g in FP64.  Springs set earlier and the device detector are
+ * dropped; later springs (pd_set_contacts, detectors) may touch only these
+ * nodes.  np = 0 turns it off.  The nested Schur complement is this
+ * library's; the paper refactors all of H.
+ * Errors: INVALID_ARG, CONTACT_OUTSIDE_REGION (a node not in x_2), NOT_SPD,
+ * CUDA, OOM. */
+pd_status pd_set_contact_nodes(pd_solver* s, const int32_t* nodes, int64_t np);
+
 /* One time step: outer_iters passes of Algorithm 1 (Section 3.4).  If cb is
  * not NULL it is called at every inner iteration before the local beta step;
  * otherwise the springs last set stay active.  Errors: NOT_SPD,

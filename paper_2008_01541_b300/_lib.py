@@ -61,6 +61,7 @@ _sigs = {
     "pd_set_dirichlet": (ctypes.c_int, [P, P]),
     "pd_set_contacts": (ctypes.c_int, [P, I64, P, P, P, P]),
     "pd_set_contact_pairs": (ctypes.c_int, [P, I64, P, P, P, P]),
+    "pd_set_contact_nodes": (ctypes.c_int, [P, P, I64]),
     "pd_set_detector_spheres": (ctypes.c_int, [P, P, I64, ctypes.c_int, P, D]),
     "pd_set_detector_pairs": (ctypes.c_int, [P, P, I64, P, I64, D, D]),
     "pd_clear_detector": (ctypes.c_int, [P]),

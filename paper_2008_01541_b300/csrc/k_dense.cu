@@ -27,13 +27,16 @@ __global__ void k_copy_sigma(const double* __restrict__ S, int64_t m, double* __
 }
 
 __global__ void k_contact_scatter(int64_t k, int ns, const int32_t* __restrict__ cidx, const double* __restrict__ cw,
-                                  const double* __restrict__ cs, double* __restrict__ H, int64_t mp) {
+                                  const double* __restrict__ cs, double* __restrict__ H, int64_t mp,
+                                  const int32_t* __restrict__ perm) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= (int64_t)ns * ns * k) return;
   int64_t j = t / (ns * ns);
   int a = (int)((t / ns) % ns), b = (int)(t % ns);
   int ra = cidx[ns * j + a], rb = cidx[ns * j + b];
-  if (ra < 0 || rb < 0 || ra < rb) return;
+  if (ra < 0 || rb < 0) return;
+  if (perm) { ra = perm[ra]; rb = perm[rb]; }
+  if (ra < rb) return;
   atomicAdd(H + ra + (int64_t)rb * mp, cs[j] * cw[ns * j + a] * cw[ns * j + b]);
 }
 
@@ -157,10 +160,10 @@ __global__ void __launch_bounds__(256) k_chol_diag(double* __restrict__ H, int64
 // Linv_kk = L_kk^-1 for every diagonal tile (blockIdx.x = k), column-major;
 // thread c solves L z = e_c with precomputed reciprocals of the diagonal.
 __global__ void __launch_bounds__(64) k_chol_inv(const double* __restrict__ H, int64_t mp,
-                                                 double* __restrict__ Linv) {
+                                                 double* __restrict__ Linv, int k0) {
   __shared__ double A[TB * LDA];
   __shared__ double rinv[TB];
-  const int kt = blockIdx.x, c = threadIdx.x;
+  const int kt = k0 + blockIdx.x, c = threadIdx.x;
   const double* Ht = H + (int64_t)kt * TB + (int64_t)kt * TB * mp;
   for (int idx = c; idx < TB * TB; idx += TB) {
     const int r = idx % TB, cc = idx / TB;
@@ -366,6 +369,38 @@ __global__ void k_pad_rhs(const double* g, int64_t m, int64_t mp, double* w) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < 3 * mp) w[i] = i < 3 * m ? g[i] : 0.0;
 }
+// w[perm[r]] = g[r] (region index r -> factor position)
+__global__ void k_perm_scatter(const double* g, int64_t m, const int32_t* perm, double* w) {
+  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= m) return;
+  const int64_t p = perm[r];
+  w[3 * p] = g[3 * r]; w[3 * p + 1] = g[3 * r + 1]; w[3 * p + 2] = g[3 * r + 2];
+}
+__global__ void k_perm_gather(const double* y, int64_t m, const int32_t* perm, double* u) {
+  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= m) return;
+  const int64_t p = perm[r];
+  u[3 * r] = y[3 * p]; u[3 * r + 1] = y[3 * p + 1]; u[3 * r + 2] = y[3 * p + 2];
+}
+// H (mp x mp, column-major, full) = P S P^T with identity padding: entry
+// (pi, pj) of H is S[iperm[pi]][iperm[pj]] for pi, pj < m
+__global__ void k_permute_sym(const double* __restrict__ S, int64_t m, const int32_t* __restrict__ iperm,
+                              double* __restrict__ H, int64_t mp) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= mp * mp) return;
+  const int64_t pi = q % mp, pj = q / mp;
+  H[q] = (pi < m && pj < m) ? S[(int64_t)iperm[pi] * m + iperm[pj]] : (pi == pj ? 1.0 : 0.0);
+}
+// copy the trailing n x n block at (off, off) of H to or from a dense buffer
+__global__ void k_block_copy(double* __restrict__ H, int64_t mp, int64_t off, double* __restrict__ B, int64_t n,
+                             int to_h) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= n * n) return;
+  const int64_t i = q % n, j = q / n;
+  double* h = H + (off + i) + (off + j) * mp;
+  if (to_h) *h = B[q];
+  else B[q] = *h;
+}
 
 __global__ void k_symv3(const double* __restrict__ S, int64_t m, const double* __restrict__ v,
                         double* __restrict__ out) {
@@ -515,10 +550,21 @@ void copy_sigma(const double* S, int64_t m, double* H, int64_t mp, cudaStream_t 
   ++g_launches;
 }
 
+void permute_sym(const double* S, int64_t m, const int32_t* iperm, double* H, int64_t mp, cudaStream_t st) {
+  k_permute_sym<<<nblk(mp * mp, 256), 256, 0, st>>>(S, m, iperm, H, mp);
+  ++g_launches;
+}
+
+void block_copy(double* H, int64_t mp, int64_t off, double* B, int64_t n, bool to_h, cudaStream_t st) {
+  if (n <= 0) return;
+  k_block_copy<<<nblk(n * n, 256), 256, 0, st>>>(H, mp, off, B, n, to_h ? 1 : 0);
+  ++g_launches;
+}
+
 void contact_scatter(int64_t k, const int32_t* cidx, const double* cw, const double* cs, double* H,
-                     int64_t mp, cudaStream_t st, int ns) {
+                     int64_t mp, cudaStream_t st, int ns, const int32_t* perm) {
   if (k > 0) {
-    k_contact_scatter<<<nblk((int64_t)ns * ns * k, 256), 256, 0, st>>>(k, ns, cidx, cw, cs, H, mp);
+    k_contact_scatter<<<nblk((int64_t)ns * ns * k, 256), 256, 0, st>>>(k, ns, cidx, cw, cs, H, mp, perm);
     ++g_launches;
   }
 }
@@ -531,13 +577,16 @@ void contact_forces(int64_t k, const int32_t* cidx, const double* cw, const doub
   }
 }
 
-void cholesky_fp64(double* H, int64_t mp, double* Linv, int* status, cudaStream_t st, const LookAhead* la) {
+void cholesky_fp64(double* H, int64_t mp, double* Linv, int* status, cudaStream_t st, const LookAhead* la, int k_begin,
+                   int k_end) {
   static std::atomic<unsigned long long> attr{0};
   const int smem = 2 * TB * TB * sizeof(double);
   if (first_on_device(attr)) cudaFuncSetAttribute(k_chol_update, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   const int T = (int)(mp / TB);
+  if (k_end < 0 || k_end > T) k_end = T;
+  if (k_begin >= k_end) return;
   if (!la || (int64_t)la->ev_panel.size() < T) {   // plain right-looking order on one stream
-    for (int k = 0; k < T; ++k) {
+    for (int k = k_begin; k < k_end; ++k) {
       k_chol_diag<<<1, 256, 0, st>>>(H, mp, k, status);
       ++g_launches;
       int n = T - k - 1;
@@ -552,7 +601,7 @@ void cholesky_fp64(double* H, int64_t mp, double* Linv, int* status, cudaStream_
     // updates only block column k+1 (in 16-row slices, to keep this chain
     // short); the low-priority side stream applies panel k to the rest of
     // the trailing matrix while tile k+1 is being factored.
-    for (int k = 0; k < T; ++k) {
+    for (int k = k_begin; k < k_end; ++k) {
       k_chol_diag<<<1, 256, 0, st>>>(H, mp, k, status);
       ++g_launches;
       int n = T - k - 1;
@@ -560,7 +609,7 @@ void cholesky_fp64(double* H, int64_t mp, double* Linv, int* status, cudaStream_
       k_chol_trsm<<<4 * n, 64, 0, st>>>(H, mp, k);
       ++g_launches;
       cudaEventRecord(la->ev_panel[k], st);
-      if (k > 0) cudaStreamWaitEvent(st, la->ev_rest[k - 1], 0);
+      if (k > k_begin) cudaStreamWaitEvent(st, la->ev_rest[k - 1], 0);
       k_chol_colupd<<<4 * n, 256, 0, st>>>(H, mp, k);
       ++g_launches;
       cudaStreamWaitEvent(la->side, la->ev_panel[k], 0);
@@ -570,14 +619,15 @@ void cholesky_fp64(double* H, int64_t mp, double* Linv, int* status, cudaStream_
       }
       cudaEventRecord(la->ev_rest[k], la->side);
     }
-    if (T > 1) cudaStreamWaitEvent(st, la->ev_rest[T - 2], 0);
+    const int last = k_end == T ? T - 2 : k_end - 1;   // the last step that recorded ev_rest
+    if (last >= k_begin) cudaStreamWaitEvent(st, la->ev_rest[last], 0);
   }
-  k_chol_inv<<<(unsigned)T, 64, 0, st>>>(H, mp, Linv);
+  k_chol_inv<<<(unsigned)(k_end - k_begin), 64, 0, st>>>(H, mp, Linv, k_begin);
   ++g_launches;
 }
 
 void chol_solve_fp64_tasks(const double* H, int64_t mp, const double* Linv, const double* g, double* u,
-                           int64_t m, double* work, int* cnt, int* status, cudaStream_t st) {
+                           int64_t m, double* work, int* cnt, int* status, cudaStream_t st, const int32_t* perm) {
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -587,7 +637,12 @@ void chol_solve_fp64_tasks(const double* H, int64_t mp, const double* Linv, cons
   const int ntask = T * (T + 1) / 2;
   double* w = work;
   double* y = work + 3 * mp;
-  k_pad_rhs<<<nblk(3 * mp, 256), 256, 0, st>>>(g, m, mp, w);
+  if (perm) {
+    cudaMemsetAsync(w, 0, sizeof(double) * 3 * mp, st);
+    k_perm_scatter<<<nblk(m, 256), 256, 0, st>>>(g, m, perm, w);
+  } else {
+    k_pad_rhs<<<nblk(3 * mp, 256), 256, 0, st>>>(g, m, mp, w);
+  }
   ++g_launches;
   cudaMemsetAsync(cnt, 0, sizeof(int) * (1 + 2 * T), st);
   k_trsv_tasks<true><<<(unsigned)std::min(grid, ntask), 256, 0, st>>>(H, mp, Linv, w, y, cnt, status);
@@ -597,7 +652,12 @@ void chol_solve_fp64_tasks(const double* H, int64_t mp, const double* Linv, cons
   cudaMemsetAsync(cnt, 0, sizeof(int) * (1 + 2 * T), st);
   k_trsv_tasks<false><<<(unsigned)std::min(grid, ntask), 256, 0, st>>>(H, mp, Linv, w, y, cnt, status);
   ++g_launches;
-  cudaMemcpyAsync(u, y, sizeof(double) * 3 * m, cudaMemcpyDeviceToDevice, st);
+  if (perm) {
+    k_perm_gather<<<nblk(m, 256), 256, 0, st>>>(y, m, perm, u);
+    ++g_launches;
+  } else {
+    cudaMemcpyAsync(u, y, sizeof(double) * 3 * m, cudaMemcpyDeviceToDevice, st);
+  }
 }
 
 void chol_solve_fp64(const double* H, int64_t mp, const double* Linv, const double* g, double* u, int64_t m,

@@ -79,8 +79,9 @@ void copy_sigma(const double* Sigma0, int64_t m, double* H, int64_t mp, cudaStre
 // proxy embedded in one tet, 8 for a two-sided spring between two proxies.
 constexpr int CSLOTS = 8;
 // H[ra][rb] += c_j w_a w_b for the k springs
+// perm (optional): region index -> position in a permuted H.
 void contact_scatter(int64_t k, const int32_t* cidx, const double* cw, const double* cs,
-                     double* H, int64_t mp, cudaStream_t st, int ns = CSLOTS);
+                     double* H, int64_t mp, cudaStream_t st, int ns = CSLOTS, const int32_t* perm = nullptr);
 // g[r][:] += -w_a c_j (p_j - t_j) with p_j = sum_a w_a x[region[r_a]]
 void contact_forces(int64_t k, const int32_t* cidx, const double* cw, const double* ct,
                     const double* cs, const int32_t* region, const double* x, double* g,
@@ -94,16 +95,26 @@ struct LookAhead {
 // the inverses of the diagonal tiles; status[0] = first failing column + 1.
 // With la (events for mp/64 steps) the trailing update is split between st
 // and la->side (depth-1 look-ahead); without it everything runs on st.
+// [k_begin, k_end) restricts the work to the panels of those tiles (a partial
+// factorisation leaves the Schur complement in the trailing block); Linv is
+// formed for the same tiles.
 void cholesky_fp64(double* H, int64_t mp, double* Linv, int* status, cudaStream_t st,
-                   const LookAhead* la = nullptr);
+                   const LookAhead* la = nullptr, int k_begin = 0, int k_end = -1);
+// H = P S P^T (mp x mp, column-major, identity padding), P given by iperm:
+// factor position -> region index
+void permute_sym(const double* S, int64_t m, const int32_t* iperm, double* H, int64_t mp, cudaStream_t st);
+// the n x n block of H at (off, off) to (to_h) or from a dense buffer B
+void block_copy(double* H, int64_t mp, int64_t off, double* B, int64_t n, bool to_h, cudaStream_t st);
 // Solve (L L^T) u = g for 3 right-hand sides, g/u [m][3] (padded internally),
 // one launch per block step.
 void chol_solve_fp64(const double* H, int64_t mp, const double* Linv, const double* g, double* u,
                      int64_t m, double* work /*[mp][3] x 2*/, cudaStream_t st);
 // The same solve as two persistent launches of dependency-counter tasks;
 // cnt: [1 + 2 mp/64] ints of scratch, status[1] <- 302 if a wait gave up.
+// perm (optional): region index -> factor position of a permuted factor.
 void chol_solve_fp64_tasks(const double* H, int64_t mp, const double* Linv, const double* g, double* u,
-                           int64_t m, double* work /*[mp][3] x 2*/, int* cnt, int* status, cudaStream_t st);
+                           int64_t m, double* work /*[mp][3] x 2*/, int* cnt, int* status, cudaStream_t st,
+                           const int32_t* perm = nullptr);
 // out[i][:] = sum_j S[i][j] v[j][:]  (S symmetric m x m, full storage), FP64
 void symv3(const double* S, int64_t m, const double* v, double* out, cudaStream_t st);
 // out[i][:] += alpha * sum_j B[i][j] v[j][:]  (CSC of a symmetric pattern)

@@ -160,7 +160,8 @@ pd_status pd_solver::region_solve_core(const double* g_dev, const double* u0_dev
   CK(cudaStreamWaitEvent(stream, ev_fac, 0));
   if (precision == PD_FP64) {
     tbegin(4);
-    pdk::chol_solve_fp64_tasks(H, mp, Linv, g_dev, u_dev, m, work, trsv_cnt, status, stream);
+    pdk::chol_solve_fp64_tasks(H, mp, Linv, g_dev, u_dev, m, work, trsv_cnt, status, stream,
+                               nested ? d_perm : nullptr);
     tend();
     last_refine = 0;
     return PD_OK;
@@ -181,7 +182,16 @@ pd_status pd_solver::refactor() {
   cudaStream_t main_stream = stream;
   stream = fstream;   // the factor kernels and their timing marks go to the factor stream
   pd_status r = PD_OK;
-  if (precision == PD_FP64) {
+  if (precision == PD_FP64 && nested) {
+    const int64_t off = 64 * (int64_t)nk0, ntr = mp - off;
+    tbegin(2);
+    pdk::block_copy(H, mp, off, Sp, ntr, true, stream);
+    pdk::contact_scatter(k, c_idx, c_w, c_s, H, mp, stream, pdk::CSLOTS, d_perm);
+    tend();
+    tbegin(4);
+    pdk::cholesky_fp64(H, mp, Linv, status, stream, &la, nk0, (int)(mp / 64));
+    tend();
+  } else if (precision == PD_FP64) {
     tbegin(2);
     pdk::copy_sigma(Sigma0, m, H, mp, stream);
     pdk::contact_scatter(k, c_idx, c_w, c_s, H, mp, stream);
@@ -310,6 +320,11 @@ static pd_status set_contacts_slots(pd_solver* s, int64_t k, int ns, const int32
         s->err = "contact " + std::to_string(j) + " names node " + std::to_string(v) + " outside the region";
         return PD_ERR_CONTACT_OUTSIDE_REGION;
       }
+      if (s->nested && wa != 0.0 && !s->contact_ok[s->region_index[v]]) {
+        s->err = "contact " + std::to_string(j) + " names node " + std::to_string(v) +
+                 ", which is not one of the contact nodes";
+        return PD_ERR_CONTACT_OUTSIDE_REGION;
+      }
       if (!std::isfinite(wa)) { s->err = "non-finite weight"; return PD_ERR_INVALID_ARG; }
       idx[(size_t)NS * j + a] = s->region_index[v];
       ww[(size_t)NS * j + a] = wa;
@@ -407,6 +422,7 @@ void pd_destroy(pd_solver* s) {
   for (void* p : s->allocs) cudaFree(p);
   cudaFree(s->c_idx); cudaFree(s->c_w); cudaFree(s->c_t); cudaFree(s->c_s);
   cudaFree(s->det_a); cudaFree(s->det_b); cudaFree(s->det_sph);
+  cudaFree(s->Sp);
   if (s->x2_host) cudaFreeHost(s->x2_host);
   if (s->status_h) cudaFreeHost(s->status_h);
   pdm::mixed_free(s);
@@ -498,6 +514,10 @@ static pd_status region_list(pd_solver* s, const int32_t* nodes, int64_t n, int3
       s->err = "detector node " + std::to_string(nodes[i]) + " is not in the region";
       return PD_ERR_CONTACT_OUTSIDE_REGION;
     }
+    if (s->nested && !s->contact_ok[s->region_index[nodes[i]]]) {
+      s->err = "detector node " + std::to_string(nodes[i]) + " is not one of the contact nodes";
+      return PD_ERR_CONTACT_OUTSIDE_REGION;
+    }
     r[i] = s->region_index[nodes[i]];
   }
   cudaFree(*dev);
@@ -550,6 +570,60 @@ pd_status pd_clear_detector(pd_solver* s) {
   if (!s) return PD_ERR_INVALID_ARG;
   s->detector = 0;
   s->k = 0;
+  return PD_OK;
+}
+
+pd_status pd_set_contact_nodes(pd_solver* s, const int32_t* nodes, int64_t np) {
+  if (!s || np < 0 || (np > 0 && !nodes)) return PD_ERR_INVALID_ARG;
+  const int64_t m = s->m, mp = s->mp;
+  if (np == 0) {
+    s->nested = false;
+    s->contact_ok.assign(m, 1);
+    s->prefactored = false;
+    return PD_OK;
+  }
+  std::vector<char> ok(m, 0);
+  for (int64_t i = 0; i < np; ++i) {
+    if (nodes[i] < 0 || nodes[i] >= s->n || s->region_index[nodes[i]] < 0) {
+      s->err = "contact node " + std::to_string(nodes[i]) + " is not in the region";
+      return PD_ERR_CONTACT_OUTSIDE_REGION;
+    }
+    ok[s->region_index[nodes[i]]] = 1;
+  }
+  // factor positions: the nodes that never carry springs first, in region
+  // order; the leading whole 64-row tiles of them form the fixed part
+  std::vector<int32_t> perm(m), iperm(m);
+  int64_t pos = 0;
+  for (int64_t r = 0; r < m; ++r)
+    if (!ok[r]) iperm[pos++] = (int32_t)r;
+  const int64_t nfree_rows = pos;
+  for (int64_t r = 0; r < m; ++r)
+    if (ok[r]) iperm[pos++] = (int32_t)r;
+  for (int64_t q = 0; q < m; ++q) perm[iperm[q]] = (int32_t)q;
+  const int nk0 = (int)(nfree_rows / 64);
+  const int64_t ntr = mp - 64 * (int64_t)nk0;
+  if (!s->d_perm) {
+    CK(dalloc(s, &s->d_perm, m));
+    CK(dalloc(s, &s->d_iperm, m));
+  }
+  CK(cudaMemcpy(s->d_perm, perm.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->d_iperm, iperm.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice));
+  if (s->Sp) { cudaFree(s->Sp); s->Sp = nullptr; }
+  CK(cudaMalloc(&s->Sp, sizeof(double) * ntr * ntr));
+  // the fixed part: partial Cholesky of P Sigma_0 P^T over the first nk0
+  // tiles; the trailing block is then the contact-free Schur complement
+  pdk::permute_sym(s->Sigma0, m, s->d_iperm, s->H, mp, s->stream);
+  pdk::cholesky_fp64(s->H, mp, s->Linv, s->status, s->stream, &s->la, 0, nk0);
+  pdk::block_copy(s->H, mp, 64 * (int64_t)nk0, s->Sp, ntr, false, s->stream);
+  CK(cudaStreamSynchronize(s->stream));
+  pd_status st = s->check_status();
+  if (st != PD_OK) return st;
+  s->contact_ok = ok;
+  s->nk0 = nk0;
+  s->nested = true;
+  s->prefactored = false;
+  s->k = 0;           // springs set before are dropped: they may touch other nodes
+  s->detector = 0;
   return PD_OK;
 }
 
@@ -651,6 +725,7 @@ pd_status pd_solver::upload(const pdh::Setup& h, const pdh::Input& in) {
   region_h.assign(in.region, in.region + m);
   region_index.assign(n, -1);
   for (int64_t i = 0; i < m; ++i) region_index[in.region[i]] = (int32_t)i;
+  contact_ok.assign(m, 1);
   hostdata.reset(new pdh::Setup());
   hostdata->Dminv = h.Dminv;
   hostdata->vol = h.vol;

@@ -74,6 +74,14 @@ struct pd_solver {
   cudaStream_t fstream = nullptr;   // factor stream: 4.3 overlaps steps 1-3 of the outer iteration
   cudaEvent_t ev_in = nullptr, ev_fac = nullptr;
   bool prefactored = false;         // the factor for the current springs is issued (ev_fac)
+  // nested Schur (FP64 form): region nodes that never carry springs come
+  // first in the factor and their part of the factor is computed once; each
+  // refactorisation covers only the trailing block from tile nk0 on
+  bool nested = false;
+  int nk0 = 0;
+  int32_t *d_perm = nullptr, *d_iperm = nullptr;   // region index <-> factor position
+  double* Sp = nullptr;                            // saved trailing block (contact-free Schur complement)
+  std::vector<char> contact_ok;                    // per region index: may carry springs
   pdm::MixedState* mixed = nullptr;
   pdn::Net* net = nullptr;       // learned warm start
   bool mlp_recording = false;

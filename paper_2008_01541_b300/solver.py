@@ -95,6 +95,12 @@ class Solver:
         fn = lib.pd_set_contact_pairs if slots == 8 else lib.pd_set_contacts
         self._check(fn(self.h, k, _ptr(nodes), _ptr(w), _ptr(target), _ptr(stiffness)))
 
+    def set_contact_nodes(self, nodes):
+        """Nested Schur refactorisation of the FP64 form on these contact nodes
+        (None or empty: off)."""
+        a = _c(nodes if nodes is not None else np.zeros(0), np.int32)
+        self._check(lib.pd_set_contact_nodes(self.h, _ptr(a) if len(a) else None, len(a)))
+
     def set_detector_spheres(self, proxies, spheres, stiffness):
         proxies = _c(proxies, np.int32)
         spheres = _c(spheres, np.float64).reshape(-1, 4)
