@@ -154,31 +154,38 @@ def time_forms(pd, sol, stream, args, fp64_ms, torch):
         out[name] = {"ms_per_step": ms, "value": 1e3 / ms, "unit": UNIT, "speedup_vs_fp64": fp64_ms / ms,
                      "schur_refactor_solve_ms": schur / args.steps, "refine_iters": iters / args.steps,
                      "max_rel_residual": res}
-    # FP64 with the nested Schur refactorisation on the contact-capable nodes
+    # the nested Schur refactorisation on the contact-capable nodes (FP64 and split-TF32)
     con = sol._contacts
-    sol.set_state(*state)
-    sol.set_precision(pd.FP64)
-    sol.set_contact_nodes(sol._scene.proxies)
-    sol.set_contacts(con.nodes, con.w, con.target, con.stiffness)
-    for _ in range(3):
-        sol.step(1)
-    schur = 0.0
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(args.steps):
-        sol.step(1)
-        st = sol.stats()
-        schur += st["ms_contact_update"] + st["ms_factor_solve"]
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    out["fp64_nested (FP64; Schur block of the %d contact nodes refactored, rest factored once)" % len(
-        sol._scene.proxies)] = {"ms_per_step": ms, "value": 1e3 / ms, "unit": UNIT, "speedup_vs_fp64": fp64_ms / ms,
-                                "schur_refactor_solve_ms": schur / args.steps, "refine_iters": 0}
-    sol.set_contact_nodes(None)
-    sol.set_contacts(con.nodes, con.w, con.target, con.stiffness)
+    npx = len(sol._scene.proxies)
+    for name, prec in (("fp64_nested (FP64; Schur block of the %d contact nodes refactored, rest factored once)" % npx,
+                        pd.FP64),
+                       ("fp32_ir_nested (split-TF32 + IR; Schur block of the %d contact nodes refactored)" % npx,
+                        pd.FP32_IR)):
+        sol.set_state(*state)
+        sol.set_precision(prec)
+        sol.set_contact_nodes(sol._scene.proxies)
+        sol.set_contacts(con.nodes, con.w, con.target, con.stiffness)
+        for _ in range(3):
+            sol.step(1)
+        schur = iters = res = 0.0
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            sol.step(1)
+            st = sol.stats()
+            schur += st["ms_contact_update"] + st["ms_factor_solve"]
+            iters += st["refine_iters"]
+            res = max(res, st["residual"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        out[name] = {"ms_per_step": ms, "value": 1e3 / ms, "unit": UNIT, "speedup_vs_fp64": fp64_ms / ms,
+                     "schur_refactor_solve_ms": schur / args.steps, "refine_iters": iters / args.steps,
+                     "max_rel_residual": res}
+        sol.set_contact_nodes(None)
+        sol.set_contacts(con.nodes, con.w, con.target, con.stiffness)
     out.update(time_learned(pd, sol, stream, args, fp64_ms, torch, state))
     sol.set_precision(pd.FP64)
     sol.set_warm_start(0)

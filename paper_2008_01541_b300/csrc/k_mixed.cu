@@ -31,13 +31,18 @@ struct Factor {
   float* E = nullptr;         // [T][128][128] Dinv^T Dinv per diagonal tile
   float* Lh = nullptr;        // [mq][mq] row-major, Lh_ik = L_ik Dinv_k (i > k)
   __nv_bfloat16* Pb[2] = {nullptr, nullptr};  // [mq][128] BF16 copies of the panel, by panel parity
-  double* d = nullptr;        // [mq] equilibration D
+  double* d = nullptr;        // [mq] equilibration D (by region index)
+  const int32_t* iperm = nullptr;   // factor position -> region index (nested form), else identity
+  int k0 = 0;                 // nested form: tiles before k0 are fixed
+  float* Sp = nullptr;        // nested form: saved trailing block
   CUtensorMap mapL{}, mapP[2]{};
   bool valid = false;
 };
 
 struct MixedState {
   int64_t mq = 0, T = 0;
+  bool nested_ready = false;  // nested form: the fixed leading tiles of f are current
+  int nested_mode = -1;
   Factor f, f0;               // per-solve factor, contact-free factor (PCG_WARM)
   double *hdiag = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *u = nullptr;
   float *Shi = nullptr, *Slo = nullptr;   // Sigma_0 = Shi + Slo (FP32 pair, ~48-bit)
@@ -97,15 +102,47 @@ __global__ void k_cast_eq(const double* __restrict__ S, int64_t m, const double*
   }
 }
 __global__ void k_contact_scatter_f32(int64_t k, const int32_t* cidx, const double* cw, const double* cs,
-                                      const double* d, float* L, int64_t mq) {
+                                      const double* d, float* L, int64_t mq, const int32_t* perm) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   constexpr int NS = pdk::CSLOTS;
   if (t >= (int64_t)NS * NS * k) return;
   int64_t j = t / (NS * NS);
   int a = (int)((t / NS) % NS), b = (int)(t % NS);
   int ra = cidx[NS * j + a], rb = cidx[NS * j + b];
-  if (ra < 0 || rb < 0 || ra < rb) return;
-  atomicAdd(L + (int64_t)ra * mq + rb, (float)(cs[j] * cw[NS * j + a] * cw[NS * j + b] * d[ra] * d[rb]));
+  if (ra < 0 || rb < 0) return;
+  const double v = cs[j] * cw[NS * j + a] * cw[NS * j + b] * d[ra] * d[rb];
+  if (perm) { ra = perm[ra]; rb = perm[rb]; }   // factor positions (d stays by region index)
+  if (ra < rb) return;
+  atomicAdd(L + (int64_t)ra * mq + rb, (float)v);
+}
+// L = D P Sigma_0 P^T D in FP32 (lower tiles, row-major), identity padding;
+// factor position p holds region index iperm[p], d by region index.
+__global__ void k_cast_eq_perm(const double* __restrict__ S, int64_t m, const double* __restrict__ d,
+                               const int32_t* __restrict__ iperm, float* __restrict__ L, int64_t mq) {
+  int ti = blockIdx.x, tj = blockIdx.y;
+  if (ti < tj) return;
+  for (int q = threadIdx.x; q < NB * NB; q += blockDim.x) {
+    int r = q / NB, c = q % NB;
+    int64_t i = (int64_t)ti * NB + r, j = (int64_t)tj * NB + c;
+    float v;
+    if (i < m && j < m) {
+      const int64_t a = iperm[i], b = iperm[j];
+      v = (float)(S[a * m + b] * d[a] * d[b]);
+    } else {
+      v = (i == j) ? 1.f : 0.f;
+    }
+    L[i * mq + j] = v;
+  }
+}
+// copy the trailing n x n block at (off, off) of the row-major L to (to_l) or from B
+__global__ void k_block_copy_f32(float* __restrict__ L, int64_t mq, int64_t off, float* __restrict__ B, int64_t n,
+                                 int to_l) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= n * n) return;
+  const int64_t i = q / n, j = q % n;
+  float* l = L + (off + i) * mq + (off + j);
+  if (to_l) *l = B[q];
+  else B[q] = *l;
 }
 
 // One warp factors the 32 x 32 block at Ap (row stride PADW) in registers
@@ -506,7 +543,7 @@ __device__ __forceinline__ void wait_at_least(const int* c, int target, int* sta
 __global__ void __launch_bounds__(256) k_precond(const float* __restrict__ Lh, const float* __restrict__ E,
                                                  int64_t mq, int64_t m, const double* __restrict__ d,
                                                  const double* __restrict__ r, double* __restrict__ z, float* w,
-                                                 float* uo, int* cnt, int* status) {
+                                                 float* uo, int* cnt, int* status, const int32_t* __restrict__ iperm) {
   __shared__ float vk[NB * 3];
   __shared__ float red[8][PS][3];
   __shared__ int cur;
@@ -555,10 +592,11 @@ __global__ void __launch_bounds__(256) k_precond(const float* __restrict__ Lh, c
         const int64_t row = R0 + rr;
         float* wr = w + 3 * row;
         if (row < m) {
-          const double dr = d[row];
-          wr[0] = (float)(dr * r[3 * row]) - a0;
-          wr[1] = (float)(dr * r[3 * row + 1]) - a1;
-          wr[2] = (float)(dr * r[3 * row + 2]) - a2;
+          const int64_t ri = iperm ? iperm[row] : row;   // region index of this factor row
+          const double dr = d[ri];
+          wr[0] = (float)(dr * r[3 * ri]) - a0;
+          wr[1] = (float)(dr * r[3 * ri + 1]) - a1;
+          wr[2] = (float)(dr * r[3 * ri + 2]) - a2;
         } else {
           wr[0] = -a0; wr[1] = -a1; wr[2] = -a2;
         }
@@ -616,8 +654,9 @@ __global__ void __launch_bounds__(256) k_precond(const float* __restrict__ Lh, c
         float* uc = uo + 3 * col;
         uc[0] = s0; uc[1] = s1; uc[2] = s2;
         if (col < m) {
-          const double dc = d[col];
-          z[3 * col] = dc * (double)s0; z[3 * col + 1] = dc * (double)s1; z[3 * col + 2] = dc * (double)s2;
+          const int64_t ci = iperm ? iperm[col] : col;
+          const double dc = d[ci];
+          z[3 * ci] = dc * (double)s0; z[3 * ci + 1] = dc * (double)s1; z[3 * ci + 2] = dc * (double)s2;
         }
         __threadfence();
       }
@@ -850,21 +889,22 @@ static void factor_cast(pd_solver* s, Factor& f, bool with_contacts) {
   k_dscale<<<nblk(mq, 256), 256, 0, st>>>(M->hdiag, m, mq, f.d, s->status); ++pdk::g_launches;
   k_cast_eq<<<dim3((unsigned)T, (unsigned)T), 256, 0, st>>>(s->Sigma0, m, f.d, f.L, mq); ++pdk::g_launches;
   if (k > 0) {
-    k_contact_scatter_f32<<<nblk((int64_t)pdk::CSLOTS * pdk::CSLOTS * k, 256), 256, 0, st>>>(k, s->c_idx, s->c_w, s->c_s, f.d, f.L, mq);
+    k_contact_scatter_f32<<<nblk((int64_t)pdk::CSLOTS * pdk::CSLOTS * k, 256), 256, 0, st>>>(k, s->c_idx, s->c_w, s->c_s, f.d, f.L, mq, nullptr);
     ++pdk::g_launches;
   }
 }
 
 // Blocked low-precision Cholesky of f.L in place.
-static void factor_panels(pd_solver* s, Factor& f, pdtc::Mode mode) {
+static void factor_panels(pd_solver* s, Factor& f, pdtc::Mode mode, int k_begin = 0, int k_end = -1) {
   MixedState* M = s->mixed;
   const int64_t mq = M->mq, T = M->T;
+  if (k_end < 0 || k_end > T) k_end = (int)T;
   cudaStream_t st = s->stream;
   // Depth-1 look-ahead: the main stream factors tile kt, solves panel kt and
   // updates only block column kt+1; the low-priority side stream applies
   // panel kt to the rest of the trailing matrix meanwhile.
   cudaStream_t sb = M->side;
-  for (int kt = 0; kt < T; ++kt) {
+  for (int kt = k_begin; kt < k_end; ++kt) {
     k_diag_f32<<<1, 256, 2 * NB * PADW * 4, st>>>(f.L, mq, kt, f.Dinv, s->status);
     ++pdk::g_launches;
     const int n = (int)(T - kt - 1);
@@ -873,7 +913,7 @@ static void factor_panels(pd_solver* s, Factor& f, pdtc::Mode mode) {
     k_trsm_f32<<<(unsigned)(n * (NB / RB)), 128, (NB * AP + NB * DP) * 4, st>>>(f.L, f.Lh, mq, kt, f.Dinv, pb);
     ++pdk::g_launches;
     cudaEventRecord(M->ev_panel[kt], st);
-    if (kt > 0) cudaStreamWaitEvent(st, M->ev_rest[kt - 1], 0);
+    if (kt > k_begin) cudaStreamWaitEvent(st, M->ev_rest[kt - 1], 0);
     const CUtensorMap* map = mode == pdtc::BF16 ? &f.mapP[kt & 1] : &f.mapL;
     const int kx = mode == pdtc::BF16 ? 0 : kt * NB, kch = mode == pdtc::BF16 ? 2 : 4;
     pdtc::rank_k_update(mode, map, map, kx, kch, f.L, mq, kt + 1, kt + 1, n, 1, 0, s->status, st);
@@ -881,9 +921,13 @@ static void factor_panels(pd_solver* s, Factor& f, pdtc::Mode mode) {
     if (n > 1) pdtc::rank_k_update(mode, map, map, kx, kch, f.L, mq, kt + 2, kt + 2, n - 1, n - 1, 1, s->status, sb);
     cudaEventRecord(M->ev_rest[kt], sb);
   }
-  if (T > 1) cudaStreamWaitEvent(st, M->ev_rest[T - 2], 0);
-  k_gram<<<(unsigned)T, 512, NB * PADW * 4, st>>>(f.Dinv, f.E);
-  ++pdk::g_launches;
+  const int last = k_end == T ? (int)T - 2 : k_end - 1;   // the last step that recorded ev_rest
+  if (last >= k_begin) cudaStreamWaitEvent(st, M->ev_rest[last], 0);
+  if (k_end > k_begin) {
+    k_gram<<<(unsigned)(k_end - k_begin), 512, NB * PADW * 4, st>>>(f.Dinv + (int64_t)k_begin * NB * NB,
+                                                                    f.E + (int64_t)k_begin * NB * NB);
+    ++pdk::g_launches;
+  }
   f.valid = true;
 }
 
@@ -893,7 +937,7 @@ static cudaError_t precond(pd_solver* s, const Factor& f, const double* r, doubl
   cudaMemsetAsync(M->pcnt, 0, sizeof(int) * (1 + 2 * T), s->stream);
   const int ntask = (int)(2 * T * NSL);
   k_precond<<<(unsigned)std::min(ntask, M->pc_grid), 256, 0, s->stream>>>(f.Lh, f.E, M->mq, s->m, f.d, r, z, M->w, M->uo,
-                                                                         M->pcnt, s->status);
+                                                                         M->pcnt, s->status, f.iperm);
   ++pdk::g_launches;
   return cudaGetLastError();
 }
@@ -966,18 +1010,78 @@ static pdtc::Mode form_mode(const pd_solver* s) {
 
 // 4.3: contact update + low-precision refactorisation on s->stream (the warm
 // PCG form has no per-solve factor; its fixed preconditioner is built once).
+// Nested form (pd_set_contact_nodes): D from Sigma_0's diagonal (fixed), the
+// region permuted with the spring-free rows first, and the factor's leading
+// k0 tiles computed once; the trailing block (the contact-free Schur
+// complement) is saved so that each refactorisation starts from it.
+static pd_status nested_setup(pd_solver* s, pdtc::Mode mode) {
+  MixedState* M = s->mixed;
+  Factor& f = M->f;
+  const int64_t m = s->m, mq = M->mq, T = M->T;
+  cudaStream_t st = s->stream;
+  f.k0 = (int)(s->n_fixed_rows / NB);
+  const int64_t ntr = mq - (int64_t)f.k0 * NB;
+  if (!f.Sp) {
+    if (cudaMalloc(&f.Sp, sizeof(float) * mq * mq) != cudaSuccess) {   // room for any trailing block
+      s->err = "device allocation for the nested factor failed";
+      return PD_ERR_OOM;
+    }
+    s->allocs.push_back(f.Sp);
+  }
+  k_hdiag<<<nblk(m, 256), 256, 0, st>>>(s->Sigma0, m, M->hdiag); ++pdk::g_launches;
+  k_dscale<<<nblk(mq, 256), 256, 0, st>>>(M->hdiag, m, mq, f.d, s->status); ++pdk::g_launches;
+  k_cast_eq_perm<<<dim3((unsigned)T, (unsigned)T), 256, 0, st>>>(s->Sigma0, m, f.d, s->d_iperm, f.L, mq);
+  ++pdk::g_launches;
+  factor_panels(s, f, mode, 0, f.k0);
+  k_block_copy_f32<<<nblk(ntr * ntr, 256), 256, 0, st>>>(f.L, mq, (int64_t)f.k0 * NB, f.Sp, ntr, 0);
+  ++pdk::g_launches;
+  f.iperm = s->d_iperm;
+  M->nested_ready = true;
+  M->nested_mode = (int)mode;
+  return PD_OK;
+}
+
 pd_status mixed_factor(pd_solver* s) {
   pd_status rs = ensure_state(s);
   if (rs != PD_OK) return rs;
   MixedState* M = s->mixed;
   if (s->precision == PD_PCG_WARM) return build_minv(s);
+  const pdtc::Mode mode = form_mode(s);
+  if (s->nested) {
+    if (!M->nested_ready || M->nested_mode != (int)mode) {
+      rs = nested_setup(s, mode);
+      if (rs != PD_OK) return rs;
+    }
+    Factor& f = M->f;
+    const int64_t mq = M->mq, ntr = mq - (int64_t)f.k0 * NB;
+    cudaStream_t st = s->stream;
+    s->tbegin(2);
+    k_block_copy_f32<<<nblk(ntr * ntr, 256), 256, 0, st>>>(f.L, mq, (int64_t)f.k0 * NB, f.Sp, ntr, 1);
+    ++pdk::g_launches;
+    if (s->k > 0) {
+      k_contact_scatter_f32<<<nblk((int64_t)pdk::CSLOTS * pdk::CSLOTS * s->k, 256), 256, 0, st>>>(
+          s->k, s->c_idx, s->c_w, s->c_s, f.d, f.L, mq, s->d_perm);
+      ++pdk::g_launches;
+    }
+    s->tend();
+    s->tbegin(4);
+    factor_panels(s, f, mode, f.k0, (int)M->T);
+    s->tend();
+    return PD_OK;
+  }
+  M->nested_ready = false;
+  M->f.iperm = nullptr;
   s->tbegin(2);
   factor_cast(s, M->f, true);
   s->tend();
   s->tbegin(4);
-  factor_panels(s, M->f, form_mode(s));
+  factor_panels(s, M->f, mode);
   s->tend();
   return PD_OK;
+}
+
+void mixed_nested_changed(pd_solver* s) {
+  if (s->mixed) s->mixed->nested_ready = false;
 }
 
 pd_status mixed_solve(pd_solver* s, const double* g, const double* u0, double* u) {

@@ -12,4 +12,6 @@ void mixed_free(pd_solver* s);
 // z = M0^-1 r with the contact-free low-precision factor of Sigma_0.
 pd_status apply_free(pd_solver* s, const double* r, double* z);
 void mixed_invalidate(pd_solver* s);
+// the contact nodes changed: the nested form's fixed part is rebuilt on next use
+void mixed_nested_changed(pd_solver* s);
 }  // namespace pdm

@@ -578,6 +578,7 @@ pd_status pd_set_contact_nodes(pd_solver* s, const int32_t* nodes, int64_t np) {
   const int64_t m = s->m, mp = s->mp;
   if (np == 0) {
     s->nested = false;
+    pdm::mixed_nested_changed(s);
     s->contact_ok.assign(m, 1);
     s->prefactored = false;
     return PD_OK;
@@ -620,7 +621,9 @@ pd_status pd_set_contact_nodes(pd_solver* s, const int32_t* nodes, int64_t np) {
   if (st != PD_OK) return st;
   s->contact_ok = ok;
   s->nk0 = nk0;
+  s->n_fixed_rows = nfree_rows;
   s->nested = true;
+  pdm::mixed_nested_changed(s);
   s->prefactored = false;
   s->k = 0;           // springs set before are dropped: they may touch other nodes
   s->detector = 0;

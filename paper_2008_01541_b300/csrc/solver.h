@@ -79,6 +79,7 @@ struct pd_solver {
   // refactorisation covers only the trailing block from tile nk0 on
   bool nested = false;
   int nk0 = 0;
+  int64_t n_fixed_rows = 0;                        // region nodes that never carry springs
   int32_t *d_perm = nullptr, *d_iperm = nullptr;   // region index <-> factor position
   double* Sp = nullptr;                            // saved trailing block (contact-free Schur complement)
   std::vector<char> contact_ok;                    // per region index: may carry springs

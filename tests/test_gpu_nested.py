@@ -113,3 +113,30 @@ def test_nested_rejects_springs_on_other_nodes(pd):
     # turning it off accepts them again
     sol.set_contact_nodes(None)
     sol.set_contacts(nodes, w, s.X[inner], np.array([1e6]))
+
+
+@pytest.mark.parametrize("prec", ["FP32_IR", "TF32_IR", "BF16_IR"])
+def test_nested_mixed_forms(pd, prec):
+    s = scenes.small_elbow(h=1.5)
+    step = 56
+    c = s.contacts(step, s.X)
+    H = _oracle_H(s, c)
+    g = rng(83).normal(size=(s.m, 3)) * 1e3
+    sol = _solver(pd, s, max_refine=500)
+    sol.set_contact_nodes(s.proxies)
+    sol.set_precision(getattr(pd, prec))
+    for rep in range(2):   # the second solve starts from the saved trailing block
+        sol.set_contacts(*contact_tuple(c))
+        u = sol.schur_solve(g)
+        res = np.linalg.norm(g - H @ u) / np.linalg.norm(g)
+        assert res <= TOL, (prec, rep, res)
+    # one outer iteration vs the oracle
+    x0 = s.X.copy()
+    sol.set_state(x0)
+    sol.set_dirichlet(s.dirichlet_positions(step))
+    sol.step(1, region_callback(s, step, x0))
+    o = oracle.OracleSolver(s.X, s.tets, s.dirichlet, s.region, s.mu)
+    o.x = x0.copy()
+    xo = o.step(1, 1, oracle_callback(s, step), s.dirichlet_positions(step))
+    err = np.linalg.norm(sol.positions() - xo) / np.linalg.norm(xo - x0)
+    assert err <= 1e-8, err
