@@ -464,69 +464,100 @@ __device__ __forceinline__ void wait_ge(const int* c, int target, int* status) {
   }
 }
 
+// Task list of one triangular solve over T block rows (in solve order b):
+// block row b holds its diagonal task, which also applies the update into
+// the next block row (the only update on the critical path), then the other
+// T - 2 - b updates; the last block row holds its diagonal task alone.
+__host__ __device__ inline int trsv_ntask(int T) { return T * (T - 1) / 2 + 1; }
+__device__ inline int trsv_start(int T, int b) { return b * (T - 1) - b * (b - 1) / 2; }
+__device__ inline void trsv_decode(int t, int T, int& b, int& q) {
+  const double d = 2.0 * T - 1.0;
+  int e = (int)floor(0.5 * (d - sqrt(fmax(d * d - 8.0 * t, 0.0))));
+  e = max(0, min(e, T - 1));
+  while (e > 0 && trsv_start(T, e) > t) --e;
+  while (e < T - 1 && trsv_start(T, e + 1) <= t) ++e;
+  b = e;
+  q = t - trsv_start(T, e);
+}
+
+// 64 x 64 FP64 tile (column-major in global, leading dimension ld) into
+// shared memory as tile[row][col] with a padded row.
+__device__ __forceinline__ void stage64(double (*tile)[LDA], const double* __restrict__ src, int64_t ld) {
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int q = threadIdx.x + 256 * k, rr = q % TB, cc = q / TB;
+    tile[rr][cc] = __ldg(src + rr + (int64_t)cc * ld);
+  }
+}
+
+// One direction of the dense triangular solve with the tiled factor in H
+// (lower, column-major; diagonal tiles replaced by their inverses in Linv),
+// three right-hand sides.  Persistent grid; tasks claimed in list order (one
+// ahead), so every wait is on a task claimed earlier and the schedule cannot
+// deadlock.  Operand tiles are staged before the wait, since they do not
+// depend on the vectors.
+//   forward : w_i complete -> y_i = L_ii^-1 w_i; update (i, j>i): w_j -= L_ji y_i
+//   backward: w_i complete -> y_i = L_ii^-T w_i; update (i, j<i): w_j -= L_ij^T y_i
+// cnt[0] claims tasks, cnt[1 + j] counts the updates applied to w_j,
+// cnt[1 + T + i] flags y_i as written.
 template <bool FWD>
 __global__ void __launch_bounds__(256) k_trsv_tasks(const double* __restrict__ H, int64_t mp,
                                                     const double* __restrict__ Linv, double* w, double* y, int* cnt,
                                                     int* status) {
-  __shared__ double tile[TB][TB + 1];
+  extern __shared__ double trsv_smem[];
+  double (*ta)[LDA] = reinterpret_cast<double (*)[LDA]>(trsv_smem);
+  double (*tn)[LDA] = reinterpret_cast<double (*)[LDA]>(trsv_smem + TB * LDA);
   __shared__ double vec[TB][3];
-  __shared__ int cur_i, cur_j;
+  __shared__ double yv[TB][3];
+  __shared__ int cur_t;
   const int T = (int)(mp / TB), tid = threadIdx.x;
-  const int ntask = T * (T + 1) / 2;
+  const int ntask = trsv_ntask(T);
   const int r = tid / 3, v = tid % 3;          // output row / component (tid < 192)
+  int ahead = 0;
+  if (tid == 0) ahead = atomicAdd(cnt, 1);
   for (;;) {
     if (tid == 0) {
-      int t = atomicAdd(cnt, 1), i = -1, j = -1;
-      if (t < ntask) {
-        // block row b (in solve order) holds T - b tasks: D first, then the updates
-        int b = 0;
-        while (t >= T - b) { t -= T - b; ++b; }
-        i = FWD ? b : T - 1 - b;
-        j = t == 0 ? i : (FWD ? i + t : i - t);
-      }
-      cur_i = i; cur_j = j;
+      cur_t = ahead;
+      if (ahead < ntask) ahead = atomicAdd(cnt, 1);
     }
     __syncthreads();
-    const int i = cur_i, j = cur_j;
-    if (i < 0) break;
-    const bool diag = i == j;
+    const int t = cur_t;
+    if (t >= ntask) break;
+    int b, q;
+    trsv_decode(t, T, b, q);
+    const int i = FWD ? b : T - 1 - b;
+    const bool diag = q == 0;
+    const int j = diag ? i : (FWD ? i + 1 + q : i - 1 - q);
+    const int jn = FWD ? i + 1 : i - 1;                      // the update fused into the diagonal task
+    const bool fused = diag && jn >= 0 && jn < T;
+    // forward update (i, j) reads L_ji, backward reads L_ij (column-major in H)
+    auto off_tile = [&](int jj) {
+      return FWD ? H + (int64_t)jj * TB + (int64_t)i * TB * mp : H + (int64_t)i * TB + (int64_t)jj * TB * mp;
+    };
+    stage64(ta, diag ? Linv + (int64_t)i * TB * TB : off_tile(j), diag ? TB : mp);
+    if (fused) stage64(tn, off_tile(jn), mp);
     if (tid == 0) {
       if (diag) wait_ge(cnt + 1 + i, FWD ? i : T - 1 - i, status);
       else wait_ge(cnt + 1 + T + i, 1, status);
       __threadfence();
     }
     __syncthreads();
-    // stage the 64 x 64 operand: diag -> Linv_ii (column-major, lower);
-    // forward update -> L_ji; backward update -> L_ij (both column-major in H)
-    const double* src = diag ? Linv + (int64_t)i * TB * TB
-                             : (FWD ? H + (int64_t)j * TB + (int64_t)i * TB * mp : H + (int64_t)i * TB + (int64_t)j * TB * mp);
-    const int64_t ld = diag ? TB : mp;
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const int q = tid + 256 * k, rr = q % TB, cc = q / TB;
-      tile[rr][cc] = __ldg(src + rr + (int64_t)cc * ld);
-    }
-    if (tid < TB * 3) {
-      // forward: diag contracts w_i, update contracts y_i; backward: z_i / u_i
-      const double* x = (diag ? w : y) + 3 * ((int64_t)i * TB) + tid;
-      (&vec[0][0])[tid] = __ldcg(x);
-    }
+    if (tid < TB * 3) (&vec[0][0])[tid] = __ldcg((diag ? w : y) + 3 * ((int64_t)i * TB) + tid);
     __syncthreads();
     if (tid < TB * 3) {
       double acc = 0.0;
       if (FWD) {
-        // out[r] = sum_c tile[r][c] vec[c]  (diag: c <= r)
-        const int c1 = diag ? r + 1 : TB;
+        const int c1 = diag ? r + 1 : TB;    // out[r] = sum_c ta[r][c] vec[c]  (diag: c <= r)
 #pragma unroll 8
-        for (int c = 0; c < c1; ++c) acc = fma(tile[r][c], vec[c][v], acc);
+        for (int c = 0; c < c1; ++c) acc = fma(ta[r][c], vec[c][v], acc);
       } else {
-        // out[r] = sum_c tile[c][r] vec[c]  (diag: c >= r)
-        const int c0 = diag ? r : 0;
+        const int c0 = diag ? r : 0;         // out[r] = sum_c ta[c][r] vec[c]  (diag: c >= r)
 #pragma unroll 8
-        for (int c = c0; c < TB; ++c) acc = fma(tile[c][r], vec[c][v], acc);
+        for (int c = c0; c < TB; ++c) acc = fma(ta[c][r], vec[c][v], acc);
       }
       if (diag) {
         y[3 * ((int64_t)i * TB) + tid] = acc;
+        yv[r][v] = acc;
       } else {
         atomicAdd(w + 3 * ((int64_t)j * TB) + tid, -acc);
       }
@@ -536,6 +567,22 @@ __global__ void __launch_bounds__(256) k_trsv_tasks(const double* __restrict__ H
     if (tid == 0) {
       if (diag) atomicAdd(cnt + 1 + T + i, 1);
       else atomicAdd(cnt + 1 + j, 1);
+    }
+    if (fused) {
+      if (tid < TB * 3) {
+        double acc = 0.0;
+        if (FWD) {
+#pragma unroll 8
+          for (int c = 0; c < TB; ++c) acc = fma(tn[r][c], yv[c][v], acc);
+        } else {
+#pragma unroll 8
+          for (int c = 0; c < TB; ++c) acc = fma(tn[c][r], yv[c][v], acc);
+        }
+        atomicAdd(w + 3 * ((int64_t)jn * TB) + tid, -acc);
+        __threadfence();
+      }
+      __syncthreads();
+      if (tid == 0) atomicAdd(cnt + 1 + jn, 1);
     }
   }
 }
@@ -628,13 +675,19 @@ void cholesky_fp64(double* H, int64_t mp, double* Linv, int* status, cudaStream_
 
 void chol_solve_fp64_tasks(const double* H, int64_t mp, const double* Linv, const double* g, double* u,
                            int64_t m, double* work, int* cnt, int* status, cudaStream_t st, const int32_t* perm) {
+  static std::atomic<unsigned long long> attr{0};
+  const int smem = 2 * TB * LDA * sizeof(double);
+  if (first_on_device(attr)) {
+    cudaFuncSetAttribute(k_trsv_tasks<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_trsv_tasks<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  }
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trsv_tasks<true>, 256, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trsv_tasks<true>, 256, smem);
   const int grid = std::max(1, nsm * std::max(1, per));
   const int T = (int)(mp / TB);
-  const int ntask = T * (T + 1) / 2;
+  const int ntask = trsv_ntask(T);
   double* w = work;
   double* y = work + 3 * mp;
   if (perm) {
@@ -645,12 +698,12 @@ void chol_solve_fp64_tasks(const double* H, int64_t mp, const double* Linv, cons
   }
   ++g_launches;
   cudaMemsetAsync(cnt, 0, sizeof(int) * (1 + 2 * T), st);
-  k_trsv_tasks<true><<<(unsigned)std::min(grid, ntask), 256, 0, st>>>(H, mp, Linv, w, y, cnt, status);
+  k_trsv_tasks<true><<<(unsigned)std::min(grid, ntask), 256, smem, st>>>(H, mp, Linv, w, y, cnt, status);
   ++g_launches;
   // backward on y (copied into w as the running right-hand side)
   cudaMemcpyAsync(w, y, sizeof(double) * 3 * mp, cudaMemcpyDeviceToDevice, st);
   cudaMemsetAsync(cnt, 0, sizeof(int) * (1 + 2 * T), st);
-  k_trsv_tasks<false><<<(unsigned)std::min(grid, ntask), 256, 0, st>>>(H, mp, Linv, w, y, cnt, status);
+  k_trsv_tasks<false><<<(unsigned)std::min(grid, ntask), 256, smem, st>>>(H, mp, Linv, w, y, cnt, status);
   ++g_launches;
   if (perm) {
     k_perm_gather<<<nblk(m, 256), 256, 0, st>>>(y, m, perm, u);
