@@ -126,6 +126,81 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def measured_peaks():
+    """Roofline denominators measured on this part (copy bandwidth, cuBLAS
+    bf16 burst), else the recorded fallback; the second value names the source."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, 1800.0, "fallback"
+
+
+def form_roofline(pd, prec, m, n_ref, refactor_ms, solve_ms, iters):
+    """Roofline of a form's dominant work.  FP64: the dense refactorisation
+    (n_ref^3 / 3 flop) against the derived FP64 ALU peak.  Low-precision forms:
+    the same algorithmic flops against the tensor peak of the operand type
+    (TF32 = bf16 measured x the nominal 1.1 / 2.25 ratio).  PCG: the bytes its
+    iterations stream (FP32 hi/lo Sigma_0 and the FP32 inverse, 12 m^2 B per
+    iteration) against the measured HBM bandwidth."""
+    hbm, bf16, src = measured_peaks()
+    if prec == pd.PCG_WARM:
+        if solve_ms <= 0:
+            return None
+        ach = iters * 12.0 * m * m / (solve_ms / 1e3) / 1e9
+        return {"bound": "hbm", "work": "PCG iterations (k_symv_df + k_minv_apply)", "achieved": ach, "peak": hbm,
+                "unit": "GB/s", "frac": ach / hbm, "peak_source": src}
+    if refactor_ms <= 0:
+        return None
+    ach = n_ref ** 3 / 3.0 / (refactor_ms / 1e3) / 1e12
+    if prec == pd.FP64:
+        peak, bound, ps = PEAK_FP64_ALU / 1e12, "alu", "derived FP64 DFMA peak"
+    elif prec == pd.BF16_IR:
+        peak, bound, ps = bf16, "tensor", src + " bf16"
+    else:
+        peak, bound, ps = bf16 * 1.1 / 2.25, "tensor", src + " bf16 x nominal TF32/BF16 ratio"
+    return {"bound": bound, "work": "dense refactorisation, n = %d" % n_ref, "achieved": ach, "peak": peak,
+            "unit": "TFLOP/s", "frac": ach / peak, "peak_source": ps}
+
+
+def time_form(pd, sol, stream, args, fp64_ms, torch, prec, nested):
+    """Device-timed steps of one form on the current state: ms per step, PD
+    iters/s, speedup over the FP64 form, the Schur contact update + refactor
+    + solve time (and the refactorisation alone), refinement iterations, the
+    worst relative residual and the form's roofline."""
+    s = sol._scene
+    for _ in range(3):
+        sol.step(1)
+    schur = ref = fs = iters = res = 0.0
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        sol.step(1)
+        st = sol.stats()
+        schur += st["ms_contact_update"] + st["ms_factor_solve"]
+        ref += st["ms_refactor"]
+        fs += st["ms_factor_solve"]
+        iters += st["refine_iters"]
+        res = max(res, st["residual"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    k = args.steps
+    if nested:
+        tile = 64 if prec == pd.FP64 else 128
+        mp = -(-s.m // tile) * tile
+        n_ref = mp - tile * ((s.m - len(s.proxies)) // tile)
+    else:
+        n_ref = s.m
+    return {"ms_per_step": ms, "value": 1e3 / ms, "unit": UNIT, "speedup_vs_fp64": fp64_ms / ms,
+            "schur_refactor_solve_ms": schur / k, "refactor_ms": ref / k, "refine_iters": iters / k,
+            "max_rel_residual": res,
+            "roofline": form_roofline(pd, prec, s.m, n_ref, ref / k, (fs - ref) / k, iters / k)}
+
+
 def time_forms(pd, sol, stream, args, fp64_ms, torch):
     """Every precision form of the region solve on the same scene and state:
     device-timed ms per step, PD iters/s, speedup over the FP64 form, the
@@ -137,25 +212,7 @@ def time_forms(pd, sol, stream, args, fp64_ms, torch):
                        ("bf16_ir (BF16 tcgen05, CG-refined)", pd.BF16_IR), ("pcg (contact-free preconditioner, cold start)", pd.PCG_WARM)):
         sol.set_state(*state)
         sol.set_precision(prec)
-        for _ in range(3):
-            sol.step(1)
-        schur = iters = res = 0.0
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(args.steps):
-            sol.step(1)
-            st = sol.stats()
-            schur += st["ms_contact_update"] + st["ms_factor_solve"]
-            iters += st["refine_iters"]
-            res = max(res, st["residual"])
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
-        out[name] = {"ms_per_step": ms, "value": 1e3 / ms, "unit": UNIT, "speedup_vs_fp64": fp64_ms / ms,
-                     "schur_refactor_solve_ms": schur / args.steps, "refine_iters": iters / args.steps,
-                     "max_rel_residual": res}
+        out[name] = time_form(pd, sol, stream, args, fp64_ms, torch, prec, False)
     # the nested Schur refactorisation on the contact-capable nodes (FP64 and split-TF32)
     con = sol._contacts
     npx = len(sol._scene.proxies)
@@ -167,25 +224,7 @@ def time_forms(pd, sol, stream, args, fp64_ms, torch):
         sol.set_precision(prec)
         sol.set_contact_nodes(sol._scene.proxies)
         sol.set_contacts(con.nodes, con.w, con.target, con.stiffness)
-        for _ in range(3):
-            sol.step(1)
-        schur = iters = res = 0.0
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(args.steps):
-            sol.step(1)
-            st = sol.stats()
-            schur += st["ms_contact_update"] + st["ms_factor_solve"]
-            iters += st["refine_iters"]
-            res = max(res, st["residual"])
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
-        out[name] = {"ms_per_step": ms, "value": 1e3 / ms, "unit": UNIT, "speedup_vs_fp64": fp64_ms / ms,
-                     "schur_refactor_solve_ms": schur / args.steps, "refine_iters": iters / args.steps,
-                     "max_rel_residual": res}
+        out[name] = time_form(pd, sol, stream, args, fp64_ms, torch, prec, True)
         sol.set_contact_nodes(None)
         sol.set_contacts(con.nodes, con.w, con.target, con.stiffness)
     out.update(time_learned(pd, sol, stream, args, fp64_ms, torch, state))
@@ -309,13 +348,14 @@ def time_learned(pd, sol, stream, args, fp64_ms, torch, state):
         sol.step(1)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    schur = it = res = 0.0
+    schur = it = res = fs = 0.0
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(args.steps):
         sol.step(1)
         st = sol.stats()
         schur += st["ms_contact_update"] + st["ms_factor_solve"]
+        fs += st["ms_factor_solve"]
         it += st["refine_iters"]
         res = max(res, st["residual"])
     e1.record(stream)
@@ -324,6 +364,7 @@ def time_learned(pd, sol, stream, args, fp64_ms, torch, state):
     return {"pcg_learned (network warm start)": {
         "ms_per_step": ms, "value": 1e3 / ms, "unit": UNIT, "speedup_vs_fp64": fp64_ms / ms,
         "schur_refactor_solve_ms": schur / args.steps, "refine_iters": it / args.steps, "max_rel_residual": res,
+        "roofline": form_roofline(pd, pd.PCG_WARM, s.m, s.m, 0.0, fs / args.steps, it / args.steps),
         "train_solves": args.train_solves, "train_steps": args.train_steps, "train_loss": loss,
         "generate_s": gen_s, "train_s": train_s,
         "heldout_err_vs_z0_start": mse_net / mse_zero if mse_zero > 0 else None,
@@ -427,7 +468,7 @@ def main():
         sol.close()
         return 0
     phase_keys = ["ms_local_alpha", "ms_forward", "ms_contact_update", "ms_local_beta", "ms_factor_solve",
-                  "ms_bookkeeping", "ms_backward"]
+                  "ms_bookkeeping", "ms_backward", "ms_refactor"]
     phases = {k: 0.0 for k in phase_keys}
     launches = 0
     if dist:

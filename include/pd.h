@@ -100,6 +100,7 @@ typedef struct {
     double ms_backward;       /* a7: sparse backward substitution                   */
     double ms_step;           /* whole pd_step                                      */
     int64_t kernel_launches;  /* kernels this library launched during the last pd_step */
+    double ms_refactor;       /* the refactorisation alone (part of ms_factor_solve; PCG forms: 0) */
 } pd_stats;
 
 typedef struct pd_solver pd_solver;

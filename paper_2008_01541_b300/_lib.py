@@ -44,7 +44,8 @@ class Stats(ctypes.Structure):
                [("refine_iters", ctypes.c_int), ("residual", ctypes.c_double), ("setup_ms", ctypes.c_double)] + \
                [(name, ctypes.c_double) for name in
                 ("ms_local_alpha", "ms_forward", "ms_contact_update", "ms_local_beta", "ms_factor_solve",
-                 "ms_bookkeeping", "ms_backward", "ms_step")] + [("kernel_launches", ctypes.c_int64)]
+                 "ms_bookkeeping", "ms_backward", "ms_step")] + [("kernel_launches", ctypes.c_int64),
+                                                                  ("ms_refactor", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

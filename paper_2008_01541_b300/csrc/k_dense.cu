@@ -464,18 +464,17 @@ __device__ __forceinline__ void wait_ge(const int* c, int target, int* status) {
   }
 }
 
-// Task list of one triangular solve over T block rows (in solve order b):
-// block row b holds its diagonal task, which also applies the update into
-// the next block row (the only update on the critical path), then the other
-// T - 2 - b updates; the last block row holds its diagonal task alone.
-__host__ __device__ inline int trsv_ntask(int T) { return T * (T - 1) / 2 + 1; }
-__device__ inline int trsv_start(int T, int b) { return b * (T - 1) - b * (b - 1) / 2; }
+// Update tasks of one triangular solve over T block rows (solve order b):
+// block row b applies y_i to the block rows two or more steps ahead (the
+// update into the adjacent row is done by the chain block itself).
+__host__ __device__ inline int trsv_ntask(int T) { return T >= 3 ? (T - 2) * (T - 1) / 2 : 0; }
+__device__ inline int trsv_start(int T, int b) { return b * (T - 2) - b * (b - 1) / 2; }
 __device__ inline void trsv_decode(int t, int T, int& b, int& q) {
-  const double d = 2.0 * T - 1.0;
+  const double d = 2.0 * T - 3.0;
   int e = (int)floor(0.5 * (d - sqrt(fmax(d * d - 8.0 * t, 0.0))));
-  e = max(0, min(e, T - 1));
+  e = max(0, min(e, T - 3));
   while (e > 0 && trsv_start(T, e) > t) --e;
-  while (e < T - 1 && trsv_start(T, e + 1) <= t) ++e;
+  while (e < T - 3 && trsv_start(T, e + 1) <= t) ++e;
   b = e;
   q = t - trsv_start(T, e);
 }
@@ -492,14 +491,17 @@ __device__ __forceinline__ void stage64(double (*tile)[LDA], const double* __res
 
 // One direction of the dense triangular solve with the tiled factor in H
 // (lower, column-major; diagonal tiles replaced by their inverses in Linv),
-// three right-hand sides.  Persistent grid; tasks claimed in list order (one
-// ahead), so every wait is on a task claimed earlier and the schedule cannot
-// deadlock.  Operand tiles are staged before the wait, since they do not
-// depend on the vectors.
-//   forward : w_i complete -> y_i = L_ii^-1 w_i; update (i, j>i): w_j -= L_ji y_i
-//   backward: w_i complete -> y_i = L_ii^-T w_i; update (i, j<i): w_j -= L_ij^T y_i
-// cnt[0] claims tasks, cnt[1 + j] counts the updates applied to w_j,
-// cnt[1 + T + i] flags y_i as written.
+// three right-hand sides, in one persistent launch.  The first block to
+// start becomes the chain: for every block row in solve order it subtracts
+// the adjacent row's contribution, applies the diagonal inverse and publishes
+// y_i, keeping y and the next tiles on chip (the tiles of step i + 1 are
+// loaded into registers while step i waits and computes).  The other blocks
+// claim the remaining updates in list order, so each waits only on the chain
+// or on tasks claimed before it and the schedule cannot deadlock.
+//   forward : y_i = L_ii^-1 (w_i - L_i,i-1 y_i-1); update (i, j >= i+2): w_j -= L_ji y_i
+//   backward: y_i = L_ii^-T (w_i - L_i+1,i^T y_i+1); update (i, j <= i-2): w_j -= L_ij^T y_i
+// cnt[0] claims updates, cnt[1 + j] counts the updates applied to w_j,
+// cnt[1 + T + i] flags y_i as written, cnt[1 + 2T] assigns the chain.
 template <bool FWD>
 __global__ void __launch_bounds__(256) k_trsv_tasks(const double* __restrict__ H, int64_t mp,
                                                     const double* __restrict__ Linv, double* w, double* y, int* cnt,
@@ -511,8 +513,83 @@ __global__ void __launch_bounds__(256) k_trsv_tasks(const double* __restrict__ H
   __shared__ double yv[TB][3];
   __shared__ int cur_t;
   const int T = (int)(mp / TB), tid = threadIdx.x;
-  const int ntask = trsv_ntask(T);
   const int r = tid / 3, v = tid % 3;          // output row / component (tid < 192)
+  if (tid == 0) cur_t = atomicAdd(cnt + 1 + 2 * T, 1);
+  __syncthreads();
+  const bool chain = cur_t == 0;
+  __syncthreads();
+  // adjacent tile feeding block row i: forward L_i,i-1, backward L_i+1,i (column-major in H)
+  auto adj_tile = [&](int i) {
+    return FWD ? H + (int64_t)i * TB + (int64_t)(i - 1) * TB * mp : H + (int64_t)(i + 1) * TB + (int64_t)i * TB * mp;
+  };
+  if (chain) {
+    double pa[16], pn[16];
+    auto fetch = [&](int i) {
+      const double* Li = Linv + (int64_t)i * TB * TB;
+      const bool has = FWD ? i > 0 : i < T - 1;
+      const double* An = has ? adj_tile(i) : nullptr;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int q = tid + 256 * k, rr = q % TB, cc = q / TB;
+        pa[k] = __ldg(Li + rr + cc * TB);
+        pn[k] = has ? __ldg(An + rr + (int64_t)cc * mp) : 0.0;
+      }
+    };
+    auto park = [&]() {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int q = tid + 256 * k, rr = q % TB, cc = q / TB;
+        ta[rr][cc] = pa[k];
+        tn[rr][cc] = pn[k];
+      }
+    };
+    fetch(FWD ? 0 : T - 1);
+    park();
+    for (int b = 0; b < T; ++b) {
+      const int i = FWD ? b : T - 1 - b;
+      if (b + 1 < T) fetch(FWD ? i + 1 : i - 1);       // in flight during this step
+      if (tid == 0) {
+        wait_ge(cnt + 1 + i, b >= 1 ? b - 1 : 0, status);
+        __threadfence();
+      }
+      __syncthreads();
+      if (tid < TB * 3) {
+        double acc = __ldcg(w + 3 * ((int64_t)i * TB) + tid);
+        if (b > 0) {
+          double s = 0.0;
+          if (FWD) {
+#pragma unroll 8
+            for (int c = 0; c < TB; ++c) s = fma(tn[r][c], yv[c][v], s);
+          } else {
+#pragma unroll 8
+            for (int c = 0; c < TB; ++c) s = fma(tn[c][r], yv[c][v], s);
+          }
+          acc -= s;
+        }
+        vec[r][v] = acc;
+      }
+      __syncthreads();
+      if (tid < TB * 3) {
+        double acc = 0.0;
+        if (FWD) {
+#pragma unroll 8
+          for (int c = 0; c <= r; ++c) acc = fma(ta[r][c], vec[c][v], acc);
+        } else {
+#pragma unroll 8
+          for (int c = r; c < TB; ++c) acc = fma(ta[c][r], vec[c][v], acc);
+        }
+        y[3 * ((int64_t)i * TB) + tid] = acc;
+        __threadfence();
+        yv[r][v] = acc;              // read again only in the next step's first phase
+      }
+      __syncthreads();
+      if (tid == 0) atomicAdd(cnt + 1 + T + i, 1);
+      if (b + 1 < T) park();
+      __syncthreads();
+    }
+    return;
+  }
+  const int ntask = trsv_ntask(T);
   int ahead = 0;
   if (tid == 0) ahead = atomicAdd(cnt, 1);
   for (;;) {
@@ -526,64 +603,30 @@ __global__ void __launch_bounds__(256) k_trsv_tasks(const double* __restrict__ H
     int b, q;
     trsv_decode(t, T, b, q);
     const int i = FWD ? b : T - 1 - b;
-    const bool diag = q == 0;
-    const int j = diag ? i : (FWD ? i + 1 + q : i - 1 - q);
-    const int jn = FWD ? i + 1 : i - 1;                      // the update fused into the diagonal task
-    const bool fused = diag && jn >= 0 && jn < T;
-    // forward update (i, j) reads L_ji, backward reads L_ij (column-major in H)
-    auto off_tile = [&](int jj) {
-      return FWD ? H + (int64_t)jj * TB + (int64_t)i * TB * mp : H + (int64_t)i * TB + (int64_t)jj * TB * mp;
-    };
-    stage64(ta, diag ? Linv + (int64_t)i * TB * TB : off_tile(j), diag ? TB : mp);
-    if (fused) stage64(tn, off_tile(jn), mp);
+    const int j = FWD ? i + 2 + q : i - 2 - q;
+    // forward update (i, j) reads L_ji, backward reads L_ij; staged before the wait
+    stage64(ta, FWD ? H + (int64_t)j * TB + (int64_t)i * TB * mp : H + (int64_t)i * TB + (int64_t)j * TB * mp, mp);
     if (tid == 0) {
-      if (diag) wait_ge(cnt + 1 + i, FWD ? i : T - 1 - i, status);
-      else wait_ge(cnt + 1 + T + i, 1, status);
+      wait_ge(cnt + 1 + T + i, 1, status);
       __threadfence();
     }
     __syncthreads();
-    if (tid < TB * 3) (&vec[0][0])[tid] = __ldcg((diag ? w : y) + 3 * ((int64_t)i * TB) + tid);
+    if (tid < TB * 3) (&vec[0][0])[tid] = __ldcg(y + 3 * ((int64_t)i * TB) + tid);
     __syncthreads();
     if (tid < TB * 3) {
       double acc = 0.0;
       if (FWD) {
-        const int c1 = diag ? r + 1 : TB;    // out[r] = sum_c ta[r][c] vec[c]  (diag: c <= r)
 #pragma unroll 8
-        for (int c = 0; c < c1; ++c) acc = fma(ta[r][c], vec[c][v], acc);
+        for (int c = 0; c < TB; ++c) acc = fma(ta[r][c], vec[c][v], acc);
       } else {
-        const int c0 = diag ? r : 0;         // out[r] = sum_c ta[c][r] vec[c]  (diag: c >= r)
 #pragma unroll 8
-        for (int c = c0; c < TB; ++c) acc = fma(ta[c][r], vec[c][v], acc);
+        for (int c = 0; c < TB; ++c) acc = fma(ta[c][r], vec[c][v], acc);
       }
-      if (diag) {
-        y[3 * ((int64_t)i * TB) + tid] = acc;
-        yv[r][v] = acc;
-      } else {
-        atomicAdd(w + 3 * ((int64_t)j * TB) + tid, -acc);
-      }
+      atomicAdd(w + 3 * ((int64_t)j * TB) + tid, -acc);
       __threadfence();
     }
     __syncthreads();
-    if (tid == 0) {
-      if (diag) atomicAdd(cnt + 1 + T + i, 1);
-      else atomicAdd(cnt + 1 + j, 1);
-    }
-    if (fused) {
-      if (tid < TB * 3) {
-        double acc = 0.0;
-        if (FWD) {
-#pragma unroll 8
-          for (int c = 0; c < TB; ++c) acc = fma(tn[r][c], yv[c][v], acc);
-        } else {
-#pragma unroll 8
-          for (int c = 0; c < TB; ++c) acc = fma(tn[c][r], yv[c][v], acc);
-        }
-        atomicAdd(w + 3 * ((int64_t)jn * TB) + tid, -acc);
-        __threadfence();
-      }
-      __syncthreads();
-      if (tid == 0) atomicAdd(cnt + 1 + jn, 1);
-    }
+    if (tid == 0) atomicAdd(cnt + 1 + j, 1);
   }
 }
 
@@ -685,9 +728,10 @@ void chol_solve_fp64_tasks(const double* H, int64_t mp, const double* Linv, cons
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trsv_tasks<true>, 256, smem);
-  const int grid = std::max(1, nsm * std::max(1, per));
   const int T = (int)(mp / TB);
   const int ntask = trsv_ntask(T);
+  // the chain block plus update blocks, all co-resident
+  const unsigned grid = (unsigned)std::max(1, std::min(nsm * std::max(1, per), 1 + ntask));
   double* w = work;
   double* y = work + 3 * mp;
   if (perm) {
@@ -697,13 +741,13 @@ void chol_solve_fp64_tasks(const double* H, int64_t mp, const double* Linv, cons
     k_pad_rhs<<<nblk(3 * mp, 256), 256, 0, st>>>(g, m, mp, w);
   }
   ++g_launches;
-  cudaMemsetAsync(cnt, 0, sizeof(int) * (1 + 2 * T), st);
-  k_trsv_tasks<true><<<(unsigned)std::min(grid, ntask), 256, smem, st>>>(H, mp, Linv, w, y, cnt, status);
+  cudaMemsetAsync(cnt, 0, sizeof(int) * (2 + 2 * T), st);
+  k_trsv_tasks<true><<<grid, 256, smem, st>>>(H, mp, Linv, w, y, cnt, status);
   ++g_launches;
   // backward on y (copied into w as the running right-hand side)
   cudaMemcpyAsync(w, y, sizeof(double) * 3 * mp, cudaMemcpyDeviceToDevice, st);
-  cudaMemsetAsync(cnt, 0, sizeof(int) * (1 + 2 * T), st);
-  k_trsv_tasks<false><<<(unsigned)std::min(grid, ntask), 256, smem, st>>>(H, mp, Linv, w, y, cnt, status);
+  cudaMemsetAsync(cnt, 0, sizeof(int) * (2 + 2 * T), st);
+  k_trsv_tasks<false><<<grid, 256, smem, st>>>(H, mp, Linv, w, y, cnt, status);
   ++g_launches;
   if (perm) {
     k_perm_gather<<<nblk(m, 256), 256, 0, st>>>(y, m, perm, u);

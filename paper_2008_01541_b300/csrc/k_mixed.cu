@@ -1064,7 +1064,7 @@ pd_status mixed_factor(pd_solver* s) {
       ++pdk::g_launches;
     }
     s->tend();
-    s->tbegin(4);
+    s->tbegin(8);
     factor_panels(s, f, mode, f.k0, (int)M->T);
     s->tend();
     return PD_OK;
@@ -1074,7 +1074,7 @@ pd_status mixed_factor(pd_solver* s) {
   s->tbegin(2);
   factor_cast(s, M->f, true);
   s->tend();
-  s->tbegin(4);
+  s->tbegin(8);
   factor_panels(s, M->f, mode);
   s->tend();
   return PD_OK;

@@ -101,15 +101,18 @@ void pd_solver::tend() {
   cudaEventRecord(events[marks.back().second + 1], stream);
 }
 
-void pd_solver::tcollect(double* out /*[8]*/) {
-  for (int i = 0; i < 8; ++i) out[i] = 0.0;
-  // phase 7 (network inference) is reported inside phase 4
+void pd_solver::tcollect(double* out /*[9]*/) {
+  for (int i = 0; i < 9; ++i) out[i] = 0.0;
+  // phase 7 (network inference) is reported inside phase 4; phase 8 (the
+  // refactorisation) both inside phase 4 and on its own
   if (!opt.timing) return;
   cudaStreamSynchronize(stream);
+  cudaStreamSynchronize(fstream);
   for (auto& mk : marks) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, events[mk.second], events[mk.second + 1]);
-    out[mk.first == 7 ? 4 : mk.first] += ms;
+    out[mk.first == 7 || mk.first == 8 ? 4 : mk.first] += ms;
+    if (mk.first == 8) out[8] += ms;
   }
   marks.clear();
   ev_used = 0;
@@ -188,7 +191,7 @@ pd_status pd_solver::refactor() {
     pdk::block_copy(H, mp, off, Sp, ntr, true, stream);
     pdk::contact_scatter(k, c_idx, c_w, c_s, H, mp, stream, pdk::CSLOTS, d_perm);
     tend();
-    tbegin(4);
+    tbegin(8);
     pdk::cholesky_fp64(H, mp, Linv, status, stream, &la, nk0, (int)(mp / 64));
     tend();
   } else if (precision == PD_FP64) {
@@ -196,7 +199,7 @@ pd_status pd_solver::refactor() {
     pdk::copy_sigma(Sigma0, m, H, mp, stream);
     pdk::contact_scatter(k, c_idx, c_w, c_s, H, mp, stream);
     tend();
-    tbegin(4);
+    tbegin(8);
     pdk::cholesky_fp64(H, mp, Linv, status, stream, &la);
     tend();
   } else {
@@ -482,10 +485,11 @@ pd_status pd_schur_solve(pd_solver* s, const double* g, const double* u0, double
   CK(cudaMemcpyAsync(s->g, g, sizeof(double) * 3 * s->m, cudaMemcpyHostToDevice, s->stream));
   if (u0) CK(cudaMemcpyAsync(s->u0, u0, sizeof(double) * 3 * s->m, cudaMemcpyHostToDevice, s->stream));
   pd_status r = pd_schur_solve_dev(s, s->g, u0 ? s->u0 : nullptr, s->u2);
-  double ph[8];
+  double ph[9];
   s->tcollect(ph);
   s->stats.ms_contact_update = ph[2];
   s->stats.ms_factor_solve = ph[4];
+  s->stats.ms_refactor = ph[8];
   if (r != PD_OK) return r;
   CK(cudaMemcpyAsync(u, s->u2, sizeof(double) * 3 * s->m, cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
@@ -898,7 +902,7 @@ pd_status pd_solver::upload(const pdh::Setup& h, const pdh::Input& in) {
   CK(cudaMemset(u_last, 0, sizeof(double) * 3 * m));
   X_rest_h.assign(in.X, in.X + 3 * n);
   CK(dalloc(s, &work, 6 * mp));
-  CK(dalloc(s, &trsv_cnt, 1 + 2 * (mp / 64)));
+  CK(dalloc(s, &trsv_cnt, 2 + 2 * (mp / 64)));
   CK(dalloc(s, &status, 4));
   sf.status = status;
   CK(cudaMemset(status, 0, sizeof(int) * 4));
@@ -1033,12 +1037,12 @@ pd_status pd_solver::step(int outer_iters, pd_contact_cb cb, void* user) {
     cudaStreamSynchronize(stream);
     return result;
   }
-  double ph[8];
+  double ph[9];
   prefactored = false;
   tcollect(ph);
   stats.ms_local_alpha = ph[0]; stats.ms_forward = ph[1]; stats.ms_contact_update = ph[2];
   stats.ms_local_beta = ph[3]; stats.ms_factor_solve = ph[4]; stats.ms_bookkeeping = ph[5];
-  stats.ms_backward = ph[6];
+  stats.ms_backward = ph[6]; stats.ms_refactor = ph[8];
   CK(cudaStreamSynchronize(stream));
   stats.ms_step = now_ms() - t0;
   stats.inner_done = inner_total;
