@@ -66,19 +66,34 @@ __global__ void k_contact_forces(int64_t k, int ns, const int32_t* __restrict__ 
   }
 }
 
+// Named barrier among the first `n` threads of the block: the producer
+// arrives without waiting, the consumers wait.
+__device__ __forceinline__ void bar_arrive(int id, int n) { asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+__device__ __forceinline__ void bar_wait(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+
 // Factor the diagonal tile (kt, kt) in shared memory (FP64), blocked by 16
-// columns: one warp factors each 16 x 16 diagonal block in registers (lane =
-// row), one thread per row solves the panel below it, all threads apply the
-// 16-column trailing update.  Only L_kk is formed here; its inverse is built
-// for all tiles at once after the factorisation (k_chol_inv), off the
-// sequential chain.  On B300 one SM retires 2 FP64 FMAs per clock, so this
-// tile (64^3/6 FMAs) costs at least ~11 us.
+// columns.  On B300 one SM retires 2 FP64 FMAs per clock, a quarter of that
+// per sub-partition, and a warp's FP64 instruction holds its sub-partition's
+// unit for 64 clocks whatever its active lanes; so the work is spread over
+// the four sub-partitions and the serial pivot chain is kept short:
+//  (a) 16 x 16 diagonal block: warps 0-3 each hold four of its columns in
+//      registers (lane = row); the owner of pivot j first applies pivot j-1
+//      to column j, factors it and publishes it (named barrier, the producer
+//      only arrives); pivot j-1 reaches the other columns afterwards, off the
+//      chain;
+//  (b) panel below: two rows per warp, lane = column, forward substitution
+//      on the unscaled x_j with the block's columns pre-divided by their
+//      pivots (x_t -= x_j L_tj / L_jj), one scaling at the end;
+//  (c) trailing update of the lower part: all threads, one entry each.
+// Only L_kk is formed; the inverses for the solves come from k_chol_inv.
 constexpr int LDA = TB + 1;   // padded column stride of a shared 64 x 64 tile
 __global__ void __launch_bounds__(256) k_chol_diag(double* __restrict__ H, int64_t mp, int kt,
                                                    int* __restrict__ status) {
   __shared__ double A[TB * LDA];   // column-major, A[c * LDA + r]
+  __shared__ double colb[16][16];  // published columns of the current block: colb[j][i] = L(c0 + i, c0 + j)
+  __shared__ double lt[16][16];    // lt[j][t] = L(c0 + t, c0 + j) / L(c0 + j, c0 + j) for t > j, else 0
   __shared__ double rinv[TB];
-  const int tid = threadIdx.x, lane = tid & 31;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   double* Ht = H + (int64_t)kt * TB + (int64_t)kt * TB * mp;
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
@@ -89,66 +104,86 @@ __global__ void __launch_bounds__(256) k_chol_diag(double* __restrict__ H, int64
 #pragma unroll 1
   for (int p = 0; p < 4; ++p) {
     const int c0 = 16 * p;
-    if (tid < 16) {
-      // 16 x 16 diagonal block on a half warp, lane = row
-      const int i = lane;
-      double a[16];
+    if (w < 4) {
+      // (a) columns w, w + 4, w + 8, w + 12 of the block; lanes 16-31 mirror rows 0-15
+      const int i = lane & 15;
+      double a[4];
 #pragma unroll
-      for (int t = 0; t < 16; ++t) a[t] = A[(c0 + t) * LDA + c0 + i];
+      for (int s = 0; s < 4; ++s) a[s] = A[(c0 + w + 4 * s) * LDA + c0 + i];
       unsigned bad = 0;
-      double my_rinv = 1.0;
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
-        double djj = __shfl_sync(0x0000ffffu, a[j], j, 16);
-        const bool b = !(djj > 0.0) || !isfinite(djj);
-        bad |= (unsigned)b << j;
-        djj = b ? 1.0 : djj;
-        const double rs = rsqrt(djj);      // 1 / L_jj
-        if (i == j) { a[j] = djj * rs; my_rinv = rs; }
-        if (i > j) a[j] *= rs;
+        const int sj = j >> 2;
+        if (w == (j & 3)) {
+          // register-only selection of slot sj (no local-memory array)
+          double cur = sj == 0 ? a[0] : sj == 1 ? a[1] : sj == 2 ? a[2] : a[3];
+          if (j > 0) cur = fma(-colb[j - 1][i], colb[j - 1][j], cur);
+          double d = __shfl_sync(0xffffffffu, cur, j);
+          const bool b = !(d > 0.0) || !isfinite(d);
+          bad |= (unsigned)b << j;
+          d = b ? 1.0 : d;
+          const double rs = rsqrt(d);
+          const double v = i > j ? cur * rs : (i == j ? d * rs : 0.0);
 #pragma unroll
-        for (int c = j + 1; c < 16; ++c) {
-          const double lcj = __shfl_sync(0x0000ffffu, a[j], c, 16);
-          if (i >= c) a[c] = fma(-a[j], lcj, a[c]);
+          for (int s2 = 0; s2 < 4; ++s2) a[s2] = s2 == sj ? v : a[s2];
+          if (lane < 16) {
+            colb[j][i] = v;
+            if (i == j) rinv[c0 + j] = rs;
+          }
+          __syncwarp();
+          bar_arrive(1 + (j & 7), 128);
+        }
+        if (j > 0) {
+          // pivot j - 1 on this warp's columns after j
+#pragma unroll
+          for (int s = 0; s < 4; ++s) {
+            const int c = w + 4 * s;
+            if (c > j) a[s] = fma(-colb[j - 1][i], colb[j - 1][c], a[s]);
+          }
+        }
+        if (w != (j & 3)) bar_wait(1 + (j & 7), 128);
+      }
+      if (lane < 16) {
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          const int c = w + 4 * s;
+          if (i >= c) A[(c0 + c) * LDA + c0 + i] = a[s];
         }
       }
-#pragma unroll
-      for (int t = 0; t < 16; ++t)
-        if (t <= i) A[(c0 + t) * LDA + c0 + i] = a[t];
-      rinv[c0 + i] = my_rinv;
       if (bad && lane == 0) atomicCAS(status, 0, kt * TB + c0 + __ffs(bad));
     }
     __syncthreads();
     const int nb = TB - c0 - 16;
-    if (tid < nb) {
-      // panel row c0 + 16 + tid: x L_D^T = a, right-looking
-      const int row = c0 + 16 + tid;
-      double x[16];
+    if (nb > 0) {
+      // (b) rows c0 + 16 .. 63: X L_D^T = A_panel
+      lt[tid >> 4][tid & 15] = (tid & 15) > (tid >> 4) ? colb[tid >> 4][tid & 15] * rinv[c0 + (tid >> 4)] : 0.0;
+      __syncthreads();
+      const int t = lane & 15, h = lane >> 4;
+      for (int pr = w; 2 * pr < nb; pr += 8) {
+        const int row = c0 + 16 + 2 * pr + h;
+        double x = A[(c0 + t) * LDA + row];
 #pragma unroll
-      for (int t = 0; t < 16; ++t) x[t] = A[(c0 + t) * LDA + row];
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        x[j] *= rinv[c0 + j];
-#pragma unroll
-        for (int t = j + 1; t < 16; ++t) x[t] = fma(-x[j], A[(c0 + j) * LDA + c0 + t], x[t]);
+        for (int j = 0; j < 16; ++j) {
+          const double xj = __shfl_sync(0xffffffffu, x, (h << 4) + j);
+          x = fma(-xj, lt[j][t], x);
+        }
+        A[(c0 + t) * LDA + row] = x * rinv[c0 + t];
       }
+      __syncthreads();
+      // (c) trailing update of rows / columns >= c0 + 16 (lower part), one
+      // entry per thread step: q runs over the nb (nb + 1) / 2 lower entries
+      for (int q = tid; q < nb * (nb + 1) / 2; q += 256) {
+        int c = (int)((sqrtf((float)(8 * q + 1)) - 1.f) * 0.5f);   // row of the triangle (entry q)
+        while (c * (c + 1) / 2 > q) --c;
+        while ((c + 1) * (c + 2) / 2 <= q) ++c;
+        const int r = c0 + 16 + c, cc = c0 + 16 + (q - c * (c + 1) / 2);
+        double acc = 0.0;
 #pragma unroll
-      for (int t = 0; t < 16; ++t) A[(c0 + t) * LDA + row] = x[t];
+        for (int t2 = 0; t2 < 16; ++t2) acc = fma(A[(c0 + t2) * LDA + r], A[(c0 + t2) * LDA + cc], acc);
+        A[cc * LDA + r] -= acc;
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    // trailing update of rows / columns >= c0 + 16 (lower part), one entry
-    // per thread step: q runs over the nb (nb + 1) / 2 lower entries
-    for (int q = tid; q < nb * (nb + 1) / 2; q += 256) {
-      int c = (int)((sqrtf((float)(8 * q + 1)) - 1.f) * 0.5f);   // row of the triangle (entry q)
-      while (c * (c + 1) / 2 > q) --c;
-      while ((c + 1) * (c + 2) / 2 <= q) ++c;
-      const int r = c0 + 16 + c, cc = c0 + 16 + (q - c * (c + 1) / 2);
-      double acc = 0.0;
-#pragma unroll
-      for (int t = 0; t < 16; ++t) acc = fma(A[(c0 + t) * LDA + r], A[(c0 + t) * LDA + cc], acc);
-      A[cc * LDA + r] -= acc;
-    }
-    __syncthreads();
   }
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
@@ -207,90 +242,92 @@ __device__ __forceinline__ void tile_mma(const double* As, const double* Bs, int
 }
 
 // L_ik = A_ik L_kk^-T for tiles i > kt by forward substitution: CTA
-// (blockIdx.x / 4) takes tile i = kt + 1 + blockIdx.x / 4, rows
-// 16 * (blockIdx.x % 4) .. + 15, held in shared memory; four threads per row.
-// At step j the first thread of the row scales x_j, then the four threads
-// eliminate it from the columns t > j, t = j + 1 + q (mod 4) -- no predicated
-// FP64 work, which matters on a part that retires 2 FP64 FMAs per SM clock.
-__global__ void __launch_bounds__(64) k_chol_trsm(double* __restrict__ H, int64_t mp, int kt) {
-  __shared__ double Lk[TB * LDA];   // L_kk, column-major
-  __shared__ double X[16 * LDA];    // the 16 rows, X[r * LDA + t]
+// (blockIdx.x / 16) takes tile i = kt + 1 + blockIdx.x / 16, rows
+// 4 * (blockIdx.x % 16) .. + 3, one warp per row with columns lane and
+// lane + 32 in registers.  Column j of L_kk is staged divided by L_jj and
+// zero on and above the diagonal, so every step is the same unpredicated
+// FMAs on the still unscaled x_j (x_t -= x_j L_tj / L_jj, exact in order),
+// and x is scaled by 1 / L_tt once at the end.  One warp per SM sub-partition:
+// on B300 a warp's FP64 instruction occupies its sub-partition's FP64 unit
+// for 64 clocks whatever its active lanes, so this keeps the chain short.
+__global__ void __launch_bounds__(128) k_chol_trsm(double* __restrict__ H, int64_t mp, int kt) {
+  __shared__ double Ls[TB * TB];   // Ls[j * TB + t] = L_tj / L_jj for t > j, else 0
   __shared__ double rinv[TB];
-  const int tid = threadIdx.x;
-  const int r = tid >> 2, q = tid & 3;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const double* Lt = H + (int64_t)kt * TB + (int64_t)kt * TB * mp;
-  const int64_t it = kt + 1 + blockIdx.x / 4;
-  double* Ai = H + it * TB + 16 * (blockIdx.x % 4) + (int64_t)kt * TB * mp;   // slice, column-major
-  for (int idx = tid; idx < TB * TB; idx += 64) {
-    const int rr = idx % TB, cc = idx / TB;
-    Lk[cc * LDA + rr] = Lt[rr + (int64_t)cc * mp];
-  }
-  for (int idx = tid; idx < 16 * TB; idx += 64) {
-    const int rr = idx % 16, cc = idx / 16;
-    X[rr * LDA + cc] = Ai[rr + (int64_t)cc * mp];
+  const int64_t it = kt + 1 + blockIdx.x / 16;
+  const int row = 4 * (blockIdx.x % 16) + w;
+  double* Ai = H + it * TB + row + (int64_t)kt * TB * mp;   // column c of this row at c * mp
+  double x0 = Ai[(int64_t)lane * mp], x1 = Ai[(int64_t)(lane + 32) * mp];
+  if (tid < TB) rinv[tid] = 1.0 / Lt[tid + (int64_t)tid * mp];
+  __syncthreads();
+#pragma unroll 16
+  for (int k = 0; k < TB * TB / 128; ++k) {
+    const int q = tid + 128 * k, t = q % TB, j = q / TB;
+    Ls[q] = t > j ? Lt[t + (int64_t)j * mp] * rinv[j] : 0.0;
   }
   __syncthreads();
-  rinv[tid] = 1.0 / Lk[tid * LDA + tid];
-  __syncthreads();
-  double* x = X + r * LDA;
-#pragma unroll 1
-  for (int j = 0; j < TB; ++j) {
-    if (q == 0) x[j] *= rinv[j];
-    __syncwarp();
-    const double xj = x[j];
-    const double* Lj = Lk + j * LDA;
-    for (int t = j + 1 + q; t < TB; t += 4) x[t] = fma(-xj, Lj[t], x[t]);
-    __syncwarp();
+#pragma unroll 8
+  for (int j = 0; j < 32; ++j) {
+    const double xj = __shfl_sync(0xffffffffu, x0, j);
+    x0 = fma(-xj, Ls[j * TB + lane], x0);
+    x1 = fma(-xj, Ls[j * TB + 32 + lane], x1);
   }
-  __syncthreads();
-  for (int idx = tid; idx < 16 * TB; idx += 64) {
-    const int rr = idx % 16, cc = idx / 16;
-    Ai[rr + (int64_t)cc * mp] = X[rr * LDA + cc];
+#pragma unroll 8
+  for (int j = 32; j < TB; ++j) {
+    const double xj = __shfl_sync(0xffffffffu, x1, j - 32);
+    x1 = fma(-xj, Ls[j * TB + 32 + lane], x1);
   }
+  Ai[(int64_t)lane * mp] = x0 * rinv[lane];
+  Ai[(int64_t)(lane + 32) * mp] = x1 * rinv[lane + 32];
 }
 
-// Column update of the look-ahead: rows 16 * (blockIdx.x % 4) .. + 15 of tile
-// (kt + 1 + blockIdx.x / 4, kt + 1) -= L_ik L_(kt+1)k^T.
-__global__ void __launch_bounds__(256) k_chol_colupd(double* __restrict__ H, int64_t mp, int kt) {
-  __shared__ double As[TB * 17];   // As[t * 17 + r]: the 16 rows of L_ik
-  __shared__ double Bs[TB * LDA];  // Bs[t * LDA + c]: L_(kt+1)k
-  const int tid = threadIdx.x;
-  const int64_t it = kt + 1 + blockIdx.x / 4, jt = kt + 1;
-  const int r0 = 16 * (blockIdx.x % 4);
-  const double* Li = H + it * TB + r0 + (int64_t)kt * TB * mp;
+// Column update of the look-ahead: rows 4 * (blockIdx.x % 16) .. + 3 of tile
+// (kt + 1 + blockIdx.x / 16, kt + 1) -= L_ik L_(kt+1)k^T; one warp per row,
+// output columns lane and lane + 32.
+__global__ void __launch_bounds__(128) k_chol_colupd(double* __restrict__ H, int64_t mp, int kt) {
+  __shared__ double Bs[TB * LDA];  // Bs[t * LDA + c] = L_(kt+1)k (row c, column t)
+  __shared__ double As[4][TB];     // the CTA's 4 rows of L_ik
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int64_t it = kt + 1 + blockIdx.x / 16, jt = kt + 1;
+  const int row = 4 * (blockIdx.x % 16) + w;
   const double* Lj = H + jt * TB + (int64_t)kt * TB * mp;
-  for (int idx = tid; idx < 16 * TB; idx += 256) {
-    const int rr = idx % 16, t = idx / 16;
-    As[t * 17 + rr] = Li[rr + (int64_t)t * mp];
+  const double* Li = H + it * TB + row + (int64_t)kt * TB * mp;
+#pragma unroll 16
+  for (int k = 0; k < TB * TB / 128; ++k) {
+    const int q = tid + 128 * k, c = q % TB, t = q / TB;
+    Bs[t * LDA + c] = Lj[c + (int64_t)t * mp];
   }
-  for (int idx = tid; idx < TB * TB; idx += 256) {
-    const int cc = idx % TB, t = idx / TB;
-    Bs[t * LDA + cc] = Lj[cc + (int64_t)t * mp];
-  }
+  As[w][lane] = Li[(int64_t)lane * mp];
+  As[w][lane + 32] = Li[(int64_t)(lane + 32) * mp];
   __syncthreads();
-  const int rr = tid % 16, cg = tid / 16;   // row, column group (columns cg + 16 e)
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  double a0 = 0.0, a1 = 0.0;
 #pragma unroll 8
   for (int t = 0; t < TB; ++t) {
-    const double a = As[t * 17 + rr];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) acc[e] = fma(a, Bs[t * LDA + cg + 16 * e], acc[e]);
+    const double at = As[w][t];
+    a0 = fma(at, Bs[t * LDA + lane], a0);
+    a1 = fma(at, Bs[t * LDA + lane + 32], a1);
   }
-  double* Aij = H + it * TB + r0 + rr + jt * TB * mp;
-#pragma unroll
-  for (int e = 0; e < 4; ++e) Aij[(int64_t)(cg + 16 * e) * mp] -= acc[e];
+  double* Aij = H + it * TB + row + jt * TB * mp;
+  Aij[(int64_t)lane * mp] -= a0;
+  Aij[(int64_t)(lane + 32) * mp] -= a1;
 }
 
 // A_ij -= L_ik L_jk^T for the tiles selected by the launch: lower != 0 ->
 // tiles it0 + ii, jt0 + jj with jj <= ii (triangular numbering); else an
-// n_i x n_j rectangle starting at (it0, jt0).
+// n_i x n_j rectangle starting at (it0, jt0).  S CTAs share a tile, each
+// taking 64 / S of its rows, so that small trailing matrices still spread
+// over the SMs (one SM retires a 64 x 64 x 64 FP64 tile in ~65 us).
+template <int S>
 __global__ void __launch_bounds__(256) k_chol_update(double* __restrict__ H, int64_t mp, int kt, int it0, int jt0,
                                                      int n_j, int lower) {
+  constexpr int R = TB / S, RA = R / 16;
   extern __shared__ double sm[];
-  double* As = sm;
-  double* Bs = sm + TB * TB;
+  double* As = sm;            // As[t * R + r]: the CTA's rows of L_ik
+  double* Bs = sm + TB * R;   // Bs[t * TB + c]: L_jk
   const int tid = threadIdx.x;
-  int64_t idx = blockIdx.x, ii, jj;
+  int64_t idx = blockIdx.x / S, ii, jj;
+  const int r0 = R * (int)(blockIdx.x % S);
   if (lower) {
     ii = (int64_t)((sqrt(8.0 * (double)idx + 1.0) - 1.0) * 0.5);
     while ((ii + 1) * (ii + 2) / 2 <= idx) ++ii;
@@ -301,22 +338,53 @@ __global__ void __launch_bounds__(256) k_chol_update(double* __restrict__ H, int
     jj = idx % n_j;
   }
   const int64_t it = it0 + ii, jt = jt0 + jj;
-  const double* Li = H + it * TB + (int64_t)kt * TB * mp;
+  const double* Li = H + it * TB + r0 + (int64_t)kt * TB * mp;
   const double* Lj = H + jt * TB + (int64_t)kt * TB * mp;
-  for (int q = tid; q < TB * TB; q += 256) {
-    int r = q % TB, t = q / TB;
+  for (int q = tid; q < R * TB; q += 256) {
+    const int r = q % R, t = q / R;
     As[q] = Li[r + (int64_t)t * mp];
-    Bs[q] = Lj[r + (int64_t)t * mp];
+  }
+  for (int q = tid; q < TB * TB; q += 256) {
+    const int c = q % TB, t = q / TB;
+    Bs[q] = Lj[c + (int64_t)t * mp];
   }
   __syncthreads();
-  int tr = tid % 16, tc = tid / 16;
-  double acc[4][4] = {};
-  tile_mma(As, Bs, tr, tc, acc);
-  double* Aij = H + it * TB + jt * TB * mp;
+  const int tr = tid % 16, tc = tid / 16;
+  double acc[RA][4] = {};
+#pragma unroll 8
+  for (int t = 0; t < TB; ++t) {
+    double a[RA], b[4];
 #pragma unroll
-  for (int p = 0; p < 4; ++p)
+    for (int p = 0; p < RA; ++p) a[p] = As[t * R + tr + 16 * p];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) b[q] = Bs[t * TB + tc + 16 * q];
+#pragma unroll
+    for (int p = 0; p < RA; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[p][q] = fma(a[p], b[q], acc[p][q]);
+  }
+  double* Aij = H + it * TB + r0 + jt * TB * mp;
+#pragma unroll
+  for (int p = 0; p < RA; ++p)
 #pragma unroll
     for (int q = 0; q < 4; ++q) Aij[(tr + 16 * p) + (int64_t)(tc + 16 * q) * mp] -= acc[p][q];
+}
+
+// Lower-triangular trailing update of n x n tiles from (t0, t0) with panel kt,
+// sliced so that the launch has at least two CTAs per SM where it can.
+void launch_update(double* H, int64_t mp, int kt, int t0, int n, cudaStream_t st) {
+  const int64_t tiles = (int64_t)n * (n + 1) / 2;
+  if (tiles <= 0) return;
+  if (tiles >= 296) {
+    k_chol_update<1><<<(unsigned)tiles, 256, 2 * TB * TB * sizeof(double), st>>>(H, mp, kt, t0, t0, 0, 1);
+  } else if (tiles >= 148) {
+    k_chol_update<2><<<(unsigned)(2 * tiles), 256, (TB / 2 + TB) * TB * sizeof(double), st>>>(H, mp, kt, t0, t0,
+                                                                                              0, 1);
+  } else {
+    k_chol_update<4><<<(unsigned)(4 * tiles), 256, (TB / 4 + TB) * TB * sizeof(double), st>>>(H, mp, kt, t0, t0,
+                                                                                              0, 1);
+  }
+  ++g_launches;
 }
 
 // Forward step kt: y_k = Linv_kk w_k (block 0 stores it), w_i -= L_ik y_k for i = kt + blockIdx.x
@@ -671,7 +739,11 @@ void cholesky_fp64(double* H, int64_t mp, double* Linv, int* status, cudaStream_
                    int k_end) {
   static std::atomic<unsigned long long> attr{0};
   const int smem = 2 * TB * TB * sizeof(double);
-  if (first_on_device(attr)) cudaFuncSetAttribute(k_chol_update, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (first_on_device(attr)) {
+    cudaFuncSetAttribute(k_chol_update<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_chol_update<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_chol_update<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  }
   const int T = (int)(mp / TB);
   if (k_end < 0 || k_end > T) k_end = T;
   if (k_begin >= k_end) return;
@@ -681,10 +753,9 @@ void cholesky_fp64(double* H, int64_t mp, double* Linv, int* status, cudaStream_
       ++g_launches;
       int n = T - k - 1;
       if (n <= 0) break;
-      k_chol_trsm<<<4 * n, 64, 0, st>>>(H, mp, k);
+      k_chol_trsm<<<16 * n, 128, 0, st>>>(H, mp, k);
       ++g_launches;
-      k_chol_update<<<(unsigned)((int64_t)n * (n + 1) / 2), 256, smem, st>>>(H, mp, k, k + 1, k + 1, 0, 1);
-      ++g_launches;
+      launch_update(H, mp, k, k + 1, n, st);
     }
   } else {
     // Depth-1 look-ahead: the main stream factors tile k, solves panel k and
@@ -696,17 +767,14 @@ void cholesky_fp64(double* H, int64_t mp, double* Linv, int* status, cudaStream_
       ++g_launches;
       int n = T - k - 1;
       if (n <= 0) break;
-      k_chol_trsm<<<4 * n, 64, 0, st>>>(H, mp, k);
+      k_chol_trsm<<<16 * n, 128, 0, st>>>(H, mp, k);
       ++g_launches;
       cudaEventRecord(la->ev_panel[k], st);
       if (k > k_begin) cudaStreamWaitEvent(st, la->ev_rest[k - 1], 0);
-      k_chol_colupd<<<4 * n, 256, 0, st>>>(H, mp, k);
+      k_chol_colupd<<<16 * n, 128, 0, st>>>(H, mp, k);
       ++g_launches;
       cudaStreamWaitEvent(la->side, la->ev_panel[k], 0);
-      if (n > 1) {
-        k_chol_update<<<(unsigned)((int64_t)(n - 1) * n / 2), 256, smem, la->side>>>(H, mp, k, k + 2, k + 2, 0, 1);
-        ++g_launches;
-      }
+      launch_update(H, mp, k, k + 2, n - 1, la->side);
       cudaEventRecord(la->ev_rest[k], la->side);
     }
     const int last = k_end == T ? T - 2 : k_end - 1;   // the last step that recorded ev_rest
