@@ -119,11 +119,14 @@ __global__ void __launch_bounds__(256) k_chol_diag(double* __restrict__ H, int64
           double cur = sj == 0 ? a[0] : sj == 1 ? a[1] : sj == 2 ? a[2] : a[3];
           if (j > 0) cur = fma(-colb[j - 1][i], colb[j - 1][j], cur);
           double d = __shfl_sync(0xffffffffu, cur, j);
-          const bool b = !(d > 0.0) || !isfinite(d);
+          // positive and finite, tested on the exponent bits (integer unit,
+          // not the FP64 pipe); a zero or subnormal pivot counts as failed
+          const int hi = __double2hiint(d);
+          const bool b = hi < 0x00100000 || hi >= 0x7ff00000;
           bad |= (unsigned)b << j;
           d = b ? 1.0 : d;
           const double rs = rsqrt(d);
-          const double v = i > j ? cur * rs : (i == j ? d * rs : 0.0);
+          const double v = i >= j ? (b && i == j ? 1.0 : cur) * rs : 0.0;   // row j: cur = d, so L_jj = d / sqrt(d)
 #pragma unroll
           for (int s2 = 0; s2 < 4; ++s2) a[s2] = s2 == sj ? v : a[s2];
           if (lane < 16) {
