@@ -6,7 +6,11 @@
 // and columns m..mp-1 hold an identity block, so every tile is full.
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "kernels.h"
+
+namespace cg = cooperative_groups;
 
 namespace pdk {
 namespace {
@@ -562,104 +566,123 @@ __device__ __forceinline__ void stage64(double (*tile)[LDA], const double* __res
 
 // One direction of the dense triangular solve with the tiled factor in H
 // (lower, column-major; diagonal tiles replaced by their inverses in Linv),
-// three right-hand sides, in one persistent launch.  The first block to
-// start becomes the chain: for every block row in solve order it subtracts
-// the adjacent row's contribution, applies the diagonal inverse and publishes
-// y_i, keeping y and the next tiles on chip (the tiles of step i + 1 are
-// loaded into registers while step i waits and computes).  The other blocks
+// three right-hand sides, in one persistent launch of 4-CTA clusters.  The
+// first cluster to start becomes the chain: for every block row in solve
+// order its four CTAs (16 rows each, on four SMs, since one SM retires only
+// 2 FP64 FMAs per clock) subtract the adjacent row's contribution, exchange
+// the 64 x 3 right-hand side through distributed shared memory, apply the
+// diagonal inverse and exchange y_i, keeping y on chip; the next step's row
+// slices are loaded into registers during the current one.  The other CTAs
 // claim the remaining updates in list order, so each waits only on the chain
 // or on tasks claimed before it and the schedule cannot deadlock.
 //   forward : y_i = L_ii^-1 (w_i - L_i,i-1 y_i-1); update (i, j >= i+2): w_j -= L_ji y_i
 //   backward: y_i = L_ii^-T (w_i - L_i+1,i^T y_i+1); update (i, j <= i-2): w_j -= L_ij^T y_i
 // cnt[0] claims updates, cnt[1 + j] counts the updates applied to w_j,
-// cnt[1 + T + i] flags y_i as written, cnt[1 + 2T] assigns the chain.
+// cnt[1 + T + i] counts the chain CTAs that wrote y_i, cnt[1 + 2T] assigns
+// the chain.
+constexpr int CK = 4;            // CTAs of the chain cluster
+constexpr int CR = TB / CK;      // rows per chain CTA
 template <bool FWD>
-__global__ void __launch_bounds__(256) k_trsv_tasks(const double* __restrict__ H, int64_t mp,
-                                                    const double* __restrict__ Linv, double* w, double* y, int* cnt,
-                                                    int* status) {
+__global__ void __cluster_dims__(CK, 1, 1) __launch_bounds__(256)
+    k_trsv_tasks(const double* __restrict__ H, int64_t mp, const double* __restrict__ Linv, double* w, double* y,
+                 int* cnt, int* status) {
   extern __shared__ double trsv_smem[];
-  double (*ta)[LDA] = reinterpret_cast<double (*)[LDA]>(trsv_smem);
-  double (*tn)[LDA] = reinterpret_cast<double (*)[LDA]>(trsv_smem + TB * LDA);
-  __shared__ double vec[TB][3];
-  __shared__ double yv[TB][3];
-  __shared__ int cur_t;
+  __shared__ double yfull[TB][3];   // y of the previous chain step (all 64 rows)
+  __shared__ double vfull[TB][3];   // right-hand side of the current diagonal step
+  __shared__ int cur_t, role;
   const int T = (int)(mp / TB), tid = threadIdx.x;
-  const int r = tid / 3, v = tid % 3;          // output row / component (tid < 192)
-  if (tid == 0) cur_t = atomicAdd(cnt + 1 + 2 * T, 1);
-  __syncthreads();
-  const bool chain = cur_t == 0;
-  __syncthreads();
-  // adjacent tile feeding block row i: forward L_i,i-1, backward L_i+1,i (column-major in H)
-  auto adj_tile = [&](int i) {
-    return FWD ? H + (int64_t)i * TB + (int64_t)(i - 1) * TB * mp : H + (int64_t)(i + 1) * TB + (int64_t)i * TB * mp;
-  };
+  cg::cluster_group cl = cg::this_cluster();
+  const unsigned rank = cl.block_rank();
+  if (rank == 0 && tid == 0) role = atomicAdd(cnt + 1 + 2 * T, 1);
+  cl.sync();
+  const bool chain = *cl.map_shared_rank(&role, 0) == 0;
+  cl.sync();    // rank 0's shared memory stays alive until every CTA has read it
   if (chain) {
-    double pa[16], pn[16];
+    // this CTA's output rows r0 .. r0 + 15 of every block row; sa / sn hold
+    // the operand rows of the diagonal inverse / the adjacent tile so that
+    // out[rr] = sum_c s[rr][c] vec[c] in both directions
+    double (*sa)[LDA] = reinterpret_cast<double (*)[LDA]>(trsv_smem);
+    double (*sn)[LDA] = reinterpret_cast<double (*)[LDA]>(trsv_smem + CR * LDA);
+    const int r0 = CR * (int)rank;
+    double pa[4], pn[4];
     auto fetch = [&](int i) {
       const double* Li = Linv + (int64_t)i * TB * TB;
       const bool has = FWD ? i > 0 : i < T - 1;
-      const double* An = has ? adj_tile(i) : nullptr;
+      // forward: rows of L_i,i-1 and of Linv_ii; backward: columns of L_i+1,i and of Linv_ii
+      const double* An = !has ? nullptr
+                         : FWD ? H + (int64_t)i * TB + (int64_t)(i - 1) * TB * mp
+                               : H + (int64_t)(i + 1) * TB + (int64_t)i * TB * mp;
 #pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const int q = tid + 256 * k, rr = q % TB, cc = q / TB;
-        pa[k] = __ldg(Li + rr + cc * TB);
-        pn[k] = has ? __ldg(An + rr + (int64_t)cc * mp) : 0.0;
+      for (int k = 0; k < 4; ++k) {
+        const int e = tid + 256 * k, rr = e % CR, c = e / CR;   // FWD: coalesced down a column
+        const int f = tid + 256 * k, c2 = f % TB, rr2 = f / TB; // BWD: coalesced down a column
+        if (FWD) {
+          pa[k] = __ldg(Li + (r0 + rr) + c * TB);
+          pn[k] = has ? __ldg(An + (r0 + rr) + (int64_t)c * mp) : 0.0;
+        } else {
+          pa[k] = __ldg(Li + c2 + (r0 + rr2) * TB);
+          pn[k] = has ? __ldg(An + c2 + (int64_t)(r0 + rr2) * mp) : 0.0;
+        }
       }
     };
     auto park = [&]() {
 #pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const int q = tid + 256 * k, rr = q % TB, cc = q / TB;
-        ta[rr][cc] = pa[k];
-        tn[rr][cc] = pn[k];
+      for (int k = 0; k < 4; ++k) {
+        const int e = tid + 256 * k;
+        const int rr = FWD ? e % CR : e / TB, c = FWD ? e / CR : e % TB;
+        sa[rr][c] = pa[k];
+        sn[rr][c] = pn[k];
       }
     };
+    // output (rr, v) of the slice, contraction quarter q4 = lanes of a group of 4
+    const int g = tid >> 2, q4 = tid & 3, rr = g / 3, v = g % 3;
+    const bool act = tid < 3 * CR * 4;
     fetch(FWD ? 0 : T - 1);
     park();
+    __syncthreads();
     for (int b = 0; b < T; ++b) {
       const int i = FWD ? b : T - 1 - b;
-      if (b + 1 < T) fetch(FWD ? i + 1 : i - 1);       // in flight during this step
+      if (b + 1 < T) fetch(FWD ? i + 1 : i - 1);         // in flight during this step
       if (tid == 0) {
         wait_ge(cnt + 1 + i, b >= 1 ? b - 1 : 0, status);
         __threadfence();
       }
       __syncthreads();
-      if (tid < TB * 3) {
-        double acc = __ldcg(w + 3 * ((int64_t)i * TB) + tid);
-        if (b > 0) {
-          double s = 0.0;
-          if (FWD) {
-#pragma unroll 8
-            for (int c = 0; c < TB; ++c) s = fma(tn[r][c], yv[c][v], s);
-          } else {
-#pragma unroll 8
-            for (int c = 0; c < TB; ++c) s = fma(tn[c][r], yv[c][v], s);
-          }
-          acc -= s;
-        }
-        vec[r][v] = acc;
+      double acc = 0.0;
+      if (act && b > 0) {
+#pragma unroll
+        for (int c = 16 * q4; c < 16 * q4 + 16; ++c) acc = fma(sn[rr][c], yfull[c][v], acc);
       }
-      __syncthreads();
-      if (tid < TB * 3) {
-        double acc = 0.0;
-        if (FWD) {
-#pragma unroll 8
-          for (int c = 0; c <= r; ++c) acc = fma(ta[r][c], vec[c][v], acc);
-        } else {
-#pragma unroll 8
-          for (int c = r; c < TB; ++c) acc = fma(ta[c][r], vec[c][v], acc);
-        }
-        y[3 * ((int64_t)i * TB) + tid] = acc;
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+      if (act && q4 == 0) {
+        const double val = __ldcg(w + 3 * ((int64_t)i * TB + r0 + rr) + v) - acc;
+#pragma unroll
+        for (int d = 0; d < CK; ++d) cl.map_shared_rank(&vfull[0][0], d)[3 * (r0 + rr) + v] = val;
+      }
+      cl.sync();
+      acc = 0.0;
+      if (act) {
+#pragma unroll
+        for (int c = 16 * q4; c < 16 * q4 + 16; ++c) acc = fma(sa[rr][c], vfull[c][v], acc);
+      }
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+      if (act && q4 == 0) {
+        y[3 * ((int64_t)i * TB + r0 + rr) + v] = acc;
         __threadfence();
-        yv[r][v] = acc;              // read again only in the next step's first phase
+#pragma unroll
+        for (int d = 0; d < CK; ++d) cl.map_shared_rank(&yfull[0][0], d)[3 * (r0 + rr) + v] = acc;
       }
       __syncthreads();
       if (tid == 0) atomicAdd(cnt + 1 + T + i, 1);
       if (b + 1 < T) park();
-      __syncthreads();
+      cl.sync();    // yfull complete in every CTA, vfull and sa / sn free
     }
     return;
   }
+  double (*ta)[LDA] = reinterpret_cast<double (*)[LDA]>(trsv_smem);
+  const int r = tid / 3, v = tid % 3;          // output row / component (tid < 192)
   const int ntask = trsv_ntask(T);
   int ahead = 0;
   if (tid == 0) ahead = atomicAdd(cnt, 1);
@@ -678,20 +701,20 @@ __global__ void __launch_bounds__(256) k_trsv_tasks(const double* __restrict__ H
     // forward update (i, j) reads L_ji, backward reads L_ij; staged before the wait
     stage64(ta, FWD ? H + (int64_t)j * TB + (int64_t)i * TB * mp : H + (int64_t)i * TB + (int64_t)j * TB * mp, mp);
     if (tid == 0) {
-      wait_ge(cnt + 1 + T + i, 1, status);
+      wait_ge(cnt + 1 + T + i, CK, status);
       __threadfence();
     }
     __syncthreads();
-    if (tid < TB * 3) (&vec[0][0])[tid] = __ldcg(y + 3 * ((int64_t)i * TB) + tid);
+    if (tid < TB * 3) yfull[r][v] = __ldcg(y + 3 * ((int64_t)i * TB) + tid);
     __syncthreads();
     if (tid < TB * 3) {
       double acc = 0.0;
       if (FWD) {
 #pragma unroll 8
-        for (int c = 0; c < TB; ++c) acc = fma(ta[r][c], vec[c][v], acc);
+        for (int c = 0; c < TB; ++c) acc = fma(ta[r][c], yfull[c][v], acc);
       } else {
 #pragma unroll 8
-        for (int c = 0; c < TB; ++c) acc = fma(ta[c][r], vec[c][v], acc);
+        for (int c = 0; c < TB; ++c) acc = fma(ta[c][r], yfull[c][v], acc);
       }
       atomicAdd(w + 3 * ((int64_t)j * TB) + tid, -acc);
       __threadfence();
@@ -790,19 +813,30 @@ void cholesky_fp64(double* H, int64_t mp, double* Linv, int* status, cudaStream_
 void chol_solve_fp64_tasks(const double* H, int64_t mp, const double* Linv, const double* g, double* u,
                            int64_t m, double* work, int* cnt, int* status, cudaStream_t st, const int32_t* perm) {
   static std::atomic<unsigned long long> attr{0};
-  const int smem = 2 * TB * LDA * sizeof(double);
+  const int smem = TB * LDA * sizeof(double);
   if (first_on_device(attr)) {
     cudaFuncSetAttribute(k_trsv_tasks<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(k_trsv_tasks<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   }
-  int dev = 0, nsm = 0, per = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trsv_tasks<true>, 256, smem);
+  static std::atomic<int> clusters{0};
+  if (clusters.load() == 0) {
+    // co-resident 4-CTA clusters of this kernel on the device
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CK * 256);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, k_trsv_tasks<true>, &cfg) != cudaSuccess || nc < 1) {
+      cudaGetLastError();
+      nc = 1;
+    }
+    clusters.store(nc);
+  }
   const int T = (int)(mp / TB);
   const int ntask = trsv_ntask(T);
-  // the chain block plus update blocks, all co-resident
-  const unsigned grid = (unsigned)std::max(1, std::min(nsm * std::max(1, per), 1 + ntask));
+  // the chain cluster plus update CTAs, all co-resident, in whole clusters
+  const int want = CK + ntask;
+  const unsigned grid = (unsigned)(CK * std::max(1, std::min(clusters.load(), (want + CK - 1) / CK)));
   double* w = work;
   double* y = work + 3 * mp;
   if (perm) {
