@@ -88,7 +88,8 @@ typedef struct {
     int refine_iters;                         /* refinement / PCG iterations: summed over the
                                                  solves of the last pd_step, or of the last
                                                  pd_schur_solve */
-    double residual;                          /* ||g - H u|| / ||g|| of the last solve */
+    double residual;                          /* ||g - H u|| / ||g|| of the last solve
+                                                 (-1: not measured, the direct FP64 form) */
     double setup_ms;                          /* wall time of pd_setup               */
     /* per-phase device time of the last pd_step (timing != 0), milliseconds:      */
     double ms_local_alpha;    /* a1: alpha polar + forces + gather                  */

@@ -53,7 +53,8 @@ struct MixedState {
   double* sc = nullptr;       // device scalars: [0] r.r  [1] r.z  [2] p.q  [3] r.z old  [4] g.g
   double* sc_h = nullptr;     // pinned copy
   float *w = nullptr, *uo = nullptr;   // [mq][3] triangular-solve vectors
-  int* pcnt = nullptr;        // preconditioner task counters [1 + 2T]
+  int* pcnt = nullptr;        // preconditioner scratch: task counters [2 + 4T], then facc, bacc
+  float *facc = nullptr, *bacc = nullptr;   // [mq][3] accumulated block products (forward / backward)
   int pc_grid = 0;            // persistent grid of the preconditioner
   cudaStream_t side = nullptr;              // low-priority stream for the bulk trailing updates
   std::vector<cudaEvent_t> ev_panel, ev_rest;
@@ -513,15 +514,18 @@ __global__ void __launch_bounds__(128) k_trsm_f32(float* __restrict__ L, float* 
 // E_k = Dinv_k^T Dinv_k the block substitutions need no dense diagonal solve:
 //   forward : w_i = D r_i - sum_{k < i} Lh_ik w_k
 //   backward: u_k = E_k w_k - sum_{i > k} Lh_ik^T u_i
-// Tasks are 32-row slices of a block row (forward, i ascending) and 32-column
-// slices of a block column (backward, k descending), claimed in that order
-// from an atomic counter by a persistent grid.  A task waits, per block it
-// needs, for the four slices of that block to be done (counters cnt[1 + k]
-// forward, cnt[1 + T + k] backward); every wait is on an earlier task, so the
-// grid cannot stall, and every wait is bounded (code 301 in status[1]).
-constexpr int PS = 32;                 // rows / columns per task
-constexpr int NSL = NB / PS;           // slices per block
-
+// One persistent launch.  The first CTA to start is the chain: it walks the
+// block rows (forward, then backward), each step applying only the adjacent
+// block (Lh_i,i-1 w_i-1, resp. Lh_k+1,k^T u_k+1) to the accumulated sum,
+// with the previous block's vector kept in shared memory and the next
+// adjacent tile loaded into registers during the step.  The other CTAs claim,
+// in list order, the non-adjacent block products (forward by block column,
+// then E_k w_k for every k, then backward by block row) and add them into the
+// accumulators facc / bacc with FP32 atomics.  Each task waits only on the
+// chain or on tasks earlier in the list, so the grid cannot stall; every wait
+// is bounded (code 301 in status[1]).
+// cnt: [0] task claims, [1] chain role, [2 + k] w_k written, [2 + T + k] u_k
+// written, [2 + 2T + i] products added into facc_i, [2 + 3T + k] into bacc_k.
 __device__ __forceinline__ unsigned long long ptimer() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
@@ -540,130 +544,292 @@ __device__ __forceinline__ void wait_at_least(const int* c, int target, int* sta
   }
 }
 
+// block b of a staircase task list over T blocks: block b holds T - 2 - b tasks
+__device__ inline int pc_start(int T, int b) { return b * (T - 2) - b * (b - 1) / 2; }
+__device__ inline void pc_decode(int t, int T, int& b, int& q) {
+  const double dd = 2.0 * T - 3.0;
+  int e = (int)floor(0.5 * (dd - sqrt(fmax(dd * dd - 8.0 * t, 0.0))));
+  e = max(0, min(e, T - 3));
+  while (e > 0 && pc_start(T, e) > t) --e;
+  while (e < T - 3 && pc_start(T, e + 1) <= t) ++e;
+  b = e;
+  q = t - pc_start(T, e);
+}
+
+// Row products: thread (g = tid >> 3, c8 = tid & 7) holds rows g + 32 j
+// (j < 4), columns 16 c8 .. + 15 of a row-major 128 x 128 block, so a warp's
+// 16-byte loads cover four 128-byte lines.  The vector is kept per component
+// with entry c at c + 4 (c >> 4) (VSW floats a component), which spreads the
+// eight column groups over distinct banks.
+constexpr int VSW = NB + 4 * (NB / 16);
+__device__ __forceinline__ int vs_pos(int c) { return c + 4 * (c >> 4); }
+
+__device__ __forceinline__ void load_rows4(float (&l)[64], const float* p, int64_t ld) {
+  const int g = threadIdx.x >> 3, c8 = threadIdx.x & 7;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(p + (int64_t)(g + 32 * j) * ld + 16 * c8) + q);
+      l[16 * j + 4 * q] = v.x; l[16 * j + 4 * q + 1] = v.y; l[16 * j + 4 * q + 2] = v.z; l[16 * j + 4 * q + 3] = v.w;
+    }
+}
+
+// a[j][v] = sum_c block[g + 32 j][c] x_v[c], complete in every lane of the group of 8
+__device__ __forceinline__ void rows4_dot(const float (&l)[64], const float (*vs)[VSW], float (&a)[4][3]) {
+  const int c8 = threadIdx.x & 7;
+  const float *x0 = vs[0] + 20 * c8, *x1 = vs[1] + 20 * c8, *x2 = vs[2] + 20 * c8;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    a[j][0] = a[j][1] = a[j][2] = 0.f;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      a[j][0] = fmaf(l[16 * j + c], x0[c], a[j][0]);
+      a[j][1] = fmaf(l[16 * j + c], x1[c], a[j][1]);
+      a[j][2] = fmaf(l[16 * j + c], x2[c], a[j][2]);
+    }
+  }
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int v = 0; v < 3; ++v) a[j][v] += __shfl_xor_sync(0xffffffffu, a[j][v], o);
+}
+
+// the 128 x 3 block of x (global, interleaved) into the per-component layout
+__device__ __forceinline__ void load_vs(float (*vs)[VSW], const float* x) {
+  for (int e = threadIdx.x; e < NB * 3; e += 256) vs[e % 3][vs_pos(e / 3)] = __ldcg(x + e);
+}
+
+// L2 prefetch of the 128 x 128 block at p (row-major, leading dimension ld):
+// thread (row tid >> 1, half tid & 1) touches the two 128-byte lines of its
+// 64 entries, so a later register load of the block hits L2
+__device__ __forceinline__ void prefetch_block(const float* p, int64_t ld) {
+  const float* q = p + (int64_t)(threadIdx.x >> 1) * ld + 64 * (threadIdx.x & 1);
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(q));
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(q + 32));
+}
+
+// column c of a row-major block (rows h * 64 .. + 63, leading dimension ld)
+__device__ __forceinline__ void load_col64(float (&l)[64], const float* p, int64_t ld) {
+#pragma unroll
+  for (int q = 0; q < 64; ++q) l[q] = __ldg(p + (int64_t)q * ld);
+}
+
+// facc = D r in factor order (zero on the padding rows), bacc = 0
+__global__ void k_pc_pre(int64_t mq, int64_t m, const double* __restrict__ d, const double* __restrict__ r,
+                         const int32_t* __restrict__ iperm, float* __restrict__ facc, float* __restrict__ bacc) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= 3 * mq) return;
+  const int64_t row = q / 3;
+  float v = 0.f;
+  if (row < m) {
+    const int64_t ri = iperm ? iperm[row] : row;   // region index of this factor row
+    v = (float)(d[ri] * r[3 * ri + q % 3]);
+  }
+  facc[q] = v;
+  bacc[q] = 0.f;
+}
+
+// z = D u back in region order
+__global__ void k_pc_post(int64_t m, const double* __restrict__ d, const float* __restrict__ uo,
+                          const int32_t* __restrict__ iperm, double* __restrict__ z) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= 3 * m) return;
+  const int64_t col = q / 3;
+  const int64_t ci = iperm ? iperm[col] : col;
+  z[3 * ci + q % 3] = d[ci] * (double)uo[q];
+}
+
 __global__ void __launch_bounds__(256) k_precond(const float* __restrict__ Lh, const float* __restrict__ E,
-                                                 int64_t mq, int64_t m, const double* __restrict__ d,
-                                                 const double* __restrict__ r, double* __restrict__ z, float* w,
-                                                 float* uo, int* cnt, int* status, const int32_t* __restrict__ iperm) {
-  __shared__ float vk[NB * 3];
-  __shared__ float red[8][PS][3];
+                                                 int64_t mq, float* w, float* uo, float* facc, float* bacc, int* cnt,
+                                                 int* status) {
+  __shared__ float vs[2][3][VSW];   // row products: previous / current block vector (chain), the operand (tasks)
+  __shared__ float vb[2][NB][3];    // column products: the same
+  __shared__ float red[2][NB][3];   // half sums of the column products
   __shared__ int cur;
-  const int T = (int)(mq / NB), ntask = 2 * T * NSL, tid = threadIdx.x;
+  const int T = (int)(mq / NB), tid = threadIdx.x;
+  const int g8 = tid >> 3, c8 = tid & 7;          // row products: rows g8 + 32 j, column group c8
+  const int cc = tid & (NB - 1), hc = tid >> 7;   // column products: column, half of the rows
+  if (tid == 0) cur = atomicAdd(cnt + 1, 1);
+  __syncthreads();
+  const bool chain = cur == 0;
+  __syncthreads();
+  float l[64];
+  if (chain) {
+    int pb = 0;   // vs[pb] / vb[pb] hold the previous block's vector
+    if (T > 1) load_rows4(l, Lh + (int64_t)NB * mq, mq);
+    // ---- forward: w_i = facc_i - Lh_i,i-1 w_i-1 (facc_i starts as D r_i); lane c8 = j < 4
+    // of a group of 8 finishes row g8 + 32 j
+    const int rj = g8 + 32 * (c8 & 3);
+    for (int i = 0; i < T; ++i) {
+      if (tid == 0) {
+        wait_at_least(cnt + 2 + 2 * T + i, i >= 1 ? i - 1 : 0, status, ptimer());
+        __threadfence();
+      }
+      __syncthreads();
+      const float* fa = facc + 3 * ((int64_t)i * NB + rj);
+      float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+      if (c8 < 4) { f0 = __ldcg(fa); f1 = __ldcg(fa + 1); f2 = __ldcg(fa + 2); }   // in flight during the dot
+      float a[4][3];
+      if (i > 0) {
+        rows4_dot(l, vs[pb], a);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) a[j][0] = a[j][1] = a[j][2] = 0.f;
+      }
+      if (c8 < 4) {
+        // a[c8], selected without indexing a register array
+        const float s0 = c8 == 0 ? a[0][0] : c8 == 1 ? a[1][0] : c8 == 2 ? a[2][0] : a[3][0];
+        const float s1 = c8 == 0 ? a[0][1] : c8 == 1 ? a[1][1] : c8 == 2 ? a[2][1] : a[3][1];
+        const float s2 = c8 == 0 ? a[0][2] : c8 == 1 ? a[1][2] : c8 == 2 ? a[2][2] : a[3][2];
+        const float w0 = f0 - s0, w1 = f1 - s1, w2 = f2 - s2;
+        float* wr = w + 3 * ((int64_t)i * NB + rj);
+        wr[0] = w0; wr[1] = w1; wr[2] = w2;
+        const int ps = vs_pos(rj);
+        vs[pb ^ 1][0][ps] = w0; vs[pb ^ 1][1][ps] = w1; vs[pb ^ 1][2][ps] = w2;
+        __threadfence();
+      }
+      if (i + 1 < T)   // next step's adjacent tile, in flight from here
+        load_rows4(l, Lh + (int64_t)(i + 1) * NB * mq + (int64_t)i * NB, mq);
+      if (i + 2 < T) prefetch_block(Lh + (int64_t)(i + 2) * NB * mq + (int64_t)(i + 1) * NB, mq);
+      __syncthreads();
+      if (tid == 0) atomicAdd(cnt + 2 + i, 1);
+      pb ^= 1;
+    }
+    // ---- backward: u_k = bacc_k - Lh_k+1,k^T u_k+1 (bacc_k holds E_k w_k and the other products)
+    for (int k = T - 1; k >= 0; --k) {
+      if (tid == 0) {
+        wait_at_least(cnt + 2 + 3 * T + k, 1 + (T - 2 - k > 0 ? T - 2 - k : 0), status, ptimer());
+        __threadfence();
+      }
+      __syncthreads();
+      const int64_t col = (int64_t)k * NB + cc;
+      const float* ba = bacc + 3 * col;
+      float b0 = 0.f, b1 = 0.f, b2 = 0.f;
+      if (hc == 0) { b0 = __ldcg(ba); b1 = __ldcg(ba + 1); b2 = __ldcg(ba + 2); }   // in flight during the dot
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+      if (k < T - 1) {
+#pragma unroll
+        for (int q = 0; q < 64; ++q) {
+          const float* x = vb[pb][64 * hc + q];
+          a0 = fmaf(l[q], x[0], a0); a1 = fmaf(l[q], x[1], a1); a2 = fmaf(l[q], x[2], a2);
+        }
+      }
+      red[hc][cc][0] = a0; red[hc][cc][1] = a1; red[hc][cc][2] = a2;
+      __syncthreads();
+      if (hc == 0) {
+        const float u0 = b0 - (red[0][cc][0] + red[1][cc][0]);
+        const float u1 = b1 - (red[0][cc][1] + red[1][cc][1]);
+        const float u2 = b2 - (red[0][cc][2] + red[1][cc][2]);
+        float* uc = uo + 3 * col;
+        uc[0] = u0; uc[1] = u1; uc[2] = u2;
+        vb[pb ^ 1][cc][0] = u0; vb[pb ^ 1][cc][1] = u1; vb[pb ^ 1][cc][2] = u2;
+        __threadfence();
+      }
+      if (k > 0)   // column cc of Lh_k,k-1, rows hc * 64 .. + 63
+        load_col64(l, Lh + ((int64_t)k * NB + 64 * hc) * mq + (int64_t)(k - 1) * NB + cc, mq);
+      if (k > 1) prefetch_block(Lh + (int64_t)(k - 1) * NB * mq + (int64_t)(k - 2) * NB, mq);
+      __syncthreads();
+      if (tid == 0) atomicAdd(cnt + 2 + T + k, 1);
+      pb ^= 1;
+    }
+    return;
+  }
+  const int nF = T >= 3 ? (T - 2) * (T - 1) / 2 : 0, ntask = 2 * nF + T;
   for (;;) {
     if (tid == 0) cur = atomicAdd(cnt, 1);
     __syncthreads();
     const int t = cur;
     if (t >= ntask) break;
-    if (t < T * NSL) {
-      // ---- forward slice: rows R0 .. R0 + 31 of block row i
-      const int i = t / NSL;
-      const int64_t R0 = (int64_t)i * NB + (int64_t)(t % NSL) * PS;
-      const int rr = tid >> 3, cc = tid & 7;           // row, 16-column chunk
-      const float* Lrow = Lh + (R0 + rr) * mq + cc * 16;
+    if (t < nF || t >= nF + T) {
+      const bool fwd = t < nF;
+      int b, q;
+      pc_decode(fwd ? t : t - nF - T, T, b, q);
       float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-      for (int k = 0; k < i; ++k) {
-        float4 l[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) l[q] = __ldg(reinterpret_cast<const float4*>(Lrow + (int64_t)k * NB) + q);
+      if (fwd) {
+        // facc_i -= Lh_ik w_k, k = b, i = k + 2 + q
+        const int k = b, i = k + 2 + q;
+        load_rows4(l, Lh + (int64_t)i * NB * mq + (int64_t)k * NB, mq);
         if (tid == 0) {
-          wait_at_least(cnt + 1 + k, NSL, status, ptimer());
+          wait_at_least(cnt + 2 + k, 1, status, ptimer());
           __threadfence();
         }
         __syncthreads();
-        for (int q = tid; q < NB * 3; q += 256) vk[q] = __ldcg(w + 3 * (int64_t)k * NB + q);
+        load_vs(vs[0], w + 3 * (int64_t)k * NB);
         __syncthreads();
-        const float* v = vk + 3 * cc * 16;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float lv[4] = {l[q].x, l[q].y, l[q].z, l[q].w};
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int c = 4 * q + e;
-            a0 = fmaf(lv[e], v[3 * c], a0); a1 = fmaf(lv[e], v[3 * c + 1], a1); a2 = fmaf(lv[e], v[3 * c + 2], a2);
-          }
+        float a[4][3];
+        rows4_dot(l, vs[0], a);
+        if (c8 < 4) {
+          float* fa = facc + 3 * ((int64_t)i * NB + g8 + 32 * c8);
+          const float s0 = c8 == 0 ? a[0][0] : c8 == 1 ? a[1][0] : c8 == 2 ? a[2][0] : a[3][0];
+          const float s1 = c8 == 0 ? a[0][1] : c8 == 1 ? a[1][1] : c8 == 2 ? a[2][1] : a[3][1];
+          const float s2 = c8 == 0 ? a[0][2] : c8 == 1 ? a[1][2] : c8 == 2 ? a[2][2] : a[3][2];
+          atomicAdd(fa, -s0); atomicAdd(fa + 1, -s1); atomicAdd(fa + 2, -s2);
+          __threadfence();
         }
-      }
-#pragma unroll
-      for (int o = 1; o < 8; o <<= 1) {
-        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-      }
-      if (cc == 0) {
-        const int64_t row = R0 + rr;
-        float* wr = w + 3 * row;
-        if (row < m) {
-          const int64_t ri = iperm ? iperm[row] : row;   // region index of this factor row
-          const double dr = d[ri];
-          wr[0] = (float)(dr * r[3 * ri]) - a0;
-          wr[1] = (float)(dr * r[3 * ri + 1]) - a1;
-          wr[2] = (float)(dr * r[3 * ri + 2]) - a2;
-        } else {
-          wr[0] = -a0; wr[1] = -a1; wr[2] = -a2;
+        __syncthreads();
+        if (tid == 0) atomicAdd(cnt + 2 + 2 * T + i, 1);
+      } else {
+        // bacc_k -= Lh_ik^T u_i, i = T - 1 - b, k = i - 2 - q
+        const int i = T - 1 - b, k = i - 2 - q;
+        load_col64(l, Lh + ((int64_t)i * NB + 64 * hc) * mq + (int64_t)k * NB + cc, mq);
+        if (tid == 0) {
+          wait_at_least(cnt + 2 + T + i, 1, status, ptimer());
+          __threadfence();
         }
-        __threadfence();
+        __syncthreads();
+        for (int e = tid; e < NB * 3; e += 256) (&vb[0][0][0])[e] = __ldcg(uo + 3 * (int64_t)i * NB + e);
+        __syncthreads();
+#pragma unroll
+        for (int q2 = 0; q2 < 64; ++q2) {
+          const float* x = vb[0][64 * hc + q2];
+          a0 = fmaf(l[q2], x[0], a0); a1 = fmaf(l[q2], x[1], a1); a2 = fmaf(l[q2], x[2], a2);
+        }
+        red[hc][cc][0] = a0; red[hc][cc][1] = a1; red[hc][cc][2] = a2;
+        __syncthreads();
+        if (hc == 0) {
+          float* ba = bacc + 3 * ((int64_t)k * NB + cc);
+          atomicAdd(ba, -(red[0][cc][0] + red[1][cc][0]));
+          atomicAdd(ba + 1, -(red[0][cc][1] + red[1][cc][1]));
+          atomicAdd(ba + 2, -(red[0][cc][2] + red[1][cc][2]));
+          __threadfence();
+        }
+        __syncthreads();
+        if (tid == 0) atomicAdd(cnt + 2 + 3 * T + k, 1);
       }
-      __syncthreads();
-      if (tid == 0) atomicAdd(cnt + 1 + i, 1);
     } else {
-      // ---- backward slice: columns C0 .. C0 + 31 of block column k
-      const int tb = t - T * NSL, k = T - 1 - tb / NSL, sl = tb % NSL;
-      const int64_t C0 = (int64_t)k * NB + (int64_t)sl * PS;
-      const int cc = tid & 31, rc = tid >> 5;          // column, 16-row chunk
-      float e[16];
-      const float* Ek = E + (int64_t)k * NB * NB + (int64_t)(rc * 16) * NB + sl * PS + cc;
-#pragma unroll
-      for (int q = 0; q < 16; ++q) e[q] = __ldg(Ek + (int64_t)q * NB);   // E_k symmetric: row c = column c
+      // bacc_k += E_k w_k (E_k symmetric, row-major), k = T - 1 - (t - nF)
+      const int k = T - 1 - (t - nF);
+      load_rows4(l, E + (int64_t)k * NB * NB, NB);
       if (tid == 0) {
-        wait_at_least(cnt + 1 + k, NSL, status, ptimer());
+        wait_at_least(cnt + 2 + k, 1, status, ptimer());
         __threadfence();
       }
       __syncthreads();
-      for (int q = tid; q < NB * 3; q += 256) vk[q] = __ldcg(w + 3 * (int64_t)k * NB + q);
+      load_vs(vs[0], w + 3 * (int64_t)k * NB);
       __syncthreads();
-      float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const float* v = vk + 3 * (rc * 16 + q);
-        a0 = fmaf(e[q], v[0], a0); a1 = fmaf(e[q], v[1], a1); a2 = fmaf(e[q], v[2], a2);
-      }
-      for (int i = T - 1; i > k; --i) {
-        float l[16];
-        const float* Lc = Lh + ((int64_t)i * NB + rc * 16) * mq + C0 + cc;
-#pragma unroll
-        for (int q = 0; q < 16; ++q) l[q] = __ldg(Lc + (int64_t)q * mq);
-        if (tid == 0) {
-          wait_at_least(cnt + 1 + T + i, NSL, status, ptimer());
-          __threadfence();
-        }
-        __syncthreads();
-        for (int q = tid; q < NB * 3; q += 256) vk[q] = __ldcg(uo + 3 * (int64_t)i * NB + q);
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const float* v = vk + 3 * (rc * 16 + q);
-          a0 = fmaf(-l[q], v[0], a0); a1 = fmaf(-l[q], v[1], a1); a2 = fmaf(-l[q], v[2], a2);
-        }
-      }
-      red[rc][cc][0] = a0; red[rc][cc][1] = a1; red[rc][cc][2] = a2;
-      __syncthreads();
-      if (tid < PS) {
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) { s0 += red[q][tid][0]; s1 += red[q][tid][1]; s2 += red[q][tid][2]; }
-        const int64_t col = C0 + tid;
-        float* uc = uo + 3 * col;
-        uc[0] = s0; uc[1] = s1; uc[2] = s2;
-        if (col < m) {
-          const int64_t ci = iperm ? iperm[col] : col;
-          const double dc = d[ci];
-          z[3 * ci] = dc * (double)s0; z[3 * ci + 1] = dc * (double)s1; z[3 * ci + 2] = dc * (double)s2;
-        }
+      float a[4][3];
+      rows4_dot(l, vs[0], a);
+      if (c8 < 4) {
+        float* ba = bacc + 3 * ((int64_t)k * NB + g8 + 32 * c8);
+        const float s0 = c8 == 0 ? a[0][0] : c8 == 1 ? a[1][0] : c8 == 2 ? a[2][0] : a[3][0];
+        const float s1 = c8 == 0 ? a[0][1] : c8 == 1 ? a[1][1] : c8 == 2 ? a[2][1] : a[3][1];
+        const float s2 = c8 == 0 ? a[0][2] : c8 == 1 ? a[1][2] : c8 == 2 ? a[2][2] : a[3][2];
+        atomicAdd(ba, s0); atomicAdd(ba + 1, s1); atomicAdd(ba + 2, s2);
         __threadfence();
       }
       __syncthreads();
-      if (tid == 0) atomicAdd(cnt + 1 + T + k, 1);
+      if (tid == 0) atomicAdd(cnt + 2 + 3 * T + k, 1);
     }
+    __syncthreads();
   }
+}
+
+// bytes of the preconditioner scratch: counters, then the two accumulators
+inline size_t pc_scratch_bytes(int64_t T, int64_t mq) {
+  return ((sizeof(int) * (2 + 4 * T) + 15) & ~(size_t)15) + 2 * sizeof(float) * 3 * mq;
 }
 
 // z = Minv0 r (FP32 dense symmetric inverse, 3 right-hand sides), one warp per row.
@@ -848,9 +1014,14 @@ static pd_status ensure_state(pd_solver* s) {
       A((void**)&M->uo, sizeof(float) * 3 * mq) || A((void**)&M->Shi, sizeof(float) * m * m) ||
       A((void**)&M->Slo, sizeof(float) * m * m) || A((void**)&M->vhi, sizeof(float) * 3 * m) ||
       A((void**)&M->vlo, sizeof(float) * 3 * m) || A((void**)&M->r32, sizeof(float) * 3 * m) ||
-      A((void**)&M->pcnt, sizeof(int) * (1 + 2 * M->T))) {
+      A((void**)&M->pcnt, pc_scratch_bytes(M->T, mq))) {
     s->err = "device allocation for the mixed-precision vectors failed";
     return PD_ERR_OOM;
+  }
+  {
+    const size_t cb = (sizeof(int) * (2 + 4 * M->T) + 15) & ~(size_t)15;
+    M->facc = reinterpret_cast<float*>(reinterpret_cast<char*>(M->pcnt) + cb);
+    M->bacc = M->facc + 3 * mq;
   }
   if (cudaMallocHost(&M->sc_h, sizeof(double) * 8) != cudaSuccess) return PD_ERR_OOM;
   k_split<<<nblk(m * m, 256), 256, 0, s->stream>>>(s->Sigma0, m * m, M->Shi, M->Slo);
@@ -934,11 +1105,13 @@ static void factor_panels(pd_solver* s, Factor& f, pdtc::Mode mode, int k_begin 
 static cudaError_t precond(pd_solver* s, const Factor& f, const double* r, double* z) {
   MixedState* M = s->mixed;
   const int64_t T = M->T;
-  cudaMemsetAsync(M->pcnt, 0, sizeof(int) * (1 + 2 * T), s->stream);
-  const int ntask = (int)(2 * T * NSL);
-  k_precond<<<(unsigned)std::min(ntask, M->pc_grid), 256, 0, s->stream>>>(f.Lh, f.E, M->mq, s->m, f.d, r, z, M->w, M->uo,
-                                                                         M->pcnt, s->status, f.iperm);
-  ++pdk::g_launches;
+  cudaMemsetAsync(M->pcnt, 0, sizeof(int) * (2 + 4 * T), s->stream);
+  k_pc_pre<<<nblk(3 * M->mq, 256), 256, 0, s->stream>>>(M->mq, s->m, f.d, r, f.iperm, M->facc, M->bacc);
+  const int nF = T >= 3 ? (int)((T - 2) * (T - 1) / 2) : 0, ntask = 2 * nF + (int)T;
+  k_precond<<<(unsigned)std::min(1 + ntask, M->pc_grid), 256, 0, s->stream>>>(
+      f.Lh, f.E, M->mq, M->w, M->uo, M->facc, M->bacc, M->pcnt, s->status);
+  k_pc_post<<<nblk(3 * s->m, 256), 256, 0, s->stream>>>(s->m, f.d, M->uo, f.iperm, z);
+  pdk::g_launches += 3;
   return cudaGetLastError();
 }
 

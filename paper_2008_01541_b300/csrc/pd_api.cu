@@ -167,6 +167,7 @@ pd_status pd_solver::region_solve_core(const double* g_dev, const double* u0_dev
                                nested ? d_perm : nullptr);
     tend();
     last_refine = 0;
+    last_residual = -1.0;   // the direct FP64 solve measures none
     return PD_OK;
   }
   return pdm::mixed_iterate(this, g_dev, u0_dev, u_dev);
