@@ -41,6 +41,7 @@ struct Factor {
 
 struct MixedState {
   int64_t mq = 0, T = 0;
+  int64_t ldm = 0;            // row stride of Shi / Slo / Minv0 and length / 3 of vhi / vlo / r32: m rounded up to 4
   bool nested_ready = false;  // nested form: the fixed leading tiles of f are current
   int nested_mode = -1;
   Factor f, f0;               // per-solve factor, contact-free factor (PCG_WARM)
@@ -833,16 +834,27 @@ inline size_t pc_scratch_bytes(int64_t T, int64_t mq) {
 }
 
 // z = Minv0 r (FP32 dense symmetric inverse, 3 right-hand sides), one warp per row.
-__global__ void k_minv_apply(const float* __restrict__ Mi, int64_t m, const float* __restrict__ r,
+// Row products with a padded FP32 matrix (row stride ld, a multiple of 4,
+// zero beyond column m) and an interleaved [ld][3] vector (zero beyond row
+// m): one warp per row, 16-byte loads, lane j4 takes columns 4 j4 .. + 3.
+// z = Minv0 r (FP32 dense symmetric inverse, 3 right-hand sides).
+__global__ void k_minv_apply(const float* __restrict__ Mi, int64_t m, int64_t ld, const float* __restrict__ r,
                              double* __restrict__ z) {
   const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= m) return;
-  const float* row = Mi + i * m;
+  const float4* row = reinterpret_cast<const float4*>(Mi + i * ld);
+  const float4* rv = reinterpret_cast<const float4*>(r);
   float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-  for (int64_t j = lane; j < m; j += 32) {
-    const float v = row[j];
-    a0 = fmaf(v, r[3 * j], a0); a1 = fmaf(v, r[3 * j + 1], a1); a2 = fmaf(v, r[3 * j + 2], a2);
+#pragma unroll 4
+  for (int64_t j4 = lane; j4 < ld / 4; j4 += 32) {
+    const float4 v = __ldg(row + j4);
+    const float4 x0 = __ldg(rv + 3 * j4), x1 = __ldg(rv + 3 * j4 + 1), x2 = __ldg(rv + 3 * j4 + 2);
+    // x0..x2 = (c0 v0 c1 v0 c2 v0 c0 v1) (c1 v1 c2 v1 c0 v2 c1 v2) (c2 v2 c0 v3 c1 v3 c2 v3)
+    a0 = fmaf(v.x, x0.x, a0); a1 = fmaf(v.x, x0.y, a1); a2 = fmaf(v.x, x0.z, a2);
+    a0 = fmaf(v.y, x0.w, a0); a1 = fmaf(v.y, x1.x, a1); a2 = fmaf(v.y, x1.y, a2);
+    a0 = fmaf(v.z, x1.z, a0); a1 = fmaf(v.z, x1.w, a1); a2 = fmaf(v.z, x2.x, a2);
+    a0 = fmaf(v.w, x2.y, a0); a1 = fmaf(v.w, x2.z, a1); a2 = fmaf(v.w, x2.w, a2);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -862,12 +874,12 @@ __global__ void k_unit3(double* r, int64_t m, int64_t q) {
   if (i >= m) return;
   for (int v = 0; v < 3; ++v) r[3 * i + v] = (i == 3 * q + v) ? 1.0 : 0.0;
 }
-// rows 3q..3q+2 of the inverse from z [m][3] (the inverse is symmetric)
-__global__ void k_store_cols(const double* z, int64_t m, int64_t q, float* Mi) {
+// rows 3q..3q+2 of the inverse from z [m][3] (the inverse is symmetric; row stride ld)
+__global__ void k_store_cols(const double* z, int64_t m, int64_t ld, int64_t q, float* Mi) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= m) return;
   for (int v = 0; v < 3; ++v)
-    if (3 * q + v < m) Mi[(3 * q + v) * m + i] = (float)z[3 * i + v];
+    if (3 * q + v < m) Mi[(3 * q + v) * ld + i] = (float)z[3 * i + v];
 }
 
 // Double-float products: a double split into an FP32 head and an FP32 tail.
@@ -879,42 +891,81 @@ __global__ void k_split(const double* __restrict__ x, int64_t n, float* __restri
   hi[i] = h;
   lo[i] = (float)(v - (double)h);
 }
+// Sigma_0 split into FP32 head and tail rows with the padded stride ld (zero padding).
+__global__ void k_split_rows(const double* __restrict__ S, int64_t m, int64_t ld, float* __restrict__ hi,
+                             float* __restrict__ lo) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= m * ld) return;
+  const int64_t i = q / ld, j = q % ld;
+  const double v = j < m ? S[i * m + j] : 0.0;
+  const float h = (float)v;
+  hi[q] = h;
+  lo[q] = (float)(v - (double)h);
+}
+
+// one term of the double-float product: exact head product (FMA remainder),
+// cross terms, compensated (two-sum) accumulation into (h, l)
+__device__ __forceinline__ void df_acc(float a, float b, float x, float y, float& h, float& l) {
+  const float p = a * x;
+  float e = fmaf(a, x, -p);
+  e = fmaf(a, y, e);
+  e = fmaf(b, x, e);
+  const float s = h + p;
+  const float bb = s - h;
+  float t = (h - (s - bb)) + (p - bb);
+  t += e + l;
+  h = s + t;
+  l = t - (h - s);
+}
+
+// (h, l) += (h2, l2) in double-float arithmetic
+__device__ __forceinline__ void df_add(float& h, float& l, float h2, float l2) {
+  const float s = h + h2;
+  const float bb = s - h;
+  float t = (h - (s - bb)) + (h2 - bb);
+  t += l + l2;
+  h = s + t;
+  l = t - (h - s);
+}
+
 // out = Sigma_0 v for 3 right-hand sides in double-float arithmetic on the
-// FP32 pipes: exact head products (FMA remainder), cross terms, and a
-// compensated (two-sum) accumulation per lane; lanes are combined in FP64.
-__global__ void k_symv_df(const float* __restrict__ Shi, const float* __restrict__ Slo, int64_t m,
+// FP32 pipes (Shi + Slo rows with stride ld, v = vhi + vlo interleaved [ld][3]);
+// lanes are combined in double-float too, so only the final conversion is FP64.
+__global__ void k_symv_df(const float* __restrict__ Shi, const float* __restrict__ Slo, int64_t m, int64_t ld,
                           const float* __restrict__ vhi, const float* __restrict__ vlo, double* __restrict__ out) {
   const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= m) return;
-  float ah[3] = {0.f, 0.f, 0.f}, al[3] = {0.f, 0.f, 0.f};
-  const float* rh = Shi + i * m;
-  const float* rl = Slo + i * m;
-  for (int64_t j = lane; j < m; j += 32) {
-    const float a = rh[j], b = rl[j];
+  float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
+  const float4* rh = reinterpret_cast<const float4*>(Shi + i * ld);
+  const float4* rl = reinterpret_cast<const float4*>(Slo + i * ld);
+  const float4* xh = reinterpret_cast<const float4*>(vhi);
+  const float4* xl = reinterpret_cast<const float4*>(vlo);
+#pragma unroll 2
+  for (int64_t j4 = lane; j4 < ld / 4; j4 += 32) {
+    const float4 a = __ldg(rh + j4), b = __ldg(rl + j4);
+    const float4 p0 = __ldg(xh + 3 * j4), p1 = __ldg(xh + 3 * j4 + 1), p2 = __ldg(xh + 3 * j4 + 2);
+    const float4 q0 = __ldg(xl + 3 * j4), q1 = __ldg(xl + 3 * j4 + 1), q2 = __ldg(xl + 3 * j4 + 2);
+    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+    const float ph[12] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w, p2.x, p2.y, p2.z, p2.w};
+    const float pl[12] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) df_acc(av[e], bv[e], ph[3 * e + c], pl[3 * e + c], h[c], l[c]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const float x = vhi[3 * j + c], y = vlo[3 * j + c];
-      const float p = a * x;
-      float e = fmaf(a, x, -p);
-      e = fmaf(a, y, e);
-      e = fmaf(b, x, e);
-      const float s = ah[c] + p;
-      const float bb = s - ah[c];
-      float t = (ah[c] - (s - bb)) + (p - bb);
-      t += e + al[c];
-      ah[c] = s + t;
-      al[c] = t - (ah[c] - s);
+      const float h2 = __shfl_xor_sync(0xffffffffu, h[c], o), l2 = __shfl_xor_sync(0xffffffffu, l[c], o);
+      df_add(h[c], l[c], h2, l2);
     }
+  if (lane < 3) {
+    const float hc = lane == 0 ? h[0] : lane == 1 ? h[1] : h[2];
+    const float lc = lane == 0 ? l[0] : lane == 1 ? l[1] : l[2];
+    out[3 * i + lane] = (double)hc + (double)lc;
   }
-  double r[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    r[c] = (double)ah[c] + (double)al[c];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) r[c] += __shfl_xor_sync(0xffffffffu, r[c], o);
-  }
-  if (lane == 0) { out[3 * i] = r[0]; out[3 * i + 1] = r[1]; out[3 * i + 2] = r[2]; }
 }
 
 __global__ void k_contact_matvec(int64_t k, const int32_t* cidx, const double* cw, const double* cs,
@@ -965,7 +1016,7 @@ __global__ void k_add(double* u, const double* z, int64_t n) {
 __global__ void k_cg_step(double* u, double* r, const double* p, const double* q, const double* sc, int64_t n) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double alpha = sc[1] / sc[2];
+  const double alpha = sc[2] != 0.0 ? sc[1] / sc[2] : 0.0;   // 0 once the residual vanished exactly
   u[i] += alpha * p[i];
   r[i] -= alpha * q[i];
 }
@@ -973,7 +1024,7 @@ __global__ void k_cg_step(double* u, double* r, const double* p, const double* q
 __global__ void k_cg_dir(double* p, const double* z, const double* sc, int64_t n, int first) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  p[i] = first ? z[i] : z[i] + (sc[1] / sc[3]) * p[i];
+  p[i] = first ? z[i] : z[i] + (sc[3] != 0.0 ? sc[1] / sc[3] : 0.0) * p[i];
 }
 
 inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
@@ -987,6 +1038,7 @@ static pd_status ensure_state(pd_solver* s) {
   s->mixed = M;
   M->mq = ((s->m + NB - 1) / NB) * NB;
   M->T = M->mq / NB;
+  M->ldm = (s->m + 3) & ~(int64_t)3;
   auto A = [&](void** p, size_t bytes) {
     cudaError_t e = cudaMalloc(p, bytes ? bytes : 1);
     if (e == cudaSuccess) s->allocs.push_back(*p);
@@ -1011,9 +1063,9 @@ static pd_status ensure_state(pd_solver* s) {
       A((void**)&M->z, sizeof(double) * 3 * m) || A((void**)&M->p, sizeof(double) * 3 * m) ||
       A((void**)&M->q, sizeof(double) * 3 * m) || A((void**)&M->u, sizeof(double) * 3 * m) ||
       A((void**)&M->sc, sizeof(double) * 8) || A((void**)&M->w, sizeof(float) * 3 * mq) ||
-      A((void**)&M->uo, sizeof(float) * 3 * mq) || A((void**)&M->Shi, sizeof(float) * m * m) ||
-      A((void**)&M->Slo, sizeof(float) * m * m) || A((void**)&M->vhi, sizeof(float) * 3 * m) ||
-      A((void**)&M->vlo, sizeof(float) * 3 * m) || A((void**)&M->r32, sizeof(float) * 3 * m) ||
+      A((void**)&M->uo, sizeof(float) * 3 * mq) || A((void**)&M->Shi, sizeof(float) * m * M->ldm) ||
+      A((void**)&M->Slo, sizeof(float) * m * M->ldm) || A((void**)&M->vhi, sizeof(float) * 3 * M->ldm) ||
+      A((void**)&M->vlo, sizeof(float) * 3 * M->ldm) || A((void**)&M->r32, sizeof(float) * 3 * M->ldm) ||
       A((void**)&M->pcnt, pc_scratch_bytes(M->T, mq))) {
     s->err = "device allocation for the mixed-precision vectors failed";
     return PD_ERR_OOM;
@@ -1024,7 +1076,11 @@ static pd_status ensure_state(pd_solver* s) {
     M->bacc = M->facc + 3 * mq;
   }
   if (cudaMallocHost(&M->sc_h, sizeof(double) * 8) != cudaSuccess) return PD_ERR_OOM;
-  k_split<<<nblk(m * m, 256), 256, 0, s->stream>>>(s->Sigma0, m * m, M->Shi, M->Slo);
+  // vectors beyond m stay zero: the padded products need no bounds checks
+  cudaMemsetAsync(M->vhi, 0, sizeof(float) * 3 * M->ldm, s->stream);
+  cudaMemsetAsync(M->vlo, 0, sizeof(float) * 3 * M->ldm, s->stream);
+  cudaMemsetAsync(M->r32, 0, sizeof(float) * 3 * M->ldm, s->stream);
+  k_split_rows<<<nblk(m * M->ldm, 256), 256, 0, s->stream>>>(s->Sigma0, m, M->ldm, M->Shi, M->Slo);
   ++pdk::g_launches;
   int lo_prio = 0, hi_prio = 0;
   cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
@@ -1122,9 +1178,10 @@ static pd_status build_minv(pd_solver* s) {
   MixedState* M = s->mixed;
   if (M->minv_valid) return PD_OK;
   if (!M->Minv0) {
-    cudaError_t e = cudaMalloc(&M->Minv0, sizeof(float) * s->m * s->m);
+    cudaError_t e = cudaMalloc(&M->Minv0, sizeof(float) * s->m * M->ldm);
     if (e != cudaSuccess) { s->err = "device allocation of the explicit inverse failed"; return PD_ERR_OOM; }
     s->allocs.push_back(M->Minv0);
+    cudaMemsetAsync(M->Minv0, 0, sizeof(float) * s->m * M->ldm, s->stream);   // padding columns
   }
   if (!M->f0.valid) {
     factor_cast(s, M->f0, false);
@@ -1135,7 +1192,7 @@ static pd_status build_minv(pd_solver* s) {
     k_unit3<<<nblk(m, 256), 256, 0, s->stream>>>(M->p, m, q);
     cudaError_t ce = precond(s, M->f0, M->p, M->z);
     if (ce != cudaSuccess) { s->err = cudaGetErrorString(ce); return PD_ERR_CUDA; }
-    k_store_cols<<<nblk(m, 256), 256, 0, s->stream>>>(M->z, m, q, M->Minv0);
+    k_store_cols<<<nblk(m, 256), 256, 0, s->stream>>>(M->z, m, M->ldm, q, M->Minv0);
     pdk::g_launches += 2;
   }
   M->minv_valid = true;
@@ -1145,7 +1202,7 @@ static pd_status build_minv(pd_solver* s) {
 static void apply_minv(pd_solver* s, const double* r, double* z) {
   MixedState* M = s->mixed;
   k_to_f32<<<nblk(3 * s->m, 256), 256, 0, s->stream>>>(r, 3 * s->m, M->r32);
-  k_minv_apply<<<nblk(32 * s->m, 256), 256, 0, s->stream>>>(M->Minv0, s->m, M->r32, z);
+  k_minv_apply<<<nblk(32 * s->m, 256), 256, 0, s->stream>>>(M->Minv0, s->m, M->ldm, M->r32, z);
   pdk::g_launches += 2;
 }
 
@@ -1153,7 +1210,7 @@ static void apply_minv(pd_solver* s, const double* r, double* z) {
 static void hmatvec(pd_solver* s, const double* p, double* q) {
   MixedState* M = s->mixed;
   k_split<<<nblk(3 * s->m, 256), 256, 0, s->stream>>>(p, 3 * s->m, M->vhi, M->vlo);
-  k_symv_df<<<nblk(32 * s->m, 256), 256, 0, s->stream>>>(M->Shi, M->Slo, s->m, M->vhi, M->vlo, q);
+  k_symv_df<<<nblk(32 * s->m, 256), 256, 0, s->stream>>>(M->Shi, M->Slo, s->m, M->ldm, M->vhi, M->vlo, q);
   pdk::g_launches += 2;
   if (s->k > 0) {
     k_contact_matvec<<<nblk(s->k, 128), 128, 0, s->stream>>>(s->k, s->c_idx, s->c_w, s->c_s, p, q);
@@ -1312,6 +1369,18 @@ pd_status mixed_iterate(pd_solver* s, const double* g, const double* u0, double*
       hmatvec(s, M->p, M->q);
       dot(s, M->p, M->q, 2);
       k_cg_step<<<nblk(n3, 256), 256, 0, st>>>(u, M->r, M->p, M->q, M->sc, n3); ++pdk::g_launches;
+      // the host reads the residual (a stream synchronisation) every iteration
+      // for the first eight, then every fourth: a long PCG run pays few round
+      // trips for at most three extra iterations
+      const bool check = it <= 8 || it % 4 == 0 || it == s->opt.max_refine;
+      if (!check) {
+        cudaMemcpyAsync(M->sc + 3, M->sc + 1, sizeof(double), cudaMemcpyDeviceToDevice, st);
+        if (warm) apply_minv(s, M->r, M->z);
+        else ce = precond(s, *f, M->r, M->z);
+        dot(s, M->r, M->z, 1);
+        k_cg_dir<<<nblk(n3, 256), 256, 0, st>>>(M->p, M->z, M->sc, n3, 0); ++pdk::g_launches;
+        continue;
+      }
       dot(s, M->r, M->r, 0);
       rr = read_slot(s, 0);
       if (!std::isfinite(rr)) break;
