@@ -1012,19 +1012,71 @@ __global__ void k_add(double* u, const double* z, int64_t n) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) u[i] += z[i];
 }
-// u += alpha p, r -= alpha q with alpha = sc[1] / sc[2]
-__global__ void k_cg_step(double* u, double* r, const double* p, const double* q, const double* sc, int64_t n) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+// Fused CG kernels; sc slots: 2 = p.q, a / b = r.z of this / the next iteration.
+// u += alpha p, r -= alpha q (alpha = sc[a] / sc[2]); r32 = (float) r; sc[b] = 0 for the next r.z
+__global__ void k_cg_step2(double* u, double* r, const double* p, const double* q, double* sc, int a, int b,
+                           int64_t n, float* r32) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const double pq = sc[2], alpha = pq != 0.0 ? sc[a] / pq : 0.0;
+  if (i == 0) sc[b] = 0.0;
   if (i >= n) return;
-  const double alpha = sc[2] != 0.0 ? sc[1] / sc[2] : 0.0;   // 0 once the residual vanished exactly
   u[i] += alpha * p[i];
-  r[i] -= alpha * q[i];
+  const double ri = r[i] - alpha * q[i];
+  r[i] = ri;
+  if (r32) r32[i] = (float)ri;
 }
-// p = z + beta p with beta = sc[1] / sc[3]
-__global__ void k_cg_dir(double* p, const double* z, const double* sc, int64_t n, int first) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+// p = z + beta p (beta = sc[b] / sc[a]; first: p = z), p split into head / tail for the
+// next Sigma_0 product, sc[2] = 0 for the next p.q
+__global__ void k_cg_dir2(double* p, const double* z, double* sc, int a, int b, int64_t n, int first,
+                          float* __restrict__ hi, float* __restrict__ lo) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const double den = sc[a], beta = first ? 0.0 : (den != 0.0 ? sc[b] / den : 0.0);
+  if (i == 0) sc[2] = 0.0;
   if (i >= n) return;
-  p[i] = first ? z[i] : z[i] + (sc[3] != 0.0 ? sc[1] / sc[3] : 0.0) * p[i];
+  const double v = z[i] + beta * (first ? 0.0 : p[i]);
+  p[i] = v;
+  const float h = (float)v;
+  hi[i] = h;
+  lo[i] = (float)(v - (double)h);
+}
+// z = Minv0 r32 as k_minv_apply, and sc[slot] += r . z (r in FP64; one atomic per block)
+__global__ void k_minv_apply_dot(const float* __restrict__ Mi, int64_t m, int64_t ld, const float* __restrict__ r32,
+                                 const double* __restrict__ r, double* __restrict__ z, double* __restrict__ acc) {
+  __shared__ double red[8];
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  double rz = 0.0;
+  if (i < m) {
+    const float4* row = reinterpret_cast<const float4*>(Mi + i * ld);
+    const float4* rv = reinterpret_cast<const float4*>(r32);
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll 4
+    for (int64_t j4 = lane; j4 < ld / 4; j4 += 32) {
+      const float4 v = __ldg(row + j4);
+      const float4 x0 = __ldg(rv + 3 * j4), x1 = __ldg(rv + 3 * j4 + 1), x2 = __ldg(rv + 3 * j4 + 2);
+      a0 = fmaf(v.x, x0.x, a0); a1 = fmaf(v.x, x0.y, a1); a2 = fmaf(v.x, x0.z, a2);
+      a0 = fmaf(v.y, x0.w, a0); a1 = fmaf(v.y, x1.x, a1); a2 = fmaf(v.y, x1.y, a2);
+      a0 = fmaf(v.z, x1.z, a0); a1 = fmaf(v.z, x1.w, a1); a2 = fmaf(v.z, x2.x, a2);
+      a0 = fmaf(v.w, x2.y, a0); a1 = fmaf(v.w, x2.z, a1); a2 = fmaf(v.w, x2.w, a2);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+      a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+      a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    }
+    if (lane == 0) {
+      z[3 * i] = a0; z[3 * i + 1] = a1; z[3 * i + 2] = a2;
+      rz = r[3 * i] * (double)a0 + r[3 * i + 1] * (double)a1 + r[3 * i + 2] * (double)a2;
+    }
+  }
+  if (lane == 0) red[wp] = rz;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+    atomicAdd(acc, t);
+  }
 }
 
 inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
@@ -1360,42 +1412,57 @@ pd_status mixed_iterate(pd_solver* s, const double* g, const double* u0, double*
     }
     ok = rr <= tol2;
   } else if (!ok) {
-    // refinement accelerated by preconditioned CG (FP64 vectors, true residual checked at the end)
-    if (warm) apply_minv(s, M->r, M->z);
-    else ce = precond(s, *f, M->r, M->z);
-    dot(s, M->r, M->z, 1);
-    k_cg_dir<<<nblk(n3, 256), 256, 0, st>>>(M->p, M->z, M->sc, n3, 1); ++pdk::g_launches;
+    // refinement accelerated by preconditioned CG (FP64 vectors, true residual checked at the end);
+    // r.z alternates between slots 1 and 5, p.q uses slot 2, each zeroed by the kernel before its use
+    auto rzs = [](int64_t k) { return (k & 1) ? 1 : 5; };
+    auto minv_dot = [&](int slot) {   // z = M^-1 r, sc[slot] = r.z (slot zeroed beforehand)
+      if (warm) {
+        k_minv_apply_dot<<<nblk(32 * s->m, 256), 256, 0, st>>>(M->Minv0, s->m, M->ldm, M->r32, M->r, M->z,
+                                                                M->sc + slot);
+        ++pdk::g_launches;
+      } else {
+        ce = precond(s, *f, M->r, M->z);
+        k_dot<<<148, 256, 0, st>>>(M->r, M->z, n3, M->sc + slot);
+        ++pdk::g_launches;
+      }
+    };
+    if (warm) { k_to_f32<<<nblk(n3, 256), 256, 0, st>>>(M->r, n3, M->r32); ++pdk::g_launches; }
+    cudaMemsetAsync(M->sc + rzs(1), 0, sizeof(double), st);
+    minv_dot(rzs(1));
+    k_cg_dir2<<<nblk(n3, 256), 256, 0, st>>>(M->p, M->z, M->sc, rzs(1), rzs(1), n3, 1, M->vhi, M->vlo);
+    ++pdk::g_launches;
     for (it = 1; it <= s->opt.max_refine && ce == cudaSuccess; ++it) {
-      hmatvec(s, M->p, M->q);
-      dot(s, M->p, M->q, 2);
-      k_cg_step<<<nblk(n3, 256), 256, 0, st>>>(u, M->r, M->p, M->q, M->sc, n3); ++pdk::g_launches;
+      const int sa = rzs(it), sb = rzs(it + 1);
+      // q = H p with p already split by k_cg_dir2
+      k_symv_df<<<nblk(32 * s->m, 256), 256, 0, st>>>(M->Shi, M->Slo, s->m, M->ldm, M->vhi, M->vlo, M->q);
+      ++pdk::g_launches;
+      if (s->k > 0) {
+        k_contact_matvec<<<nblk(s->k, 128), 128, 0, st>>>(s->k, s->c_idx, s->c_w, s->c_s, M->p, M->q);
+        ++pdk::g_launches;
+      }
+      k_dot<<<148, 256, 0, st>>>(M->p, M->q, n3, M->sc + 2);
+      k_cg_step2<<<nblk(n3, 256), 256, 0, st>>>(u, M->r, M->p, M->q, M->sc, sa, sb, n3, warm ? M->r32 : nullptr);
+      pdk::g_launches += 2;
       // the host reads the residual (a stream synchronisation) every iteration
       // for the first eight, then every fourth: a long PCG run pays few round
       // trips for at most three extra iterations
       const bool check = it <= 8 || it % 4 == 0 || it == s->opt.max_refine;
-      if (!check) {
-        cudaMemcpyAsync(M->sc + 3, M->sc + 1, sizeof(double), cudaMemcpyDeviceToDevice, st);
-        if (warm) apply_minv(s, M->r, M->z);
-        else ce = precond(s, *f, M->r, M->z);
-        dot(s, M->r, M->z, 1);
-        k_cg_dir<<<nblk(n3, 256), 256, 0, st>>>(M->p, M->z, M->sc, n3, 0); ++pdk::g_launches;
-        continue;
-      }
-      dot(s, M->r, M->r, 0);
-      rr = read_slot(s, 0);
-      if (!std::isfinite(rr)) break;
-      if (rr <= tol2) {   // confirm with the true residual
-        hmatvec(s, u, M->q);
-        k_sub<<<nblk(n3, 256), 256, 0, st>>>(g, M->q, M->r, n3); ++pdk::g_launches;
+      if (check) {
         dot(s, M->r, M->r, 0);
         rr = read_slot(s, 0);
-        if (rr <= tol2) break;
+        if (!std::isfinite(rr)) break;
+        if (rr <= tol2) {   // confirm with the true residual
+          hmatvec(s, u, M->q);
+          k_sub<<<nblk(n3, 256), 256, 0, st>>>(g, M->q, M->r, n3); ++pdk::g_launches;
+          dot(s, M->r, M->r, 0);
+          rr = read_slot(s, 0);
+          if (rr <= tol2) break;
+          if (warm) { k_to_f32<<<nblk(n3, 256), 256, 0, st>>>(M->r, n3, M->r32); ++pdk::g_launches; }
+        }
       }
-      cudaMemcpyAsync(M->sc + 3, M->sc + 1, sizeof(double), cudaMemcpyDeviceToDevice, st);
-      if (warm) apply_minv(s, M->r, M->z);
-      else ce = precond(s, *f, M->r, M->z);
-      dot(s, M->r, M->z, 1);
-      k_cg_dir<<<nblk(n3, 256), 256, 0, st>>>(M->p, M->z, M->sc, n3, 0); ++pdk::g_launches;
+      minv_dot(sb);
+      k_cg_dir2<<<nblk(n3, 256), 256, 0, st>>>(M->p, M->z, M->sc, sa, sb, n3, 0, M->vhi, M->vlo);
+      ++pdk::g_launches;
     }
     ok = rr <= tol2;
   }
