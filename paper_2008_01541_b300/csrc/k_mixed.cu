@@ -846,7 +846,7 @@ __global__ void k_minv_apply(const float* __restrict__ Mi, int64_t m, int64_t ld
   const float4* row = reinterpret_cast<const float4*>(Mi + i * ld);
   const float4* rv = reinterpret_cast<const float4*>(r);
   float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-#pragma unroll 4
+#pragma unroll 8
   for (int64_t j4 = lane; j4 < ld / 4; j4 += 32) {
     const float4 v = __ldg(row + j4);
     const float4 x0 = __ldg(rv + 3 * j4), x1 = __ldg(rv + 3 * j4 + 1), x2 = __ldg(rv + 3 * j4 + 2);
@@ -941,7 +941,7 @@ __global__ void k_symv_df(const float* __restrict__ Shi, const float* __restrict
   const float4* rl = reinterpret_cast<const float4*>(Slo + i * ld);
   const float4* xh = reinterpret_cast<const float4*>(vhi);
   const float4* xl = reinterpret_cast<const float4*>(vlo);
-#pragma unroll 2
+#pragma unroll 4
   for (int64_t j4 = lane; j4 < ld / 4; j4 += 32) {
     const float4 a = __ldg(rh + j4), b = __ldg(rl + j4);
     const float4 p0 = __ldg(xh + 3 * j4), p1 = __ldg(xh + 3 * j4 + 1), p2 = __ldg(xh + 3 * j4 + 2);
@@ -1050,7 +1050,7 @@ __global__ void k_minv_apply_dot(const float* __restrict__ Mi, int64_t m, int64_
     const float4* row = reinterpret_cast<const float4*>(Mi + i * ld);
     const float4* rv = reinterpret_cast<const float4*>(r32);
     float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-#pragma unroll 4
+#pragma unroll 8
     for (int64_t j4 = lane; j4 < ld / 4; j4 += 32) {
       const float4 v = __ldg(row + j4);
       const float4 x0 = __ldg(rv + 3 * j4), x1 = __ldg(rv + 3 * j4 + 1), x2 = __ldg(rv + 3 * j4 + 2);
