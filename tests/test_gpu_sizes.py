@@ -1,6 +1,8 @@
 """Region sizes at and around the tile boundaries of the dense kernels (FP64
 tiles of 64, low-precision tiles of 128, 32-row panel slices), every form,
-against the oracle's H = Sigma_0 + C_22 and one outer iteration vs the oracle."""
+against the oracle's H = Sigma_0 + C_22 and one outer iteration vs the oracle.
+Sizes 300 and 400 give the low-precision preconditioner three and four block
+rows, so its off-chain block products run as well."""
 import numpy as np
 import pytest
 import scipy.sparse as sp
@@ -12,7 +14,7 @@ from gpu_util import need_gpu, rng, contact_tuple
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-10
-SIZES = [1, 3, 17, 63, 64, 65, 127, 128, 129, 200]
+SIZES = [1, 3, 17, 63, 64, 65, 127, 128, 129, 200, 300, 400]
 
 
 @pytest.fixture(scope="module")
