@@ -148,16 +148,18 @@ __global__ void k_block_copy_f32(float* __restrict__ L, int64_t mq, int64_t off,
 }
 
 // One warp factors the 32 x 32 block at Ap (row stride PADW) in registers
-// (lane i holds row i) and writes L back to Ap.  Each scaled column goes
-// through shared memory once and is read back with 16-byte broadcasts; a
-// non-positive pivot is replaced by 1 and reported in *status (first bad
-// column + 1, offset by code0).
-__device__ __noinline__ void warp_chol32(float* Ap, int* status, int code0) {
+// (lane i holds row i) and writes L back to Ap, and 1 / L_jj to rinv.  Each
+// scaled column goes through shared memory once (double-buffered, so one warp
+// barrier per pivot) and is read back with 16-byte broadcasts; the next
+// pivot's column is updated first so that its square root overlaps the rest
+// of the current update.  A non-positive pivot is replaced by 1 and reported
+// in *status (first bad column + 1, offset by code0).
+__device__ __noinline__ void warp_chol32(float* Ap, float* rinv, int* status, int code0) {
   const int lane = threadIdx.x & 31;
   float a[32];
 #pragma unroll
   for (int c = 0; c < 32; ++c) a[c] = Ap[lane * PADW + c];
-  __shared__ __align__(16) float col[32];
+  __shared__ __align__(16) float col[2][32];
   unsigned bad = 0;
 #pragma unroll
   for (int j = 0; j < 32; ++j) {
@@ -166,22 +168,26 @@ __device__ __noinline__ void warp_chol32(float* Ap, int* status, int code0) {
     bad |= (unsigned)b << j;
     djj = b ? 1.f : djj;
     const float rs = rsqrtf(djj);
-    if (lane == j) a[j] = djj * rs;
-    if (lane > j) a[j] *= rs;
-    col[lane] = a[j];
+    a[j] = lane == j ? djj * rs : (lane > j ? a[j] * rs : a[j]);
+    if (lane == j) rinv[j] = rs;
+    float* cb = col[j & 1];
+    cb[lane] = a[j];
     __syncwarp();
-    const float4* c4 = reinterpret_cast<const float4*>(col);
+    if (j + 1 < 32) {
+      const float v = cb[j + 1];
+      if (lane >= j + 1) a[j + 1] = fmaf(-a[j], v, a[j + 1]);
+    }
+    const float4* c4 = reinterpret_cast<const float4*>(cb);
 #pragma unroll
-    for (int q = (j + 1) / 4; q < 8; ++q) {
+    for (int q = (j + 2) / 4; q < 8; ++q) {
       const float4 v = c4[q];
       const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int c = 4 * q + e;
-        if (c > j && lane >= c) a[c] = fmaf(-a[j], vv[e], a[c]);
+        if (c > j + 1 && lane >= c) a[c] = fmaf(-a[j], vv[e], a[c]);
       }
     }
-    __syncwarp();
   }
   if (bad && lane == 0) atomicCAS(status, 0, code0 + __ffs(bad));
 #pragma unroll
@@ -257,6 +263,7 @@ __global__ void __launch_bounds__(256) k_diag_f32(float* __restrict__ L, int64_t
   extern __shared__ float sm[];
   float* A = sm;                   // [128][PADW]
   float* Z = sm + NB * PADW;       // [128][PADW] inverse
+  __shared__ float rinv32[32];     // 1 / L_jj of the current 32 x 32 sub-block
   const int tid = threadIdx.x, warp = tid >> 5;
 #define LB(i, j) (A + (32 * (i)) * PADW + 32 * (j))
 #define ZB(i, j) (Z + (32 * (i)) * PADW + 32 * (j))
@@ -283,7 +290,7 @@ __global__ void __launch_bounds__(256) k_diag_f32(float* __restrict__ L, int64_t
     const int c0 = 32 * p;
     // ---- phase 1: factor block p | rest of panel p-1's update | invert block p-1
     if (warp == 0) {
-      warp_chol32(A + c0 * PADW + c0, status, kt * NB + c0);
+      warp_chol32(A + c0 * PADW + c0, rinv32, status, kt * NB + c0);
     } else if (warp == 7) {
       if (p > 0) warp_inv32(A + (c0 - 32) * PADW + (c0 - 32), Z + (c0 - 32) * PADW + (c0 - 32));
     } else if (p == 3) {
@@ -323,7 +330,7 @@ __global__ void __launch_bounds__(256) k_diag_f32(float* __restrict__ L, int64_t
       for (int j = 0; j < 32; ++j) x[j] = row[j];
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
-        x[j] *= __frcp_rn(Ap[j * PADW + j]);
+        x[j] *= rinv32[j];
 #pragma unroll
         for (int t = j + 1; t < 32; ++t) x[t] = fmaf(-x[j], Ap[t * PADW + j], x[t]);
       }
