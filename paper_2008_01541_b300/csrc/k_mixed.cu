@@ -194,81 +194,19 @@ __device__ __noinline__ void warp_chol32(float* Ap, float* rinv, int* status, in
   for (int c = 0; c < 32; ++c) if (c <= lane) Ap[lane * PADW + c] = a[c];
 }
 
-// One warp inverts the lower-triangular 32 x 32 block at Ap into Zp.
-__device__ __noinline__ void warp_inv32(const float* Ap, float* Zp) {
-  const int lane = threadIdx.x & 31;
-  float a[32], z[32];
-#pragma unroll
-  for (int c = 0; c < 32; ++c) { a[c] = (c <= lane) ? Ap[lane * PADW + c] : 0.f; z[c] = (c == lane) ? 1.f : 0.f; }
-#pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    if (lane == j) {
-      const float ip = __frcp_rn(a[j]);
-#pragma unroll
-      for (int c = 0; c <= j; ++c) z[c] *= ip;
-    }
-#pragma unroll
-    for (int c = 0; c <= j; ++c) {
-      const float zjc = __shfl_sync(0xffffffffu, z[c], j);
-      if (lane > j) z[c] = fmaf(-a[j], zjc, z[c]);
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < 32; ++c) Zp[lane * PADW + c] = z[c];
-}
-
-// Up to three 32 x 32 block products O_w = sg_w X_w Y_w (acc: O_w += ...), all
-// blocks with leading dimension PADW; threads [t0, t0 + nthr) take 2 x 2
-// outputs each.
-__device__ __forceinline__ void blk_prods(int np, int acc, int t0, int nthr,
-                                          const float* X0, const float* Y0, float* O0, float g0,
-                                          const float* X1 = nullptr, const float* Y1 = nullptr, float* O1 = nullptr,
-                                          float g1 = 0.f, const float* X2 = nullptr, const float* Y2 = nullptr,
-                                          float* O2 = nullptr, float g2 = 0.f) {
-  const int me = threadIdx.x - t0;
-  if (me < 0 || me >= nthr) return;
-  for (int q = me; q < np * 256; q += nthr) {
-    const int w = q >> 8;
-    const float* X = w == 0 ? X0 : (w == 1 ? X1 : X2);
-    const float* Y = w == 0 ? Y0 : (w == 1 ? Y1 : Y2);
-    float* O = w == 0 ? O0 : (w == 1 ? O1 : O2);
-    const float g = w == 0 ? g0 : (w == 1 ? g1 : g2);
-    const int r = 2 * ((q & 255) >> 4), c = 2 * (q & 15);
-    float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f;
-#pragma unroll 8
-    for (int t = 0; t < 32; ++t) {
-      const float x0 = X[r * PADW + t], x1 = X[(r + 1) * PADW + t];
-      const float y0 = Y[t * PADW + c], y1 = Y[t * PADW + c + 1];
-      s00 = fmaf(x0, y0, s00); s01 = fmaf(x0, y1, s01); s10 = fmaf(x1, y0, s10); s11 = fmaf(x1, y1, s11);
-    }
-    float* o = O + r * PADW + c;
-    if (acc) {
-      o[0] += g * s00; o[1] += g * s01; o[PADW] += g * s10; o[PADW + 1] += g * s11;
-    } else {
-      o[0] = g * s00; o[1] = g * s01; o[PADW] = g * s10; o[PADW + 1] = g * s11;
-    }
-  }
-}
-
-// Factor the diagonal tile (kt, kt) in FP32 and invert it (L_kk and
-// Dinv_k = L_kk^-1), blocked in shared memory with 32-wide sub-blocks and a
-// look-ahead inside the tile: while warp 0 factors sub-block p, warps 1-6
-// apply the rest of panel p-1's trailing update and warp 7 inverts
-// sub-block p-1.  The panel below sub-block p is solved one thread per row;
-// the off-diagonal blocks of the inverse, Z_ij = -Z_ii sum_t L_it Z_tj, are
-// formed in the phases where threads are idle, their partial sums S_ij kept
-// in the unused blocks above the diagonal of Z.
-__global__ void __launch_bounds__(256) k_diag_f32(float* __restrict__ L, int64_t mq, int kt,
-                                                  float* __restrict__ Dinv, int* __restrict__ status) {
+// Factor the diagonal tile (kt, kt) in FP32 (L_kk), blocked in shared memory
+// with 32-wide sub-blocks and a look-ahead inside the tile: while warp 0
+// factors sub-block p, warps 1-7 apply the rest of panel p-1's trailing
+// update; the panel below sub-block p is solved one thread per row.  The
+// tile's inverse is formed by k_inv_f32.  Each of the two kernels needs one
+// 128 x 129 FP32 tile of shared memory (plus small buffers), so either fits
+// on an SM beside two CTAs of the concurrent tensor-core trailing update: the
+// serial chain never waits for the whole bulk update to drain.
+__global__ void __launch_bounds__(256) k_diag_f32(float* __restrict__ L, int64_t mq, int kt, int* __restrict__ status) {
   extern __shared__ float sm[];
   float* A = sm;                   // [128][PADW]
-  float* Z = sm + NB * PADW;       // [128][PADW] inverse
   __shared__ float rinv32[32];     // 1 / L_jj of the current 32 x 32 sub-block
   const int tid = threadIdx.x, warp = tid >> 5;
-#define LB(i, j) (A + (32 * (i)) * PADW + 32 * (j))
-#define ZB(i, j) (Z + (32 * (i)) * PADW + 32 * (j))
-// the six S_ij live in the (zero, unused) blocks above the diagonal of Z
-#define SB(k) ((k) == 0 ? ZB(0, 1) : (k) == 1 ? ZB(0, 2) : (k) == 2 ? ZB(0, 3) : (k) == 3 ? ZB(1, 2) : (k) == 4 ? ZB(1, 3) : ZB(2, 3))
   float* Lt = L + (int64_t)kt * NB * mq + (int64_t)kt * NB;
   {
     float4 v[16];
@@ -281,26 +219,20 @@ __global__ void __launch_bounds__(256) k_diag_f32(float* __restrict__ L, int64_t
     for (int k = 0; k < 16; ++k) {
       const int q = tid + 256 * k, r = q >> 5, c = 4 * (q & 31);
       A[r * PADW + c] = v[k].x; A[r * PADW + c + 1] = v[k].y; A[r * PADW + c + 2] = v[k].z; A[r * PADW + c + 3] = v[k].w;
-      Z[r * PADW + c] = 0.f; Z[r * PADW + c + 1] = 0.f; Z[r * PADW + c + 2] = 0.f; Z[r * PADW + c + 3] = 0.f;
     }
   }
   __syncthreads();
 #pragma unroll 1
   for (int p = 0; p < 4; ++p) {
     const int c0 = 32 * p;
-    // ---- phase 1: factor block p | rest of panel p-1's update | invert block p-1
+    // ---- phase 1: factor block p | rest of panel p-1's update
     if (warp == 0) {
       warp_chol32(A + c0 * PADW + c0, rinv32, status, kt * NB + c0);
-    } else if (warp == 7) {
-      if (p > 0) warp_inv32(A + (c0 - 32) * PADW + (c0 - 32), Z + (c0 - 32) * PADW + (c0 - 32));
-    } else if (p == 3) {
-      // S20 += L21 Z10, S30 += L31 Z10 (warps 1-6; no trailing rows are left)
-      blk_prods(2, 1, 32, 192, LB(2, 1), ZB(1, 0), SB(0), 1.f, LB(3, 1), ZB(1, 0), SB(1), 1.f);
     } else if (p > 0) {
       // rows >= c0 + 32, columns c0 .. row (sub-block p itself was updated in phase 3)
       const int pc = c0 - 32;                      // panel columns pc .. pc + 31
       const int nbr = (NB - c0 - 32) / 2, nbc = (NB - c0) / 2;
-      for (int q = tid - 32; q < nbr * nbc; q += 192) {
+      for (int q = tid - 32; q < nbr * nbc; q += 224) {
         const int bi = q / nbc, bj = q % nbc;
         const int r = c0 + 32 + 2 * bi, c = c0 + 2 * bj;
         if (c > r) continue;
@@ -337,27 +269,8 @@ __global__ void __launch_bounds__(256) k_diag_f32(float* __restrict__ L, int64_t
 #pragma unroll
       for (int j = 0; j < 32; ++j) row[j] = x[j];
     }
-    // blocks of the inverse whose inputs are ready, on the threads the panel leaves idle
-    if (p == 1) {
-      blk_prods(3, 0, 64, 192, LB(1, 0), ZB(0, 0), SB(2), 1.f, LB(2, 0), ZB(0, 0), SB(0), 1.f, LB(3, 0), ZB(0, 0),
-                SB(1), 1.f);
-    } else if (p == 2) {
-      blk_prods(3, 0, 32, 224, ZB(1, 1), SB(2), ZB(1, 0), -1.f, LB(2, 1), ZB(1, 1), SB(3), 1.f, LB(3, 1), ZB(1, 1),
-                SB(4), 1.f);
-    } else if (p == 3) {
-      // no panel below the last sub-block: warp 7 inverts it, the others form
-      // Z20 = -Z22 S20, Z21 = -Z22 S21 and S32 = L32 Z22
-      if (warp == 7) warp_inv32(A + 96 * PADW + 96, Z + 96 * PADW + 96);
-      blk_prods(3, 0, 0, 224, ZB(2, 2), SB(0), ZB(2, 0), -1.f, ZB(2, 2), SB(3), ZB(2, 1), -1.f, LB(3, 2), ZB(2, 2),
-                SB(5), 1.f);
-    }
     __syncthreads();
     // ---- phase 3: update of the next diagonal block with panel p
-    if (p == 3) {
-      // S30 += L32 Z20, S31 += L32 Z21
-      blk_prods(2, 1, 0, 256, LB(3, 2), ZB(2, 0), SB(1), 1.f, LB(3, 2), ZB(2, 1), SB(4), 1.f);
-      __syncthreads();
-    }
     if (p < 3) {
       const int b0 = c0 + 32;
       for (int q = tid; q < 16 * 16; q += 256) {
@@ -379,24 +292,114 @@ __global__ void __launch_bounds__(256) k_diag_f32(float* __restrict__ L, int64_t
       __syncthreads();
     }
   }
-  {
-    // Z3j = -Z33 S3j
-    blk_prods(3, 0, 0, 256, ZB(3, 3), SB(1), ZB(3, 0), -1.f, ZB(3, 3), SB(4), ZB(3, 1), -1.f, ZB(3, 3), SB(5),
-              ZB(3, 2), -1.f);
-  }
-  __syncthreads();
-  float* Di = Dinv + (int64_t)kt * NB * NB;
   for (int q = tid; q < NB * NB; q += 256) {
     const int r = q / NB, c = q % NB;
     if (c <= r) Lt[(int64_t)r * mq + c] = A[r * PADW + c];
-    Di[q] = (c <= r) ? Z[r * PADW + c] : 0.f;
   }
-#undef LB
-#undef ZB
-#undef SB
 }
 
+// 32 x 32 block product into registers: thread (r = 2 * (tid >> 4), c = 2 * (tid & 15))
+// of the first 256 threads accumulates o[2][2] += X[r.., t] Y[t, c..] (leading
+// dimensions ldx, ldy).
+__device__ __forceinline__ void prod32_acc(const float* X, int ldx, const float* Y, int ldy, float (&o)[2][2]) {
+  const int r = 2 * (threadIdx.x >> 4), c = 2 * (threadIdx.x & 15);
+#pragma unroll 8
+  for (int t = 0; t < 32; ++t) {
+    const float x0 = X[r * ldx + t], x1 = X[(r + 1) * ldx + t];
+    const float y0 = Y[t * ldy + c], y1 = Y[t * ldy + c + 1];
+    o[0][0] = fmaf(x0, y0, o[0][0]); o[0][1] = fmaf(x0, y1, o[0][1]);
+    o[1][0] = fmaf(x1, y0, o[1][0]); o[1][1] = fmaf(x1, y1, o[1][1]);
+  }
+}
 
+// Dinv_k = L_kk^-1 for the factored diagonal tile kt (row-major, zero above the
+// diagonal).  The four diagonal 32 x 32 blocks are inverted by one warp each;
+// then, by block diagonals, Z_ij = -Z_ii T_ij with T_ij = sum_{j <= t < i} L_it Z_tj.
+// The diagonal blocks Z_ii sit in Zd (leading dimension 33); an off-diagonal
+// block Z_ij (i > j) sits in the unused block (j, i) above the diagonal of A.
+__global__ void __launch_bounds__(256) k_inv_f32(const float* __restrict__ L, int64_t mq, int kt,
+                                                 float* __restrict__ Dinv) {
+  extern __shared__ float sm[];
+  float* A = sm;                    // [128][PADW]: L_kk below the diagonal, Z_ij above
+  float* Zd = sm + NB * PADW;       // [4][32][33]
+  const int tid = threadIdx.x, warp = tid >> 5;
+  constexpr int LZ = 33;
+  const float* Lt = L + (int64_t)kt * NB * mq + (int64_t)kt * NB;
+  {
+    float4 v[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int q = tid + 256 * k, r = q >> 5, c = 4 * (q & 31);
+      v[k] = __ldcg(reinterpret_cast<const float4*>(Lt + (int64_t)r * mq + c));
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int q = tid + 256 * k, r = q >> 5, c = 4 * (q & 31);
+      A[r * PADW + c] = v[k].x; A[r * PADW + c + 1] = v[k].y; A[r * PADW + c + 2] = v[k].z; A[r * PADW + c + 3] = v[k].w;
+    }
+  }
+  __syncthreads();
+  // level 0: Z_ii = L_ii^-1 (rows of Zd, leading dimension 33)
+  if (warp < 4) {
+    const int lane = tid & 31, c0 = 32 * warp;
+    const float* Ap = A + c0 * PADW + c0;
+    float a[32], z[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) { a[c] = (c <= lane) ? Ap[lane * PADW + c] : 0.f; z[c] = (c == lane) ? 1.f : 0.f; }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if (lane == j) {
+        const float ip = __frcp_rn(a[j]);
+#pragma unroll
+        for (int c = 0; c <= j; ++c) z[c] *= ip;
+      }
+#pragma unroll
+      for (int c = 0; c <= j; ++c) {
+        const float zjc = __shfl_sync(0xffffffffu, z[c], j);
+        if (lane > j) z[c] = fmaf(-a[j], zjc, z[c]);
+      }
+    }
+    float* Zp = Zd + warp * 32 * LZ;
+#pragma unroll
+    for (int c = 0; c < 32; ++c) Zp[lane * LZ + c] = z[c];
+  }
+  __syncthreads();
+  const int orr = 2 * (tid >> 4), occ = 2 * (tid & 15);
+  // levels 1-3: d = i - j; the (4 - d) blocks of a level are taken in turn
+#pragma unroll 1
+  for (int d = 1; d < 4; ++d) {
+#pragma unroll 1
+    for (int j = 0; j + d < 4; ++j) {
+      const int i = j + d;
+      float* Zij = A + (32 * j) * PADW + 32 * i;     // block (j, i) of A holds Z_ij
+      // T_ij = sum_{t = j .. i-1} L_it Z_tj
+      float o[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+      for (int t = j; t < i; ++t) {
+        const float* Lit = A + (32 * i) * PADW + 32 * t;
+        if (t == j) prod32_acc(Lit, PADW, Zd + j * 32 * LZ, LZ, o);
+        else prod32_acc(Lit, PADW, A + (32 * j) * PADW + 32 * t, PADW, o);   // Z_tj in block (j, t)
+      }
+      Zij[orr * PADW + occ] = o[0][0]; Zij[orr * PADW + occ + 1] = o[0][1];
+      Zij[(orr + 1) * PADW + occ] = o[1][0]; Zij[(orr + 1) * PADW + occ + 1] = o[1][1];
+      __syncthreads();
+      // Z_ij = -Z_ii T_ij
+      float q2[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+      prod32_acc(Zd + i * 32 * LZ, LZ, Zij, PADW, q2);
+      __syncthreads();
+      Zij[orr * PADW + occ] = -q2[0][0]; Zij[orr * PADW + occ + 1] = -q2[0][1];
+      Zij[(orr + 1) * PADW + occ] = -q2[1][0]; Zij[(orr + 1) * PADW + occ + 1] = -q2[1][1];
+      __syncthreads();
+    }
+  }
+  float* Di = Dinv + (int64_t)kt * NB * NB;
+  for (int q = tid; q < NB * NB; q += 256) {
+    const int r = q / NB, c = q % NB, bi = r >> 5, bj = c >> 5;
+    float v = 0.f;
+    if (bi == bj) v = (c <= r) ? Zd[bi * 32 * LZ + (r & 31) * LZ + (c & 31)] : 0.f;
+    else if (bi > bj) v = A[(32 * bj + (r & 31)) * PADW + 32 * bi + (c & 31)];
+    Di[q] = v;
+  }
+}
 
 // E_k = Dinv_k^T Dinv_k for every diagonal tile (one CTA per tile, off the
 // factorisation's critical path).
@@ -1157,7 +1160,8 @@ static pd_status ensure_state(pd_solver* s) {
   M->pc_grid = std::max(1, nsm * std::max(1, per));
   static std::atomic<unsigned long long> attr{0};
   if (pdk::first_on_device(attr)) {
-    cudaFuncSetAttribute(k_diag_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * NB * PADW * 4);
+    cudaFuncSetAttribute(k_diag_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, NB * PADW * 4);
+    cudaFuncSetAttribute(k_inv_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (NB * PADW + 4 * 32 * 33) * 4);
     cudaFuncSetAttribute(k_trsm_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (NB * AP + NB * DP) * 4);
     cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, NB * PADW * 4);
   }
@@ -1191,8 +1195,9 @@ static void factor_panels(pd_solver* s, Factor& f, pdtc::Mode mode, int k_begin 
   // panel kt to the rest of the trailing matrix meanwhile.
   cudaStream_t sb = M->side;
   for (int kt = k_begin; kt < k_end; ++kt) {
-    k_diag_f32<<<1, 256, 2 * NB * PADW * 4, st>>>(f.L, mq, kt, f.Dinv, s->status);
-    ++pdk::g_launches;
+    k_diag_f32<<<1, 256, NB * PADW * 4, st>>>(f.L, mq, kt, s->status);
+    k_inv_f32<<<1, 256, (NB * PADW + 4 * 32 * 33) * 4, st>>>(f.L, mq, kt, f.Dinv);
+    pdk::g_launches += 2;
     const int n = (int)(T - kt - 1);
     if (n <= 0) break;
     __nv_bfloat16* pb = mode == pdtc::BF16 ? f.Pb[kt & 1] : nullptr;
