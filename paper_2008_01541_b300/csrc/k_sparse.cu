@@ -128,6 +128,21 @@ __global__ void __launch_bounds__(256, 4) k_sf_solve(SparseFactor f, int64_t nta
     if (tk.x < 0) break;
     const int s = tk.x & 0x1fffffff, kind = (tk.x >> 29) & 3;
     const int rb = tk.y, cb = tk.z, oi = tk.w;
+    const int64_t c0 = f.col0[s], nc = f.col0[s + 1] - c0, nr = f.rowptr[s + 1] - f.rowptr[s], ld = nc + nr;
+    const double* Pd = f.L + f.valptr[s];     // diagonal block (its inverse, lower)
+    const double* Po = Pd + nc;               // off-diagonal block
+    const int32_t* R = f.rows + f.rowptr[s];
+    // ---- the factor tile this task starts with does not depend on the
+    // vectors: stage it while the inputs are awaited
+    const bool diag = kind == KIND_DIAG;
+    const int64_t nrows = diag ? nc : nr;
+    const int rows_t = (int)min((int64_t)TT, nrows - rb), cols_t = (int)min((int64_t)TT, nc - cb);
+    if (kind == KIND_FUSED) {
+      if (FWD) stage_tile(tile, Pd, ld, 0, 0, (int)nc, (int)nc, true);
+      else if (nr > 0) stage_tile(tile, Po, ld, 0, 0, (int)min((int64_t)TT, nr), (int)nc, false);
+    } else {
+      stage_tile(tile, diag ? Pd : Po, ld, rb, cb, rows_t, cols_t, diag);
+    }
     // ---- wait for the inputs
     if (tid == 0) {
       const unsigned long long t0 = gtimer();
@@ -142,16 +157,11 @@ __global__ void __launch_bounds__(256, 4) k_sf_solve(SparseFactor f, int64_t nta
       __threadfence();
     }
     __syncthreads();
-    const int64_t c0 = f.col0[s], nc = f.col0[s + 1] - c0, nr = f.rowptr[s + 1] - f.rowptr[s], ld = nc + nr;
-    const double* Pd = f.L + f.valptr[s];     // diagonal block (its inverse, lower)
-    const double* Po = Pd + nc;               // off-diagonal block
-    const int32_t* R = f.rows + f.rowptr[s];
     double a0 = 0.0, a1 = 0.0, a2 = 0.0;
     if (kind == KIND_FUSED) {
       const int n = (int)nc;
       if (FWD) {
-        // y_s = Dinv_s b_s, then b[rows] -= L_off y_s
-        stage_tile(tile, Pd, ld, 0, 0, n, n, true);
+        // y_s = Dinv_s b_s (its tile staged before the wait), then b[rows] -= L_off y_s
         if (tid < TT) {
           if (tid < n) load3(xs, tid, v0 + 3 * (c0 + tid));
           else xs[tid][0] = xs[tid][1] = xs[tid][2] = 0.0;
@@ -181,7 +191,7 @@ __global__ void __launch_bounds__(256, 4) k_sf_solve(SparseFactor f, int64_t nta
         // z_s = y_s - L_off^T u[rows], then u_s = Dinv_s^T z_s
         for (int r0 = 0; r0 < nr; r0 += TT) {
           const int nrow = (int)min((int64_t)TT, nr - r0);
-          stage_tile(tile, Po, ld, r0, 0, nrow, n, false);
+          if (r0 > 0) stage_tile(tile, Po, ld, r0, 0, nrow, n, false);   // the first was staged before the wait
           if (tid < TT) {
             if (tid < nrow) load3(xs, tid, v0 + 3 * (int64_t)R[r0 + tid]);
             else xs[tid][0] = xs[tid][1] = xs[tid][2] = 0.0;
@@ -207,10 +217,6 @@ __global__ void __launch_bounds__(256, 4) k_sf_solve(SparseFactor f, int64_t nta
         if (ch == 0 && o < n) { double* d = v0 + 3 * (c0 + o); d[0] = a0; d[1] = a1; d[2] = a2; }
       }
     } else {
-      const bool diag = kind == KIND_DIAG;
-      const int64_t nrows = diag ? nc : nr;
-      const int rows_t = (int)min((int64_t)TT, nrows - rb), cols_t = (int)min((int64_t)TT, nc - cb);
-      stage_tile(tile, diag ? Pd : Po, ld, rb, cb, rows_t, cols_t, diag);
       if (tid < TT) {
         xs[tid][0] = xs[tid][1] = xs[tid][2] = 0.0;
         if (FWD) {
