@@ -25,6 +25,9 @@ namespace pdm {
 constexpr int NB = 128;      // tile of the low-precision factor
 constexpr int PADW = NB + 1; // padded shared-memory row
 
+// named barrier among n threads (id 1..15; 0 is __syncthreads)
+__device__ __forceinline__ void bar_sync_n(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+
 struct Factor {
   float* L = nullptr;         // [mq][mq] row-major, lower tiles hold the factor
   float* Dinv = nullptr;      // [T][128][128] row-major inverses of the diagonal tiles
@@ -298,25 +301,30 @@ __global__ void __launch_bounds__(256) k_diag_f32(float* __restrict__ L, int64_t
   }
 }
 
-// 32 x 32 block product into registers: thread (r = 2 * (tid >> 4), c = 2 * (tid & 15))
-// of the first 256 threads accumulates o[2][2] += X[r.., t] Y[t, c..] (leading
-// dimensions ldx, ldy).
-__device__ __forceinline__ void prod32_acc(const float* X, int ldx, const float* Y, int ldy, float (&o)[2][2]) {
-  const int r = 2 * (threadIdx.x >> 4), c = 2 * (threadIdx.x & 15);
-#pragma unroll 8
+// 32 x 32 block product on a group of 64 threads: thread gr = tid & 63 holds
+// rows 4 (gr >> 3) .. + 3 and columns 4 (gr & 7) .. + 3 and accumulates
+// o += X[rows, t] Y[t, columns] (leading dimensions ldx, ldy).
+__device__ __forceinline__ void prod32_g64(const float* X, int ldx, const float* Y, int ldy, float (&o)[4][4]) {
+  const int gr = threadIdx.x & 63, r = 4 * (gr >> 3), c = 4 * (gr & 7);
+#pragma unroll 4
   for (int t = 0; t < 32; ++t) {
-    const float x0 = X[r * ldx + t], x1 = X[(r + 1) * ldx + t];
-    const float y0 = Y[t * ldy + c], y1 = Y[t * ldy + c + 1];
-    o[0][0] = fmaf(x0, y0, o[0][0]); o[0][1] = fmaf(x0, y1, o[0][1]);
-    o[1][0] = fmaf(x1, y0, o[1][0]); o[1][1] = fmaf(x1, y1, o[1][1]);
+    float x[4], y[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { x[q] = X[(r + q) * ldx + t]; y[q] = Y[t * ldy + c + q]; }
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) o[p][q] = fmaf(x[p], y[q], o[p][q]);
   }
 }
 
 // Dinv_k = L_kk^-1 for the factored diagonal tile kt (row-major, zero above the
 // diagonal).  The four diagonal 32 x 32 blocks are inverted by one warp each;
-// then, by block diagonals, Z_ij = -Z_ii T_ij with T_ij = sum_{j <= t < i} L_it Z_tj.
-// The diagonal blocks Z_ii sit in Zd (leading dimension 33); an off-diagonal
-// block Z_ij (i > j) sits in the unused block (j, i) above the diagonal of A.
+// then, by block diagonals d = i - j, Z_ij = -Z_ii T_ij with
+// T_ij = sum_{j <= t < i} L_it Z_tj, the (4 - d) blocks of a diagonal at once
+// on groups of 64 threads.  The diagonal blocks Z_ii sit in Zd (leading
+// dimension 33); an off-diagonal block Z_ij (i > j) sits in the unused block
+// (j, i) above the diagonal of A.
 __global__ void __launch_bounds__(256) k_inv_f32(const float* __restrict__ L, int64_t mq, int kt,
                                                  float* __restrict__ Dinv) {
   extern __shared__ float sm[];
@@ -364,32 +372,32 @@ __global__ void __launch_bounds__(256) k_inv_f32(const float* __restrict__ L, in
     for (int c = 0; c < 32; ++c) Zp[lane * LZ + c] = z[c];
   }
   __syncthreads();
-  const int orr = 2 * (tid >> 4), occ = 2 * (tid & 15);
-  // levels 1-3: d = i - j; the (4 - d) blocks of a level are taken in turn
+  const int grp = tid >> 6, gr = tid & 63, orr = 4 * (gr >> 3), occ = 4 * (gr & 7);
 #pragma unroll 1
   for (int d = 1; d < 4; ++d) {
-#pragma unroll 1
-    for (int j = 0; j + d < 4; ++j) {
-      const int i = j + d;
+    const int j = grp, i = j + d;
+    if (i < 4) {
       float* Zij = A + (32 * j) * PADW + 32 * i;     // block (j, i) of A holds Z_ij
-      // T_ij = sum_{t = j .. i-1} L_it Z_tj
-      float o[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
-      for (int t = j; t < i; ++t) {
+      float o[4][4] = {};
+      for (int t = j; t < i; ++t) {                  // T_ij = sum_t L_it Z_tj
         const float* Lit = A + (32 * i) * PADW + 32 * t;
-        if (t == j) prod32_acc(Lit, PADW, Zd + j * 32 * LZ, LZ, o);
-        else prod32_acc(Lit, PADW, A + (32 * j) * PADW + 32 * t, PADW, o);   // Z_tj in block (j, t)
+        if (t == j) prod32_g64(Lit, PADW, Zd + j * 32 * LZ, LZ, o);
+        else prod32_g64(Lit, PADW, A + (32 * j) * PADW + 32 * t, PADW, o);   // Z_tj in block (j, t)
       }
-      Zij[orr * PADW + occ] = o[0][0]; Zij[orr * PADW + occ + 1] = o[0][1];
-      Zij[(orr + 1) * PADW + occ] = o[1][0]; Zij[(orr + 1) * PADW + occ + 1] = o[1][1];
-      __syncthreads();
-      // Z_ij = -Z_ii T_ij
-      float q2[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
-      prod32_acc(Zd + i * 32 * LZ, LZ, Zij, PADW, q2);
-      __syncthreads();
-      Zij[orr * PADW + occ] = -q2[0][0]; Zij[orr * PADW + occ + 1] = -q2[0][1];
-      Zij[(orr + 1) * PADW + occ] = -q2[1][0]; Zij[(orr + 1) * PADW + occ + 1] = -q2[1][1];
-      __syncthreads();
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) Zij[(orr + p) * PADW + occ + q] = o[p][q];
+      bar_sync_n(1 + grp, 64);
+      float z2[4][4] = {};
+      prod32_g64(Zd + i * 32 * LZ, LZ, Zij, PADW, z2);   // Z_ij = -Z_ii T_ij
+      bar_sync_n(1 + grp, 64);
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) Zij[(orr + p) * PADW + occ + q] = -z2[p][q];
     }
+    __syncthreads();
   }
   float* Di = Dinv + (int64_t)kt * NB * NB;
   for (int q = tid; q < NB * NB; q += 256) {

@@ -19,12 +19,15 @@ namespace pdtc {
 namespace {
 using namespace dev;
 
-// MODE: 0 = TF32, 1 = 3xTF32 (hi*hi + hi*lo + lo*hi), 2 = BF16.
-template <int MODE>
+// MODE: 0 = TF32, 1 = 3xTF32 (hi*hi + hi*lo + lo*hi), 2 = BF16.  NSTAGE: stages
+// resident in shared memory (0: the default that keeps three CTAs per SM; a
+// one-wave launch such as the look-ahead column takes two stages instead, so
+// the next chunk's loads overlap the current chunk's MMAs).
+template <int MODE, int NSTAGE>
 __global__ void __launch_bounds__(128, 3)
     k_rank_k(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int kx0, int kchunks,
              float* __restrict__ C, int64_t ldc, int ti0, int tj0, int n_j, int lower, int* __restrict__ status) {
-  constexpr int NST = (MODE == 1) ? 1 : 2;                 // stages resident in shared memory (3 CTAs/SM)
+  constexpr int NST = NSTAGE > 0 ? NSTAGE : ((MODE == 1) ? 1 : 2);
   constexpr int STAGE = (MODE == 1) ? 4 * kChunkBytes : 2 * kChunkBytes;  // A, B (+ A_lo, B_lo)
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t full[NST], done[NST];
@@ -163,9 +166,9 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   return fn;
 }
 
-template <int MODE>
+template <int MODE, int NSTAGE = 0>
 constexpr int smem_bytes() {
-  return ((MODE == 1) ? 1 * 4 * kChunkBytes : 2 * 2 * kChunkBytes) + 1024;
+  return (NSTAGE > 0 ? NSTAGE : ((MODE == 1) ? 1 : 2)) * ((MODE == 1) ? 4 : 2) * kChunkBytes + 1024;
 }
 
 }  // namespace
@@ -186,21 +189,26 @@ bool make_map(CUtensorMap* map, const void* base, int esize, uint64_t rows, uint
 
 void rank_k_update(Mode mode, const CUtensorMap* a, const CUtensorMap* b, int kx0, int kchunks, float* C,
                    int64_t ldc, int ti0, int tj0, int n_i, int n_j, int lower, int* status, cudaStream_t st) {
-  static std::atomic<unsigned long long> attr[3];
+  static std::atomic<unsigned long long> attr[4];
   unsigned grid = lower ? (unsigned)((int64_t)n_i * (n_i + 1) / 2) : (unsigned)(n_i * n_j);
   if (grid == 0 || kchunks <= 0) return;
   switch (mode) {
     case TF32:
-      if (pdk::first_on_device(attr[0])) cudaFuncSetAttribute(k_rank_k<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<0>());
-      k_rank_k<0><<<grid, 128, smem_bytes<0>(), st>>>(*a, *b, kx0, kchunks, C, ldc, ti0, tj0, n_j, lower, status);
+      if (pdk::first_on_device(attr[0])) cudaFuncSetAttribute(k_rank_k<0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<0>());
+      k_rank_k<0, 0><<<grid, 128, smem_bytes<0>(), st>>>(*a, *b, kx0, kchunks, C, ldc, ti0, tj0, n_j, lower, status);
       break;
     case TF32X3:
-      if (pdk::first_on_device(attr[1])) cudaFuncSetAttribute(k_rank_k<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<1>());
-      k_rank_k<1><<<grid, 128, smem_bytes<1>(), st>>>(*a, *b, kx0, kchunks, C, ldc, ti0, tj0, n_j, lower, status);
+      if (grid <= 148 && kchunks > 1) {   // one wave: two stages, one CTA per SM
+        if (pdk::first_on_device(attr[3])) cudaFuncSetAttribute(k_rank_k<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<1, 2>());
+        k_rank_k<1, 2><<<grid, 128, smem_bytes<1, 2>(), st>>>(*a, *b, kx0, kchunks, C, ldc, ti0, tj0, n_j, lower, status);
+      } else {
+        if (pdk::first_on_device(attr[1])) cudaFuncSetAttribute(k_rank_k<1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<1>());
+        k_rank_k<1, 0><<<grid, 128, smem_bytes<1>(), st>>>(*a, *b, kx0, kchunks, C, ldc, ti0, tj0, n_j, lower, status);
+      }
       break;
     default:
-      if (pdk::first_on_device(attr[2])) cudaFuncSetAttribute(k_rank_k<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<2>());
-      k_rank_k<2><<<grid, 128, smem_bytes<2>(), st>>>(*a, *b, kx0, kchunks, C, ldc, ti0, tj0, n_j, lower, status);
+      if (pdk::first_on_device(attr[2])) cudaFuncSetAttribute(k_rank_k<2, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<2>());
+      k_rank_k<2, 0><<<grid, 128, smem_bytes<2>(), st>>>(*a, *b, kx0, kchunks, C, ldc, ti0, tj0, n_j, lower, status);
       break;
   }
   ++pdk::g_launches;
