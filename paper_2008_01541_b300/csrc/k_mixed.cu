@@ -197,17 +197,108 @@ __device__ __noinline__ void warp_chol32(float* Ap, float* rinv, int* status, in
   for (int c = 0; c < 32; ++c) if (c <= lane) Ap[lane * PADW + c] = a[c];
 }
 
+// 32 x 32 block product on a group of 64 threads: thread gr = tid & 63 holds
+// rows 4 (gr >> 3) .. + 3 and columns 4 (gr & 7) .. + 3 and accumulates
+// o += X[rows, t] Y[t, columns] (leading dimensions ldx, ldy).
+__device__ __forceinline__ void prod32_g64(const float* X, int ldx, const float* Y, int ldy, float (&o)[4][4]) {
+  const int gr = threadIdx.x & 63, r = 4 * (gr >> 3), c = 4 * (gr & 7);
+#pragma unroll 4
+  for (int t = 0; t < 32; ++t) {
+    float x[4], y[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { x[q] = X[(r + q) * ldx + t]; y[q] = Y[t * ldy + c + q]; }
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) o[p][q] = fmaf(x[p], y[q], o[p][q]);
+  }
+}
+
+// Dinv_k = L_kk^-1 from the factored tile in shared memory (A, row stride
+// PADW, lower triangle), written row-major to Di (zero above the diagonal).
+// The four diagonal 32 x 32 blocks are inverted by one warp each; then, by
+// block diagonals d = i - j, Z_ij = -Z_ii T_ij with T_ij = sum_{j <= t < i}
+// L_it Z_tj, the (4 - d) blocks of a diagonal at once on groups of 64
+// threads.  The diagonal blocks Z_ii sit in Zd (leading dimension 33); an
+// off-diagonal block Z_ij (i > j) sits in the unused block (j, i) above the
+// diagonal of A.  Called by all 256 threads after a barrier.
+__device__ __forceinline__ void tile_inverse(float* A, float* Zd, float* __restrict__ Di) {
+  const int tid = threadIdx.x, warp = tid >> 5;
+  constexpr int LZ = 33;
+  // level 0: Z_ii = L_ii^-1 (rows of Zd, leading dimension 33)
+  if (warp < 4) {
+    const int lane = tid & 31, c0 = 32 * warp;
+    const float* Ap = A + c0 * PADW + c0;
+    float a[32], z[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) { a[c] = (c <= lane) ? Ap[lane * PADW + c] : 0.f; z[c] = (c == lane) ? 1.f : 0.f; }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if (lane == j) {
+        const float ip = __frcp_rn(a[j]);
+#pragma unroll
+        for (int c = 0; c <= j; ++c) z[c] *= ip;
+      }
+#pragma unroll
+      for (int c = 0; c <= j; ++c) {
+        const float zjc = __shfl_sync(0xffffffffu, z[c], j);
+        if (lane > j) z[c] = fmaf(-a[j], zjc, z[c]);
+      }
+    }
+    float* Zp = Zd + warp * 32 * LZ;
+#pragma unroll
+    for (int c = 0; c < 32; ++c) Zp[lane * LZ + c] = z[c];
+  }
+  __syncthreads();
+  const int grp = tid >> 6, gr = tid & 63, orr = 4 * (gr >> 3), occ = 4 * (gr & 7);
+#pragma unroll 1
+  for (int d = 1; d < 4; ++d) {
+    const int j = grp, i = j + d;
+    if (i < 4) {
+      float* Zij = A + (32 * j) * PADW + 32 * i;     // block (j, i) of A holds Z_ij
+      float o[4][4] = {};
+      for (int t = j; t < i; ++t) {                  // T_ij = sum_t L_it Z_tj
+        const float* Lit = A + (32 * i) * PADW + 32 * t;
+        if (t == j) prod32_g64(Lit, PADW, Zd + j * 32 * LZ, LZ, o);
+        else prod32_g64(Lit, PADW, A + (32 * j) * PADW + 32 * t, PADW, o);   // Z_tj in block (j, t)
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) Zij[(orr + p) * PADW + occ + q] = o[p][q];
+      bar_sync_n(1 + grp, 64);
+      float z2[4][4] = {};
+      prod32_g64(Zd + i * 32 * LZ, LZ, Zij, PADW, z2);   // Z_ij = -Z_ii T_ij
+      bar_sync_n(1 + grp, 64);
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) Zij[(orr + p) * PADW + occ + q] = -z2[p][q];
+    }
+    __syncthreads();
+  }
+  for (int q = tid; q < NB * NB; q += 256) {
+    const int r = q / NB, c = q % NB, bi = r >> 5, bj = c >> 5;
+    float v = 0.f;
+    if (bi == bj) v = (c <= r) ? Zd[bi * 32 * LZ + (r & 31) * LZ + (c & 31)] : 0.f;
+    else if (bi > bj) v = A[(32 * bj + (r & 31)) * PADW + 32 * bi + (c & 31)];
+    Di[q] = v;
+  }
+}
+
 // Factor the diagonal tile (kt, kt) in FP32 (L_kk), blocked in shared memory
 // with 32-wide sub-blocks and a look-ahead inside the tile: while warp 0
 // factors sub-block p, warps 1-7 apply the rest of panel p-1's trailing
-// update; the panel below sub-block p is solved one thread per row.  The
-// tile's inverse is formed by k_inv_f32.  Each of the two kernels needs one
-// 128 x 129 FP32 tile of shared memory (plus small buffers), so either fits
-// on an SM beside two CTAs of the concurrent tensor-core trailing update: the
-// serial chain never waits for the whole bulk update to drain.
-__global__ void __launch_bounds__(256) k_diag_f32(float* __restrict__ L, int64_t mq, int kt, int* __restrict__ status) {
+// update; the panel below sub-block p is solved one thread per row.  Then the
+// tile's inverse Dinv_k (tile_inverse) from the same shared-memory tile.  One
+// 128 x 129 FP32 tile plus the four 32 x 33 diagonal inverse blocks (83 KB)
+// fit on an SM beside two CTAs of the concurrent tensor-core trailing update,
+// so the serial chain never waits for the whole bulk update to drain.
+__global__ void __launch_bounds__(256) k_diag_f32(float* __restrict__ L, int64_t mq, int kt,
+                                                  float* __restrict__ Dinv, int* __restrict__ status) {
   extern __shared__ float sm[];
   float* A = sm;                   // [128][PADW]
+  float* Zd = sm + NB * PADW;      // [4][32][33] diagonal blocks of the inverse
   __shared__ float rinv32[32];     // 1 / L_jj of the current 32 x 32 sub-block
   const int tid = threadIdx.x, warp = tid >> 5;
   float* Lt = L + (int64_t)kt * NB * mq + (int64_t)kt * NB;
@@ -299,114 +390,8 @@ __global__ void __launch_bounds__(256) k_diag_f32(float* __restrict__ L, int64_t
     const int r = q / NB, c = q % NB;
     if (c <= r) Lt[(int64_t)r * mq + c] = A[r * PADW + c];
   }
-}
-
-// 32 x 32 block product on a group of 64 threads: thread gr = tid & 63 holds
-// rows 4 (gr >> 3) .. + 3 and columns 4 (gr & 7) .. + 3 and accumulates
-// o += X[rows, t] Y[t, columns] (leading dimensions ldx, ldy).
-__device__ __forceinline__ void prod32_g64(const float* X, int ldx, const float* Y, int ldy, float (&o)[4][4]) {
-  const int gr = threadIdx.x & 63, r = 4 * (gr >> 3), c = 4 * (gr & 7);
-#pragma unroll 4
-  for (int t = 0; t < 32; ++t) {
-    float x[4], y[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) { x[q] = X[(r + q) * ldx + t]; y[q] = Y[t * ldy + c + q]; }
-#pragma unroll
-    for (int p = 0; p < 4; ++p)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) o[p][q] = fmaf(x[p], y[q], o[p][q]);
-  }
-}
-
-// Dinv_k = L_kk^-1 for the factored diagonal tile kt (row-major, zero above the
-// diagonal).  The four diagonal 32 x 32 blocks are inverted by one warp each;
-// then, by block diagonals d = i - j, Z_ij = -Z_ii T_ij with
-// T_ij = sum_{j <= t < i} L_it Z_tj, the (4 - d) blocks of a diagonal at once
-// on groups of 64 threads.  The diagonal blocks Z_ii sit in Zd (leading
-// dimension 33); an off-diagonal block Z_ij (i > j) sits in the unused block
-// (j, i) above the diagonal of A.
-__global__ void __launch_bounds__(256) k_inv_f32(const float* __restrict__ L, int64_t mq, int kt,
-                                                 float* __restrict__ Dinv) {
-  extern __shared__ float sm[];
-  float* A = sm;                    // [128][PADW]: L_kk below the diagonal, Z_ij above
-  float* Zd = sm + NB * PADW;       // [4][32][33]
-  const int tid = threadIdx.x, warp = tid >> 5;
-  constexpr int LZ = 33;
-  const float* Lt = L + (int64_t)kt * NB * mq + (int64_t)kt * NB;
-  {
-    float4 v[16];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const int q = tid + 256 * k, r = q >> 5, c = 4 * (q & 31);
-      v[k] = __ldcg(reinterpret_cast<const float4*>(Lt + (int64_t)r * mq + c));
-    }
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const int q = tid + 256 * k, r = q >> 5, c = 4 * (q & 31);
-      A[r * PADW + c] = v[k].x; A[r * PADW + c + 1] = v[k].y; A[r * PADW + c + 2] = v[k].z; A[r * PADW + c + 3] = v[k].w;
-    }
-  }
-  __syncthreads();
-  // level 0: Z_ii = L_ii^-1 (rows of Zd, leading dimension 33)
-  if (warp < 4) {
-    const int lane = tid & 31, c0 = 32 * warp;
-    const float* Ap = A + c0 * PADW + c0;
-    float a[32], z[32];
-#pragma unroll
-    for (int c = 0; c < 32; ++c) { a[c] = (c <= lane) ? Ap[lane * PADW + c] : 0.f; z[c] = (c == lane) ? 1.f : 0.f; }
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      if (lane == j) {
-        const float ip = __frcp_rn(a[j]);
-#pragma unroll
-        for (int c = 0; c <= j; ++c) z[c] *= ip;
-      }
-#pragma unroll
-      for (int c = 0; c <= j; ++c) {
-        const float zjc = __shfl_sync(0xffffffffu, z[c], j);
-        if (lane > j) z[c] = fmaf(-a[j], zjc, z[c]);
-      }
-    }
-    float* Zp = Zd + warp * 32 * LZ;
-#pragma unroll
-    for (int c = 0; c < 32; ++c) Zp[lane * LZ + c] = z[c];
-  }
-  __syncthreads();
-  const int grp = tid >> 6, gr = tid & 63, orr = 4 * (gr >> 3), occ = 4 * (gr & 7);
-#pragma unroll 1
-  for (int d = 1; d < 4; ++d) {
-    const int j = grp, i = j + d;
-    if (i < 4) {
-      float* Zij = A + (32 * j) * PADW + 32 * i;     // block (j, i) of A holds Z_ij
-      float o[4][4] = {};
-      for (int t = j; t < i; ++t) {                  // T_ij = sum_t L_it Z_tj
-        const float* Lit = A + (32 * i) * PADW + 32 * t;
-        if (t == j) prod32_g64(Lit, PADW, Zd + j * 32 * LZ, LZ, o);
-        else prod32_g64(Lit, PADW, A + (32 * j) * PADW + 32 * t, PADW, o);   // Z_tj in block (j, t)
-      }
-#pragma unroll
-      for (int p = 0; p < 4; ++p)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) Zij[(orr + p) * PADW + occ + q] = o[p][q];
-      bar_sync_n(1 + grp, 64);
-      float z2[4][4] = {};
-      prod32_g64(Zd + i * 32 * LZ, LZ, Zij, PADW, z2);   // Z_ij = -Z_ii T_ij
-      bar_sync_n(1 + grp, 64);
-#pragma unroll
-      for (int p = 0; p < 4; ++p)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) Zij[(orr + p) * PADW + occ + q] = -z2[p][q];
-    }
-    __syncthreads();
-  }
-  float* Di = Dinv + (int64_t)kt * NB * NB;
-  for (int q = tid; q < NB * NB; q += 256) {
-    const int r = q / NB, c = q % NB, bi = r >> 5, bj = c >> 5;
-    float v = 0.f;
-    if (bi == bj) v = (c <= r) ? Zd[bi * 32 * LZ + (r & 31) * LZ + (c & 31)] : 0.f;
-    else if (bi > bj) v = A[(32 * bj + (r & 31)) * PADW + 32 * bi + (c & 31)];
-    Di[q] = v;
-  }
+  // the inverse for the panel solve and the preconditioner, from the tile in shared memory
+  tile_inverse(A, Zd, Dinv + (int64_t)kt * NB * NB);
 }
 
 // E_k = Dinv_k^T Dinv_k for every diagonal tile (one CTA per tile, off the
@@ -1168,8 +1153,7 @@ static pd_status ensure_state(pd_solver* s) {
   M->pc_grid = std::max(1, nsm * std::max(1, per));
   static std::atomic<unsigned long long> attr{0};
   if (pdk::first_on_device(attr)) {
-    cudaFuncSetAttribute(k_diag_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, NB * PADW * 4);
-    cudaFuncSetAttribute(k_inv_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (NB * PADW + 4 * 32 * 33) * 4);
+    cudaFuncSetAttribute(k_diag_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (NB * PADW + 4 * 32 * 33) * 4);
     cudaFuncSetAttribute(k_trsm_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (NB * AP + NB * DP) * 4);
     cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, NB * PADW * 4);
   }
@@ -1203,9 +1187,8 @@ static void factor_panels(pd_solver* s, Factor& f, pdtc::Mode mode, int k_begin 
   // panel kt to the rest of the trailing matrix meanwhile.
   cudaStream_t sb = M->side;
   for (int kt = k_begin; kt < k_end; ++kt) {
-    k_diag_f32<<<1, 256, NB * PADW * 4, st>>>(f.L, mq, kt, s->status);
-    k_inv_f32<<<1, 256, (NB * PADW + 4 * 32 * 33) * 4, st>>>(f.L, mq, kt, f.Dinv);
-    pdk::g_launches += 2;
+    k_diag_f32<<<1, 256, (NB * PADW + 4 * 32 * 33) * 4, st>>>(f.L, mq, kt, f.Dinv, s->status);
+    ++pdk::g_launches;
     const int n = (int)(T - kt - 1);
     if (n <= 0) break;
     __nv_bfloat16* pb = mode == pdtc::BF16 ? f.Pb[kt & 1] : nullptr;
