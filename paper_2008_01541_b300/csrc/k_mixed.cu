@@ -907,18 +907,24 @@ __global__ void k_split_rows(const double* __restrict__ S, int64_t m, int64_t ld
 }
 
 // one term of the double-float product: exact head product (FMA remainder),
-// cross terms, compensated (two-sum) accumulation into (h, l)
-__device__ __forceinline__ void df_acc(float a, float b, float x, float y, float& h, float& l) {
+// cross terms, and the exact rounding error of h + p, all collected in l
+// without renormalising; (h, l) is renormalised by df_norm every four terms,
+// which keeps |l| a few units of h's last place in between
+__device__ __forceinline__ void df_acc_lazy(float a, float b, float x, float y, float& h, float& l) {
   const float p = a * x;
   float e = fmaf(a, x, -p);
   e = fmaf(a, y, e);
   e = fmaf(b, x, e);
   const float s = h + p;
   const float bb = s - h;
-  float t = (h - (s - bb)) + (p - bb);
-  t += e + l;
-  h = s + t;
-  l = t - (h - s);
+  l += ((h - (s - bb)) + (p - bb)) + e;
+  h = s;
+}
+__device__ __forceinline__ void df_norm(float& h, float& l) {   // two-sum: no magnitude assumption
+  const float s = h + l;
+  const float bb = s - h;
+  l = (h - (s - bb)) + (l - bb);
+  h = s;
 }
 
 // (h, l) += (h2, l2) in double-float arithmetic
@@ -955,7 +961,9 @@ __global__ void k_symv_df(const float* __restrict__ Shi, const float* __restrict
 #pragma unroll
     for (int e = 0; e < 4; ++e)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) df_acc(av[e], bv[e], ph[3 * e + c], pl[3 * e + c], h[c], l[c]);
+      for (int c = 0; c < 3; ++c) df_acc_lazy(av[e], bv[e], ph[3 * e + c], pl[3 * e + c], h[c], l[c]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) df_norm(h[c], l[c]);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1)
