@@ -939,43 +939,59 @@ __device__ __forceinline__ void df_add(float& h, float& l, float h2, float l2) {
 
 // out = Sigma_0 v for 3 right-hand sides in double-float arithmetic on the
 // FP32 pipes (Shi + Slo rows with stride ld, v = vhi + vlo interleaved [ld][3]);
-// lanes are combined in double-float too, so only the final conversion is FP64.
+// one warp takes two rows, so every vector load serves both; lanes are
+// combined in double-float too, so only the final conversion is FP64.
 __global__ void k_symv_df(const float* __restrict__ Shi, const float* __restrict__ Slo, int64_t m, int64_t ld,
                           const float* __restrict__ vhi, const float* __restrict__ vlo, double* __restrict__ out) {
-  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t i0 = 2 * ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
-  if (i >= m) return;
-  float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
-  const float4* rh = reinterpret_cast<const float4*>(Shi + i * ld);
-  const float4* rl = reinterpret_cast<const float4*>(Slo + i * ld);
+  if (i0 >= m) return;
+  const int64_t i1 = i0 + 1 < m ? i0 + 1 : i0;      // an odd last row is computed twice, stored once
+  float h[2][3] = {}, l[2][3] = {};
+  const float4* rh0 = reinterpret_cast<const float4*>(Shi + i0 * ld);
+  const float4* rl0 = reinterpret_cast<const float4*>(Slo + i0 * ld);
+  const float4* rh1 = reinterpret_cast<const float4*>(Shi + i1 * ld);
+  const float4* rl1 = reinterpret_cast<const float4*>(Slo + i1 * ld);
   const float4* xh = reinterpret_cast<const float4*>(vhi);
   const float4* xl = reinterpret_cast<const float4*>(vlo);
-#pragma unroll 4
+#pragma unroll 2
   for (int64_t j4 = lane; j4 < ld / 4; j4 += 32) {
-    const float4 a = __ldg(rh + j4), b = __ldg(rl + j4);
+    const float4 a0 = __ldg(rh0 + j4), b0 = __ldg(rl0 + j4), a1 = __ldg(rh1 + j4), b1 = __ldg(rl1 + j4);
     const float4 p0 = __ldg(xh + 3 * j4), p1 = __ldg(xh + 3 * j4 + 1), p2 = __ldg(xh + 3 * j4 + 2);
     const float4 q0 = __ldg(xl + 3 * j4), q1 = __ldg(xl + 3 * j4 + 1), q2 = __ldg(xl + 3 * j4 + 2);
-    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+    const float av[2][4] = {{a0.x, a0.y, a0.z, a0.w}, {a1.x, a1.y, a1.z, a1.w}};
+    const float bv[2][4] = {{b0.x, b0.y, b0.z, b0.w}, {b1.x, b1.y, b1.z, b1.w}};
     const float ph[12] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w, p2.x, p2.y, p2.z, p2.w};
     const float pl[12] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
 #pragma unroll
-    for (int e = 0; e < 4; ++e)
+    for (int w = 0; w < 2; ++w) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) df_acc_lazy(av[e], bv[e], ph[3 * e + c], pl[3 * e + c], h[c], l[c]);
+      for (int e = 0; e < 4; ++e)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) df_norm(h[c], l[c]);
+        for (int c = 0; c < 3; ++c) df_acc_lazy(av[w][e], bv[w][e], ph[3 * e + c], pl[3 * e + c], h[w][c], l[w][c]);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) df_norm(h[w][c], l[w][c]);
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const float h2 = __shfl_xor_sync(0xffffffffu, h[c], o), l2 = __shfl_xor_sync(0xffffffffu, l[c], o);
-      df_add(h[c], l[c], h2, l2);
-    }
-  if (lane < 3) {
-    const float hc = lane == 0 ? h[0] : lane == 1 ? h[1] : h[2];
-    const float lc = lane == 0 ? l[0] : lane == 1 ? l[1] : l[2];
-    out[3 * i + lane] = (double)hc + (double)lc;
+    for (int w = 0; w < 2; ++w)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, h[w][c], o), l2 = __shfl_xor_sync(0xffffffffu, l[w][c], o);
+        df_add(h[w][c], l[w][c], h2, l2);
+      }
+  if (lane < 6) {
+    const int w = lane / 3, c = lane % 3;
+    float hc = 0.f, lc = 0.f;
+#pragma unroll
+    for (int ww = 0; ww < 2; ++ww)
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc)
+        if (ww == w && cc == c) { hc = h[ww][cc]; lc = l[ww][cc]; }
+    const int64_t row = w == 0 ? i0 : i1;
+    if (w == 0 || i1 != i0) out[3 * row + c] = (double)hc + (double)lc;
   }
 }
 
@@ -1273,7 +1289,7 @@ static void apply_minv(pd_solver* s, const double* r, double* z) {
 static void hmatvec(pd_solver* s, const double* p, double* q) {
   MixedState* M = s->mixed;
   k_split<<<nblk(3 * s->m, 256), 256, 0, s->stream>>>(p, 3 * s->m, M->vhi, M->vlo);
-  k_symv_df<<<nblk(32 * s->m, 256), 256, 0, s->stream>>>(M->Shi, M->Slo, s->m, M->ldm, M->vhi, M->vlo, q);
+  k_symv_df<<<nblk(16 * (s->m + 1), 256), 256, 0, s->stream>>>(M->Shi, M->Slo, s->m, M->ldm, M->vhi, M->vlo, q);
   pdk::g_launches += 2;
   if (s->k > 0) {
     k_contact_matvec<<<nblk(s->k, 128), 128, 0, s->stream>>>(s->k, s->c_idx, s->c_w, s->c_s, p, q);
@@ -1445,7 +1461,7 @@ pd_status mixed_iterate(pd_solver* s, const double* g, const double* u0, double*
     for (it = 1; it <= s->opt.max_refine && ce == cudaSuccess; ++it) {
       const int sa = rzs(it), sb = rzs(it + 1);
       // q = H p with p already split by k_cg_dir2
-      k_symv_df<<<nblk(32 * s->m, 256), 256, 0, st>>>(M->Shi, M->Slo, s->m, M->ldm, M->vhi, M->vlo, M->q);
+      k_symv_df<<<nblk(16 * (s->m + 1), 256), 256, 0, st>>>(M->Shi, M->Slo, s->m, M->ldm, M->vhi, M->vlo, M->q);
       ++pdk::g_launches;
       if (s->k > 0) {
         k_contact_matvec<<<nblk(s->k, 128), 128, 0, st>>>(s->k, s->c_idx, s->c_w, s->c_s, M->p, M->q);
