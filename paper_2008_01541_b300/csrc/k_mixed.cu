@@ -411,15 +411,16 @@ __global__ void __launch_bounds__(512) k_gram(const float* __restrict__ Dinv, fl
 }
 
 // Panel solve for the 32-row slab blockIdx.x below tile kt: L_ik = A_ik Dinv_k^T
-// and Lh_ik = L_ik Dinv_k.  128 threads, 4 x 8 outputs each; operands are held
-// k-major in shared memory so every inner step is three 16-byte loads.
+// and Lh_ik = L_ik Dinv_k.  256 threads, 4 x 4 outputs each (warp = 4 rows);
+// operands are held k-major in shared memory so every inner step is two
+// 16-byte loads.
 constexpr int RB = 32, AP = RB + 4, DP = NB + 4;
-__global__ void __launch_bounds__(128) k_trsm_f32(float* __restrict__ L, float* __restrict__ Lh, int64_t mq, int kt,
+__global__ void __launch_bounds__(256) k_trsm_f32(float* __restrict__ L, float* __restrict__ Lh, int64_t mq, int kt,
                                                const float* __restrict__ Dinv, __nv_bfloat16* __restrict__ Pb) {
   extern __shared__ float4 sm4[];
-  float* AT = reinterpret_cast<float*>(sm4);   // [NB][AP]  A^T, later L^T
+  float* AT = reinterpret_cast<float*>(sm4);   // [NB][AP]  A^T, later L row-major
   float* DT = AT + NB * AP;                     // [NB][DP]  Dinv^T, later Dinv
-  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int tid = threadIdx.x, ty = tid >> 5, tx = tid & 31;
   const int64_t r0 = (int64_t)(kt + 1) * NB + (int64_t)blockIdx.x * RB;
   float* Ab = L + r0 * mq + (int64_t)kt * NB;
   float* Hb = Lh + r0 * mq + (int64_t)kt * NB;
@@ -427,90 +428,84 @@ __global__ void __launch_bounds__(128) k_trsm_f32(float* __restrict__ L, float* 
   {
     // consecutive threads take consecutive rows, so the transposed shared
     // stores hit consecutive banks
-    float4 va[8];
+    float4 va[4];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {   // A slab: 32 rows x 32 float4
-      const int q = tid + 128 * k, r = q & 31, c = 4 * (q >> 5);
+    for (int k = 0; k < 4; ++k) {   // A slab: 32 rows x 32 float4
+      const int q = tid + 256 * k, r = q & 31, c = 4 * (q >> 5);
       va[k] = __ldcg(reinterpret_cast<const float4*>(Ab + (int64_t)r * mq + c));
     }
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int q = tid + 128 * k, r = q & 31, c = 4 * (q >> 5);
+    for (int k = 0; k < 4; ++k) {
+      const int q = tid + 256 * k, r = q & 31, c = 4 * (q >> 5);
       AT[(c + 0) * AP + r] = va[k].x; AT[(c + 1) * AP + r] = va[k].y; AT[(c + 2) * AP + r] = va[k].z; AT[(c + 3) * AP + r] = va[k].w;
     }
+    const int row = tid & 127, kh = 16 * (tid >> 7);
 #pragma unroll 4
-    for (int k = 0; k < 32; ++k) {  // Dinv: row tid, float4 k, stored transposed
-      const float4 v = __ldcg(reinterpret_cast<const float4*>(Di + tid * NB + 4 * k));
-      DT[(4 * k + 0) * DP + tid] = v.x; DT[(4 * k + 1) * DP + tid] = v.y;
-      DT[(4 * k + 2) * DP + tid] = v.z; DT[(4 * k + 3) * DP + tid] = v.w;
+    for (int kk = 0; kk < 16; ++kk) {  // Dinv: row `row`, float4 k, stored transposed
+      const int k = kh + kk;
+      const float4 v = __ldcg(reinterpret_cast<const float4*>(Di + row * NB + 4 * k));
+      DT[(4 * k + 0) * DP + row] = v.x; DT[(4 * k + 1) * DP + row] = v.y;
+      DT[(4 * k + 2) * DP + row] = v.z; DT[(4 * k + 3) * DP + row] = v.w;
     }
   }
   __syncthreads();
-  float acc[4][8];
+  float acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
 #pragma unroll 4
   for (int t = 0; t < NB; ++t) {
     const float4 a = *reinterpret_cast<const float4*>(AT + t * AP + 4 * ty);
-    const float4 b0 = *reinterpret_cast<const float4*>(DT + t * DP + 8 * tx);
-    const float4 b1 = *reinterpret_cast<const float4*>(DT + t * DP + 8 * tx + 4);
-    const float av[4] = {a.x, a.y, a.z, a.w}, bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+    const float4 b = *reinterpret_cast<const float4*>(DT + t * DP + 4 * tx);
+    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+      for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
   }
   __syncthreads();
-  // L to global (and its BF16 copy), L^T into AT; Dinv (row-major) into DT
+  // L to global (and its BF16 copy), L row-major into AT; Dinv (row-major) into DT
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int rr = 4 * ty + i;
-    float* dst = Ab + (int64_t)rr * mq + 8 * tx;
-    *reinterpret_cast<float4*>(dst) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-    *reinterpret_cast<float4*>(dst + 4) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+    *reinterpret_cast<float4*>(Ab + (int64_t)rr * mq + 4 * tx) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
     if (Pb) {
-      __nv_bfloat16 hb[8];
+      __nv_bfloat16 hb[4];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) hb[j] = __float2bfloat16_rn(acc[i][j]);
-      *reinterpret_cast<uint4*>(Pb + (r0 + rr) * NB + 8 * tx) = *reinterpret_cast<const uint4*>(hb);
+      for (int j = 0; j < 4; ++j) hb[j] = __float2bfloat16_rn(acc[i][j]);
+      *reinterpret_cast<uint2*>(Pb + (r0 + rr) * NB + 4 * tx) = *reinterpret_cast<const uint2*>(hb);
     }
   }
   float* LS = AT;   // L row-major [RB][DP], reusing the A^T buffer
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    *reinterpret_cast<float4*>(LS + (4 * ty + i) * DP + 8 * tx) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-    *reinterpret_cast<float4*>(LS + (4 * ty + i) * DP + 8 * tx + 4) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
-  }
+  for (int i = 0; i < 4; ++i)
+    *reinterpret_cast<float4*>(LS + (4 * ty + i) * DP + 4 * tx) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
 #pragma unroll 4
-  for (int k = 0; k < 32; ++k) {
-    const int q = tid + 128 * k, r = q >> 5, c = 4 * (q & 31);
+  for (int k = 0; k < 16; ++k) {
+    const int q = tid + 256 * k, r = q >> 5, c = 4 * (q & 31);
     *reinterpret_cast<float4*>(DT + r * DP + c) = __ldcg(reinterpret_cast<const float4*>(Di + r * NB + c));
   }
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
 #pragma unroll 4
   for (int t = 0; t < NB; ++t) {
     const float av[4] = {LS[(4 * ty) * DP + t], LS[(4 * ty + 1) * DP + t], LS[(4 * ty + 2) * DP + t],
                          LS[(4 * ty + 3) * DP + t]};
-    const float4 b0 = *reinterpret_cast<const float4*>(DT + t * DP + 8 * tx);
-    const float4 b1 = *reinterpret_cast<const float4*>(DT + t * DP + 8 * tx + 4);
-    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+    const float4 b = *reinterpret_cast<const float4*>(DT + t * DP + 4 * tx);
+    const float bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+      for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    float* dst = Hb + (int64_t)(4 * ty + i) * mq + 8 * tx;
-    *reinterpret_cast<float4*>(dst) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-    *reinterpret_cast<float4*>(dst + 4) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
-  }
+  for (int i = 0; i < 4; ++i)
+    *reinterpret_cast<float4*>(Hb + (int64_t)(4 * ty + i) * mq + 4 * tx) =
+        make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
 }
 
 
@@ -1216,7 +1211,7 @@ static void factor_panels(pd_solver* s, Factor& f, pdtc::Mode mode, int k_begin 
     const int n = (int)(T - kt - 1);
     if (n <= 0) break;
     __nv_bfloat16* pb = mode == pdtc::BF16 ? f.Pb[kt & 1] : nullptr;
-    k_trsm_f32<<<(unsigned)(n * (NB / RB)), 128, (NB * AP + NB * DP) * 4, st>>>(f.L, f.Lh, mq, kt, f.Dinv, pb);
+    k_trsm_f32<<<(unsigned)(n * (NB / RB)), 256, (NB * AP + NB * DP) * 4, st>>>(f.L, f.Lh, mq, kt, f.Dinv, pb);
     ++pdk::g_launches;
     cudaEventRecord(M->ev_panel[kt], st);
     if (kt > k_begin) cudaStreamWaitEvent(st, M->ev_rest[kt - 1], 0);
