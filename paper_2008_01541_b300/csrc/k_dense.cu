@@ -566,9 +566,9 @@ __device__ __forceinline__ void stage64(double (*tile)[LDA], const double* __res
 
 // One direction of the dense triangular solve with the tiled factor in H
 // (lower, column-major; diagonal tiles replaced by their inverses in Linv),
-// three right-hand sides, in one persistent launch of 4-CTA clusters.  The
+// three right-hand sides, in one persistent launch of 8-CTA clusters.  The
 // first cluster to start becomes the chain: for every block row in solve
-// order its four CTAs (16 rows each, on four SMs, since one SM retires only
+// order its eight CTAs (8 rows each, on eight SMs, since one SM retires only
 // 2 FP64 FMAs per clock) subtract the adjacent row's contribution, exchange
 // the 64 x 3 right-hand side through distributed shared memory, apply the
 // diagonal inverse and exchange y_i, keeping y on chip; the next step's row
@@ -580,7 +580,7 @@ __device__ __forceinline__ void stage64(double (*tile)[LDA], const double* __res
 // cnt[0] claims updates, cnt[1 + j] counts the updates applied to w_j,
 // cnt[1 + T + i] counts the chain CTAs that wrote y_i, cnt[1 + 2T] assigns
 // the chain.
-constexpr int CK = 4;            // CTAs of the chain cluster
+constexpr int CK = 8;            // CTAs of the chain cluster
 constexpr int CR = TB / CK;      // rows per chain CTA
 template <bool FWD>
 __global__ void __cluster_dims__(CK, 1, 1) __launch_bounds__(256)
@@ -598,13 +598,14 @@ __global__ void __cluster_dims__(CK, 1, 1) __launch_bounds__(256)
   const bool chain = *cl.map_shared_rank(&role, 0) == 0;
   cl.sync();    // rank 0's shared memory stays alive until every CTA has read it
   if (chain) {
-    // this CTA's output rows r0 .. r0 + 15 of every block row; sa / sn hold
+    // this CTA's output rows r0 .. r0 + CR - 1 of every block row; sa / sn hold
     // the operand rows of the diagonal inverse / the adjacent tile so that
     // out[rr] = sum_c s[rr][c] vec[c] in both directions
     double (*sa)[LDA] = reinterpret_cast<double (*)[LDA]>(trsv_smem);
     double (*sn)[LDA] = reinterpret_cast<double (*)[LDA]>(trsv_smem + CR * LDA);
     const int r0 = CR * (int)rank;
-    double pa[4], pn[4];
+    constexpr int NF = CR * TB / 256;   // operand entries per thread and tile
+    double pa[NF], pn[NF];
     auto fetch = [&](int i) {
       const double* Li = Linv + (int64_t)i * TB * TB;
       const bool has = FWD ? i > 0 : i < T - 1;
@@ -613,7 +614,7 @@ __global__ void __cluster_dims__(CK, 1, 1) __launch_bounds__(256)
                          : FWD ? H + (int64_t)i * TB + (int64_t)(i - 1) * TB * mp
                                : H + (int64_t)(i + 1) * TB + (int64_t)i * TB * mp;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < NF; ++k) {
         const int e = tid + 256 * k, rr = e % CR, c = e / CR;   // FWD: coalesced down a column
         const int f = tid + 256 * k, c2 = f % TB, rr2 = f / TB; // BWD: coalesced down a column
         if (FWD) {
@@ -627,7 +628,7 @@ __global__ void __cluster_dims__(CK, 1, 1) __launch_bounds__(256)
     };
     auto park = [&]() {
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < NF; ++k) {
         const int e = tid + 256 * k;
         const int rr = FWD ? e % CR : e / TB, c = FWD ? e / CR : e % TB;
         sa[rr][c] = pa[k];
@@ -820,7 +821,7 @@ void chol_solve_fp64_tasks(const double* H, int64_t mp, const double* Linv, cons
   }
   static std::atomic<int> clusters{0};
   if (clusters.load() == 0) {
-    // co-resident 4-CTA clusters of this kernel on the device
+    // co-resident CK-CTA clusters of this kernel on the device
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(CK * 256);
     cfg.blockDim = dim3(256);
