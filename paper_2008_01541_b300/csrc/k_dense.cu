@@ -233,21 +233,6 @@ __global__ void __launch_bounds__(64) k_chol_inv(const double* __restrict__ H, i
     if (i >= c) Z[i] = z[i];
 }
 
-// 64x64x64 FP64 product in shared memory: acc[a][b] = sum_t As[t][r_a] * Bs[t][c_b],
-// r_a = tr + 16a, c_b = tc + 16b.
-__device__ __forceinline__ void tile_mma(const double* As, const double* Bs, int tr, int tc, double acc[4][4]) {
-#pragma unroll 8
-  for (int t = 0; t < TB; ++t) {
-    double a[4], b[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) { a[q] = As[t * TB + tr + 16 * q]; b[q] = Bs[t * TB + tc + 16 * q]; }
-#pragma unroll
-    for (int p = 0; p < 4; ++p)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[p][q] = fma(a[p], b[q], acc[p][q]);
-  }
-}
-
 // L_ik = A_ik L_kk^-T for tiles i > kt by forward substitution: CTA
 // (blockIdx.x / 16) takes tile i = kt + 1 + blockIdx.x / 16, rows
 // 4 * (blockIdx.x % 16) .. + 3, one warp per row with columns lane and
