@@ -812,9 +812,16 @@ void chol_solve_fp64_tasks(const double* H, int64_t mp, const double* Linv, cons
     cfg.blockDim = dim3(256);
     cfg.dynamicSmemBytes = smem;
     int nc = 0;
-    if (cudaOccupancyMaxActiveClusters(&nc, k_trsv_tasks<true>, &cfg) != cudaSuccess || nc < 1) {
+    if (cudaOccupancyMaxActiveClusters(&nc, k_trsv_tasks<true>, &cfg) != cudaSuccess || nc < 2) {
+      // estimate from the per-SM occupancy instead: more clusters than fit at
+      // once only wait to be scheduled (a CTA claims tasks once it runs), but
+      // the chain cluster alone could not make progress
       cudaGetLastError();
-      nc = 1;
+      int dev = 0, nsm = 0, per = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trsv_tasks<true>, 256, smem);
+      nc = std::max(2, nsm * std::max(1, per) / CK);
     }
     clusters.store(nc);
   }
