@@ -42,9 +42,15 @@ typedef enum {
 /* Precision of the collision-region solve H u_2 = g (Algorithm 1, step 4.5). */
 enum {
     PD_FP64 = 0,      /* FP64 blocked Cholesky of H and FP64 triangular solves      */
-    PD_FP32_IR = 1,   /* FP32 factor, FP64-residual iterative refinement            */
-    PD_TF32_IR = 2,   /* TF32 tensor-core trailing updates, FP64-residual refinement */
-    PD_BF16_IR = 3,   /* BF16 tensor-core trailing updates, FP64-residual refinement */
+    PD_FP32_IR = 1,   /* FP32 factor (split-TF32 tensor-core updates), iterative
+                         refinement with FP64-accurate residuals                    */
+    PD_TF32_IR = 2,   /* TF32 tensor-core trailing updates, CG refinement with
+                         FP64-accurate residuals                                   */
+    PD_BF16_IR = 3,   /* BF16 tensor-core trailing updates, CG refinement with
+                         FP64-accurate residuals                                   */
+    /* FP64-accurate residual r = g - H u: FP64 vectors, Sigma_0 u from Sigma_0
+     * held as an FP32 head + tail pair (~48 bits) in double-float arithmetic,
+     * the contact term C_22 u in FP64.                                         */
     PD_PCG_WARM = 4   /* PCG on H preconditioned by the contact-free factor of Sigma,
                          started from a caller-supplied (e.g. learned) guess        */
 };
@@ -175,7 +181,40 @@ pd_status pd_set_detector_spheres(pd_solver* s, const int32_t* proxies, int64_t 
                                   const double* spheres /*[nsph][4]*/, double stiffness);
 pd_status pd_set_detector_pairs(pd_solver* s, const int32_t* side_a, int64_t na, const int32_t* side_b,
                                 int64_t nb, double gap, double stiffness);
+/* Point-triangle self-contact on the device (Algorithm 1, step 4.1; the
+ * paper's proxies are barycentric points of surface elements, Section 3.1):
+ * each side-A proxy node is tested against the side-B surface triangles
+ * tris_b [ntb][3] (node ids, wound so that (b - a) x (c - a) is the outward
+ * normal), and each side-B proxy against tris_a [nta][3].  A node skips the
+ * triangles that lay within rest_min of it in the rest pose (the surface
+ * around it, e.g. across the crease where the two sides meet), takes the
+ * nearest remaining triangle (lowest index on ties) and, if its closest
+ * point q is nearer than gap, gets a two-sided spring on x_node - q (q = the
+ * barycentric combination of the triangle's nodes: slots 0 and 4..6 of the
+ * 8-slot row) of the given stiffness toward gap * n, n the triangle's unit
+ * normal at detection, i.e. the node is pushed to the surface offset by gap
+ * in front of q.  One spring slot per proxy (na + nb); inactive proxies
+ * contribute nothing.  Every node named must lie in x_2.  The arrays are
+ * copied.  Errors: INVALID_ARG (negative counts, null arrays, gap <= 0,
+ * rest_min < 0, non-finite values), CONTACT_OUTSIDE_REGION, CUDA. */
+pd_status pd_set_detector_triangles(pd_solver* s, const int32_t* prox_a, int64_t na, const int32_t* tris_a,
+                                    int64_t nta, const int32_t* prox_b, int64_t nb, const int32_t* tris_b,
+                                    int64_t ntb, double gap, double rest_min, double stiffness);
 pd_status pd_clear_detector(pd_solver* s);
+
+/* Run the device detector once on the current positions (Algorithm 1, step
+ * 4.1 alone, no solve); its springs become the active ones, as they would at
+ * the start of an inner iteration.  Synchronous.  Errors: INVALID_ARG (no
+ * detector set), CUDA. */
+pd_status pd_detect(pd_solver* s);
+
+/* Read back the active spring slots (as pd_set_contact_pairs takes them:
+ * [k][8] node ids with -1 in unused slots, weights, targets [k][3],
+ * stiffness [k]; a detector's inactive slots have stiffness 0 and no nodes).
+ * *k receives the number of slots; at most cap are copied.  Synchronous.
+ * Errors: INVALID_ARG, CUDA. */
+pd_status pd_get_contacts(const pd_solver* s, int64_t cap, int64_t* k, int32_t* nodes /*[cap][8]*/,
+                          double* w /*[cap][8]*/, double* target /*[cap][3]*/, double* stiffness /*[cap]*/);
 
 /* Declare the region nodes that springs may touch (FP64 form).  H = Sigma_0
  * + C_22 has C_22 = 0 outside those rows and columns, so the region is
@@ -272,10 +311,13 @@ pd_status pd_host_schur(const pd_mesh* mesh, const pd_material* mat, double dt,
  *   g_dev, u_dev : [m][3] device right-hand sides and solution
  *   cuda_stream  : stream to run on (NULL = the default stream)
  *   err, err_len : optional buffer for a message
- * The call is synchronous (it reads the pivot status back).  The first call
- * on each device looks up the scratch array's device address; make that
- * first call before any stream capture.  All calls share the one array, so
- * calls that overlap on the GPU (other threads, other streams) race.
+ * The call is synchronous: it copies the contact indices and the pivot
+ * status back to the host and waits for its stream, so it must not be issued
+ * while that stream is being captured.  The first call on each device also
+ * looks up the scratch array's device address.  All calls share the one
+ * array, which keeps the last call's contents (the call rewrites everything
+ * it reads), so calls that overlap on the GPU (other threads, other streams)
+ * race.
  * Errors: INVALID_ARG, CONTACT_OUTSIDE_REGION, NOT_SPD, CUDA. */
 pd_status pd_schur_solve_noalloc(const double* sigma_dev, int64_t m, int64_t k,
                                  const int32_t* cidx_dev, const double* cw_dev, const double* cs_dev,

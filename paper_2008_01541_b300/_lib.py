@@ -65,7 +65,10 @@ _sigs = {
     "pd_set_contact_nodes": (ctypes.c_int, [P, P, I64]),
     "pd_set_detector_spheres": (ctypes.c_int, [P, P, I64, ctypes.c_int, P, D]),
     "pd_set_detector_pairs": (ctypes.c_int, [P, P, I64, P, I64, D, D]),
+    "pd_set_detector_triangles": (ctypes.c_int, [P, P, I64, P, I64, P, I64, P, I64, D, D, D]),
     "pd_clear_detector": (ctypes.c_int, [P]),
+    "pd_detect": (ctypes.c_int, [P]),
+    "pd_get_contacts": (ctypes.c_int, [P, I64, ctypes.POINTER(I64), P, P, P, P]),
     "pd_step": (ctypes.c_int, [P, ctypes.c_int, CB, P]),
     "pd_get_positions": (ctypes.c_int, [P, P]),
     "pd_get_positions_dev": (ctypes.c_int, [P, P]),

@@ -804,32 +804,38 @@ void chol_solve_fp64_tasks(const double* H, int64_t mp, const double* Linv, cons
     cudaFuncSetAttribute(k_trsv_tasks<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(k_trsv_tasks<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   }
-  static std::atomic<int> clusters{0};
-  if (clusters.load() == 0) {
-    // co-resident CK-CTA clusters of this kernel on the device
+  // co-resident CK-CTA clusters of this kernel, cached per device (devices
+  // of different kinds may hold different numbers)
+  static std::atomic<int> clusters[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::atomic<int>& ncache = clusters[dev & 63];
+  if (ncache.load() == 0) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(CK * 256);
     cfg.blockDim = dim3(256);
     cfg.dynamicSmemBytes = smem;
     int nc = 0;
-    if (cudaOccupancyMaxActiveClusters(&nc, k_trsv_tasks<true>, &cfg) != cudaSuccess || nc < 2) {
-      // estimate from the per-SM occupancy instead: more clusters than fit at
-      // once only wait to be scheduled (a CTA claims tasks once it runs), but
-      // the chain cluster alone could not make progress
+    if (cudaOccupancyMaxActiveClusters(&nc, k_trsv_tasks<true>, &cfg) != cudaSuccess) {
+      // estimate from the per-SM occupancy instead: clusters beyond those that
+      // fit at once only wait to be scheduled (a CTA claims tasks once it runs)
       cudaGetLastError();
-      int dev = 0, nsm = 0, per = 0;
-      cudaGetDevice(&dev);
+      int nsm = 0, per = 0;
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trsv_tasks<true>, 256, smem);
-      nc = std::max(2, nsm * std::max(1, per) / CK);
+      nc = nsm * std::max(0, per) / CK;
     }
-    clusters.store(nc);
+    ncache.store(nc >= 2 ? nc : -1);   // -1: the chain cluster could not run beside an update cluster
+  }
+  if (ncache.load() < 0) {
+    chol_solve_fp64(H, mp, Linv, g, u, m, work, st, perm);
+    return;
   }
   const int T = (int)(mp / TB);
   const int ntask = trsv_ntask(T);
   // the chain cluster plus update CTAs, all co-resident, in whole clusters
   const int want = CK + ntask;
-  const unsigned grid = (unsigned)(CK * std::max(1, std::min(clusters.load(), (want + CK - 1) / CK)));
+  const unsigned grid = (unsigned)(CK * std::max(1, std::min(ncache.load(), (want + CK - 1) / CK)));
   double* w = work;
   double* y = work + 3 * mp;
   if (perm) {
@@ -856,11 +862,16 @@ void chol_solve_fp64_tasks(const double* H, int64_t mp, const double* Linv, cons
 }
 
 void chol_solve_fp64(const double* H, int64_t mp, const double* Linv, const double* g, double* u, int64_t m,
-                     double* work, cudaStream_t st) {
+                     double* work, cudaStream_t st, const int32_t* perm) {
   const int T = (int)(mp / TB);
   double* w = work;
   double* y = work + 3 * mp;
-  k_pad_rhs<<<nblk(3 * mp, 256), 256, 0, st>>>(g, m, mp, w);
+  if (perm) {
+    cudaMemsetAsync(w, 0, sizeof(double) * 3 * mp, st);
+    k_perm_scatter<<<nblk(m, 256), 256, 0, st>>>(g, m, perm, w);
+  } else {
+    k_pad_rhs<<<nblk(3 * mp, 256), 256, 0, st>>>(g, m, mp, w);
+  }
   ++g_launches;
   for (int k = 0; k < T; ++k) {
     k_trsv_fwd<<<T - k, 192, 0, st>>>(H, mp, k, Linv, w, y);
@@ -872,7 +883,12 @@ void chol_solve_fp64(const double* H, int64_t mp, const double* Linv, const doub
     k_trsv_bwd<<<k + 1, 192, 0, st>>>(H, mp, k, Linv, w, y);
     ++g_launches;
   }
-  cudaMemcpyAsync(u, y, sizeof(double) * 3 * m, cudaMemcpyDeviceToDevice, st);
+  if (perm) {
+    k_perm_gather<<<nblk(m, 256), 256, 0, st>>>(y, m, perm, u);
+    ++g_launches;
+  } else {
+    cudaMemcpyAsync(u, y, sizeof(double) * 3 * m, cudaMemcpyDeviceToDevice, st);
+  }
 }
 
 void symv3(const double* S, int64_t m, const double* v, double* out, cudaStream_t st) {

@@ -2,17 +2,37 @@
 // run at every inner iteration instead of a host callback.  Every proxy owns
 // one fixed spring slot, so the spring count never has to travel back to the
 // host: an inactive proxy writes an empty slot (no nodes, stiffness 0).
-//   spheres: proxy inside a rigid sphere -> zero-rest-length spring to its
-//            projection on the sphere surface (Section 2.3)
-//   pairs  : side-A proxy within `gap` of its nearest side-B proxy -> two-sided
-//            spring on x_a - x_b toward separation `gap` along their current
-//            direction (self-collision)
+//   spheres : proxy inside a rigid sphere -> zero-rest-length spring to its
+//             projection on the sphere surface (Section 2.3)
+//   pairs   : side-A proxy within `gap` of its nearest side-B proxy -> two-sided
+//             spring on x_a - x_b toward separation `gap` along their current
+//             direction (self-collision)
+//   triangles: proxy node of one side against the surface triangles of the
+//             other side (pairs already within rest_min of each other in the
+//             rest pose are skipped); the nearest triangle, if nearer than
+//             `gap`, gives a two-sided spring on x_a - q (q its closest point,
+//             a barycentric combination of the triangle's nodes, Eq. 5) toward
+//             gap * n, n the triangle's unit normal from its winding
+// Every quantity that decides which obstacle is nearest or whether a proxy is
+// active is computed with explicitly rounded operations (no fused
+// multiply-add) in a fixed order, so the decision is reproducible operation
+// for operation by any IEEE double implementation that follows that order.
 #include "kernels.h"
 
 namespace pdk {
 namespace {
 
 constexpr int NS = CSLOTS;
+
+struct V3 {
+  double x, y, z;
+};
+__device__ __forceinline__ V3 ld3(const double* p) { return {p[0], p[1], p[2]}; }
+__device__ __forceinline__ V3 sub(V3 a, V3 b) { return {__dsub_rn(a.x, b.x), __dsub_rn(a.y, b.y), __dsub_rn(a.z, b.z)}; }
+// (u.x v.x + u.y v.y) + u.z v.z, each operation rounded
+__device__ __forceinline__ double dot(V3 u, V3 v) {
+  return __dadd_rn(__dadd_rn(__dmul_rn(u.x, v.x), __dmul_rn(u.y, v.y)), __dmul_rn(u.z, v.z));
+}
 
 __device__ __forceinline__ void empty_slot(int64_t j, int32_t* cidx, double* cw, double* ct, double* cs) {
   for (int a = 0; a < NS; ++a) { cidx[NS * j + a] = -1; cw[NS * j + a] = 0.0; }
@@ -26,22 +46,24 @@ __global__ void k_detect_spheres(int64_t np, const int32_t* __restrict__ prox_r,
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= np) return;
   const int r = prox_r[j];
-  const double* p = x + 3 * (int64_t)region[r];
+  const V3 p = ld3(x + 3 * (int64_t)region[r]);
   int best = -1;
   double depth = 0.0;
   for (int q = 0; q < ns_sph; ++q) {
-    const double dx = p[0] - sph[4 * q], dy = p[1] - sph[4 * q + 1], dz = p[2] - sph[4 * q + 2];
-    const double d = sqrt(dx * dx + dy * dy + dz * dz), rad = sph[4 * q + 3];
-    if (d < rad && d > 1e-12 && rad - d > depth) { depth = rad - d; best = q; }
+    const V3 d3 = sub(p, ld3(sph + 4 * q));
+    const double d = sqrt(dot(d3, d3)), rad = sph[4 * q + 3];
+    if (d < rad && d > 1e-12 && __dsub_rn(rad, d) > depth) { depth = __dsub_rn(rad, d); best = q; }
   }
   empty_slot(j, cidx, cw, ct, cs);
   if (best < 0) return;
   const double* c = sph + 4 * best;
-  const double dx = p[0] - c[0], dy = p[1] - c[1], dz = p[2] - c[2];
-  const double d = sqrt(dx * dx + dy * dy + dz * dz), s = c[3] / d;
+  const V3 d3 = sub(p, ld3(c));
+  const double s = __ddiv_rn(c[3], sqrt(dot(d3, d3)));
   cidx[NS * j] = r;
   cw[NS * j] = 1.0;
-  ct[3 * j] = c[0] + s * dx; ct[3 * j + 1] = c[1] + s * dy; ct[3 * j + 2] = c[2] + s * dz;
+  ct[3 * j] = __dadd_rn(c[0], __dmul_rn(s, d3.x));
+  ct[3 * j + 1] = __dadd_rn(c[1], __dmul_rn(s, d3.y));
+  ct[3 * j + 2] = __dadd_rn(c[2], __dmul_rn(s, d3.z));
   cs[j] = stiffness;
 }
 
@@ -52,27 +74,153 @@ __global__ void k_detect_pairs(int64_t na, const int32_t* __restrict__ ra_list, 
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= na) return;
   const int ra = ra_list[j];
-  const double* pa = x + 3 * (int64_t)region[ra];
+  const V3 pa = ld3(x + 3 * (int64_t)region[ra]);
   double best = 1e300;
   int bi = -1;
   for (int64_t q = 0; q < nb; ++q) {   // nearest side-B proxy (first index on ties)
-    const double* pb = x + 3 * (int64_t)region[rb_list[q]];
-    const double dx = pa[0] - pb[0], dy = pa[1] - pb[1], dz = pa[2] - pb[2];
-    const double d2 = dx * dx + dy * dy + dz * dz;
+    const V3 d3 = sub(pa, ld3(x + 3 * (int64_t)region[rb_list[q]]));
+    const double d2 = dot(d3, d3);
     if (d2 < best) { best = d2; bi = (int)q; }
   }
   empty_slot(j, cidx, cw, ct, cs);
   const double dist = sqrt(best);
   if (bi < 0 || !(dist < gap) || !(dist > 1e-12)) return;
   const int rb = rb_list[bi];
-  const double* pb = x + 3 * (int64_t)region[rb];
-  const double s = gap / dist;
+  const V3 d3 = sub(pa, ld3(x + 3 * (int64_t)region[rb]));
+  const double s = __ddiv_rn(gap, dist);
   cidx[NS * j] = ra;
   cw[NS * j] = 1.0;
   cidx[NS * j + 4] = rb;
   cw[NS * j + 4] = -1.0;
-  ct[3 * j] = s * (pa[0] - pb[0]); ct[3 * j + 1] = s * (pa[1] - pb[1]); ct[3 * j + 2] = s * (pa[2] - pb[2]);
+  ct[3 * j] = __dmul_rn(s, d3.x); ct[3 * j + 1] = __dmul_rn(s, d3.y); ct[3 * j + 2] = __dmul_rn(s, d3.z);
   cs[j] = stiffness;
+}
+
+// Closest point of the triangle (a, b, c) to p: returns |p - q|^2 and the
+// barycentric weights of q.  The projection on the triangle's plane if its
+// barycentric coordinates lie in [0, 1]; otherwise the nearest of the three
+// segment projections (edges ab, bc, ca; the first on ties).  A zero-area
+// triangle goes through its edges.
+__device__ double closest_on_triangle(V3 p, V3 a, V3 b, V3 c, double* w) {
+  const V3 e0 = sub(b, a), e1 = sub(c, a), pw = sub(p, a);
+  const double d00 = dot(e0, e0), d01 = dot(e0, e1), d11 = dot(e1, e1), d20 = dot(pw, e0), d21 = dot(pw, e1);
+  const double den = __dsub_rn(__dmul_rn(d00, d11), __dmul_rn(d01, d01));
+  if (den > 0.0) {
+    const double s = __ddiv_rn(__dsub_rn(__dmul_rn(d11, d20), __dmul_rn(d01, d21)), den);
+    const double t = __ddiv_rn(__dsub_rn(__dmul_rn(d00, d21), __dmul_rn(d01, d20)), den);
+    if (s >= 0.0 && t >= 0.0 && __dadd_rn(s, t) <= 1.0) {
+      const V3 q = {__dadd_rn(__dadd_rn(a.x, __dmul_rn(s, e0.x)), __dmul_rn(t, e1.x)),
+                    __dadd_rn(__dadd_rn(a.y, __dmul_rn(s, e0.y)), __dmul_rn(t, e1.y)),
+                    __dadd_rn(__dadd_rn(a.z, __dmul_rn(s, e0.z)), __dmul_rn(t, e1.z))};
+      const V3 r = sub(p, q);
+      w[0] = __dsub_rn(__dsub_rn(1.0, s), t);
+      w[1] = s;
+      w[2] = t;
+      return dot(r, r);
+    }
+  }
+  double best = 0.0;
+  const V3 us[3] = {a, b, c};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const V3 u = us[k], v = us[(k + 1) % 3];
+    const V3 e = sub(v, u);
+    const double ee = dot(e, e);
+    double f = ee > 0.0 ? __ddiv_rn(dot(sub(p, u), e), ee) : 0.0;
+    f = f < 0.0 ? 0.0 : (f > 1.0 ? 1.0 : f);
+    const V3 q = {__dadd_rn(u.x, __dmul_rn(f, e.x)), __dadd_rn(u.y, __dmul_rn(f, e.y)),
+                  __dadd_rn(u.z, __dmul_rn(f, e.z))};
+    const V3 r = sub(p, q);
+    const double d2 = dot(r, r);
+    if (k == 0 || d2 < best) {
+      best = d2;
+      w[0] = w[1] = w[2] = 0.0;
+      w[k] = __dsub_rn(1.0, f);
+      w[(k + 1) % 3] = f;
+    }
+  }
+  return best;
+}
+
+// Bounding sphere of each triangle at the current positions, in FP32 and
+// enlarged so that it is never smaller than the exact one.
+__global__ void k_tri_bounds(int64_t nt, const int32_t* __restrict__ tri, const int32_t* __restrict__ region,
+                             const double* __restrict__ x, float4* __restrict__ bnd) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  const V3 a = ld3(x + 3 * (int64_t)region[tri[3 * t]]), b = ld3(x + 3 * (int64_t)region[tri[3 * t + 1]]),
+           c = ld3(x + 3 * (int64_t)region[tri[3 * t + 2]]);
+  const double cx = (a.x + b.x + c.x) / 3.0, cy = (a.y + b.y + c.y) / 3.0, cz = (a.z + b.z + c.z) / 3.0;
+  double r2 = 0.0;
+  for (const V3& v : {a, b, c}) {
+    const double dx = v.x - cx, dy = v.y - cy, dz = v.z - cz;
+    r2 = fmax(r2, dx * dx + dy * dy + dz * dz);
+  }
+  bnd[t] = make_float4((float)cx, (float)cy, (float)cz, (float)(sqrt(r2) * (1.0 + 1e-5) + 1e-6));
+}
+
+// One warp per proxy: lanes scan the triangles q = lane, lane + 32, ... with a
+// conservative FP32 bounding-sphere test, take the exact FP64 closest point
+// for the survivors (rest-pose exclusion first), and the warp keeps the
+// smallest distance, the lowest triangle index on ties -- the same choice as
+// a scan of every triangle in index order.  Slot j of the spring arrays.
+__global__ void __launch_bounds__(256) k_detect_tris(
+    int64_t np, const int32_t* __restrict__ prox, int64_t nt, const int32_t* __restrict__ tri,
+    const float4* __restrict__ bnd, const int32_t* __restrict__ region, const double* __restrict__ x,
+    const double* __restrict__ xr, double gap, double rest_min, double stiffness, int64_t slot0, int32_t* cidx,
+    double* cw, double* ct, double* cs) {
+  const int lane = threadIdx.x & 31;
+  const int64_t j = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (j >= np) return;
+  const int r = prox[j];
+  const V3 p = ld3(x + 3 * (int64_t)region[r]), P = ld3(xr + 3 * (int64_t)r);
+  const float px = (float)p.x, py = (float)p.y, pz = (float)p.z, fg = (float)gap;
+  const double rm2 = __dmul_rn(rest_min, rest_min);
+  double best = 1e300, bw[3] = {0.0, 0.0, 0.0};
+  int64_t bi = -1;
+  for (int64_t q = lane; q < nt; q += 32) {
+    const float4 b = __ldg(bnd + q);
+    const float dx = px - b.x, dy = py - b.y, dz = pz - b.z;
+    const float margin = 1e-4f * (fabsf(b.x) + fabsf(b.y) + fabsf(b.z) + b.w + fg) + 1e-6f;
+    if (sqrtf(dx * dx + dy * dy + dz * dz) > b.w + fg + margin) continue;
+    const int i0 = tri[3 * q], i1 = tri[3 * q + 1], i2 = tri[3 * q + 2];
+    double w[3];
+    const double d2r = closest_on_triangle(P, ld3(xr + 3 * (int64_t)i0), ld3(xr + 3 * (int64_t)i1),
+                                           ld3(xr + 3 * (int64_t)i2), w);
+    if (d2r < rm2) continue;
+    const double d2 = closest_on_triangle(p, ld3(x + 3 * (int64_t)region[i0]), ld3(x + 3 * (int64_t)region[i1]),
+                                          ld3(x + 3 * (int64_t)region[i2]), w);
+    if (d2 < best) { best = d2; bi = q; bw[0] = w[0]; bw[1] = w[1]; bw[2] = w[2]; }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_down_sync(0xffffffffu, best, o);
+    const long long oi = __shfl_down_sync(0xffffffffu, (long long)bi, o);
+    const double o0 = __shfl_down_sync(0xffffffffu, bw[0], o), o1 = __shfl_down_sync(0xffffffffu, bw[1], o),
+                 o2 = __shfl_down_sync(0xffffffffu, bw[2], o);
+    const bool take = oi >= 0 && (bi < 0 || ob < best || (ob == best && oi < bi));
+    if (take) { best = ob; bi = oi; bw[0] = o0; bw[1] = o1; bw[2] = o2; }
+  }
+  if (lane != 0) return;
+  const int64_t sj = slot0 + j;
+  empty_slot(sj, cidx, cw, ct, cs);
+  if (bi < 0 || !(sqrt(best) < gap)) return;
+  const int i0 = tri[3 * bi], i1 = tri[3 * bi + 1], i2 = tri[3 * bi + 2];
+  const V3 A = ld3(x + 3 * (int64_t)region[i0]), B = ld3(x + 3 * (int64_t)region[i1]),
+           C = ld3(x + 3 * (int64_t)region[i2]);
+  const V3 e0 = sub(B, A), e1 = sub(C, A);
+  const V3 n = {__dsub_rn(__dmul_rn(e0.y, e1.z), __dmul_rn(e0.z, e1.y)),
+                __dsub_rn(__dmul_rn(e0.z, e1.x), __dmul_rn(e0.x, e1.z)),
+                __dsub_rn(__dmul_rn(e0.x, e1.y), __dmul_rn(e0.y, e1.x))};
+  const double nn = sqrt(dot(n, n));
+  if (!(nn > 0.0)) return;
+  const double s = __ddiv_rn(gap, nn);
+  cidx[NS * sj] = r;
+  cw[NS * sj] = 1.0;
+  cidx[NS * sj + 4] = i0; cidx[NS * sj + 5] = i1; cidx[NS * sj + 6] = i2;
+  cw[NS * sj + 4] = -bw[0]; cw[NS * sj + 5] = -bw[1]; cw[NS * sj + 6] = -bw[2];
+  ct[3 * sj] = __dmul_rn(s, n.x); ct[3 * sj + 1] = __dmul_rn(s, n.y); ct[3 * sj + 2] = __dmul_rn(s, n.z);
+  cs[sj] = stiffness;
 }
 
 inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
@@ -93,6 +241,27 @@ void detect_pairs(int64_t na, const int32_t* ra, int64_t nb, const int32_t* rb, 
   if (na <= 0) return;
   k_detect_pairs<<<nblk(na, 128), 128, 0, st>>>(na, ra, nb, rb, region, x, gap, stiffness, cidx, cw, ct, cs);
   ++g_launches;
+}
+
+void detect_tris(const TriDetector& d, const int32_t* region, const double* x, int32_t* cidx, double* cw, double* ct,
+                 double* cs, cudaStream_t st) {
+  const int64_t nt = d.nta + d.ntb;
+  if (nt > 0) {
+    k_tri_bounds<<<nblk(nt, 128), 128, 0, st>>>(nt, d.tris, region, x, d.bnd);
+    ++g_launches;
+  }
+  // side-A proxies against side-B triangles, then side-B proxies against side-A triangles
+  const int32_t* tris_b = d.tris + 3 * d.nta;
+  if (d.na > 0) {
+    k_detect_tris<<<nblk(d.na, 8), 256, 0, st>>>(d.na, d.prox, d.ntb, tris_b, d.bnd + d.nta, region, x, d.xr, d.gap,
+                                                 d.rest_min, d.stiffness, 0, cidx, cw, ct, cs);
+    ++g_launches;
+  }
+  if (d.nb > 0) {
+    k_detect_tris<<<nblk(d.nb, 8), 256, 0, st>>>(d.nb, d.prox + d.na, d.nta, d.tris, d.bnd, region, x, d.xr, d.gap,
+                                                 d.rest_min, d.stiffness, d.na, cidx, cw, ct, cs);
+    ++g_launches;
+  }
 }
 
 }  // namespace pdk

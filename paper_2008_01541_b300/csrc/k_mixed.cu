@@ -4,7 +4,9 @@
 // Cholesky (128 x 128 tiles): FP32 diagonal-tile factorisation and inversion,
 // FP32 panel solve, and tcgen05 trailing updates in TF32, split TF32 (three
 // products, ~FP32 accuracy) or BF16, all accumulated in FP32.  Accuracy is
-// recovered with FP64 residuals r = g - H u: plain iterative refinement for
+// recovered with FP64-accurate residuals r = g - H u (FP64 vectors; Sigma_0 u
+// from Sigma_0 stored as an FP32 head + tail pair, ~48 bits, multiplied in
+// double-float arithmetic; the contact term in FP64): plain iterative refinement for
 // the split-TF32 factor, and refinement accelerated by preconditioned CG for
 // TF32 and BF16.  PD_PCG_WARM runs PCG on H with the contact-free factor of
 // Sigma_0 (computed once) as the preconditioner, started from a given guess.
@@ -1421,7 +1423,8 @@ pd_status mixed_iterate(pd_solver* s, const double* g, const double* u0, double*
   const bool use_cg = warm || mode != pdtc::TF32X3;
   cudaError_t ce = cudaSuccess;
   if (!ok && !use_cg) {
-    // classic refinement: u += M^-1 r; r = g - H u (FP64)
+    // classic refinement: u += M^-1 r; r = g - H u (FP64 vectors; Sigma_0 u in
+    // double-float arithmetic from the ~48-bit FP32 pair, the contact term in FP64)
     for (it = 1; it <= s->opt.max_refine; ++it) {
       ce = precond(s, *f, M->r, M->z);
       if (ce != cudaSuccess) break;

@@ -108,9 +108,11 @@ void block_copy(double* H, int64_t mp, int64_t off, double* B, int64_t n, bool t
 // Solve (L L^T) u = g for 3 right-hand sides, g/u [m][3] (padded internally),
 // one launch per block step.
 void chol_solve_fp64(const double* H, int64_t mp, const double* Linv, const double* g, double* u,
-                     int64_t m, double* work /*[mp][3] x 2*/, cudaStream_t st);
+                     int64_t m, double* work /*[mp][3] x 2*/, cudaStream_t st, const int32_t* perm = nullptr);
 // The same solve as two persistent launches of dependency-counter tasks;
 // cnt: [1 + 2 mp/64] ints of scratch, status[1] <- 302 if a wait gave up.
+// A device on which the chain cluster cannot run beside an update cluster
+// takes the per-step solve instead.
 // perm (optional): region index -> factor position of a permuted factor.
 void chol_solve_fp64_tasks(const double* H, int64_t mp, const double* Linv, const double* g, double* u,
                            int64_t m, double* work /*[mp][3] x 2*/, int* cnt, int* status, cudaStream_t st,
@@ -128,6 +130,21 @@ void detect_spheres(int64_t np, const int32_t* prox_r, const int32_t* region, co
 void detect_pairs(int64_t na, const int32_t* ra, int64_t nb, const int32_t* rb, const int32_t* region,
                   const double* x, double gap, double stiffness, int32_t* cidx, double* cw, double* ct, double* cs,
                   cudaStream_t st);
+// Point-triangle detector: na side-A proxies then nb side-B proxies (region
+// indices, prox[0 .. na + nb)), nta side-A triangles then ntb side-B
+// triangles (region indices, tris[0 .. 3 (nta + ntb))), rest positions of the
+// region nodes xr [m][3], bounding-sphere scratch bnd [nta + ntb].  Slots
+// 0 .. na + nb of the spring arrays, one per proxy.
+struct TriDetector {
+  int64_t na = 0, nb = 0, nta = 0, ntb = 0;
+  const int32_t* prox = nullptr;
+  const int32_t* tris = nullptr;
+  const double* xr = nullptr;
+  float4* bnd = nullptr;
+  double gap = 0.0, rest_min = 0.0, stiffness = 0.0;
+};
+void detect_tris(const TriDetector& d, const int32_t* region, const double* x, int32_t* cidx, double* cw, double* ct,
+                 double* cs, cudaStream_t st);
 // Algorithm 1, 4.6-4.7: x2 += u2, U2 += u2, ft2 -= (Su - Bu)   (Bu already in Su: Su holds Sigma_alpha u)
 void inner_update(int64_t m, const double* u2, const double* Sau, const int32_t* region, double* x,
                   double* U2, double* ft2, cudaStream_t st);

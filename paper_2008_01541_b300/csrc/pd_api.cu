@@ -426,6 +426,7 @@ void pd_destroy(pd_solver* s) {
   for (void* p : s->allocs) cudaFree(p);
   cudaFree(s->c_idx); cudaFree(s->c_w); cudaFree(s->c_t); cudaFree(s->c_s);
   cudaFree(s->det_a); cudaFree(s->det_b); cudaFree(s->det_sph);
+  cudaFree(s->tri_prox); cudaFree(s->tri_idx); cudaFree(s->tri_xr); cudaFree(s->tri_bnd);
   cudaFree(s->Sp);
   if (s->x2_host) cudaFreeHost(s->x2_host);
   if (s->status_h) cudaFreeHost(s->status_h);
@@ -568,6 +569,94 @@ pd_status pd_set_detector_pairs(pd_solver* s, const int32_t* side_a, int64_t na,
   s->det_gap = gap;
   s->det_stiffness = stiffness;
   s->detector = 2;
+  return PD_OK;
+}
+
+pd_status pd_set_detector_triangles(pd_solver* s, const int32_t* prox_a, int64_t na, const int32_t* tris_a,
+                                    int64_t nta, const int32_t* prox_b, int64_t nb, const int32_t* tris_b,
+                                    int64_t ntb, double gap, double rest_min, double stiffness) {
+  if (!s || na < 0 || nb < 0 || nta < 0 || ntb < 0 || (na > 0 && !prox_a) || (nb > 0 && !prox_b) ||
+      (nta > 0 && !tris_a) || (ntb > 0 && !tris_b) || !(gap > 0) || !(rest_min >= 0) || !std::isfinite(rest_min) ||
+      !std::isfinite(gap) || !std::isfinite(stiffness))
+    return PD_ERR_INVALID_ARG;
+  // every proxy and triangle node must be a region node (a contact node in the nested form)
+  std::vector<int32_t> prox(na + nb), tris(3 * (nta + ntb));
+  auto to_region = [&](int32_t node, int32_t* out) -> pd_status {
+    if (node < 0 || node >= s->n || s->region_index[node] < 0) {
+      s->err = "detector node " + std::to_string(node) + " is not in the region";
+      return PD_ERR_CONTACT_OUTSIDE_REGION;
+    }
+    if (s->nested && !s->contact_ok[s->region_index[node]]) {
+      s->err = "detector node " + std::to_string(node) + " is not one of the contact nodes";
+      return PD_ERR_CONTACT_OUTSIDE_REGION;
+    }
+    *out = s->region_index[node];
+    return PD_OK;
+  };
+  for (int64_t i = 0; i < na + nb; ++i) {
+    pd_status r = to_region(i < na ? prox_a[i] : prox_b[i - na], &prox[i]);
+    if (r != PD_OK) return r;
+  }
+  for (int64_t i = 0; i < 3 * (nta + ntb); ++i) {
+    pd_status r = to_region(i < 3 * nta ? tris_a[i] : tris_b[i - 3 * nta], &tris[i]);
+    if (r != PD_OK) return r;
+  }
+  pd_status r = detector_buffers(s, na + nb);
+  if (r != PD_OK) return r;
+  cudaFree(s->tri_prox); cudaFree(s->tri_idx); cudaFree(s->tri_bnd);
+  s->tri_prox = s->tri_idx = nullptr;
+  s->tri_bnd = nullptr;
+  CK(cudaMalloc(&s->tri_prox, sizeof(int32_t) * std::max<int64_t>(1, na + nb)));
+  CK(cudaMalloc(&s->tri_idx, sizeof(int32_t) * std::max<int64_t>(1, 3 * (nta + ntb))));
+  CK(cudaMalloc(&s->tri_bnd, sizeof(float4) * std::max<int64_t>(1, nta + ntb)));
+  if (na + nb) CK(cudaMemcpy(s->tri_prox, prox.data(), sizeof(int32_t) * (na + nb), cudaMemcpyHostToDevice));
+  if (nta + ntb) CK(cudaMemcpy(s->tri_idx, tris.data(), sizeof(int32_t) * 3 * (nta + ntb), cudaMemcpyHostToDevice));
+  if (!s->tri_xr) {   // rest positions of the region nodes, region order
+    std::vector<double> xr(3 * s->m);
+    for (int64_t i = 0; i < s->m; ++i)
+      for (int c = 0; c < 3; ++c) xr[3 * i + c] = s->X_rest_h[3 * (int64_t)s->region_h[i] + c];
+    CK(cudaMalloc(&s->tri_xr, sizeof(double) * 3 * s->m));
+    CK(cudaMemcpy(s->tri_xr, xr.data(), sizeof(double) * 3 * s->m, cudaMemcpyHostToDevice));
+  }
+  s->tri.na = na; s->tri.nb = nb; s->tri.nta = nta; s->tri.ntb = ntb;
+  s->tri.prox = s->tri_prox; s->tri.tris = s->tri_idx; s->tri.xr = s->tri_xr; s->tri.bnd = s->tri_bnd;
+  s->tri.gap = gap; s->tri.rest_min = rest_min; s->tri.stiffness = stiffness;
+  s->det_n = na + nb;
+  s->detector = 3;
+  return PD_OK;
+}
+
+pd_status pd_detect(pd_solver* s) {
+  if (!s) return PD_ERR_INVALID_ARG;
+  if (!s->detector) { s->err = "no detector is set"; return PD_ERR_INVALID_ARG; }
+  if (s->detector == 1)
+    pdk::detect_spheres(s->det_n, s->det_a, s->d_region, s->x, s->nsph, s->det_sph, s->det_stiffness, s->c_idx, s->c_w,
+                        s->c_t, s->c_s, s->stream);
+  else if (s->detector == 2)
+    pdk::detect_pairs(s->det_n, s->det_a, s->det_nb, s->det_b, s->d_region, s->x, s->det_gap, s->det_stiffness,
+                      s->c_idx, s->c_w, s->c_t, s->c_s, s->stream);
+  else
+    pdk::detect_tris(s->tri, s->d_region, s->x, s->c_idx, s->c_w, s->c_t, s->c_s, s->stream);
+  s->k = s->det_n;
+  CK(cudaStreamSynchronize(s->stream));
+  return PD_OK;
+}
+
+pd_status pd_get_contacts(const pd_solver* s, int64_t cap, int64_t* k, int32_t* nodes, double* w, double* target,
+                          double* stiffness) {
+  if (!s || !k || cap < 0 || (cap > 0 && (!nodes || !w || !target || !stiffness))) return PD_ERR_INVALID_ARG;
+  *k = s->k;
+  const int64_t n = std::min(cap, s->k);
+  if (n <= 0) return PD_OK;
+  constexpr int NS = pdk::CSLOTS;
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess ||
+      cudaMemcpy(nodes, s->c_idx, sizeof(int32_t) * NS * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(w, s->c_w, sizeof(double) * NS * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(target, s->c_t, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(stiffness, s->c_s, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return PD_ERR_CUDA;
+  for (int64_t q = 0; q < NS * n; ++q)   // region index -> node id
+    if (nodes[q] >= 0) nodes[q] = s->region_h[nodes[q]];
   return PD_OK;
 }
 
@@ -947,9 +1036,11 @@ pd_status pd_solver::step(int outer_iters, pd_contact_cb cb, void* user) {
       tbegin(3);
       if (detector == 1)
         pdk::detect_spheres(det_n, det_a, d_region, x, nsph, det_sph, det_stiffness, c_idx, c_w, c_t, c_s, stream);
-      else
+      else if (detector == 2)
         pdk::detect_pairs(det_n, det_a, det_nb, det_b, d_region, x, det_gap, det_stiffness, c_idx, c_w, c_t, c_s,
                           stream);
+      else
+        pdk::detect_tris(tri, d_region, x, c_idx, c_w, c_t, c_s, stream);
       tend();
       k = det_n;
     }

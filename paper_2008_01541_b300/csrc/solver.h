@@ -95,13 +95,17 @@ struct pd_solver {
   int64_t k = 0, kcap = 0;
   int32_t* c_idx = nullptr;
   double *c_w = nullptr, *c_t = nullptr, *c_s = nullptr;
-  // device collision detection (0 = off, 1 = spheres, 2 = pairs)
+  // device collision detection (0 = off, 1 = spheres, 2 = pairs, 3 = point-triangle)
   int detector = 0;
   int64_t det_n = 0, det_nb = 0;
   int nsph = 0;
   int32_t *det_a = nullptr, *det_b = nullptr;   // region indices
   double* det_sph = nullptr;                    // [nsph][4]
   double det_gap = 0.0, det_stiffness = 0.0;
+  pdk::TriDetector tri;                         // point-triangle detector (device arrays owned here)
+  int32_t *tri_prox = nullptr, *tri_idx = nullptr;
+  double* tri_xr = nullptr;
+  float4* tri_bnd = nullptr;
   // bookkeeping
   pd_stats stats{};
   std::string err;

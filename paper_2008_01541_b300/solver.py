@@ -112,6 +112,31 @@ class Solver:
         b = _c(side_b, np.int32)
         self._check(lib.pd_set_detector_pairs(self.h, _ptr(a), len(a), _ptr(b), len(b), float(gap), float(stiffness)))
 
+    def set_detector_triangles(self, prox_a, tris_a, prox_b, tris_b, gap, rest_min, stiffness):
+        """Point-triangle self-contact: side-A nodes against side-B triangles
+        and side-B nodes against side-A triangles (outward-wound [nt, 3])."""
+        pa, pb = _c(prox_a, np.int32), _c(prox_b, np.int32)
+        ta, tb = _c(tris_a, np.int32).reshape(-1, 3), _c(tris_b, np.int32).reshape(-1, 3)
+        self._check(lib.pd_set_detector_triangles(self.h, _ptr(pa), len(pa), _ptr(ta), len(ta), _ptr(pb), len(pb),
+                                                  _ptr(tb), len(tb), float(gap), float(rest_min), float(stiffness)))
+
+    def detect(self):
+        """Run the device detector once on the current positions."""
+        self._check(lib.pd_detect(self.h))
+
+    def contacts(self):
+        """The active spring slots: (nodes [k,8], w [k,8], target [k,3], stiffness [k])."""
+        k = ctypes.c_int64()
+        self._check(lib.pd_get_contacts(self.h, 0, ctypes.byref(k), None, None, None, None))
+        n = k.value
+        nodes = np.empty((n, 8), np.int32)
+        w = np.empty((n, 8))
+        t = np.empty((n, 3))
+        c = np.empty(n)
+        if n:
+            self._check(lib.pd_get_contacts(self.h, n, ctypes.byref(k), _ptr(nodes), _ptr(w), _ptr(t), _ptr(c)))
+        return nodes, w, t, c
+
     def clear_detector(self):
         self._check(lib.pd_clear_detector(self.h))
 

@@ -19,8 +19,8 @@ def he_init(seed):
 
 def indenter_path(scene, seed, steps, radius=None, step_len=None):
     """Seeded random walk of a rigid sphere over the collision-prone surface.
-    Returns a list of sphere centres (one per time step)."""
-    import scenes
+    Returns a list of sphere centres (one per time step).  `scene` is any
+    object with rest positions X, proxies and an info dict (spacing h)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     P = scene.X[scene.proxies]
     h = scene.info.get("h", 1.0)
@@ -37,20 +37,17 @@ def indenter_path(scene, seed, steps, radius=None, step_len=None):
 
 
 def run_path(solver, scene, centres, radius, outer=1, depth=0.3):
-    """One pd_step per centre; contacts from the sphere pushed `depth*radius`
-    into the surface, detected at every inner iteration."""
-    import scenes
-    x_ref = scene.X.copy()
+    """One pd_step per centre with the sphere pushed `depth*radius` into the
+    surface; the library's device detector re-detects the proxies inside it
+    at every inner iteration (Algorithm 1, step 4.1).  The detector is
+    cleared afterwards.  Returns the refinement / PCG iterations per step."""
     iters = []
-    for c in centres:
-        ctr = np.asarray(c)
-
-        def cb(x2, ctr=ctr):
-            x = x_ref.copy()
-            x[scene.region] = x2
-            con = scenes.sphere_contacts(scene.proxies, x, ctr, radius * (1.0 + depth), scene.stiffness)
-            return (con.nodes, con.w, con.target, con.stiffness)
-
-        solver.step(outer, cb)
-        iters.append(solver.stats()["refine_iters"])
+    try:
+        for c in centres:
+            sph = np.array([[c[0], c[1], c[2], radius * (1.0 + depth)]], dtype=np.float64)
+            solver.set_detector_spheres(scene.proxies, sph, scene.stiffness)
+            solver.step(outer)
+            iters.append(solver.stats()["refine_iters"])
+    finally:
+        solver.clear_detector()
     return iters

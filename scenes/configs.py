@@ -9,7 +9,7 @@ from typing import Callable, Optional
 import math
 import numpy as np
 
-from .mesh import voxel_mesh, grid_mesh, boundary_nodes, jitter_interior, node_adjacency
+from .mesh import voxel_mesh, grid_mesh, boundary_nodes, boundary_faces_outward, jitter_interior, node_adjacency
 
 
 @dataclass
@@ -274,6 +274,15 @@ def elbow(h=0.585, seed=0, region_fraction=0.05, inner_iters=1, contact_mode="se
 
     all_a = proxies[(X[proxies, 0] + X[proxies, 1]) < 0.0]
     all_b = proxies[(X[proxies, 0] + X[proxies, 1]) >= 0.0]
+    # point-triangle self-contact (config 2): the outward surface triangles of
+    # the region, split by the same plane; a side's nodes are tested against
+    # the other side's triangles, skipping pairs within 3h at rest (the
+    # surface that runs continuously through the crease)
+    faces = boundary_faces_outward(X, tets)
+    faces = faces[in_region[faces].all(axis=1)]
+    fc = X[faces].mean(axis=1)
+    tris_a = faces[(fc[:, 0] + fc[:, 1]) < 0.0].astype(np.int32)
+    tris_b = faces[(fc[:, 0] + fc[:, 1]) >= 0.0].astype(np.int32)
 
     def self_pairs(x, gap=None):
         return pair_contacts(all_a, all_b, x, 2.0 * h if gap is None else gap, stiffness)
@@ -283,7 +292,8 @@ def elbow(h=0.585, seed=0, region_fraction=0.05, inner_iters=1, contact_mode="se
                  stiffness=stiffness, dirichlet_positions=dirichlet_positions,
                  contacts=contacts,
                  info={"h": h, "theta": theta, "rest_step": 45, "self_pairs": self_pairs,
-                       "pair_sides": (all_a, all_b)})
+                       "pair_sides": (all_a, all_b), "tri_sides": (all_a, tris_a, all_b, tris_b),
+                       "tri_gap": h, "tri_rest_min": 3.0 * h})
 
 
 def small_elbow(h=2.0, seed=0, region_fraction=0.05, inner_iters=1):

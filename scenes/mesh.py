@@ -77,6 +77,18 @@ def boundary_faces(tets):
     return faces[idx[cnt == 1]]
 
 
+def boundary_faces_outward(X, tets):
+    """Boundary triangles [F, 3] wound so that (b - a) x (c - a) points out of
+    the mesh: for a positively oriented tet (0, 1, 2, 3) the faces (0, 2, 1),
+    (0, 1, 3), (0, 3, 2) and (1, 2, 3) face away from the opposite vertex."""
+    tets = _orient(X, np.asarray(tets, dtype=np.int64))
+    faces = np.concatenate([tets[:, [0, 2, 1]], tets[:, [0, 1, 3]],
+                            tets[:, [0, 3, 2]], tets[:, [1, 2, 3]]])
+    key = np.sort(faces, axis=1)
+    _, idx, cnt = np.unique(key, axis=0, return_index=True, return_counts=True)
+    return faces[np.sort(idx[cnt == 1])].astype(np.int32)
+
+
 def boundary_nodes(tets, n):
     """Boolean mask of nodes on the mesh boundary."""
     mask = np.zeros(n, dtype=bool)

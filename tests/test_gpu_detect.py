@@ -1,9 +1,11 @@
 """Collision detection on the device (Algorithm 1, step 4.1) vs the oracle
-with the same detection done on the host at every inner iteration."""
+with the same detection done on the host at every inner iteration, by the
+brute-force references of oracle/detect.py."""
 import numpy as np
 import pytest
 
 import oracle
+from oracle import detect
 import scenes
 from gpu_util import need_gpu, rng
 
@@ -26,6 +28,14 @@ def _oracle(s):
     return oracle.OracleSolver(s.X, s.tets, s.dirichlet, s.region, s.mu, s.density, s.dt)
 
 
+def _spheres_fn(proxies, spheres, stiffness):
+    return lambda x: scenes.Contacts(*detect.sphere_springs(proxies, x, spheres, stiffness)[:4])
+
+
+def _pairs_fn(side_a, side_b, gap, stiffness):
+    return lambda x: scenes.Contacts(*detect.nearest_pair_springs(side_a, side_b, x, gap, stiffness)[:4])
+
+
 def test_sphere_detector_trajectory_matches_oracle(pd):
     # 3 backward-Euler steps x 10 outer x 2 inner iterations, the descending
     # sphere re-detected against the current x_2 at every inner iteration
@@ -36,11 +46,13 @@ def test_sphere_detector_trajectory_matches_oracle(pd):
     centre = s.info["sphere_centre"]
     active = 0
     for st in range(3):
+        sph = np.r_[centre(st), 3.0][None, :]
+        fn = _spheres_fn(s.proxies, sph, s.stiffness)
         sol.set_dirichlet(s.dirichlet_positions(st))
-        sol.set_detector_spheres(s.proxies, np.r_[centre(st), 3.0][None, :], s.stiffness)
+        sol.set_detector_spheres(s.proxies, sph, s.stiffness)
         sol.step(s.outer_iters)
-        o.step(s.outer_iters, s_inner, lambda x, st=st: s.contacts(st, x), s.dirichlet_positions(st))
-        active = max(active, s.contacts(st, o.x).k)
+        o.step(s.outer_iters, s_inner, fn, s.dirichlet_positions(st))
+        active = max(active, fn(o.x).k)
     xg, vg = sol.get_state()
     assert active > 0
     err = np.linalg.norm(xg - o.x) / np.linalg.norm(o.x - s.X)
@@ -64,10 +76,12 @@ def test_sphere_detector_equals_host_callback(pd):
     b = _solver(pd, s, inner_iters=3)
     b.set_state(x0)
 
+    fn = _spheres_fn(s.proxies, spheres, s.stiffness)
+
     def cb(x2):
         x = x0.copy()
         x[s.region] = x2
-        cc = scenes.sphere_contacts(s.proxies, x, c, 3.0, s.stiffness)
+        cc = fn(x)
         return (cc.nodes, cc.w, cc.target, cc.stiffness)
 
     b.step(2, cb)
@@ -79,9 +93,9 @@ def test_pair_detector_matches_oracle(pd):
     # two-sided self-collision springs re-detected on the device
     s = scenes.small_elbow(h=1.5)
     x0 = s.X.copy()
-    fn = s.info["self_pairs"]
-    assert fn(x0, gap=6.0).k > 5
     side_a, side_b = s.info["pair_sides"]
+    fn = _pairs_fn(side_a, side_b, 6.0, s.stiffness)
+    assert fn(x0).k > 5
     sol = _solver(pd, s, inner_iters=2)
     sol.set_state(x0)
     sol.set_dirichlet(s.dirichlet_positions(50))
@@ -89,7 +103,7 @@ def test_pair_detector_matches_oracle(pd):
     sol.step(2)
     o = oracle.OracleSolver(s.X, s.tets, s.dirichlet, s.region, s.mu)
     o.x = x0.copy()
-    xo = o.step(2, 2, lambda x: fn(x, gap=6.0), s.dirichlet_positions(50))
+    xo = o.step(2, 2, fn, s.dirichlet_positions(50))
     err = np.linalg.norm(sol.positions() - xo) / np.linalg.norm(xo - x0)
     assert err <= TOL, err
 
@@ -116,3 +130,98 @@ def test_detector_errors_and_clear(pd):
     sol.set_detector_spheres(s.proxies, np.array([[100.0, 0, 0, 1.0]]), 1e6)
     sol.step(2)
     assert np.array_equal(x_det, sol.positions())
+
+
+def _closed_elbow(h=1.5, frac=0.08, angle=30.0):
+    """Small elbow with every side-B node turned rigidly by `angle` about the
+    hinge (the joint closed by that much), so that side-A nodes come within
+    the gap of side-B triangles; the caps at the matching flexion step."""
+    s = scenes.small_elbow(h=h, region_fraction=frac)
+    x0 = s.X.copy()
+    side_b = (s.X[:, 0] + s.X[:, 1]) >= 0.0
+    x0[side_b] = s.X[side_b] @ scenes.rotation_z(np.radians(angle)).T
+    step = int(round(45 + angle / 2.0))
+    return s, x0, s.dirichlet_positions(step)
+
+
+def _tri_fn(s):
+    pa, ta, pb, tb = s.info["tri_sides"]
+    gap, rmin = s.info["tri_gap"], s.info["tri_rest_min"]
+
+    def fn(x):
+        A = detect.point_triangle_springs(pa, tb, x, s.X, gap, rmin, s.stiffness)
+        B = detect.point_triangle_springs(pb, ta, x, s.X, gap, rmin, s.stiffness)
+        return scenes.Contacts(*(np.concatenate([A[i], B[i]]) for i in range(4)))
+
+    return fn
+
+
+def _set_tri(sol, s):
+    pa, ta, pb, tb = s.info["tri_sides"]
+    sol.set_detector_triangles(pa, ta, pb, tb, s.info["tri_gap"], s.info["tri_rest_min"], s.stiffness)
+
+
+def test_triangle_detector_springs_equal_oracle(pd):
+    # the detected springs themselves: which nodes are active, which triangle
+    # and which closest point (decisions bit for bit), weights and targets
+    s, x0, dpos = _closed_elbow()
+    sol = _solver(pd, s)
+    sol.set_state(x0)
+    _set_tri(sol, s)
+    sol.detect()
+    nodes, w, t, c = sol.contacts()
+    pa, ta, pb, tb = s.info["tri_sides"]
+    assert len(c) == len(pa) + len(pb)
+    ref = _tri_fn(s)(x0)
+    act = c > 0
+    assert act.sum() == ref.k and ref.k >= 20
+    np.testing.assert_array_equal(nodes[act], ref.nodes)
+    np.testing.assert_array_equal(w[act], ref.w)
+    np.testing.assert_array_equal(t[act], ref.target)
+    np.testing.assert_array_equal(c[act], ref.stiffness)
+    assert np.all(nodes[~act] == -1) and np.all(w[~act] == 0.0)
+
+
+@pytest.mark.parametrize("inner", [1, 2])
+def test_triangle_detector_step_matches_oracle(pd, inner):
+    # one step of 2 outer iterations from the closed pose, the springs
+    # re-detected on the device at every inner iteration
+    s, x0, dpos = _closed_elbow()
+    fn = _tri_fn(s)
+    assert fn(x0).k >= 20
+    sol = _solver(pd, s, inner_iters=inner)
+    sol.set_state(x0)
+    sol.set_dirichlet(dpos)
+    _set_tri(sol, s)
+    sol.step(2)
+    o = oracle.OracleSolver(s.X, s.tets, s.dirichlet, s.region, s.mu)
+    o.x = x0.copy()
+    xo = o.step(2, inner, fn, dpos)
+    xg = sol.positions()
+    scale = np.abs(xo - x0).max()
+    assert np.abs(xg - xo).max() / scale <= TOL
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo - x0) <= TOL
+
+
+def test_triangle_detector_errors(pd):
+    s, x0, dpos = _closed_elbow(h=2.0, frac=0.05)
+    sol = _solver(pd, s)
+    pa, ta, pb, tb = s.info["tri_sides"]
+    outside = np.setdiff1d(np.arange(s.n), s.region)[:1]
+    with pytest.raises(RuntimeError):
+        sol.set_detector_triangles(outside, ta, pb, tb, 1.0, 1.0, 1e6)
+    bad = ta.copy()
+    bad[0, 1] = outside[0]
+    with pytest.raises(RuntimeError):
+        sol.set_detector_triangles(pa, bad, pb, tb, 1.0, 1.0, 1e6)
+    with pytest.raises(RuntimeError):
+        sol.set_detector_triangles(pa, ta, pb, tb, 0.0, 1.0, 1e6)
+    with pytest.raises(RuntimeError):
+        sol.set_detector_triangles(pa, ta, pb, tb, 1.0, -1.0, 1e6)
+    with pytest.raises(RuntimeError):
+        sol.detect()                      # no detector set
+    # at rest nothing is within the gap: every slot empty
+    sol.set_detector_triangles(pa, ta, pb, tb, s.info["tri_gap"], s.info["tri_rest_min"], 1e6)
+    sol.detect()
+    _, _, _, c = sol.contacts()
+    assert len(c) == len(pa) + len(pb) and np.all(c == 0.0)

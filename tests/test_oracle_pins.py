@@ -339,6 +339,48 @@ def test_backward_euler_rest_state_stays_at_rest():
     np.testing.assert_allclose(o.v, 0.0, atol=1e-10)
 
 
+def _read_gold_tagged(name):
+    rows = {}
+    for line in open(os.path.join(GOLD, name)):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        tag, rest = line.split(None, 1)
+        a, b = rest.split("|")
+        rows.setdefault(tag, []).append((np.array(a.split(), float), np.array(b.split(), float)))
+    return rows
+
+
+def _be_one_tet(v0, t):
+    """The one-tet backward-Euler scene of be_one_tet_closed_form.txt."""
+    X = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], float)
+    tets = np.array([[0, 1, 2, 3]])
+    o = oracle.OracleSolver(X, tets, [0, 1, 2], [3], 300.0, density=24.0, dt=0.1)
+    o.v[3] = v0
+    con = scenes.Contacts(np.array([[3, -1, -1, -1]], np.int32), np.array([[1.0, 0, 0, 0]]),
+                          np.asarray(t, float)[None], np.array([200.0]))
+    return o, X, (lambda x: con)
+
+
+def test_backward_euler_inertia_closed_form():
+    # the inertia term m/(2 dt^2)||x - y||^2 with y = x_n + dt v_n, and
+    # v_{n+1} = (x_{n+1} - x_n)/dt, against the hand solution of one tet
+    gold = _read_gold_tagged("be_one_tet_closed_form.txt")
+    for a, expect in gold["single"]:
+        o, X, fn = _be_one_tet(a[0:3], a[3:6])
+        o.step(1, 1, fn, X[:3])
+        np.testing.assert_allclose(o.x[3], expect[0:3], rtol=0, atol=1e-12)
+        np.testing.assert_allclose(o.v[3], expect[3:6], rtol=0, atol=1e-10)
+        np.testing.assert_array_equal(o.x[:3], X[:3])
+    # several steps along the axis, each with 2 outer x 2 inner iterations:
+    # y must stay the start-of-step inertia target across all of them
+    o, X, fn = _be_one_tet([0.0, 0.0, 3.0], [0.0, 0.0, 0.8])
+    for a, expect in gold["axis"]:
+        o.step(2, 2, fn, X[:3])
+        np.testing.assert_allclose(o.x[3], [0.0, 0.0, expect[0]], rtol=0, atol=1e-12)
+        np.testing.assert_allclose(o.v[3], [0.0, 0.0, expect[1]], rtol=0, atol=1e-10)
+
+
 def test_paper_dense_flop_estimate_reading():
     # Section 3.3 quotes ~8/3 GFLOP for a Cholesky at m = 2000: that is m^3 / 3
     m = 2000
