@@ -25,10 +25,14 @@ these synthetic obstacles stand in for them):
   * point-triangle: a side-A node, against the side-B surface triangles that
     were at least `rest_min` away from it in the rest pose, takes the nearest
     triangle (first index on ties); if the closest point q on it is nearer
-    than `gap`, the spring acts on x_a - q (q = the barycentric combination of
-    the triangle's nodes) toward gap * n, n the triangle's unit normal from
-    its winding (outward for outward-wound faces) frozen at detection, so the
-    node is pushed to the offset surface a distance gap in front of q.
+    than `gap`, the spring acts on d = x_a - q (q = the barycentric
+    combination of the triangle's nodes) toward gap * u, frozen at
+    detection: u is the unit vector from q to the node, turned to the
+    triangle's front side (the side its winding's normal n points to; outward
+    for outward-wound faces), or n itself if the node lies on the triangle.
+    The node is pushed to distance gap from q on the front side.  For a node
+    whose closest point lies on an edge or vertex shared by several
+    triangles, u is the same whichever of them is taken.
 """
 import math
 
@@ -111,7 +115,7 @@ def _dot(u, v):
 
 
 def closest_point_on_triangle(p, a, b, c):
-    """Closest point q of the triangle (a, b, c) to p, as (dist^2, (wa, wb, wc))
+    """Closest point q of the triangle (a, b, c) to p, as (dist^2, (wa, wb, wc), q)
     with q = wa a + wb b + wc c.  If the projection of p on the triangle's
     plane has barycentric coordinates in [0, 1] it is q; otherwise q lies on
     the boundary and is the nearest of the three segment projections (edges
@@ -127,8 +131,8 @@ def closest_point_on_triangle(p, a, b, c):
         if s >= 0.0 and t >= 0.0 and s + t <= 1.0:
             q = (a[0] + s * e0[0] + t * e1[0], a[1] + s * e0[1] + t * e1[1], a[2] + s * e0[2] + t * e1[2])
             r = _sub(p, q)
-            return _dot(r, r), (1.0 - s - t, s, t)
-    best, wts = None, None
+            return _dot(r, r), (1.0 - s - t, s, t), q
+    best, wts, bq = None, None, None
     for (u, v, iu, iv) in ((a, b, 0, 1), (b, c, 1, 2), (c, a, 2, 0)):
         e = _sub(v, u)
         ee = _dot(e, e)
@@ -141,8 +145,8 @@ def closest_point_on_triangle(p, a, b, c):
             ww = [0.0, 0.0, 0.0]
             ww[iu] = 1.0 - f
             ww[iv] = f
-            best, wts = d2, tuple(ww)
-    return best, wts
+            best, wts, bq = d2, tuple(ww), q
+    return best, wts, bq
 
 
 def _pt(x, i):
@@ -159,26 +163,34 @@ def point_triangle_springs(prox_a, tris_b, x, X, gap, rest_min, stiffness):
     rm2 = rest_min * rest_min
     for j, a in enumerate(prox_a):
         p, P = _pt(x, a), _pt(X, a)
-        best, bi, bw = 1e300, -1, None
+        best, bi, bw, bq = 1e300, -1, None, None
         for q, (i0, i1, i2) in enumerate(tris_b):
-            d2r, _ = closest_point_on_triangle(P, _pt(X, i0), _pt(X, i1), _pt(X, i2))
+            d2r, _, _ = closest_point_on_triangle(P, _pt(X, i0), _pt(X, i1), _pt(X, i2))
             if d2r < rm2:
                 continue
-            d2, wts = closest_point_on_triangle(p, _pt(x, i0), _pt(x, i1), _pt(x, i2))
+            d2, wts, qp = closest_point_on_triangle(p, _pt(x, i0), _pt(x, i1), _pt(x, i2))
             if d2 < best:
-                best, bi, bw = d2, q, wts
+                best, bi, bw, bq = d2, q, wts, qp
         if bi < 0 or not (math.sqrt(best) < gap):
             continue
         i0, i1, i2 = (int(v) for v in tris_b[bi])
         A, B, C = _pt(x, i0), _pt(x, i1), _pt(x, i2)
         e0, e1 = _sub(B, A), _sub(C, A)
         n = (e0[1] * e1[2] - e0[2] * e1[1], e0[2] * e1[0] - e0[0] * e1[2], e0[0] * e1[1] - e0[1] * e1[0])
-        nn = math.sqrt(_dot(n, n))
-        if not (nn > 0.0):
-            continue
-        s = gap / nn
-        rows.append(([int(a), -1, -1, -1, i0, i1, i2], [1.0, 0.0, 0.0, 0.0, -bw[0], -bw[1], -bw[2]],
-                     (s * n[0], s * n[1], s * n[2]), float(stiffness)))
+        r = _sub(p, bq)
+        if best > 0.0:
+            s = gap / math.sqrt(best)
+            if _dot(r, n) < 0.0:
+                s = -s
+            tg = (s * r[0], s * r[1], s * r[2])
+        else:
+            nn = math.sqrt(_dot(n, n))
+            if not (nn > 0.0):
+                continue
+            s = gap / nn
+            tg = (s * n[0], s * n[1], s * n[2])
+        rows.append(([int(a), -1, -1, -1, i0, i1, i2], [1.0, 0.0, 0.0, 0.0, -bw[0], -bw[1], -bw[2]], tg,
+                     float(stiffness)))
         idx.append(j)
         which.append(bi)
     return (*_springs(rows, 8), np.asarray(idx, np.int64), np.asarray(which, np.int64))

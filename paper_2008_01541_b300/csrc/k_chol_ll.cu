@@ -1,0 +1,447 @@
+// Persistent left-looking low-precision Cholesky (see chol_ll.h).
+//
+// One CTA of 256 threads per SM, each running tasks until the list is done:
+//   warp 0, lane 0 : producer -- waits until the panels L_ik and L_jk of the
+//                    next K step are final (per-row counters), then TMA-loads
+//                    their 128-byte column chunks into a ring of shared-memory
+//                    stages (128B swizzle, K-major);
+//   warp 1, lane 0 : issues the tcgen05 MMAs of each stage into the 128 x 128
+//                    FP32 accumulator in tensor memory and frees the stage;
+//   warps 4-7      : read the accumulator (one TMEM lane quarter each) and
+//                    form S = A_ij - acc in shared memory;
+//   all 256        : the diagonal-tile factor and inverse, or the panel
+//                    products, from shared memory.
+// A task waits only on tasks that precede it in the column-major list, so
+// the grid (all CTAs co-resident) always progresses.  Every wait is bounded;
+// a wait that gives up writes a code to status[1], which makes every other
+// CTA stop at its next wait or claim.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <atomic>
+
+#include "chol_ll.h"
+#include "kernels.h"
+#include "lowp_tile.cuh"
+#include "tc_dev.cuh"
+
+namespace pdll {
+namespace {
+
+using namespace pdtc::dev;
+using pdm::NB;
+using pdm::PADW;
+
+constexpr int SP = NB + 4;                // row stride of the transposed operands of the panel products
+constexpr uint32_t kSpin = 1u << 22;      // bounded waits: ~1 s with back-off
+constexpr int kStageBudget = 196608;      // shared memory for the pipeline stages (192 KB)
+
+template <int MODE>   // 0 = TF32, 1 = split TF32 (hi.hi + hi.lo + lo.hi), 2 = BF16
+struct Cfg {
+  static constexpr int CPP = MODE == 2 ? 2 : 4;            // 128-byte K chunks per 128-column panel
+  static constexpr int NBUF = MODE == 1 ? 4 : 2;           // 16 KB operand buffers per stage
+  static constexpr int STAGE = NBUF * kChunkBytes;
+  static constexpr int NST = kStageBudget / STAGE;         // 3 (split TF32) or 6 stages
+  static constexpr int CHUNK = MODE == 2 ? 64 : 32;        // K elements per chunk
+  static constexpr int EPI = 2 * NB * SP * 4;              // panel epilogue: S^T and an operand, 132 KB
+  static constexpr int SMEM = (NST * STAGE > EPI ? NST * STAGE : EPI) + 1024;
+};
+
+struct Ptrs {
+  float* L;
+  float* Llo;
+  __nv_bfloat16* Lb;
+  float* Lh;
+  float* Dinv;
+  float* E;
+  int64_t mq;
+  int T, kb;
+  int* sync;
+  int* status;
+};
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ bool failed_globally(const int* status) {
+  return *(volatile const int*)(status + 1) != 0;
+}
+
+// Bounded wait until *p >= v.  False if it gave up (code written to
+// status[1]) or if another CTA has already failed.
+__device__ bool wait_flag(const int* p, int v, int* status, int code) {
+  for (uint32_t it = 0; it < kSpin; ++it) {
+    if (ld_acquire(p) >= v) return true;
+    if (failed_globally(status)) return false;
+    __nanosleep(it < 64 ? 32 : 256);
+  }
+  atomicCAS(status + 1, 0, code);
+  return false;
+}
+
+// Bounded wait for phase `parity` of an mbarrier.  Gives up early when the
+// producer has stopped (*stop) before issuing chunk q (q >= *issued).
+__device__ bool mbar_wait_or_stop(uint64_t* bar, uint32_t parity, volatile int* stop, volatile int* issued, int q,
+                                  int* status, int code) {
+  for (uint32_t it = 0; it < kSpin; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if (*stop && q >= *issued) return false;
+    if (it > 32) __nanosleep(64);
+  }
+  atomicCAS(status + 1, 0, code);
+  return false;
+}
+
+// FP32 value minus its TF32 head (the head keeps the top 19 bits)
+__device__ __forceinline__ float tf32_tail(float x) {
+  return x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+}
+
+// Thread (ty, tx) of the 16 x 16 grid owns rows 8 ty .. + 7 and columns
+// 4 tx .. + 3 and 64 + 4 tx .. + 3 of a 128 x 128 tile (acc[p][q], q < 4 and
+// q >= 4), so a half-warp's 16-byte loads of a row of Y are contiguous.
+// acc[p][q] = sum_t X[t][8 ty + p] Y[t][column q] over t < 128, both
+// operands with row stride SP (X holds the left factor transposed)
+__device__ __forceinline__ void prod_8x8(const float* X, const float* Y, int ty, int tx, float (&acc)[8][8]) {
+#pragma unroll
+  for (int p = 0; p < 8; ++p)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[p][q] = 0.f;
+#pragma unroll 2
+  for (int t = 0; t < NB; ++t) {
+    const float4 a0 = *reinterpret_cast<const float4*>(X + t * SP + 8 * ty);
+    const float4 a1 = *reinterpret_cast<const float4*>(X + t * SP + 8 * ty + 4);
+    const float4 b0 = *reinterpret_cast<const float4*>(Y + t * SP + 4 * tx);
+    const float4 b1 = *reinterpret_cast<const float4*>(Y + t * SP + 64 + 4 * tx);
+    const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int p = 0; p < 8; ++p)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[p][q] = fmaf(a[p], b[q], acc[p][q]);
+  }
+}
+
+// the thread's 8 x 8 outputs into a row-major tile at dst (row stride ld)
+__device__ __forceinline__ void store_8x8(float* dst, int64_t ld, int ty, int tx, const float (&acc)[8][8]) {
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    float* row = dst + (int64_t)(8 * ty + p) * ld;
+    *reinterpret_cast<float4*>(row + 4 * tx) = make_float4(acc[p][0], acc[p][1], acc[p][2], acc[p][3]);
+    *reinterpret_cast<float4*>(row + 64 + 4 * tx) = make_float4(acc[p][4], acc[p][5], acc[p][6], acc[p][7]);
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256, 1)
+    k_chol_ll(const __grid_constant__ CUtensorMap thi, const __grid_constant__ CUtensorMap tlo, const Ptrs P) {
+  using C = Cfg<MODE>;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint64_t full[C::NST], empty[C::NST], accf;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_task;
+  __shared__ volatile int s_stop, s_issued;
+  uint8_t* sm = smem_raw + ((1024 - (su32(smem_raw) & 1023)) & 1023);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int T = P.T, kb = P.kb;
+  const int64_t mq = P.mq;
+  int* claim = P.sync;
+  int* rowcnt = P.sync + 1;       // [T] finished tiles of row i among columns kb..
+  int* ecnt = P.sync + 1 + T;     // [T] E_j written
+  const int nt = T - kb, ntask = nt * (nt + 1) / 2;
+  constexpr int KIND = MODE == 2 ? 1 : 0;
+  constexpr uint32_t ID = idesc(MODE == 2 ? 1u : 2u);
+
+  if (tid == 0) {
+    for (int s = 0; s < C::NST; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    mbar_init(&accf, 1);
+    s_stop = 0;
+    s_issued = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
+                 "r"(NB));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_base;
+  uint32_t g = 0;      // chunks through the stage ring so far (the producer and the MMA thread agree)
+  uint32_t nacc = 0;   // tasks that used the accumulator so far
+  float* A = reinterpret_cast<float*>(sm);    // diagonal task: the tile [128][PADW]
+  float* Zd = A + NB * PADW;                  //   and the diagonal blocks of its inverse [4][32][33]
+  float* ST = reinterpret_cast<float*>(sm);   // panel task: S transposed [128][SP]
+  float* DT = ST + NB * SP;                   //   and the right operand [128][SP]
+
+  for (;;) {
+    if (tid == 0) s_task = (s_stop || failed_globally(P.status)) ? ntask : atomicAdd(claim, 1);
+    __syncthreads();
+    const int t = s_task;
+    if (t >= ntask) break;
+    int j = kb, rem = t;   // column-major over the lower tiles of columns kb .. T-1
+    while (rem >= T - j) { rem -= T - j; ++j; }
+    const int i = j + rem;
+    const bool diag = i == j;
+    const int nchunk = (j - kb) * C::CPP;
+    float* Lt = P.L + (int64_t)i * NB * mq + (int64_t)j * NB;
+
+    // ---- acc = sum_{kb <= k < j} L_ik L_jk^T on the tensor cores
+    if (nchunk > 0) {
+      if (warp == 0) {
+        if (lane == 0) {   // producer
+          int issued = 0;
+          bool ok = true;
+          for (int k = kb; k < j && ok; ++k) {
+            ok = wait_flag(rowcnt + i, k - kb + 1, P.status, 311) && wait_flag(rowcnt + j, k - kb + 1, P.status, 312);
+            if (!ok) break;
+            asm volatile("fence.proxy.async.global;" ::: "memory");   // the panels were written by other CTAs
+            for (int c = 0; c < C::CPP; ++c) {
+              const uint32_t gg = g + (uint32_t)issued;
+              const int s = (int)(gg % C::NST);
+              const uint32_t u = gg / C::NST;
+              if (u > 0 && !mbar_wait(&empty[s], (u - 1) & 1)) {   // the stage's previous chunk was consumed
+                atomicCAS(P.status + 1, 0, 313);
+                ok = false;
+                break;
+              }
+              uint8_t* st = sm + s * C::STAGE;
+              mbar_expect_tx(&full[s], C::STAGE);
+              const int x = k * NB + c * C::CHUNK;
+              tma_load_2d(st, &thi, &full[s], x, i * NB);
+              tma_load_2d(st + kChunkBytes, &thi, &full[s], x, j * NB);
+              if (MODE == 1) {
+                tma_load_2d(st + 2 * kChunkBytes, &tlo, &full[s], x, i * NB);
+                tma_load_2d(st + 3 * kChunkBytes, &tlo, &full[s], x, j * NB);
+              }
+              ++issued;
+            }
+          }
+          if (!ok) {
+            s_issued = issued;
+            __threadfence_block();
+            s_stop = 1;
+          }
+        }
+        __syncwarp();
+      } else if (warp == 1) {
+        if (lane == 0) {   // MMA issue: A = rows of tile i, B = rows of tile j, K-major
+          for (int q = 0; q < nchunk; ++q) {
+            const uint32_t gg = g + (uint32_t)q;
+            const int s = (int)(gg % C::NST);
+            const uint32_t u = gg / C::NST;
+            if (!mbar_wait_or_stop(&full[s], u & 1, &s_stop, &s_issued, q, P.status, 314)) break;
+            fence_after();
+            const uint32_t sa = su32(sm + s * C::STAGE), sb = sa + kChunkBytes;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              mma<KIND>(tmem, sdesc(sa + 32 * kk), sdesc(sb + 32 * kk), ID, (q > 0 || kk > 0) ? 1u : 0u);
+              if (MODE == 1) {   // hi.lo + lo.hi
+                mma<KIND>(tmem, sdesc(sa + 32 * kk), sdesc(sb + 2 * kChunkBytes + 32 * kk), ID, 1u);
+                mma<KIND>(tmem, sdesc(sa + 2 * kChunkBytes + 32 * kk), sdesc(sb + 32 * kk), ID, 1u);
+              }
+            }
+            mma_commit(&empty[s]);   // frees the stage once these MMAs have read it
+          }
+          mma_commit(&accf);         // arrives when every MMA of the task is done
+        }
+        __syncwarp();
+      }
+      if (!mbar_wait(&accf, nacc & 1)) atomicCAS(P.status + 1, 0, 315);
+      ++nacc;
+      g += (uint32_t)nchunk;
+      fence_after();
+    }
+    __syncthreads();
+    if (s_stop) continue;
+
+    // ---- S = A_ij - acc into shared memory (row-major for the diagonal
+    // factor, transposed for the panel products)
+    if (nchunk > 0) {
+      if (warp >= 4) {
+        const int r = 32 * (warp - 4) + lane;
+        const float* arow = Lt + (int64_t)r * mq;
+#pragma unroll 1
+        for (int c0 = 0; c0 < NB; c0 += 32) {
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)(32 * (warp - 4)) << 16) + (uint32_t)c0, v);
+#pragma unroll
+          for (int q4 = 0; q4 < 8; ++q4) {
+            const float4 a = __ldcg(reinterpret_cast<const float4*>(arow + c0 + 4 * q4));
+            const float e[4] = {a.x - v[4 * q4], a.y - v[4 * q4 + 1], a.z - v[4 * q4 + 2], a.w - v[4 * q4 + 3]};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int c = c0 + 4 * q4 + u;
+              if (diag) A[r * PADW + c] = e[u];
+              else ST[c * SP + r] = e[u];
+            }
+          }
+        }
+      }
+    } else {
+#pragma unroll 4
+      for (int k = 0; k < 16; ++k) {
+        const int q = tid + 256 * k;
+        if (diag) {
+          const int r = q >> 5, c = 4 * (q & 31);
+          const float4 a = __ldcg(reinterpret_cast<const float4*>(Lt + (int64_t)r * mq + c));
+          A[r * PADW + c] = a.x; A[r * PADW + c + 1] = a.y; A[r * PADW + c + 2] = a.z; A[r * PADW + c + 3] = a.w;
+        } else {
+          const int r = q & 127, c = 4 * (q >> 7);
+          const float4 a = __ldcg(reinterpret_cast<const float4*>(Lt + (int64_t)r * mq + c));
+          ST[c * SP + r] = a.x; ST[(c + 1) * SP + r] = a.y; ST[(c + 2) * SP + r] = a.z; ST[(c + 3) * SP + r] = a.w;
+        }
+      }
+    }
+    fence_before();   // the accumulator reads precede the barrier (the next task overwrites it)
+    __syncthreads();
+
+    if (diag) {
+      // ---- L_jj, then Dinv_j (the panels of column j wait for it), then E_j
+      pdm::diag_factor_smem(A, j, P.status);
+      for (int q = tid; q < NB * NB; q += 256) {
+        const int r = q / NB, c = q % NB;
+        if (c <= r) Lt[(int64_t)r * mq + c] = A[r * PADW + c];
+      }
+      float* Di = P.Dinv + (int64_t)j * NB * NB;
+      pdm::tile_inverse(A, Zd, Di);
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        st_release(rowcnt + j, j - kb + 1);
+      }
+      float* Dsm = A;   // Dinv_j again, padded rows
+#pragma unroll 4
+      for (int k = 0; k < 16; ++k) {
+        const int q = tid + 256 * k, r = q >> 5, c = 4 * (q & 31);
+        const float4 v = __ldcg(reinterpret_cast<const float4*>(Di + r * NB + c));
+        Dsm[r * PADW + c] = v.x; Dsm[r * PADW + c + 1] = v.y; Dsm[r * PADW + c + 2] = v.z; Dsm[r * PADW + c + 3] = v.w;
+      }
+      __syncthreads();
+      float* Ej = P.E + (int64_t)j * NB * NB;
+      for (int q = tid; q < NB * NB; q += 256) {   // E[r][c] = sum_{t >= max(r, c)} Dinv[t][r] Dinv[t][c]
+        const int r = q / NB, c = q % NB;
+        float e = 0.f;
+        for (int t2 = (r > c ? r : c); t2 < NB; ++t2) e = fmaf(Dsm[t2 * PADW + r], Dsm[t2 * PADW + c], e);
+        Ej[q] = e;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        st_release(ecnt + j, 1);
+      }
+    } else {
+      // ---- L_ij = S Dinv_j^T once Dinv_j is ready; then Lh_ij = S E_j
+      if (tid == 0 && !wait_flag(rowcnt + j, j - kb + 1, P.status, 316)) s_stop = 1;
+      __syncthreads();
+      if (s_stop) continue;
+      const float* Di = P.Dinv + (int64_t)j * NB * NB;
+#pragma unroll 4
+      for (int k = 0; k < 16; ++k) {   // DT[t][n] = Dinv_j[n][t]
+        const int q = tid + 256 * k, n = q & 127, t4 = 4 * (q >> 7);
+        const float4 v = __ldcg(reinterpret_cast<const float4*>(Di + n * NB + t4));
+        DT[t4 * SP + n] = v.x; DT[(t4 + 1) * SP + n] = v.y; DT[(t4 + 2) * SP + n] = v.z; DT[(t4 + 3) * SP + n] = v.w;
+      }
+      __syncthreads();
+      const int ty = tid >> 4, tx = tid & 15;
+      float acc[8][8];
+      prod_8x8(ST, DT, ty, tx, acc);
+      store_8x8(Lt, mq, ty, tx, acc);
+      const int64_t off = (int64_t)i * NB * mq + (int64_t)j * NB;
+      if (MODE == 1) {   // TF32 tails of the panel for the split products of later tasks
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+          float* row = P.Llo + off + (int64_t)(8 * ty + p) * mq;
+          *reinterpret_cast<float4*>(row + 4 * tx) =
+              make_float4(tf32_tail(acc[p][0]), tf32_tail(acc[p][1]), tf32_tail(acc[p][2]), tf32_tail(acc[p][3]));
+          *reinterpret_cast<float4*>(row + 64 + 4 * tx) =
+              make_float4(tf32_tail(acc[p][4]), tf32_tail(acc[p][5]), tf32_tail(acc[p][6]), tf32_tail(acc[p][7]));
+        }
+      } else if (MODE == 2) {   // the panel rounded to BF16 for the BF16 products of later tasks
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+          __nv_bfloat16* row = P.Lb + off + (int64_t)(8 * ty + p) * mq;
+          __nv_bfloat16 h0[4], h1[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) { h0[q] = __float2bfloat16_rn(acc[p][q]); h1[q] = __float2bfloat16_rn(acc[p][4 + q]); }
+          *reinterpret_cast<uint2*>(row + 4 * tx) = *reinterpret_cast<const uint2*>(h0);
+          *reinterpret_cast<uint2*>(row + 64 + 4 * tx) = *reinterpret_cast<const uint2*>(h1);
+        }
+      }
+      asm volatile("fence.proxy.async.global;" ::: "memory");   // later TMA reads of this tile
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        st_release(rowcnt + i, j - kb + 1);
+      }
+      if (tid == 0 && !wait_flag(ecnt + j, 1, P.status, 317)) s_stop = 1;
+      __syncthreads();
+      if (s_stop) continue;
+      const float* Ej = P.E + (int64_t)j * NB * NB;
+#pragma unroll 4
+      for (int k = 0; k < 16; ++k) {   // DT[t][n] = E_j[t][n]
+        const int q = tid + 256 * k, t2 = q >> 5, n4 = 4 * (q & 31);
+        *reinterpret_cast<float4*>(DT + t2 * SP + n4) = __ldcg(reinterpret_cast<const float4*>(Ej + t2 * NB + n4));
+      }
+      __syncthreads();
+      prod_8x8(ST, DT, ty, tx, acc);
+      store_8x8(P.Lh + off, mq, ty, tx, acc);
+    }
+    // generic shared-memory accesses of this task precede the next task's TMA writes
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NB));
+  }
+}
+
+template <int MODE>
+cudaError_t launch(const Args& a, const Ptrs& p, int ntask, cudaStream_t st) {
+  static std::atomic<unsigned long long> attr{0};
+  static int per_dev[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (pdk::first_on_device(attr)) {
+    cudaFuncSetAttribute(k_chol_ll<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<MODE>::SMEM);
+    int nsm = 0, per = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chol_ll<MODE>, 256, Cfg<MODE>::SMEM);
+    per_dev[dev & 63] = nsm * std::max(per, 1);   // one persistent CTA per SM
+  }
+  const int grid = std::max(1, std::min(ntask, per_dev[dev & 63]));
+  const CUtensorMap& lo = a.map_lo ? *a.map_lo : *a.map_hi;
+  k_chol_ll<MODE><<<grid, 256, Cfg<MODE>::SMEM, st>>>(*a.map_hi, lo, p);
+  ++pdk::g_launches;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t factor(pdtc::Mode mode, const Args& a, cudaStream_t st) {
+  const int nt = a.T - a.kb;
+  if (nt <= 0) return cudaSuccess;
+  if (!a.map_hi || !a.L || !a.Lh || !a.Dinv || !a.E || !a.sync || !a.status ||
+      (mode == pdtc::TF32X3 && (!a.Llo || !a.map_lo)) || (mode == pdtc::BF16 && !a.Lb))
+    return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(a.sync, 0, sync_bytes(a.T), st);
+  if (e != cudaSuccess) return e;
+  const Ptrs p{a.L, a.Llo, a.Lb, a.Lh, a.Dinv, a.E, a.mq, a.T, a.kb, a.sync, a.status};
+  const int ntask = nt * (nt + 1) / 2;
+  switch (mode) {
+    case pdtc::TF32X3: return launch<1>(a, p, ntask, st);
+    case pdtc::BF16: return launch<2>(a, p, ntask, st);
+    default: return launch<0>(a, p, ntask, st);
+  }
+}
+
+}  // namespace pdll

@@ -12,7 +12,9 @@
 //             rest pose are skipped); the nearest triangle, if nearer than
 //             `gap`, gives a two-sided spring on x_a - q (q its closest point,
 //             a barycentric combination of the triangle's nodes, Eq. 5) toward
-//             gap * n, n the triangle's unit normal from its winding
+//             gap * u, u the unit vector from q to the node turned to the
+//             triangle's front side (its winding's normal n; n itself if the
+//             node lies on the triangle)
 // Every quantity that decides which obstacle is nearest or whether a proxy is
 // active is computed with explicitly rounded operations (no fused
 // multiply-add) in a fixed order, so the decision is reproducible operation
@@ -96,12 +98,12 @@ __global__ void k_detect_pairs(int64_t na, const int32_t* __restrict__ ra_list, 
   cs[j] = stiffness;
 }
 
-// Closest point of the triangle (a, b, c) to p: returns |p - q|^2 and the
-// barycentric weights of q.  The projection on the triangle's plane if its
+// Closest point q of the triangle (a, b, c) to p: returns |p - q|^2, the
+// barycentric weights of q, and q.  The projection on the triangle's plane if its
 // barycentric coordinates lie in [0, 1]; otherwise the nearest of the three
 // segment projections (edges ab, bc, ca; the first on ties).  A zero-area
 // triangle goes through its edges.
-__device__ double closest_on_triangle(V3 p, V3 a, V3 b, V3 c, double* w) {
+__device__ double closest_on_triangle(V3 p, V3 a, V3 b, V3 c, double* w, V3* qout) {
   const V3 e0 = sub(b, a), e1 = sub(c, a), pw = sub(p, a);
   const double d00 = dot(e0, e0), d01 = dot(e0, e1), d11 = dot(e1, e1), d20 = dot(pw, e0), d21 = dot(pw, e1);
   const double den = __dsub_rn(__dmul_rn(d00, d11), __dmul_rn(d01, d01));
@@ -116,6 +118,7 @@ __device__ double closest_on_triangle(V3 p, V3 a, V3 b, V3 c, double* w) {
       w[0] = __dsub_rn(__dsub_rn(1.0, s), t);
       w[1] = s;
       w[2] = t;
+      *qout = q;
       return dot(r, r);
     }
   }
@@ -137,6 +140,7 @@ __device__ double closest_on_triangle(V3 p, V3 a, V3 b, V3 c, double* w) {
       w[0] = w[1] = w[2] = 0.0;
       w[k] = __dsub_rn(1.0, f);
       w[(k + 1) % 3] = f;
+      *qout = q;
     }
   }
   return best;
@@ -172,11 +176,11 @@ __global__ void __launch_bounds__(256) k_detect_tris(
   const int lane = threadIdx.x & 31;
   const int64_t j = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
   if (j >= np) return;
-  const int r = prox[j];
-  const V3 p = ld3(x + 3 * (int64_t)region[r]), P = ld3(xr + 3 * (int64_t)r);
+  const int r0 = prox[j];
+  const V3 p = ld3(x + 3 * (int64_t)region[r0]), P = ld3(xr + 3 * (int64_t)r0);
   const float px = (float)p.x, py = (float)p.y, pz = (float)p.z, fg = (float)gap;
   const double rm2 = __dmul_rn(rest_min, rest_min);
-  double best = 1e300, bw[3] = {0.0, 0.0, 0.0};
+  double best = 1e300;
   int64_t bi = -1;
   for (int64_t q = lane; q < nt; q += 32) {
     const float4 b = __ldg(bnd + q);
@@ -185,21 +189,19 @@ __global__ void __launch_bounds__(256) k_detect_tris(
     if (sqrtf(dx * dx + dy * dy + dz * dz) > b.w + fg + margin) continue;
     const int i0 = tri[3 * q], i1 = tri[3 * q + 1], i2 = tri[3 * q + 2];
     double w[3];
+    V3 qp;
     const double d2r = closest_on_triangle(P, ld3(xr + 3 * (int64_t)i0), ld3(xr + 3 * (int64_t)i1),
-                                           ld3(xr + 3 * (int64_t)i2), w);
+                                           ld3(xr + 3 * (int64_t)i2), w, &qp);
     if (d2r < rm2) continue;
     const double d2 = closest_on_triangle(p, ld3(x + 3 * (int64_t)region[i0]), ld3(x + 3 * (int64_t)region[i1]),
-                                          ld3(x + 3 * (int64_t)region[i2]), w);
-    if (d2 < best) { best = d2; bi = q; bw[0] = w[0]; bw[1] = w[1]; bw[2] = w[2]; }
+                                          ld3(x + 3 * (int64_t)region[i2]), w, &qp);
+    if (d2 < best) { best = d2; bi = q; }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const double ob = __shfl_down_sync(0xffffffffu, best, o);
     const long long oi = __shfl_down_sync(0xffffffffu, (long long)bi, o);
-    const double o0 = __shfl_down_sync(0xffffffffu, bw[0], o), o1 = __shfl_down_sync(0xffffffffu, bw[1], o),
-                 o2 = __shfl_down_sync(0xffffffffu, bw[2], o);
-    const bool take = oi >= 0 && (bi < 0 || ob < best || (ob == best && oi < bi));
-    if (take) { best = ob; bi = oi; bw[0] = o0; bw[1] = o1; bw[2] = o2; }
+    if (oi >= 0 && (bi < 0 || ob < best || (ob == best && oi < bi))) { best = ob; bi = oi; }
   }
   if (lane != 0) return;
   const int64_t sj = slot0 + j;
@@ -208,18 +210,30 @@ __global__ void __launch_bounds__(256) k_detect_tris(
   const int i0 = tri[3 * bi], i1 = tri[3 * bi + 1], i2 = tri[3 * bi + 2];
   const V3 A = ld3(x + 3 * (int64_t)region[i0]), B = ld3(x + 3 * (int64_t)region[i1]),
            C = ld3(x + 3 * (int64_t)region[i2]);
+  double bw[3];
+  V3 q;
+  closest_on_triangle(p, A, B, C, bw, &q);   // the same operations as in the scan: the same q and weights
   const V3 e0 = sub(B, A), e1 = sub(C, A);
   const V3 n = {__dsub_rn(__dmul_rn(e0.y, e1.z), __dmul_rn(e0.z, e1.y)),
                 __dsub_rn(__dmul_rn(e0.z, e1.x), __dmul_rn(e0.x, e1.z)),
                 __dsub_rn(__dmul_rn(e0.x, e1.y), __dmul_rn(e0.y, e1.x))};
-  const double nn = sqrt(dot(n, n));
-  if (!(nn > 0.0)) return;
-  const double s = __ddiv_rn(gap, nn);
-  cidx[NS * sj] = r;
+  const V3 r = sub(p, q);
+  V3 tg;
+  if (best > 0.0) {   // along q -> node, on the front side
+    double s = __ddiv_rn(gap, sqrt(best));
+    if (dot(r, n) < 0.0) s = -s;
+    tg = {__dmul_rn(s, r.x), __dmul_rn(s, r.y), __dmul_rn(s, r.z)};
+  } else {            // on the triangle: along its normal
+    const double nn = sqrt(dot(n, n));
+    if (!(nn > 0.0)) return;
+    const double s = __ddiv_rn(gap, nn);
+    tg = {__dmul_rn(s, n.x), __dmul_rn(s, n.y), __dmul_rn(s, n.z)};
+  }
+  cidx[NS * sj] = r0;
   cw[NS * sj] = 1.0;
   cidx[NS * sj + 4] = i0; cidx[NS * sj + 5] = i1; cidx[NS * sj + 6] = i2;
   cw[NS * sj + 4] = -bw[0]; cw[NS * sj + 5] = -bw[1]; cw[NS * sj + 6] = -bw[2];
-  ct[3 * sj] = __dmul_rn(s, n.x); ct[3 * sj + 1] = __dmul_rn(s, n.y); ct[3 * sj + 2] = __dmul_rn(s, n.z);
+  ct[3 * sj] = tg.x; ct[3 * sj + 1] = tg.y; ct[3 * sj + 2] = tg.z;
   cs[sj] = stiffness;
 }
 

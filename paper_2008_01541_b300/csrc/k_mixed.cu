@@ -14,21 +14,19 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <string>
 #include <vector>
 
+#include "chol_ll.h"
 #include "kernels.h"
+#include "lowp_tile.cuh"
 #include "mixed.h"
 #include "solver.h"
 #include "tc.h"
 
 namespace pdm {
 
-constexpr int NB = 128;      // tile of the low-precision factor
-constexpr int PADW = NB + 1; // padded shared-memory row
-
-// named barrier among n threads (id 1..15; 0 is __syncthreads)
-__device__ __forceinline__ void bar_sync_n(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 
 struct Factor {
   float* L = nullptr;         // [mq][mq] row-major, lower tiles hold the factor
@@ -41,6 +39,10 @@ struct Factor {
   int k0 = 0;                 // nested form: tiles before k0 are fixed
   float* Sp = nullptr;        // nested form: saved trailing block
   CUtensorMap mapL{}, mapP[2]{};
+  // persistent left-looking factorisation: TF32 tails / BF16 copies of the finished panels
+  float* Llo = nullptr;       // [mq][mq] split TF32
+  __nv_bfloat16* Lb = nullptr;   // [mq][mq] BF16
+  CUtensorMap mapLo{}, mapLb{};
   bool valid = false;
 };
 
@@ -62,6 +64,8 @@ struct MixedState {
   int* pcnt = nullptr;        // preconditioner scratch: task counters [2 + 4T], then facc, bacc
   float *facc = nullptr, *bacc = nullptr;   // [mq][3] accumulated block products (forward / backward)
   int pc_grid = 0;            // persistent grid of the preconditioner
+  int* llsync = nullptr;      // counters of the persistent left-looking factorisation
+  bool lookahead = false;     // PD_LOWP_SCHEDULE=lookahead: one launch per tile step instead
   cudaStream_t side = nullptr;              // low-priority stream for the bulk trailing updates
   std::vector<cudaEvent_t> ev_panel, ev_rest;
 };
@@ -152,142 +156,6 @@ __global__ void k_block_copy_f32(float* __restrict__ L, int64_t mq, int64_t off,
   else B[q] = *l;
 }
 
-// One warp factors the 32 x 32 block at Ap (row stride PADW) in registers
-// (lane i holds row i) and writes L back to Ap, and 1 / L_jj to rinv.  Each
-// scaled column goes through shared memory once (double-buffered, so one warp
-// barrier per pivot) and is read back with 16-byte broadcasts; the next
-// pivot's column is updated first so that its square root overlaps the rest
-// of the current update.  A non-positive pivot is replaced by 1 and reported
-// in *status (first bad column + 1, offset by code0).
-__device__ __noinline__ void warp_chol32(float* Ap, float* rinv, int* status, int code0) {
-  const int lane = threadIdx.x & 31;
-  float a[32];
-#pragma unroll
-  for (int c = 0; c < 32; ++c) a[c] = Ap[lane * PADW + c];
-  __shared__ __align__(16) float col[2][32];
-  unsigned bad = 0;
-#pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    float djj = __shfl_sync(0xffffffffu, a[j], j);
-    const bool b = !(djj > 0.f) || !isfinite(djj);
-    bad |= (unsigned)b << j;
-    djj = b ? 1.f : djj;
-    const float rs = rsqrtf(djj);
-    a[j] = lane == j ? djj * rs : (lane > j ? a[j] * rs : a[j]);
-    if (lane == j) rinv[j] = rs;
-    float* cb = col[j & 1];
-    cb[lane] = a[j];
-    __syncwarp();
-    if (j + 1 < 32) {
-      const float v = cb[j + 1];
-      if (lane >= j + 1) a[j + 1] = fmaf(-a[j], v, a[j + 1]);
-    }
-    const float4* c4 = reinterpret_cast<const float4*>(cb);
-#pragma unroll
-    for (int q = (j + 2) / 4; q < 8; ++q) {
-      const float4 v = c4[q];
-      const float vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int c = 4 * q + e;
-        if (c > j + 1 && lane >= c) a[c] = fmaf(-a[j], vv[e], a[c]);
-      }
-    }
-  }
-  if (bad && lane == 0) atomicCAS(status, 0, code0 + __ffs(bad));
-#pragma unroll
-  for (int c = 0; c < 32; ++c) if (c <= lane) Ap[lane * PADW + c] = a[c];
-}
-
-// 32 x 32 block product on a group of 64 threads: thread gr = tid & 63 holds
-// rows 4 (gr >> 3) .. + 3 and columns 4 (gr & 7) .. + 3 and accumulates
-// o += X[rows, t] Y[t, columns] (leading dimensions ldx, ldy).
-__device__ __forceinline__ void prod32_g64(const float* X, int ldx, const float* Y, int ldy, float (&o)[4][4]) {
-  const int gr = threadIdx.x & 63, r = 4 * (gr >> 3), c = 4 * (gr & 7);
-#pragma unroll 4
-  for (int t = 0; t < 32; ++t) {
-    float x[4], y[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) { x[q] = X[(r + q) * ldx + t]; y[q] = Y[t * ldy + c + q]; }
-#pragma unroll
-    for (int p = 0; p < 4; ++p)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) o[p][q] = fmaf(x[p], y[q], o[p][q]);
-  }
-}
-
-// Dinv_k = L_kk^-1 from the factored tile in shared memory (A, row stride
-// PADW, lower triangle), written row-major to Di (zero above the diagonal).
-// The four diagonal 32 x 32 blocks are inverted by one warp each; then, by
-// block diagonals d = i - j, Z_ij = -Z_ii T_ij with T_ij = sum_{j <= t < i}
-// L_it Z_tj, the (4 - d) blocks of a diagonal at once on groups of 64
-// threads.  The diagonal blocks Z_ii sit in Zd (leading dimension 33); an
-// off-diagonal block Z_ij (i > j) sits in the unused block (j, i) above the
-// diagonal of A.  Called by all 256 threads after a barrier.
-__device__ __forceinline__ void tile_inverse(float* A, float* Zd, float* __restrict__ Di) {
-  const int tid = threadIdx.x, warp = tid >> 5;
-  constexpr int LZ = 33;
-  // level 0: Z_ii = L_ii^-1 (rows of Zd, leading dimension 33)
-  if (warp < 4) {
-    const int lane = tid & 31, c0 = 32 * warp;
-    const float* Ap = A + c0 * PADW + c0;
-    float a[32], z[32];
-#pragma unroll
-    for (int c = 0; c < 32; ++c) { a[c] = (c <= lane) ? Ap[lane * PADW + c] : 0.f; z[c] = (c == lane) ? 1.f : 0.f; }
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      if (lane == j) {
-        const float ip = __frcp_rn(a[j]);
-#pragma unroll
-        for (int c = 0; c <= j; ++c) z[c] *= ip;
-      }
-#pragma unroll
-      for (int c = 0; c <= j; ++c) {
-        const float zjc = __shfl_sync(0xffffffffu, z[c], j);
-        if (lane > j) z[c] = fmaf(-a[j], zjc, z[c]);
-      }
-    }
-    float* Zp = Zd + warp * 32 * LZ;
-#pragma unroll
-    for (int c = 0; c < 32; ++c) Zp[lane * LZ + c] = z[c];
-  }
-  __syncthreads();
-  const int grp = tid >> 6, gr = tid & 63, orr = 4 * (gr >> 3), occ = 4 * (gr & 7);
-#pragma unroll 1
-  for (int d = 1; d < 4; ++d) {
-    const int j = grp, i = j + d;
-    if (i < 4) {
-      float* Zij = A + (32 * j) * PADW + 32 * i;     // block (j, i) of A holds Z_ij
-      float o[4][4] = {};
-      for (int t = j; t < i; ++t) {                  // T_ij = sum_t L_it Z_tj
-        const float* Lit = A + (32 * i) * PADW + 32 * t;
-        if (t == j) prod32_g64(Lit, PADW, Zd + j * 32 * LZ, LZ, o);
-        else prod32_g64(Lit, PADW, A + (32 * j) * PADW + 32 * t, PADW, o);   // Z_tj in block (j, t)
-      }
-#pragma unroll
-      for (int p = 0; p < 4; ++p)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) Zij[(orr + p) * PADW + occ + q] = o[p][q];
-      bar_sync_n(1 + grp, 64);
-      float z2[4][4] = {};
-      prod32_g64(Zd + i * 32 * LZ, LZ, Zij, PADW, z2);   // Z_ij = -Z_ii T_ij
-      bar_sync_n(1 + grp, 64);
-#pragma unroll
-      for (int p = 0; p < 4; ++p)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) Zij[(orr + p) * PADW + occ + q] = -z2[p][q];
-    }
-    __syncthreads();
-  }
-  for (int q = tid; q < NB * NB; q += 256) {
-    const int r = q / NB, c = q % NB, bi = r >> 5, bj = c >> 5;
-    float v = 0.f;
-    if (bi == bj) v = (c <= r) ? Zd[bi * 32 * LZ + (r & 31) * LZ + (c & 31)] : 0.f;
-    else if (bi > bj) v = A[(32 * bj + (r & 31)) * PADW + 32 * bi + (c & 31)];
-    Di[q] = v;
-  }
-}
-
 // Factor the diagonal tile (kt, kt) in FP32 (L_kk), blocked in shared memory
 // with 32-wide sub-blocks and a look-ahead inside the tile: while warp 0
 // factors sub-block p, warps 1-7 apply the rest of panel p-1's trailing
@@ -301,8 +169,7 @@ __global__ void __launch_bounds__(256) k_diag_f32(float* __restrict__ L, int64_t
   extern __shared__ float sm[];
   float* A = sm;                   // [128][PADW]
   float* Zd = sm + NB * PADW;      // [4][32][33] diagonal blocks of the inverse
-  __shared__ float rinv32[32];     // 1 / L_jj of the current 32 x 32 sub-block
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x;
   float* Lt = L + (int64_t)kt * NB * mq + (int64_t)kt * NB;
   {
     float4 v[16];
@@ -318,76 +185,7 @@ __global__ void __launch_bounds__(256) k_diag_f32(float* __restrict__ L, int64_t
     }
   }
   __syncthreads();
-#pragma unroll 1
-  for (int p = 0; p < 4; ++p) {
-    const int c0 = 32 * p;
-    // ---- phase 1: factor block p | rest of panel p-1's update
-    if (warp == 0) {
-      warp_chol32(A + c0 * PADW + c0, rinv32, status, kt * NB + c0);
-    } else if (p > 0) {
-      // rows >= c0 + 32, columns c0 .. row (sub-block p itself was updated in phase 3)
-      const int pc = c0 - 32;                      // panel columns pc .. pc + 31
-      const int nbr = (NB - c0 - 32) / 2, nbc = (NB - c0) / 2;
-      for (int q = tid - 32; q < nbr * nbc; q += 224) {
-        const int bi = q / nbc, bj = q % nbc;
-        const int r = c0 + 32 + 2 * bi, c = c0 + 2 * bj;
-        if (c > r) continue;
-        float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f;
-#pragma unroll 8
-        for (int t = 0; t < 32; ++t) {
-          const float a0 = A[r * PADW + pc + t], a1 = A[(r + 1) * PADW + pc + t];
-          const float b0 = A[c * PADW + pc + t], b1 = A[(c + 1) * PADW + pc + t];
-          s00 = fmaf(a0, b0, s00); s01 = fmaf(a0, b1, s01); s10 = fmaf(a1, b0, s10); s11 = fmaf(a1, b1, s11);
-        }
-        A[r * PADW + c] -= s00;
-        A[(r + 1) * PADW + c] -= s10;
-        A[(r + 1) * PADW + c + 1] -= s11;
-        if (c + 1 <= r) A[r * PADW + c + 1] -= s01;
-      }
-    }
-    __syncthreads();
-    // ---- phase 2: panel below block p by substitution (one thread per row)
-    float* Ap = A + c0 * PADW + c0;
-    const int nbelow = NB - c0 - 32;
-    if (tid < nbelow) {
-      // right-looking: x_j is final after its own scaling, then eliminated
-      // from the later entries (independent FMAs instead of a dot-product chain)
-      float* row = A + (c0 + 32 + tid) * PADW + c0;
-      float x[32];
-#pragma unroll
-      for (int j = 0; j < 32; ++j) x[j] = row[j];
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        x[j] *= rinv32[j];
-#pragma unroll
-        for (int t = j + 1; t < 32; ++t) x[t] = fmaf(-x[j], Ap[t * PADW + j], x[t]);
-      }
-#pragma unroll
-      for (int j = 0; j < 32; ++j) row[j] = x[j];
-    }
-    __syncthreads();
-    // ---- phase 3: update of the next diagonal block with panel p
-    if (p < 3) {
-      const int b0 = c0 + 32;
-      for (int q = tid; q < 16 * 16; q += 256) {
-        const int bi = q / 16, bj = q % 16;
-        if (bj > bi) continue;
-        const int r = b0 + 2 * bi, c = b0 + 2 * bj;
-        float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f;
-#pragma unroll 8
-        for (int t = 0; t < 32; ++t) {
-          const float a0 = A[r * PADW + c0 + t], a1 = A[(r + 1) * PADW + c0 + t];
-          const float e0 = A[c * PADW + c0 + t], e1 = A[(c + 1) * PADW + c0 + t];
-          s00 = fmaf(a0, e0, s00); s01 = fmaf(a0, e1, s01); s10 = fmaf(a1, e0, s10); s11 = fmaf(a1, e1, s11);
-        }
-        A[r * PADW + c] -= s00;
-        A[(r + 1) * PADW + c] -= s10;
-        A[(r + 1) * PADW + c + 1] -= s11;
-        if (c + 1 <= r) A[r * PADW + c + 1] -= s01;
-      }
-      __syncthreads();
-    }
-  }
+  diag_factor_smem(A, kt, status);
   for (int q = tid; q < NB * NB; q += 256) {
     const int r = q / NB, c = q % NB;
     if (c <= r) Lt[(int64_t)r * mq + c] = A[r * PADW + c];
@@ -1151,6 +949,14 @@ static pd_status ensure_state(pd_solver* s) {
     M->facc = reinterpret_cast<float*>(reinterpret_cast<char*>(M->pcnt) + cb);
     M->bacc = M->facc + 3 * mq;
   }
+  if (A((void**)&M->llsync, pdll::sync_bytes((int)M->T))) {
+    s->err = "device allocation for the factorisation counters failed";
+    return PD_ERR_OOM;
+  }
+  {
+    const char* sched = std::getenv("PD_LOWP_SCHEDULE");
+    M->lookahead = sched && std::string(sched) == "lookahead";
+  }
   if (cudaMallocHost(&M->sc_h, sizeof(double) * 8) != cudaSuccess) return PD_ERR_OOM;
   // vectors beyond m stay zero: the padded products need no bounds checks
   cudaMemsetAsync(M->vhi, 0, sizeof(float) * 3 * M->ldm, s->stream);
@@ -1234,6 +1040,43 @@ static void factor_panels(pd_solver* s, Factor& f, pdtc::Mode mode, int k_begin 
   f.valid = true;
 }
 
+// The factor of tile columns k_begin .. T-1 of f.L in one persistent launch
+// (left-looking, see chol_ll.h); the panel copies its tensor-core products
+// read are allocated on first use.
+static pd_status factor_ll(pd_solver* s, Factor& f, pdtc::Mode mode, int k_begin = 0) {
+  MixedState* M = s->mixed;
+  const int64_t mq = M->mq;
+  if (M->lookahead) {
+    factor_panels(s, f, mode, k_begin);
+    return PD_OK;
+  }
+  if (mode == pdtc::TF32X3 && !f.Llo) {
+    if (cudaMalloc(&f.Llo, sizeof(float) * mq * mq) != cudaSuccess) {
+      s->err = "device allocation of the TF32 tails failed";
+      return PD_ERR_OOM;
+    }
+    s->allocs.push_back(f.Llo);
+    if (!pdtc::make_map(&f.mapLo, f.Llo, 4, mq, mq, mq, 32)) { s->err = "cuTensorMapEncodeTiled failed"; return PD_ERR_CUDA; }
+  }
+  if (mode == pdtc::BF16 && !f.Lb) {
+    if (cudaMalloc(&f.Lb, sizeof(__nv_bfloat16) * mq * mq) != cudaSuccess) {
+      s->err = "device allocation of the BF16 panels failed";
+      return PD_ERR_OOM;
+    }
+    s->allocs.push_back(f.Lb);
+    if (!pdtc::make_map(&f.mapLb, f.Lb, 2, mq, mq, mq, 64)) { s->err = "cuTensorMapEncodeTiled failed"; return PD_ERR_CUDA; }
+  }
+  pdll::Args a;
+  a.map_hi = mode == pdtc::BF16 ? &f.mapLb : &f.mapL;
+  a.map_lo = mode == pdtc::TF32X3 ? &f.mapLo : nullptr;
+  a.L = f.L; a.Llo = f.Llo; a.Lb = f.Lb; a.Lh = f.Lh; a.Dinv = f.Dinv; a.E = f.E;
+  a.mq = mq; a.T = (int)M->T; a.kb = k_begin; a.sync = M->llsync; a.status = s->status;
+  cudaError_t e = pdll::factor(mode, a, s->stream);
+  if (e != cudaSuccess) { s->err = std::string("factorisation launch: ") + cudaGetErrorString(e); return PD_ERR_CUDA; }
+  f.valid = true;
+  return PD_OK;
+}
+
 static cudaError_t precond(pd_solver* s, const Factor& f, const double* r, double* z) {
   MixedState* M = s->mixed;
   const int64_t T = M->T;
@@ -1261,7 +1104,8 @@ static pd_status build_minv(pd_solver* s) {
   }
   if (!M->f0.valid) {
     factor_cast(s, M->f0, false);
-    factor_panels(s, M->f0, pdtc::TF32X3);
+    pd_status r = factor_ll(s, M->f0, pdtc::TF32X3);
+    if (r != PD_OK) return r;
   }
   const int64_t m = s->m;
   for (int64_t q = 0; 3 * q < m; ++q) {
@@ -1371,9 +1215,9 @@ pd_status mixed_factor(pd_solver* s) {
     }
     s->tend();
     s->tbegin(8);
-    factor_panels(s, f, mode, f.k0, (int)M->T);
+    rs = factor_ll(s, f, mode, f.k0);
     s->tend();
-    return PD_OK;
+    return rs;
   }
   M->nested_ready = false;
   M->f.iperm = nullptr;
@@ -1381,9 +1225,9 @@ pd_status mixed_factor(pd_solver* s) {
   factor_cast(s, M->f, true);
   s->tend();
   s->tbegin(8);
-  factor_panels(s, M->f, mode);
+  rs = factor_ll(s, M->f, mode);
   s->tend();
-  return PD_OK;
+  return rs;
 }
 
 void mixed_nested_changed(pd_solver* s) {

@@ -132,14 +132,20 @@ def test_detector_errors_and_clear(pd):
     assert np.array_equal(x_det, sol.positions())
 
 
-def _closed_elbow(h=1.5, frac=0.08, angle=30.0):
-    """Small elbow with every side-B node turned rigidly by `angle` about the
-    hinge (the joint closed by that much), so that side-A nodes come within
-    the gap of side-B triangles; the caps at the matching flexion step."""
+def _closed_elbow(h=1.5, frac=0.08, angle=40.0, band=8.0):
+    """Small elbow with the joint closed by `angle` about the hinge: every
+    node turned by angle * smoothstep over a band of half-width `band` across
+    the plane x + y = 0 that separates the two sides (no element inverts),
+    so that side-A nodes come within the gap of side-B triangles; the caps at
+    the matching flexion step."""
     s = scenes.small_elbow(h=h, region_fraction=frac)
+    d = (s.X[:, 0] + s.X[:, 1]) / np.sqrt(2.0)
+    t = np.clip((d + band) / (2.0 * band), 0.0, 1.0)
+    ang = np.radians(angle) * t * t * (3.0 - 2.0 * t)
+    c, sn = np.cos(ang), np.sin(ang)
     x0 = s.X.copy()
-    side_b = (s.X[:, 0] + s.X[:, 1]) >= 0.0
-    x0[side_b] = s.X[side_b] @ scenes.rotation_z(np.radians(angle)).T
+    x0[:, 0] = c * s.X[:, 0] - sn * s.X[:, 1]
+    x0[:, 1] = sn * s.X[:, 0] + c * s.X[:, 1]
     step = int(round(45 + angle / 2.0))
     return s, x0, s.dirichlet_positions(step)
 
@@ -161,46 +167,64 @@ def _set_tri(sol, s):
     sol.set_detector_triangles(pa, ta, pb, tb, s.info["tri_gap"], s.info["tri_rest_min"], s.stiffness)
 
 
-def test_triangle_detector_springs_equal_oracle(pd):
-    # the detected springs themselves: which nodes are active, which triangle
-    # and which closest point (decisions bit for bit), weights and targets
-    s, x0, dpos = _closed_elbow()
-    sol = _solver(pd, s)
-    sol.set_state(x0)
-    _set_tri(sol, s)
-    sol.detect()
+def _compare_springs(sol, s, x):
     nodes, w, t, c = sol.contacts()
     pa, ta, pb, tb = s.info["tri_sides"]
     assert len(c) == len(pa) + len(pb)
-    ref = _tri_fn(s)(x0)
+    ref = _tri_fn(s)(x)
     act = c > 0
-    assert act.sum() == ref.k and ref.k >= 20
+    assert act.sum() == ref.k
     np.testing.assert_array_equal(nodes[act], ref.nodes)
     np.testing.assert_array_equal(w[act], ref.w)
     np.testing.assert_array_equal(t[act], ref.target)
     np.testing.assert_array_equal(c[act], ref.stiffness)
     assert np.all(nodes[~act] == -1) and np.all(w[~act] == 0.0)
+    return ref.k
 
 
-@pytest.mark.parametrize("inner", [1, 2])
-def test_triangle_detector_step_matches_oracle(pd, inner):
-    # one step of 2 outer iterations from the closed pose, the springs
-    # re-detected on the device at every inner iteration
+def test_triangle_detector_springs_equal_oracle(pd):
+    # the detected springs themselves -- which nodes are active, which
+    # triangle and closest point (decisions bit for bit), weights, targets --
+    # on the closed pose and again on the state one solver step later (the
+    # same positions go to both sides)
+    s, x0, dpos = _closed_elbow()
+    sol = _solver(pd, s)
+    sol.set_state(x0)
+    _set_tri(sol, s)
+    sol.detect()
+    assert _compare_springs(sol, s, x0) >= 20
+    sol.set_dirichlet(dpos)
+    sol.step(1)
+    x1 = sol.positions()
+    sol.detect()
+    assert _compare_springs(sol, s, x1) >= 5
+
+
+def test_triangle_detector_steps_match_oracle_from_the_same_state(pd):
+    # three outer iterations from the closed pose, the springs re-detected on
+    # the device; each compared with the oracle's iteration from the same
+    # state (a node equidistant from two surfaces makes the nearest-triangle
+    # choice discontinuous, so two runs apart by rounding may pick
+    # differently later; the same state gives the same choice)
     s, x0, dpos = _closed_elbow()
     fn = _tri_fn(s)
     assert fn(x0).k >= 20
-    sol = _solver(pd, s, inner_iters=inner)
+    sol = _solver(pd, s)
     sol.set_state(x0)
     sol.set_dirichlet(dpos)
     _set_tri(sol, s)
-    sol.step(2)
-    o = oracle.OracleSolver(s.X, s.tets, s.dirichlet, s.region, s.mu)
-    o.x = x0.copy()
-    xo = o.step(2, inner, fn, dpos)
-    xg = sol.positions()
-    scale = np.abs(xo - x0).max()
-    assert np.abs(xg - xo).max() / scale <= TOL
-    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo - x0) <= TOL
+    x = x0.copy()
+    for it in range(3):
+        sol.step(1)
+        xg = sol.positions()
+        o = oracle.OracleSolver(s.X, s.tets, s.dirichlet, s.region, s.mu)
+        o.x = x.copy()
+        xo = o.step(1, 1, fn, dpos)
+        scale = np.abs(xo - x).max()
+        err_node = np.abs(xg - xo).max() / scale
+        err = np.linalg.norm(xg - xo) / np.linalg.norm(xo - x)
+        assert err_node <= TOL and err <= TOL, (it, err_node, err)
+        x = xg
 
 
 def test_triangle_detector_errors(pd):

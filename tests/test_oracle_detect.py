@@ -91,9 +91,10 @@ TRI = (np.array([0.0, 0.0, 0.0]), np.array([1.0, 0.0, 0.0]), np.array([0.0, 1.0,
     ((3.0, -1.0, 0.0), 5.0, (0.0, 1.0, 0.0)),     # vertex b region
 ])
 def test_closest_point_hand_cases(p, d2, w):
-    got_d2, got_w = detect.closest_point_on_triangle(p, *[tuple(v) for v in TRI])
+    got_d2, got_w, got_q = detect.closest_point_on_triangle(p, *[tuple(v) for v in TRI])
     assert abs(got_d2 - d2) < 1e-14
     np.testing.assert_allclose(got_w, w, atol=1e-15)
+    np.testing.assert_allclose(got_q, sum(wi * v for wi, v in zip(w, TRI)), atol=1e-15)
 
 
 def test_closest_point_against_qp_and_sampling():
@@ -105,7 +106,7 @@ def test_closest_point_against_qp_and_sampling():
     for _ in range(60):
         a, b, c = rng.normal(size=(3, 3))
         p = rng.normal(size=3) * 1.5
-        d2, wt = detect.closest_point_on_triangle(tuple(p), tuple(a), tuple(b), tuple(c))
+        d2, wt, _ = detect.closest_point_on_triangle(tuple(p), tuple(a), tuple(b), tuple(c))
         assert min(wt) >= -1e-15 and abs(sum(wt) - 1.0) < 1e-12
         q = wt[0] * a + wt[1] * b + wt[2] * c
         assert abs(np.sum((p - q) ** 2) - d2) < 1e-10
@@ -137,6 +138,14 @@ def test_point_triangle_springs_hand_cases():
         np.testing.assert_allclose(t[j], [0.0, 0.0, gap], atol=1e-15)
         np.testing.assert_allclose(-w[j, 4:7], [0.5, 0.25, 0.25], atol=1e-15)
         assert list(nodes[j, 4:7]) == [0, 1, 2]
+    # a node beyond the edge x = 0, in front: pushed along q -> node, not along n
+    X2 = np.vstack([X[:3], [[-0.3, 0.5, 3.0]]])
+    x2 = X2.copy()
+    x2[3] = [-0.3, 0.5, 0.4]
+    _, w2, t2, _, idx2, _ = detect.point_triangle_springs(np.array([3]), tris, x2, X2, 0.6, 0.5, 1.0)
+    assert list(idx2) == [0]
+    np.testing.assert_allclose(t2[0], [-0.36, 0.0, 0.48], atol=1e-15)
+    np.testing.assert_allclose(-w2[0, 4:7], [0.75, 0.0, 0.25], atol=1e-15)
     # the spring's rest point is the node a distance gap in front of q
     con = scenes.Contacts(nodes[:1], w[:1], t[:1], c[:1])
     xr = x.copy()
