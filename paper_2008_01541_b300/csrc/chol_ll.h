@@ -6,11 +6,12 @@
 // L_ik L_jk^T is accumulated on the tensor cores (tcgen05, TF32 / split TF32
 // / BF16 operands, FP32 accumulator in tensor memory) from TMA loads that
 // start as soon as the panels they read are final; then either the diagonal
-// tile is factored and inverted in FP32 (L_jj, Dinv_j = L_jj^-1, E_j =
-// Dinv_j^T Dinv_j), or the panel tile is L_ij = S Dinv_j^T and
-// Lh_ij = L_ij Dinv_j = S E_j.  Tasks are claimed in column-major order by a
-// grid of co-resident CTAs and each waits only on earlier tasks, through
-// per-row counters in global memory; every wait is bounded.
+// tile is factored in FP32 (L_jj, published at once) and inverted (Dinv_j =
+// L_jj^-1, E_j = Dinv_j^T Dinv_j), or the panel tile solves L_ij L_jj^T = S
+// by blocked substitution (published at once) and then forms
+// Lh_ij = L_ij Dinv_j.  A few CTAs take the diagonal tasks in order, the
+// others the panel tasks in column-major order; each waits only on earlier
+// tasks, through per-row counters in global memory; every wait is bounded.
 #pragma once
 #include <cstddef>
 #include <cstdint>
@@ -35,10 +36,11 @@ struct Args {
   int T = 0;
   int kb = 0;                            // first tile column factored (earlier panels are final and unused)
   int* sync = nullptr;                   // sync_bytes(T) of scratch (zeroed by factor())
+  int max_ctas = 0;                      // cap on the persistent grid (0: two thirds of the SMs)
   int* status = nullptr;                 // [0] first non-positive pivot + 1, [1] wait failure code
 };
 
-inline size_t sync_bytes(int T) { return sizeof(int) * (1 + 2 * (size_t)T); }
+inline size_t sync_bytes(int T) { return sizeof(int) * (2 + 2 * (size_t)T); }
 
 // Launch the factorisation of tile columns kb .. T-1 on st.
 cudaError_t factor(pdtc::Mode mode, const Args& a, cudaStream_t st);

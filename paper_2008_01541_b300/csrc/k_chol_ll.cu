@@ -35,6 +35,7 @@ using pdm::PADW;
 constexpr int SP = NB + 4;                // row stride of the transposed operands of the panel products
 constexpr uint32_t kSpin = 1u << 22;      // bounded waits: ~1 s with back-off
 constexpr int kStageBudget = 196608;      // shared memory for the pipeline stages (192 KB)
+constexpr int kDiagCtas = 6;              // CTAs dedicated to the diagonal tasks
 
 template <int MODE>   // 0 = TF32, 1 = split TF32 (hi.hi + hi.lo + lo.hi), 2 = BF16
 struct Cfg {
@@ -48,6 +49,7 @@ struct Cfg {
 };
 
 struct Ptrs {
+  int ndiag;   // CTAs that run the diagonal tasks
   float* L;
   float* Llo;
   __nv_bfloat16* Lb;
@@ -127,6 +129,69 @@ __device__ __forceinline__ void prod_8x8(const float* X, const float* Y, int ty,
   }
 }
 
+// X L^T = S for the 128 x 128 panel tile: on entry XT[t * SP + r] = S[r][t],
+// on exit X[r][t]; Lj = the factored diagonal tile (row stride SP, lower),
+// rinv[k] = 1 / L[k][k].  Blocked by 32 columns: thread r < 128 solves its row
+// against the 32 x 32 diagonal block with its 32 unknowns in registers,
+// x_k = (s_k - sum_{t < k} L_kt x_t) / L_kk, reading each row of L with
+// 16-byte broadcasts; then all 256 threads remove the block's contribution
+// from the later columns (row r = tid & 127, half of those columns each),
+// again one 16-byte load per four multiply-adds.
+__device__ __forceinline__ void panel_substitution(float* XT, const float* Lj, const float* rinv) {
+  const int tid = threadIdx.x;
+#pragma unroll 1
+  for (int b = 0; b < 4; ++b) {
+    const int c0 = 32 * b;
+    if (tid < NB) {
+      float x[32];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) x[k] = XT[(c0 + k) * SP + tid];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        const float4* lr = reinterpret_cast<const float4*>(Lj + (c0 + k) * SP + c0);
+        float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+#pragma unroll
+        for (int t4 = 0; t4 < k / 4; ++t4) {
+          const float4 l = lr[t4];
+          p0 = fmaf(l.x, x[4 * t4], p0); p1 = fmaf(l.y, x[4 * t4 + 1], p1);
+          p2 = fmaf(l.z, x[4 * t4 + 2], p2); p3 = fmaf(l.w, x[4 * t4 + 3], p3);
+        }
+        if (k & 3) {   // the last, partial group of four
+          const float4 l = lr[k / 4];
+          const int t = 4 * (k / 4);
+          p0 = fmaf(l.x, x[t], p0);
+          if ((k & 3) > 1) p1 = fmaf(l.y, x[t + 1], p1);
+          if ((k & 3) > 2) p2 = fmaf(l.z, x[t + 2], p2);
+        }
+        x[k] = (x[k] - ((p0 + p1) + (p2 + p3))) * rinv[c0 + k];
+      }
+#pragma unroll
+      for (int k = 0; k < 32; ++k) XT[(c0 + k) * SP + tid] = x[k];
+    }
+    __syncthreads();
+    const int rest = NB - c0 - 32;
+    if (rest > 0) {
+      const int r = tid & 127, half = tid >> 7, n = rest / 2, cbeg = c0 + 32 + half * n;
+      float x[32];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) x[k] = XT[(c0 + k) * SP + r];
+#pragma unroll 1
+      for (int c = cbeg; c < cbeg + n; ++c) {
+        const float4* lr = reinterpret_cast<const float4*>(Lj + c * SP + c0);
+        float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+#pragma unroll
+        for (int t4 = 0; t4 < 8; ++t4) {
+          const float4 l = lr[t4];
+          p0 = fmaf(l.x, x[4 * t4], p0); p1 = fmaf(l.y, x[4 * t4 + 1], p1);
+          p2 = fmaf(l.z, x[4 * t4 + 2], p2); p3 = fmaf(l.w, x[4 * t4 + 3], p3);
+        }
+        XT[c * SP + r] -= (p0 + p1) + (p2 + p3);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // the thread's 8 x 8 outputs into a row-major tile at dst (row stride ld)
 __device__ __forceinline__ void store_8x8(float* dst, int64_t ld, int ty, int tx, const float (&acc)[8][8]) {
 #pragma unroll
@@ -150,10 +215,18 @@ __global__ void __launch_bounds__(256, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int T = P.T, kb = P.kb;
   const int64_t mq = P.mq;
-  int* claim = P.sync;
-  int* rowcnt = P.sync + 1;       // [T] finished tiles of row i among columns kb..
-  int* ecnt = P.sync + 1 + T;     // [T] E_j written
-  const int nt = T - kb, ntask = nt * (nt + 1) / 2;
+  // Roles: the first NDIAG CTAs run only the diagonal tasks (in order, from
+  // their own counter), the others only the panel tasks (column-major), so
+  // each CTA keeps running the same code and finds it in its instruction
+  // cache.  A diagonal task waits only on panels of earlier columns and a
+  // panel only on earlier diagonals and earlier panels, so both lists
+  // progress.
+  int* claim = P.sync;            // [0] diagonal tasks, [1] panel tasks
+  int* rowcnt = P.sync + 2;       // [T] finished tiles of row i among columns kb..
+  int* dcnt = P.sync + 2 + T;     // [T] Dinv_j written
+  const int nt = T - kb;
+  const bool diag_cta = (int)blockIdx.x < P.ndiag;
+  const int ntask = diag_cta ? nt : nt * (nt - 1) / 2;
   constexpr int KIND = MODE == 2 ? 1 : 0;
   constexpr uint32_t ID = idesc(MODE == 2 ? 1u : 2u);
 
@@ -175,19 +248,25 @@ __global__ void __launch_bounds__(256, 1)
   const uint32_t tmem = tmem_base;
   uint32_t g = 0;      // chunks through the stage ring so far (the producer and the MMA thread agree)
   uint32_t nacc = 0;   // tasks that used the accumulator so far
-  float* A = reinterpret_cast<float*>(sm);    // diagonal task: the tile [128][PADW]
-  float* Zd = A + NB * PADW;                  //   and the diagonal blocks of its inverse [4][32][33]
+  float* A = reinterpret_cast<float*>(sm);    // diagonal task: the tile [128][SP]
+  float* Zd = A + NB * SP;                    //   and the diagonal blocks of its inverse [4][32][33]
   float* ST = reinterpret_cast<float*>(sm);   // panel task: S transposed [128][SP]
   float* DT = ST + NB * SP;                   //   and the right operand [128][SP]
 
   for (;;) {
-    if (tid == 0) s_task = (s_stop || failed_globally(P.status)) ? ntask : atomicAdd(claim, 1);
+    if (tid == 0) s_task = (s_stop || failed_globally(P.status)) ? ntask : atomicAdd(claim + (diag_cta ? 0 : 1), 1);
     __syncthreads();
     const int t = s_task;
     if (t >= ntask) break;
-    int j = kb, rem = t;   // column-major over the lower tiles of columns kb .. T-1
-    while (rem >= T - j) { rem -= T - j; ++j; }
-    const int i = j + rem;
+    int i, j;
+    if (diag_cta) {
+      i = j = kb + t;
+    } else {   // column-major over the tiles below the diagonal of columns kb .. T-2
+      int rem = t;
+      j = kb;
+      while (rem >= T - j - 1) { rem -= T - j - 1; ++j; }
+      i = j + 1 + rem;
+    }
     const bool diag = i == j;
     const int nchunk = (j - kb) * C::CPP;
     float* Lt = P.L + (int64_t)i * NB * mq + (int64_t)j * NB;
@@ -278,7 +357,7 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
               const int c = c0 + 4 * q4 + u;
-              if (diag) A[r * PADW + c] = e[u];
+              if (diag) A[r * SP + c] = e[u];
               else ST[c * SP + r] = e[u];
             }
           }
@@ -291,7 +370,7 @@ __global__ void __launch_bounds__(256, 1)
         if (diag) {
           const int r = q >> 5, c = 4 * (q & 31);
           const float4 a = __ldcg(reinterpret_cast<const float4*>(Lt + (int64_t)r * mq + c));
-          A[r * PADW + c] = a.x; A[r * PADW + c + 1] = a.y; A[r * PADW + c + 2] = a.z; A[r * PADW + c + 3] = a.w;
+          *reinterpret_cast<float4*>(A + r * SP + c) = a;
         } else {
           const int r = q & 127, c = 4 * (q >> 7);
           const float4 a = __ldcg(reinterpret_cast<const float4*>(Lt + (int64_t)r * mq + c));
@@ -303,18 +382,24 @@ __global__ void __launch_bounds__(256, 1)
     __syncthreads();
 
     if (diag) {
-      // ---- L_jj, then Dinv_j (the panels of column j wait for it), then E_j
-      pdm::diag_factor_smem(A, j, P.status);
+      // ---- L_jj (the panels of column j wait for it), then Dinv_j (their Lh
+      // products wait for it), then E_j for the preconditioner
+      pdm::diag_factor_f4(A, j, P.status);
       for (int q = tid; q < NB * NB; q += 256) {
         const int r = q / NB, c = q % NB;
-        if (c <= r) Lt[(int64_t)r * mq + c] = A[r * PADW + c];
+        if (c <= r) Lt[(int64_t)r * mq + c] = A[r * SP + c];
       }
-      float* Di = P.Dinv + (int64_t)j * NB * NB;
-      pdm::tile_inverse(A, Zd, Di);
       __syncthreads();
-      if (tid == 0) {
+      if (tid == 0) {   // the panels of column j solve against L_jj
         __threadfence();
         st_release(rowcnt + j, j - kb + 1);
+      }
+      float* Di = P.Dinv + (int64_t)j * NB * NB;
+      pdm::tile_inverse<SP>(A, Zd, Di);
+      __syncthreads();
+      if (tid == 0) {   // their Lh products need Dinv_j
+        __threadfence();
+        st_release(dcnt + j, 1);
       }
       float* Dsm = A;   // Dinv_j again, padded rows
 #pragma unroll 4
@@ -331,48 +416,38 @@ __global__ void __launch_bounds__(256, 1)
         for (int t2 = (r > c ? r : c); t2 < NB; ++t2) e = fmaf(Dsm[t2 * PADW + r], Dsm[t2 * PADW + c], e);
         Ej[q] = e;
       }
-      __syncthreads();
-      if (tid == 0) {
-        __threadfence();
-        st_release(ecnt + j, 1);
-      }
     } else {
-      // ---- L_ij = S Dinv_j^T once Dinv_j is ready; then Lh_ij = S E_j
+      // ---- L_ij from L_ij L_jj^T = S once L_jj is final; then Lh_ij = L_ij Dinv_j
       if (tid == 0 && !wait_flag(rowcnt + j, j - kb + 1, P.status, 316)) s_stop = 1;
       __syncthreads();
       if (s_stop) continue;
-      const float* Di = P.Dinv + (int64_t)j * NB * NB;
+      float* Lj = DT;                      // L_jj, rows of SP
+      __shared__ float rinv[NB];
+      const float* Ljg = P.L + (int64_t)j * NB * mq + (int64_t)j * NB;
 #pragma unroll 4
-      for (int k = 0; k < 16; ++k) {   // DT[t][n] = Dinv_j[n][t]
-        const int q = tid + 256 * k, n = q & 127, t4 = 4 * (q >> 7);
-        const float4 v = __ldcg(reinterpret_cast<const float4*>(Di + n * NB + t4));
-        DT[t4 * SP + n] = v.x; DT[(t4 + 1) * SP + n] = v.y; DT[(t4 + 2) * SP + n] = v.z; DT[(t4 + 3) * SP + n] = v.w;
+      for (int k = 0; k < 16; ++k) {
+        const int q = tid + 256 * k, r = q >> 5, c = 4 * (q & 31);
+        *reinterpret_cast<float4*>(Lj + r * SP + c) = __ldcg(reinterpret_cast<const float4*>(Ljg + (int64_t)r * mq + c));
       }
       __syncthreads();
-      const int ty = tid >> 4, tx = tid & 15;
-      float acc[8][8];
-      prod_8x8(ST, DT, ty, tx, acc);
-      store_8x8(Lt, mq, ty, tx, acc);
+      if (tid < NB) rinv[tid] = 1.f / Lj[tid * SP + tid];
+      __syncthreads();
+      panel_substitution(ST, Lj, rinv);
+      // X (in ST, transposed) -> row-major with padded rows in the L_jj buffer, then coalesced stores
+      float* XR = DT;
+      for (int q = tid; q < NB * NB; q += 256) {
+        const int r = q & 127, c = q >> 7;
+        XR[r * PADW + c] = ST[c * SP + r];
+      }
+      __syncthreads();
       const int64_t off = (int64_t)i * NB * mq + (int64_t)j * NB;
-      if (MODE == 1) {   // TF32 tails of the panel for the split products of later tasks
-#pragma unroll
-        for (int p = 0; p < 8; ++p) {
-          float* row = P.Llo + off + (int64_t)(8 * ty + p) * mq;
-          *reinterpret_cast<float4*>(row + 4 * tx) =
-              make_float4(tf32_tail(acc[p][0]), tf32_tail(acc[p][1]), tf32_tail(acc[p][2]), tf32_tail(acc[p][3]));
-          *reinterpret_cast<float4*>(row + 64 + 4 * tx) =
-              make_float4(tf32_tail(acc[p][4]), tf32_tail(acc[p][5]), tf32_tail(acc[p][6]), tf32_tail(acc[p][7]));
-        }
-      } else if (MODE == 2) {   // the panel rounded to BF16 for the BF16 products of later tasks
-#pragma unroll
-        for (int p = 0; p < 8; ++p) {
-          __nv_bfloat16* row = P.Lb + off + (int64_t)(8 * ty + p) * mq;
-          __nv_bfloat16 h0[4], h1[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) { h0[q] = __float2bfloat16_rn(acc[p][q]); h1[q] = __float2bfloat16_rn(acc[p][4 + q]); }
-          *reinterpret_cast<uint2*>(row + 4 * tx) = *reinterpret_cast<const uint2*>(h0);
-          *reinterpret_cast<uint2*>(row + 64 + 4 * tx) = *reinterpret_cast<const uint2*>(h1);
-        }
+      for (int q = tid; q < NB * NB; q += 256) {
+        const int r = q >> 7, c = q & 127;
+        const float v = XR[r * PADW + c];
+        const int64_t o = off + (int64_t)r * mq + c;
+        P.L[o] = v;
+        if (MODE == 1) P.Llo[o] = tf32_tail(v);   // TF32 tails for the split products of later tasks
+        if (MODE == 2) P.Lb[o] = __float2bfloat16_rn(v);   // BF16 copy for the BF16 products
       }
       asm volatile("fence.proxy.async.global;" ::: "memory");   // later TMA reads of this tile
       __syncthreads();
@@ -380,17 +455,19 @@ __global__ void __launch_bounds__(256, 1)
         __threadfence();
         st_release(rowcnt + i, j - kb + 1);
       }
-      if (tid == 0 && !wait_flag(ecnt + j, 1, P.status, 317)) s_stop = 1;
+      if (tid == 0 && !wait_flag(dcnt + j, 1, P.status, 317)) s_stop = 1;
       __syncthreads();
       if (s_stop) continue;
-      const float* Ej = P.E + (int64_t)j * NB * NB;
+      const float* Di = P.Dinv + (int64_t)j * NB * NB;
 #pragma unroll 4
-      for (int k = 0; k < 16; ++k) {   // DT[t][n] = E_j[t][n]
+      for (int k = 0; k < 16; ++k) {   // DT[t][n] = Dinv_j[t][n]
         const int q = tid + 256 * k, t2 = q >> 5, n4 = 4 * (q & 31);
-        *reinterpret_cast<float4*>(DT + t2 * SP + n4) = __ldcg(reinterpret_cast<const float4*>(Ej + t2 * NB + n4));
+        *reinterpret_cast<float4*>(DT + t2 * SP + n4) = __ldcg(reinterpret_cast<const float4*>(Di + t2 * NB + n4));
       }
       __syncthreads();
-      prod_8x8(ST, DT, ty, tx, acc);
+      const int ty = tid >> 4, tx = tid & 15;
+      float acc[8][8];
+      prod_8x8(ST, DT, ty, tx, acc);   // Lh_ij[r][n] = sum_t X[r][t] Dinv_j[t][n]
       store_8x8(P.Lh + off, mq, ty, tx, acc);
     }
     // generic shared-memory accesses of this task precede the next task's TMA writes
@@ -406,7 +483,7 @@ __global__ void __launch_bounds__(256, 1)
 }
 
 template <int MODE>
-cudaError_t launch(const Args& a, const Ptrs& p, int ntask, cudaStream_t st) {
+cudaError_t launch(const Args& a, Ptrs p, int ntask, cudaStream_t st) {
   static std::atomic<unsigned long long> attr{0};
   static int per_dev[64];
   int dev = 0;
@@ -418,7 +495,16 @@ cudaError_t launch(const Args& a, const Ptrs& p, int ntask, cudaStream_t st) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chol_ll<MODE>, 256, Cfg<MODE>::SMEM);
     per_dev[dev & 63] = nsm * std::max(per, 1);   // one persistent CTA per SM
   }
-  const int grid = std::max(1, std::min(ntask, per_dev[dev & 63]));
+  // By default two thirds of the SMs: the chain of diagonal tiles, not the
+  // tensor-core work, sets the time, and the remaining SMs run the main
+  // stream's local step and sparse substitution concurrently.
+  int cap = a.max_ctas > 0 ? std::min(per_dev[dev & 63], a.max_ctas) : std::max(8, 2 * per_dev[dev & 63] / 3);
+  // a few diagonal CTAs (each diagonal task is claimed several steps before
+  // it is on the critical chain, time to accumulate its operands), the rest
+  // panel CTAs
+  const int nt = a.T - a.kb;
+  p.ndiag = std::min(nt, kDiagCtas);
+  const int grid = std::max(p.ndiag + 1, std::min(p.ndiag + ntask, cap));
   const CUtensorMap& lo = a.map_lo ? *a.map_lo : *a.map_hi;
   k_chol_ll<MODE><<<grid, 256, Cfg<MODE>::SMEM, st>>>(*a.map_hi, lo, p);
   ++pdk::g_launches;
@@ -435,8 +521,8 @@ cudaError_t factor(pdtc::Mode mode, const Args& a, cudaStream_t st) {
     return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(a.sync, 0, sync_bytes(a.T), st);
   if (e != cudaSuccess) return e;
-  const Ptrs p{a.L, a.Llo, a.Lb, a.Lh, a.Dinv, a.E, a.mq, a.T, a.kb, a.sync, a.status};
-  const int ntask = nt * (nt + 1) / 2;
+  const Ptrs p{0, a.L, a.Llo, a.Lb, a.Lh, a.Dinv, a.E, a.mq, a.T, a.kb, a.sync, a.status};
+  const int ntask = nt * (nt - 1) / 2;   // panel tasks
   switch (mode) {
     case pdtc::TF32X3: return launch<1>(a, p, ntask, st);
     case pdtc::BF16: return launch<2>(a, p, ntask, st);

@@ -66,6 +66,7 @@ struct MixedState {
   int pc_grid = 0;            // persistent grid of the preconditioner
   int* llsync = nullptr;      // counters of the persistent left-looking factorisation
   bool lookahead = false;     // PD_LOWP_SCHEDULE=lookahead: one launch per tile step instead
+  int ll_ctas = 0;            // PD_LOWP_CTAS: cap on the persistent factorisation's grid (0: two thirds of the SMs)
   cudaStream_t side = nullptr;              // low-priority stream for the bulk trailing updates
   std::vector<cudaEvent_t> ev_panel, ev_rest;
 };
@@ -956,6 +957,8 @@ static pd_status ensure_state(pd_solver* s) {
   {
     const char* sched = std::getenv("PD_LOWP_SCHEDULE");
     M->lookahead = sched && std::string(sched) == "lookahead";
+    const char* ctas = std::getenv("PD_LOWP_CTAS");
+    M->ll_ctas = ctas ? std::max(0, std::atoi(ctas)) : 0;
   }
   if (cudaMallocHost(&M->sc_h, sizeof(double) * 8) != cudaSuccess) return PD_ERR_OOM;
   // vectors beyond m stay zero: the padded products need no bounds checks
@@ -1070,7 +1073,7 @@ static pd_status factor_ll(pd_solver* s, Factor& f, pdtc::Mode mode, int k_begin
   a.map_hi = mode == pdtc::BF16 ? &f.mapLb : &f.mapL;
   a.map_lo = mode == pdtc::TF32X3 ? &f.mapLo : nullptr;
   a.L = f.L; a.Llo = f.Llo; a.Lb = f.Lb; a.Lh = f.Lh; a.Dinv = f.Dinv; a.E = f.E;
-  a.mq = mq; a.T = (int)M->T; a.kb = k_begin; a.sync = M->llsync; a.status = s->status;
+  a.mq = mq; a.T = (int)M->T; a.kb = k_begin; a.sync = M->llsync; a.status = s->status; a.max_ctas = M->ll_ctas;
   cudaError_t e = pdll::factor(mode, a, s->stream);
   if (e != cudaSuccess) { s->err = std::string("factorisation launch: ") + cudaGetErrorString(e); return PD_ERR_CUDA; }
   f.valid = true;

@@ -24,11 +24,20 @@ namespace {
 // pivot's column is updated first so that its square root overlaps the rest
 // of the current update.  A non-positive pivot is replaced by 1 and reported
 // in *status (first bad column + 1, offset by code0).
-__device__ __noinline__ void warp_chol32(float* Ap, float* rinv, int* status, int code0) {
+template <int LD = PADW>
+__device__ __forceinline__ void warp_chol32(float* Ap, float* rinv, int* status, int code0) {
   const int lane = threadIdx.x & 31;
   float a[32];
+  if (LD % 4 == 0) {   // 16-byte aligned rows
 #pragma unroll
-  for (int c = 0; c < 32; ++c) a[c] = Ap[lane * PADW + c];
+    for (int q = 0; q < 8; ++q) {
+      const float4 v = *reinterpret_cast<const float4*>(Ap + lane * LD + 4 * q);
+      a[4 * q] = v.x; a[4 * q + 1] = v.y; a[4 * q + 2] = v.z; a[4 * q + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 32; ++c) a[c] = Ap[lane * LD + c];
+  }
   __shared__ __align__(16) float col[2][32];
   unsigned bad = 0;
 #pragma unroll
@@ -60,8 +69,14 @@ __device__ __noinline__ void warp_chol32(float* Ap, float* rinv, int* status, in
     }
   }
   if (bad && lane == 0) atomicCAS(status, 0, code0 + __ffs(bad));
+  if (LD % 4 == 0) {   // the whole row (the part above the diagonal is never read)
 #pragma unroll
-  for (int c = 0; c < 32; ++c) if (c <= lane) Ap[lane * PADW + c] = a[c];
+    for (int q = 0; q < 8; ++q)
+      *reinterpret_cast<float4*>(Ap + lane * LD + 4 * q) = make_float4(a[4 * q], a[4 * q + 1], a[4 * q + 2], a[4 * q + 3]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 32; ++c) if (c <= lane) Ap[lane * LD + c] = a[c];
+  }
 }
 
 // 32 x 32 block product on a group of 64 threads: thread gr = tid & 63 holds
@@ -82,23 +97,24 @@ __device__ __forceinline__ void prod32_g64(const float* X, int ldx, const float*
 }
 
 // Dinv_k = L_kk^-1 from the factored tile in shared memory (A, row stride
-// PADW, lower triangle), written row-major to Di (zero above the diagonal).
+// LD, lower triangle), written row-major to Di (zero above the diagonal).
 // The four diagonal 32 x 32 blocks are inverted by one warp each; then, by
 // block diagonals d = i - j, Z_ij = -Z_ii T_ij with T_ij = sum_{j <= t < i}
 // L_it Z_tj, the (4 - d) blocks of a diagonal at once on groups of 64
 // threads.  The diagonal blocks Z_ii sit in Zd (leading dimension 33); an
 // off-diagonal block Z_ij (i > j) sits in the unused block (j, i) above the
 // diagonal of A.  Called by all 256 threads after a barrier.
+template <int LD = PADW>
 __device__ __forceinline__ void tile_inverse(float* A, float* Zd, float* __restrict__ Di) {
   const int tid = threadIdx.x, warp = tid >> 5;
   constexpr int LZ = 33;
   // level 0: Z_ii = L_ii^-1 (rows of Zd, leading dimension 33)
   if (warp < 4) {
     const int lane = tid & 31, c0 = 32 * warp;
-    const float* Ap = A + c0 * PADW + c0;
+    const float* Ap = A + c0 * LD + c0;
     float a[32], z[32];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) { a[c] = (c <= lane) ? Ap[lane * PADW + c] : 0.f; z[c] = (c == lane) ? 1.f : 0.f; }
+    for (int c = 0; c < 32; ++c) { a[c] = (c <= lane) ? Ap[lane * LD + c] : 0.f; z[c] = (c == lane) ? 1.f : 0.f; }
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
       if (lane == j) {
@@ -122,25 +138,25 @@ __device__ __forceinline__ void tile_inverse(float* A, float* Zd, float* __restr
   for (int d = 1; d < 4; ++d) {
     const int j = grp, i = j + d;
     if (i < 4) {
-      float* Zij = A + (32 * j) * PADW + 32 * i;     // block (j, i) of A holds Z_ij
+      float* Zij = A + (32 * j) * LD + 32 * i;     // block (j, i) of A holds Z_ij
       float o[4][4] = {};
       for (int t = j; t < i; ++t) {                  // T_ij = sum_t L_it Z_tj
-        const float* Lit = A + (32 * i) * PADW + 32 * t;
-        if (t == j) prod32_g64(Lit, PADW, Zd + j * 32 * LZ, LZ, o);
-        else prod32_g64(Lit, PADW, A + (32 * j) * PADW + 32 * t, PADW, o);   // Z_tj in block (j, t)
+        const float* Lit = A + (32 * i) * LD + 32 * t;
+        if (t == j) prod32_g64(Lit, LD, Zd + j * 32 * LZ, LZ, o);
+        else prod32_g64(Lit, LD, A + (32 * j) * LD + 32 * t, LD, o);   // Z_tj in block (j, t)
       }
 #pragma unroll
       for (int p = 0; p < 4; ++p)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) Zij[(orr + p) * PADW + occ + q] = o[p][q];
+        for (int q = 0; q < 4; ++q) Zij[(orr + p) * LD + occ + q] = o[p][q];
       bar_sync_n(1 + grp, 64);
       float z2[4][4] = {};
-      prod32_g64(Zd + i * 32 * LZ, LZ, Zij, PADW, z2);   // Z_ij = -Z_ii T_ij
+      prod32_g64(Zd + i * 32 * LZ, LZ, Zij, LD, z2);   // Z_ij = -Z_ii T_ij
       bar_sync_n(1 + grp, 64);
 #pragma unroll
       for (int p = 0; p < 4; ++p)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) Zij[(orr + p) * PADW + occ + q] = -z2[p][q];
+        for (int q = 0; q < 4; ++q) Zij[(orr + p) * LD + occ + q] = -z2[p][q];
     }
     __syncthreads();
   }
@@ -148,7 +164,7 @@ __device__ __forceinline__ void tile_inverse(float* A, float* Zd, float* __restr
     const int r = q / NB, c = q % NB, bi = r >> 5, bj = c >> 5;
     float v = 0.f;
     if (bi == bj) v = (c <= r) ? Zd[bi * 32 * LZ + (r & 31) * LZ + (c & 31)] : 0.f;
-    else if (bi > bj) v = A[(32 * bj + (r & 31)) * PADW + 32 * bi + (c & 31)];
+    else if (bi > bj) v = A[(32 * bj + (r & 31)) * LD + 32 * bi + (c & 31)];
     Di[q] = v;
   }
 }
@@ -160,7 +176,7 @@ __device__ __forceinline__ void tile_inverse(float* A, float* Zd, float* __restr
 // is solved one thread per row.  A non-positive pivot is replaced by 1 and
 // reported in status[0] as the first bad column (of tile kt) + 1.  Called by
 // all 256 threads after a barrier; ends with one.
-__device__ __forceinline__ void diag_factor_smem(float* A, int kt, int* status) {
+__device__ __noinline__ void diag_factor_smem(float* A, int kt, int* status) {
   __shared__ float rinv32[32];     // 1 / L_jj of the current 32 x 32 sub-block
   const int tid = threadIdx.x, warp = tid >> 5;
 #pragma unroll 1
@@ -230,6 +246,111 @@ __device__ __forceinline__ void diag_factor_smem(float* A, int kt, int* status) 
         A[(r + 1) * PADW + c + 1] -= s11;
         if (c + 1 <= r) A[r * PADW + c + 1] -= s01;
       }
+      __syncthreads();
+    }
+  }
+}
+
+// A[r][c] -= sum_{k < 32} A[r][pc + k] A[c][pc + k] over the 32 x 32
+// super-block at rows R.., columns C.. of a tile with row stride LD (a
+// multiple of 4 with LD % 32 == 4), for c <= r only (so a super-block on
+// the diagonal keeps its upper part).  64 threads, g = 0..63: rows
+// R + bi + 8 i and columns C + bj + 8 j (bi = g & 7, bj = g >> 3), so the
+// eight lanes of a quarter-warp read rows in distinct 16-byte bank groups
+// (row loads) or the same row (broadcast), and the stores hit 32 banks.
+template <int LD>
+__device__ __forceinline__ void superblock_update(float* A, int R, int C, int pc, int g) {
+  const int bi = g & 7, bj = g >> 3;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+#pragma unroll
+  for (int k4 = 0; k4 < 8; ++k4) {
+    float4 a[4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = *reinterpret_cast<const float4*>(A + (R + bi + 8 * i) * LD + pc + 4 * k4);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) b[j] = *reinterpret_cast<const float4*>(A + (C + bj + 8 * j) * LD + pc + 4 * k4);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        acc[i][j] = fmaf(a[i].w, b[j].w, fmaf(a[i].z, b[j].z, fmaf(a[i].y, b[j].y, fmaf(a[i].x, b[j].x, acc[i][j]))));
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = R + bi + 8 * i, c = C + bj + 8 * j;
+      if (c <= r) A[r * LD + c] -= acc[i][j];
+    }
+}
+
+// Factor the 128 x 128 tile A (shared memory, row stride NB + 4, lower
+// triangle) in place with 256 threads: the same blocked order as
+// diag_factor_smem (32-wide sub-blocks, warp 0 factoring sub-block p while
+// warps 1-6 apply the rest of panel p-1), with every operand read as 16-byte
+// rows: the trailing updates on 32 x 32 super-blocks of 64 threads, the panel
+// below each sub-block by one thread per row in dot-product form.  A
+// non-positive pivot is replaced by 1 and reported in status[0] as the first
+// bad column (of tile kt) + 1.  Called by all 256 threads after a barrier;
+// ends with one.
+__device__ __noinline__ void diag_factor_f4(float* A, int kt, int* status) {
+  constexpr int LD = NB + 4;
+  __shared__ __align__(16) float rinv[NB];   // 1 / L_jj
+  const int tid = threadIdx.x, warp = tid >> 5;
+#pragma unroll 1
+  for (int p = 0; p < 4; ++p) {
+    const int c0 = 32 * p;
+    if (warp == 0) {
+      warp_chol32<LD>(A + c0 * LD + c0, rinv + c0, status, kt * NB + c0);
+    } else if (p > 0 && tid < 224) {
+      // rest of panel p-1: super-blocks (rb, cb), p < rb <= 3, p <= cb <= rb, on three groups of 64
+      const int grp = (tid - 32) >> 6, g = (tid - 32) & 63;
+      int idx = 0;
+      for (int rb = p + 1; rb < 4; ++rb)
+        for (int cb = p; cb <= rb; ++cb, ++idx)
+          if (idx % 3 == grp) superblock_update<LD>(A, 32 * rb, 32 * cb, c0 - 32, g);
+    }
+    __syncthreads();
+    // the panel below sub-block p: x L_pp^T = a for each row, x_k = (a_k - sum_{t<k} L_kt x_t) / L_kk
+    const int nbelow = NB - c0 - 32;
+    if (tid < nbelow) {
+      float* row = A + (c0 + 32 + tid) * LD + c0;
+      float x[32];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float4 v = *reinterpret_cast<const float4*>(row + 4 * q);
+        x[4 * q] = v.x; x[4 * q + 1] = v.y; x[4 * q + 2] = v.z; x[4 * q + 3] = v.w;
+      }
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        const float4* lr = reinterpret_cast<const float4*>(A + (c0 + k) * LD + c0);
+        float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+#pragma unroll
+        for (int t4 = 0; t4 < k / 4; ++t4) {
+          const float4 l = lr[t4];
+          p0 = fmaf(l.x, x[4 * t4], p0); p1 = fmaf(l.y, x[4 * t4 + 1], p1);
+          p2 = fmaf(l.z, x[4 * t4 + 2], p2); p3 = fmaf(l.w, x[4 * t4 + 3], p3);
+        }
+        if (k & 3) {
+          const float4 l = lr[k / 4];
+          const int t = 4 * (k / 4);
+          p0 = fmaf(l.x, x[t], p0);
+          if ((k & 3) > 1) p1 = fmaf(l.y, x[t + 1], p1);
+          if ((k & 3) > 2) p2 = fmaf(l.z, x[t + 2], p2);
+        }
+        x[k] = (x[k] - ((p0 + p1) + (p2 + p3))) * rinv[c0 + k];
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        *reinterpret_cast<float4*>(row + 4 * q) = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+    }
+    __syncthreads();
+    if (p < 3) {   // the next diagonal sub-block with panel p (its factor comes next)
+      if (tid < 64) superblock_update<LD>(A, c0 + 32, c0 + 32, c0, tid);
       __syncthreads();
     }
   }
