@@ -1,12 +1,14 @@
 """Benchmark: PD iterations per second of the localized-collision PD hot path.
 
 One step = one outer iteration of Algorithm 1 with one inner iteration
-(local alpha step + forces, sparse forward substitution, contact update of
-Sigma, local beta step + RHS, dense refactor + solve, bookkeeping, sparse
-backward substitution) on the ~598K-tet elbow scene with 5% collision-prone
-nodes.  `value` is device-timed with every input resident in HBM; `e2e`
-repeats the measurement through the C ABI with host buffers (Dirichlet
-positions and contacts uploaded and positions read back every step).
+(local alpha step + forces, sparse forward substitution, point-triangle
+self-contact detection on the device, contact update of Sigma, local beta
+step + RHS, dense refactor + solve, bookkeeping, sparse backward
+substitution) on the ~598K-tet elbow with 5% collision-prone nodes, the
+joint flexed 40 degrees past the rest L so the crease surfaces are in
+contact.  `value` is device-timed with every input resident in HBM; `e2e`
+repeats the measurement through the C ABI with host buffers (the step's
+Dirichlet positions uploaded and the positions read back every step).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32|tf32|bf16|pcg]
     python bench.py --impl reference ...   # the FP64 CPU oracle on the same workload
@@ -18,6 +20,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import subprocess
 import sys
 import tempfile
@@ -30,8 +33,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "PD iters/sec at 600K tets, 5% contact DOFs; Schur refactor+solve ms at 1e-10"
 UNIT = "PD iters/s"
-CONTACT_STEP = 60          # flexion step whose rest-pose contact set drives the timed steps
+CLOSE_ANGLE = 40.0         # the joint closed this many degrees past the rest L (flexion step 65)
 PEAK_FP64_ALU = 148 * 2 * 2 * 2032e6   # SMs x DFMA/clk/SM x flops/FMA x max SM clock
+# DRAM bytes per FP64 refactor + solve at m = 6,572, from the ncu capture in
+# profiles/fp64_refactor_dram_elbow598k.md (sum of dram__bytes_read.sum and
+# dram__bytes_write.sum over the kernels of one refactorisation and solve).
+FP64_A5_DRAM_BYTES = None
 
 
 def parse():
@@ -44,11 +51,11 @@ def parse():
     ap.add_argument("--h", type=float, default=0.585, help="elbow voxel spacing (0.585 -> ~598K tets)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip timing the other precision forms")
+    ap.add_argument("--no-extra", action="store_true", help="skip the flexion trajectory and the lips rows")
     ap.add_argument("--train-solves", type=int, default=200, help="solves recorded to train the warm start")
     ap.add_argument("--train-steps", type=int, default=1000)
     ap.add_argument("--sweep", action="store_true",
-                    help="also measure inner = 3 and 5, the Schur refactor+solve median / p90 over repeated "
-                         "solves, and the two-slab lips scene at 2.5 / 5 / 10%% region (adds a 'sweep' key)")
+                    help="also measure inner = 3 and 5 and the Schur refactor+solve median / p90 over repeated solves")
     ap.add_argument("--nested", action="store_true",
                     help="main timed region with pd_set_contact_nodes on the proxies (nested Schur refactorisation)")
     ap.add_argument("--profile-step", action="store_true",
@@ -80,7 +87,9 @@ def aggregate_replicas(local_ms, steps, world, dist=None, device="cpu"):
 def workload_name(s, precision):
     return (f"elbow (two r=8 L=60 cylinders + joint ball, voxel h={s.info['h']}): {s.E} tets, {s.n} nodes, "
             f"m={s.m} collision-prone nodes ({100.0 * s.m / s.n:.1f}%), quasistatic, {precision} region solve, "
-            f"1 outer x 1 inner iteration per step, rest-pose cylinder self-contact set of flexion step {CONTACT_STEP}")
+            f"1 outer x 1 inner iteration per step, joint closed {CLOSE_ANGLE:.0f} deg past the rest L "
+            f"(flexion step {int(round(45 + CLOSE_ANGLE / 2))}), point-triangle self-contact (k=1e6) detected on "
+            f"the device every inner iteration")
 
 
 class ClockSampler:
@@ -137,6 +146,25 @@ def measured_peaks():
         return 6400.0, 1800.0, "fallback"
 
 
+def host_info():
+    """Host cores and CPU model of this machine."""
+    model = platform.processor() or ""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
+
+
+def set_detector(sol, s):
+    """Point-triangle self-contact of the two elbow segments (device detection)."""
+    pa, ta, pb, tb = s.info["tri_sides"]
+    sol.set_detector_triangles(pa, ta, pb, tb, s.info["tri_gap"], s.info["tri_rest_min"], s.stiffness)
+
+
 def form_roofline(pd, prec, m, n_ref, refactor_ms, solve_ms, iters):
     """Roofline of a form's dominant work.  FP64: the dense refactorisation
     (n_ref^3 / 3 flop) against the derived FP64 ALU peak.  Low-precision forms:
@@ -162,6 +190,11 @@ def form_roofline(pd, prec, m, n_ref, refactor_ms, solve_ms, iters):
         peak, bound, ps = bf16 * 1.1 / 2.25, "tensor", src + " bf16 x nominal TF32/BF16 ratio"
     return {"bound": bound, "work": "dense refactorisation, n = %d" % n_ref, "achieved": ach, "peak": peak,
             "unit": "TFLOP/s", "frac": ach / peak, "peak_source": ps}
+
+
+def active_springs(sol):
+    _, _, _, c = sol.contacts()
+    return int((c > 0).sum())
 
 
 def time_form(pd, sol, stream, args, fp64_ms, torch, prec, nested):
@@ -198,6 +231,7 @@ def time_form(pd, sol, stream, args, fp64_ms, torch, prec, nested):
     return {"ms_per_step": ms, "value": 1e3 / ms, "unit": UNIT, "speedup_vs_fp64": fp64_ms / ms,
             "schur_refactor_solve_ms": schur / k, "refactor_ms": ref / k, "refine_iters": iters / k,
             "max_rel_residual": res if res > 0 else None,   # None: the direct FP64 solve measures none
+            "active_springs": active_springs(sol),
             "roofline": form_roofline(pd, prec, s.m, n_ref, ref / k, (fs - ref) / k, iters / k)}
 
 
@@ -207,6 +241,7 @@ def time_forms(pd, sol, stream, args, fp64_ms, torch):
     Schur refactor+solve time and the refinement iterations it took to reach
     the 1e-10 relative residual."""
     out = {}
+    s = sol._scene
     state = sol.get_state()
     for name, prec in (("fp32_ir (split-TF32 tcgen05)", pd.FP32_IR), ("tf32_ir (TF32 tcgen05, CG-refined)", pd.TF32_IR),
                        ("bf16_ir (BF16 tcgen05, CG-refined)", pd.BF16_IR), ("pcg (contact-free preconditioner, cold start)", pd.PCG_WARM)):
@@ -214,23 +249,23 @@ def time_forms(pd, sol, stream, args, fp64_ms, torch):
         sol.set_precision(prec)
         out[name] = time_form(pd, sol, stream, args, fp64_ms, torch, prec, False)
     # the nested Schur refactorisation on the contact-capable nodes (FP64 and split-TF32)
-    con = sol._contacts
-    npx = len(sol._scene.proxies)
+    npx = len(s.proxies)
     for name, prec in (("fp64_nested (FP64; Schur block of the %d contact nodes refactored, rest factored once)" % npx,
                         pd.FP64),
                        ("fp32_ir_nested (split-TF32 + IR; Schur block of the %d contact nodes refactored)" % npx,
                         pd.FP32_IR)):
         sol.set_state(*state)
         sol.set_precision(prec)
-        sol.set_contact_nodes(sol._scene.proxies)
-        sol.set_contacts(con.nodes, con.w, con.target, con.stiffness)
+        sol.set_contact_nodes(s.proxies)
+        set_detector(sol, s)
         out[name] = time_form(pd, sol, stream, args, fp64_ms, torch, prec, True)
         sol.set_contact_nodes(None)
-        sol.set_contacts(con.nodes, con.w, con.target, con.stiffness)
+        set_detector(sol, s)
     out.update(time_learned(pd, sol, stream, args, fp64_ms, torch, state))
     sol.set_precision(pd.FP64)
     sol.set_warm_start(0)
     sol.set_state(*state)
+    set_detector(sol, s)
     return out
 
 
@@ -263,25 +298,44 @@ def step_rate(sol, stream, torch, steps):
     return {"ms_per_step": ms, "value": 1e3 / ms, "unit": UNIT}
 
 
-def sweep(pd, sol, stream, torch, args):
-    """Measurements beyond the headline line: inner = 3 and 5 on the elbow,
-    Schur refactor+solve median / p90 over repeated solves, and the two-slab
-    lips scene at 2.5 / 5 / 10% collision-prone nodes."""
+def trajectory(pd, sol, stream, torch):
+    """The whole flexion of configuration 2 (Dirichlet rotation 0 -> 120
+    degrees over 60 time steps, 10 PD iterations per step, point-triangle
+    self-contact re-detected on the device at every inner iteration) in the
+    split-TF32 form, with 1 and 5 inner iterations: PD iterations per second
+    over the run and the most springs active at any step."""
+    s = sol._scene
+    out = {}
+    rest = (s.X.copy(), np.zeros_like(s.X))
+    sol.set_precision(pd.FP32_IR)
+    for inner in (1, 5):
+        sol.set_state(*rest)
+        sol.set_inner_iters(inner)
+        set_detector(sol, s)
+        most = 0
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for step in range(61):
+            sol.set_dirichlet(s.dirichlet_positions(step))
+            sol.step(10)
+            most = max(most, active_springs(sol))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[f"inner{inner}"] = {"pd_iterations": 610, "ms_total": ms, "value": 610e3 / ms, "unit": UNIT,
+                                "max_active_springs": most}
+    sol.set_inner_iters(1)
+    return out
+
+
+def lips_rows(pd, stream, torch, full):
+    """Configuration 4: the two-slab lips scene at 2.5 / 5 / 10% collision-prone
+    nodes (m = 3,125 / 6,250 / 12,500), FP64 and split-TF32 forms, about 500
+    penalty springs on the facing proxies."""
     import scenes
-    out = {"elbow": {}, "lips": {}}
-    state = sol.get_state()
-    g = np.random.Generator(np.random.PCG64(5)).normal(size=(sol.m, 3)) * 1e3
-    for name, prec in (("fp64", pd.FP64), ("fp32_ir", pd.FP32_IR)):
-        sol.set_precision(prec)
-        row = {"schur_refactor_solve": schur_stats(sol, g, 50 if prec != pd.FP64 else 20)}
-        for inner in (1, 3, 5):
-            sol.set_state(*state)
-            sol.set_inner_iters(inner)
-            row[f"inner{inner}"] = step_rate(sol, stream, torch, 3)
-        sol.set_inner_iters(1)
-        out["elbow"][name] = row
-    sol.set_precision(pd.FP64)
-    sol.set_state(*state)
+    rows = {}
     for m in (3125, 6250, 12500):
         s = scenes.slabs(m=m)
         t0 = time.perf_counter()
@@ -302,22 +356,43 @@ def sweep(pd, sol, stream, torch, args):
                "setup_s": setup_s}
         for name, prec in (("fp64", pd.FP64), ("fp32_ir", pd.FP32_IR)):
             ls.set_precision(prec)
-            r = step_rate(ls, stream, torch, 3)
-            r["schur_refactor_solve"] = schur_stats(ls, gl, 10 if prec == pd.FP64 else 30)
+            r = step_rate(ls, stream, torch, 2 if prec == pd.FP64 else 3)
+            r["schur_refactor_solve"] = schur_stats(ls, gl, (10 if full else 3) if prec == pd.FP64 else (30 if full else 10))
             row[name] = r
         ls.close()
-        out["lips"][f"m{m}"] = row
+        rows[f"m{m}"] = row
+    return rows
+
+
+def sweep(pd, sol, stream, torch, args):
+    """inner = 3 and 5 on the elbow and the Schur refactor+solve median / p90
+    over repeated solves."""
+    out = {}
+    state = sol.get_state()
+    g = np.random.Generator(np.random.PCG64(5)).normal(size=(sol.m, 3)) * 1e3
+    for name, prec in (("fp64", pd.FP64), ("fp32_ir", pd.FP32_IR)):
+        sol.set_precision(prec)
+        row = {"schur_refactor_solve": schur_stats(sol, g, 50 if prec != pd.FP64 else 20)}
+        for inner in (1, 3, 5):
+            sol.set_state(*state)
+            sol.set_inner_iters(inner)
+            row[f"inner{inner}"] = step_rate(sol, stream, torch, 3)
+        sol.set_inner_iters(1)
+        out[name] = row
+    sol.set_precision(pd.FP64)
+    sol.set_state(*state)
     return out
 
 
 def time_learned(pd, sol, stream, args, fp64_ms, torch, state):
-    """The learned warm start on this scene: record region solves along seeded
-    random indenter paths (split-TF32 form), train the network on the device,
-    then time the PCG form started from the network's prediction and report
-    PCG iterations by starting point.  A bounded sample of the 20K-solve
-    training run (see the training recipe in the package's warmstart module)."""
+    """The learned warm start: record region solves along seeded random
+    indenter paths (a rigid sphere pressed into the crease surface, detected
+    on the device; split-TF32 form), train the network on the device, then
+    run the PCG form along a held-out indenter path from each starting point
+    (zero, the previous solution, z0 = the contact-free response, the
+    network) and report PCG iterations and device ms per step by start.  A
+    bounded sample of the 20K-solve training run of the warmstart module."""
     from paper_2008_01541_b300 import warmstart as ws
-    import scenes
     s = sol._scene
     t0 = time.perf_counter()
     sol.set_precision(pd.FP32_IR)
@@ -337,90 +412,177 @@ def time_learned(pd, sol, stream, args, fp64_ms, torch, state):
     mse_net, mse_zero = sol.mlp_eval()
     sol.mlp_record(0)
     sol.set_precision(pd.PCG_WARM)
-    iters = {}
-    for name, src in (("zero", 0), ("z0", 3), ("network", 2)):
+    iters, ms = {}, {}
+    for name, src in (("zero", 0), ("previous", 1), ("z0", 3), ("network", 2)):
         sol.set_state(*state)
         sol.set_warm_start(src)
-        iters[name] = float(np.mean(ws.run_path(sol, s, held, radius)))
-    sol.set_state(*state)
-    sol.set_warm_start(2)
-    c = s.contacts(CONTACT_STEP, s.X)
-    sol.set_contacts(c.nodes, c.w, c.target, c.stiffness)
-    for _ in range(3):
-        sol.step(1)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    schur = it = res = fs = 0.0
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(args.steps):
-        sol.step(1)
-        st = sol.stats()
-        schur += st["ms_contact_update"] + st["ms_factor_solve"]
-        fs += st["ms_factor_solve"]
-        it += st["refine_iters"]
-        res = max(res, st["residual"])
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    return {"pcg_learned (network warm start)": {
-        "ms_per_step": ms, "value": 1e3 / ms, "unit": UNIT, "speedup_vs_fp64": fp64_ms / ms,
-        "schur_refactor_solve_ms": schur / args.steps, "refine_iters": it / args.steps, "max_rel_residual": res,
-        "roofline": form_roofline(pd, pd.PCG_WARM, s.m, s.m, 0.0, fs / args.steps, it / args.steps),
-        "train_solves": args.train_solves, "train_steps": args.train_steps, "train_loss": loss,
-        "generate_s": gen_s, "train_s": train_s,
-        "heldout_err_vs_z0_start": mse_net / mse_zero if mse_zero > 0 else None,
-        "heldout_pcg_iters_by_start": iters}}
+        ws.run_path(sol, s, held[:2], radius)          # warm-up along the first two centres
+        sol.set_state(*state)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        its = ws.run_path(sol, s, held, radius)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        iters[name] = float(np.mean(its))
+        ms[name] = e0.elapsed_time(e1) / len(held)
+    r = {"ms_per_step": ms["network"], "value": 1e3 / ms["network"], "unit": UNIT,
+         "speedup_vs_fp64": fp64_ms / ms["network"],
+         "what": "PCG from the network's start along a held-out indenter path (sphere springs detected on the "
+                 "device), %d steps of 1 outer x 1 inner iteration" % len(held),
+         "heldout_pcg_iters_by_start": iters, "heldout_ms_per_step_by_start": ms,
+         "train_solves": args.train_solves, "train_steps": args.train_steps, "train_loss": loss,
+         "generate_s": gen_s, "train_s": train_s,
+         "heldout_err_vs_z0_start": mse_net / mse_zero if mse_zero > 0 else None}
+    sol.set_warm_start(0)
+    return {"pcg_learned (network warm start)": r}
 
 
-def cpu_baseline(scene, x_state):
-    """The FP64 oracle as it stands on this host: one outer x one inner
-    iteration of the same scene (a bounded sample of the workload)."""
+def frozen_contacts(sol, s):
+    """The springs the device detector found in the current state, as host
+    arrays in node ids (empty slots dropped)."""
+    import scenes
+    nodes, w, t, c = sol.contacts()
+    act = c > 0
+    return scenes.Contacts(nodes[act], w[act], t[act], c[act])
+
+
+def _host_baseline_worker(path):
+    """Child process of cpu_baseline (its BLAS / OpenMP threads fixed by the
+    environment): times the oracle iteration and the LAPACK dense solve on
+    the inputs saved at `path` and prints one JSON line."""
     import oracle
-    o = oracle.OracleSolver(scene.X, scene.tets, scene.dirichlet, scene.region, scene.mu)
-    o.x = x_state.copy()
+    import scenes
+    import scipy.linalg as sla
+    d = np.load(path)
+    s = scenes.elbow(h=float(d["h"]))
+    con = scenes.Contacts(d["nodes"], d["w"], d["target"], d["stiffness"])
+    o = oracle.OracleSolver(s.X, s.tets, s.dirichlet, s.region, s.mu)
+    o.x = d["x"].copy()
     t = time.perf_counter()
-    o.step(1, 1, lambda x: scene.contacts(CONTACT_STEP, scene.X), scene.dirichlet_positions(scene.info["rest_step"]))
-    el = time.perf_counter() - t
-    return {"value": 1.0 / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "1 time step x 1 outer x 1 inner iteration of the same elbow scene "
-                      "(full free-node sparse LU solve, scipy SuperLU, single-threaded)",
-            "seconds": el}
+    o.step(1, 1, lambda x: con, d["dpos"])
+    t_oracle = time.perf_counter() - t
+    # LAPACK dense Cholesky + 3-RHS solve of H = Sigma_0 + C_22 (region rows)
+    m = s.m
+    ridx = np.full(s.n, -1, np.int64)
+    ridx[s.region] = np.arange(m)
+    H = d["sigma"].copy()
+    for j in range(con.k):
+        for a in range(con.nodes.shape[1]):
+            na = con.nodes[j, a]
+            if na < 0:
+                continue
+            for b in range(con.nodes.shape[1]):
+                nb = con.nodes[j, b]
+                if nb >= 0:
+                    H[ridx[na], ridx[nb]] += con.stiffness[j] * con.w[j, a] * con.w[j, b]
+    g = np.random.Generator(np.random.PCG64(7)).normal(size=(m, 3))
+    t = time.perf_counter()
+    cl = sla.cho_factor(H, lower=True, check_finite=False)
+    u = sla.cho_solve(cl, g, check_finite=False)
+    t_dense = time.perf_counter() - t
+    print(json.dumps({"oracle_s": t_oracle, "dense_s": t_dense,
+                      "dense_rel_residual": float(np.linalg.norm(g - H @ u) / np.linalg.norm(g))}), flush=True)
+
+
+def cpu_baseline(scene, x_state, dpos, con, sigma):
+    """Host baselines on this machine's cores, each in a child process with
+    its BLAS / OpenMP threads fixed by the environment (1 and all cores).  The
+    FP64 oracle as it stands: one outer x one inner iteration of the same
+    scene and state (its global step a full free-node sparse LU, scipy
+    SuperLU), with the springs frozen at those the device detected there.
+    And the dense half of the metric: LAPACK FP64 Cholesky + solve (scipy)
+    of the same H = Sigma_0 + C_22 at the same m."""
+    info = host_info()
+    out = dict(info)
+    fd, path = tempfile.mkstemp(suffix=".npz")
+    os.close(fd)
+    np.savez(path, h=scene.info["h"], x=x_state, dpos=dpos, nodes=con.nodes, w=con.w, target=con.target,
+             stiffness=con.stiffness, sigma=sigma)
+    res = {}
+    try:
+        for cores in (1, info["nproc"]):
+            env = dict(os.environ)
+            for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+                env[v] = str(cores)
+            r = subprocess.run([sys.executable, os.path.abspath(__file__), "--host-baseline-worker", path],
+                               env=env, capture_output=True, text=True, timeout=600)
+            if r.returncode != 0:
+                return {"error": r.stderr[-400:], **info}
+            res[cores] = json.loads(r.stdout.strip().splitlines()[-1])
+    finally:
+        os.unlink(path)
+    a, one = res[info["nproc"]], res[1]
+    out.update({"value": 1.0 / a["oracle_s"], "unit": UNIT, "cores": info["nproc"], "kind": "oracle",
+                "value_1core": 1.0 / one["oracle_s"],
+                "sample": "1 outer x 1 inner iteration of the same elbow state (full free-node sparse LU, scipy "
+                          "SuperLU, whose sparse solve is single-threaded; BLAS and OpenMP on the given threads), "
+                          "springs frozen at the %d the device detected; seconds %.1f (all cores) / %.1f (1 core)"
+                          % (con.k, a["oracle_s"], one["oracle_s"])})
+    out["lapack_schur_refactor_solve"] = {"ms_1core": 1e3 * one["dense_s"], "ms_all_cores": 1e3 * a["dense_s"],
+                                          "m": scene.m, "rel_residual": a["dense_rel_residual"],
+                                          "what": "FP64 LAPACK Cholesky (potrf) + 3-RHS solve of H = Sigma_0 + C_22"}
+    return out
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands on the host cores, on
+    the same workload, metric and unit; each timed step is one oracle PD
+    iteration, and the number of timed steps is bounded so the run ends
+    within a few minutes (the line reports how many were timed)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     import scenes
-    s = scenes.elbow(h=args.h)
     import oracle
+    from oracle import detect
+    s = scenes.elbow(h=args.h)
     o = oracle.OracleSolver(s.X, s.tets, s.dirichlet, s.region, s.mu)
-    con = s.contacts(CONTACT_STEP, s.X)
-    dpos = s.dirichlet_positions(s.info["rest_step"])
+    x0, fstep = scenes.closed_pose(s, CLOSE_ANGLE)
+    dpos = s.dirichlet_positions(fstep)
+    pa, ta, pb, tb = s.info["tri_sides"]
+    gap, rmin = s.info["tri_gap"], s.info["tri_rest_min"]
+
+    def detect_fn(x):   # the oracle's own point-triangle detection, every inner iteration
+        A = detect.point_triangle_springs(pa, tb, x, s.X, gap, rmin, s.stiffness)
+        B = detect.point_triangle_springs(pb, ta, x, s.X, gap, rmin, s.stiffness)
+        return scenes.Contacts(*(np.concatenate([A[i], B[i]]) for i in range(4)))
+
+    o.x = x0.copy()
 
     def one():
-        o.step(1, 1, lambda x: con, dpos)
+        o.step(1, 1, detect_fn, dpos)
 
-    for _ in range(args.warmup):
-        one()
+    budget_s = 150.0
     t = time.perf_counter()
-    for _ in range(args.steps):
+    one()                               # one untimed warm-up iteration (bounded: W is capped at 1)
+    first = time.perf_counter() - t
+    n = int(max(1, min(args.steps, budget_s // max(first, 1e-3))))
+    t = time.perf_counter()
+    for _ in range(n):
         one()
     el = time.perf_counter() - t
-    v = args.steps / el
+    v = n / el
+    info = host_info()
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "steps": n, "warmup": 1, "ms_per_step": 1e3 * el / n,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": workload_name(s, "oracle full-system FP64")},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "each step = 1 outer x 1 inner iteration of the full elbow scene"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": info["nproc"], "kind": "oracle",
+                             "cpu_model": info["cpu_model"],
+                             "sample": "each step = 1 outer x 1 inner oracle iteration of the full elbow scene with "
+                                       "its own point-triangle detection; %d of the %d requested steps timed and 1 "
+                                       "warm-up, to stay within a few minutes" % (n, args.steps)},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
 def main():
+    if len(sys.argv) == 3 and sys.argv[1] == "--host-baseline-worker":
+        _host_baseline_worker(sys.argv[2])
+        return 0
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
@@ -444,13 +606,13 @@ def main():
                     inner_iters=1, stream=stream.cuda_stream, timing=True, max_refine=500)
     setup_s = time.perf_counter() - t_setup
     sol._scene = s
-    rest = s.info["rest_step"]
-    con = s.contacts(CONTACT_STEP, s.X)
-    sol.set_dirichlet(s.dirichlet_positions(rest))
+    x0, fstep = scenes.closed_pose(s, CLOSE_ANGLE)
+    dpos = s.dirichlet_positions(fstep)
+    sol.set_state(x0, np.zeros_like(x0))
+    sol.set_dirichlet(dpos)
     if args.nested:
         sol.set_contact_nodes(s.proxies)
-    sol.set_contacts(con.nodes, con.w, con.target, con.stiffness)
-    sol._contacts = con
+    set_detector(sol, s)
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()          # started before warm-up: NVML start-up must not fall in the timed region
     time.sleep(1.0)
@@ -469,10 +631,12 @@ def main():
                           "kernel_launches": sol.stats()["kernel_launches"]}), flush=True)
         sol.close()
         return 0
+    state = sol.get_state()
     phase_keys = ["ms_local_alpha", "ms_forward", "ms_contact_update", "ms_local_beta", "ms_factor_solve",
                   "ms_bookkeeping", "ms_backward", "ms_refactor"]
     phases = {k: 0.0 for k in phase_keys}
     launches = 0
+    springs = []
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -492,26 +656,27 @@ def main():
     if dist:
         dist.barrier()
     st = sol.stats()
+    springs_end = active_springs(sol)
 
-    # ---- end to end through the C ABI with host buffers
-    dpos_seq = [np.ascontiguousarray(s.dirichlet_positions(rest + (i % 2))) for i in range(2)]
-    con_seq = [s.contacts(CONTACT_STEP - (i % 2), s.X) for i in range(2)]
+    # ---- end to end through the C ABI with host buffers: the step's Dirichlet
+    # positions go up, the positions come back (contacts are detected on the device)
+    sol.set_state(*state)
+    dpos_seq = [np.ascontiguousarray(s.dirichlet_positions(fstep - (i % 2))) for i in range(2)]
     xbuf = np.empty((s.n, 3))
-    h2d = dpos_seq[0].nbytes + sum(a.nbytes for a in (con_seq[0].nodes, con_seq[0].w, con_seq[0].target,
-                                                      con_seq[0].stiffness))
+    h2d = dpos_seq[0].nbytes
     d2h = xbuf.nbytes
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for i in range(args.steps):
-        c = con_seq[i % 2]
         sol.set_dirichlet(dpos_seq[i % 2])
-        sol.set_contacts(c.nodes, c.w, c.target, c.stiffness)
         sol.step(1)
         xbuf[:] = sol.positions()
     torch.cuda.synchronize()
     e2e_ms, e2e = aggregate_replicas(1e3 * (time.perf_counter() - t0), args.steps, world, dist, "cuda")
+    sol.set_state(*state)
+    sol.set_dirichlet(dpos)
 
     # ---- roofline of the dominant kernel group: the dense refactor + solve (a5)
     m = s.m
@@ -527,18 +692,21 @@ def main():
         roof = {"kernel": "a5 FP64 dense refactor+solve (k_chol_diag/trsm/colupd/update/inv + k_trsv_tasks)"
                           + (", nested: trailing contact-node block" if args.nested else ""),
                 "bound": "alu", "achieved": ach, "peak": PEAK_FP64_ALU / 1e12, "unit": "TFLOP/s",
-                "frac": ach / (PEAK_FP64_ALU / 1e12), "traffic": None,
+                "frac": ach / (PEAK_FP64_ALU / 1e12),
+                "traffic": None if args.nested else FP64_A5_DRAM_BYTES,
+                "algorithmic_flop": flops_a5,
                 "peak_source": "FP64 DFMA: 148 SMs x 2 FMA/clk x 2 flop x 2032 MHz (derived; "
                                "microbenchmark reached 0.95-0.99 TFLOP/s)"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(s, args.precision + (" nested-Schur" if args.nested else "")), "tets": s.E, "nodes": s.n, "m": s.m,
+        "config": {"workload": workload_name(s, args.precision + (" nested-Schur" if args.nested else "")),
+                   "tets": s.E, "nodes": s.n, "m": s.m,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (interior factor %.0f MB, Sigma %.0f MB)" % (
                        8e-6 * st["nnz_L"], 8e-6 * m * m),
-                   "contacts": int(st["contacts"])},
+                   "spring_slots": int(st["contacts"]), "active_springs_end": springs_end},
         "schur_refactor_solve_ms": (phases["ms_contact_update"] + phases["ms_factor_solve"]) / args.steps,
         "phases_ms": {k[3:]: v / args.steps for k, v in phases.items()},
         "roofline": roof,
@@ -549,11 +717,22 @@ def main():
     }
     if not args.no_forms and not args.nested:
         line["forms"] = time_forms(pd, sol, stream, args, ms / args.steps, torch)
+    if not args.no_extra and not args.nested:
+        sol.set_state(*state)
+        line["trajectory_split_tf32"] = trajectory(pd, sol, stream, torch)
+        sol.set_precision(prec)
+        line["lips_config4"] = lips_rows(pd, stream, torch, args.sweep)
     if args.sweep:
+        sol.set_state(*state)
+        set_detector(sol, s)
         line["sweep"] = sweep(pd, sol, stream, torch, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        x_now = sol.positions()
-        line["cpu_baseline"] = cpu_baseline(s, x_now)
+        sol.set_state(*state)
+        sol.set_dirichlet(dpos)
+        set_detector(sol, s)
+        sol.detect()
+        con = frozen_contacts(sol, s)
+        line["cpu_baseline"] = cpu_baseline(s, state[0], dpos, con, sol.schur())
     sol.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

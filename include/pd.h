@@ -352,7 +352,9 @@ pd_status pd_tc_rank_k(int mode, const float* A, const float* B, float* C, int64
 
 /* Starting point of PD_PCG_WARM solves inside pd_step: 0 = zero, 1 = the
  * previous region solution, 2 = the network's prediction z0 + s N (needs
- * parameters), 3 = z0 alone (the contact-free response, no network). */
+ * parameters), 3 = z0 alone (the contact-free response, no network).  A
+ * start whose residual ||g - H u0|| is not smaller than ||g|| is replaced by
+ * zero (so a poor prediction never costs more than the cold start). */
 pd_status pd_set_warm_start(pd_solver* s, int source);
 
 /* Set / read the network parameters (n must be PD_MLP_NPARAMS); setting them

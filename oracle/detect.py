@@ -161,16 +161,27 @@ def point_triangle_springs(prox_a, tris_b, x, X, gap, rest_min, stiffness):
     stiffness, active positions in prox_a, chosen triangle per active node)."""
     rows, idx, which = [], [], []
     rm2 = rest_min * rest_min
+    # A triangle whose bounding sphere is farther than gap from the node
+    # cannot be active; skipping it (with a relative margin for rounding)
+    # leaves the choice unchanged: the nearest candidate is only used if it
+    # is nearer than gap.
+    tb = np.asarray(tris_b, dtype=np.int64).reshape(-1, 3)
+    V = np.asarray(x, dtype=np.float64)[tb]                      # [nt, 3, 3]
+    cen = V.mean(axis=1)
+    rad = np.sqrt(((V - cen[:, None, :]) ** 2).sum(-1)).max(axis=1)
     for j, a in enumerate(prox_a):
         p, P = _pt(x, a), _pt(X, a)
         best, bi, bw, bq = 1e300, -1, None, None
-        for q, (i0, i1, i2) in enumerate(tris_b):
+        dc = np.sqrt(((cen - np.asarray(p)) ** 2).sum(-1))
+        near = np.nonzero(dc <= (rad + gap) * (1.0 + 1e-9) + 1e-12)[0]
+        for q in near:
+            i0, i1, i2 = (int(v) for v in tb[q])
             d2r, _, _ = closest_point_on_triangle(P, _pt(X, i0), _pt(X, i1), _pt(X, i2))
             if d2r < rm2:
                 continue
             d2, wts, qp = closest_point_on_triangle(p, _pt(x, i0), _pt(x, i1), _pt(x, i2))
             if d2 < best:
-                best, bi, bw, bq = d2, q, wts, qp
+                best, bi, bw, bq = d2, int(q), wts, qp
         if bi < 0 or not (math.sqrt(best) < gap):
             continue
         i0, i1, i2 = (int(v) for v in tris_b[bi])

@@ -37,7 +37,8 @@ struct Args {
   int kb = 0;                            // first tile column factored (earlier panels are final and unused)
   int* sync = nullptr;                   // sync_bytes(T) of scratch (zeroed by factor())
   int max_ctas = 0;                      // cap on the persistent grid (0: two thirds of the SMs)
-  int* status = nullptr;                 // [0] first non-positive pivot + 1, [1] wait failure code
+  int* status = nullptr;                 // [1] receives a wait failure code
+  int* piv = nullptr;                    // [0] first non-positive pivot + 1 (replaced by 1 in the factor)
 };
 
 inline size_t sync_bytes(int T) { return sizeof(int) * (2 + 2 * (size_t)T); }

@@ -60,6 +60,7 @@ struct Ptrs {
   int T, kb;
   int* sync;
   int* status;
+  int* piv;
 };
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
@@ -384,7 +385,7 @@ __global__ void __launch_bounds__(256, 1)
     if (diag) {
       // ---- L_jj (the panels of column j wait for it), then Dinv_j (their Lh
       // products wait for it), then E_j for the preconditioner
-      pdm::diag_factor_f4(A, j, P.status);
+      pdm::diag_factor_f4(A, j, P.piv);
       for (int q = tid; q < NB * NB; q += 256) {
         const int r = q / NB, c = q % NB;
         if (c <= r) Lt[(int64_t)r * mq + c] = A[r * SP + c];
@@ -516,12 +517,12 @@ cudaError_t launch(const Args& a, Ptrs p, int ntask, cudaStream_t st) {
 cudaError_t factor(pdtc::Mode mode, const Args& a, cudaStream_t st) {
   const int nt = a.T - a.kb;
   if (nt <= 0) return cudaSuccess;
-  if (!a.map_hi || !a.L || !a.Lh || !a.Dinv || !a.E || !a.sync || !a.status ||
+  if (!a.map_hi || !a.L || !a.Lh || !a.Dinv || !a.E || !a.sync || !a.status || !a.piv ||
       (mode == pdtc::TF32X3 && (!a.Llo || !a.map_lo)) || (mode == pdtc::BF16 && !a.Lb))
     return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(a.sync, 0, sync_bytes(a.T), st);
   if (e != cudaSuccess) return e;
-  const Ptrs p{0, a.L, a.Llo, a.Lb, a.Lh, a.Dinv, a.E, a.mq, a.T, a.kb, a.sync, a.status};
+  const Ptrs p{0, a.L, a.Llo, a.Lb, a.Lh, a.Dinv, a.E, a.mq, a.T, a.kb, a.sync, a.status, a.piv};
   const int ntask = nt * (nt - 1) / 2;   // panel tasks
   switch (mode) {
     case pdtc::TF32X3: return launch<1>(a, p, ntask, st);

@@ -13,6 +13,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <cmath>
 #include <cstdlib>
 #include <string>
@@ -65,6 +66,11 @@ struct MixedState {
   float *facc = nullptr, *bacc = nullptr;   // [mq][3] accumulated block products (forward / backward)
   int pc_grid = 0;            // persistent grid of the preconditioner
   int* llsync = nullptr;      // counters of the persistent left-looking factorisation
+  // first non-positive pivot + 1 of the low-precision factor (the pivot is
+  // replaced by 1: H is SPD, the FP32 factor of an ill-conditioned D H D can
+  // still lose a pivot; the refinement against H then decides)
+  int* lpiv = nullptr;
+  int* lpiv_h = nullptr;      // pinned copy
   bool lookahead = false;     // PD_LOWP_SCHEDULE=lookahead: one launch per tile step instead
   int ll_ctas = 0;            // PD_LOWP_CTAS: cap on the persistent factorisation's grid (0: two thirds of the SMs)
   cudaStream_t side = nullptr;              // low-priority stream for the bulk trailing updates
@@ -950,7 +956,7 @@ static pd_status ensure_state(pd_solver* s) {
     M->facc = reinterpret_cast<float*>(reinterpret_cast<char*>(M->pcnt) + cb);
     M->bacc = M->facc + 3 * mq;
   }
-  if (A((void**)&M->llsync, pdll::sync_bytes((int)M->T))) {
+  if (A((void**)&M->llsync, pdll::sync_bytes((int)M->T)) || A((void**)&M->lpiv, sizeof(int))) {
     s->err = "device allocation for the factorisation counters failed";
     return PD_ERR_OOM;
   }
@@ -961,6 +967,8 @@ static pd_status ensure_state(pd_solver* s) {
     M->ll_ctas = ctas ? std::max(0, std::atoi(ctas)) : 0;
   }
   if (cudaMallocHost(&M->sc_h, sizeof(double) * 8) != cudaSuccess) return PD_ERR_OOM;
+  if (cudaMallocHost(&M->lpiv_h, sizeof(int)) != cudaSuccess) return PD_ERR_OOM;
+  cudaMemsetAsync(M->lpiv, 0, sizeof(int), s->stream);
   // vectors beyond m stay zero: the padded products need no bounds checks
   cudaMemsetAsync(M->vhi, 0, sizeof(float) * 3 * M->ldm, s->stream);
   cudaMemsetAsync(M->vlo, 0, sizeof(float) * 3 * M->ldm, s->stream);
@@ -1017,7 +1025,7 @@ static void factor_panels(pd_solver* s, Factor& f, pdtc::Mode mode, int k_begin 
   // panel kt to the rest of the trailing matrix meanwhile.
   cudaStream_t sb = M->side;
   for (int kt = k_begin; kt < k_end; ++kt) {
-    k_diag_f32<<<1, 256, (NB * PADW + 4 * 32 * 33) * 4, st>>>(f.L, mq, kt, f.Dinv, s->status);
+    k_diag_f32<<<1, 256, (NB * PADW + 4 * 32 * 33) * 4, st>>>(f.L, mq, kt, f.Dinv, M->lpiv);
     ++pdk::g_launches;
     const int n = (int)(T - kt - 1);
     if (n <= 0) break;
@@ -1073,7 +1081,8 @@ static pd_status factor_ll(pd_solver* s, Factor& f, pdtc::Mode mode, int k_begin
   a.map_hi = mode == pdtc::BF16 ? &f.mapLb : &f.mapL;
   a.map_lo = mode == pdtc::TF32X3 ? &f.mapLo : nullptr;
   a.L = f.L; a.Llo = f.Llo; a.Lb = f.Lb; a.Lh = f.Lh; a.Dinv = f.Dinv; a.E = f.E;
-  a.mq = mq; a.T = (int)M->T; a.kb = k_begin; a.sync = M->llsync; a.status = s->status; a.max_ctas = M->ll_ctas;
+  a.mq = mq; a.T = (int)M->T; a.kb = k_begin; a.sync = M->llsync; a.status = s->status; a.piv = M->lpiv;
+  a.max_ctas = M->ll_ctas;
   cudaError_t e = pdll::factor(mode, a, s->stream);
   if (e != cudaSuccess) { s->err = std::string("factorisation launch: ") + cudaGetErrorString(e); return PD_ERR_CUDA; }
   f.valid = true;
@@ -1200,6 +1209,7 @@ pd_status mixed_factor(pd_solver* s) {
   MixedState* M = s->mixed;
   if (s->precision == PD_PCG_WARM) return build_minv(s);
   const pdtc::Mode mode = form_mode(s);
+  cudaMemsetAsync(M->lpiv, 0, sizeof(int), s->stream);
   if (s->nested) {
     if (!M->nested_ready || M->nested_mode != (int)mode) {
       rs = nested_setup(s, mode);
@@ -1262,12 +1272,23 @@ pd_status mixed_iterate(pd_solver* s, const double* g, const double* u0, double*
   k_sub<<<nblk(n3, 256), 256, 0, st>>>(g, M->q, M->r, n3); ++pdk::g_launches;
   dot(s, g, g, 4);
   dot(s, M->r, M->r, 0);
-  const double gg = read_slot(s, 4);
+  cudaMemcpyAsync(M->lpiv_h, M->lpiv, sizeof(int), cudaMemcpyDeviceToHost, st);
+  const double gg = read_slot(s, 4);   // (synchronises: lpiv_h is current)
+  const int lost_pivot = warm ? 0 : *M->lpiv_h;
   const double tol2 = s->opt.tol * s->opt.tol * (gg > 0 ? gg : 1.0);
   double rr = read_slot(s, 0);
+  if (u0 && !(rr <= gg)) {   // a supplied start worse than zero (or not finite): start from zero
+    cudaMemsetAsync(u, 0, sizeof(double) * n3, st);
+    cudaMemcpyAsync(M->r, g, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st);
+    rr = gg;
+    ++s->starts_rejected;
+  }
   int it = 0;
   bool ok = rr <= tol2;
-  const bool use_cg = warm || mode != pdtc::TF32X3;
+  // classic refinement for the split-TF32 factor; factor-preconditioned CG
+  // for TF32 / BF16, and for any factor that lost a pivot (CG absorbs the few
+  // outlier directions a replaced pivot leaves, plain refinement stalls on them)
+  const bool use_cg = warm || mode != pdtc::TF32X3 || lost_pivot;
   cudaError_t ce = cudaSuccess;
   if (!ok && !use_cg) {
     // classic refinement: u += M^-1 r; r = g - H u (FP64 vectors; Sigma_0 u in
@@ -1349,15 +1370,22 @@ pd_status mixed_iterate(pd_solver* s, const double* g, const double* u0, double*
     int h[4] = {0, 0, 0, 0};
     cudaMemcpy(h, s->status, sizeof h, cudaMemcpyDeviceToHost);
     if (h[0]) {
-      s->err = "low-precision Cholesky pivot " + std::to_string(h[0] - 1) + " is not positive";
+      s->err = "collision-region matrix has a non-positive diagonal entry " + std::to_string(h[0] - 1);
+      return PD_ERR_NOT_SPD;
+    }
+    if (lost_pivot) {
+      s->err = "low-precision Cholesky pivot " + std::to_string(lost_pivot - 1) +
+               " was not positive and the refinement did not reach tol";
       return PD_ERR_NOT_SPD;
     }
     if (h[1]) {
       s->err = "a bounded device wait gave up (code " + std::to_string(h[1]) + ")";
       return PD_ERR_TIMEOUT;
     }
-    s->err = "refinement reached relative residual " + std::to_string(s->last_residual) + " after " +
-             std::to_string(it) + " iterations (tol " + std::to_string(s->opt.tol) + ")";
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "refinement reached relative residual %.3e after %d iterations (tol %.1e)",
+                  s->last_residual, it, s->opt.tol);
+    s->err = buf;
     return PD_ERR_NO_CONVERGENCE;
   }
   return PD_OK;
@@ -1403,6 +1431,7 @@ namespace pdm {
 void mixed_free(pd_solver* s) {
   if (!s->mixed) return;
   if (s->mixed->sc_h) cudaFreeHost(s->mixed->sc_h);
+  if (s->mixed->lpiv_h) cudaFreeHost(s->mixed->lpiv_h);
   for (auto e : s->mixed->ev_panel) cudaEventDestroy(e);
   for (auto e : s->mixed->ev_rest) cudaEventDestroy(e);
   if (s->mixed->side) cudaStreamDestroy(s->mixed->side);

@@ -90,6 +90,7 @@ struct pd_solver {
   double* u_last = nullptr;      // [m][3] solution of the previous region solve
   std::vector<double> X_rest_h;  // rest positions (host)
   int last_refine = 0;
+  int64_t starts_rejected = 0;   // PCG starts worse than zero, replaced by zero (counted)
   double last_residual = 0.0;
   // contacts (region indices)
   int64_t k = 0, kcap = 0;

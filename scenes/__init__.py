@@ -8,9 +8,9 @@ oracle and the CUDA library are fed from it.
 from .mesh import grid_mesh, voxel_mesh, boundary_nodes, boundary_faces_outward, node_adjacency
 from .configs import (Scene, Contacts, config1, elbow, slabs, small_elbow,
                       tiny_cube, sphere_contacts, cylinder_contacts,
-                      empty_contacts, rotation_z, pair_contacts)
+                      empty_contacts, rotation_z, pair_contacts, closed_pose)
 
 __all__ = ["grid_mesh", "voxel_mesh", "boundary_nodes", "boundary_faces_outward", "node_adjacency",
            "Scene", "Contacts", "config1", "elbow", "slabs", "small_elbow",
            "tiny_cube", "sphere_contacts", "cylinder_contacts",
-           "empty_contacts", "rotation_z", "pair_contacts"]
+           "empty_contacts", "rotation_z", "pair_contacts", "closed_pose"]

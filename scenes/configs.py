@@ -296,6 +296,23 @@ def elbow(h=0.585, seed=0, region_fraction=0.05, inner_iters=1, contact_mode="se
                        "tri_gap": h, "tri_rest_min": 3.0 * h})
 
 
+def closed_pose(scene, angle=40.0, band=8.0):
+    """Initial positions of an elbow with the joint closed by `angle` degrees
+    beyond the rest L (flexion step 45 + angle / 2): every node turned about
+    the hinge by angle * smoothstep across a band of half-width `band` around
+    the plane x + y = 0 between the two segments, so no element inverts and
+    the crease surfaces of the two segments meet.  Returns (x, flexion step)."""
+    X = scene.X
+    d = (X[:, 0] + X[:, 1]) / math.sqrt(2.0)
+    t = np.clip((d + band) / (2.0 * band), 0.0, 1.0)
+    ang = np.radians(angle) * t * t * (3.0 - 2.0 * t)
+    c, sn = np.cos(ang), np.sin(ang)
+    x = X.copy()
+    x[:, 0] = c * X[:, 0] - sn * X[:, 1]
+    x[:, 1] = sn * X[:, 0] + c * X[:, 1]
+    return x, int(round(45 + angle / 2.0))
+
+
 def small_elbow(h=2.0, seed=0, region_fraction=0.05, inner_iters=1):
     """The elbow at a coarse spacing, for parity runs the oracle finishes fast."""
     s = elbow(h=h, seed=seed, region_fraction=region_fraction, inner_iters=inner_iters)

@@ -133,20 +133,10 @@ def test_detector_errors_and_clear(pd):
 
 
 def _closed_elbow(h=1.5, frac=0.08, angle=40.0, band=8.0):
-    """Small elbow with the joint closed by `angle` about the hinge: every
-    node turned by angle * smoothstep over a band of half-width `band` across
-    the plane x + y = 0 that separates the two sides (no element inverts),
-    so that side-A nodes come within the gap of side-B triangles; the caps at
-    the matching flexion step."""
+    """Small elbow in the closed-joint pose (no element inverted; side-A
+    nodes within the gap of side-B triangles) and the matching caps."""
     s = scenes.small_elbow(h=h, region_fraction=frac)
-    d = (s.X[:, 0] + s.X[:, 1]) / np.sqrt(2.0)
-    t = np.clip((d + band) / (2.0 * band), 0.0, 1.0)
-    ang = np.radians(angle) * t * t * (3.0 - 2.0 * t)
-    c, sn = np.cos(ang), np.sin(ang)
-    x0 = s.X.copy()
-    x0[:, 0] = c * s.X[:, 0] - sn * s.X[:, 1]
-    x0[:, 1] = sn * s.X[:, 0] + c * s.X[:, 1]
-    step = int(round(45 + angle / 2.0))
+    x0, step = scenes.closed_pose(s, angle, band)
     return s, x0, s.dirichlet_positions(step)
 
 
