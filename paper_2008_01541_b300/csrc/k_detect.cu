@@ -146,6 +146,39 @@ __device__ double closest_on_triangle(V3 p, V3 a, V3 b, V3 c, double* w, V3* qou
   return best;
 }
 
+// FP32 distance from p to the triangle (a, b, c), for classifying a pair
+// before the exact FP64 test; negative if the triangle is too close to
+// degenerate for FP32 to be trusted (its smallest angle below ~2 degrees).
+__device__ __forceinline__ float dist_f32(float3 p, float3 a, float3 b, float3 c) {
+  const float3 e0 = make_float3(b.x - a.x, b.y - a.y, b.z - a.z), e1 = make_float3(c.x - a.x, c.y - a.y, c.z - a.z);
+  const float3 w = make_float3(p.x - a.x, p.y - a.y, p.z - a.z);
+  const float d00 = e0.x * e0.x + e0.y * e0.y + e0.z * e0.z, d11 = e1.x * e1.x + e1.y * e1.y + e1.z * e1.z;
+  const float d01 = e0.x * e1.x + e0.y * e1.y + e0.z * e1.z;
+  const float den = d00 * d11 - d01 * d01;
+  if (!(den > 1e-3f * d00 * d11)) return -1.f;
+  const float d20 = w.x * e0.x + w.y * e0.y + w.z * e0.z, d21 = w.x * e1.x + w.y * e1.y + w.z * e1.z;
+  float s = (d11 * d20 - d01 * d21) / den, t = (d00 * d21 - d01 * d20) / den;
+  float best;
+  if (s >= 0.f && t >= 0.f && s + t <= 1.f) {
+    const float qx = a.x + s * e0.x + t * e1.x, qy = a.y + s * e0.y + t * e1.y, qz = a.z + s * e0.z + t * e1.z;
+    best = (p.x - qx) * (p.x - qx) + (p.y - qy) * (p.y - qy) + (p.z - qz) * (p.z - qz);
+  } else {
+    best = 3.4e38f;
+    const float3 us[3] = {a, b, c};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float3 u = us[k], v = us[(k + 1) % 3];
+      const float ex = v.x - u.x, ey = v.y - u.y, ez = v.z - u.z;
+      const float ee = ex * ex + ey * ey + ez * ez;
+      float f = ((p.x - u.x) * ex + (p.y - u.y) * ey + (p.z - u.z) * ez) / ee;
+      f = fminf(fmaxf(f, 0.f), 1.f);
+      const float rx = p.x - (u.x + f * ex), ry = p.y - (u.y + f * ey), rz = p.z - (u.z + f * ez);
+      best = fminf(best, rx * rx + ry * ry + rz * rz);
+    }
+  }
+  return sqrtf(best);
+}
+
 // Bounding sphere of each triangle at the current positions, in FP32 and
 // enlarged so that it is never smaller than the exact one.
 __global__ void k_tri_bounds(int64_t nt, const int32_t* __restrict__ tri, const int32_t* __restrict__ region,
@@ -164,10 +197,14 @@ __global__ void k_tri_bounds(int64_t nt, const int32_t* __restrict__ tri, const 
 }
 
 // One warp per proxy: lanes scan the triangles q = lane, lane + 32, ... with a
-// conservative FP32 bounding-sphere test, take the exact FP64 closest point
-// for the survivors (rest-pose exclusion first), and the warp keeps the
-// smallest distance, the lowest triangle index on ties -- the same choice as
-// a scan of every triangle in index order.  Slot j of the spring arrays.
+// conservative FP32 bounding-sphere test, then classify the survivors with
+// FP32 closest points (rest-pose exclusion, then farther than gap) whenever
+// a wide margin settles the question, and take the exact FP64 closest point
+// for the rest; the warp keeps the smallest exact distance, the lowest
+// triangle index on ties.  A triangle skipped by the FP32 tests is either
+// excluded or farther than gap, so it can never be the active choice: the
+// result is the same as a scan of every triangle in index order with the
+// exact test.  Slot j of the spring arrays.
 __global__ void __launch_bounds__(256) k_detect_tris(
     int64_t np, const int32_t* __restrict__ prox, int64_t nt, const int32_t* __restrict__ tri,
     const float4* __restrict__ bnd, const int32_t* __restrict__ region, const double* __restrict__ x,
@@ -182,19 +219,33 @@ __global__ void __launch_bounds__(256) k_detect_tris(
   const double rm2 = __dmul_rn(rest_min, rest_min);
   double best = 1e300;
   int64_t bi = -1;
+  const float3 p32 = make_float3(px, py, pz), P32 = make_float3((float)P.x, (float)P.y, (float)P.z);
+  const float frm = (float)rest_min;
   for (int64_t q = lane; q < nt; q += 32) {
     const float4 b = __ldg(bnd + q);
     const float dx = px - b.x, dy = py - b.y, dz = pz - b.z;
     const float margin = 1e-4f * (fabsf(b.x) + fabsf(b.y) + fabsf(b.z) + b.w + fg) + 1e-6f;
     if (sqrtf(dx * dx + dy * dy + dz * dz) > b.w + fg + margin) continue;
     const int i0 = tri[3 * q], i1 = tri[3 * q + 1], i2 = tri[3 * q + 2];
+    const V3 R0 = ld3(xr + 3 * (int64_t)i0), R1 = ld3(xr + 3 * (int64_t)i1), R2 = ld3(xr + 3 * (int64_t)i2);
+    const V3 C0 = ld3(x + 3 * (int64_t)region[i0]), C1 = ld3(x + 3 * (int64_t)region[i1]),
+             C2 = ld3(x + 3 * (int64_t)region[i2]);
+    // FP32 classification with a margin (1% + 1e-3) far beyond its rounding;
+    // only the pairs it cannot settle take the exact FP64 test
+    const float dr32 = dist_f32(P32, make_float3((float)R0.x, (float)R0.y, (float)R0.z),
+                                make_float3((float)R1.x, (float)R1.y, (float)R1.z),
+                                make_float3((float)R2.x, (float)R2.y, (float)R2.z));
     double w[3];
     V3 qp;
-    const double d2r = closest_on_triangle(P, ld3(xr + 3 * (int64_t)i0), ld3(xr + 3 * (int64_t)i1),
-                                           ld3(xr + 3 * (int64_t)i2), w, &qp);
-    if (d2r < rm2) continue;
-    const double d2 = closest_on_triangle(p, ld3(x + 3 * (int64_t)region[i0]), ld3(x + 3 * (int64_t)region[i1]),
-                                          ld3(x + 3 * (int64_t)region[i2]), w, &qp);
+    if (dr32 >= 0.f && dr32 < 0.99f * frm - 1e-3f) continue;            // near at rest: excluded
+    if (!(dr32 >= 0.f && dr32 > 1.01f * frm + 1e-3f)) {                  // undecided: exact test
+      if (closest_on_triangle(P, R0, R1, R2, w, &qp) < rm2) continue;
+    }
+    const float d32 = dist_f32(p32, make_float3((float)C0.x, (float)C0.y, (float)C0.z),
+                               make_float3((float)C1.x, (float)C1.y, (float)C1.z),
+                               make_float3((float)C2.x, (float)C2.y, (float)C2.z));
+    if (d32 >= 0.f && d32 > 1.01f * fg + 1e-3f) continue;                // farther than gap: never the active choice
+    const double d2 = closest_on_triangle(p, C0, C1, C2, w, &qp);
     if (d2 < best) { best = d2; bi = q; }
   }
 #pragma unroll
