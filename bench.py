@@ -35,10 +35,11 @@ METRIC = "PD iters/sec at 600K tets, 5% contact DOFs; Schur refactor+solve ms at
 UNIT = "PD iters/s"
 CLOSE_ANGLE = 40.0         # the joint closed this many degrees past the rest L (flexion step 65)
 PEAK_FP64_ALU = 148 * 2 * 2 * 2032e6   # SMs x DFMA/clk/SM x flops/FMA x max SM clock
-# DRAM bytes per FP64 refactor + solve at m = 6,572, from the ncu capture in
-# profiles/fp64_refactor_dram_elbow598k.md (sum of dram__bytes_read.sum and
-# dram__bytes_write.sum over the kernels of one refactorisation and solve).
-FP64_A5_DRAM_BYTES = None
+# DRAM bytes of one FP64 refactor + solve at m = 6,572 (the dense group: every
+# k_chol_* kernel, k_trsv_tasks, k_copy_sigma, k_contact_scatter), from the
+# one-pass ncu capture summarised in profiles/fp64_step_elbow598k_launches.md
+# (dram__bytes_read.sum + dram__bytes_write.sum over the group's launches).
+FP64_A5_DRAM_BYTES = 9.26e9
 
 
 def parse():
