@@ -36,32 +36,41 @@ def init_params(seed):
     return pack(layers)
 
 
-def forward(params, X):
-    """Returns (prediction [B,3], list of activations)."""
+def _identity(x):
+    return x
+
+
+def forward(params, X, store=_identity):
+    """Returns (prediction [B,3], list of activations).  `store` is applied to
+    each hidden activation as it is kept for the next layer (the identity in
+    FP64; bf16_round for a network that stores its activations in BF16)."""
     layers = unpack(params)
     H = [np.asarray(X, dtype=np.float64)]
     Z = []
     for i, (W, b) in enumerate(layers):
         z = H[-1] @ W.T + b
         Z.append(z)
-        H.append(np.maximum(z, 0.0) if i < len(layers) - 1 else z)
+        H.append(store(np.maximum(z, 0.0)) if i < len(layers) - 1 else z)
     return H[-1], (H, Z)
 
 
-def loss_grad(params, X, T):
-    """Mean-squared error over all B*3 outputs and its gradient (logical layout)."""
+def loss_grad(params, X, T, store=_identity):
+    """Mean-squared error over all B*3 outputs and its gradient (logical
+    layout).  `store` is applied wherever an intermediate is kept for a later
+    product: the hidden activations and the back-propagated dL/dZ of every
+    layer (the identity gives the plain FP64 chain rule)."""
     layers = unpack(params)
-    pred, (H, Z) = forward(params, X)
+    pred, (H, Z) = forward(params, X, store)
     B = len(X)
     r = pred - T
     loss = float(np.sum(r * r) / (3 * B))
-    dZ = 2.0 * r / (3 * B)
+    dZ = store(2.0 * r / (3 * B))
     grads = [None] * len(layers)
     for i in range(len(layers) - 1, -1, -1):
         W, b = layers[i]
         grads[i] = (dZ.T @ H[i], dZ.sum(axis=0))
         if i > 0:
-            dZ = (dZ @ W) * (Z[i - 1] > 0)
+            dZ = store((dZ @ W) * (Z[i - 1] > 0))
     return loss, pack(grads)
 
 

@@ -33,3 +33,21 @@ def oracle_callback(scene, step):
     def fn(x):
         return scene.contacts(step, x)
     return fn
+
+
+def parity_errors(xg, xo, x0):
+    """(norm error, per-node error) of a GPU result xg against the oracle's
+    xo, both relative to the oracle's displacement from x0: the norm error is
+    ||xg - xo|| / ||xo - x0||, the per-node error max_i |xg_i - xo_i| /
+    max_i |xo_i - x0_i| over the nodes' position vectors."""
+    d = np.linalg.norm(xo - x0)
+    dn = np.linalg.norm(xo - x0, axis=1).max()
+    return (np.linalg.norm(xg - xo) / d if d > 0 else np.linalg.norm(xg - xo),
+            np.linalg.norm(xg - xo, axis=1).max() / dn if dn > 0 else np.linalg.norm(xg - xo, axis=1).max())
+
+
+def assert_parity(xg, xo, x0, tol, what=""):
+    """Both the norm and the per-node error of xg against xo within tol."""
+    e, en = parity_errors(xg, xo, x0)
+    assert e <= tol and en <= tol, (what, e, en)
+    return e, en

@@ -7,7 +7,7 @@ import pytest
 import oracle
 from oracle import detect
 import scenes
-from gpu_util import need_gpu, rng
+from gpu_util import need_gpu, rng, assert_parity
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-10
@@ -55,9 +55,8 @@ def test_sphere_detector_trajectory_matches_oracle(pd):
         active = max(active, fn(o.x).k)
     xg, vg = sol.get_state()
     assert active > 0
-    err = np.linalg.norm(xg - o.x) / np.linalg.norm(o.x - s.X)
-    assert err <= 1e-8, err
-    assert np.linalg.norm(vg - o.v) / np.linalg.norm(o.v) <= 1e-8
+    assert_parity(xg, o.x, s.X, 1e-8, "positions")
+    assert_parity(vg, o.v, np.zeros_like(o.v), 1e-8, "velocities")
     assert sol.stats()["contacts"] == len(s.proxies)
 
 
@@ -104,8 +103,7 @@ def test_pair_detector_matches_oracle(pd):
     o = oracle.OracleSolver(s.X, s.tets, s.dirichlet, s.region, s.mu)
     o.x = x0.copy()
     xo = o.step(2, 2, fn, s.dirichlet_positions(50))
-    err = np.linalg.norm(sol.positions() - xo) / np.linalg.norm(xo - x0)
-    assert err <= TOL, err
+    assert_parity(sol.positions(), xo, x0, TOL)
 
 
 def test_detector_errors_and_clear(pd):

@@ -28,6 +28,15 @@ def _round_weights(p):
     return out
 
 
+# Per-layer bound of the device gradients against the FP64 reference that
+# stores the same intermediates in BF16 (activations and dL/dZ, where the
+# device does): both round the same values, so they differ by FP32 against
+# FP64 accumulation (~256 x 2^-24 relative per product) and the rare BF16
+# rounding it flips (one BF16 spacing, 2^-8, on single entries).  A wrong
+# bias gradient or ReLU mask in any layer moves its block by O(1).
+GRAD_MAX_REL = 1e-3      # observed <= 3e-4 per block
+
+
 def test_gradients_match_the_fp64_oracle(pd):
     s = scenes.config1(nx=3, ny=3, nz=5)
     sol = pd.Solver(s.X, s.tets, s.region, s.dirichlet, s.mu)
@@ -39,14 +48,19 @@ def test_gradients_match_the_fp64_oracle(pd):
     sol.mlp_set_params(p.astype(np.float32))
     np.testing.assert_array_equal(sol.mlp_get_params(), p.astype(np.float32))
     loss_g, grad_g = sol.mlp_loss_grad(X.astype(np.float32), T.astype(np.float32))
-    loss_o, grad_o = mlp.loss_grad(_round_weights(p.astype(np.float32)), mlp.bf16_round(X), T.astype(np.float32))
-    assert abs(loss_g - loss_o) <= 2e-2 * loss_o
+    loss_o, grad_o = mlp.loss_grad(_round_weights(p.astype(np.float32)), mlp.bf16_round(X), T.astype(np.float32),
+                                   store=mlp.bf16_round)
+    assert abs(loss_g - loss_o) <= 1e-4 * loss_o
     q = 0
+    worst = []
     for n, k in mlp.SIZES:
         for size in (n * k, n):
             a, b = grad_g[q:q + size], grad_o[q:q + size]
-            assert np.linalg.norm(a - b) <= 5e-2 * np.linalg.norm(b) + 1e-12, (n, k, size)
+            rel = np.abs(a - b).max() / np.abs(b).max()
+            worst.append(((n, k, size), rel))
+            assert rel <= GRAD_MAX_REL, (n, k, size, rel)
             q += size
+    print("per-block max relative gradient error:", ["%s %.1e" % w for w in worst])
 
 
 def test_learned_start_cuts_pcg_iterations(pd):

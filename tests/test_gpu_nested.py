@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 import scenes
-from gpu_util import need_gpu, rng, contact_tuple, region_callback, oracle_callback
+from gpu_util import need_gpu, rng, contact_tuple, region_callback, oracle_callback, assert_parity
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-10
@@ -77,8 +77,7 @@ def test_nested_outer_iterations_match_oracle(pd):
     o = oracle.OracleSolver(s.X, s.tets, s.dirichlet, s.region, s.mu)
     o.x = x0.copy()
     xo = o.step(2, 2, oracle_callback(s, step), s.dirichlet_positions(step))
-    err = np.linalg.norm(sol.positions() - xo) / np.linalg.norm(xo - x0)
-    assert err <= TOL, err
+    assert_parity(sol.positions(), xo, x0, TOL)
 
 
 def test_nested_with_device_pair_detector(pd):
@@ -94,8 +93,7 @@ def test_nested_with_device_pair_detector(pd):
     o = oracle.OracleSolver(s.X, s.tets, s.dirichlet, s.region, s.mu)
     o.x = x0.copy()
     xo = o.step(2, 2, lambda x: s.info["self_pairs"](x, gap=6.0), s.dirichlet_positions(50))
-    err = np.linalg.norm(sol.positions() - xo) / np.linalg.norm(xo - x0)
-    assert err <= TOL, err
+    assert_parity(sol.positions(), xo, x0, TOL)
 
 
 def test_nested_rejects_springs_on_other_nodes(pd):
@@ -138,5 +136,4 @@ def test_nested_mixed_forms(pd, prec):
     o = oracle.OracleSolver(s.X, s.tets, s.dirichlet, s.region, s.mu)
     o.x = x0.copy()
     xo = o.step(1, 1, oracle_callback(s, step), s.dirichlet_positions(step))
-    err = np.linalg.norm(sol.positions() - xo) / np.linalg.norm(xo - x0)
-    assert err <= 1e-8, err
+    assert_parity(sol.positions(), xo, x0, 1e-8)

@@ -5,7 +5,7 @@ import scipy.sparse as sp
 
 import oracle
 import scenes
-from gpu_util import need_gpu, rng, contact_tuple, region_callback, oracle_callback
+from gpu_util import need_gpu, rng, contact_tuple, region_callback, oracle_callback, parity_errors, assert_parity
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-10      # relative tolerance of the FP64 form
@@ -115,8 +115,8 @@ def _compare_step(pd, s, step, outer, inner, x0, tol):
     o = oracle.OracleSolver(s.X, s.tets, s.dirichlet, s.region, s.mu, s.density, s.dt)
     o.x = x0.copy()
     xo = o.step(outer, inner, oracle_callback(s, step), s.dirichlet_positions(step))
-    disp = np.linalg.norm(xo - x0)
-    err = np.linalg.norm(xg - xo) / disp
+    err, err_node = parity_errors(xg, xo, x0)
+    assert err_node <= tol, ("per node", err_node)
     return err, sol
 
 
@@ -150,9 +150,8 @@ def test_full_time_steps_config1_trajectory(pd):
         sol.step(s.outer_iters, region_callback(s, st, xg_prev))
         o.step(s.outer_iters, 1, oracle_callback(s, st), s.dirichlet_positions(st))
     xg, vg = sol.get_state()
-    err = np.linalg.norm(xg - o.x) / np.linalg.norm(o.x - s.X)
-    assert err <= 1e-8, err
-    assert np.linalg.norm(vg - o.v) / np.linalg.norm(o.v) <= 1e-8
+    assert_parity(xg, o.x, s.X, 1e-8, "positions")
+    assert_parity(vg, o.v, np.zeros_like(o.v), 1e-8, "velocities")
 
 
 def test_errors_leave_the_handle_usable(pd):
@@ -225,5 +224,4 @@ def test_two_sided_springs_match_oracle(pd):
     o = oracle.OracleSolver(s.X, s.tets, s.dirichlet, s.region, s.mu)
     o.x = x0.copy()
     xo = o.step(1, 1, lambda x: s.info["self_pairs"](x, gap=6.0), s.dirichlet_positions(50))
-    err = np.linalg.norm(sol.positions() - xo) / np.linalg.norm(xo - x0)
-    assert err <= TOL, err
+    assert_parity(sol.positions(), xo, x0, TOL)

@@ -4,7 +4,7 @@ import pytest
 
 import oracle
 import scenes
-from gpu_util import need_gpu, rng, region_callback, oracle_callback
+from gpu_util import need_gpu, rng, region_callback, oracle_callback, assert_parity
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-10
@@ -73,8 +73,7 @@ def test_one_outer_iteration_matches_oracle(pd, inner):
     o = _oracle(s, mp, lo, hi)
     o.x = x0.copy()
     xo = o.step(1, inner, oracle_callback(s, 0), s.dirichlet_positions(0))
-    err = np.linalg.norm(sol.positions() - xo) / np.linalg.norm(xo - x0)
-    assert err <= TOL, err
+    assert_parity(sol.positions(), xo, x0, TOL)
 
 
 def test_trajectory_matches_oracle(pd):
@@ -88,8 +87,7 @@ def test_trajectory_matches_oracle(pd):
         sol.set_dirichlet(s.dirichlet_positions(st))
         sol.step(s.outer_iters, region_callback(s, st, xg_prev))
         o.step(s.outer_iters, 1, oracle_callback(s, st), s.dirichlet_positions(st))
-    err = np.linalg.norm(sol.positions() - o.x) / np.linalg.norm(o.x - s.X)
-    assert err <= 1e-8, err
+    assert_parity(sol.positions(), o.x, s.X, 1e-8)
     F = oracle.deformation_gradients(o.x, o.tets, o.Dm_inv)
     sv = np.linalg.svd(F, compute_uv=False)
     assert (sv > hi).any() or (sv < lo).any()
@@ -107,8 +105,7 @@ def test_elbow_bend_matches_oracle_and_limits_strain(pd):
     o = _oracle(s, mp, lo, hi)
     o.x = x0.copy()
     xo = o.step(3, 2, oracle_callback(s, step), s.dirichlet_positions(step))
-    err = np.linalg.norm(sol.positions() - xo) / np.linalg.norm(xo - x0)
-    assert err <= TOL, err
+    assert_parity(sol.positions(), xo, x0, TOL)
 
 
 def test_mixed_form_with_strain_limit_matches_fp64(pd):
