@@ -108,6 +108,8 @@ typedef struct {
     double ms_step;           /* whole pd_step                                      */
     int64_t kernel_launches;  /* kernels this library launched during the last pd_step */
     double ms_refactor;       /* the refactorisation alone (part of ms_factor_solve; PCG forms: 0) */
+    int64_t starts_rejected;  /* supplied PCG starts replaced by zero since pd_setup
+                                 (see pd_set_warm_start)                              */
 } pd_stats;
 
 typedef struct pd_solver pd_solver;
@@ -353,8 +355,12 @@ pd_status pd_tc_rank_k(int mode, const float* A, const float* B, float* C, int64
 /* Starting point of PD_PCG_WARM solves inside pd_step: 0 = zero, 1 = the
  * previous region solution, 2 = the network's prediction z0 + s N (needs
  * parameters), 3 = z0 alone (the contact-free response, no network).  A
- * start whose residual ||g - H u0|| is not smaller than ||g|| is replaced by
- * zero (so a poor prediction never costs more than the cold start). */
+ * start u0 (here or through pd_schur_solve's u0) is kept only when it lowers
+ * the energy PCG minimises, phi(u) = u^T H u / 2 - g^T u, below phi(0) = 0,
+ * i.e. when it is closer to the solution than zero in the H-norm; any other
+ * start (or a non-finite one) is replaced by zero and counted in
+ * pd_stats.starts_rejected, so a poor prediction never starts PCG farther
+ * from the answer than the cold start. */
 pd_status pd_set_warm_start(pd_solver* s, int source);
 
 /* Set / read the network parameters (n must be PD_MLP_NPARAMS); setting them
@@ -367,7 +373,15 @@ pd_status pd_mlp_get_params(pd_solver* s, float* params, int64_t n);
  * by the method itself).  0 stops recording.  Recording restarts the set. */
 pd_status pd_mlp_record(pd_solver* s, int64_t max_solves);
 
-/* Adam (lr, beta 0.9/0.999) on mean-squared error over `steps` minibatches
+/* Training loss: 0 = mean squared error of the correction (the default);
+ * 1 = every node row weighted by H_ii / mean diag(Sigma_0), H_ii = Sigma_0[i][i]
+ * + C_22[i][i] of the recorded solve: the diagonal of the energy norm
+ * (u - u*)^T H (u - u*) that CG minimises, exact for the contact term of
+ * single-node springs, so errors at the stiff spring nodes count as much as
+ * they cost PCG.  pd_mlp_eval reports the same weighting.  Errors: INVALID_ARG. */
+pd_status pd_mlp_set_loss(pd_solver* s, int kind);
+
+/* Adam (lr, beta 0.9/0.999) on the training loss over `steps` minibatches
  * of `batch` recorded node rows (multiple of 128, <= 8192) drawn with a
  * counter-based generator from `seed`.  *loss = mean loss of the last steps. */
 pd_status pd_mlp_train(pd_solver* s, int64_t steps, int64_t batch, double lr, uint64_t seed, double* loss);

@@ -45,7 +45,8 @@ class Stats(ctypes.Structure):
                [(name, ctypes.c_double) for name in
                 ("ms_local_alpha", "ms_forward", "ms_contact_update", "ms_local_beta", "ms_factor_solve",
                  "ms_bookkeeping", "ms_backward", "ms_step")] + [("kernel_launches", ctypes.c_int64),
-                                                                  ("ms_refactor", ctypes.c_double)]
+                                                                  ("ms_refactor", ctypes.c_double),
+                                                                  ("starts_rejected", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -90,6 +91,7 @@ _sigs = {
     "pd_mlp_record": (ctypes.c_int, [P, I64]),
     "pd_mlp_train": (ctypes.c_int, [P, I64, I64, D, ctypes.c_uint64, ctypes.POINTER(D)]),
     "pd_mlp_eval": (ctypes.c_int, [P, ctypes.POINTER(D), ctypes.POINTER(D)]),
+    "pd_mlp_set_loss": (ctypes.c_int, [P, ctypes.c_int]),
     "pd_mlp_loss_grad": (ctypes.c_int, [P, P, P, I64, ctypes.POINTER(D), P]),
     "pd_tc_rank_k": (ctypes.c_int, [ctypes.c_int, P, P, P, I64, I64, I64, P]),
     "pd_schur_solve_noalloc": (ctypes.c_int, [P, I64, I64, P, P, P, P, P, P, ctypes.c_char_p, I64]),

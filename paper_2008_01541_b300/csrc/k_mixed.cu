@@ -1277,11 +1277,22 @@ pd_status mixed_iterate(pd_solver* s, const double* g, const double* u0, double*
   const int lost_pivot = warm ? 0 : *M->lpiv_h;
   const double tol2 = s->opt.tol * s->opt.tol * (gg > 0 ? gg : 1.0);
   double rr = read_slot(s, 0);
-  if (u0 && !(rr <= gg)) {   // a supplied start worse than zero (or not finite): start from zero
-    cudaMemsetAsync(u, 0, sizeof(double) * n3, st);
-    cudaMemcpyAsync(M->r, g, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st);
-    rr = gg;
-    ++s->starts_rejected;
+  if (u0) {
+    // CG decreases phi(u) = u^T H u / 2 - g^T u = -(u . r + g . u) / 2 with
+    // r = g - H u, and phi(u) - phi(u*) = ||u - u*||_H^2 / 2: a start with
+    // phi(u0) >= phi(0) = 0 is farther from the solution in the energy norm
+    // than zero (or not finite), and is replaced by zero
+    dot(s, u, M->r, 6);
+    dot(s, g, u, 7);
+    cudaMemcpyAsync(M->sc_h + 7, M->sc + 7, sizeof(double), cudaMemcpyDeviceToHost, st);
+    const double ur = read_slot(s, 6), gu = M->sc_h[7];   // (read_slot synchronises: slot 7 is current)
+    const double phi = -0.5 * (ur + gu);
+    if (!(phi < 0.0) || !std::isfinite(rr)) {
+      cudaMemsetAsync(u, 0, sizeof(double) * n3, st);
+      cudaMemcpyAsync(M->r, g, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st);
+      rr = gg;
+      ++s->starts_rejected;
+    }
   }
   int it = 0;
   bool ok = rr <= tol2;

@@ -47,6 +47,9 @@ struct Net {
   int64_t rec_cap = 0, rec_rows = 0;
   bf16* recX = nullptr;       // [rec_cap][IN_PAD]
   float* recT = nullptr;      // [rec_cap][3]
+  float* recW = nullptr;      // [rec_cap] row weight H_ii / mean diag(Sigma_0) of the recorded solve
+  float* wgt = nullptr;       // [Bmax] weights of the current batch
+  int loss_kind = 0;          // 0: mean squared error; 1: rows weighted by H_ii (diagonal energy norm)
   int64_t adam_t = 0;
   double* loss_d = nullptr;
   double* loss_h = nullptr;
@@ -292,15 +295,19 @@ __global__ void k_predict(int64_t m, const float* __restrict__ pred, const doubl
   if (i >= m) return;
   for (int c = 0; c < 3; ++c) u0[3 * i + c] = z0[3 * i + c] + (double)pred[i * OUT_PAD + c] * scal[1];
 }
+// One solve's rows: features, target (u - z0) / s, and the row weight
+// H_ii / hbar = (Sigma_0[i][i] + C_22[i][i]) / mean diag(Sigma_0).
 __global__ void k_record(int64_t m, const bf16* __restrict__ X, const double* __restrict__ u,
-                         const double* __restrict__ z0, const double* __restrict__ scal, bf16* __restrict__ recX,
-                         float* __restrict__ recT) {
+                         const double* __restrict__ z0, const double* __restrict__ scal,
+                         const double* __restrict__ S0, const float* __restrict__ cacc, double hbar,
+                         bf16* __restrict__ recX, float* __restrict__ recT, float* __restrict__ recW) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= m) return;
   const uint4* src = reinterpret_cast<const uint4*>(X + i * IN_PAD);
   uint4* dst = reinterpret_cast<uint4*>(recX + i * IN_PAD);
   for (int q = 0; q < IN_PAD / 8; ++q) dst[q] = src[q];
   for (int c = 0; c < 3; ++c) recT[3 * i + c] = (float)((u[3 * i + c] - z0[3 * i + c]) / scal[1]);
+  recW[i] = (float)((S0[i * m + i] + (double)cacc[4 * i + 3]) / hbar);
 }
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {   // splitmix64 finaliser
   z += 0x9E3779B97F4A7C15ull;
@@ -308,8 +315,9 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {   // splitmix64 finalise
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
   return z ^ (z >> 31);
 }
-__global__ void k_gather_batch(const bf16* __restrict__ recX, const float* __restrict__ recT, int64_t nrows,
-                               int64_t B, uint64_t seed, int64_t step, bf16* __restrict__ X, float* __restrict__ T) {
+__global__ void k_gather_batch(const bf16* __restrict__ recX, const float* __restrict__ recT,
+                               const float* __restrict__ recW, int64_t nrows, int64_t B, uint64_t seed, int64_t step,
+                               bf16* __restrict__ X, float* __restrict__ T, float* __restrict__ W) {
   int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (b >= B) return;
   const int64_t r = (int64_t)(mix64(seed ^ mix64((uint64_t)step * 0x100000001B3ull + (uint64_t)b)) % (uint64_t)nrows);
@@ -317,20 +325,24 @@ __global__ void k_gather_batch(const bf16* __restrict__ recX, const float* __res
   uint4* dst = reinterpret_cast<uint4*>(X + b * IN_PAD);
   for (int q = 0; q < IN_PAD / 8; ++q) dst[q] = src[q];
   for (int c = 0; c < 3; ++c) T[3 * b + c] = recT[3 * r + c];
+  W[b] = recW[r];
 }
-// MSE over the first nvalid rows; dZ = d loss / d pred (BF16, plus transpose).
+// Mean over the first nvalid rows of w_b |pred_b - T_b|^2 / 3 (w = 1 without
+// weights); dZ = d loss / d pred (BF16, plus transpose).
 __global__ void k_loss(int64_t B, int64_t nvalid, const float* __restrict__ pred, const float* __restrict__ T,
-                       bf16* __restrict__ dZ, bf16* __restrict__ dZt, int64_t ldt, double* __restrict__ loss) {
+                       const float* __restrict__ wgt, bf16* __restrict__ dZ, bf16* __restrict__ dZt, int64_t ldt,
+                       double* __restrict__ loss) {
   int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (b >= B) return;
   const double scale = 1.0 / (3.0 * (double)nvalid);
+  const float w = (wgt && b < nvalid) ? wgt[b] : 1.f;
   double l = 0.0;
   for (int c = 0; c < OUT_PAD; ++c) {
     float d = 0.f;
     if (c < OUT && b < nvalid) {
       const float e = pred[b * OUT_PAD + c] - T[3 * b + c];
-      l += (double)e * e;
-      d = (float)(2.0 * scale) * e;
+      l += (double)w * e * e;
+      d = (float)(2.0 * scale) * w * e;
     }
     const bf16 v = __float2bfloat16_rn(d);
     dZ[b * OUT_PAD + c] = v;
@@ -428,7 +440,8 @@ pd_status ensure_net(pd_solver* s) {
   n->Bmax = n->mq > 8192 ? n->mq : 8192;
   const int64_t B = n->Bmax;
   if (A((void**)&n->X, 2 * B * IN_PAD) || A((void**)&n->Xt, 2 * B * IN_PAD) || A((void**)&n->pred, 4 * B * OUT_PAD) ||
-      A((void**)&n->tgt, 4 * B * 3) || A((void**)&n->scal, 8 * 4) || A((void**)&n->cacc, 4 * 4 * s->m) ||
+      A((void**)&n->tgt, 4 * B * 3) || A((void**)&n->wgt, 4 * B) || A((void**)&n->scal, 8 * 4) ||
+      A((void**)&n->cacc, 4 * 4 * s->m) ||
       A((void**)&n->Xr, 4 * 3 * s->m) || A((void**)&n->loss_d, 8) ||
       A((void**)&n->z0, 8 * 3 * s->m))
     return PD_ERR_OOM;
@@ -489,9 +502,10 @@ void forward(pd_solver* s, Net* n, int64_t B) {
 }
 
 // loss on the first nvalid rows of a B-row batch, gradients into L[l].gW / gb
-void backward(pd_solver* s, Net* n, int64_t B, int64_t nvalid) {
+// backward pass of the loss of rows 0 .. nvalid-1 (row weights w, or none)
+void backward(pd_solver* s, Net* n, int64_t B, int64_t nvalid, const float* w) {
   cudaMemsetAsync(n->loss_d, 0, sizeof(double), s->stream);
-  k_loss<<<nblk(B, 128), 128, 0, s->stream>>>(B, nvalid, n->pred, n->tgt, n->dZ[3], n->dZt[3], n->Bmax, n->loss_d);
+  k_loss<<<nblk(B, 128), 128, 0, s->stream>>>(B, nvalid, n->pred, n->tgt, w, n->dZ[3], n->dZt[3], n->Bmax, n->loss_d);
   ++pdk::g_launches;
   for (int l = 3; l >= 0; --l) {
     Layer& L = n->L[l];
@@ -602,13 +616,16 @@ pd_status record(pd_solver* s, int64_t max_solves) {
   const int64_t cap = max_solves * s->m;
   if (cap > n->rec_cap) {
     bf16* x = nullptr;
-    float* t = nullptr;
+    float *t = nullptr, *w = nullptr;
     if (cudaMalloc(&x, 2 * cap * IN_PAD) != cudaSuccess) return PD_ERR_OOM;
     if (cudaMalloc(&t, 4 * cap * 3) != cudaSuccess) { cudaFree(x); return PD_ERR_OOM; }
+    if (cudaMalloc(&w, 4 * cap) != cudaSuccess) { cudaFree(x); cudaFree(t); return PD_ERR_OOM; }
     cudaFree(n->recX);
     cudaFree(n->recT);
+    cudaFree(n->recW);
     n->recX = x;
     n->recT = t;
+    n->recW = w;
     n->rec_cap = cap;
   }
   n->rec_rows = 0;
@@ -624,11 +641,12 @@ pd_status train(pd_solver* s, int64_t steps, int64_t batch, double lr, uint64_t 
   double acc = 0.0;
   int64_t cnt = 0;
   for (int64_t it = 0; it < steps; ++it) {
-    k_gather_batch<<<nblk(batch, 128), 128, 0, s->stream>>>(n->recX, n->recT, n->rec_rows, batch, seed, n->adam_t, n->X, n->tgt);
+    k_gather_batch<<<nblk(batch, 128), 128, 0, s->stream>>>(n->recX, n->recT, n->recW, n->rec_rows, batch, seed,
+                                                            n->adam_t, n->X, n->tgt, n->wgt);
     k_transpose_in<<<nblk(batch * IN_PAD, 256), 256, 0, s->stream>>>(n->X, batch, n->Xt, n->Bmax);
     pdk::g_launches += 2;
     forward(s, n, batch);
-    backward(s, n, batch, batch);
+    backward(s, n, batch, batch, n->loss_kind == 1 ? n->wgt : nullptr);
     ++n->adam_t;
     const float c1 = 1.f - powf(0.9f, (float)n->adam_t), c2 = 1.f - powf(0.999f, (float)n->adam_t);
     for (int l = 0; l < 4; ++l) {
@@ -650,12 +668,13 @@ pd_status train(pd_solver* s, int64_t steps, int64_t batch, double lr, uint64_t 
 }
 
 // Mean squared error of the network over all recorded rows, and of the zero
-// prediction (the mean squared target), both in the scaled units.
-__global__ void k_sq_targets(const float* __restrict__ T, int64_t n, double* out) {
+// prediction (the mean squared target), both in the scaled units; with the
+// weighted loss both are weighted by the rows' H_ii.
+__global__ void k_sq_targets(const float* __restrict__ T, const float* __restrict__ W, int64_t n, double* out) {
   __shared__ double red[32];
   double s2 = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    s2 += (double)T[i] * T[i];
+    s2 += (W ? (double)W[i / 3] : 1.0) * T[i] * T[i];
   for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s2;
   __syncthreads();
@@ -677,21 +696,31 @@ pd_status eval(pd_solver* s, double* mse_net, double* mse_zero) {
     cudaMemsetAsync(n->X, 0, 2 * Bp * IN_PAD, s->stream);
     cudaMemcpyAsync(n->X, n->recX + r0 * IN_PAD, 2 * nv * IN_PAD, cudaMemcpyDeviceToDevice, s->stream);
     cudaMemcpyAsync(n->tgt, n->recT + r0 * 3, 4 * nv * 3, cudaMemcpyDeviceToDevice, s->stream);
+    cudaMemcpyAsync(n->wgt, n->recW + r0, 4 * nv, cudaMemcpyDeviceToDevice, s->stream);
     forward(s, n, Bp);
     cudaMemsetAsync(n->loss_d, 0, sizeof(double), s->stream);
-    k_loss<<<nblk(Bp, 128), 128, 0, s->stream>>>(Bp, nv, n->pred, n->tgt, n->dZ[3], n->dZt[3], n->Bmax, n->loss_d);
+    k_loss<<<nblk(Bp, 128), 128, 0, s->stream>>>(Bp, nv, n->pred, n->tgt, n->loss_kind == 1 ? n->wgt : nullptr,
+                                                  n->dZ[3], n->dZt[3], n->Bmax, n->loss_d);
     ++pdk::g_launches;
     cudaMemcpyAsync(n->loss_h, n->loss_d, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) return PD_ERR_CUDA;
     net_sum += *n->loss_h * (3.0 * nv);
   }
   cudaMemsetAsync(n->loss_d, 0, sizeof(double), s->stream);
-  k_sq_targets<<<148, 256, 0, s->stream>>>(n->recT, 3 * n->rec_rows, n->loss_d);
+  k_sq_targets<<<148, 256, 0, s->stream>>>(n->recT, n->loss_kind == 1 ? n->recW : nullptr, 3 * n->rec_rows,
+                                           n->loss_d);
   ++pdk::g_launches;
   cudaMemcpyAsync(n->loss_h, n->loss_d, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
   if (cudaStreamSynchronize(s->stream) != cudaSuccess) return PD_ERR_CUDA;
   if (mse_net) *mse_net = net_sum / (3.0 * n->rec_rows);
   if (mse_zero) *mse_zero = *n->loss_h / (3.0 * n->rec_rows);
+  return PD_OK;
+}
+
+pd_status set_loss(pd_solver* s, int kind) {
+  pd_status r = ensure_net(s);
+  if (r != PD_OK) return r;
+  s->net->loss_kind = kind;
   return PD_OK;
 }
 
@@ -711,7 +740,7 @@ pd_status loss_grad(pd_solver* s, const float* X, const float* T, int64_t B, dou
   k_transpose_in<<<nblk(Bp * IN_PAD, 256), 256, 0, s->stream>>>(n->X, Bp, n->Xt, n->Bmax);
   ++pdk::g_launches;
   forward(s, n, Bp);
-  backward(s, n, Bp, B);
+  backward(s, n, Bp, B, nullptr);
   cudaMemcpyAsync(n->loss_h, n->loss_d, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
   if (cudaStreamSynchronize(s->stream) != cudaSuccess) return PD_ERR_CUDA;
   if (loss) *loss = *n->loss_h;
@@ -738,8 +767,9 @@ pd_status after_solve(pd_solver* s, const double* u) {
   Net* n = s->net;
   if (!n) return PD_OK;
   if (s->mlp_recording && n->rec_rows + s->m <= n->rec_cap) {
-    k_record<<<nblk(s->m, 128), 128, 0, s->stream>>>(s->m, n->X, u, n->z0, n->scal, n->recX + n->rec_rows * IN_PAD,
-                                                       n->recT + n->rec_rows * 3);
+    k_record<<<nblk(s->m, 128), 128, 0, s->stream>>>(s->m, n->X, u, n->z0, n->scal, s->Sigma0, n->cacc, n->hbar,
+                                                       n->recX + n->rec_rows * IN_PAD, n->recT + n->rec_rows * 3,
+                                                       n->recW + n->rec_rows);
     ++pdk::g_launches;
     n->rec_rows += s->m;
   }
@@ -750,6 +780,7 @@ void free_net(pd_solver* s) {
   if (!s->net) return;
   cudaFree(s->net->recX);
   cudaFree(s->net->recT);
+  cudaFree(s->net->recW);
   if (s->net->loss_h) cudaFreeHost(s->net->loss_h);
   delete s->net;
   s->net = nullptr;

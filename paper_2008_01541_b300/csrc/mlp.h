@@ -21,6 +21,8 @@ pd_status record(pd_solver* s, int64_t max_solves);
 pd_status train(pd_solver* s, int64_t steps, int64_t batch, double lr, uint64_t seed, double* loss);
 pd_status eval(pd_solver* s, double* mse_net, double* mse_zero);
 pd_status loss_grad(pd_solver* s, const float* X, const float* T, int64_t B, double* loss, float* grad);
+// 0: mean squared error; 1: rows weighted by H_ii / mean diag(Sigma_0)
+pd_status set_loss(pd_solver* s, int kind);
 // Hooks around every collision-region solve.
 pd_status before_solve(pd_solver* s, const double* g, double* u0 /* out, may be null */);
 pd_status after_solve(pd_solver* s, const double* u);

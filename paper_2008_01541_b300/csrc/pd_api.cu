@@ -410,6 +410,7 @@ pd_status pd_set_state(pd_solver* s, const double* x, const double* v) {
 pd_status pd_get_stats(const pd_solver* s, pd_stats* out) {
   if (!s || !out) return PD_ERR_INVALID_ARG;
   *out = s->stats;
+  out->starts_rejected = s->starts_rejected;
   return PD_OK;
 }
 
@@ -751,6 +752,11 @@ pd_status pd_mlp_record(pd_solver* s, int64_t max_solves) {
 pd_status pd_mlp_train(pd_solver* s, int64_t steps, int64_t batch, double lr, uint64_t seed, double* loss) {
   if (!s || steps < 0 || !(lr > 0)) return PD_ERR_INVALID_ARG;
   return pdn::train(s, steps, batch, lr, seed, loss);
+}
+
+pd_status pd_mlp_set_loss(pd_solver* s, int kind) {
+  if (!s || kind < 0 || kind > 1) return PD_ERR_INVALID_ARG;
+  return pdn::set_loss(s, kind);
 }
 
 pd_status pd_mlp_eval(pd_solver* s, double* mse_net, double* mse_zero) {

@@ -252,6 +252,10 @@ class Solver:
         self._check(lib.pd_mlp_loss_grad(self.h, _ptr(X), _ptr(T), len(X), ctypes.byref(loss), _ptr(grad)))
         return loss.value, grad
 
+    def mlp_set_loss(self, kind):
+        """0: mean squared error; 1: rows weighted by H_ii (diagonal energy norm)."""
+        self._check(lib.pd_mlp_set_loss(self.h, int(kind)))
+
     def mlp_eval(self):
         """(mse of the network, mse of the zero prediction) over the recorded rows."""
         a, b = ctypes.c_double(), ctypes.c_double()
