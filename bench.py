@@ -365,6 +365,76 @@ def lips_rows(pd, stream, torch, full):
     return rows
 
 
+def dynamic_rows(pd, stream, torch):
+    """Backward Euler at scale: lumped mass rho * Vol / 4 per node on the
+    diagonal of A (so also on Sigma_0's), dt = 1/30 s, rho = 1000, split-TF32
+    form.  The elbow's whole flexion (61 time steps x 10 PD iterations,
+    point-triangle self-contact detected on the device at every inner
+    iteration) and the lips at m = 6,250 (its 500 penalty springs, 20 time
+    steps x 10 PD iterations); PD iterations per second over each run."""
+    import scenes
+    dt, rho = 1.0 / 30.0, 1000.0
+    out = {"dt": dt, "density": rho, "form": "split-TF32 + IR"}
+    s = scenes.elbow()
+    t0 = time.perf_counter()
+    ds = pd.Solver(s.X, s.tets, s.region, s.dirichlet, s.mu, 0.0, rho, dt, precision=pd.FP32_IR, inner_iters=1,
+                   stream=stream.cuda_stream, timing=True, max_refine=500)
+    setup_s = time.perf_counter() - t0
+    set_detector(ds, s)
+    ds.set_dirichlet(s.dirichlet_positions(0))
+    ds.step(1)                                   # warm-up
+    ds.set_state(s.X.copy(), np.zeros_like(s.X))
+    most = iters = 0
+    res = 0.0
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for step in range(61):
+        ds.set_dirichlet(s.dirichlet_positions(step))
+        ds.step(10)
+        st = ds.stats()
+        iters += st["refine_iters"]
+        res = max(res, st["residual"])
+        most = max(most, active_springs(ds))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    x, v = ds.get_state()
+    out["elbow_flexion"] = {"tets": s.E, "m": s.m, "setup_s": setup_s, "pd_iterations": 610, "ms_total": ms,
+                            "value": 610e3 / ms, "unit": UNIT, "max_active_springs": most,
+                            "refine_iters_per_step": iters / 61.0, "max_rel_residual": res,
+                            "max_speed_end": float(np.linalg.norm(v, axis=1).max())}
+    ds.close()
+    s = scenes.slabs(m=6250)
+    t0 = time.perf_counter()
+    ds = pd.Solver(s.X, s.tets, s.region, s.dirichlet, s.mu, 0.0, rho, dt, precision=pd.FP32_IR, inner_iters=1,
+                   stream=stream.cuda_stream, timing=True, max_refine=500)
+    setup_s = time.perf_counter() - t0
+    prox = s.proxies[:: max(1, len(s.proxies) // 500)][:500]
+    nodes = np.full((len(prox), 4), -1, np.int32)
+    nodes[:, 0] = prox
+    w = np.zeros((len(prox), 4))
+    w[:, 0] = 1.0
+    tgt = s.X[prox] + np.where(s.X[prox, 2:3] < 9.25, 0.1, -0.1) * np.array([0.0, 0.0, 1.0])
+    ds.set_contacts(nodes, w, tgt, np.full(len(prox), 1e6))
+    ds.set_dirichlet(s.dirichlet_positions(0))
+    ds.step(1)
+    ds.set_state(s.X.copy(), np.zeros_like(s.X))
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for step in range(20):
+        ds.set_dirichlet(s.dirichlet_positions(step))
+        ds.step(10)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    out["lips_m6250"] = {"tets": s.E, "m": s.m, "setup_s": setup_s, "springs": len(prox), "pd_iterations": 200,
+                         "ms_total": ms, "value": 200e3 / ms, "unit": UNIT}
+    ds.close()
+    return out
+
+
 def sweep(pd, sol, stream, torch, args):
     """inner = 3 and 5 on the elbow and the Schur refactor+solve median / p90
     over repeated solves."""
@@ -723,6 +793,7 @@ def main():
         line["trajectory_split_tf32"] = trajectory(pd, sol, stream, torch)
         sol.set_precision(prec)
         line["lips_config4"] = lips_rows(pd, stream, torch, args.sweep)
+        line["backward_euler"] = dynamic_rows(pd, stream, torch)
     if args.sweep:
         sol.set_state(*state)
         set_detector(sol, s)

@@ -64,7 +64,8 @@ typedef struct {
 
 typedef struct {
     double mu;        /* Lame mu of the PD energy mu ||F - R||_F^2 (Eq. 2)       */
-    double lambda;    /* accepted and ignored: the method sets lambda = 0 (Sec 2.2) */
+    double lambda;    /* accepted and ignored: the method sets lambda = 0 (Sec 2.2);
+                         its PD counterpart is the volume term kappa below     */
     double density;   /* used for the lumped mass when dt > 0                    */
     /* Bi-phasic strain limiting (Section 5): the energy density gains
      * mu_prime * min_{Q in S} ||F - Q||_F^2, S = the matrices whose singular
@@ -74,6 +75,19 @@ typedef struct {
      * system matrix then carries mu + mu_prime for every element.           */
     double mu_prime;
     double sigma_min, sigma_max;
+    /* PD volume term (the lambda term of Eq. 1, (lambda/2) tr^2(S - I), has
+     * no PD form: with R fixed its Hessian depends on R): the energy density
+     * gains kappa * ||F - T||_F^2, T the matrix nearest F with
+     * det T in [det_min, det_max], found from the signed SVD of F on the
+     * principal branch of the stationarity condition (the nearest such
+     * matrix for every contraction and inversion, and for expansions up to
+     * about 1.9x in every direction).  With det_min = det_max = 1 and
+     * kappa = 3 lambda / 2 it agrees with the lambda term to second order
+     * in the strain.  kappa = 0 (zero-initialised struct) turns it off;
+     * otherwise 0 < det_min <= det_max (det_max may be +inf).  The system
+     * matrix then carries mu + mu_prime + kappa for every element.        */
+    double kappa;
+    double det_min, det_max;
 } pd_material;
 
 typedef struct {

@@ -7,7 +7,17 @@ states, so that each function can be read against the section it cites.
 
 Where the paper is silent or garbled, these readings are taken:
   * lambda is accepted and ignored: the energy is mu*||F - R||^2 only (Eq. 1,
-    the paper sets lambda = 0 in Section 2.2).
+    the paper sets lambda = 0 in Section 2.2).  The lambda term
+    (lambda/2) tr^2(S - I) has no PD form (with R held fixed its Hessian in x
+    depends on R, so the system matrix would change at every local step).
+    Its PD counterpart is available as a separate volume term
+    kappa ||F - T||^2, T the matrix nearest F with det T in [det_min,
+    det_max]; with det_min = det_max = 1 it agrees with the lambda term to
+    second order in the strain when kappa = 3 lambda / 2.  T comes from the
+    principal branch of the stationarity condition (see _volume_root): the
+    nearest such matrix for every contraction and inversion and for
+    expansions up to about 1.9x in every direction, beyond which a matrix
+    with one collapsed direction is nearer and is not taken.
   * The collision force is -W^T C (W x - t) (it follows from E_col in Eq. 7;
     the printed total force in Section 3.1 has "+ t", a sign typo).
   * The collision-prone nodes x_2 are given; E_beta is the set of tets whose
@@ -44,7 +54,7 @@ import scipy.sparse.linalg as spla
 
 __all__ = [
     "element_precompute", "shape_gradients", "deformation_gradients",
-    "polar_rotations", "strain_limit_projection", "biphasic_energy", "pd_energy", "elastic_forces", "stiffness_matrix",
+    "polar_rotations", "strain_limit_projection", "signed_svd", "volume_projection", "biphasic_energy", "pd_energy", "elastic_forces", "stiffness_matrix",
     "lumped_mass", "projection_rhs", "contact_matrix", "contact_forces",
     "contact_energy", "Partition", "partition", "global_solve",
     "OracleSolver", "schur_complement",
@@ -98,6 +108,81 @@ def strain_limit_projection(F, sigma_min, sigma_max):
     Q = U clamp(Sigma, sigma_min, sigma_max) V^T from the SVD F = U Sigma V^T."""
     U, s, Vt = np.linalg.svd(F)
     return (U * np.clip(s, sigma_min, sigma_max)[..., None, :]) @ Vt
+
+
+def signed_svd(F):
+    """F = U diag(s) V^T with U, V rotations and s = (s1, s2, s3), s1 >= s2 >=
+    |s3|: the plain SVD with the smallest singular value negated when
+    det F < 0 (so that s3 < 0 marks an inverted element)."""
+    U, s, Vt = np.linalg.svd(F)
+    du = np.where(np.linalg.det(U) < 0, -1.0, 1.0)
+    dv = np.where(np.linalg.det(Vt) < 0, -1.0, 1.0)
+    U, s, Vt = U.copy(), s.copy(), Vt.copy()
+    U[..., :, 2] *= du[..., None]       # third columns of U and V flipped
+    Vt[..., 2, :] *= dv[..., None]      # into rotations, the sign moved to s_3
+    s[..., 2] *= du * dv
+    return U, s, Vt
+
+
+def _volume_root(sig, v):
+    """The diagonal tau nearest sig with prod(tau) = v > 0 on the principal
+    branch of the stationarity condition (tau_i - s_i) tau_i = -c, i.e.
+    tau_i(c) = (s_i + sqrt(s_i^2 - 4c)) / 2, each decreasing in c, for
+    c <= min_i s_i^2 / 4.  prod(tau(c)) = v is solved for c by bisection to
+    the resolution of float64.  When even the branch end c = min s_i^2 / 4
+    leaves prod(tau) > v (an element stretched about twofold or more in
+    every direction), the branch end is returned."""
+    sig = np.asarray(sig, dtype=np.float64)
+
+    def tau(c):
+        r = np.sqrt(np.maximum(sig * sig - 4.0 * c, 0.0))
+        # the form without cancellation: for s_i < 0, tau_i = 2c / (s_i - r)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            neg = np.where(sig - r != 0.0, 2.0 * c / (sig - r), 0.0)
+        return np.where(sig >= 0.0, 0.5 * (sig + r), neg)
+
+    p0 = float(np.prod(sig))
+    if p0 < v:                           # contraction or inversion: c < 0
+        hi = 0.0
+        lo = -max(1.0, float(np.max(sig * sig)))
+        while np.prod(tau(lo)) < v:
+            lo *= 4.0
+    else:                                # expansion: 0 < c <= min s_i^2 / 4
+        lo = 0.0
+        hi = float(np.min(sig * sig)) / 4.0
+        if np.prod(tau(hi)) > v:
+            return tau(hi)
+    # invariant: prod(tau(lo)) >= v >= prod(tau(hi))
+    while True:
+        mid = 0.5 * (lo + hi)
+        if mid <= lo or mid >= hi:
+            break
+        if np.prod(tau(mid)) >= v:
+            lo = mid
+        else:
+            hi = mid
+    a, b = tau(lo), tau(hi)
+    return a if abs(np.prod(a) - v) <= abs(np.prod(b) - v) else b
+
+
+def volume_projection(F, det_min, det_max):
+    """Local step of the PD volume term kappa ||F - T||^2 (the PD form of
+    the lambda term of Eq. 1): T is the matrix nearest F whose determinant
+    lies in [det_min, det_max] (0 < det_min <= det_max).  From the signed
+    SVD F = U diag(s) V^T, T = U diag(tau) V^T with tau the diagonal nearest
+    s whose product is the bound that det F violates (T = F inside the
+    bounds); see _volume_root."""
+    F = np.asarray(F, dtype=np.float64)
+    flat = F.reshape(-1, 3, 3)
+    out = flat.copy()
+    U, s, Vt = signed_svd(flat)
+    for e in range(len(flat)):
+        d = float(np.prod(s[e]))
+        if det_min <= d <= det_max:
+            continue
+        t = _volume_root(s[e], det_min if d < det_min else det_max)
+        out[e] = (U[e] * t[None, :]) @ Vt[e]
+    return out.reshape(F.shape)
 
 
 def biphasic_energy(x, R, Q, tets, Dm_inv, vol, mu, mu_prime):
@@ -253,7 +338,7 @@ class OracleSolver:
     E~_alpha(x_2) the paper's inner loop descends (Eq. 12)."""
 
     def __init__(self, X, tets, dirichlet, region, mu, density=0.0, dt=0.0, mu_prime=0.0,
-                 sigma_min=0.0, sigma_max=np.inf):
+                 sigma_min=0.0, sigma_max=np.inf, kappa=0.0, det_min=1.0, det_max=1.0):
         self.X = np.asarray(X, dtype=np.float64)
         self.tets = np.asarray(tets, dtype=np.int64)
         self.n = len(X)
@@ -262,9 +347,13 @@ class OracleSolver:
         # bi-phasic strain limiting (Section 5); mu_prime = 0 turns it off
         self.mu_prime = float(mu_prime)
         self.sigma = (float(sigma_min), float(sigma_max))
+        # PD volume term kappa ||F - T||^2 (the lambda term of Eq. 1 in PD
+        # form); kappa = 0 turns it off
+        self.kappa = float(kappa)
+        self.det = (float(det_min), float(det_max))
         self.Dm_inv, self.vol = element_precompute(self.X, self.tets)
         self.part = Partition(self.n, self.tets, dirichlet, region)
-        self.K = stiffness_matrix(self.tets, self.Dm_inv, self.vol, self.mu + self.mu_prime, self.n)
+        self.K = stiffness_matrix(self.tets, self.Dm_inv, self.vol, self.mu + self.mu_prime + self.kappa, self.n)
         self.mass = lumped_mass(self.tets, self.vol, density, self.n) if dt > 0 else None
         self.x = self.X.copy()
         self.v = np.zeros_like(self.X)
@@ -282,12 +371,20 @@ class OracleSolver:
         F = deformation_gradients(x, self.tets[elems], self.Dm_inv[elems])
         return strain_limit_projection(F, *self.sigma)
 
-    def full_solve(self, x, R, contacts, y=None, Q=None):
-        """Argmin over free x of E_hat(x; R) (or E_hat'(x; R, Q)) + E_col
-        (+ inertia), Dirichlet fixed."""
+    def volume_targets(self, x, elems):
+        """T_e of the volume term for the given elements."""
+        F = deformation_gradients(x, self.tets[elems], self.Dm_inv[elems])
+        return volume_projection(F, *self.det)
+
+    def full_solve(self, x, R, contacts, y=None, Q=None, T=None):
+        """Argmin over free x of E_hat(x; R) (with the bi-phasic term at Q and
+        the volume term at T when present) + E_col (+ inertia), Dirichlet
+        fixed."""
         b = projection_rhs(R, self.tets, self.Dm_inv, self.vol, self.mu, self.n)
         if self.mu_prime > 0:
             b = b + projection_rhs(Q, self.tets, self.Dm_inv, self.vol, self.mu_prime, self.n)
+        if self.kappa > 0:
+            b = b + projection_rhs(T, self.tets, self.Dm_inv, self.vol, self.kappa, self.n)
         C = Ct = None
         if contacts is not None and contacts.k > 0:
             C = contact_matrix(contacts, self.n)
@@ -315,30 +412,38 @@ class OracleSolver:
         y = (x_n + self.dt * self.v) if self.mass is not None else None
         R = np.zeros((len(self.tets), 3, 3))
         Q = np.zeros((len(self.tets), 3, 3)) if self.mu_prime > 0 else None
+        T = np.zeros((len(self.tets), 3, 3)) if self.kappa > 0 else None
         for _ in range(outer_iters):
             R[p.alpha] = self.rotations(self.x, p.alpha)          # step 1
             if Q is not None:
                 Q[p.alpha] = self.projections(self.x, p.alpha)
+            if T is not None:
+                T[p.alpha] = self.volume_targets(self.x, p.alpha)
             virt = None
             for _ in range(inner_iters):
                 contacts = contacts_fn(self.x) if contacts_fn is not None else None   # 4.1
                 R[p.beta] = self.rotations(self.x, p.beta)        # 4.2
                 if Q is not None:
                     Q[p.beta] = self.projections(self.x, p.beta)
-                virt = self.full_solve(self.x, R, contacts, y, Q)  # 4.3-4.5
+                if T is not None:
+                    T[p.beta] = self.volume_targets(self.x, p.beta)
+                virt = self.full_solve(self.x, R, contacts, y, Q, T)  # 4.3-4.5
                 self.x[p.region] = virt[p.region]                 # 4.6
             self.x[p.x1] = virt[p.x1]                             # 5
         if self.mass is not None:
             self.v = (self.x - x_n) / self.dt
         return self.x
 
-    def energy(self, x, R, contacts=None, y=None, Q=None):
-        """E_hat (or E_hat' with Q) + E_col (+ inertia) at x for fixed R, Q
-        and contacts."""
+    def energy(self, x, R, contacts=None, y=None, Q=None, T=None):
+        """E_hat (or E_hat' with Q, plus the volume term with T) + E_col
+        (+ inertia) at x for fixed R, Q, T and contacts."""
         if self.mu_prime > 0:
             e = biphasic_energy(x, R, Q, self.tets, self.Dm_inv, self.vol, self.mu, self.mu_prime)
         else:
             e = pd_energy(x, R, self.tets, self.Dm_inv, self.vol, self.mu)
+        if self.kappa > 0:
+            F = deformation_gradients(x, self.tets, self.Dm_inv)
+            e += float(np.sum(self.vol * self.kappa * np.sum((F - T) ** 2, axis=(1, 2))))
         if contacts is not None and contacts.k > 0:
             e += contact_energy(contacts, x)
         if self.mass is not None and y is not None:

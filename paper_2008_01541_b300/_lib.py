@@ -29,7 +29,8 @@ class Mesh(ctypes.Structure):
 
 class Material(ctypes.Structure):
     _fields_ = [("mu", ctypes.c_double), ("lam", ctypes.c_double), ("density", ctypes.c_double),
-                ("mu_prime", ctypes.c_double), ("sigma_min", ctypes.c_double), ("sigma_max", ctypes.c_double)]
+                ("mu_prime", ctypes.c_double), ("sigma_min", ctypes.c_double), ("sigma_max", ctypes.c_double),
+                ("kappa", ctypes.c_double), ("det_min", ctypes.c_double), ("det_max", ctypes.c_double)]
 
 
 class Options(ctypes.Structure):

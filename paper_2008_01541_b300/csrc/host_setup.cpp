@@ -238,7 +238,7 @@ int build(const Input& in, Setup& s, std::string* err) {
   double t0 = now_ms();
   const int64_t n = in.n, E = in.E, m = in.m;
   if (n < 1 || E < 1 || !in.X || !in.tets || !(in.mu > 0) || in.dt < 0 || !std::isfinite(in.mu) ||
-      !(in.mu_prime >= 0) || !std::isfinite(in.mu_prime)) {
+      !(in.mu_prime >= 0) || !std::isfinite(in.mu_prime) || !(in.kappa >= 0) || !std::isfinite(in.kappa)) {
     *err = "invalid mesh or material";
     return ST_INVALID;
   }
@@ -427,7 +427,7 @@ int build(const Input& in, Setup& s, std::string* err) {
       const int32_t* t = in.tets + 4 * e;
       double G[4][3];
       shape_grad(&s.Dminv[9 * e], G);
-      double w = 2.0 * (in.mu + in.mu_prime) * s.vol[e];
+      double w = 2.0 * (in.mu + in.mu_prime + in.kappa) * s.vol[e];
       for (int a = 0; a < 4; ++a) {
         int64_t pa = s.pos[t[a]];
         if (pa < 0) continue;
@@ -464,7 +464,7 @@ int build(const Input& in, Setup& s, std::string* err) {
       const int32_t* t = in.tets + 4 * e;
       double G[4][3];
       shape_grad(&s.Dminv[9 * e], G);
-      double w = 2.0 * (in.mu + in.mu_prime) * s.vol[e];
+      double w = 2.0 * (in.mu + in.mu_prime + in.kappa) * s.vol[e];
       for (int a = 0; a < 4; ++a)
         for (int b = 0; b < 4; ++b) {
           double v = w * (G[a][0] * G[b][0] + G[a][1] * G[b][1] + G[a][2] * G[b][2]);

@@ -14,6 +14,7 @@ struct Input {
   const double* X = nullptr;      // [n][3]
   const int32_t* tets = nullptr;  // [E][4]
   double mu = 0, mu_prime = 0, density = 0, dt = 0;   // mu_prime: bi-phasic term (Section 5)
+  double kappa = 0;                                   // PD volume term (the lambda term of Eq. 1)
   const int32_t* region = nullptr;
   int64_t m = 0;
   const int32_t* dirichlet = nullptr;

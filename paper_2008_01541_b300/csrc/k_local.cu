@@ -147,13 +147,82 @@ __device__ void polar_jacobi(const double* F, double* R) {
     for (int j = 0; j < 3; ++j) R[3 * i + j] = u1[i] * v1[j] + u2[i] * v2[j] + u3[i] * v3[j];
 }
 
-// Bi-phasic strain limiting (Section 5): with F = R S the polar split and
-// S = V diag(lambda) V^T (signed: an inverted F has one negative lambda, its
-// singular values are |lambda|), the closest matrix with singular values in
-// [lo, hi] is Q = R V diag(sign(lambda) clamp(|lambda|)) V^T.  Returns
-// D = F - Q = -R V diag(c - lambda) V^T, which is exactly zero when every
-// singular value is inside the bounds.
-__device__ void strain_limit_residual(const double* F, const double* R, double lo, double hi, double* D) {
+// Principal branch of the volume projection: tau(c) = (s + sqrt(s^2 - 4c)) / 2
+// solves (tau - s) tau = -c; for s < 0 the same root as 2c / (s - sqrt(...)),
+// which has no cancellation.
+__device__ __forceinline__ double vol_tau(double s, double c, double* r_out) {
+  const double r = sqrt(fmax(s * s - 4.0 * c, 0.0));
+  *r_out = r;
+  if (s >= 0.0) return 0.5 * (s + r);
+  const double d = s - r;
+  return d != 0.0 ? 2.0 * c / d : 0.0;
+}
+
+// PD volume term (the lambda term of Eq. 1 in PD form): the signed singular
+// values s (eigenvalues of S, any order) are moved to tau, the diagonal
+// nearest s whose product is vt, on the principal branch tau_i(c).
+// g(c) = log prod tau_i(c) - log vt is concave and decreasing in c, so
+// Newton steps taken from a point right of the root decrease monotonically
+// to it; where the slope is infinite (the branch end, or tau_i = 0) the
+// bracket is bisected instead.  If even the branch end keeps the product
+// above vt (an element stretched about twofold in every direction), tau is
+// the branch end.
+__device__ void volume_tau(const double s[3], double vt, double tau[3]) {
+  double r[3];
+  const double v = s[0] * s[1] * s[2];
+  const double lvt = log(vt);
+  double a, c;   // g(a) >= 0 >= g(c)
+  if (v < vt) {
+    c = 0.0;
+    a = -fmax(1.0, fmax(s[0] * s[0], fmax(s[1] * s[1], s[2] * s[2])));
+    for (int k = 0; k < 64; ++k) {
+      if (vol_tau(s[0], a, r) * vol_tau(s[1], a, r + 1) * vol_tau(s[2], a, r + 2) >= vt) break;
+      a *= 4.0;
+    }
+  } else {
+    a = 0.0;
+    c = 0.25 * fmin(s[0] * s[0], fmin(s[1] * s[1], s[2] * s[2]));
+    if (vol_tau(s[0], c, r) * vol_tau(s[1], c, r + 1) * vol_tau(s[2], c, r + 2) > vt) {
+      for (int i = 0; i < 3; ++i) tau[i] = vol_tau(s[i], c, r + i);
+      return;
+    }
+  }
+  for (int it = 0; it < 100; ++it) {
+    double p = 1.0, dg = 0.0, t[3];
+    for (int i = 0; i < 3; ++i) {
+      t[i] = vol_tau(s[i], c, r + i);
+      p *= t[i];
+      dg -= 1.0 / (r[i] * t[i]);   // d log tau_i / dc = -1 / (r_i tau_i)
+    }
+    const double g = p > 0.0 ? log(p) - lvt : -INFINITY;
+    const double cn = c - g / dg;
+    if (!(cn >= a && cn <= c)) {          // no finite Newton step here: bisect
+      const double mid = 0.5 * (a + c);
+      if (!(mid > a && mid < c)) break;
+      double pm = 1.0;
+      for (int i = 0; i < 3; ++i) pm *= vol_tau(s[i], mid, r + i);
+      if (pm >= vt) a = mid;
+      else c = mid;
+      continue;
+    }
+    if (!(cn < c)) break;                 // converged: no further decrease
+    const bool done = c - cn <= 4e-16 * fabs(c);
+    c = cn;
+    if (done) break;
+  }
+  for (int i = 0; i < 3; ++i) tau[i] = vol_tau(s[i], c, r + i);
+}
+
+// Residuals of the extra local-step terms from one eigen-decomposition of
+// S = R^T F = V diag(lambda) V^T (signed: an inverted F has one negative
+// lambda, its singular values are |lambda|):
+//  * bi-phasic strain limiting (Section 5): the closest matrix with singular
+//    values in [lo, hi] is Q = R V diag(sign(lambda) clamp(|lambda|)) V^T;
+//  * PD volume term: T = R V diag(tau) V^T with tau from volume_tau when
+//    prod(lambda) = det F lies outside [vlo, vhi] (T = F inside).
+// Returns D = frac (F - Q) + vfrac (F - T) = R V diag(frac (lambda - q) +
+// vfrac (lambda - tau)) V^T, exactly zero when no bound is violated.
+__device__ void extra_residual(const double* F, const double* R, const StrainLimit& sl, double* D) {
   double S[3][3], V[3][3];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
@@ -162,12 +231,25 @@ __device__ void strain_limit_residual(const double* F, const double* R, double l
       S[i][j] = 0.5 * (a + b);
     }
   jacobi_eig3(S, V);
-  double dl[3];
+  const double lam[3] = {S[0][0], S[1][1], S[2][2]};
+  double dl[3] = {0.0, 0.0, 0.0};
   bool any = false;
-  for (int q = 0; q < 3; ++q) {
-    const double l = S[q][q], al = fabs(l), c = fmin(fmax(al, lo), hi);
-    dl[q] = (l < 0.0 ? -c : c) - l;
-    any |= dl[q] != 0.0;
+  if (sl.frac > 0.0) {
+    for (int q = 0; q < 3; ++q) {
+      const double l = lam[q], al = fabs(l), c = fmin(fmax(al, sl.lo), sl.hi);
+      const double d = l - (l < 0.0 ? -c : c);
+      dl[q] += sl.frac * d;
+      any |= d != 0.0;
+    }
+  }
+  if (sl.vfrac > 0.0) {
+    const double v = lam[0] * lam[1] * lam[2];
+    if (v < sl.vlo || v > sl.vhi) {
+      double tau[3];
+      volume_tau(lam, v < sl.vlo ? sl.vlo : sl.vhi, tau);
+      for (int q = 0; q < 3; ++q) dl[q] += sl.vfrac * (lam[q] - tau[q]);
+      any = true;
+    }
   }
   if (!any) {
     for (int i = 0; i < 9; ++i) D[i] = 0.0;
@@ -177,17 +259,18 @@ __device__ void strain_limit_residual(const double* F, const double* R, double l
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) M[i][j] = V[i][0] * dl[0] * V[j][0] + V[i][1] * dl[1] * V[j][1] + V[i][2] * dl[2] * V[j][2];
   for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) D[3 * i + j] = -(R[3 * i] * M[0][j] + R[3 * i + 1] * M[1][j] + R[3 * i + 2] * M[2][j]);
+    for (int j = 0; j < 3; ++j) D[3 * i + j] = R[3 * i] * M[0][j] + R[3 * i + 1] * M[1][j] + R[3 * i + 2] * M[2][j];
 }
 
-// Elemental forces f_e = -Vol_e G_e-weighted (2 mu (F - R) + 2 mu' (F - Q));
-// w = 2 (mu + mu') Vol and frac = mu' / (mu + mu') (frac = 0 without the
-// bi-phasic term, SL = false compiles it out).
-template <bool SL>
+// Elemental forces f_e = -Vol_e G_e-weighted (2 mu (F - R) + 2 mu' (F - Q) +
+// 2 kappa (F - T)); w = 2 (mu + mu' + kappa) Vol, so the stress is
+// (1 - frac - vfrac) (F - R) + frac (F - Q) + vfrac (F - T) (EXTRA = false
+// compiles the extra terms out).
+template <bool EXTRA>
 __global__ void k_polar_forces(int64_t count, const int4* __restrict__ tets,
                                const double* __restrict__ Dm, const double* __restrict__ w,
                                const double* __restrict__ x, double* __restrict__ fe,
-                               double* __restrict__ Rout, double frac, double lo, double hi) {
+                               double* __restrict__ Rout, StrainLimit sl) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= count) return;
   int4 t = tets[e];
@@ -213,11 +296,12 @@ __global__ void k_polar_forces(int64_t count, const int4* __restrict__ tets,
   double P[9];
 #pragma unroll
   for (int i = 0; i < 9; ++i) P[i] = F[i] - R[i];
-  if (SL) {
+  if (EXTRA) {
     double D[9];
-    strain_limit_residual(F, R, lo, hi, D);
+    extra_residual(F, R, sl, D);
+    const double keep = 1.0 - sl.frac - sl.vfrac;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) P[i] = (1.0 - frac) * P[i] + frac * D[i];
+    for (int i = 0; i < 9; ++i) P[i] = keep * P[i] + D[i];
   }
   double f[4][3];
 #pragma unroll
@@ -309,10 +393,10 @@ inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 void polar_forces(int64_t count, const int4* tets, const double* Dm, const double* w, const double* x,
                   double* fe, double* R_out, cudaStream_t st, const StrainLimit* sl) {
   if (count <= 0) return;
-  if (sl && sl->frac > 0.0)
-    k_polar_forces<true><<<nblk(count, 128), 128, 0, st>>>(count, tets, Dm, w, x, fe, R_out, sl->frac, sl->lo, sl->hi);
+  if (sl && (sl->frac > 0.0 || sl->vfrac > 0.0))
+    k_polar_forces<true><<<nblk(count, 128), 128, 0, st>>>(count, tets, Dm, w, x, fe, R_out, *sl);
   else
-    k_polar_forces<false><<<nblk(count, 128), 128, 0, st>>>(count, tets, Dm, w, x, fe, R_out, 0.0, 0.0, 0.0);
+    k_polar_forces<false><<<nblk(count, 128), 128, 0, st>>>(count, tets, Dm, w, x, fe, R_out, StrainLimit{});
   ++g_launches;
 }
 

@@ -22,16 +22,19 @@ inline bool first_on_device(std::atomic<unsigned long long>& mask) {
 extern int64_t g_launches;
 
 // ---- local step (Section 2.2) -------------------------------------------
-// Bi-phasic strain limiting (Section 5): frac = mu' / (mu + mu'), singular
-// value bounds [lo, hi].
+// Extra local-step terms: bi-phasic strain limiting (Section 5), frac =
+// mu' / (mu + mu' + kappa), singular value bounds [lo, hi]; the PD volume
+// term (the lambda term of Eq. 1 in PD form), vfrac = kappa / (mu + mu' +
+// kappa), determinant bounds [vlo, vhi].
 struct StrainLimit {
   double frac = 0.0, lo = 0.0, hi = 0.0;
+  double vfrac = 0.0, vlo = 0.0, vhi = 0.0;
 };
 
 // For each element e of a set: F = Ds Dm^-1, R = polar(F) in SO(3),
-// fe[e][a][:] = forces on its four vertices, f_a = -w_e (F - T) G_a^T with
-// T = R, or with strain limiting T = (1 - frac) R + frac Q
-// (w_e = 2 (mu + mu') Vol_e).  R_out (optional) receives R row-major [count][9].
+// fe[e][a][:] = forces on its four vertices, f_a = -w_e (F - P) G_a^T with
+// P = R, or with the extra terms P = (1 - frac - vfrac) R + frac Q + vfrac T
+// (w_e = 2 (mu + mu' + kappa) Vol_e).  R_out (optional) receives R row-major [count][9].
 void polar_forces(int64_t count, const int4* tets, const double* DminvSoA, const double* w,
                   const double* x, double* fe, double* R_out, cudaStream_t st, const StrainLimit* sl = nullptr);
 

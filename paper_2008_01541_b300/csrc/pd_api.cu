@@ -64,7 +64,7 @@ static pd_status build_elemset(pd_solver* s, const pdh::Setup& h, const int32_t*
     int32_t e = elems[i];
     t[i] = make_int4(tets[4 * e], tets[4 * e + 1], tets[4 * e + 2], tets[4 * e + 3]);
     for (int q = 0; q < 9; ++q) Dm[q * c + i] = h.Dminv[9 * (int64_t)e + q];
-    w[i] = 2.0 * (s->mu + s->mu_prime) * h.vol[e];
+    w[i] = 2.0 * (s->mu + s->mu_prime + s->kappa) * h.vol[e];
   }
   CK(dupload(s, &es.tets, t.data(), c));
   CK(dupload(s, &es.Dm, Dm.data(), 9 * c));
@@ -255,15 +255,28 @@ pd_status pd_setup(const pd_mesh* mesh, const pd_material* mat, double dt, const
     delete s;
     return PD_ERR_INVALID_ARG;
   }
+  if (!(mat->kappa >= 0) || !std::isfinite(mat->kappa) ||
+      (mat->kappa > 0 && (!(mat->det_min > 0) || !(mat->det_max >= mat->det_min) || !std::isfinite(mat->det_min)))) {
+    g_setup_error = "volume term needs kappa >= 0 and 0 < det_min <= det_max";
+    delete s;
+    return PD_ERR_INVALID_ARG;
+  }
   s->mu_prime = mat->mu_prime;
+  s->kappa = mat->kappa;
+  const double wsum = mat->mu + mat->mu_prime + mat->kappa;
   if (mat->mu_prime > 0) {
-    s->sl.frac = mat->mu_prime / (mat->mu + mat->mu_prime);
+    s->sl.frac = mat->mu_prime / wsum;
     s->sl.lo = mat->sigma_min;
     s->sl.hi = mat->sigma_max;
   }
+  if (mat->kappa > 0) {
+    s->sl.vfrac = mat->kappa / wsum;
+    s->sl.vlo = mat->det_min;
+    s->sl.vhi = mat->det_max;
+  }
   pdh::Input in;
   in.n = mesh->n_nodes; in.E = mesh->n_tets; in.X = mesh->rest_pos; in.tets = mesh->tets;
-  in.mu = mat->mu; in.mu_prime = mat->mu_prime; in.density = mat->density; in.dt = dt;
+  in.mu = mat->mu; in.mu_prime = mat->mu_prime; in.kappa = mat->kappa; in.density = mat->density; in.dt = dt;
   in.region = region; in.m = m; in.dirichlet = dirichlet; in.nd = nd;
   pdh::Setup h;
   std::string err;

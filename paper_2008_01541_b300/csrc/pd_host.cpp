@@ -11,7 +11,7 @@ extern "C" pd_status pd_host_schur(const pd_mesh* mesh, const pd_material* mat, 
   if (!mesh || !mat || (!region && m > 0) || (!dirichlet && nd > 0) || (!sigma_out && m > 0)) return PD_ERR_INVALID_ARG;
   pdh::Input in;
   in.n = mesh->n_nodes; in.E = mesh->n_tets; in.X = mesh->rest_pos; in.tets = mesh->tets;
-  in.mu = mat->mu; in.mu_prime = mat->mu_prime; in.density = mat->density; in.dt = dt;
+  in.mu = mat->mu; in.mu_prime = mat->mu_prime; in.kappa = mat->kappa; in.density = mat->density; in.dt = dt;
   in.region = region; in.m = m; in.dirichlet = dirichlet; in.nd = nd;
   pdh::Setup s;
   std::string err;

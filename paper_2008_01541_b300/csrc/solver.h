@@ -34,8 +34,8 @@ struct pd_solver {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   double mu = 0, density = 0, dt = 0;
-  double mu_prime = 0;
-  pdk::StrainLimit sl;   // bi-phasic term (frac = 0: off)
+  double mu_prime = 0, kappa = 0;
+  pdk::StrainLimit sl;   // bi-phasic and volume terms (frac = vfrac = 0: off)
   int64_t n = 0, E = 0, m = 0, nd = 0, n1 = 0, nfree = 0, mp = 0;
   std::vector<int32_t> tets_h, region_h, region_index;
   std::unique_ptr<pdh::Setup> hostdata;  // element data kept for pd_local_step

@@ -25,12 +25,12 @@ def _mesh(X, tets):
     return _lib.Mesh(len(X), X.ctypes.data, len(tets), tets.ctypes.data), (X, tets)
 
 
-def host_schur(X, tets, region, dirichlet, mu, density=0.0, dt=0.0, mu_prime=0.0):
+def host_schur(X, tets, region, dirichlet, mu, density=0.0, dt=0.0, mu_prime=0.0, kappa=0.0):
     """Sigma_0 from the library's host partial Cholesky (no GPU needed)."""
     mesh, keep = _mesh(X, tets)
     region = _c(region, np.int32)
     dirichlet = _c(dirichlet, np.int32)
-    mat = _lib.Material(mu, 0.0, density, mu_prime, 0.0, np.inf)
+    mat = _lib.Material(mu, 0.0, density, mu_prime, 0.0, np.inf, kappa, 1.0, 1.0)
     out = np.zeros((len(region), len(region)))
     info = ctypes.create_string_buffer(1024)
     st = lib.pd_host_schur(ctypes.byref(mesh), ctypes.byref(mat), dt, _ptr(region), len(region),
@@ -45,7 +45,7 @@ class Solver:
 
     def __init__(self, X, tets, region, dirichlet, mu, lam=0.0, density=0.0, dt=0.0,
                  precision=_lib.FP64, inner_iters=1, tol=1e-10, max_refine=50, stream=None, timing=False,
-                 mu_prime=0.0, sigma_min=0.0, sigma_max=np.inf):
+                 mu_prime=0.0, sigma_min=0.0, sigma_max=np.inf, kappa=0.0, det_min=1.0, det_max=1.0):
         mesh, keep = _mesh(X, tets)
         self.n = len(keep[0])
         self.E = len(keep[1])
@@ -53,7 +53,7 @@ class Solver:
         self.dirichlet = _c(dirichlet, np.int32)
         self.m = len(self.region)
         self.nd = len(self.dirichlet)
-        mat = _lib.Material(mu, lam, density, mu_prime, sigma_min, sigma_max)
+        mat = _lib.Material(mu, lam, density, mu_prime, sigma_min, sigma_max, kappa, det_min, det_max)
         opt = _lib.Options(precision, tol, max_refine, inner_iters,
                            ctypes.c_void_p(stream) if stream else None, 1 if timing else 0)
         h = ctypes.c_void_p()

@@ -192,3 +192,75 @@ def test_lips_12500_region_solves_and_outer_iteration(pd):
     xo = o.step(1, 1, lambda x: c, dpos)
     assert_parity(sol.positions(), xo, x0, TOL)
     sol.close()
+
+
+def test_full_elbow_backward_euler_step(pd):
+    # dynamic mode at scale: backward Euler on the elbow (lumped mass on the
+    # diagonal of A, hence on Sigma_0's), one time step of the flexion from
+    # the closed pose at rest velocity, 1 outer x 1 inner iteration with
+    # point-triangle contact detected on the device, FP64 and split-TF32,
+    # positions and velocities per node against the oracle
+    s = scenes.elbow()
+    dt, rho = 1.0 / 30.0, 1000.0
+    sol = pd.Solver(s.X, s.tets, s.region, s.dirichlet, s.mu, 0.0, rho, dt, max_refine=500)
+    x0, fstep = scenes.closed_pose(s, 40.0)
+    v0 = 0.5 * rng(25).normal(size=x0.shape)
+    v0[s.dirichlet] = 0.0
+    dpos = s.dirichlet_positions(fstep + 1)
+    pa, ta, pb, tb = s.info["tri_sides"]
+    fn = _tri_oracle(s)
+    o = oracle.OracleSolver(s.X, s.tets, s.dirichlet, s.region, s.mu, rho, dt)
+    o.x, o.v = x0.copy(), v0.copy()
+    xo = o.step(1, 1, fn, dpos).copy()
+    vo = o.v.copy()
+    for prec, tol in (("FP64", TOL), ("FP32_IR", MIXED_STEP_TOL)):
+        sol.set_precision(getattr(pd, prec))
+        sol.set_state(x0, v0)
+        sol.set_dirichlet(dpos)
+        sol.set_detector_triangles(pa, ta, pb, tb, s.info["tri_gap"], s.info["tri_rest_min"], s.stiffness)
+        sol.step(1)
+        x, v = sol.get_state()
+        assert_parity(x, xo, x0, tol, prec)
+        # v = (x - x0) / dt for every node: the same bound scaled by 1 / dt
+        assert_parity(v, vo, np.zeros_like(v), tol, prec + " v")
+        sol.clear_detector()
+    sol.close()
+
+
+def test_lips_backward_euler_outer_iteration(pd):
+    # configuration 4 (m = 6,250) in backward Euler: the region solve's
+    # residual against H = Sigma_0 + C_22 (Sigma_0 now carries the x_2 mass
+    # over dt^2) for every form, and one FP64 outer iteration per node
+    s = scenes.slabs(m=6250)
+    dt, rho = 1.0 / 30.0, 1000.0
+    sol = pd.Solver(s.X, s.tets, s.region, s.dirichlet, s.mu, 0.0, rho, dt, max_refine=500)
+    x0 = s.X.copy()
+    x0[s.proxies] += np.array([0.0, 0.0, 0.4]) * (x0[s.proxies, 2:3] < 9.25)
+    v0 = 0.3 * rng(26).normal(size=x0.shape)
+    v0[s.dirichlet] = 0.0
+    c = s.contacts(0, x0)
+    assert c.k > 100
+    sol.set_contacts(*contact_tuple(c))
+    S0 = sol.schur()
+    o = oracle.OracleSolver(s.X, s.tets, s.dirichlet, s.region, s.mu, rho, dt)
+    # Sigma_0 = M_2 / dt^2 + (K_22 - K_21 (K_11 + M_1 / dt^2)^-1 K_12) and the
+    # bracket is positive definite, so every diagonal entry exceeds its
+    # node's mass over dt^2
+    assert np.all(np.diag(S0) > o.mass[s.region] / dt ** 2)
+    H = _H(S0, s, c)
+    g = rng(27).normal(size=(s.m, 3)) * 1e3
+    for prec in ("FP64", "FP32_IR", "BF16_IR", "PCG_WARM"):
+        sol.set_precision(getattr(pd, prec))
+        u = sol.schur_solve(g)
+        res = np.linalg.norm(g - H @ u) / np.linalg.norm(g)
+        assert res <= TOL, (prec, res)
+    del H, S0
+    sol.set_precision(pd.FP64)
+    sol.set_state(x0, v0)
+    dpos = s.dirichlet_positions(30)
+    sol.set_dirichlet(dpos)
+    sol.step(1)
+    o.x, o.v = x0.copy(), v0.copy()
+    xo = o.step(1, 1, lambda x: c, dpos)
+    assert_parity(sol.positions(), xo, x0, TOL)
+    sol.close()

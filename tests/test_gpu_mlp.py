@@ -63,7 +63,15 @@ def test_gradients_match_the_fp64_oracle(pd):
     print("per-block max relative gradient error:", ["%s %.1e" % w for w in worst])
 
 
-def test_learned_start_cuts_pcg_iterations(pd):
+def test_learned_start_by_starting_point(pd):
+    # configuration 5 in small: region solves recorded by the method along
+    # seeded indenter paths, the network trained on them, then held-out
+    # paths run with PCG from each starting point (zero, previous solution,
+    # z0, network).  A start is kept only when it is closer to the solution
+    # than zero in the H-norm (the energy PCG minimises); with penalty
+    # springs of 1e6 an error at a spring node costs ~1e6 / diag(Sigma_0)
+    # more than elsewhere, so starts that are good in the Euclidean norm are
+    # routinely worse than zero in the H-norm
     from paper_2008_01541_b300 import warmstart as ws
     s = scenes.small_elbow(h=1.5)
     sol = pd.Solver(s.X, s.tets, s.region, s.dirichlet, s.mu, precision=pd.FP32_IR, inner_iters=2,
@@ -71,6 +79,7 @@ def test_learned_start_cuts_pcg_iterations(pd):
     sol.set_dirichlet(s.dirichlet_positions(s.info["rest_step"]))
     x0, v0 = sol.get_state()
     sol.mlp_set_params(ws.he_init(0))
+    sol.mlp_set_loss(1)
     sol.mlp_record(400)
     centres, radius = ws.indenter_path(s, seed=1, steps=200)
     ws.run_path(sol, s, centres, radius)
@@ -82,18 +91,23 @@ def test_learned_start_cuts_pcg_iterations(pd):
     centres, radius = ws.indenter_path(s, seed=99, steps=25)
     sol.set_state(x0, v0)
     ws.run_path(sol, s, centres, radius)
-    mse_net, mse_zero = sol.mlp_eval()
+    err_net, err_zero = sol.mlp_eval()
     sol.mlp_record(0)
-    # beyond the contact-free response z0, the network predicts a good part of the rest
-    assert mse_net < 0.7 * mse_zero, (mse_net, mse_zero)
-    # PCG iterations to 1e-10 by starting point, reported (the contact-free
-    # preconditioner leaves one outlier eigenvalue per active spring, which
-    # bounds what any starting point can save)
+    # beyond the contact-free response z0, the network predicts most of the rest
+    assert err_net < 0.3 * err_zero, (err_net, err_zero)
     sol.set_precision(pd.PCG_WARM)
-    total = {}
+    total, rejected = {}, {}
     for src in (0, 1, 3, 2):
         sol.set_state(x0, v0)
         sol.set_warm_start(src)
-        total[src] = sum(ws.run_path(sol, s, centres, radius))
-    print("held-out squared error of the correction after z0: network %.3f of the z0 start" % (mse_net / mse_zero))
-    print("PCG iterations by start (0 zero, 1 previous, 3 z0, 2 network):", total)
+        r0 = sol.stats()["starts_rejected"]
+        total[src] = sum(ws.run_path(sol, s, centres, radius))   # every solve reached 1e-10
+        rejected[src] = sol.stats()["starts_rejected"] - r0
+    print("held-out error of the correction after z0: network %.4f of the z0 start" % (err_net / err_zero))
+    print("PCG iterations by start (0 zero, 1 previous, 3 z0, 2 network):", total,
+          "starts replaced by zero:", rejected)
+    assert rejected[0] == 0
+    # a start is never worse than the cold start in the H-norm, so no start
+    # costs materially more iterations than zero
+    for src in (1, 3, 2):
+        assert total[src] <= 1.1 * total[0] + 2, (src, total)
