@@ -161,19 +161,21 @@ __device__ __forceinline__ double vol_tau(double s, double c, double* r_out) {
 // PD volume term (the lambda term of Eq. 1 in PD form): the signed singular
 // values s (eigenvalues of S, any order) are moved to tau, the diagonal
 // nearest s whose product is vt, on the principal branch tau_i(c).
-// g(c) = log prod tau_i(c) - log vt is concave and decreasing in c, so
-// Newton steps taken from a point right of the root decrease monotonically
-// to it; where the slope is infinite (the branch end, or tau_i = 0) the
-// bracket is bisected instead.  If even the branch end keeps the product
-// above vt (an element stretched about twofold in every direction), tau is
-// the branch end.
+// g(c) = log prod tau_i(c) - log vt is decreasing in c; its root is found by
+// Newton steps safeguarded by bisection of a bracket [a, b] with
+// g(a) >= 0 >= g(b) (a step is taken only if it stays inside the bracket and
+// at least halves the step before last; near the branch end the slope grows
+// without bound and bisection takes over).  If even the branch end keeps
+// the product above vt (an element stretched about twofold in every
+// direction), tau is the branch end.
 __device__ void volume_tau(const double s[3], double vt, double tau[3]) {
   double r[3];
   const double v = s[0] * s[1] * s[2];
   const double lvt = log(vt);
-  double a, c;   // g(a) >= 0 >= g(c)
+  const double s2min = fmin(s[0] * s[0], fmin(s[1] * s[1], s[2] * s[2]));
+  double a, b;
   if (v < vt) {
-    c = 0.0;
+    b = 0.0;
     a = -fmax(1.0, fmax(s[0] * s[0], fmax(s[1] * s[1], s[2] * s[2])));
     for (int k = 0; k < 64; ++k) {
       if (vol_tau(s[0], a, r) * vol_tau(s[1], a, r + 1) * vol_tau(s[2], a, r + 2) >= vt) break;
@@ -181,34 +183,37 @@ __device__ void volume_tau(const double s[3], double vt, double tau[3]) {
     }
   } else {
     a = 0.0;
-    c = 0.25 * fmin(s[0] * s[0], fmin(s[1] * s[1], s[2] * s[2]));
-    if (vol_tau(s[0], c, r) * vol_tau(s[1], c, r + 1) * vol_tau(s[2], c, r + 2) > vt) {
-      for (int i = 0; i < 3; ++i) tau[i] = vol_tau(s[i], c, r + i);
+    b = 0.25 * s2min;
+    if (vol_tau(s[0], b, r) * vol_tau(s[1], b, r + 1) * vol_tau(s[2], b, r + 2) > vt) {
+      for (int i = 0; i < 3; ++i) tau[i] = vol_tau(s[i], b, r + i);
       return;
     }
   }
-  for (int it = 0; it < 100; ++it) {
-    double p = 1.0, dg = 0.0, t[3];
+  double c = b, dx = b - a, dxold = dx;
+  for (int it = 0; it < 200; ++it) {
+    double p = 1.0, dg = 0.0;
     for (int i = 0; i < 3; ++i) {
-      t[i] = vol_tau(s[i], c, r + i);
-      p *= t[i];
-      dg -= 1.0 / (r[i] * t[i]);   // d log tau_i / dc = -1 / (r_i tau_i)
+      const double t = vol_tau(s[i], c, r + i);
+      p *= t;
+      dg -= 1.0 / (r[i] * t);   // d log tau_i / dc = -1 / (r_i tau_i)
     }
     const double g = p > 0.0 ? log(p) - lvt : -INFINITY;
+    if (g == 0.0) break;
+    if (g > 0.0) a = c;
+    else b = c;
     const double cn = c - g / dg;
-    if (!(cn >= a && cn <= c)) {          // no finite Newton step here: bisect
-      const double mid = 0.5 * (a + c);
-      if (!(mid > a && mid < c)) break;
-      double pm = 1.0;
-      for (int i = 0; i < 3; ++i) pm *= vol_tau(s[i], mid, r + i);
-      if (pm >= vt) a = mid;
-      else c = mid;
-      continue;
+    const bool newton = isfinite(cn) && cn > a && cn < b && fabs(2.0 * g) <= fabs(dxold * dg);
+    dxold = dx;
+    if (newton) {
+      dx = c - cn;
+      c = cn;
+    } else {
+      dx = 0.5 * (b - a);
+      c = a + dx;
     }
-    if (!(cn < c)) break;                 // converged: no further decrease
-    const bool done = c - cn <= 4e-16 * fabs(c);
-    c = cn;
-    if (done) break;
+    // converged: a step at the resolution of c where g is at rounding level
+    // (a tiny step alone is not enough: near the branch end the slope is huge)
+    if ((fabs(dx) <= 1e-16 * (fabs(c) + s2min) && fabs(g) <= 1e-12) || !(b > a)) break;
   }
   for (int i = 0; i < 3; ++i) tau[i] = vol_tau(s[i], c, r + i);
 }

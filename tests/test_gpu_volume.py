@@ -31,6 +31,19 @@ def _oracle(s, kappa, lo, hi, **kw):
                                kappa=kappa, det_min=lo, det_max=hi, **kw)
 
 
+def _well_conditioned_t(F, T):
+    # T = U diag(tau) V^T on the principal branch tau_i = (s_i + r_i) / 2;
+    # dtau / ds grows like 1 / r_i, so within 5% of the branch end
+    # (min r_i < 0.05 max |s_i|) rounding-level differences in s become
+    # ~sqrt(eps) differences in T: such elements are left out
+    from oracle import pd_oracle
+    U, sv, Vt = pd_oracle.signed_svd(F)
+    tau = np.diagonal(np.swapaxes(U, 1, 2) @ T @ np.swapaxes(Vt, 1, 2), axis1=1, axis2=2)
+    r = np.abs(2.0 * tau - sv)
+    moved = np.abs(T - F).max(axis=(1, 2)) > 0
+    return ~moved | (r.min(axis=1) >= 0.05 * np.abs(sv).max(axis=1))
+
+
 def _unique_r(F):
     # R (and so S's eigenvectors) is unique where the two smallest signed
     # singular values are apart
@@ -55,19 +68,29 @@ def test_local_step_forces_match_oracle(pd, with_strain_limit):
     F = oracle.deformation_gradients(x, o.tets, o.Dm_inv)
     det = np.linalg.det(F)
     assert (det < lo).any() and (det > hi).any() and (det < 0).any()
-    keep = _unique_r(F)
     Ro = o.rotations(x, all_e)
     To = o.volume_targets(x, all_e)
+    keep = _unique_r(F) & _well_conditioned_t(F, To)
     fo = (oracle.elastic_forces(x, Ro, o.tets, o.Dm_inv, o.vol, o.mu)
           + oracle.elastic_forces(x, To, o.tets, o.Dm_inv, o.vol, kappa))
     if with_strain_limit:
         fo += oracle.elastic_forces(x, o.projections(x, all_e), o.tets, o.Dm_inv, o.vol, mp)
-    assert keep.mean() > 0.99
+    assert keep.mean() > 0.97
     assert np.abs(R[keep] - Ro[keep]).max() <= 1e-12
     bad = np.zeros(s.n, bool)
     bad[s.tets[~keep].ravel()] = True
     assert (~bad).sum() > 0.9 * s.n
     assert np.abs(f[~bad] - fo[~bad]).max() <= TOL * np.abs(fo).max()
+
+
+def test_rest_state_has_no_volume_force(pd):
+    # at rest det F = 1 up to rounding, on either side of the bound: T = F up
+    # to rounding (the projection's Newton iteration must not stop at the
+    # branch end, where its slope is unbounded)
+    s = scenes.config1(nx=5, ny=5, nz=8)
+    sol = _solver(pd, s, 1.5 * s.lam, 1.0, 1.0)
+    _, f = sol.local_step(s.X.copy())
+    assert np.abs(f).max() <= 1e-8, np.abs(f).max()
 
 
 @pytest.mark.parametrize("inner", [1, 3])
