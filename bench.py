@@ -166,7 +166,7 @@ def set_detector(sol, s):
     sol.set_detector_triangles(pa, ta, pb, tb, s.info["tri_gap"], s.info["tri_rest_min"], s.stiffness)
 
 
-def form_roofline(pd, prec, m, n_ref, refactor_ms, solve_ms, iters):
+def form_roofline(pd, prec, m, n_ref, refactor_ms, solve_ms, iters, k_active=0):
     """Roofline of a form's dominant work.  FP64: the dense refactorisation
     (n_ref^3 / 3 flop) against the derived FP64 ALU peak.  Low-precision forms:
     the same algorithmic flops against the tensor peak of the operand type
@@ -177,9 +177,12 @@ def form_roofline(pd, prec, m, n_ref, refactor_ms, solve_ms, iters):
     if prec == pd.PCG_WARM:
         if solve_ms <= 0:
             return None
-        ach = iters * 12.0 * m * m / (solve_ms / 1e3) / 1e9
-        return {"bound": "hbm", "work": "PCG iterations (k_symv_df + k_minv_apply)", "achieved": ach, "peak": hbm,
-                "unit": "GB/s", "frac": ach / hbm, "peak_source": src}
+        # per iteration: Sigma_0 as an FP32 pair (8 m^2 B), the FP32 inverse
+        # (4 m^2 B) and, with the capacitance correction, the FP32 rows Y (4 k m B)
+        ach = iters * (12.0 * m * m + 4.0 * k_active * m) / (solve_ms / 1e3) / 1e9
+        return {"bound": "hbm", "work": "PCG iterations (k_symv_df + k_minv_apply%s)" % (
+                    " + k_cap_part, k = %d" % k_active if k_active else ""),
+                "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "peak_source": src}
     if refactor_ms <= 0:
         return None
     ach = n_ref ** 3 / 3.0 / (refactor_ms / 1e3) / 1e12
@@ -198,7 +201,7 @@ def active_springs(sol):
     return int((c > 0).sum())
 
 
-def time_form(pd, sol, stream, args, fp64_ms, torch, prec, nested):
+def time_form(pd, sol, stream, args, fp64_ms, torch, prec, nested, cap=False):
     """Device-timed steps of one form on the current state: ms per step, PD
     iters/s, speedup over the FP64 form, the Schur contact update + refactor
     + solve time (and the refactorisation alone), refinement iterations, the
@@ -233,7 +236,8 @@ def time_form(pd, sol, stream, args, fp64_ms, torch, prec, nested):
             "schur_refactor_solve_ms": schur / k, "refactor_ms": ref / k, "refine_iters": iters / k,
             "max_rel_residual": res if res > 0 else None,   # None: the direct FP64 solve measures none
             "active_springs": active_springs(sol),
-            "roofline": form_roofline(pd, prec, s.m, n_ref, ref / k, (fs - ref) / k, iters / k)}
+            "roofline": form_roofline(pd, prec, s.m, n_ref, ref / k, (fs - ref) / k, iters / k,
+                                      active_springs(sol) if cap else 0)}
 
 
 def time_forms(pd, sol, stream, args, fp64_ms, torch):
@@ -244,11 +248,17 @@ def time_forms(pd, sol, stream, args, fp64_ms, torch):
     out = {}
     s = sol._scene
     state = sol.get_state()
-    for name, prec in (("fp32_ir (split-TF32 tcgen05)", pd.FP32_IR), ("tf32_ir (TF32 tcgen05, CG-refined)", pd.TF32_IR),
-                       ("bf16_ir (BF16 tcgen05, CG-refined)", pd.BF16_IR), ("pcg (contact-free preconditioner, cold start)", pd.PCG_WARM)):
+    for name, prec, cap in (("fp32_ir (split-TF32 tcgen05)", pd.FP32_IR, True),
+                            ("tf32_ir (TF32 tcgen05, CG-refined)", pd.TF32_IR, True),
+                            ("bf16_ir (BF16 tcgen05, CG-refined)", pd.BF16_IR, True),
+                            ("pcg (contact-free preconditioner M0, cold start)", pd.PCG_WARM, False),
+                            ("pcg_capacitance (M0 + Woodbury correction for the active springs, cold start)",
+                             pd.PCG_WARM, True)):
         sol.set_state(*state)
         sol.set_precision(prec)
-        out[name] = time_form(pd, sol, stream, args, fp64_ms, torch, prec, False)
+        sol.set_pcg_capacitance(cap)
+        out[name] = time_form(pd, sol, stream, args, fp64_ms, torch, prec, False, cap and prec == pd.PCG_WARM)
+    sol.set_pcg_capacitance(True)
     # the nested Schur refactorisation on the contact-capable nodes (FP64 and split-TF32)
     npx = len(s.proxies)
     for name, prec in (("fp64_nested (FP64; Schur block of the %d contact nodes refactored, rest factored once)" % npx,

@@ -52,7 +52,10 @@ enum {
      * held as an FP32 head + tail pair (~48 bits) in double-float arithmetic,
      * the contact term C_22 u in FP64.                                         */
     PD_PCG_WARM = 4   /* PCG on H preconditioned by the contact-free factor of Sigma,
-                         started from a caller-supplied (e.g. learned) guess        */
+                         started from a caller-supplied (e.g. learned) guess; the
+                         preconditioner carries the active springs exactly through
+                         a capacitance (Woodbury) correction unless
+                         pd_set_pcg_capacitance turns it off                        */
 };
 
 typedef struct {
@@ -376,6 +379,17 @@ pd_status pd_tc_rank_k(int mode, const float* A, const float* B, float* C, int64
  * pd_stats.starts_rejected, so a poor prediction never starts PCG farther
  * from the answer than the cold start. */
 pd_status pd_set_warm_start(pd_solver* s, int source);
+
+/* Capacitance correction of the PD_PCG_WARM preconditioner (beyond the
+ * paper; on by default).  M0 (the FP32 factor of the contact-free Sigma_0,
+ * Section 3.3) leaves one outlier eigenvalue of M0^-1 H per active spring.
+ * With the correction, each refactorisation step instead gathers the k
+ * active springs' rows V = C^1/2 W, forms Y = V M0^-1 and the k x k matrix
+ * S = I + V M0^-1 V^T, and factors S in FP64; each PCG iteration then
+ * applies P^-1 r = M0^-1 r - Y^T S^-1 V M0^-1 r (the Woodbury identity for
+ * P = M0 + W^T C W).  The solve still meets tol against the FP64-accurate
+ * residual of H.  on = 0 uses M0 alone.  Errors: INVALID_ARG (NULL s). */
+pd_status pd_set_pcg_capacitance(pd_solver* s, int on);
 
 /* Set / read the network parameters (n must be PD_MLP_NPARAMS); setting them
  * resets the optimiser state. */

@@ -87,6 +87,7 @@ _sigs = {
     "pd_set_inner_iters": (ctypes.c_int, [P, ctypes.c_int]),
     "pd_debug_wait_timeout": (ctypes.c_int, [P]),
     "pd_set_warm_start": (ctypes.c_int, [P, ctypes.c_int]),
+    "pd_set_pcg_capacitance": (ctypes.c_int, [P, ctypes.c_int]),
     "pd_mlp_set_params": (ctypes.c_int, [P, P, I64]),
     "pd_mlp_get_params": (ctypes.c_int, [P, P, I64]),
     "pd_mlp_record": (ctypes.c_int, [P, I64]),

@@ -75,6 +75,23 @@ struct MixedState {
   int ll_ctas = 0;            // PD_LOWP_CTAS: cap on the persistent factorisation's grid (0: two thirds of the SMs)
   cudaStream_t side = nullptr;              // low-priority stream for the bulk trailing updates
   std::vector<cudaEvent_t> ev_panel, ev_rest;
+  // Capacitance (Woodbury) correction of the PCG form's preconditioner: with
+  // V = C^1/2 W over the active springs, P^-1 = M0^-1 - Y^T S^-1 V M0^-1,
+  // Y = V M0^-1 [kact][ldm] (rows of the explicit inverse, FP32) and
+  // S = I + V M0^-1 V^T [kp][kp] (FP64, column-major, identity padding,
+  // factored by the FP64 blocked Cholesky); P = M0 + C_22 up to the FP32
+  // inverse, so the one outlier eigenvalue per spring of M0^-1 H is removed.
+  int64_t cap_rows = 0;       // spring slots the buffers below hold
+  int64_t cap_kp = 0;         // order of Scap (kact rounded up to 64)
+  int64_t kact = 0;           // active springs of the current solve (0: no correction)
+  int* cap_act = nullptr;     // [cap_rows] slot of each active spring, in slot order
+  int* cap_cnt = nullptr;     // [1] active count; cap_cnt_h its pinned copy
+  int* cap_cnt_h = nullptr;
+  float* Y = nullptr;
+  double *Scap = nullptr, *Slinv = nullptr;   // S and the inverses of its 64 x 64 diagonal tiles
+  double *ct = nullptr, *cy = nullptr, *cwork = nullptr;   // [kp][3] V z, S^-1 V z; [kp][3] x 2 solve work
+  double* cpart = nullptr;    // [kp / 64][m][3] chunk partial sums of Y^T S^-1 V z
+  int *ccnt = nullptr, *cstat = nullptr;     // solve task counters; factor status
 };
 
 namespace {
@@ -868,6 +885,151 @@ __global__ void k_cg_dir2(double* p, const double* z, double* sc, int a, int b, 
   hi[i] = h;
   lo[i] = (float)(v - (double)h);
 }
+// ---- capacitance correction of the PCG preconditioner (Woodbury identity)
+// Active springs (stiffness > 0 and at least one node in the region) in slot
+// order, by one block scanning the slots in chunks of blockDim.x (a
+// multiple of 32, at most 1024): deterministic, unlike an atomic append.
+__global__ void k_cap_active(int64_t k, const int32_t* __restrict__ cidx, const double* __restrict__ cs,
+                             int* __restrict__ act, int* __restrict__ cnt) {
+  constexpr int NS = pdk::CSLOTS;
+  __shared__ int wsum[32], woff[32];
+  __shared__ int base, tot;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  for (int64_t j0 = 0; j0 < k; j0 += blockDim.x) {
+    const int64_t j = j0 + threadIdx.x;
+    bool on = false;
+    if (j < k && cs[j] > 0.0)
+      for (int a = 0; a < NS; ++a) on |= cidx[NS * j + a] >= 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, on);
+    if (lane == 0) wsum[wp] = __popc(bal);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int acc = 0;
+      for (int q = 0; q < nw; ++q) { woff[q] = acc; acc += wsum[q]; }
+      tot = acc;
+    }
+    __syncthreads();
+    if (on) act[base + woff[wp] + __popc(bal & ((1u << lane) - 1u))] = (int)j;
+    __syncthreads();
+    if (threadIdx.x == 0) base += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *cnt = base;
+}
+// Y[a][:] = sqrt(c_j) sum_s w_js Minv0[node_js][:] for active spring a = slot j
+// (the rows of V M0^-1; the padding columns of Minv0 are zero).
+__global__ void k_cap_rows(const int* __restrict__ act, const int32_t* __restrict__ cidx,
+                           const double* __restrict__ cw, const double* __restrict__ cs,
+                           const float* __restrict__ Mi, int64_t ldm, float* __restrict__ Y) {
+  constexpr int NS = pdk::CSLOTS;
+  const int64_t a = blockIdx.y;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= ldm) return;
+  const int j = act[a];
+  const double sc = sqrt(cs[j]);
+  float acc = 0.f;
+  for (int q = 0; q < NS; ++q) {
+    const int r = cidx[NS * j + q];
+    if (r < 0) continue;
+    acc = fmaf((float)(sc * cw[NS * j + q]), __ldg(Mi + (int64_t)r * ldm + i), acc);
+  }
+  Y[a * ldm + i] = acc;
+}
+// S = I + V M0^-1 V^T (symmetrised), kp x kp column-major, identity padding.
+__global__ void k_cap_matrix(int64_t kact, int64_t kp, const int* __restrict__ act, const int32_t* __restrict__ cidx,
+                             const double* __restrict__ cw, const double* __restrict__ cs,
+                             const float* __restrict__ Y, int64_t ldm, double* __restrict__ S) {
+  constexpr int NS = pdk::CSLOTS;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= kp * kp) return;
+  const int64_t a = t % kp, b = t / kp;
+  if (a >= kact || b >= kact) {
+    S[t] = a == b ? 1.0 : 0.0;
+    return;
+  }
+  const int ja = act[a], jb = act[b];
+  const double sa = sqrt(cs[ja]), sb = sqrt(cs[jb]);
+  double h1 = 0.0, h2 = 0.0;
+  for (int q = 0; q < NS; ++q) {
+    const int ra = cidx[NS * ja + q];
+    if (ra >= 0) h1 += sa * cw[NS * ja + q] * (double)Y[b * ldm + ra];
+    const int rb = cidx[NS * jb + q];
+    if (rb >= 0) h2 += sb * cw[NS * jb + q] * (double)Y[a * ldm + rb];
+  }
+  S[t] = (a == b ? 1.0 : 0.0) + 0.5 * (h1 + h2);
+}
+// t[a][:] = sqrt(c_j) sum_s w_js z[node_js][:]  (V z, 3 right-hand sides)
+__global__ void k_cap_gather(int64_t kact, const int* __restrict__ act, const int32_t* __restrict__ cidx,
+                             const double* __restrict__ cw, const double* __restrict__ cs,
+                             const double* __restrict__ z, double* __restrict__ t) {
+  constexpr int NS = pdk::CSLOTS;
+  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a >= kact) return;
+  const int j = act[a];
+  const double sc = sqrt(cs[j]);
+  double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+  for (int q = 0; q < NS; ++q) {
+    const int r = cidx[NS * j + q];
+    if (r < 0) continue;
+    const double w = sc * cw[NS * j + q];
+    t0 += w * z[3 * r]; t1 += w * z[3 * r + 1]; t2 += w * z[3 * r + 2];
+  }
+  t[3 * a] = t0; t[3 * a + 1] = t1; t[3 * a + 2] = t2;
+}
+// part[ch][i][:] = sum over the springs a of chunk ch (kCapChunk of them) of
+// Y[a][i] y[a][:]  (FP64 accumulation of the FP32 rows)
+constexpr int kCapChunk = 64;
+__global__ void k_cap_part(int64_t m, int64_t kact, const float* __restrict__ Y, int64_t ldm,
+                           const double* __restrict__ y, double* __restrict__ part) {
+  __shared__ double ys[3 * kCapChunk];
+  const int64_t ch = blockIdx.y, a0 = ch * kCapChunk;
+  const int na = (int)(kact - a0 < kCapChunk ? kact - a0 : kCapChunk);
+  for (int t = threadIdx.x; t < 3 * na; t += blockDim.x) ys[t] = y[3 * a0 + t];
+  __syncthreads();
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const float* Yc = Y + a0 * ldm + i;
+  double c0 = 0.0, c1 = 0.0, c2 = 0.0;
+  for (int a = 0; a < na; ++a) {
+    const double v = (double)__ldg(Yc + a * ldm);
+    c0 = fma(v, ys[3 * a], c0);
+    c1 = fma(v, ys[3 * a + 1], c1);
+    c2 = fma(v, ys[3 * a + 2], c2);
+  }
+  double* o = part + (ch * m + i) * 3;
+  o[0] = c0; o[1] = c1; o[2] = c2;
+}
+// z -= sum over the chunks of part (in chunk order), and acc += r . z after
+// the correction (one atomic per block)
+__global__ void k_cap_apply(int64_t m, int nch, const double* __restrict__ part, double* __restrict__ z,
+                            const double* __restrict__ r, double* __restrict__ acc) {
+  __shared__ double red[8];
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  double rz = 0.0;
+  if (i < m) {
+    double c0 = 0.0, c1 = 0.0, c2 = 0.0;
+    for (int ch = 0; ch < nch; ++ch) {
+      const double* p = part + (ch * m + i) * 3;
+      c0 += p[0]; c1 += p[1]; c2 += p[2];
+    }
+    const double z0 = z[3 * i] - c0, z1 = z[3 * i + 1] - c1, z2 = z[3 * i + 2] - c2;
+    z[3 * i] = z0; z[3 * i + 1] = z1; z[3 * i + 2] = z2;
+    rz = r[3 * i] * z0 + r[3 * i + 1] * z1 + r[3 * i + 2] * z2;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) rz += __shfl_xor_sync(0xffffffffu, rz, o);
+  if (lane == 0) red[wp] = rz;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+    atomicAdd(acc, t);
+  }
+}
+
 // z = Minv0 r32 as k_minv_apply, and sc[slot] += r . z (r in FP64; one atomic per block)
 __global__ void k_minv_apply_dot(const float* __restrict__ Mi, int64_t m, int64_t ld, const float* __restrict__ r32,
                                  const double* __restrict__ r, double* __restrict__ z, double* __restrict__ acc) {
@@ -1131,6 +1293,78 @@ static pd_status build_minv(pd_solver* s) {
   return PD_OK;
 }
 
+// (Re)allocate a device buffer owned by the solver (freed in pd_destroy).
+static bool dev_realloc(pd_solver* s, void** ptr, size_t bytes) {
+  if (*ptr) {
+    for (auto it = s->allocs.begin(); it != s->allocs.end(); ++it)
+      if (*it == *ptr) { s->allocs.erase(it); break; }
+    cudaFree(*ptr);
+    *ptr = nullptr;
+  }
+  if (cudaMalloc(ptr, bytes) != cudaSuccess) { *ptr = nullptr; return false; }
+  s->allocs.push_back(*ptr);
+  return true;
+}
+
+// The capacitance correction for the current springs (PCG form): the active
+// springs, Y = V M0^-1, S = I + V M0^-1 V^T and its FP64 Cholesky factor.
+// The active count is read back to the host (one synchronisation of the
+// stream), since it sizes S.
+static pd_status build_capacitance(pd_solver* s) {
+  MixedState* M = s->mixed;
+  M->kact = 0;
+  if (!s->pcg_capacitance || s->k <= 0) return PD_OK;
+  cudaStream_t st = s->stream;
+  if (s->k > M->cap_rows) {
+    const int64_t rows = s->k, kp = (rows + 63) / 64 * 64;
+    bool ok = dev_realloc(s, (void**)&M->cap_act, sizeof(int) * rows) &&
+              dev_realloc(s, (void**)&M->Y, sizeof(float) * rows * M->ldm) &&
+              dev_realloc(s, (void**)&M->Scap, sizeof(double) * kp * kp) &&
+              dev_realloc(s, (void**)&M->Slinv, sizeof(double) * kp * 64) &&
+              dev_realloc(s, (void**)&M->ct, sizeof(double) * 3 * kp) &&
+              dev_realloc(s, (void**)&M->cy, sizeof(double) * 3 * kp) &&
+              dev_realloc(s, (void**)&M->cwork, sizeof(double) * 6 * kp) &&
+              dev_realloc(s, (void**)&M->ccnt, sizeof(int) * (2 + 2 * (kp / 64))) &&
+              dev_realloc(s, (void**)&M->cpart, sizeof(double) * 3 * s->m * (kp / kCapChunk));
+    if (!M->cap_cnt) ok = ok && dev_realloc(s, (void**)&M->cap_cnt, sizeof(int)) &&
+                          dev_realloc(s, (void**)&M->cstat, sizeof(int) * 4) &&
+                          cudaMallocHost(&M->cap_cnt_h, sizeof(int)) == cudaSuccess;
+    if (!ok) { s->err = "device allocation for the capacitance correction failed"; return PD_ERR_OOM; }
+    M->cap_rows = rows;
+  }
+  k_cap_active<<<1, 1024, 0, st>>>(s->k, s->c_idx, s->c_s, M->cap_act, M->cap_cnt);
+  ++pdk::g_launches;
+  cudaMemcpyAsync(M->cap_cnt_h, M->cap_cnt, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) { s->err = "capacitance set-up failed"; return PD_ERR_CUDA; }
+  const int64_t kact = *M->cap_cnt_h;
+  if (kact <= 0) return PD_OK;
+  const int64_t kp = (kact + 63) / 64 * 64;
+  k_cap_rows<<<dim3(nblk(M->ldm, 256), (unsigned)kact), 256, 0, st>>>(M->cap_act, s->c_idx, s->c_w, s->c_s,
+                                                                      M->Minv0, M->ldm, M->Y);
+  k_cap_matrix<<<nblk(kp * kp, 256), 256, 0, st>>>(kact, kp, M->cap_act, s->c_idx, s->c_w, s->c_s, M->Y,
+                                                   M->ldm, M->Scap);
+  pdk::g_launches += 2;
+  cudaMemsetAsync(M->cstat, 0, sizeof(int) * 4, st);
+  pdk::cholesky_fp64(M->Scap, kp, M->Slinv, M->cstat, st);
+  M->kact = kact;
+  M->cap_kp = kp;
+  return PD_OK;
+}
+
+// z = P^-1 r with the capacitance correction, acc += r . z; r32 holds r in FP32
+static void apply_cap_dot(pd_solver* s, const double* r, double* z, double* acc) {
+  MixedState* M = s->mixed;
+  cudaStream_t st = s->stream;
+  k_minv_apply<<<nblk(32 * s->m, 256), 256, 0, st>>>(M->Minv0, s->m, M->ldm, M->r32, z);
+  k_cap_gather<<<nblk(M->kact, 128), 128, 0, st>>>(M->kact, M->cap_act, s->c_idx, s->c_w, s->c_s, z, M->ct);
+  pdk::g_launches += 2;
+  pdk::chol_solve_fp64_tasks(M->Scap, M->cap_kp, M->Slinv, M->ct, M->cy, M->kact, M->cwork, M->ccnt, s->status, st);
+  const int nch = (int)((M->kact + kCapChunk - 1) / kCapChunk);
+  k_cap_part<<<dim3(nblk(s->m, 256), (unsigned)nch), 256, 0, st>>>(s->m, M->kact, M->Y, M->ldm, M->cy, M->cpart);
+  k_cap_apply<<<nblk(s->m, 256), 256, 0, st>>>(s->m, nch, M->cpart, z, r, acc);
+  pdk::g_launches += 2;
+}
+
 static void apply_minv(pd_solver* s, const double* r, double* z) {
   MixedState* M = s->mixed;
   k_to_f32<<<nblk(3 * s->m, 256), 256, 0, s->stream>>>(r, 3 * s->m, M->r32);
@@ -1207,7 +1441,14 @@ pd_status mixed_factor(pd_solver* s) {
   pd_status rs = ensure_state(s);
   if (rs != PD_OK) return rs;
   MixedState* M = s->mixed;
-  if (s->precision == PD_PCG_WARM) return build_minv(s);
+  if (s->precision == PD_PCG_WARM) {
+    rs = build_minv(s);
+    if (rs != PD_OK) return rs;
+    s->tbegin(8);
+    rs = build_capacitance(s);
+    s->tend();
+    return rs;
+  }
   const pdtc::Mode mode = form_mode(s);
   cudaMemsetAsync(M->lpiv, 0, sizeof(int), s->stream);
   if (s->nested) {
@@ -1320,7 +1561,9 @@ pd_status mixed_iterate(pd_solver* s, const double* g, const double* u0, double*
     // r.z alternates between slots 1 and 5, p.q uses slot 2, each zeroed by the kernel before its use
     auto rzs = [](int64_t k) { return (k & 1) ? 1 : 5; };
     auto minv_dot = [&](int slot) {   // z = M^-1 r, sc[slot] = r.z (slot zeroed beforehand)
-      if (warm) {
+      if (warm && M->kact > 0) {
+        apply_cap_dot(s, M->r, M->z, M->sc + slot);
+      } else if (warm) {
         k_minv_apply_dot<<<nblk(32 * s->m, 256), 256, 0, st>>>(M->Minv0, s->m, M->ldm, M->r32, M->r, M->z,
                                                                 M->sc + slot);
         ++pdk::g_launches;
@@ -1443,6 +1686,7 @@ void mixed_free(pd_solver* s) {
   if (!s->mixed) return;
   if (s->mixed->sc_h) cudaFreeHost(s->mixed->sc_h);
   if (s->mixed->lpiv_h) cudaFreeHost(s->mixed->lpiv_h);
+  if (s->mixed->cap_cnt_h) cudaFreeHost(s->mixed->cap_cnt_h);
   for (auto e : s->mixed->ev_panel) cudaEventDestroy(e);
   for (auto e : s->mixed->ev_rest) cudaEventDestroy(e);
   if (s->mixed->side) cudaStreamDestroy(s->mixed->side);

@@ -744,6 +744,12 @@ pd_status pd_set_warm_start(pd_solver* s, int source) {
   return PD_OK;
 }
 
+pd_status pd_set_pcg_capacitance(pd_solver* s, int on) {
+  if (!s) return PD_ERR_INVALID_ARG;
+  s->pcg_capacitance = on != 0;
+  return PD_OK;
+}
+
 pd_status pd_mlp_set_params(pd_solver* s, const float* params, int64_t n) {
   if (!s || !params || n != pdn::NPARAMS) {
     if (s) s->err = "expected " + std::to_string(pdn::NPARAMS) + " parameters";

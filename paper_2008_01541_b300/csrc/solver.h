@@ -87,6 +87,7 @@ struct pd_solver {
   pdn::Net* net = nullptr;       // learned warm start
   bool mlp_recording = false;
   int warm_source = 0;           // PD_PCG_WARM start: 0 zero, 1 previous solution, 2 network
+  bool pcg_capacitance = true;   // PD_PCG_WARM: Woodbury correction of M0 for the active springs
   double* u_last = nullptr;      // [m][3] solution of the previous region solve
   std::vector<double> X_rest_h;  // rest positions (host)
   int last_refine = 0;

@@ -224,8 +224,12 @@ class Solver:
 
     # ---- learned warm start (PD_PCG_WARM) ----
     def set_warm_start(self, source):
-        """0 = zero, 1 = previous region solution, 2 = network prediction."""
+        """0 = zero, 1 = previous region solution, 2 = network prediction, 3 = z0."""
         self._check(lib.pd_set_warm_start(self.h, int(source)))
+
+    def set_pcg_capacitance(self, on):
+        """Capacitance (Woodbury) correction of the PCG preconditioner for the active springs."""
+        self._check(lib.pd_set_pcg_capacitance(self.h, 1 if on else 0))
 
     def mlp_set_params(self, params):
         p = _c(params, np.float32).ravel()

@@ -100,6 +100,13 @@ def test_full_elbow_bench_step_matches_oracle(pd, elbow):
     sol.set_detector_triangles(pa, ta, pb, tb, s.info["tri_gap"], s.info["tri_rest_min"], s.stiffness)
     sol.step(1)
     xg = sol.positions()
+    # the PCG form with the capacitance correction, same step
+    sol.set_precision(pd.PCG_WARM)
+    sol.set_state(x0)
+    sol.step(1)
+    xp = sol.positions()
+    pcg_iters = sol.stats()["refine_iters"]
+    sol.set_precision(pd.FP64)
     sol.clear_detector()
     fn = _tri_oracle(s)
     assert fn(x0).k > 100
@@ -107,6 +114,8 @@ def test_full_elbow_bench_step_matches_oracle(pd, elbow):
     o.x = x0.copy()
     xo = o.step(1, 1, fn, dpos)
     assert_parity(xg, xo, x0, TOL)
+    assert_parity(xp, xo, x0, MIXED_STEP_TOL, "PCG_WARM + capacitance")
+    assert pcg_iters <= 8, pcg_iters
 
 
 def test_full_elbow_resampled_contacts_mixed_forms(pd, elbow):

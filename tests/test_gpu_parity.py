@@ -211,6 +211,12 @@ def test_two_sided_springs_match_oracle(pd):
     g = rng(31).normal(size=(s.m, 3)) * 1e3
     u = sol.schur_solve(g)
     assert np.linalg.norm(g - H @ u) / np.linalg.norm(g) <= TOL
+    # the PCG form's capacitance correction with 8-slot rows
+    sol.set_precision(pd.PCG_WARM)
+    u = sol.schur_solve(g)
+    assert np.linalg.norm(g - H @ u) / np.linalg.norm(g) <= TOL
+    assert sol.stats()["refine_iters"] <= 8
+    sol.set_precision(pd.FP64)
     # one outer iteration with the pairs re-detected at every inner iteration
     sol.set_state(x0)
     sol.set_dirichlet(s.dirichlet_positions(50))
