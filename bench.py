@@ -59,6 +59,10 @@ def parse():
                     help="also measure inner = 3 and 5 and the Schur refactor+solve median / p90 over repeated solves")
     ap.add_argument("--nested", action="store_true",
                     help="main timed region with pd_set_contact_nodes on the proxies (nested Schur refactorisation)")
+    ap.add_argument("--config5", action="store_true",
+                    help="run configuration 5 at its full size (20K method-generated solves split 18K/1K/1K, the "
+                         "network trained on the device, held-out PCG iterations and ms by start) and print its "
+                         "JSON instead of the bench line (about 5 minutes)")
     ap.add_argument("--profile-step", action="store_true",
                     help="after warm-up run one step between cudaProfilerStart/Stop (for ncu --profile-from-start off) "
                          "and exit; prints no measurement")
@@ -520,6 +524,38 @@ def time_learned(pd, sol, stream, args, fp64_ms, torch, state):
     return {"pcg_learned (network warm start)": r}
 
 
+def run_config5(pd, s, stream, torch):
+    """Configuration 5 as specified: the learned warm start trained on 18K
+    method-generated region solves from seeded random indenter paths on the
+    elbow, validated on 1K and tested on 1K held-out solves (disjoint paths);
+    PCG iterations and device ms per step from each start, with the
+    contact-free preconditioner alone and with its capacitance correction,
+    beside the split-TF32 refactorisation."""
+    from paper_2008_01541_b300 import warmstart as ws
+    sol = pd.Solver(s.X, s.tets, s.region, s.dirichlet, s.mu, 0.0, 0.0, 0.0, stream=stream.cuda_stream,
+                    timing=True, max_refine=1000)
+    sol.set_dirichlet(s.dirichlet_positions(s.info["rest_step"]))
+    state = sol.get_state()
+
+    def timer(fn):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    t0 = time.perf_counter()
+    r = ws.config5(sol, s, state, timer=timer)
+    r["wall_s"] = time.perf_counter() - t0
+    r["workload"] = "elbow %d tets, m = %d, indenter springs detected on the device" % (s.E, s.m)
+    sol.close()
+    print(json.dumps({"config5": r}), flush=True)
+    return 0
+
+
 def frozen_contacts(sol, s):
     """The springs the device detector found in the current state, as host
     arrays in node ids (empty slots dropped)."""
@@ -682,6 +718,8 @@ def main():
             "pcg": pd.PCG_WARM}[args.precision]
     s = scenes.elbow(h=args.h, seed=rank)
     stream = torch.cuda.Stream()
+    if args.config5:
+        return run_config5(pd, s, stream, torch)
     t_setup = time.perf_counter()
     sol = pd.Solver(s.X, s.tets, s.region, s.dirichlet, s.mu, 0.0, 0.0, 0.0, precision=prec,
                     inner_iters=1, stream=stream.cuda_stream, timing=True, max_refine=500)

@@ -92,6 +92,8 @@ struct MixedState {
   double *ct = nullptr, *cy = nullptr, *cwork = nullptr;   // [kp][3] V z, S^-1 V z; [kp][3] x 2 solve work
   double* cpart = nullptr;    // [kp / 64][m][3] chunk partial sums of Y^T S^-1 V z
   int *ccnt = nullptr, *cstat = nullptr;     // solve task counters; factor status
+  bool cap_pending = false;   // active springs counted (ev_cap), S not yet built
+  cudaEvent_t ev_cap = nullptr, ev_capdone = nullptr;
 };
 
 namespace {
@@ -1306,13 +1308,18 @@ static bool dev_realloc(pd_solver* s, void** ptr, size_t bytes) {
   return true;
 }
 
-// The capacitance correction for the current springs (PCG form): the active
-// springs, Y = V M0^-1, S = I + V M0^-1 V^T and its FP64 Cholesky factor.
-// The active count is read back to the host (one synchronisation of the
-// stream), since it sizes S.
-static pd_status build_capacitance(pd_solver* s) {
+// The capacitance correction for the current springs (PCG form), in two
+// parts.  cap_begin (with the refactorisation, on its stream): the active
+// springs in slot order and their count, copied to the host behind ev_cap.
+// cap_finish (at the solve, once the host has issued the local steps and
+// the substitutions): wait for the count, which sizes S, then on the factor
+// stream Y = V M0^-1, S = I + V M0^-1 V^T and its FP64 Cholesky factor; the
+// solver stream waits for them.  The host never waits before the local step
+// is queued, so the factorisation of S overlaps it on the device.
+static pd_status cap_begin(pd_solver* s) {
   MixedState* M = s->mixed;
   M->kact = 0;
+  M->cap_pending = false;
   if (!s->pcg_capacitance || s->k <= 0) return PD_OK;
   cudaStream_t st = s->stream;
   if (s->k > M->cap_rows) {
@@ -1328,17 +1335,31 @@ static pd_status build_capacitance(pd_solver* s) {
               dev_realloc(s, (void**)&M->cpart, sizeof(double) * 3 * s->m * (kp / kCapChunk));
     if (!M->cap_cnt) ok = ok && dev_realloc(s, (void**)&M->cap_cnt, sizeof(int)) &&
                           dev_realloc(s, (void**)&M->cstat, sizeof(int) * 4) &&
-                          cudaMallocHost(&M->cap_cnt_h, sizeof(int)) == cudaSuccess;
+                          cudaMallocHost(&M->cap_cnt_h, sizeof(int)) == cudaSuccess &&
+                          cudaEventCreateWithFlags(&M->ev_cap, cudaEventDisableTiming) == cudaSuccess &&
+                          cudaEventCreateWithFlags(&M->ev_capdone, cudaEventDisableTiming) == cudaSuccess;
     if (!ok) { s->err = "device allocation for the capacitance correction failed"; return PD_ERR_OOM; }
     M->cap_rows = rows;
   }
   k_cap_active<<<1, 1024, 0, st>>>(s->k, s->c_idx, s->c_s, M->cap_act, M->cap_cnt);
   ++pdk::g_launches;
   cudaMemcpyAsync(M->cap_cnt_h, M->cap_cnt, sizeof(int), cudaMemcpyDeviceToHost, st);
-  if (cudaStreamSynchronize(st) != cudaSuccess) { s->err = "capacitance set-up failed"; return PD_ERR_CUDA; }
+  cudaEventRecord(M->ev_cap, st);
+  M->cap_pending = true;
+  return PD_OK;
+}
+
+static pd_status cap_finish(pd_solver* s) {
+  MixedState* M = s->mixed;
+  M->cap_pending = false;
+  if (cudaEventSynchronize(M->ev_cap) != cudaSuccess) { s->err = "capacitance set-up failed"; return PD_ERR_CUDA; }
   const int64_t kact = *M->cap_cnt_h;
   if (kact <= 0) return PD_OK;
   const int64_t kp = (kact + 63) / 64 * 64;
+  cudaStream_t main_stream = s->stream;
+  s->stream = s->fstream;
+  cudaStream_t st = s->stream;
+  s->tbegin(8);
   k_cap_rows<<<dim3(nblk(M->ldm, 256), (unsigned)kact), 256, 0, st>>>(M->cap_act, s->c_idx, s->c_w, s->c_s,
                                                                       M->Minv0, M->ldm, M->Y);
   k_cap_matrix<<<nblk(kp * kp, 256), 256, 0, st>>>(kact, kp, M->cap_act, s->c_idx, s->c_w, s->c_s, M->Y,
@@ -1346,6 +1367,10 @@ static pd_status build_capacitance(pd_solver* s) {
   pdk::g_launches += 2;
   cudaMemsetAsync(M->cstat, 0, sizeof(int) * 4, st);
   pdk::cholesky_fp64(M->Scap, kp, M->Slinv, M->cstat, st);
+  s->tend();
+  s->stream = main_stream;
+  cudaEventRecord(M->ev_capdone, st);
+  cudaStreamWaitEvent(main_stream, M->ev_capdone, 0);
   M->kact = kact;
   M->cap_kp = kp;
   return PD_OK;
@@ -1444,10 +1469,7 @@ pd_status mixed_factor(pd_solver* s) {
   if (s->precision == PD_PCG_WARM) {
     rs = build_minv(s);
     if (rs != PD_OK) return rs;
-    s->tbegin(8);
-    rs = build_capacitance(s);
-    s->tend();
-    return rs;
+    return cap_begin(s);
   }
   const pdtc::Mode mode = form_mode(s);
   cudaMemsetAsync(M->lpiv, 0, sizeof(int), s->stream);
@@ -1505,29 +1527,39 @@ pd_status mixed_iterate(pd_solver* s, const double* g, const double* u0, double*
   const bool warm = s->precision == PD_PCG_WARM;
   const pdtc::Mode mode = form_mode(s);
   Factor* f = warm ? &M->f0 : &M->f;
+  if (warm && M->cap_pending) {
+    rs = cap_finish(s);
+    if (rs != PD_OK) return rs;
+  }
   s->tbegin(4);
-  // u = u0 (or 0); r = g - H u
-  if (u0) cudaMemcpyAsync(u, u0, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st);
-  else cudaMemsetAsync(u, 0, sizeof(double) * n3, st);
-  hmatvec(s, u, M->q);
-  k_sub<<<nblk(n3, 256), 256, 0, st>>>(g, M->q, M->r, n3); ++pdk::g_launches;
+  // u = u0 (or 0); r = g - H u (r = g for the zero start, no product).  The
+  // scalars the start needs (g.g, r.r; for a supplied start u.r and g.u)
+  // come back to the host with the lost-pivot word in one synchronisation.
+  if (u0) {
+    cudaMemcpyAsync(u, u0, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st);
+    hmatvec(s, u, M->q);
+    k_sub<<<nblk(n3, 256), 256, 0, st>>>(g, M->q, M->r, n3); ++pdk::g_launches;
+    dot(s, M->r, M->r, 0);
+    dot(s, u, M->r, 6);
+    dot(s, g, u, 7);
+  } else {
+    cudaMemsetAsync(u, 0, sizeof(double) * n3, st);
+    cudaMemcpyAsync(M->r, g, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st);
+  }
   dot(s, g, g, 4);
-  dot(s, M->r, M->r, 0);
   cudaMemcpyAsync(M->lpiv_h, M->lpiv, sizeof(int), cudaMemcpyDeviceToHost, st);
-  const double gg = read_slot(s, 4);   // (synchronises: lpiv_h is current)
+  cudaMemcpyAsync(M->sc_h, M->sc, sizeof(double) * 8, cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  const double gg = M->sc_h[4];
   const int lost_pivot = warm ? 0 : *M->lpiv_h;
   const double tol2 = s->opt.tol * s->opt.tol * (gg > 0 ? gg : 1.0);
-  double rr = read_slot(s, 0);
+  double rr = u0 ? M->sc_h[0] : gg;
   if (u0) {
     // CG decreases phi(u) = u^T H u / 2 - g^T u = -(u . r + g . u) / 2 with
     // r = g - H u, and phi(u) - phi(u*) = ||u - u*||_H^2 / 2: a start with
     // phi(u0) >= phi(0) = 0 is farther from the solution in the energy norm
     // than zero (or not finite), and is replaced by zero
-    dot(s, u, M->r, 6);
-    dot(s, g, u, 7);
-    cudaMemcpyAsync(M->sc_h + 7, M->sc + 7, sizeof(double), cudaMemcpyDeviceToHost, st);
-    const double ur = read_slot(s, 6), gu = M->sc_h[7];   // (read_slot synchronises: slot 7 is current)
-    const double phi = -0.5 * (ur + gu);
+    const double phi = -0.5 * (M->sc_h[6] + M->sc_h[7]);
     if (!(phi < 0.0) || !std::isfinite(rr)) {
       cudaMemsetAsync(u, 0, sizeof(double) * n3, st);
       cudaMemcpyAsync(M->r, g, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st);
@@ -1687,6 +1719,8 @@ void mixed_free(pd_solver* s) {
   if (s->mixed->sc_h) cudaFreeHost(s->mixed->sc_h);
   if (s->mixed->lpiv_h) cudaFreeHost(s->mixed->lpiv_h);
   if (s->mixed->cap_cnt_h) cudaFreeHost(s->mixed->cap_cnt_h);
+  if (s->mixed->ev_cap) cudaEventDestroy(s->mixed->ev_cap);
+  if (s->mixed->ev_capdone) cudaEventDestroy(s->mixed->ev_capdone);
   for (auto e : s->mixed->ev_panel) cudaEventDestroy(e);
   for (auto e : s->mixed->ev_rest) cudaEventDestroy(e);
   if (s->mixed->side) cudaStreamDestroy(s->mixed->side);

@@ -82,8 +82,9 @@ def config5(solver, scene, state, n_train=18000, n_val=1000, n_test=1000, path_l
     inner iteration per step) along seeded random indenter paths, split into
     training / validation / test solves on disjoint paths; the network
     trained on the device; then every test path run with PCG from each
-    starting point (zero, previous solution, z0, network) and with plain
-    refactorisation, reporting iterations and time per step.  `state` is the
+    starting point (zero, previous solution, z0, network), with the
+    contact-free preconditioner M0 alone and with its capacitance correction,
+    and with plain refactorisation, reporting iterations and time per step.  `state` is the
     (x, v) every path starts from; `timer(fn)` returns the device ms of fn().
     Host orchestration only: every solve, feature and gradient runs in the
     library."""
@@ -114,10 +115,13 @@ def config5(solver, scene, state, n_train=18000, n_val=1000, n_test=1000, path_l
     out["val_err_network_vs_z0"] = net / zero if zero > 0 else None
     solver.mlp_record(0)
     by = {}
-    for name, prec, src in (("refactor (split-TF32 + IR)", L.FP32_IR, 0), ("pcg zero", L.PCG_WARM, 0),
-                            ("pcg previous", L.PCG_WARM, 1), ("pcg z0", L.PCG_WARM, 3),
-                            ("pcg network", L.PCG_WARM, 2)):
+    runs = [("refactor (split-TF32 + IR)", L.FP32_IR, 0, True)]
+    for cap, tag in ((False, "pcg M0"), (True, "pcg M0 + capacitance")):
+        runs += [(tag + " zero", L.PCG_WARM, 0, cap), (tag + " previous", L.PCG_WARM, 1, cap),
+                 (tag + " z0", L.PCG_WARM, 3, cap), (tag + " network", L.PCG_WARM, 2, cap)]
+    for name, prec, src, cap in runs:
         solver.set_precision(prec)
+        solver.set_pcg_capacitance(cap)
         solver.set_warm_start(src)
         its = []
         rej0 = solver.stats()["starts_rejected"]
@@ -125,6 +129,7 @@ def config5(solver, scene, state, n_train=18000, n_val=1000, n_test=1000, path_l
         by[name] = {"iterations": float(np.mean(its)), "ms_per_step": ms / n_test if ms is not None else None,
                     "starts_rejected": int(solver.stats()["starts_rejected"] - rej0)}
     solver.set_warm_start(0)
+    solver.set_pcg_capacitance(True)
     solver.set_precision(L.FP64)
     out["test"] = by
     return out
