@@ -280,6 +280,7 @@ def time_forms(pd, sol, stream, args, fp64_ms, torch):
     sol.set_precision(pd.FP64)
     sol.set_warm_start(0)
     sol.set_state(*state)
+    sol.set_dirichlet(sol._dpos)
     set_detector(sol, s)
     return out
 
@@ -313,34 +314,46 @@ def step_rate(sol, stream, torch, steps):
     return {"ms_per_step": ms, "value": 1e3 / ms, "unit": UNIT}
 
 
-def trajectory(pd, sol, stream, torch):
-    """The whole flexion of configuration 2 (Dirichlet rotation 0 -> 120
-    degrees over 60 time steps, 10 PD iterations per step, point-triangle
-    self-contact re-detected on the device at every inner iteration) in the
-    split-TF32 form, with 1 and 5 inner iterations: PD iterations per second
-    over the run and the most springs active at any step."""
+TRAJ_STEPS = 71
+
+
+def trajectory(pd, sol, stream, torch, forms=None):
+    """The flexion of configuration 2 (Dirichlet rotation of cap B, 2 degrees
+    per time step from the straight arm, 10 PD iterations per step,
+    point-triangle self-contact re-detected on the device at every inner
+    iteration), continued to step 70 (140 degrees, 50 past the L) because
+    the synthetic arm's crease first closes into contact about 35 degrees
+    past the L; with 1 and 5 inner iterations: PD iterations per second over
+    the run, the step at which springs first appear and the most springs
+    active at any step."""
     s = sol._scene
     out = {}
     rest = (s.X.copy(), np.zeros_like(s.X))
-    sol.set_precision(pd.FP32_IR)
-    for inner in (1, 5):
-        sol.set_state(*rest)
-        sol.set_inner_iters(inner)
-        set_detector(sol, s)
-        most = 0
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for step in range(61):
-            sol.set_dirichlet(s.dirichlet_positions(step))
-            sol.step(10)
-            most = max(most, active_springs(sol))
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        out[f"inner{inner}"] = {"pd_iterations": 610, "ms_total": ms, "value": 610e3 / ms, "unit": UNIT,
-                                "max_active_springs": most}
+    forms = forms or [("split_tf32", pd.FP32_IR)]
+    for fname, prec in forms:
+        sol.set_precision(prec)
+        for inner in (1, 5):
+            sol.set_state(*rest)
+            sol.set_inner_iters(inner)
+            set_detector(sol, s)
+            most, first = 0, None
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for step in range(TRAJ_STEPS):
+                sol.set_dirichlet(s.dirichlet_positions(step))
+                sol.step(10)
+                k = active_springs(sol)
+                most = max(most, k)
+                if k > 0 and first is None:
+                    first = step
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            n = 10 * TRAJ_STEPS
+            out[f"{fname}_inner{inner}"] = {"pd_iterations": n, "ms_total": ms, "value": n * 1e3 / ms, "unit": UNIT,
+                                            "first_contact_step": first, "max_active_springs": most}
     sol.set_inner_iters(1)
     return out
 
@@ -382,7 +395,8 @@ def lips_rows(pd, stream, torch, full):
 def dynamic_rows(pd, stream, torch):
     """Backward Euler at scale: lumped mass rho * Vol / 4 per node on the
     diagonal of A (so also on Sigma_0's), dt = 1/30 s, rho = 1000, split-TF32
-    form.  The elbow's whole flexion (61 time steps x 10 PD iterations,
+    form.  The elbow from the joint closed 40 degrees past the L, opened 40
+    degrees and closed again (41 time steps x 10 PD iterations,
     point-triangle self-contact detected on the device at every inner
     iteration) and the lips at m = 6,250 (its 500 penalty springs, 20 time
     steps x 10 PD iterations); PD iterations per second over each run."""
@@ -395,30 +409,41 @@ def dynamic_rows(pd, stream, torch):
                    stream=stream.cuda_stream, timing=True, max_refine=500)
     setup_s = time.perf_counter() - t0
     set_detector(ds, s)
-    ds.set_dirichlet(s.dirichlet_positions(0))
+    x0, fstep = scenes.closed_pose(s, CLOSE_ANGLE)
+    cycle = list(range(fstep, fstep - 21, -1)) + list(range(fstep - 19, fstep + 1))   # open 40 deg and close again
+    ds.set_dirichlet(s.dirichlet_positions(fstep))
+    ds.set_state(x0, np.zeros_like(x0))
     ds.step(1)                                   # warm-up
-    ds.set_state(s.X.copy(), np.zeros_like(s.X))
+    ds.set_state(x0, np.zeros_like(x0))
     most = iters = 0
     res = 0.0
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for step in range(61):
+    springs = []
+    for step in cycle:
         ds.set_dirichlet(s.dirichlet_positions(step))
         ds.step(10)
         st = ds.stats()
         iters += st["refine_iters"]
         res = max(res, st["residual"])
-        most = max(most, active_springs(ds))
+        k = active_springs(ds)
+        springs.append(k)
+        most = max(most, k)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     x, v = ds.get_state()
-    out["elbow_flexion"] = {"tets": s.E, "m": s.m, "setup_s": setup_s, "pd_iterations": 610, "ms_total": ms,
-                            "value": 610e3 / ms, "unit": UNIT, "max_active_springs": most,
-                            "refine_iters_per_step": iters / 61.0, "max_rel_residual": res,
-                            "max_speed_end": float(np.linalg.norm(v, axis=1).max())}
+    n = 10 * len(cycle)
+    out["elbow_flexion_cycle"] = {"tets": s.E, "m": s.m, "setup_s": setup_s, "time_steps": len(cycle),
+                                  "what": "from the joint closed %g deg past the L (flexion step %d), opened 40 deg "
+                                          "and closed again, 10 PD iterations per time step" % (CLOSE_ANGLE, fstep),
+                                  "pd_iterations": n, "ms_total": ms, "value": n * 1e3 / ms, "unit": UNIT,
+                                  "active_springs_first_mid_last": [springs[0], springs[len(springs) // 2],
+                                                                    springs[-1]],
+                                  "max_active_springs": most, "refine_iters_per_step": iters / float(len(cycle)),
+                                  "max_rel_residual": res, "max_speed_end": float(np.linalg.norm(v, axis=1).max())}
     ds.close()
     s = scenes.slabs(m=6250)
     t0 = time.perf_counter()
@@ -479,8 +504,13 @@ def time_learned(pd, sol, stream, args, fp64_ms, torch, state):
     bounded sample of the 20K-solve training run of the warmstart module."""
     from paper_2008_01541_b300 import warmstart as ws
     s = sol._scene
+    # the indenter paths start from the rest state, as in the full configuration 5
+    state = (s.X.copy(), np.zeros_like(s.X))
+    sol.set_dirichlet(s.dirichlet_positions(s.info["rest_step"]))
+    sol.clear_detector()
     t0 = time.perf_counter()
     sol.set_precision(pd.FP32_IR)
+    sol.mlp_set_loss(1)
     sol.mlp_set_params(ws.he_init(0))
     sol.mlp_record(args.train_solves + 8)
     centres, radius = ws.indenter_path(s, seed=1, steps=args.train_solves)
@@ -727,6 +757,7 @@ def main():
     sol._scene = s
     x0, fstep = scenes.closed_pose(s, CLOSE_ANGLE)
     dpos = s.dirichlet_positions(fstep)
+    sol._dpos = dpos
     sol.set_state(x0, np.zeros_like(x0))
     sol.set_dirichlet(dpos)
     if args.nested:
@@ -838,7 +869,8 @@ def main():
         line["forms"] = time_forms(pd, sol, stream, args, ms / args.steps, torch)
     if not args.no_extra and not args.nested:
         sol.set_state(*state)
-        line["trajectory_split_tf32"] = trajectory(pd, sol, stream, torch)
+        line["trajectory"] = trajectory(pd, sol, stream, torch,
+                                        [("split_tf32", pd.FP32_IR), ("pcg_capacitance", pd.PCG_WARM)])
         sol.set_precision(prec)
         line["lips_config4"] = lips_rows(pd, stream, torch, args.sweep)
         line["backward_euler"] = dynamic_rows(pd, stream, torch)
