@@ -93,7 +93,7 @@ struct MixedState {
   double* cpart = nullptr;    // [kp / 64][m][3] chunk partial sums of Y^T S^-1 V z
   int *ccnt = nullptr, *cstat = nullptr;     // solve task counters; factor status
   bool cap_pending = false;   // active springs counted (ev_cap), S not yet built
-  cudaEvent_t ev_cap = nullptr, ev_capdone = nullptr;
+  cudaEvent_t ev_cap = nullptr;
 };
 
 namespace {
@@ -1312,10 +1312,12 @@ static bool dev_realloc(pd_solver* s, void** ptr, size_t bytes) {
 // parts.  cap_begin (with the refactorisation, on its stream): the active
 // springs in slot order and their count, copied to the host behind ev_cap.
 // cap_finish (at the solve, once the host has issued the local steps and
-// the substitutions): wait for the count, which sizes S, then on the factor
-// stream Y = V M0^-1, S = I + V M0^-1 V^T and its FP64 Cholesky factor; the
-// solver stream waits for them.  The host never waits before the local step
-// is queued, so the factorisation of S overlaps it on the device.
+// the substitutions, so the host never waits before they are queued): wait
+// for the count, which sizes S, then on the solver stream Y = V M0^-1,
+// S = I + V M0^-1 V^T and its FP64 Cholesky factor (with the depth-1
+// look-ahead of the FP64 form).  Issued on the factor stream instead, to run
+// beside the local step and the substitutions, it took as long in total:
+// both are FP64-bound and share the same FP64 units.
 static pd_status cap_begin(pd_solver* s) {
   MixedState* M = s->mixed;
   M->kact = 0;
@@ -1336,8 +1338,7 @@ static pd_status cap_begin(pd_solver* s) {
     if (!M->cap_cnt) ok = ok && dev_realloc(s, (void**)&M->cap_cnt, sizeof(int)) &&
                           dev_realloc(s, (void**)&M->cstat, sizeof(int) * 4) &&
                           cudaMallocHost(&M->cap_cnt_h, sizeof(int)) == cudaSuccess &&
-                          cudaEventCreateWithFlags(&M->ev_cap, cudaEventDisableTiming) == cudaSuccess &&
-                          cudaEventCreateWithFlags(&M->ev_capdone, cudaEventDisableTiming) == cudaSuccess;
+                          cudaEventCreateWithFlags(&M->ev_cap, cudaEventDisableTiming) == cudaSuccess;
     if (!ok) { s->err = "device allocation for the capacitance correction failed"; return PD_ERR_OOM; }
     M->cap_rows = rows;
   }
@@ -1356,8 +1357,6 @@ static pd_status cap_finish(pd_solver* s) {
   const int64_t kact = *M->cap_cnt_h;
   if (kact <= 0) return PD_OK;
   const int64_t kp = (kact + 63) / 64 * 64;
-  cudaStream_t main_stream = s->stream;
-  s->stream = s->fstream;
   cudaStream_t st = s->stream;
   s->tbegin(8);
   k_cap_rows<<<dim3(nblk(M->ldm, 256), (unsigned)kact), 256, 0, st>>>(M->cap_act, s->c_idx, s->c_w, s->c_s,
@@ -1366,11 +1365,8 @@ static pd_status cap_finish(pd_solver* s) {
                                                    M->ldm, M->Scap);
   pdk::g_launches += 2;
   cudaMemsetAsync(M->cstat, 0, sizeof(int) * 4, st);
-  pdk::cholesky_fp64(M->Scap, kp, M->Slinv, M->cstat, st);
+  pdk::cholesky_fp64(M->Scap, kp, M->Slinv, M->cstat, st, s->la.side ? &s->la : nullptr);
   s->tend();
-  s->stream = main_stream;
-  cudaEventRecord(M->ev_capdone, st);
-  cudaStreamWaitEvent(main_stream, M->ev_capdone, 0);
   M->kact = kact;
   M->cap_kp = kp;
   return PD_OK;
@@ -1720,7 +1716,6 @@ void mixed_free(pd_solver* s) {
   if (s->mixed->lpiv_h) cudaFreeHost(s->mixed->lpiv_h);
   if (s->mixed->cap_cnt_h) cudaFreeHost(s->mixed->cap_cnt_h);
   if (s->mixed->ev_cap) cudaEventDestroy(s->mixed->ev_cap);
-  if (s->mixed->ev_capdone) cudaEventDestroy(s->mixed->ev_capdone);
   for (auto e : s->mixed->ev_panel) cudaEventDestroy(e);
   for (auto e : s->mixed->ev_rest) cudaEventDestroy(e);
   if (s->mixed->side) cudaStreamDestroy(s->mixed->side);
