@@ -5,6 +5,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <queue>
 #include <string>
 #include <vector>
 
@@ -52,6 +53,91 @@ static cudaError_t dupload(pd_solver* s, T** p, const T* h, size_t n) {
   if (e != cudaSuccess) return e;
   if (n) e = cudaMemcpy(*p, h, n * sizeof(T), cudaMemcpyHostToDevice);
   return e;
+}
+
+// ---- claim order of the sparse substitution tasks
+// The persistent substitution kernels claim tasks in list order and wait for
+// a claimed task's inputs, so a task whose inputs are late holds its CTA.
+// The list is therefore the start order of a list schedule simulated on the
+// host: `nw` workers (the resident CTAs), each task's duration estimated from
+// its nonzero entries, and among the ready tasks the one with the longest
+// remaining path to the end first.  A task starts in the simulation only
+// after its inputs have finished, so the order stays topological (a task
+// waits only for tasks earlier in the list, which running CTAs hold).
+// Dependencies go through group nodes of zero duration: group g waits for
+// `pred` tasks and releases `succ` tasks.
+struct TaskGraph {
+  std::vector<double> dur;               // per task, microseconds (estimate)
+  std::vector<std::vector<int>> out;     // node -> nodes it releases (tasks: 0 .. nt-1, groups after)
+  std::vector<int> indeg;                // per node
+  int nt = 0;
+};
+
+static std::vector<int> list_schedule(const TaskGraph& g, int nw) {
+  const int nn = (int)g.indeg.size(), nt = g.nt;
+  auto dur = [&](int v) { return v < nt ? g.dur[v] : 0.0; };
+  // longest path from each node to a sink (reverse topological order by Kahn)
+  std::vector<int> topo;
+  topo.reserve(nn);
+  {
+    std::vector<int> deg(g.indeg);
+    for (int v = 0; v < nn; ++v)
+      if (deg[v] == 0) topo.push_back(v);
+    for (size_t i = 0; i < topo.size(); ++i)
+      for (int w : g.out[topo[i]])
+        if (--deg[w] == 0) topo.push_back(w);
+  }
+  if ((int)topo.size() != nn) return {};   // not a DAG: keep the given order
+  std::vector<double> blev(nn, 0.0);
+  for (int i = nn - 1; i >= 0; --i) {
+    const int v = topo[i];
+    double b = 0.0;
+    for (int w : g.out[v]) b = std::max(b, blev[w]);
+    blev[v] = b + dur(v);
+  }
+  // event-driven list scheduling (groups complete the moment they are ready)
+  std::vector<int> deg(g.indeg);
+  std::priority_queue<std::pair<double, int>> ready;   // (remaining path, task)
+  using Ev = std::pair<double, int>;                     // (finish time, task)
+  std::priority_queue<Ev, std::vector<Ev>, std::greater<Ev>> run;
+  std::vector<int> order, stack;
+  order.reserve(nt);
+  auto release = [&](int v) {   // v is done: release its successors
+    stack.push_back(v);
+    while (!stack.empty()) {
+      const int u = stack.back();
+      stack.pop_back();
+      for (int w : g.out[u])
+        if (--deg[w] == 0) {
+          if (w >= nt) stack.push_back(w);
+          else ready.push({blev[w], w});
+        }
+    }
+  };
+  for (int v = 0; v < nn; ++v)
+    if (g.indeg[v] == 0) {
+      if (v >= nt) release(v);
+      else ready.push({blev[v], v});
+    }
+  double now = 0.0;
+  int busy = 0;
+  while (!ready.empty() || !run.empty()) {
+    while (!ready.empty() && busy < nw) {
+      const int v = ready.top().second;
+      ready.pop();
+      order.push_back(v);
+      run.push({now + dur(v), v});
+      ++busy;
+    }
+    if (run.empty()) break;
+    const Ev e = run.top();
+    run.pop();
+    now = e.first;
+    --busy;
+    release(e.second);
+  }
+  if ((int)order.size() != nt) return {};
+  return order;
 }
 
 static pd_status build_elemset(pd_solver* s, const pdh::Setup& h, const int32_t* tets,
@@ -968,6 +1054,58 @@ pd_status pd_solver::upload(const pdh::Setup& h, const pdh::Input& in) {
         }
       }
       init[NF] = 0; init[NB2] = 0;
+      // claim order: the start order of a simulated list schedule (see list_schedule)
+      {
+        const int nw = pdk::sparse_grid();
+        auto entries = [&](const int4& t) -> double {
+          const int32_t sn = t.x & 0x1fffffff, kind = t.x & (3 << 29), nc = ncol(sn), nr = nrow(sn);
+          if (kind == KF) return 0.5 * nc * (nc + 1.0) + (double)nr * nc;
+          const double cols = std::min(64, nc - t.z);
+          if (kind == KD) {
+            const double rws = std::min(64, nc - t.y);
+            return t.y == t.z ? 0.5 * rws * (rws + 1.0) : rws * cols;
+          }
+          return std::min(64, nr - t.y) * cols;
+        };
+        auto reorder = [&](std::vector<int4>& tl, bool fwd) {
+          TaskGraph gr;
+          const int nt = (int)tl.size();
+          gr.nt = nt;
+          const int nn = nt + 2 * (int)nsn;
+          gr.dur.resize(nt);
+          gr.out.assign(nn, {});
+          gr.indeg.assign(nn, 0);
+          auto edge = [&](int a, int b) { gr.out[a].push_back(b); ++gr.indeg[b]; };
+          // fwd: group A(s) = FIN (inputs of s's diagonal / fused work), B(s) = YD (s's y done)
+          // bwd: group A(s) = UD (s's u done), B(s) = ZP (s's off tiles done)
+          auto A = [&](int32_t sn) { return nt + sn; };
+          auto B = [&](int32_t sn) { return nt + (int)nsn + sn; };
+          for (int i = 0; i < nt; ++i) {
+            const int4& t = tl[i];
+            const int32_t sn = t.x & 0x1fffffff, kind = t.x & (3 << 29);
+            gr.dur[i] = 1.5 + 4.5 * entries(t) / 4096.0;
+            auto each_target = [&](auto fn) {
+              for (int64_t q = tptr[t.w]; q < tptr[t.w + 1]; ++q) fn(tg[q]);
+            };
+            if (fwd) {
+              if (kind == KD) { edge(A(sn), i); edge(i, B(sn)); }
+              else if (kind == KF) { edge(A(sn), i); each_target([&](int32_t a) { edge(i, A(a)); }); }
+              else { edge(B(sn), i); each_target([&](int32_t a) { edge(i, A(a)); }); }
+            } else {
+              if (kind == KD) { edge(B(sn), i); edge(i, A(sn)); }
+              else if (kind == KF) { each_target([&](int32_t a) { edge(A(a), i); }); edge(i, A(sn)); }
+              else { each_target([&](int32_t a) { edge(A(a), i); }); edge(i, B(sn)); }
+            }
+          }
+          const std::vector<int> ord = list_schedule(gr, nw);
+          if ((int)ord.size() != nt) return;   // keep the level order
+          std::vector<int4> out(nt);
+          for (int k = 0; k < nt; ++k) out[k] = tl[ord[k]];
+          tl.swap(out);
+        };
+        reorder(ft, true);
+        reorder(bt, false);
+      }
       CK(dupload(s, &sf_ftasks, ft.data(), ft.size()));
       CK(dupload(s, &sf_btasks, bt.data(), bt.size()));
       CK(dupload(s, &sf_tptr, tptr.data(), tptr.size()));
