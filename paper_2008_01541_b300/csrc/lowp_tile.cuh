@@ -47,14 +47,17 @@ __device__ __forceinline__ void warp_chol32(float* Ap, float* rinv, int* status,
     bad |= (unsigned)b << j;
     djj = b ? 1.f : djj;
     const float rs = rsqrtf(djj);
-    a[j] = lane == j ? djj * rs : (lane > j ? a[j] * rs : a[j]);
+    // lanes above the diagonal (lane < c) update their upper entries too:
+    // those are never read (a lower entry only depends on lower entries), and
+    // leaving out the lane test keeps every update an unpredicated FMA
+    a[j] = lane == j ? djj * rs : a[j] * rs;
     if (lane == j) rinv[j] = rs;
     float* cb = col[j & 1];
     cb[lane] = a[j];
     __syncwarp();
     if (j + 1 < 32) {
       const float v = cb[j + 1];
-      if (lane >= j + 1) a[j + 1] = fmaf(-a[j], v, a[j + 1]);
+      a[j + 1] = fmaf(-a[j], v, a[j + 1]);
     }
     const float4* c4 = reinterpret_cast<const float4*>(cb);
 #pragma unroll
@@ -64,7 +67,7 @@ __device__ __forceinline__ void warp_chol32(float* Ap, float* rinv, int* status,
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int c = 4 * q + e;
-        if (c > j + 1 && lane >= c) a[c] = fmaf(-a[j], vv[e], a[c]);
+        if (c > j + 1) a[c] = fmaf(-a[j], vv[e], a[c]);
       }
     }
   }
