@@ -18,11 +18,12 @@ __device__ __forceinline__ void bar_sync_n(int id, int n) { asm volatile("bar.sy
 namespace {
 
 // One warp factors the 32 x 32 block at Ap (row stride PADW) in registers
-// (lane i holds row i) and writes L back to Ap, and 1 / L_jj to rinv.  Each
-// scaled column goes through shared memory once (double-buffered, so one warp
-// barrier per pivot) and is read back with 16-byte broadcasts; the next
-// pivot's column is updated first so that its square root overlaps the rest
-// of the current update.  A non-positive pivot is replaced by 1 and reported
+// (lane i holds row i) and writes L back to Ap, and 1 / L_jj to rinv.  The
+// next pivot's column is updated first, with L[j+1][j] taken by a shuffle,
+// so that the chain from pivot to pivot is two shuffles, a reciprocal square
+// root and two multiplies; the rest of each scaled column goes through shared
+// memory (double-buffered, so one warp barrier per pivot) and is read back
+// with 16-byte broadcasts.  A non-positive pivot is replaced by 1 and reported
 // in *status (first bad column + 1, offset by code0).
 template <int LD = PADW>
 __device__ __forceinline__ void warp_chol32(float* Ap, float* rinv, int* status, int code0) {
@@ -52,22 +53,24 @@ __device__ __forceinline__ void warp_chol32(float* Ap, float* rinv, int* status,
     // leaving out the lane test keeps every update an unpredicated FMA
     a[j] = lane == j ? djj * rs : a[j] * rs;
     if (lane == j) rinv[j] = rs;
-    float* cb = col[j & 1];
-    cb[lane] = a[j];
-    __syncwarp();
-    if (j + 1 < 32) {
-      const float v = cb[j + 1];
+    if (j + 1 < 32) {   // the next pivot's column first, with L[j+1][j] by shuffle
+      const float v = __shfl_sync(0xffffffffu, a[j], j + 1);
       a[j + 1] = fmaf(-a[j], v, a[j + 1]);
     }
-    const float4* c4 = reinterpret_cast<const float4*>(cb);
+    if (j + 2 < 32) {   // the rest of the update from the column in shared memory
+      float* cb = col[j & 1];
+      cb[lane] = a[j];
+      __syncwarp();
+      const float4* c4 = reinterpret_cast<const float4*>(cb);
 #pragma unroll
-    for (int q = (j + 2) / 4; q < 8; ++q) {
-      const float4 v = c4[q];
-      const float vv[4] = {v.x, v.y, v.z, v.w};
+      for (int q = (j + 2) / 4; q < 8; ++q) {
+        const float4 v = c4[q];
+        const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int c = 4 * q + e;
-        if (c > j + 1) a[c] = fmaf(-a[j], vv[e], a[c]);
+        for (int e = 0; e < 4; ++e) {
+          const int c = 4 * q + e;
+          if (c > j + 1) a[c] = fmaf(-a[j], vv[e], a[c]);
+        }
       }
     }
   }
