@@ -205,14 +205,27 @@ __global__ void k_tri_bounds(int64_t nt, const int32_t* __restrict__ tri, const 
 // excluded or farther than gap, so it can never be the active choice: the
 // result is the same as a scan of every triangle in index order with the
 // exact test.  Slot j of the spring arrays.
-__global__ void __launch_bounds__(256) k_detect_tris(
-    int64_t np, const int32_t* __restrict__ prox, int64_t nt, const int32_t* __restrict__ tri,
-    const float4* __restrict__ bnd, const int32_t* __restrict__ region, const double* __restrict__ x,
-    const double* __restrict__ xr, double gap, double rest_min, double stiffness, int64_t slot0, int32_t* cidx,
-    double* cw, double* ct, double* cs) {
-  const int lane = threadIdx.x & 31;
-  const int64_t j = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (j >= np) return;
+// One warp per proxy of either side (side-A proxies against side-B triangles,
+// then side-B proxies against side-A triangles; slot j = proxy j).  Pass 1:
+// each lane screens its triangles in FP32 (bounding sphere, then the rest and
+// current distances with the margins of dist_f32) and the survivors go to a
+// per-warp list; pass 2: the lanes take the listed candidates side by side
+// for the exact FP64 tests, so a proxy with several candidates pays for the
+// FP64 work about once instead of once per candidate.
+constexpr int kCand = 64;
+__global__ void __launch_bounds__(128) k_detect_tris(
+    int64_t na, int64_t nb, const int32_t* __restrict__ prox, int64_t nta, int64_t ntb,
+    const int32_t* __restrict__ tris, const float4* __restrict__ bnd_all, const int32_t* __restrict__ region,
+    const double* __restrict__ x, const double* __restrict__ xr, double gap, double rest_min, double stiffness,
+    int32_t* cidx, double* cw, double* ct, double* cs) {
+  __shared__ int cand[4][kCand];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t j = blockIdx.x * (int64_t)(blockDim.x >> 5) + wib;
+  if (j >= na + nb) return;
+  const bool side_a = j < na;
+  const int64_t nt = side_a ? ntb : nta;
+  const int32_t* tri = side_a ? tris + 3 * nta : tris;
+  const float4* bnd = side_a ? bnd_all + nta : bnd_all;
   const int r0 = prox[j];
   const V3 p = ld3(x + 3 * (int64_t)region[r0]), P = ld3(xr + 3 * (int64_t)r0);
   const float px = (float)p.x, py = (float)p.y, pz = (float)p.z, fg = (float)gap;
@@ -221,33 +234,63 @@ __global__ void __launch_bounds__(256) k_detect_tris(
   int64_t bi = -1;
   const float3 p32 = make_float3(px, py, pz), P32 = make_float3((float)P.x, (float)P.y, (float)P.z);
   const float frm = (float)rest_min;
-  for (int64_t q = lane; q < nt; q += 32) {
-    const float4 b = __ldg(bnd + q);
-    const float dx = px - b.x, dy = py - b.y, dz = pz - b.z;
-    const float margin = 1e-4f * (fabsf(b.x) + fabsf(b.y) + fabsf(b.z) + b.w + fg) + 1e-6f;
-    if (sqrtf(dx * dx + dy * dy + dz * dz) > b.w + fg + margin) continue;
-    const int i0 = tri[3 * q], i1 = tri[3 * q + 1], i2 = tri[3 * q + 2];
-    const V3 R0 = ld3(xr + 3 * (int64_t)i0), R1 = ld3(xr + 3 * (int64_t)i1), R2 = ld3(xr + 3 * (int64_t)i2);
-    const V3 C0 = ld3(x + 3 * (int64_t)region[i0]), C1 = ld3(x + 3 * (int64_t)region[i1]),
-             C2 = ld3(x + 3 * (int64_t)region[i2]);
-    // FP32 classification with a margin (1% + 1e-3) far beyond its rounding;
-    // only the pairs it cannot settle take the exact FP64 test
-    const float dr32 = dist_f32(P32, make_float3((float)R0.x, (float)R0.y, (float)R0.z),
-                                make_float3((float)R1.x, (float)R1.y, (float)R1.z),
-                                make_float3((float)R2.x, (float)R2.y, (float)R2.z));
-    double w[3];
-    V3 qp;
-    if (dr32 >= 0.f && dr32 < 0.99f * frm - 1e-3f) continue;            // near at rest: excluded
-    if (!(dr32 >= 0.f && dr32 > 1.01f * frm + 1e-3f)) {                  // undecided: exact test
-      if (closest_on_triangle(P, R0, R1, R2, w, &qp) < rm2) continue;
+  int* cl = cand[wib];
+  int ncand = 0;
+  auto exact = [&]() {   // pass 2 on the listed candidates (ascending triangle index)
+    for (int c = lane; c < ncand; c += 32) {
+      const int e = cl[c];
+      const int64_t q = e & 0x3fffffff;
+      const int i0 = tri[3 * q], i1 = tri[3 * q + 1], i2 = tri[3 * q + 2];
+      double w[3];
+      V3 qp;
+      if (e & 0x40000000) {   // near the rest exclusion distance: the exact rest test decides
+        const V3 R0 = ld3(xr + 3 * (int64_t)i0), R1 = ld3(xr + 3 * (int64_t)i1), R2 = ld3(xr + 3 * (int64_t)i2);
+        if (closest_on_triangle(P, R0, R1, R2, w, &qp) < rm2) continue;
+      }
+      const V3 C0 = ld3(x + 3 * (int64_t)region[i0]), C1 = ld3(x + 3 * (int64_t)region[i1]),
+               C2 = ld3(x + 3 * (int64_t)region[i2]);
+      const double d2 = closest_on_triangle(p, C0, C1, C2, w, &qp);
+      if (d2 < best || (d2 == best && q < bi)) { best = d2; bi = q; }
     }
-    const float d32 = dist_f32(p32, make_float3((float)C0.x, (float)C0.y, (float)C0.z),
-                               make_float3((float)C1.x, (float)C1.y, (float)C1.z),
-                               make_float3((float)C2.x, (float)C2.y, (float)C2.z));
-    if (d32 >= 0.f && d32 > 1.01f * fg + 1e-3f) continue;                // farther than gap: never the active choice
-    const double d2 = closest_on_triangle(p, C0, C1, C2, w, &qp);
-    if (d2 < best) { best = d2; bi = q; }
+    ncand = 0;
+    __syncwarp();
+  };
+  for (int64_t q0 = 0; q0 < nt; q0 += 32) {
+    const int64_t q = q0 + lane;
+    bool keep = false, undecided = false;
+    if (q < nt) {
+      const float4 b = __ldg(bnd + q);
+      const float dx = px - b.x, dy = py - b.y, dz = pz - b.z;
+      const float margin = 1e-4f * (fabsf(b.x) + fabsf(b.y) + fabsf(b.z) + b.w + fg) + 1e-6f;
+      if (sqrtf(dx * dx + dy * dy + dz * dz) <= b.w + fg + margin) {
+        const int i0 = tri[3 * q], i1 = tri[3 * q + 1], i2 = tri[3 * q + 2];
+        const V3 R0 = ld3(xr + 3 * (int64_t)i0), R1 = ld3(xr + 3 * (int64_t)i1), R2 = ld3(xr + 3 * (int64_t)i2);
+        const V3 C0 = ld3(x + 3 * (int64_t)region[i0]), C1 = ld3(x + 3 * (int64_t)region[i1]),
+                 C2 = ld3(x + 3 * (int64_t)region[i2]);
+        // FP32 classification with a margin (1% + 1e-3) far beyond its
+        // rounding; only the pairs it cannot settle take the exact FP64 test
+        const float dr32 = dist_f32(P32, make_float3((float)R0.x, (float)R0.y, (float)R0.z),
+                                    make_float3((float)R1.x, (float)R1.y, (float)R1.z),
+                                    make_float3((float)R2.x, (float)R2.y, (float)R2.z));
+        const float d32 = dist_f32(p32, make_float3((float)C0.x, (float)C0.y, (float)C0.z),
+                                   make_float3((float)C1.x, (float)C1.y, (float)C1.z),
+                                   make_float3((float)C2.x, (float)C2.y, (float)C2.z));
+        const bool excluded = dr32 >= 0.f && dr32 < 0.99f * frm - 1e-3f;   // near at rest
+        const bool far = d32 >= 0.f && d32 > 1.01f * fg + 1e-3f;           // farther than gap: never the choice
+        keep = !excluded && !far;
+        undecided = !(dr32 >= 0.f && dr32 > 1.01f * frm + 1e-3f);
+      }
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (bal) {
+      const int cnt = __popc(bal);
+      if (ncand + cnt > kCand) exact();
+      if (keep) cl[ncand + __popc(bal & ((1u << lane) - 1u))] = (int)q | (undecided ? 0x40000000 : 0);
+      ncand += cnt;
+      __syncwarp();
+    }
   }
+  exact();
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const double ob = __shfl_down_sync(0xffffffffu, best, o);
@@ -255,7 +298,7 @@ __global__ void __launch_bounds__(256) k_detect_tris(
     if (oi >= 0 && (bi < 0 || ob < best || (ob == best && oi < bi))) { best = ob; bi = oi; }
   }
   if (lane != 0) return;
-  const int64_t sj = slot0 + j;
+  const int64_t sj = j;
   empty_slot(sj, cidx, cw, ct, cs);
   if (bi < 0 || !(sqrt(best) < gap)) return;
   const int i0 = tri[3 * bi], i1 = tri[3 * bi + 1], i2 = tri[3 * bi + 2];
@@ -315,16 +358,11 @@ void detect_tris(const TriDetector& d, const int32_t* region, const double* x, i
     k_tri_bounds<<<nblk(nt, 128), 128, 0, st>>>(nt, d.tris, region, x, d.bnd);
     ++g_launches;
   }
-  // side-A proxies against side-B triangles, then side-B proxies against side-A triangles
-  const int32_t* tris_b = d.tris + 3 * d.nta;
-  if (d.na > 0) {
-    k_detect_tris<<<nblk(d.na, 8), 256, 0, st>>>(d.na, d.prox, d.ntb, tris_b, d.bnd + d.nta, region, x, d.xr, d.gap,
-                                                 d.rest_min, d.stiffness, 0, cidx, cw, ct, cs);
-    ++g_launches;
-  }
-  if (d.nb > 0) {
-    k_detect_tris<<<nblk(d.nb, 8), 256, 0, st>>>(d.nb, d.prox + d.na, d.nta, d.tris, d.bnd, region, x, d.xr, d.gap,
-                                                 d.rest_min, d.stiffness, d.na, cidx, cw, ct, cs);
+  // side-A proxies against side-B triangles and side-B proxies against side-A
+  // triangles, one launch
+  if (d.na + d.nb > 0) {
+    k_detect_tris<<<nblk(d.na + d.nb, 4), 128, 0, st>>>(d.na, d.nb, d.prox, d.nta, d.ntb, d.tris, d.bnd, region, x,
+                                                         d.xr, d.gap, d.rest_min, d.stiffness, cidx, cw, ct, cs);
     ++g_launches;
   }
 }
