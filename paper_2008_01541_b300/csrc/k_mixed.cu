@@ -1673,6 +1673,15 @@ pd_status mixed_iterate(pd_solver* s, const double* g, const double* u0, double*
   return PD_OK;
 }
 
+bool sigma_product(pd_solver* s, const double* p, double* q) {
+  MixedState* M = s->mixed;
+  if (!M) return false;
+  k_split<<<nblk(3 * s->m, 256), 256, 0, s->stream>>>(p, 3 * s->m, M->vhi, M->vlo);
+  k_symv_df<<<nblk(16 * (s->m + 1), 256), 256, 0, s->stream>>>(M->Shi, M->Slo, s->m, M->ldm, M->vhi, M->vlo, q);
+  pdk::g_launches += 2;
+  return true;
+}
+
 // z = M0^-1 r with the contact-free factor of Sigma_0 (computed on first use).
 pd_status apply_free(pd_solver* s, const double* r, double* z) {
   pd_status rs = ensure_state(s);

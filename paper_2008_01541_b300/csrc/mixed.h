@@ -9,6 +9,10 @@ pd_status mixed_solve(pd_solver* s, const double* g, const double* u0, double* u
 pd_status mixed_factor(pd_solver* s);
 pd_status mixed_iterate(pd_solver* s, const double* g, const double* u0, double* u);
 void mixed_free(pd_solver* s);
+// q = Sigma_0 p (3 right-hand sides) from Sigma_0's FP32 head + tail pair in
+// double-float arithmetic (the residual product, FP64-accurate); false when
+// the low-precision state does not exist (the FP64 form).
+bool sigma_product(pd_solver* s, const double* p, double* q);
 // z = M0^-1 r with the contact-free low-precision factor of Sigma_0.
 pd_status apply_free(pd_solver* s, const double* r, double* z);
 void mixed_invalidate(pd_solver* s);

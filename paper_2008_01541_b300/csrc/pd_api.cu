@@ -1256,9 +1256,12 @@ pd_status pd_solver::step(int outer_iters, pd_contact_cb cb, void* user) {
       pd_status r = region_solve(g, nullptr, u2);
       if (r != PD_OK) { result = r; break; }
       refine_total += last_refine;
-      // 4.6, 4.7: x2 += u2; f~_2 -= Sigma_alpha u2 (= Sigma_0 u2 - A22^beta u2 - M2/dt^2 u2)
+      // 4.6, 4.7: x2 += u2; f~_2 -= Sigma_alpha u2 (= Sigma_0 u2 - A22^beta u2 - M2/dt^2 u2).
+      // The low-precision and PCG forms take Sigma_0 u2 from the FP32 pair their
+      // residuals use (double-float, FP64-accurate, 12 instead of 8 bytes per
+      // entry pair but on the FP32 pipes); the FP64 form from Sigma_0 in FP64.
       tbegin(5);
-      pdk::symv3(Sigma0, m, u2, Sau, stream);
+      if (precision == PD_FP64 || !pdm::sigma_product(this, u2, Sau)) pdk::symv3(Sigma0, m, u2, Sau, stream);
       pdk::spmv3(m, b22_ptr, b22_row, b22_val, u2, -1.0, Sau, stream);
       pdk::inner_update(m, u2, Sau, d_region, x, U2, ft2, stream);
       tend();
