@@ -92,6 +92,7 @@ struct MixedState {
   double *ct = nullptr, *cy = nullptr, *cwork = nullptr;   // [kp][3] V z, S^-1 V z; [kp][3] x 2 solve work
   double* cpart = nullptr;    // [kp / 64][m][3] chunk partial sums of Y^T S^-1 V z
   int *ccnt = nullptr, *cstat = nullptr;     // solve task counters; factor status
+  int cg_hint = 1;            // PCG iterations of the previous solve (where the checks start)
   bool cap_pending = false;   // active springs counted (ev_cap), S not yet built
   cudaEvent_t ev_cap = nullptr;
 };
@@ -1543,13 +1544,20 @@ pd_status mixed_iterate(pd_solver* s, const double* g, const double* u0, double*
     cudaMemcpyAsync(M->r, g, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st);
   }
   dot(s, g, g, 4);
-  cudaMemcpyAsync(M->lpiv_h, M->lpiv, sizeof(int), cudaMemcpyDeviceToHost, st);
-  cudaMemcpyAsync(M->sc_h, M->sc, sizeof(double) * 8, cudaMemcpyDeviceToHost, st);
-  cudaStreamSynchronize(st);
-  const double gg = M->sc_h[4];
-  const int lost_pivot = warm ? 0 : *M->lpiv_h;
-  const double tol2 = s->opt.tol * s->opt.tol * (gg > 0 ? gg : 1.0);
-  double rr = u0 ? M->sc_h[0] : gg;
+  // PCG from zero needs none of these before its first convergence check,
+  // which reads g.g with r.r (slot 4 is not reused in the loop)
+  const bool defer = warm && !u0;
+  double gg = 0.0, tol2 = 0.0, rr = 0.0;
+  int lost_pivot = 0;
+  if (!defer) {
+    cudaMemcpyAsync(M->lpiv_h, M->lpiv, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(M->sc_h, M->sc, sizeof(double) * 8, cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    gg = M->sc_h[4];
+    lost_pivot = warm ? 0 : *M->lpiv_h;
+    tol2 = s->opt.tol * s->opt.tol * (gg > 0 ? gg : 1.0);
+    rr = u0 ? M->sc_h[0] : gg;
+  }
   if (u0) {
     // CG decreases phi(u) = u^T H u / 2 - g^T u = -(u . r + g . u) / 2 with
     // r = g - H u, and phi(u) - phi(u*) = ||u - u*||_H^2 / 2: a start with
@@ -1564,7 +1572,7 @@ pd_status mixed_iterate(pd_solver* s, const double* g, const double* u0, double*
     }
   }
   int it = 0;
-  bool ok = rr <= tol2;
+  bool ok = !defer && rr <= tol2;
   // classic refinement for the split-TF32 factor; factor-preconditioned CG
   // for TF32 / BF16, and for any factor that lost a pivot (CG absorbs the few
   // outlier directions a replaced pivot leaves, plain refinement stalls on them)
@@ -1620,11 +1628,21 @@ pd_status mixed_iterate(pd_solver* s, const double* g, const double* u0, double*
       pdk::g_launches += 2;
       // the host reads the residual (a stream synchronisation) every iteration
       // for the first eight, then every fourth: a long PCG run pays few round
-      // trips for at most three extra iterations
-      const bool check = it <= 8 || it % 4 == 0 || it == s->opt.max_refine;
+      // trips for at most three extra iterations.  PCG from zero starts
+      // checking one iteration before the count of its previous solve, at
+      // most at the fourth (the iterations between cost less than the round
+      // trips they save, and an easier solve wastes at most three)
+      const int first = defer ? std::min(4, std::max(1, M->cg_hint - 1)) : 1;
+      const bool check = (it >= first && (it <= 8 || it % 4 == 0)) || it == s->opt.max_refine;
       if (check) {
         dot(s, M->r, M->r, 0);
-        rr = read_slot(s, 0);
+        cudaMemcpyAsync(M->sc_h, M->sc, sizeof(double) * 8, cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        rr = M->sc_h[0];
+        if (defer && gg == 0.0) {
+          gg = M->sc_h[4];
+          tol2 = s->opt.tol * s->opt.tol * (gg > 0 ? gg : 1.0);
+        }
         if (!std::isfinite(rr)) break;
         if (rr <= tol2) {   // confirm with the true residual
           hmatvec(s, u, M->q);
@@ -1643,6 +1661,7 @@ pd_status mixed_iterate(pd_solver* s, const double* g, const double* u0, double*
   }
   s->tend();
   s->last_refine = it;
+  if (warm && ok) M->cg_hint = it;
   s->last_residual = std::sqrt(rr / (gg > 0 ? gg : 1.0));
   if (ce != cudaSuccess) {
     s->err = std::string("preconditioner launch failed: ") + cudaGetErrorString(ce);
