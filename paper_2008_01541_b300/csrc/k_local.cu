@@ -65,6 +65,126 @@ __device__ bool polar_newton(const double* F, double* R) {
   return false;
 }
 
+// The same scaled Newton iteration in FP32 (64 times the FP64 rate on B300),
+// to FP32 accuracy; false if it cannot be used (det <= 0, no convergence).
+__device__ bool polar_newton_f32(const double* F, float* X) {
+  float C[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) X[i] = (float)F[i];
+  float nx = 0.f;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) nx += X[i] * X[i];
+  bool scaled = true;
+  for (int it = 0; it < 30; ++it) {
+    C[0] = X[4] * X[8] - X[5] * X[7];
+    C[1] = X[5] * X[6] - X[3] * X[8];
+    C[2] = X[3] * X[7] - X[4] * X[6];
+    C[3] = X[2] * X[7] - X[1] * X[8];
+    C[4] = X[0] * X[8] - X[2] * X[6];
+    C[5] = X[1] * X[6] - X[0] * X[7];
+    C[6] = X[1] * X[5] - X[2] * X[4];
+    C[7] = X[2] * X[3] - X[0] * X[5];
+    C[8] = X[0] * X[4] - X[1] * X[3];
+    const float det = X[0] * C[0] + X[1] * C[1] + X[2] * C[2];
+    if (!(det > 1e-6f * nx * sqrtf(nx))) return false;
+    float g = 1.f;
+    if (scaled) {
+      float nc = 0.f;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) nc += C[i] * C[i];
+      g = sqrtf(sqrtf(nc / nx) / det);
+    }
+    const float a = 0.5f * g, b = 0.5f / (g * det);
+    float d2 = 0.f, nn = 0.f;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const float v = a * X[i] + b * C[i];
+      const float dv = v - X[i];
+      d2 += dv * dv;
+      nn += v * v;
+      X[i] = v;
+    }
+    nx = nn;
+    if (d2 < 1e-4f) scaled = false;
+    if (d2 < 1e-12f) return true;
+  }
+  return false;
+}
+
+// Closest rotation of F (det F > 0) to FP64 accuracy from an FP32 estimate
+// R0 of it.  One FP64 Newton step (X + X^-T) / 2 first makes the estimate
+// orthogonal (it leaves its rotation unchanged and squares the rest); then,
+// with M = X^T F = H + K (H symmetric, K small and skew), the rotation
+// X exp([w]x) with w = 2 (tr(H) I - H)^-1 axial(K) makes its transpose
+// times F symmetric to first order.  The error left after a pass is of the
+// order of the square of its correction, so a pass whose correction is below
+// ~3e-7 is the last (an FP32 estimate of a well-conditioned F needs one); at
+// most three passes, else false.
+__device__ bool polar_refine(const double* F, const float* X32, double* R) {
+  double X[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) X[i] = (double)X32[i];
+  for (int pass = 0; pass < 3; ++pass) {
+    {   // orthogonalise: X = (X + X^-T) / 2
+      double Cx[9];
+      const double dx = cofactor(X, Cx);
+      if (!(dx > 0.0)) return false;
+      const double b = 0.5 / dx;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) X[i] = 0.5 * X[i] + b * Cx[i];
+    }
+    double M[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) M[3 * i + j] = X[i] * F[j] + X[3 + i] * F[3 + j] + X[6 + i] * F[6 + j];   // (X^T F)_ij
+    // axial vector of the skew part, and tr(H) I - H for the symmetric part H
+    const double s0 = 0.5 * (M[7] - M[5]), s1 = 0.5 * (M[2] - M[6]), s2 = 0.5 * (M[3] - M[1]);
+    const double h01 = 0.5 * (M[1] + M[3]), h02 = 0.5 * (M[2] + M[6]), h12 = 0.5 * (M[5] + M[7]);
+    const double tr = M[0] + M[4] + M[8];
+    const double A[9] = {tr - M[0], -h01, -h02, -h01, tr - M[4], -h12, -h02, -h12, tr - M[8]};
+    double Ci[9];
+    const double det = cofactor(A, Ci);   // A symmetric: A^-1 = cof(A) / det
+    if (!(det > 0.0)) return false;
+    const double w0 = 2.0 * (Ci[0] * s0 + Ci[1] * s1 + Ci[2] * s2) / det;
+    const double w1 = 2.0 * (Ci[3] * s0 + Ci[4] * s1 + Ci[5] * s2) / det;
+    const double w2 = 2.0 * (Ci[6] * s0 + Ci[7] * s1 + Ci[8] * s2) / det;
+    // Q = exp([w]x) (Rodrigues); X <- X Q
+    const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
+    double c1, c2;   // sin(th) / th, (1 - cos(th)) / th^2
+    if (th2 < 1e-8) {
+      c1 = 1.0 - th2 / 6.0;
+      c2 = 0.5 - th2 / 24.0;
+    } else {
+      const double th = sqrt(th2);
+      c1 = sin(th) / th;
+      c2 = (1.0 - cos(th)) / th2;
+    }
+    const double K[9] = {0.0, -w2, w1, w2, 0.0, -w0, -w1, w0, 0.0};
+    double Q[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const double kk = K[3 * i] * K[j] + K[3 * i + 1] * K[3 + j] + K[3 * i + 2] * K[6 + j];
+        Q[3 * i + j] = (i == j ? 1.0 : 0.0) + c1 * K[3 * i + j] + c2 * kk;
+      }
+    double Y[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Y[3 * i + j] = X[3 * i] * Q[j] + X[3 * i + 1] * Q[3 + j] + X[3 * i + 2] * Q[6 + j];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) X[i] = Y[i];
+    if (th2 < 1e-13) {   // the next correction would be ~th2: below 1e-12 relative, X is R
+#pragma unroll
+      for (int i = 0; i < 9; ++i) R[i] = X[i];
+      return true;
+    }
+  }
+  return false;
+}
+
 // Closest rotation through the eigen-decomposition of F^T F (cyclic Jacobi):
 // R = [u1 u2 u1 x u2] [v1 v2 v1 x v2]^T with u_i = F v_i / sigma_i.  Used for
 // inverted, degenerate or badly conditioned F, where the smallest singular
@@ -295,8 +415,13 @@ __global__ void k_polar_forces(int64_t count, const int4* __restrict__ tets,
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) F[3 * i + j] = D[3 * i] * Mi[j] + D[3 * i + 1] * Mi[3 + j] + D[3 * i + 2] * Mi[6 + j];
+  // R: FP32 Newton iterations refined in FP64; the FP64 Newton iteration
+  // where FP32 cannot serve; the Jacobi route for inverted or degenerate F
   double R[9];
-  if (!polar_newton(F, R)) polar_jacobi(F, R);
+  {
+    float X32[9];
+    if (!(polar_newton_f32(F, X32) && polar_refine(F, X32, R)) && !polar_newton(F, R)) polar_jacobi(F, R);
+  }
   double we = __ldg(w + e);
   double P[9];
 #pragma unroll
