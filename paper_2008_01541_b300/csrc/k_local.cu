@@ -138,44 +138,55 @@ __device__ bool polar_refine(const double* F, const float* X32, double* R) {
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) M[3 * i + j] = X[i] * F[j] + X[3 + i] * F[3 + j] + X[6 + i] * F[6 + j];   // (X^T F)_ij
-    // axial vector of the skew part, and tr(H) I - H for the symmetric part H
+    // axial vector of the skew part, and A = tr(H) I - H for the symmetric part H
     const double s0 = 0.5 * (M[7] - M[5]), s1 = 0.5 * (M[2] - M[6]), s2 = 0.5 * (M[3] - M[1]);
     const double h01 = 0.5 * (M[1] + M[3]), h02 = 0.5 * (M[2] + M[6]), h12 = 0.5 * (M[5] + M[7]);
     const double tr = M[0] + M[4] + M[8];
-    const double A[9] = {tr - M[0], -h01, -h02, -h01, tr - M[4], -h12, -h02, -h12, tr - M[8]};
-    double Ci[9];
-    const double det = cofactor(A, Ci);   // A symmetric: A^-1 = cof(A) / det
+    const double a00 = tr - M[0], a11 = tr - M[4], a22 = tr - M[8];
+    // w = 2 A^-1 s from the symmetric adjugate of A (off-diagonal a_ij = -h_ij)
+    const double c00 = a11 * a22 - h12 * h12, c11 = a00 * a22 - h02 * h02, c22 = a00 * a11 - h01 * h01;
+    const double c01 = a22 * h01 + h02 * h12, c02 = a11 * h02 + h01 * h12, c12 = a00 * h12 + h01 * h02;
+    const double det = a00 * c00 - h01 * c01 - h02 * c02;
     if (!(det > 0.0)) return false;
-    const double w0 = 2.0 * (Ci[0] * s0 + Ci[1] * s1 + Ci[2] * s2) / det;
-    const double w1 = 2.0 * (Ci[3] * s0 + Ci[4] * s1 + Ci[5] * s2) / det;
-    const double w2 = 2.0 * (Ci[6] * s0 + Ci[7] * s1 + Ci[8] * s2) / det;
-    // Q = exp([w]x) (Rodrigues); X <- X Q
+    const double rd = 2.0 / det;
+    const double w0 = rd * (c00 * s0 + c01 * s1 + c02 * s2);
+    const double w1 = rd * (c01 * s0 + c11 * s1 + c12 * s2);
+    const double w2 = rd * (c02 * s0 + c12 * s1 + c22 * s2);
     const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
-    double c1, c2;   // sin(th) / th, (1 - cos(th)) / th^2
-    if (th2 < 1e-8) {
-      c1 = 1.0 - th2 / 6.0;
-      c2 = 0.5 - th2 / 24.0;
+    // X <- X Q with Q = exp([w]x): to first order, X + X [w]x, when the
+    // correction is small enough that Q's departure from orthogonality,
+    // ~th2, is below 1e-12; else Rodrigues' formula
+    if (th2 < 1e-12) {
+      double Y[9];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const double x0 = X[3 * i], x1 = X[3 * i + 1], x2 = X[3 * i + 2];
+        Y[3 * i] = x0 + (x1 * w2 - x2 * w1);
+        Y[3 * i + 1] = x1 + (x2 * w0 - x0 * w2);
+        Y[3 * i + 2] = x2 + (x0 * w1 - x1 * w0);
+      }
+#pragma unroll
+      for (int i = 0; i < 9; ++i) X[i] = Y[i];
     } else {
       const double th = sqrt(th2);
-      c1 = sin(th) / th;
-      c2 = (1.0 - cos(th)) / th2;
+      const double c1 = sin(th) / th, c2 = (1.0 - cos(th)) / th2;   // sin(th) / th, (1 - cos(th)) / th^2
+      const double K[9] = {0.0, -w2, w1, w2, 0.0, -w0, -w1, w0, 0.0};
+      double Q[9];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const double kk = K[3 * i] * K[j] + K[3 * i + 1] * K[3 + j] + K[3 * i + 2] * K[6 + j];
+          Q[3 * i + j] = (i == j ? 1.0 : 0.0) + c1 * K[3 * i + j] + c2 * kk;
+        }
+      double Y[9];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Y[3 * i + j] = X[3 * i] * Q[j] + X[3 * i + 1] * Q[3 + j] + X[3 * i + 2] * Q[6 + j];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) X[i] = Y[i];
     }
-    const double K[9] = {0.0, -w2, w1, w2, 0.0, -w0, -w1, w0, 0.0};
-    double Q[9];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        const double kk = K[3 * i] * K[j] + K[3 * i + 1] * K[3 + j] + K[3 * i + 2] * K[6 + j];
-        Q[3 * i + j] = (i == j ? 1.0 : 0.0) + c1 * K[3 * i + j] + c2 * kk;
-      }
-    double Y[9];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) Y[3 * i + j] = X[3 * i] * Q[j] + X[3 * i + 1] * Q[3 + j] + X[3 * i + 2] * Q[6 + j];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) X[i] = Y[i];
     if (th2 < 1e-13) {   // the next correction would be ~th2: below 1e-12 relative, X is R
 #pragma unroll
       for (int i = 0; i < 9; ++i) R[i] = X[i];
