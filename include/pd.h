@@ -127,6 +127,8 @@ typedef struct {
     double ms_refactor;       /* the refactorisation alone (part of ms_factor_solve; PCG forms: 0) */
     int64_t starts_rejected;  /* supplied PCG starts replaced by zero since pd_setup
                                  (see pd_set_warm_start)                              */
+    int64_t precision_fallbacks; /* low-precision solves redone in FP64 since pd_setup
+                                    (see pd_set_precision_fallback)                   */
 } pd_stats;
 
 typedef struct pd_solver pd_solver;
@@ -390,6 +392,20 @@ pd_status pd_set_warm_start(pd_solver* s, int source);
  * P = M0 + W^T C W).  The solve still meets tol against the FP64-accurate
  * residual of H.  on = 0 uses M0 alone.  Errors: INVALID_ARG (NULL s). */
 pd_status pd_set_pcg_capacitance(pd_solver* s, int on);
+
+/* Precision escalation of the low-precision forms (beyond the paper; on by
+ * default).  A region solve of PD_FP32_IR, PD_TF32_IR, PD_BF16_IR or
+ * PD_PCG_WARM whose low-precision factor lost a pivot (the pivot was not
+ * positive and the refinement did not reach tol), or whose refinement did not
+ * reach tol within max_refine, is redone for that system by the FP64
+ * factorisation and direct solve of the same H (Section 3.3), and counted in
+ * pd_stats.precision_fallbacks; the next refactorisation is low precision
+ * again.  Not applied with pd_set_contact_nodes (the nested form), nor when H
+ * itself has a non-positive diagonal entry.  If the FP64 factorisation fails
+ * too, the step reports PD_ERR_NOT_SPD as the FP64 form does.  on = 0 reports
+ * the low-precision failure (PD_ERR_NOT_SPD or PD_ERR_NO_CONVERGENCE) at once.
+ * Errors: INVALID_ARG (NULL s). */
+pd_status pd_set_precision_fallback(pd_solver* s, int on);
 
 /* Set / read the network parameters (n must be PD_MLP_NPARAMS); setting them
  * resets the optimiser state. */

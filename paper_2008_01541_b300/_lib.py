@@ -47,7 +47,8 @@ class Stats(ctypes.Structure):
                 ("ms_local_alpha", "ms_forward", "ms_contact_update", "ms_local_beta", "ms_factor_solve",
                  "ms_bookkeeping", "ms_backward", "ms_step")] + [("kernel_launches", ctypes.c_int64),
                                                                   ("ms_refactor", ctypes.c_double),
-                                                                  ("starts_rejected", ctypes.c_int64)]
+                                                                  ("starts_rejected", ctypes.c_int64),
+                                                                  ("precision_fallbacks", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -88,6 +89,7 @@ _sigs = {
     "pd_debug_wait_timeout": (ctypes.c_int, [P]),
     "pd_set_warm_start": (ctypes.c_int, [P, ctypes.c_int]),
     "pd_set_pcg_capacitance": (ctypes.c_int, [P, ctypes.c_int]),
+    "pd_set_precision_fallback": (ctypes.c_int, [P, ctypes.c_int]),
     "pd_mlp_set_params": (ctypes.c_int, [P, P, I64]),
     "pd_mlp_get_params": (ctypes.c_int, [P, P, I64]),
     "pd_mlp_record": (ctypes.c_int, [P, I64]),

@@ -1677,6 +1677,7 @@ pd_status mixed_iterate(pd_solver* s, const double* g, const double* u0, double*
     if (lost_pivot) {
       s->err = "low-precision Cholesky pivot " + std::to_string(lost_pivot - 1) +
                " was not positive and the refinement did not reach tol";
+      s->mixed_escalate = true;
       return PD_ERR_NOT_SPD;
     }
     if (h[1]) {
@@ -1687,6 +1688,7 @@ pd_status mixed_iterate(pd_solver* s, const double* g, const double* u0, double*
     std::snprintf(buf, sizeof buf, "refinement reached relative residual %.3e after %d iterations (tol %.1e)",
                   s->last_residual, it, s->opt.tol);
     s->err = buf;
+    s->mixed_escalate = true;
     return PD_ERR_NO_CONVERGENCE;
   }
   return PD_OK;

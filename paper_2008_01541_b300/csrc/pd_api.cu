@@ -256,7 +256,27 @@ pd_status pd_solver::region_solve_core(const double* g_dev, const double* u0_dev
     last_residual = -1.0;   // the direct FP64 solve measures none
     return PD_OK;
   }
-  return pdm::mixed_iterate(this, g_dev, u0_dev, u_dev);
+  mixed_escalate = false;
+  pd_status r = pdm::mixed_iterate(this, g_dev, u0_dev, u_dev);
+  if (r == PD_OK || !mixed_escalate || !precision_fallback || nested) return r;
+  // Precision escalation: the low-precision factor lost a pivot or its
+  // refinement did not reach tol; this system is factored and solved in FP64
+  // (H from Sigma_0 and the same springs), and the next refactorisation is
+  // low precision again.  A failing FP64 pivot is reported by the step's
+  // status check, as in the FP64 form.
+  const int low = precision;
+  precision = PD_FP64;
+  r = refactor();
+  if (r == PD_OK) {
+    CK(cudaStreamWaitEvent(stream, ev_fac, 0));
+    tbegin(4);
+    pdk::chol_solve_fp64_tasks(H, mp, Linv, g_dev, u_dev, m, work, trsv_cnt, status, stream, nullptr);
+    tend();
+    ++precision_fallbacks;
+    last_residual = -1.0;
+  }
+  precision = low;
+  return r;
 }
 
 // Algorithm 1, 4.3: H = Sigma_0 + C_22 for the current springs, and its
@@ -510,6 +530,7 @@ pd_status pd_get_stats(const pd_solver* s, pd_stats* out) {
   if (!s || !out) return PD_ERR_INVALID_ARG;
   *out = s->stats;
   out->starts_rejected = s->starts_rejected;
+  out->precision_fallbacks = s->precision_fallbacks;
   return PD_OK;
 }
 
@@ -827,6 +848,12 @@ pd_status pd_set_contact_nodes(pd_solver* s, const int32_t* nodes, int64_t np) {
 pd_status pd_set_warm_start(pd_solver* s, int source) {
   if (!s || source < 0 || source > 3) return PD_ERR_INVALID_ARG;
   s->warm_source = source;
+  return PD_OK;
+}
+
+pd_status pd_set_precision_fallback(pd_solver* s, int on) {
+  if (!s) return PD_ERR_INVALID_ARG;
+  s->precision_fallback = on != 0;
   return PD_OK;
 }
 

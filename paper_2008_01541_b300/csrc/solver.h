@@ -92,6 +92,9 @@ struct pd_solver {
   std::vector<double> X_rest_h;  // rest positions (host)
   int last_refine = 0;
   int64_t starts_rejected = 0;   // PCG starts worse than zero, replaced by zero (counted)
+  int64_t precision_fallbacks = 0;   // low-precision solves redone in FP64 (counted)
+  bool precision_fallback = true;    // redo a failed low-precision solve in FP64
+  bool mixed_escalate = false;       // set by the mixed solve: its failure may be escalated
   double last_residual = 0.0;
   // contacts (region indices)
   int64_t k = 0, kcap = 0;

@@ -231,6 +231,10 @@ class Solver:
         """Capacitance (Woodbury) correction of the PCG preconditioner for the active springs."""
         self._check(lib.pd_set_pcg_capacitance(self.h, 1 if on else 0))
 
+    def set_precision_fallback(self, on):
+        """Redo a failed low-precision region solve by the FP64 factorisation (on by default)."""
+        self._check(lib.pd_set_precision_fallback(self.h, 1 if on else 0))
+
     def mlp_set_params(self, params):
         p = _c(params, np.float32).ravel()
         self._check(lib.pd_mlp_set_params(self.h, _ptr(p), len(p)))

@@ -132,3 +132,41 @@ def test_resampled_contacts_per_step_error_vs_oracle(pd):
         print(prec, "per-step relative error vs oracle (worse of norm and per node):", ["%.1e" % e for e in errs])
         assert max(errs) <= 1e-8, (prec, errs)
         sol.close()
+
+
+def test_precision_fallback_to_fp64(pd):
+    # with max_refine = 1 no low-precision form reaches tol: each solve is
+    # redone by the FP64 factorisation of the same H (counted), unless the
+    # fallback is off, when the refinement's failure is reported
+    s, c = _scene("small_elbow")
+    S0, H = _oracle_H(s, c)
+    sol = _solver(pd, s, max_refine=1)
+    sol.set_contacts(*contact_tuple(c))
+    g = rng(5).normal(size=(s.m, 3)) * 1e3
+    for i, p in enumerate(PRECS):
+        sol.set_precision(getattr(pd, p))
+        u = sol.schur_solve(g)
+        res = np.linalg.norm(g - H @ u) / np.linalg.norm(g)
+        assert res <= TOL, (p, res)
+        assert sol.stats()["precision_fallbacks"] == i + 1, p
+    sol.set_precision_fallback(False)
+    for p in PRECS:
+        sol.set_precision(getattr(pd, p))
+        with pytest.raises(pd.PDError) as e:
+            sol.schur_solve(g)
+        assert e.value.name == "PD_ERR_NO_CONVERGENCE", p
+    assert sol.stats()["precision_fallbacks"] == len(PRECS)
+    # in a step: every inner iteration's solve falls back, and the step
+    # matches the FP64 form's from the same state
+    sol.set_precision_fallback(True)
+    x0 = s.X.copy()
+    out = []
+    for p in ("FP32_IR", "FP64"):
+        sol.set_precision(getattr(pd, p))
+        sol.set_state(x0)
+        sol.set_dirichlet(s.dirichlet_positions(52))
+        f0 = sol.stats()["precision_fallbacks"]
+        sol.step(1, region_callback(s, 52, x0))
+        out.append((sol.positions(), sol.stats()["precision_fallbacks"] - f0))
+    assert out[0][1] == s.inner_iters and out[1][1] == 0
+    assert_parity(out[0][0], out[1][0], x0, TOL)
