@@ -5,13 +5,14 @@
 // Tile (i, j), i >= j, of 128 x 128 is one task: S = A_ij - sum_{kb <= k < j}
 // L_ik L_jk^T is accumulated on the tensor cores (tcgen05, TF32 / split TF32
 // / BF16 operands, FP32 accumulator in tensor memory) from TMA loads that
-// start as soon as the panels they read are final; then either the diagonal
-// tile is factored in FP32 (L_jj, published at once) and inverted (Dinv_j =
-// L_jj^-1, E_j = Dinv_j^T Dinv_j), or the panel tile solves L_ij L_jj^T = S
-// by blocked substitution (published at once) and then forms
-// Lh_ij = L_ij Dinv_j.  A few CTAs take the diagonal tasks in order, the
-// others the panel tasks in column-major order; each waits only on earlier
-// tasks, through per-row counters in global memory; every wait is bounded.
+// start as soon as the panels they read are final; then either the panel
+// tile solves L_ij L_jj^T = S by blocked substitution (published at once) and
+// then forms Lh_ij = L_ij Dinv_j, or, for a diagonal tile, S_jj goes back to
+// global memory, where one CTA that does nothing else factors it in FP32
+// (L_jj, published at once) and a few others invert it (Dinv_j = L_jj^-1,
+// E_j = Dinv_j^T Dinv_j).  The tensor-core tasks run in column-major order;
+// each task waits only on earlier ones, through per-row counters in global
+// memory; every wait is bounded.
 #pragma once
 #include <cstddef>
 #include <cstdint>
@@ -41,7 +42,7 @@ struct Args {
   int* piv = nullptr;                    // [0] first non-positive pivot + 1 (replaced by 1 in the factor)
 };
 
-inline size_t sync_bytes(int T) { return sizeof(int) * (2 + 2 * (size_t)T); }
+inline size_t sync_bytes(int T) { return sizeof(int) * (2 + 3 * (size_t)T); }
 
 // Launch the factorisation of tile columns kb .. T-1 on st.
 cudaError_t factor(pdtc::Mode mode, const Args& a, cudaStream_t st);

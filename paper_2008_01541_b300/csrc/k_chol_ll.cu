@@ -1,20 +1,22 @@
 // Persistent left-looking low-precision Cholesky (see chol_ll.h).
 //
-// One CTA of 256 threads per SM, each running tasks until the list is done:
+// One CTA of 256 threads per SM, each running tasks until its list is done.
+// CTA 0 factors the diagonal tiles in order (FP32, shared memory); a few CTAs
+// invert them; the rest run the tensor-core tasks, in which
 //   warp 0, lane 0 : producer -- waits until the panels L_ik and L_jk of the
 //                    next K step are final (per-row counters), then TMA-loads
 //                    their 128-byte column chunks into a ring of shared-memory
 //                    stages (128B swizzle, K-major);
 //   warp 1, lane 0 : issues the tcgen05 MMAs of each stage into the 128 x 128
 //                    FP32 accumulator in tensor memory and frees the stage;
-//   warps 4-7      : read the accumulator (one TMEM lane quarter each) and
-//                    form S = A_ij - acc in shared memory;
-//   all 256        : the diagonal-tile factor and inverse, or the panel
-//                    products, from shared memory.
-// A task waits only on tasks that precede it in the column-major list, so
-// the grid (all CTAs co-resident) always progresses.  Every wait is bounded;
-// a wait that gives up writes a code to status[1], which makes every other
-// CTA stop at its next wait or claim.
+//   all 8 warps    : read the accumulator (warp w the TMEM lane quarter w % 4,
+//                    half the columns) and form S = A_ij - acc in shared
+//                    memory; then the panel products, or S_jj back to global
+//                    memory for CTA 0.
+// A task waits only on tasks that precede it in these orders, so the grid
+// (all CTAs co-resident) always progresses.  Every wait is bounded; a wait
+// that gives up writes a code to status[1], which makes every other CTA stop
+// at its next wait or claim.
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -35,7 +37,7 @@ using pdm::PADW;
 constexpr int SP = NB + 4;                // row stride of the transposed operands of the panel products
 constexpr uint32_t kSpin = 1u << 22;      // bounded waits: ~1 s with back-off
 constexpr int kStageBudget = 196608;      // shared memory for the pipeline stages (192 KB)
-constexpr int kDiagCtas = 6;              // CTAs dedicated to the diagonal tasks
+constexpr int kDiagCtas = 6;              // CTAs for the diagonal tiles: one factors, the others invert
 
 template <int MODE>   // 0 = TF32, 1 = split TF32 (hi.hi + hi.lo + lo.hi), 2 = BF16
 struct Cfg {
@@ -49,7 +51,7 @@ struct Cfg {
 };
 
 struct Ptrs {
-  int ndiag;   // CTAs that run the diagonal tasks
+  int ndiag;   // CTAs of the diagonal tiles: the factor CTA, then the inversion CTAs
   float* L;
   float* Llo;
   __nv_bfloat16* Lb;
@@ -136,8 +138,8 @@ __device__ __forceinline__ void prod_8x8(const float* X, const float* Y, int ty,
 // against the 32 x 32 diagonal block with its 32 unknowns in registers,
 // x_k = (s_k - sum_{t < k} L_kt x_t) / L_kk, reading each row of L with
 // 16-byte broadcasts; then all 256 threads remove the block's contribution
-// from the later columns (row r = tid & 127, half of those columns each),
-// again one 16-byte load per four multiply-adds.
+// from the later columns (rows r and r + 64, r = tid & 63, a quarter of
+// those columns each), one 16-byte load per eight multiply-adds.
 __device__ __forceinline__ void panel_substitution(float* XT, const float* Lj, const float* rinv) {
   const int tid = threadIdx.x;
 #pragma unroll 1
@@ -172,24 +174,57 @@ __device__ __forceinline__ void panel_substitution(float* XT, const float* Lj, c
     __syncthreads();
     const int rest = NB - c0 - 32;
     if (rest > 0) {
-      const int r = tid & 127, half = tid >> 7, n = rest / 2, cbeg = c0 + 32 + half * n;
-      float x[32];
+      // rows r and r + 64 (r = tid & 63), a quarter of the later columns
+      // each: every 16-byte row of L read serves both rows
+      const int r = tid & 63, n = rest / 4, cbeg = c0 + 32 + (tid >> 6) * n;
+      float x[32], y[32];
 #pragma unroll
-      for (int k = 0; k < 32; ++k) x[k] = XT[(c0 + k) * SP + r];
+      for (int k = 0; k < 32; ++k) {
+        x[k] = XT[(c0 + k) * SP + r];
+        y[k] = XT[(c0 + k) * SP + r + 64];
+      }
 #pragma unroll 1
       for (int c = cbeg; c < cbeg + n; ++c) {
         const float4* lr = reinterpret_cast<const float4*>(Lj + c * SP + c0);
-        float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+        float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f, q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
 #pragma unroll
         for (int t4 = 0; t4 < 8; ++t4) {
           const float4 l = lr[t4];
           p0 = fmaf(l.x, x[4 * t4], p0); p1 = fmaf(l.y, x[4 * t4 + 1], p1);
           p2 = fmaf(l.z, x[4 * t4 + 2], p2); p3 = fmaf(l.w, x[4 * t4 + 3], p3);
+          q0 = fmaf(l.x, y[4 * t4], q0); q1 = fmaf(l.y, y[4 * t4 + 1], q1);
+          q2 = fmaf(l.z, y[4 * t4 + 2], q2); q3 = fmaf(l.w, y[4 * t4 + 3], q3);
         }
         XT[c * SP + r] -= (p0 + p1) + (p2 + p3);
+        XT[c * SP + r + 64] -= (q0 + q1) + (q2 + q3);
       }
     }
     __syncthreads();
+  }
+}
+
+// The 128 x 128 tile at src (global, row stride ld) into shared memory (row
+// stride SP), sixteen 16-byte loads per thread all in flight; and back.
+__device__ __forceinline__ void load_tile(float* dst, const float* src, int64_t ld) {
+  const int tid = threadIdx.x;
+  float4 v[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int q = tid + 256 * k, r = q >> 5, c = 4 * (q & 31);
+    v[k] = __ldcg(reinterpret_cast<const float4*>(src + (int64_t)r * ld + c));
+  }
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int q = tid + 256 * k, r = q >> 5, c = 4 * (q & 31);
+    *reinterpret_cast<float4*>(dst + r * SP + c) = v[k];
+  }
+}
+__device__ __forceinline__ void store_tile(float* dst, int64_t ld, const float* src) {
+  const int tid = threadIdx.x;
+#pragma unroll 4
+  for (int k = 0; k < 16; ++k) {
+    const int q = tid + 256 * k, r = q >> 5, c = 4 * (q & 31);
+    *reinterpret_cast<float4*>(dst + (int64_t)r * ld + c) = *reinterpret_cast<const float4*>(src + r * SP + c);
   }
 }
 
@@ -216,18 +251,26 @@ __global__ void __launch_bounds__(256, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int T = P.T, kb = P.kb;
   const int64_t mq = P.mq;
-  // Roles: the first NDIAG CTAs run only the diagonal tasks (in order, from
-  // their own counter), the others only the panel tasks (column-major), so
-  // each CTA keeps running the same code and finds it in its instruction
-  // cache.  A diagonal task waits only on panels of earlier columns and a
-  // panel only on earlier diagonals and earlier panels, so both lists
-  // progress.
-  int* claim = P.sync;            // [0] diagonal tasks, [1] panel tasks
+  // Roles.  CTA 0 factors the diagonal tiles, in order, and does nothing
+  // else: the factor is long unrolled code on the critical path, and it runs
+  // from a cold instruction cache on an SM (or beside a TPC partner) that
+  // streams operands through TMA.  The grid is launched as CTA pairs
+  // (clusters of two, one TPC each), so CTA 0 shares its TPC with CTA 1.
+  // CTAs 1 .. NDIAG-1 invert the factored diagonal tiles (Dinv_j, E_j),
+  // claiming them in order.  The others run the tensor-core tasks in
+  // column-major order: the panels (i, j), and after the first panel of
+  // column j the accumulation S_j+1,j+1 = A - sum L L^T of the next diagonal
+  // tile, which they write back to its tile of L for CTA 0.  Each task waits
+  // only on tasks earlier in these orders, so all progress.
+  int* claim = P.sync;            // [0] inversions, [1] tensor-core tasks
   int* rowcnt = P.sync + 2;       // [T] finished tiles of row i among columns kb..
   int* dcnt = P.sync + 2 + T;     // [T] Dinv_j written
+  int* scnt = P.sync + 2 + 2 * T; // [T] S_jj formed (the factor of tile j may start)
   const int nt = T - kb;
-  const bool diag_cta = (int)blockIdx.x < P.ndiag;
-  const int ntask = diag_cta ? nt : nt * (nt - 1) / 2;
+  const int role = blockIdx.x == 0 ? 0 : (int)blockIdx.x < P.ndiag ? 1 : 2;   // factor, inversion, tensor core
+  const int ntask = role < 2 ? nt : nt * (nt + 1) / 2 - 1;
+  int fnext = 0;   // the factor CTA's next tile (thread 0)
+
   constexpr int KIND = MODE == 2 ? 1 : 0;
   constexpr uint32_t ID = idesc(MODE == 2 ? 1u : 2u);
 
@@ -255,22 +298,74 @@ __global__ void __launch_bounds__(256, 1)
   float* DT = ST + NB * SP;                   //   and the right operand [128][SP]
 
   for (;;) {
-    if (tid == 0) s_task = (s_stop || failed_globally(P.status)) ? ntask : atomicAdd(claim + (diag_cta ? 0 : 1), 1);
+    if (tid == 0)
+      s_task = (s_stop || failed_globally(P.status)) ? ntask : role == 0 ? fnext++ : atomicAdd(claim + role - 1, 1);
     __syncthreads();
     const int t = s_task;
     if (t >= ntask) break;
     int i, j;
-    if (diag_cta) {
+    if (role < 2) {
       i = j = kb + t;
-    } else {   // column-major over the tiles below the diagonal of columns kb .. T-2
+    } else {   // column j = kb .. T-2: panel (j+1, j), the accumulation of tile j+1, panels (j+2 .., j)
       int rem = t;
       j = kb;
-      while (rem >= T - j - 1) { rem -= T - j - 1; ++j; }
-      i = j + 1 + rem;
+      while (rem >= T - j) { rem -= T - j; ++j; }
+      if (rem == 1) i = j = j + 1;
+      else i = j + (rem == 0 ? 1 : rem);
     }
     const bool diag = i == j;
-    const int nchunk = (j - kb) * C::CPP;
+    const int nchunk = role == 2 ? (j - kb) * C::CPP : 0;
     float* Lt = P.L + (int64_t)i * NB * mq + (int64_t)j * NB;
+
+    if (role == 0) {
+      // ---- L_jj from S_jj (written by the accumulation task; A_jj itself
+      // for the first column), published at once
+      if (j > kb && tid == 0 && !wait_flag(scnt + j, 1, P.status, 318)) s_stop = 1;
+      __syncthreads();
+      if (s_stop) continue;
+      load_tile(A, Lt, mq);
+      __syncthreads();
+      pdm::diag_factor_f4(A, j, P.piv);
+      store_tile(Lt, mq, A);   // whole rows: the strict upper triangle of a diagonal tile of L is scratch
+      __syncthreads();
+      if (tid == 0) {   // the panels of column j solve against L_jj
+        __threadfence();
+        st_release(rowcnt + j, j - kb + 1);
+      }
+      continue;
+    }
+    if (role == 1) {
+      // ---- Dinv_j (the panels' Lh products wait for it), then E_j for the preconditioner
+      if (tid == 0 && !wait_flag(rowcnt + j, j - kb + 1, P.status, 319)) s_stop = 1;
+      __syncthreads();
+      if (s_stop) continue;
+      load_tile(A, Lt, mq);
+      __syncthreads();
+      float* Di = P.Dinv + (int64_t)j * NB * NB;
+      pdm::tile_inverse<SP>(A, Zd, Di);
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        st_release(dcnt + j, 1);
+      }
+      float* Dsm = A;   // Dinv_j again, padded rows
+#pragma unroll 4
+      for (int k = 0; k < 16; ++k) {
+        const int q = tid + 256 * k, r = q >> 5, c = 4 * (q & 31);
+        const float4 v = __ldcg(reinterpret_cast<const float4*>(Di + r * NB + c));
+        Dsm[r * PADW + c] = v.x; Dsm[r * PADW + c + 1] = v.y; Dsm[r * PADW + c + 2] = v.z; Dsm[r * PADW + c + 3] = v.w;
+      }
+      __syncthreads();
+      float* Ej = P.E + (int64_t)j * NB * NB;
+      for (int q = tid; q < NB * NB; q += 256) {   // E[r][c] = sum_{t >= max(r, c)} Dinv[t][r] Dinv[t][c]
+        const int r = q / NB, c = q % NB;
+        float e = 0.f;
+        for (int t2 = (r > c ? r : c); t2 < NB; ++t2) e = fmaf(Dsm[t2 * PADW + r], Dsm[t2 * PADW + c], e);
+        Ej[q] = e;
+      }
+      __syncthreads();
+      continue;
+    }
 
     // ---- acc = sum_{kb <= k < j} L_ik L_jk^T on the tensor cores
     if (nchunk > 0) {
@@ -344,23 +439,27 @@ __global__ void __launch_bounds__(256, 1)
     // ---- S = A_ij - acc into shared memory (row-major for the diagonal
     // factor, transposed for the panel products)
     if (nchunk > 0) {
-      if (warp >= 4) {
-        const int r = 32 * (warp - 4) + lane;
-        const float* arow = Lt + (int64_t)r * mq;
+      // all eight warps: warp w reads the accumulator lanes of its
+      // sub-partition, 32 (w & 3) .. + 31, in columns 64 (w >> 2) .. + 63
+      const int r = 32 * (warp & 3) + lane;
+      const float* arow = Lt + (int64_t)r * mq;
 #pragma unroll 1
-        for (int c0 = 0; c0 < NB; c0 += 32) {
-          float v[32];
-          tmem_ld32(tmem + ((uint32_t)(32 * (warp - 4)) << 16) + (uint32_t)c0, v);
+      for (int c0 = 64 * (warp >> 2); c0 < 64 * (warp >> 2) + 64; c0 += 32) {
+        float4 a[8];
 #pragma unroll
-          for (int q4 = 0; q4 < 8; ++q4) {
-            const float4 a = __ldcg(reinterpret_cast<const float4*>(arow + c0 + 4 * q4));
-            const float e[4] = {a.x - v[4 * q4], a.y - v[4 * q4 + 1], a.z - v[4 * q4 + 2], a.w - v[4 * q4 + 3]};
+        for (int q4 = 0; q4 < 8; ++q4) a[q4] = __ldcg(reinterpret_cast<const float4*>(arow + c0 + 4 * q4));
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0, v);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const int c = c0 + 4 * q4 + u;
-              if (diag) A[r * SP + c] = e[u];
-              else ST[c * SP + r] = e[u];
-            }
+        for (int q4 = 0; q4 < 8; ++q4) {
+          const float e[4] = {a[q4].x - v[4 * q4], a[q4].y - v[4 * q4 + 1], a[q4].z - v[4 * q4 + 2],
+                              a[q4].w - v[4 * q4 + 3]};
+          const int c = c0 + 4 * q4;
+          if (diag) {
+            *reinterpret_cast<float4*>(A + r * SP + c) = make_float4(e[0], e[1], e[2], e[3]);
+          } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) ST[(c + u) * SP + r] = e[u];
           }
         }
       }
@@ -383,53 +482,21 @@ __global__ void __launch_bounds__(256, 1)
     __syncthreads();
 
     if (diag) {
-      // ---- L_jj (the panels of column j wait for it), then Dinv_j (their Lh
-      // products wait for it), then E_j for the preconditioner
-      pdm::diag_factor_f4(A, j, P.piv);
-      for (int q = tid; q < NB * NB; q += 256) {
-        const int r = q / NB, c = q % NB;
-        if (c <= r) Lt[(int64_t)r * mq + c] = A[r * SP + c];
-      }
+      // ---- accumulation task: S_jj back into its tile of L, for the factor CTA
+      store_tile(Lt, mq, A);
       __syncthreads();
-      if (tid == 0) {   // the panels of column j solve against L_jj
+      if (tid == 0) {
         __threadfence();
-        st_release(rowcnt + j, j - kb + 1);
-      }
-      float* Di = P.Dinv + (int64_t)j * NB * NB;
-      pdm::tile_inverse<SP>(A, Zd, Di);
-      __syncthreads();
-      if (tid == 0) {   // their Lh products need Dinv_j
-        __threadfence();
-        st_release(dcnt + j, 1);
-      }
-      float* Dsm = A;   // Dinv_j again, padded rows
-#pragma unroll 4
-      for (int k = 0; k < 16; ++k) {
-        const int q = tid + 256 * k, r = q >> 5, c = 4 * (q & 31);
-        const float4 v = __ldcg(reinterpret_cast<const float4*>(Di + r * NB + c));
-        Dsm[r * PADW + c] = v.x; Dsm[r * PADW + c + 1] = v.y; Dsm[r * PADW + c + 2] = v.z; Dsm[r * PADW + c + 3] = v.w;
-      }
-      __syncthreads();
-      float* Ej = P.E + (int64_t)j * NB * NB;
-      for (int q = tid; q < NB * NB; q += 256) {   // E[r][c] = sum_{t >= max(r, c)} Dinv[t][r] Dinv[t][c]
-        const int r = q / NB, c = q % NB;
-        float e = 0.f;
-        for (int t2 = (r > c ? r : c); t2 < NB; ++t2) e = fmaf(Dsm[t2 * PADW + r], Dsm[t2 * PADW + c], e);
-        Ej[q] = e;
+        st_release(scnt + j, 1);
       }
     } else {
       // ---- L_ij from L_ij L_jj^T = S once L_jj is final; then Lh_ij = L_ij Dinv_j
+      float* Lj = DT;                      // L_jj, rows of SP
+      __shared__ float rinv[NB];
       if (tid == 0 && !wait_flag(rowcnt + j, j - kb + 1, P.status, 316)) s_stop = 1;
       __syncthreads();
       if (s_stop) continue;
-      float* Lj = DT;                      // L_jj, rows of SP
-      __shared__ float rinv[NB];
-      const float* Ljg = P.L + (int64_t)j * NB * mq + (int64_t)j * NB;
-#pragma unroll 4
-      for (int k = 0; k < 16; ++k) {
-        const int q = tid + 256 * k, r = q >> 5, c = 4 * (q & 31);
-        *reinterpret_cast<float4*>(Lj + r * SP + c) = __ldcg(reinterpret_cast<const float4*>(Ljg + (int64_t)r * mq + c));
-      }
+      load_tile(Lj, P.L + (int64_t)j * NB * mq + (int64_t)j * NB, mq);
       __syncthreads();
       if (tid < NB) rinv[tid] = 1.f / Lj[tid * SP + tid];
       __syncthreads();
@@ -495,21 +562,50 @@ cudaError_t launch(const Args& a, Ptrs p, int ntask, cudaStream_t st) {
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chol_ll<MODE>, 256, Cfg<MODE>::SMEM);
     per_dev[dev & 63] = nsm * std::max(per, 1);   // one persistent CTA per SM
+    // and no more CTA pairs than fit at once (every CTA must be resident)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)per_dev[dev & 63]);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = Cfg<MODE>::SMEM;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, k_chol_ll<MODE>, &cfg) == cudaSuccess && ncl > 0)
+      per_dev[dev & 63] = std::min(per_dev[dev & 63], 2 * ncl);
   }
   // By default two thirds of the SMs: the chain of diagonal tiles, not the
   // tensor-core work, sets the time, and the remaining SMs run the main
   // stream's local step and sparse substitution concurrently.
   int cap = a.max_ctas > 0 ? std::min(per_dev[dev & 63], a.max_ctas) : std::max(8, 2 * per_dev[dev & 63] / 3);
-  // a few diagonal CTAs (each diagonal task is claimed several steps before
-  // it is on the critical chain, time to accumulate its operands), the rest
-  // panel CTAs
+  // one factor CTA, a few inversion CTAs (each inversion is off the
+  // critical chain), the rest tensor-core CTAs
   const int nt = a.T - a.kb;
-  p.ndiag = std::min(nt, kDiagCtas);
-  const int grid = std::max(p.ndiag + 1, std::min(p.ndiag + ntask, cap));
+  p.ndiag = 1 + std::min(nt, kDiagCtas - 1);   // the factor CTA and the inversion CTAs
+  int grid = std::max(p.ndiag + 1, std::min(p.ndiag + ntask, cap));
+  grid += grid & 1;
   const CUtensorMap& lo = a.map_lo ? *a.map_lo : *a.map_hi;
-  k_chol_ll<MODE><<<grid, 256, Cfg<MODE>::SMEM, st>>>(*a.map_hi, lo, p);
+  // Clusters of two: CTA 0 (the factor) shares its TPC with CTA 1 (an
+  // inversion CTA, no TMA traffic) rather than with a tensor-core CTA.
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = Cfg<MODE>::SMEM;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_chol_ll<MODE>, *a.map_hi, lo, p);
   ++pdk::g_launches;
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace
@@ -523,7 +619,7 @@ cudaError_t factor(pdtc::Mode mode, const Args& a, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(a.sync, 0, sync_bytes(a.T), st);
   if (e != cudaSuccess) return e;
   const Ptrs p{0, a.L, a.Llo, a.Lb, a.Lh, a.Dinv, a.E, a.mq, a.T, a.kb, a.sync, a.status, a.piv};
-  const int ntask = nt * (nt - 1) / 2;   // panel tasks
+  const int ntask = nt * (nt + 1) / 2 - 1;   // panel and accumulation tasks
   switch (mode) {
     case pdtc::TF32X3: return launch<1>(a, p, ntask, st);
     case pdtc::BF16: return launch<2>(a, p, ntask, st);
