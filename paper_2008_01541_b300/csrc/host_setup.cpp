@@ -234,6 +234,101 @@ void trinv(double* L, int64_t ld, int64_t nc) {
 
 }  // namespace
 
+// The numeric phase on the host: multifrontal partial Cholesky with x_2 never
+// pivoted (Eq. 9), L (diagonal blocks inverted) into s.Lval and Sigma_0.
+int numeric_phase(Setup& s, LowerCSC& A, double& t_num, std::string* err) {
+  const int64_t n1 = s.n1, m = s.m, nf = n1 + m, nsn = s.nsn;
+  try {
+    s.Lval.assign(s.nnzL, 0.0);
+  } catch (...) {
+    *err = "host allocation of the interior factor failed";
+    return ST_OOM;
+  }
+  // ---- numeric: multifrontal partial Cholesky, x_2 never pivoted (Eq. 9)
+  std::vector<double> Sig((size_t)m * m, 0.0);   // Sigma_alpha, column-major = row-major (symmetric)
+  for (int64_t j = n1; j < nf; ++j)
+    for (int64_t q = A.colptr[j]; q < A.colptr[j + 1]; ++q) {
+      int64_t i = A.row[q];
+      Sig[(i - n1) + (j - n1) * m] += A.val[q];
+      if (i != j) Sig[(j - n1) + (i - n1) * m] += A.val[q];
+    }
+  struct Upd { int32_t sn; std::vector<double> U; };
+  std::vector<Upd> stack;
+  std::vector<int32_t> loc(nf, -1);
+  double flops = 0.0;
+  for (int64_t k = 0; k < nsn; ++k) {
+    const int64_t c0 = s.sn_col0[k], nc = s.sn_col0[k + 1] - c0;
+    const int64_t nr = s.sn_rowptr[k + 1] - s.sn_rowptr[k];
+    const int32_t* R = &s.rows[s.sn_rowptr[k]];
+    const int64_t fsz = nc + nr;
+    std::vector<double> F;
+    try { F.assign(fsz * fsz, 0.0); } catch (...) { *err = "host allocation of a front failed"; return ST_OOM; }
+    for (int64_t c = 0; c < nc; ++c) loc[c0 + c] = (int32_t)c;
+    for (int64_t r = 0; r < nr; ++r) loc[R[r]] = (int32_t)(nc + r);
+    for (int64_t c = 0; c < nc; ++c) {
+      int64_t j = c0 + c;
+      for (int64_t q = A.colptr[j]; q < A.colptr[j + 1]; ++q) F[loc[A.row[q]] + c * fsz] += A.val[q];
+    }
+    // extend-add the children's update matrices (top of the stack)
+    while (!stack.empty() && s.sn_parent[stack.back().sn] == k) {
+      Upd& u = stack.back();
+      int64_t cn = s.sn_rowptr[u.sn + 1] - s.sn_rowptr[u.sn];
+      const int32_t* CR = &s.rows[s.sn_rowptr[u.sn]];
+      for (int64_t b = 0; b < cn; ++b) {
+        int64_t lb = loc[CR[b]];
+        double* Fc = &F[lb * fsz];
+        const double* Uc = &u.U[b * cn];
+        for (int64_t a = b; a < cn; ++a) Fc[loc[CR[a]]] += Uc[a];
+      }
+      stack.pop_back();
+    }
+    if (!potrf(F.data(), fsz, nc)) {
+      *err = "interior matrix is not positive definite (a free part without a Dirichlet node?)";
+      return ST_NOT_SPD;
+    }
+    trsm(F.data(), fsz, nc, nr);
+    syrk(F.data(), fsz, nc, nr);
+    flops += nc * nc * nc / 3.0 + (double)nr * nc * nc + (double)nr * nr * nc;
+    double* P = &s.Lval[s.sn_valptr[k]];
+    for (int64_t c = 0; c < nc; ++c) std::memcpy(P + c * fsz, &F[c * fsz], sizeof(double) * fsz);
+    trinv(P, fsz, nc);
+    if (nr > 0) {
+      if (s.sn_parent[k] >= 0) {
+        Upd u;
+        u.sn = (int32_t)k;
+        u.U.resize(nr * nr);
+        for (int64_t b = 0; b < nr; ++b)
+          for (int64_t a = b; a < nr; ++a) u.U[a + b * nr] = F[(nc + a) + (nc + b) * fsz];
+        stack.push_back(std::move(u));
+      } else {
+        // every remaining row is in x_2: add into Sigma_alpha (both triangles)
+        for (int64_t b = 0; b < nr; ++b) {
+          int64_t gb = R[b] - n1;
+          for (int64_t a = b; a < nr; ++a) {
+            int64_t ga = R[a] - n1;
+            double v = F[(nc + a) + (nc + b) * fsz];
+            Sig[ga + gb * m] += v;
+            if (ga != gb) Sig[gb + ga * m] += v;
+          }
+        }
+      }
+    }
+    for (int64_t c = 0; c < nc; ++c) loc[c0 + c] = -1;
+    for (int64_t r = 0; r < nr; ++r) loc[R[r]] = -1;
+  }
+  s.factor_flops = flops;
+  t_num = now_ms();
+
+  // Sigma_0 = Sigma_alpha + A22^beta (+ M_2/dt^2)
+  s.Sigma0.swap(Sig);
+  for (int64_t j = 0; j < m; ++j)
+    for (int64_t q = s.B22.colptr[j]; q < s.B22.colptr[j + 1]; ++q)
+      s.Sigma0[s.B22.row[q] + j * m] += s.B22.val[q];
+  A = LowerCSC();   // not needed once Sigma_0 and L are formed
+  return 0;
+}
+
+
 int build(const Input& in, Setup& s, std::string* err) {
   double t0 = now_ms();
   const int64_t n = in.n, E = in.E, m = in.m;
@@ -419,7 +514,7 @@ int build(const Input& in, Setup& s, std::string* err) {
 
   // ---- assemble the alpha matrix (lower, final positions) and B22 = A22^beta (+ M2/dt^2)
   const int64_t nf = n1 + m;
-  LowerCSC A;
+  LowerCSC& A = s.A;
   {
     std::vector<std::pair<int64_t, double>> trip;
     trip.reserve(s.alpha.size() * 10 + n1);
@@ -560,94 +655,13 @@ int build(const Input& in, Setup& s, std::string* err) {
   s.nlevels = 0;
   for (int64_t k = 0; k < nsn; ++k) s.nlevels = std::max<int64_t>(s.nlevels, s.sn_level[k] + 1);
   s.nnzL = s.sn_valptr[nsn];
-  try {
-    s.Lval.assign(s.nnzL, 0.0);
-  } catch (...) {
-    *err = "host allocation of the interior factor failed";
-    return ST_OOM;
-  }
   double t_sym = now_ms();
 
-  // ---- numeric: multifrontal partial Cholesky, x_2 never pivoted (Eq. 9)
-  std::vector<double> Sig((size_t)m * m, 0.0);   // Sigma_alpha, column-major = row-major (symmetric)
-  for (int64_t j = n1; j < nf; ++j)
-    for (int64_t q = A.colptr[j]; q < A.colptr[j + 1]; ++q) {
-      int64_t i = A.row[q];
-      Sig[(i - n1) + (j - n1) * m] += A.val[q];
-      if (i != j) Sig[(j - n1) + (i - n1) * m] += A.val[q];
-    }
-  struct Upd { int32_t sn; std::vector<double> U; };
-  std::vector<Upd> stack;
-  std::vector<int32_t> loc(nf, -1);
-  double flops = 0.0;
-  for (int64_t k = 0; k < nsn; ++k) {
-    const int64_t c0 = s.sn_col0[k], nc = s.sn_col0[k + 1] - c0;
-    const int64_t nr = s.sn_rowptr[k + 1] - s.sn_rowptr[k];
-    const int32_t* R = &s.rows[s.sn_rowptr[k]];
-    const int64_t fsz = nc + nr;
-    std::vector<double> F;
-    try { F.assign(fsz * fsz, 0.0); } catch (...) { *err = "host allocation of a front failed"; return ST_OOM; }
-    for (int64_t c = 0; c < nc; ++c) loc[c0 + c] = (int32_t)c;
-    for (int64_t r = 0; r < nr; ++r) loc[R[r]] = (int32_t)(nc + r);
-    for (int64_t c = 0; c < nc; ++c) {
-      int64_t j = c0 + c;
-      for (int64_t q = A.colptr[j]; q < A.colptr[j + 1]; ++q) F[loc[A.row[q]] + c * fsz] += A.val[q];
-    }
-    // extend-add the children's update matrices (top of the stack)
-    while (!stack.empty() && s.sn_parent[stack.back().sn] == k) {
-      Upd& u = stack.back();
-      int64_t cn = s.sn_rowptr[u.sn + 1] - s.sn_rowptr[u.sn];
-      const int32_t* CR = &s.rows[s.sn_rowptr[u.sn]];
-      for (int64_t b = 0; b < cn; ++b) {
-        int64_t lb = loc[CR[b]];
-        double* Fc = &F[lb * fsz];
-        const double* Uc = &u.U[b * cn];
-        for (int64_t a = b; a < cn; ++a) Fc[loc[CR[a]]] += Uc[a];
-      }
-      stack.pop_back();
-    }
-    if (!potrf(F.data(), fsz, nc)) {
-      *err = "interior matrix is not positive definite (a free part without a Dirichlet node?)";
-      return ST_NOT_SPD;
-    }
-    trsm(F.data(), fsz, nc, nr);
-    syrk(F.data(), fsz, nc, nr);
-    flops += nc * nc * nc / 3.0 + (double)nr * nc * nc + (double)nr * nr * nc;
-    double* P = &s.Lval[s.sn_valptr[k]];
-    for (int64_t c = 0; c < nc; ++c) std::memcpy(P + c * fsz, &F[c * fsz], sizeof(double) * fsz);
-    trinv(P, fsz, nc);
-    if (nr > 0) {
-      if (s.sn_parent[k] >= 0) {
-        Upd u;
-        u.sn = (int32_t)k;
-        u.U.resize(nr * nr);
-        for (int64_t b = 0; b < nr; ++b)
-          for (int64_t a = b; a < nr; ++a) u.U[a + b * nr] = F[(nc + a) + (nc + b) * fsz];
-        stack.push_back(std::move(u));
-      } else {
-        // every remaining row is in x_2: add into Sigma_alpha (both triangles)
-        for (int64_t b = 0; b < nr; ++b) {
-          int64_t gb = R[b] - n1;
-          for (int64_t a = b; a < nr; ++a) {
-            int64_t ga = R[a] - n1;
-            double v = F[(nc + a) + (nc + b) * fsz];
-            Sig[ga + gb * m] += v;
-            if (ga != gb) Sig[gb + ga * m] += v;
-          }
-        }
-      }
-    }
-    for (int64_t c = 0; c < nc; ++c) loc[c0 + c] = -1;
-    for (int64_t r = 0; r < nr; ++r) loc[R[r]] = -1;
+  double t_num = t_sym;
+  if (in.numeric) {
+    int st = numeric_phase(s, A, t_num, err);
+    if (st) return st;
   }
-  s.factor_flops = flops;
-  double t_num = now_ms();
-
-  // Sigma_0 = Sigma_alpha + A22^beta (+ M_2/dt^2)
-  s.Sigma0.swap(Sig);
-  for (int64_t j = 0; j < m; ++j)
-    for (int64_t q = s.B22.colptr[j]; q < s.B22.colptr[j + 1]; ++q)
-      s.Sigma0[s.B22.row[q] + j * m] += s.B22.val[q];
 
   // ---- gather maps
   auto build_gather = [](int64_t ntarget, const std::vector<int32_t>& elems, const int32_t* tets,
@@ -679,7 +693,7 @@ int build(const Input& in, Setup& s, std::string* err) {
            "n=%lld n1=%lld m=%lld alpha=%zu beta=%zu supernodes=%lld levels=%lld nnzL=%lld "
            "flops=%.3g | nd %.0f ms, assemble %.0f ms, symbolic %.0f ms, numeric %.0f ms, total %.0f ms",
            (long long)n, (long long)n1, (long long)m, s.alpha.size(), s.beta.size(), (long long)nsn,
-           (long long)s.nlevels, (long long)s.nnzL, flops, t_nd - t0, t_asm - t_nd, t_sym - t_asm,
+           (long long)s.nlevels, (long long)s.nnzL, s.factor_flops, t_nd - t0, t_asm - t_nd, t_sym - t_asm,
            t_num - t_sym, s.ms_total);
   s.log = buf;
   return 0;

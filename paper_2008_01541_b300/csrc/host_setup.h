@@ -19,6 +19,7 @@ struct Input {
   int64_t m = 0;
   const int32_t* dirichlet = nullptr;
   int64_t nd = 0;
+  bool numeric = true;   // false: stop after the symbolic analysis (the device forms L and Sigma_0)
 };
 
 // Sparse symmetric matrix, lower triangle, compressed by column.
@@ -45,14 +46,15 @@ struct Setup {
   std::vector<int64_t> sn_rowptr; // [nsn+1] into rows
   std::vector<int32_t> rows;      // off-diagonal row positions (may be >= n1: x_2 rows)
   std::vector<int64_t> sn_valptr; // [nsn+1] into Lval; panel is (nc+nr) x nc column-major
-  std::vector<double> Lval;       // diag block holds L_ss^-1 (lower), then L_rs
+  std::vector<double> Lval;       // diag block holds L_ss^-1 (lower), then L_rs (empty unless numeric)
   std::vector<int32_t> sn_parent; // parent supernode, -1 = the x_2 root
   std::vector<int32_t> sn_level;  // height above the leaves
   int64_t nlevels = 0;
   int64_t nnzL = 0;
   double factor_flops = 0;
+  LowerCSC A;                     // the alpha matrix (lower, factor positions; kept unless numeric)
   // --- dense collision-region block ---
-  std::vector<double> Sigma0;     // [m][m] = Sigma_alpha + A22^beta (+ M_2/dt^2)
+  std::vector<double> Sigma0;     // [m][m] = Sigma_alpha + A22^beta (+ M_2/dt^2) (empty unless numeric)
   LowerCSC B22;                   // A22^beta (+ M_2/dt^2), region indices, full symmetric pattern
   // --- gather maps: for each target, the element-vertex slots (e*4 + a) ---
   std::vector<int64_t> ga_ptr; std::vector<int32_t> ga_slot;  // alpha -> free positions [nfree]

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <queue>
 #include <string>
@@ -12,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include "host_setup.h"
+#include "setup_dev.h"
 #include "kernels.h"
 #include "mixed.h"
 #include "mlp.h"
@@ -384,6 +386,7 @@ pd_status pd_setup(const pd_mesh* mesh, const pd_material* mat, double dt, const
   in.n = mesh->n_nodes; in.E = mesh->n_tets; in.X = mesh->rest_pos; in.tets = mesh->tets;
   in.mu = mat->mu; in.mu_prime = mat->mu_prime; in.kappa = mat->kappa; in.density = mat->density; in.dt = dt;
   in.region = region; in.m = m; in.dirichlet = dirichlet; in.nd = nd;
+  in.numeric = false;   // L and Sigma_0 are formed on the device (upload)
   pdh::Setup h;
   std::string err;
   int st;
@@ -405,7 +408,9 @@ pd_status pd_setup(const pd_mesh* mesh, const pd_material* mat, double dt, const
     return rs;
   }
   s->stats.setup_ms = now_ms() - t0;
-  s->setup_log = h.log;
+  char nb[64];
+  std::snprintf(nb, sizeof nb, " | device numeric %.0f ms", s->numeric_ms);
+  s->setup_log = h.log + nb;
   *out = s;
   return PD_OK;
 }
@@ -1004,7 +1009,7 @@ pd_status pd_solver::upload(const pdh::Setup& h, const pdh::Input& in) {
   CK(dupload(s, &sn_rowptr, h.sn_rowptr.data(), h.sn_rowptr.size()));
   CK(dupload(s, &rows, h.rows.data(), h.rows.size()));
   CK(dupload(s, &sn_valptr, h.sn_valptr.data(), h.sn_valptr.size()));
-  CK(dupload(s, &Lval, h.Lval.data(), h.Lval.size()));
+  CK(dalloc(s, &Lval, (size_t)h.nnzL));
   {
     int64_t nl = h.nlevels;
     std::vector<std::vector<int32_t>> bylevel(nl);
@@ -1153,7 +1158,17 @@ pd_status pd_solver::upload(const pdh::Setup& h, const pdh::Input& in) {
   CK(dalloc(s, &u, 3 * nfree));
   CK(dalloc(s, &z, 3 * nfree));
   // dense block
-  CK(dupload(s, &Sigma0, h.Sigma0.data(), (size_t)m * m));
+  CK(dalloc(s, &Sigma0, (size_t)m * m));
+  {   // the numeric phase: L_1, L_21 and Sigma_0 (Section 3.1, Eq. 9) on the device
+    std::string e2;
+    const double t2 = now_ms();
+    const int r2 = pdk::numeric_factor(h, Lval, Sigma0, stream, &e2);
+    numeric_ms = now_ms() - t2;
+    if (r2 != 0) {
+      err = e2;
+      return (pd_status)r2;
+    }
+  }
   CK(dupload(s, &b22_ptr, h.B22.colptr.data(), h.B22.colptr.size()));
   CK(dupload(s, &b22_row, h.B22.row.data(), h.B22.row.size()));
   CK(dupload(s, &b22_val, h.B22.val.data(), h.B22.val.size()));

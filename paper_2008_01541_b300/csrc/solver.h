@@ -40,6 +40,7 @@ struct pd_solver {
   std::vector<int32_t> tets_h, region_h, region_index;
   std::unique_ptr<pdh::Setup> hostdata;  // element data kept for pd_local_step
   std::string setup_log;
+  double numeric_ms = 0;   // the numeric phase of the setup on the device
   // device state
   std::vector<void*> allocs;
   double *x = nullptr, *v = nullptr, *x_save = nullptr, *v_save = nullptr, *x_n = nullptr;
