@@ -13,7 +13,8 @@
 //      shared memory for fronts of order <= kSmallFront, else by the blocked
 //      FP64 tile Cholesky of the dense collision block (a partial
 //      factorisation of the front padded to 64-multiples with identity);
-//      the factor panel goes to L with its diagonal block inverted;
+//      the factor panel goes to L as L_ss^-1 over L_rs L_ss^-1, so that
+//      both triangular solves apply each supernode in one step;
 //   3. the update of a front whose parent is x_2 itself (every row in x_2)
 //      is added into Sigma_0, one front per launch in supernode order.
 // Sigma_0 starts as A_22 of the alpha elements and receives A_22 of the beta
@@ -134,7 +135,14 @@ __global__ void __launch_bounds__(256) k_front_small(const int32_t* __restrict__
   double* P = L + f.valptr;   // P[c * n + r]
   for (int idx = tid; idx < n * nc; idx += blockDim.x) {
     const int c = idx / n, r = idx % n;
-    P[idx] = r < nc ? (r < c ? 0.0 : r == c ? dinv[c] : F[c + r * n]) : F[r + c * n];
+    double v;
+    if (r < nc) {
+      v = r < c ? 0.0 : r == c ? dinv[c] : F[c + r * n];
+    } else {   // (L_rs L_ss^-1)[r][c] = sum_{c <= k < nc} L_rk X_kc
+      v = F[r + c * n] * dinv[c];
+      for (int k = c + 1; k < nc; ++k) v = fma(F[r + k * n], F[c + k * n], v);
+    }
+    P[idx] = v;
   }
   for (int idx = tid; idx < f.nr * f.nr; idx += blockDim.x) {
     const int c = nc + idx / f.nr, i = nc + idx % f.nr;
@@ -204,16 +212,54 @@ __global__ void __launch_bounds__(256) k_binv_row(const double* __restrict__ F, 
     for (int q = 0; q < 4; ++q) Xij[(r0 + p) + (int64_t)(c0 + q) * ncp] = -out[p][q];
 }
 
-// The panel of a large front to L: rows < nc from X (zero above the
-// diagonal), the nr off-diagonal rows from the factored front.
-__global__ void k_extract_big(Front f, const double* __restrict__ F, const double* __restrict__ X,
-                              double* __restrict__ L) {
+// The diagonal block of a large front's panel in L: X = L_ss^-1, zero above
+// the diagonal.
+__global__ void k_extract_big(Front f, const double* __restrict__ X, double* __restrict__ L) {
   const int n = f.nc + f.nr;
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)n * f.nc) return;
-  const int c = (int)(idx / n), r = (int)(idx % n);
-  L[f.valptr + idx] = r < f.nc ? (r < c ? 0.0 : X[r + (int64_t)c * f.ncp])
-                               : F[(f.ncp + r - f.nc) + (int64_t)c * f.ld];
+  if (idx >= (int64_t)f.nc * f.nc) return;
+  const int c = (int)(idx / f.nc), r = (int)(idx % f.nc);
+  L[f.valptr + (int64_t)c * n + r] = r < c ? 0.0 : X[r + (int64_t)c * f.ncp];
+}
+
+// The off-diagonal rows of a large front's panel in L: M = L_rs X with
+// X = L_ss^-1 (lower, ncp x ncp), by 64 x 64 tiles: CTA (ri, cj) forms rows
+// 64 ri .. + 63 and columns 64 cj .. + 63 of M from the tiles t >= cj.
+__global__ void __launch_bounds__(256) k_lrs_x(Front f, const double* __restrict__ F, const double* __restrict__ X,
+                                               double* __restrict__ L) {
+  extern __shared__ double sm[];
+  double* As = sm;             // As[k * 65 + r] = L_rs (64 ri + r, 64 t + k)
+  double* Bs = sm + 64 * 65;   // Bs[c * 65 + k] = X (64 t + k, 64 cj + c)
+  const int tid = threadIdx.x, ri = blockIdx.x, cj = blockIdx.y, r0 = 4 * (tid & 15), c0 = 4 * (tid >> 4);
+  const int T = f.ncp / TBS;
+  double acc[4][4] = {};
+  for (int t = cj; t < T; ++t) {
+    for (int idx = tid; idx < TBS * TBS; idx += blockDim.x) {
+      const int r = idx & 63, k = idx >> 6;
+      As[k * 65 + r] = F[(f.ncp + TBS * ri + r) + (int64_t)(TBS * t + k) * f.ld];
+      Bs[k * 65 + r] = X[(TBS * t + r) + (int64_t)(TBS * cj + k) * f.ncp];
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < TBS; ++k) {
+      double a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { a[q] = As[k * 65 + r0 + q]; b[q] = Bs[(c0 + q) * 65 + k]; }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = fma(a[p], b[q], acc[p][q]);
+    }
+    __syncthreads();
+  }
+  const int n = f.nc + f.nr;
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = TBS * ri + r0 + p, c = TBS * cj + c0 + q;
+      if (r < f.nr && c < f.nc) L[f.valptr + (int64_t)c * n + f.nc + r] = acc[p][q];
+    }
 }
 
 inline int64_t round64(int64_t x) { return (x + TBS - 1) / TBS * TBS; }
@@ -397,6 +443,7 @@ int numeric_factor(const pdh::Setup& s, double* Lval, double* Sigma0, cudaStream
     cudaFuncSetAttribute(k_front_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          kSmallFront * kSmallFront * (int)sizeof(double));
     cudaFuncSetAttribute(k_binv_row, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * 65 * (int)sizeof(double));
+    cudaFuncSetAttribute(k_lrs_x, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * 65 * (int)sizeof(double));
   }
   for (int64_t l = 0; l < nl; ++l) {
     for (const auto& ps : passes[l]) {
@@ -420,9 +467,14 @@ int numeric_factor(const pdh::Setup& s, double* Lval, double* Sigma0, cudaStream
                                                                        f.ncp, i);
         ++g_launches;
       }
-      const int64_t nel = (int64_t)(f.nc + f.nr) * f.nc;
-      k_extract_big<<<(unsigned)((nel + 255) / 256), 256, 0, st>>>(f, F, d_x.as<double>(), Lval);
+      const int64_t nel = (int64_t)f.nc * f.nc;
+      k_extract_big<<<(unsigned)((nel + 255) / 256), 256, 0, st>>>(f, d_x.as<double>(), Lval);
       ++g_launches;
+      if (f.nr > 0) {
+        k_lrs_x<<<dim3((unsigned)((f.nr + TBS - 1) / TBS), (unsigned)(f.ncp / TBS)), 256, 2 * 64 * 65 * sizeof(double),
+                  st>>>(f, F, d_x.as<double>(), Lval);
+        ++g_launches;
+      }
     }
     for (int32_t k : bylevel[l]) {
       const Front& f = fr[k];

@@ -2,20 +2,25 @@
 // per elimination-tree level (Section 3.2, Step 1 forward and Step 3 backward
 // substitution; Algorithm 1 steps 3 and 5).
 //
+// The factor holds, per supernode s, D_s = L_ss^-1 and M_s = L_rs L_ss^-1
+// (the off-diagonal rows times the inverse), so that
+//   forward   y_s = D_s b_s,           b_r -= M_s b_s
+//   backward  u_s = D_s^T y_s - M_s^T u_r
+// and every tile of a supernode needs only inputs that are final before any
+// of them starts: one dependent step per supernode along the tree.
+//
 // Work is listed once as tasks in a topological order (forward: leaves first;
 // backward: the reverse).  A supernode of at most 64 columns and 128
-// off-diagonal rows is one task; a larger one is cut into 64 x 64 tiles of its
-// diagonal block (stored as the inverse) and of its off-diagonal block.  A
-// persistent grid claims tasks in list order from one atomic counter; a task
-// waits only for tasks earlier in the list, which are already claimed by
-// running CTAs, so the grid always makes progress whatever the hardware's CTA
-// order.
-//   forward  diag tile / small supernode s: waits until every task writing
-//            into s's rows is done
-//            off tile of s: waits until every diag tile of s is done
+// off-diagonal rows is one task; a larger one is cut into 64 x 64 tiles of D_s
+// and of M_s.  A persistent grid claims tasks in list order from one atomic
+// counter; a task waits only for tasks earlier in the list, which are already
+// claimed by running CTAs, so the grid always makes progress whatever the
+// hardware's CTA order.
+//   forward  any task of s: waits until every task writing into s's rows is
+//            done
 //   backward off tile / small supernode s: waits until the supernodes owning
 //            its off-diagonal rows are done
-//            diag tile of s: waits until every off tile of s is done
+//            diag tile of s: waits for nothing (y is final)
 // Results move through FP64 atomics in L2; producers fence before signalling,
 // consumers fence after waiting and read the vectors with L1-bypassing loads.
 // On B300 these solves are bound by the FP64 FMA rate (three right-hand sides
@@ -146,13 +151,10 @@ __global__ void __launch_bounds__(256, 4) k_sf_solve(SparseFactor f, int64_t nta
     // ---- wait for the inputs
     if (tid == 0) {
       const unsigned long long t0 = gtimer();
-      const bool on_targets = FWD ? false : (kind != KIND_DIAG);
-      if (on_targets) {
-        for (int64_t q = f.tgt_ptr[oi]; q < f.tgt_ptr[oi + 1]; ++q) wait_zero(cB + f.tgt[q], f.status, t0);
-      } else if (FWD && kind == KIND_OFF) {
-        wait_zero(cB + s, f.status, t0);
-      } else {
+      if (FWD) {
         wait_zero(cA + s, f.status, t0);
+      } else if (kind != KIND_DIAG) {
+        for (int64_t q = f.tgt_ptr[oi]; q < f.tgt_ptr[oi + 1]; ++q) wait_zero(cB + f.tgt[q], f.status, t0);
       }
       __threadfence();
     }
@@ -161,7 +163,7 @@ __global__ void __launch_bounds__(256, 4) k_sf_solve(SparseFactor f, int64_t nta
     if (kind == KIND_FUSED) {
       const int n = (int)nc;
       if (FWD) {
-        // y_s = Dinv_s b_s (its tile staged before the wait), then b[rows] -= L_off y_s
+        // y_s = D_s b_s (its tile staged before the wait), then b[rows] -= M_s b_s
         if (tid < TT) {
           if (tid < n) load3(xs, tid, v0 + 3 * (c0 + tid));
           else xs[tid][0] = xs[tid][1] = xs[tid][2] = 0.0;
@@ -179,7 +181,7 @@ __global__ void __launch_bounds__(256, 4) k_sf_solve(SparseFactor f, int64_t nta
           stage_tile(tile, Po, ld, r0, 0, nrow, n, false);
           __syncthreads();
           a0 = a1 = a2 = 0.0;
-          if (o < nrow) partial(tile, ys, false, 0, n, a0, a1, a2);
+          if (o < nrow) partial(tile, xs, false, 0, n, a0, a1, a2);
           reduce4(part, a0, a1, a2);
           if (ch == 0 && o < nrow) {
             double* d = v0 + 3 * (int64_t)R[r0 + o];
@@ -188,7 +190,7 @@ __global__ void __launch_bounds__(256, 4) k_sf_solve(SparseFactor f, int64_t nta
           __syncthreads();
         }
       } else {
-        // z_s = y_s - L_off^T u[rows], then u_s = Dinv_s^T z_s
+        // e = M_s^T u[rows], then u_s = D_s^T y_s - e
         for (int r0 = 0; r0 < nr; r0 += TT) {
           const int nrow = (int)min((int64_t)TT, nr - r0);
           if (r0 > 0) stage_tile(tile, Po, ld, r0, 0, nrow, n, false);   // the first was staged before the wait
@@ -201,10 +203,11 @@ __global__ void __launch_bounds__(256, 4) k_sf_solve(SparseFactor f, int64_t nta
           __syncthreads();
         }
         reduce4(part, a0, a1, a2);
+        const double e0 = a0, e1 = a1, e2 = a2;   // valid in threads with ch == 0
         if (ch == 0) {
           if (o < n) {
-            const double* zz = v1 + 3 * (c0 + o);
-            ys[o][0] = __ldcg(zz) - a0; ys[o][1] = __ldcg(zz + 1) - a1; ys[o][2] = __ldcg(zz + 2) - a2;
+            const double* yy = v1 + 3 * (c0 + o);
+            ys[o][0] = __ldcg(yy); ys[o][1] = __ldcg(yy + 1); ys[o][2] = __ldcg(yy + 2);
           } else {
             ys[o][0] = ys[o][1] = ys[o][2] = 0.0;
           }
@@ -214,14 +217,14 @@ __global__ void __launch_bounds__(256, 4) k_sf_solve(SparseFactor f, int64_t nta
         a0 = a1 = a2 = 0.0;
         if (o < n) partial(tile, ys, true, o, n, a0, a1, a2);
         reduce4(part, a0, a1, a2);
-        if (ch == 0 && o < n) { double* d = v0 + 3 * (c0 + o); d[0] = a0; d[1] = a1; d[2] = a2; }
+        if (ch == 0 && o < n) { double* d = v0 + 3 * (c0 + o); d[0] = a0 - e0; d[1] = a1 - e1; d[2] = a2 - e2; }
       }
     } else {
       if (tid < TT) {
         xs[tid][0] = xs[tid][1] = xs[tid][2] = 0.0;
         if (FWD) {
-          // forward contracts over the tile's columns
-          if (tid < cols_t) load3(xs, tid, (diag ? v0 : v1) + 3 * (c0 + cb + tid));
+          // forward contracts over the tile's columns (b_s for both kinds)
+          if (tid < cols_t) load3(xs, tid, v0 + 3 * (c0 + cb + tid));
         } else {
           // backward contracts over the tile's rows
           if (tid < rows_t) load3(xs, tid, diag ? v1 + 3 * (c0 + rb + tid) : v0 + 3 * (int64_t)R[rb + tid]);
@@ -239,7 +242,7 @@ __global__ void __launch_bounds__(256, 4) k_sf_solve(SparseFactor f, int64_t nta
       if (ch == 0 && o < (FWD ? rows_t : cols_t)) {
         double* d;
         if (FWD) d = diag ? v1 + 3 * (c0 + rb + o) : v0 + 3 * (int64_t)R[rb + o];
-        else d = diag ? v0 + 3 * (c0 + cb + o) : v1 + 3 * (c0 + cb + o);
+        else d = v0 + 3 * (c0 + cb + o);
         const double sg = diag ? 1.0 : -1.0;
         atomicAdd(d, sg * a0); atomicAdd(d + 1, sg * a1); atomicAdd(d + 2, sg * a2);
       }
@@ -253,8 +256,7 @@ __global__ void __launch_bounds__(256, 4) k_sf_solve(SparseFactor f, int64_t nta
         else
           for (int64_t q = f.tgt_ptr[oi]; q < f.tgt_ptr[oi + 1]; ++q) atomicSub(cA + f.tgt[q], 1);
       } else {
-        if (kind == KIND_OFF) atomicSub(cA + s, 1);
-        else atomicSub(cB + s, 1);
+        atomicSub(cB + s, 1);   // every task of s counts towards u_s
       }
       cur = my_next < ntasks ? tasks[my_next] : make_int4(-1, 0, 0, 0);
       if (my_next < ntasks) my_next = atomicAdd(next, 1);

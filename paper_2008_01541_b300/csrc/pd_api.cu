@@ -1063,7 +1063,7 @@ pd_status pd_solver::upload(const pdh::Setup& h, const pdh::Input& in) {
             const int ti = targets(sn, rb, std::min(nr, rb + 64), (nc + 63) / 64);
             for (int32_t cb = 0; cb < nc; cb += 64) {
               fo.push_back(make_int4(sn | KO, rb, cb, ti));
-              init[ZP + sn]++;
+              init[ZP + sn]++; init[UD + sn]++;   // backward: every tile of sn adds into u_sn
             }
           }
         }
@@ -1108,10 +1108,9 @@ pd_status pd_solver::upload(const pdh::Setup& h, const pdh::Input& in) {
           gr.out.assign(nn, {});
           gr.indeg.assign(nn, 0);
           auto edge = [&](int a, int b) { gr.out[a].push_back(b); ++gr.indeg[b]; };
-          // fwd: group A(s) = FIN (inputs of s's diagonal / fused work), B(s) = YD (s's y done)
-          // bwd: group A(s) = UD (s's u done), B(s) = ZP (s's off tiles done)
+          // fwd: group A(s) = FIN (the inputs of every task of s)
+          // bwd: group A(s) = UD (s's u done: every task of s)
           auto A = [&](int32_t sn) { return nt + sn; };
-          auto B = [&](int32_t sn) { return nt + (int)nsn + sn; };
           for (int i = 0; i < nt; ++i) {
             const int4& t = tl[i];
             const int32_t sn = t.x & 0x1fffffff, kind = t.x & (3 << 29);
@@ -1120,13 +1119,11 @@ pd_status pd_solver::upload(const pdh::Setup& h, const pdh::Input& in) {
               for (int64_t q = tptr[t.w]; q < tptr[t.w + 1]; ++q) fn(tg[q]);
             };
             if (fwd) {
-              if (kind == KD) { edge(A(sn), i); edge(i, B(sn)); }
-              else if (kind == KF) { edge(A(sn), i); each_target([&](int32_t a) { edge(i, A(a)); }); }
-              else { edge(B(sn), i); each_target([&](int32_t a) { edge(i, A(a)); }); }
+              edge(A(sn), i);
+              if (kind != KD) each_target([&](int32_t a) { edge(i, A(a)); });
             } else {
-              if (kind == KD) { edge(B(sn), i); edge(i, A(sn)); }
-              else if (kind == KF) { each_target([&](int32_t a) { edge(A(a), i); }); edge(i, A(sn)); }
-              else { each_target([&](int32_t a) { edge(A(a), i); }); edge(i, B(sn)); }
+              if (kind != KD) each_target([&](int32_t a) { edge(A(a), i); });
+              edge(i, A(sn));
             }
           }
           const std::vector<int> ord = list_schedule(gr, nw);

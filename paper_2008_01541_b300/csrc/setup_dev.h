@@ -15,8 +15,10 @@ namespace pdk {
 // From the host's symbolic analysis s (ordering, supernodes, elimination
 // tree, assembled matrix s.A and s.B22, built with Input::numeric = false):
 // writes the supernodal factor into Lval (s.nnzL doubles on the device, the
-// layout of pdh::Setup::Lval: per supernode an (nc + nr) x nc column-major
-// panel whose diagonal block holds L_ss^-1, lower, zero above) and
+// layout of pdh::Setup::Lval, per supernode an (nc + nr) x nc column-major
+// panel, but with the off-diagonal rows multiplied by the inverse: the
+// diagonal block holds L_ss^-1 (lower, zero above), the rows below
+// L_rs L_ss^-1) and
 // Sigma_0 into Sigma0 (m x m, column-major, both triangles).  Temporary
 // device memory (the fronts) is allocated and freed here.  Returns 0, or
 // a pd_status code with *err set (5: the interior matrix is not positive
