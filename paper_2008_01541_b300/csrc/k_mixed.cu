@@ -54,6 +54,8 @@ struct MixedState {
   int nested_mode = -1;
   Factor f, f0;               // per-solve factor, contact-free factor (PCG_WARM)
   double *hdiag = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *u = nullptr;
+  double* sig = nullptr;          // [m][3] Sigma_0 x of the last residual product's x (sig_x)
+  const double* sig_x = nullptr;  // that x's buffer; null once its contents may have changed
   float *Shi = nullptr, *Slo = nullptr;   // Sigma_0 = Shi + Slo (FP32 pair, ~48-bit)
   float *vhi = nullptr, *vlo = nullptr;   // [m][3] split of the vector being multiplied
   float* Minv0 = nullptr;     // [m][m] explicit inverse of the contact-free factor (PCG form), built once
@@ -763,8 +765,10 @@ __device__ __forceinline__ void df_add(float& h, float& l, float h2, float l2) {
 // FP32 pipes (Shi + Slo rows with stride ld, v = vhi + vlo interleaved [ld][3]);
 // one warp takes two rows, so every vector load serves both; lanes are
 // combined in double-float too, so only the final conversion is FP64.
+// out2 (optional) receives a second copy.
 __global__ void k_symv_df(const float* __restrict__ Shi, const float* __restrict__ Slo, int64_t m, int64_t ld,
-                          const float* __restrict__ vhi, const float* __restrict__ vlo, double* __restrict__ out) {
+                          const float* __restrict__ vhi, const float* __restrict__ vlo, double* __restrict__ out,
+                          double* __restrict__ out2) {
   const int64_t i0 = 2 * ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (i0 >= m) return;
@@ -813,7 +817,10 @@ __global__ void k_symv_df(const float* __restrict__ Shi, const float* __restrict
       for (int cc = 0; cc < 3; ++cc)
         if (ww == w && cc == c) { hc = h[ww][cc]; lc = l[ww][cc]; }
     const int64_t row = w == 0 ? i0 : i1;
-    if (w == 0 || i1 != i0) out[3 * row + c] = (double)hc + (double)lc;
+    if (w == 0 || i1 != i0) {
+      out[3 * row + c] = (double)hc + (double)lc;
+      if (out2) out2[3 * row + c] = (double)hc + (double)lc;
+    }
   }
 }
 
@@ -1108,6 +1115,7 @@ static pd_status ensure_state(pd_solver* s) {
   if (A((void**)&M->hdiag, sizeof(double) * m) || A((void**)&M->r, sizeof(double) * 3 * m) ||
       A((void**)&M->z, sizeof(double) * 3 * m) || A((void**)&M->p, sizeof(double) * 3 * m) ||
       A((void**)&M->q, sizeof(double) * 3 * m) || A((void**)&M->u, sizeof(double) * 3 * m) ||
+      A((void**)&M->sig, sizeof(double) * 3 * m) ||
       A((void**)&M->sc, sizeof(double) * 8) || A((void**)&M->w, sizeof(float) * 3 * mq) ||
       A((void**)&M->uo, sizeof(float) * 3 * mq) || A((void**)&M->Shi, sizeof(float) * m * M->ldm) ||
       A((void**)&M->Slo, sizeof(float) * m * M->ldm) || A((void**)&M->vhi, sizeof(float) * 3 * M->ldm) ||
@@ -1395,10 +1403,14 @@ static void apply_minv(pd_solver* s, const double* r, double* z) {
 }
 
 // q = H p = Sigma_0 p + C_22 p  (double-float Sigma_0 product, FP64 contact term)
+// q = H p; Sigma_0 p is also kept (M->sig), for the bookkeeping's Sigma_0 u
+// when p is the solve's result
 static void hmatvec(pd_solver* s, const double* p, double* q) {
   MixedState* M = s->mixed;
   k_split<<<nblk(3 * s->m, 256), 256, 0, s->stream>>>(p, 3 * s->m, M->vhi, M->vlo);
-  k_symv_df<<<nblk(16 * (s->m + 1), 256), 256, 0, s->stream>>>(M->Shi, M->Slo, s->m, M->ldm, M->vhi, M->vlo, q);
+  k_symv_df<<<nblk(16 * (s->m + 1), 256), 256, 0, s->stream>>>(M->Shi, M->Slo, s->m, M->ldm, M->vhi, M->vlo, q,
+                                                               M->sig);
+  M->sig_x = p;
   pdk::g_launches += 2;
   if (s->k > 0) {
     k_contact_matvec<<<nblk(s->k, 128), 128, 0, s->stream>>>(s->k, s->c_idx, s->c_w, s->c_s, p, q);
@@ -1528,6 +1540,7 @@ pd_status mixed_iterate(pd_solver* s, const double* g, const double* u0, double*
     rs = cap_finish(s);
     if (rs != PD_OK) return rs;
   }
+  M->sig_x = nullptr;   // u is about to change
   s->tbegin(4);
   // u = u0 (or 0); r = g - H u (r = g for the zero start, no product).  The
   // scalars the start needs (g.g, r.r; for a supplied start u.r and g.u)
@@ -1617,8 +1630,10 @@ pd_status mixed_iterate(pd_solver* s, const double* g, const double* u0, double*
     for (it = 1; it <= s->opt.max_refine && ce == cudaSuccess; ++it) {
       const int sa = rzs(it), sb = rzs(it + 1);
       // q = H p with p already split by k_cg_dir2
-      k_symv_df<<<nblk(16 * (s->m + 1), 256), 256, 0, st>>>(M->Shi, M->Slo, s->m, M->ldm, M->vhi, M->vlo, M->q);
+      k_symv_df<<<nblk(16 * (s->m + 1), 256), 256, 0, st>>>(M->Shi, M->Slo, s->m, M->ldm, M->vhi, M->vlo, M->q,
+                                                            nullptr);
       ++pdk::g_launches;
+      M->sig_x = nullptr;   // u changes in this iteration's step
       if (s->k > 0) {
         k_contact_matvec<<<nblk(s->k, 128), 128, 0, st>>>(s->k, s->c_idx, s->c_w, s->c_s, M->p, M->q);
         ++pdk::g_launches;
@@ -1697,10 +1712,19 @@ pd_status mixed_iterate(pd_solver* s, const double* g, const double* u0, double*
 bool sigma_product(pd_solver* s, const double* p, double* q) {
   MixedState* M = s->mixed;
   if (!M) return false;
+  if (p == M->sig_x) {   // the solve's last residual product was of this vector: the same values
+    cudaMemcpyAsync(q, M->sig, sizeof(double) * 3 * s->m, cudaMemcpyDeviceToDevice, s->stream);
+    return true;
+  }
   k_split<<<nblk(3 * s->m, 256), 256, 0, s->stream>>>(p, 3 * s->m, M->vhi, M->vlo);
-  k_symv_df<<<nblk(16 * (s->m + 1), 256), 256, 0, s->stream>>>(M->Shi, M->Slo, s->m, M->ldm, M->vhi, M->vlo, q);
+  k_symv_df<<<nblk(16 * (s->m + 1), 256), 256, 0, s->stream>>>(M->Shi, M->Slo, s->m, M->ldm, M->vhi, M->vlo, q,
+                                                               nullptr);
   pdk::g_launches += 2;
   return true;
+}
+
+void forget_sigma_product(pd_solver* s) {
+  if (s->mixed) s->mixed->sig_x = nullptr;
 }
 
 // z = M0^-1 r with the contact-free factor of Sigma_0 (computed on first use).

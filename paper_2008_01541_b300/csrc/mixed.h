@@ -13,6 +13,8 @@ void mixed_free(pd_solver* s);
 // double-float arithmetic (the residual product, FP64-accurate); false when
 // the low-precision state does not exist (the FP64 form).
 bool sigma_product(pd_solver* s, const double* p, double* q);
+// the kept Sigma_0 u of the last solve no longer matches its buffer
+void forget_sigma_product(pd_solver* s);
 // z = M0^-1 r with the contact-free low-precision factor of Sigma_0.
 pd_status apply_free(pd_solver* s, const double* r, double* z);
 void mixed_invalidate(pd_solver* s);

@@ -277,6 +277,7 @@ pd_status pd_solver::region_solve_core(const double* g_dev, const double* u0_dev
     ++precision_fallbacks;
     last_residual = -1.0;
   }
+  pdm::forget_sigma_product(this);   // u now comes from the FP64 solve
   precision = low;
   return r;
 }
