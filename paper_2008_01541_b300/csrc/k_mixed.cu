@@ -90,6 +90,7 @@ struct MixedState {
   int* cap_cnt = nullptr;     // [1] active count; cap_cnt_h its pinned copy
   int* cap_cnt_h = nullptr;
   float* Y = nullptr;
+  double* ccoef = nullptr;    // [cap_rows][8] sqrt(c_j) w_js of each active spring's slots (0: unused slot)
   double *Scap = nullptr, *Slinv = nullptr;   // S and the inverses of its 64 x 64 diagonal tiles
   double *ct = nullptr, *cy = nullptr, *cwork = nullptr;   // [kp][3] V z, S^-1 V z; [kp][3] x 2 solve work
   double* cpart = nullptr;    // [kp / 64][m][3] chunk partial sums of Y^T S^-1 V z
@@ -928,29 +929,49 @@ __global__ void k_cap_active(int64_t k, const int32_t* __restrict__ cidx, const 
   }
   if (threadIdx.x == 0) *cnt = base;
 }
-// Y[a][:] = sqrt(c_j) sum_s w_js Minv0[node_js][:] for active spring a = slot j
-// (the rows of V M0^-1; the padding columns of Minv0 are zero).
-__global__ void k_cap_rows(const int* __restrict__ act, const int32_t* __restrict__ cidx,
-                           const double* __restrict__ cw, const double* __restrict__ cs,
-                           const float* __restrict__ Mi, int64_t ldm, float* __restrict__ Y) {
+// coef[a][s] = sqrt(c_j) w_js for active spring a = slot j (0 for an unused slot):
+// the entries of V = C^1/2 W, formed once per refactorisation
+__global__ void k_cap_coef(int64_t kact, const int* __restrict__ act, const int32_t* __restrict__ cidx,
+                           const double* __restrict__ cw, const double* __restrict__ cs, double* __restrict__ coef) {
   constexpr int NS = pdk::CSLOTS;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= NS * kact) return;
+  const int64_t a = t / NS;
+  const int q = (int)(t % NS), j = act[a];
+  coef[t] = cidx[NS * j + q] >= 0 ? sqrt(cs[j]) * cw[NS * j + q] : 0.0;
+}
+// Y[a][:] = sum_s coef[a][s] Minv0[node_js][:] for active spring a = slot j
+// (the rows of V M0^-1; the padding columns of Minv0 are zero): one spring
+// per blockIdx.y, four columns per thread.
+__global__ void __launch_bounds__(256) k_cap_rows(const int* __restrict__ act, const int32_t* __restrict__ cidx,
+                                                  const double* __restrict__ coef, const float* __restrict__ Mi,
+                                                  int64_t ldm, float* __restrict__ Y) {
+  constexpr int NS = pdk::CSLOTS;
+  __shared__ float cf[NS];
+  __shared__ int rw[NS];
   const int64_t a = blockIdx.y;
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= ldm) return;
-  const int j = act[a];
-  const double sc = sqrt(cs[j]);
-  float acc = 0.f;
-  for (int q = 0; q < NS; ++q) {
-    const int r = cidx[NS * j + q];
-    if (r < 0) continue;
-    acc = fmaf((float)(sc * cw[NS * j + q]), __ldg(Mi + (int64_t)r * ldm + i), acc);
+  if (threadIdx.x < NS) {
+    const int j = act[a];
+    rw[threadIdx.x] = cidx[NS * j + threadIdx.x];
+    cf[threadIdx.x] = (float)coef[NS * a + threadIdx.x];
   }
-  Y[a * ldm + i] = acc;
+  __syncthreads();
+  const int64_t i4 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;   // ldm is a multiple of 4
+  if (4 * i4 >= ldm) return;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int q = 0; q < NS; ++q) {
+    if (rw[q] < 0) continue;
+    const float4 v = __ldg(reinterpret_cast<const float4*>(Mi + (int64_t)rw[q] * ldm) + i4);
+    acc.x = fmaf(cf[q], v.x, acc.x); acc.y = fmaf(cf[q], v.y, acc.y);
+    acc.z = fmaf(cf[q], v.z, acc.z); acc.w = fmaf(cf[q], v.w, acc.w);
+  }
+  reinterpret_cast<float4*>(Y + a * ldm)[i4] = acc;
 }
 // S = I + V M0^-1 V^T (symmetrised), kp x kp column-major, identity padding.
 __global__ void k_cap_matrix(int64_t kact, int64_t kp, const int* __restrict__ act, const int32_t* __restrict__ cidx,
-                             const double* __restrict__ cw, const double* __restrict__ cs,
-                             const float* __restrict__ Y, int64_t ldm, double* __restrict__ S) {
+                             const double* __restrict__ coef, const float* __restrict__ Y, int64_t ldm,
+                             double* __restrict__ S) {
   constexpr int NS = pdk::CSLOTS;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= kp * kp) return;
@@ -960,53 +981,51 @@ __global__ void k_cap_matrix(int64_t kact, int64_t kp, const int* __restrict__ a
     return;
   }
   const int ja = act[a], jb = act[b];
-  const double sa = sqrt(cs[ja]), sb = sqrt(cs[jb]);
   double h1 = 0.0, h2 = 0.0;
   for (int q = 0; q < NS; ++q) {
     const int ra = cidx[NS * ja + q];
-    if (ra >= 0) h1 += sa * cw[NS * ja + q] * (double)Y[b * ldm + ra];
+    if (ra >= 0) h1 += coef[NS * a + q] * (double)Y[b * ldm + ra];
     const int rb = cidx[NS * jb + q];
-    if (rb >= 0) h2 += sb * cw[NS * jb + q] * (double)Y[a * ldm + rb];
+    if (rb >= 0) h2 += coef[NS * b + q] * (double)Y[a * ldm + rb];
   }
   S[t] = (a == b ? 1.0 : 0.0) + 0.5 * (h1 + h2);
 }
 // t[a][:] = sqrt(c_j) sum_s w_js z[node_js][:]  (V z, 3 right-hand sides)
 __global__ void k_cap_gather(int64_t kact, const int* __restrict__ act, const int32_t* __restrict__ cidx,
-                             const double* __restrict__ cw, const double* __restrict__ cs,
-                             const double* __restrict__ z, double* __restrict__ t) {
+                             const double* __restrict__ coef, const double* __restrict__ z, double* __restrict__ t) {
   constexpr int NS = pdk::CSLOTS;
   const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (a >= kact) return;
   const int j = act[a];
-  const double sc = sqrt(cs[j]);
   double t0 = 0.0, t1 = 0.0, t2 = 0.0;
   for (int q = 0; q < NS; ++q) {
     const int r = cidx[NS * j + q];
     if (r < 0) continue;
-    const double w = sc * cw[NS * j + q];
+    const double w = coef[NS * a + q];
     t0 += w * z[3 * r]; t1 += w * z[3 * r + 1]; t2 += w * z[3 * r + 2];
   }
   t[3 * a] = t0; t[3 * a + 1] = t1; t[3 * a + 2] = t2;
 }
 // part[ch][i][:] = sum over the springs a of chunk ch (kCapChunk of them) of
-// Y[a][i] y[a][:]  (FP64 accumulation of the FP32 rows)
+// Y[a][i] y[a][:], accumulated in FP32 like the M0^-1 r it corrects (the
+// preconditioner is FP32-accurate as a whole; FP64 here ran at the FP64 rate)
 constexpr int kCapChunk = 64;
 __global__ void k_cap_part(int64_t m, int64_t kact, const float* __restrict__ Y, int64_t ldm,
                            const double* __restrict__ y, double* __restrict__ part) {
-  __shared__ double ys[3 * kCapChunk];
+  __shared__ float ys[3 * kCapChunk];
   const int64_t ch = blockIdx.y, a0 = ch * kCapChunk;
   const int na = (int)(kact - a0 < kCapChunk ? kact - a0 : kCapChunk);
-  for (int t = threadIdx.x; t < 3 * na; t += blockDim.x) ys[t] = y[3 * a0 + t];
+  for (int t = threadIdx.x; t < 3 * na; t += blockDim.x) ys[t] = (float)y[3 * a0 + t];
   __syncthreads();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= m) return;
   const float* Yc = Y + a0 * ldm + i;
-  double c0 = 0.0, c1 = 0.0, c2 = 0.0;
+  float c0 = 0.f, c1 = 0.f, c2 = 0.f;
   for (int a = 0; a < na; ++a) {
-    const double v = (double)__ldg(Yc + a * ldm);
-    c0 = fma(v, ys[3 * a], c0);
-    c1 = fma(v, ys[3 * a + 1], c1);
-    c2 = fma(v, ys[3 * a + 2], c2);
+    const float v = __ldg(Yc + a * ldm);
+    c0 = fmaf(v, ys[3 * a], c0);
+    c1 = fmaf(v, ys[3 * a + 1], c1);
+    c2 = fmaf(v, ys[3 * a + 2], c2);
   }
   double* o = part + (ch * m + i) * 3;
   o[0] = c0; o[1] = c1; o[2] = c2;
@@ -1337,6 +1356,7 @@ static pd_status cap_begin(pd_solver* s) {
     const int64_t rows = s->k, kp = (rows + 63) / 64 * 64;
     bool ok = dev_realloc(s, (void**)&M->cap_act, sizeof(int) * rows) &&
               dev_realloc(s, (void**)&M->Y, sizeof(float) * rows * M->ldm) &&
+              dev_realloc(s, (void**)&M->ccoef, sizeof(double) * pdk::CSLOTS * rows) &&
               dev_realloc(s, (void**)&M->Scap, sizeof(double) * kp * kp) &&
               dev_realloc(s, (void**)&M->Slinv, sizeof(double) * kp * 64) &&
               dev_realloc(s, (void**)&M->ct, sizeof(double) * 3 * kp) &&
@@ -1368,11 +1388,11 @@ static pd_status cap_finish(pd_solver* s) {
   const int64_t kp = (kact + 63) / 64 * 64;
   cudaStream_t st = s->stream;
   s->tbegin(8);
-  k_cap_rows<<<dim3(nblk(M->ldm, 256), (unsigned)kact), 256, 0, st>>>(M->cap_act, s->c_idx, s->c_w, s->c_s,
-                                                                      M->Minv0, M->ldm, M->Y);
-  k_cap_matrix<<<nblk(kp * kp, 256), 256, 0, st>>>(kact, kp, M->cap_act, s->c_idx, s->c_w, s->c_s, M->Y,
-                                                   M->ldm, M->Scap);
-  pdk::g_launches += 2;
+  k_cap_coef<<<nblk(pdk::CSLOTS * kact, 256), 256, 0, st>>>(kact, M->cap_act, s->c_idx, s->c_w, s->c_s, M->ccoef);
+  k_cap_rows<<<dim3(nblk(M->ldm / 4, 256), (unsigned)kact), 256, 0, st>>>(M->cap_act, s->c_idx, M->ccoef, M->Minv0,
+                                                                          M->ldm, M->Y);
+  k_cap_matrix<<<nblk(kp * kp, 256), 256, 0, st>>>(kact, kp, M->cap_act, s->c_idx, M->ccoef, M->Y, M->ldm, M->Scap);
+  pdk::g_launches += 3;
   cudaMemsetAsync(M->cstat, 0, sizeof(int) * 4, st);
   pdk::cholesky_fp64(M->Scap, kp, M->Slinv, M->cstat, st, s->la.side ? &s->la : nullptr);
   s->tend();
@@ -1386,7 +1406,7 @@ static void apply_cap_dot(pd_solver* s, const double* r, double* z, double* acc)
   MixedState* M = s->mixed;
   cudaStream_t st = s->stream;
   k_minv_apply<<<nblk(32 * s->m, 256), 256, 0, st>>>(M->Minv0, s->m, M->ldm, M->r32, z);
-  k_cap_gather<<<nblk(M->kact, 128), 128, 0, st>>>(M->kact, M->cap_act, s->c_idx, s->c_w, s->c_s, z, M->ct);
+  k_cap_gather<<<nblk(M->kact, 128), 128, 0, st>>>(M->kact, M->cap_act, s->c_idx, M->ccoef, z, M->ct);
   pdk::g_launches += 2;
   pdk::chol_solve_fp64_tasks(M->Scap, M->cap_kp, M->Slinv, M->ct, M->cy, M->kact, M->cwork, M->ccnt, s->status, st);
   const int nch = (int)((M->kact + kCapChunk - 1) / kCapChunk);
