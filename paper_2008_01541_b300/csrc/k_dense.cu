@@ -362,14 +362,40 @@ __global__ void __launch_bounds__(256) k_chol_update(double* __restrict__ H, int
     for (int q = 0; q < 4; ++q) Aij[(tr + 16 * p) + (int64_t)(tc + 16 * q) * mp] -= acc[p][q];
 }
 
-// Lower-triangular trailing update of n x n tiles from (t0, t0) with panel kt,
-// sliced so that the launch has at least two CTAs per SM where it can.
+// Lower-triangular trailing update of n x n tiles from (t0, t0) with panel kt.
+// S CTAs per tile (S = 1, 2, 4) trade panel reloads for finer work units:
+// each launch takes the S whose whole waves of resident CTAs cover its tiles
+// with the least idle capacity, cost_S = ceil(S tiles / slots_S) slots_S / S
+// in units of one SM's time per tile (one wave of a partly used grid leaves
+// the rest of the FP64 units idle until the next launch).
 void launch_update(double* H, int64_t mp, int kt, int t0, int n, cudaStream_t st) {
   const int64_t tiles = (int64_t)n * (n + 1) / 2;
   if (tiles <= 0) return;
-  if (tiles >= 296) {
+  static int slots[64][3];   // resident CTAs per device for S = 1, 2, 4
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int* sl = slots[dev & 63];
+  if (sl[0] == 0) {
+    int nsm = 0, p1 = 0, p2 = 0, p4 = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p1, k_chol_update<1>, 256, 2 * TB * TB * sizeof(double));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p2, k_chol_update<2>, 256, (TB / 2 + TB) * TB * sizeof(double));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p4, k_chol_update<4>, 256, (TB / 4 + TB) * TB * sizeof(double));
+    sl[1] = std::max(1, nsm * p2);
+    sl[2] = std::max(1, nsm * p4);
+    sl[0] = std::max(1, nsm * p1);
+  }
+  int best = 0;
+  double best_cost = 0.0;
+  for (int v = 0; v < 3; ++v) {
+    const int S = 1 << v;
+    const int64_t units = S * tiles;
+    const double cost = (double)((units + sl[v] - 1) / sl[v]) * sl[v] / S;
+    if (v == 0 || cost < best_cost) { best = v; best_cost = cost; }
+  }
+  if (best == 0) {
     k_chol_update<1><<<(unsigned)tiles, 256, 2 * TB * TB * sizeof(double), st>>>(H, mp, kt, t0, t0, 0, 1);
-  } else if (tiles >= 148) {
+  } else if (best == 1) {
     k_chol_update<2><<<(unsigned)(2 * tiles), 256, (TB / 2 + TB) * TB * sizeof(double), st>>>(H, mp, kt, t0, t0,
                                                                                               0, 1);
   } else {
