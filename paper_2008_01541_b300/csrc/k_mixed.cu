@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "chol_ll.h"
+#include "df_arith.cuh"
 #include "kernels.h"
 #include "lowp_tile.cuh"
 #include "mixed.h"
@@ -731,36 +732,9 @@ __global__ void k_split_rows(const double* __restrict__ S, int64_t m, int64_t ld
   lo[q] = (float)(v - (double)h);
 }
 
-// one term of the double-float product: exact head product (FMA remainder),
-// cross terms, and the exact rounding error of h + p, all collected in l
-// without renormalising; (h, l) is renormalised by df_norm every four terms,
-// which keeps |l| a few units of h's last place in between
-__device__ __forceinline__ void df_acc_lazy(float a, float b, float x, float y, float& h, float& l) {
-  const float p = a * x;
-  float e = fmaf(a, x, -p);
-  e = fmaf(a, y, e);
-  e = fmaf(b, x, e);
-  const float s = h + p;
-  const float bb = s - h;
-  l += ((h - (s - bb)) + (p - bb)) + e;
-  h = s;
-}
-__device__ __forceinline__ void df_norm(float& h, float& l) {   // two-sum: no magnitude assumption
-  const float s = h + l;
-  const float bb = s - h;
-  l = (h - (s - bb)) + (l - bb);
-  h = s;
-}
-
-// (h, l) += (h2, l2) in double-float arithmetic
-__device__ __forceinline__ void df_add(float& h, float& l, float h2, float l2) {
-  const float s = h + h2;
-  const float bb = s - h;
-  float t = (h - (s - bb)) + (h2 - bb);
-  t += l + l2;
-  h = s + t;
-  l = t - (h - s);
-}
+using pddf::df_acc_lazy;
+using pddf::df_add;
+using pddf::df_norm;
 
 // out = Sigma_0 v for 3 right-hand sides in double-float arithmetic on the
 // FP32 pipes (Shi + Slo rows with stride ld, v = vhi + vlo interleaved [ld][3]);

@@ -23,10 +23,13 @@
 //            diag tile of s: waits for nothing (y is final)
 // Results move through FP64 atomics in L2; producers fence before signalling,
 // consumers fence after waiting and read the vectors with L1-bypassing loads.
-// On B300 these solves are bound by the FP64 FMA rate (three right-hand sides
-// make 3 FMAs per 8-byte factor entry), so only the nonzero part of every tile
-// is multiplied.  Every wait is bounded (about a second); on expiry code 300
-// goes to status[1] and all later waits are skipped.
+// Three right-hand sides make 3 FP64 FMAs per 8-byte factor entry, and only
+// the nonzero part of every tile is multiplied.  The time is nonetheless set
+// by the dependency waits along the elimination tree rather than by the FP64
+// rate or the bytes: the same tasks with the products in double-float on the
+// FP32 pipes (a fifth of the FP64-pipe time) ran no faster.  Every wait is
+// bounded (about a second); on expiry code 300 goes to status[1] and all later
+// waits are skipped.
 #include <algorithm>
 
 #include "kernels.h"
@@ -77,8 +80,7 @@ __device__ __forceinline__ void stage_tile(double (*tile)[TT + 1], const double*
 
 // Partial sums of out[o] = sum_t T[o][t] vec[t] (trans: T[t][o]) over the
 // terms t in [lo, hi) of chunk ch (thread o = tid % 64, ch = tid / 64, 16
-// terms per chunk).  Only the nonzero range is visited: FP64 FMAs are the
-// scarce resource of these solves.
+// terms per chunk).  Only the nonzero range is visited.
 __device__ __forceinline__ void partial(const double (*tile)[TT + 1], const double (*vec)[3], bool trans, int lo,
                                         int hi, double& a0, double& a1, double& a2) {
   const int o = threadIdx.x % TT, ch = threadIdx.x / TT;
