@@ -14,7 +14,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU = ["k_local.cu", "k_sparse.cu", "k_dense.cu", "k_mixed.cu", "k_chol_ll.cu", "pd_api.cu", "k_noalloc.cu", "k_tc.cu", "k_mlp.cu",
       "k_detect.cu", "k_setup.cu"]
 CPP = ["host_setup.cpp", "pd_host.cpp"]
-HEADERS = ["kernels.h", "host_setup.h", "solver.h", "mixed.h", "tc.h", "tc_dev.cuh", "mlp.h", "lowp_tile.cuh", "chol_ll.h"]
+HEADERS = ["kernels.h", "host_setup.h", "solver.h", "mixed.h", "tc.h", "tc_dev.cuh", "mlp.h", "lowp_tile.cuh", "chol_ll.h",
+           "df_arith.cuh", "setup_dev.h"]
 
 
 def _newer(target, deps):
