@@ -25,11 +25,14 @@
 // consumers fence after waiting and read the vectors with L1-bypassing loads.
 // Three right-hand sides make 3 FP64 FMAs per 8-byte factor entry, and only
 // the nonzero part of every tile is multiplied.  The time is nonetheless set
-// by the dependency waits along the elimination tree rather than by the FP64
-// rate or the bytes: the same tasks with the products in double-float on the
-// FP32 pipes (a fifth of the FP64-pipe time) ran no faster.  Every wait is
-// bounded (about a second); on expiry code 300 goes to status[1] and all later
-// waits are skipped.
+// by per-task latency rather than by the FP64 rate or the bytes: on the
+// 598K-tet elbow each direction runs ~36K tasks on 592 resident CTAs, each
+// ~4 us of staging and dependency wait plus 5-8 us of work that is mostly
+// fixed latency (vector loads from L2, the chunk reduction, the atomics and
+// the fence before the signal).  The same tasks with the products in
+// double-float on the FP32 pipes (a fifth of the FP64-pipe time) ran no
+// faster.  Every wait is bounded (about a second); on expiry code 300 goes to
+// status[1] and all later waits are skipped.
 #include <algorithm>
 
 #include "kernels.h"

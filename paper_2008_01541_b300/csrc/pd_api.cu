@@ -1044,13 +1044,16 @@ pd_status pd_solver::upload(const pdh::Setup& h, const pdh::Input& in) {
         return (int)(tptr.size() - 2);
       };
       constexpr int KD = 0, KO = 1 << 29, KF = 2 << 29;
+      // rows of the largest fused task: 256 measured the same, 512 and no
+      // limit slower (serial row blocks on the tree's critical path)
+      constexpr int kFusedRows = 128;
       std::vector<int4> fd, fo, ff;   // per level: diag tiles, off tiles, fused
       std::vector<int4> ft, bt;
       for (int64_t l = 0; l < nl; ++l) {
         fd.clear(); fo.clear(); ff.clear();
         for (int32_t sn : bylevel[l]) {
           const int32_t nc = ncol(sn), nr = nrow(sn);
-          if (nc <= 64 && nr <= 128) {
+          if (nc <= 64 && nr <= kFusedRows) {
             ff.push_back(make_int4(sn | KF, 0, 0, targets(sn, 0, nr, 1)));
             init[UD + sn] = 1;
             continue;
