@@ -65,10 +65,12 @@ struct SparseFactor {
   int* cnt = nullptr;                     // counters, reset from cnt_init before each solve
   const int* cnt_init = nullptr;
   int64_t cnt_fin = 0, cnt_ydone = 0, cnt_next_f = 0, cnt_zpend = 0, cnt_udone = 0, cnt_next_b = 0;
-  int grid = 0;
+  int grid_f = 0, grid_b = 0;             // persistent CTAs of the forward / backward launch
   int* status = nullptr;                  // status[1] <- 300 if a wait gave up
 };
-int sparse_grid();
+// CTAs of the persistent grid: every resident slot of the direction's build
+// (four per SM forward, five backward).
+int sparse_grid(bool forward);
 // b [nfree][3] in: forces (factor order).  Out: y[0..n1) = L_1^-1 b_1 and
 // b[n1..nfree) = b_2 - L_21 y_1.
 void sparse_forward(const SparseFactor& f, double* b, double* y, cudaStream_t st);

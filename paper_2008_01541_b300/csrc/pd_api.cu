@@ -1092,7 +1092,7 @@ pd_status pd_solver::upload(const pdh::Setup& h, const pdh::Input& in) {
       init[NF] = 0; init[NB2] = 0;
       // claim order: the start order of a simulated list schedule (see list_schedule)
       {
-        const int nw = pdk::sparse_grid();
+        const int nwf = pdk::sparse_grid(true), nwb = pdk::sparse_grid(false);
         auto entries = [&](const int4& t) -> double {
           const int32_t sn = t.x & 0x1fffffff, kind = t.x & (3 << 29), nc = ncol(sn), nr = nrow(sn);
           if (kind == KF) return 0.5 * nc * (nc + 1.0) + (double)nr * nc;
@@ -1130,7 +1130,7 @@ pd_status pd_solver::upload(const pdh::Setup& h, const pdh::Input& in) {
               edge(i, A(sn));
             }
           }
-          const std::vector<int> ord = list_schedule(gr, nw);
+          const std::vector<int> ord = list_schedule(gr, fwd ? nwf : nwb);
           if ((int)ord.size() != nt) return;   // keep the level order
           std::vector<int4> out(nt);
           for (int k = 0; k < nt; ++k) out[k] = tl[ord[k]];
@@ -1149,7 +1149,8 @@ pd_status pd_solver::upload(const pdh::Setup& h, const pdh::Input& in) {
       sf.ftasks = sf_ftasks; sf.btasks = sf_btasks; sf.tgt_ptr = sf_tptr; sf.tgt = sf_tgt;
       sf.cnt = sf_cnt; sf.cnt_init = sf_cnt_init;
       sf.cnt_fin = FIN; sf.cnt_ydone = YD; sf.cnt_next_f = NF; sf.cnt_zpend = ZP; sf.cnt_udone = UD; sf.cnt_next_b = NB2;
-      sf.grid = pdk::sparse_grid();
+      sf.grid_f = pdk::sparse_grid(true);
+      sf.grid_b = pdk::sparse_grid(false);
     }
     sf.n1 = n1; sf.nfree = nfree; sf.nsn = h.nsn; sf.nlevels = nl;
     sf.col0 = sn_col0; sf.rowptr = sn_rowptr; sf.rows = rows; sf.valptr = sn_valptr; sf.L = Lval;
