@@ -5,6 +5,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <iterator>
 #include <numeric>
 #include <omp.h>
 
@@ -16,6 +17,32 @@ enum { ST_INVALID = 1, ST_BAD_MESH = 2, ST_REGION = 3, ST_NOT_SPD = 5, ST_OOM = 
 double now_ms() {
   return std::chrono::duration<double, std::milli>(
              std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// Sorted, duplicate-free rows of a sparse pattern from the (row, column)
+// pairs that pairs(f) reports by calling f(row, column): a counting pass, a
+// filling pass, then every row sorted on its own (rows in parallel).
+template <class Pairs>
+void pattern_rows(int64_t nrows, Pairs pairs, std::vector<int64_t>& ptr, std::vector<int32_t>& adj) {
+  std::vector<int64_t> start(nrows + 1, 0);
+  pairs([&](int64_t r, int64_t) { ++start[r + 1]; });
+  for (int64_t i = 0; i < nrows; ++i) start[i + 1] += start[i];
+  std::vector<int32_t> tmp(start[nrows]);
+  std::vector<int64_t> cur(start.begin(), start.end() - 1);
+  pairs([&](int64_t r, int64_t c) { tmp[cur[r]++] = (int32_t)c; });
+  std::vector<int64_t> len(nrows);
+#pragma omp parallel for schedule(dynamic, 512)
+  for (int64_t i = 0; i < nrows; ++i) {
+    const auto b = tmp.begin() + start[i], e = tmp.begin() + start[i + 1];
+    std::sort(b, e);
+    len[i] = std::unique(b, e) - b;
+  }
+  ptr.assign(nrows + 1, 0);
+  for (int64_t i = 0; i < nrows; ++i) ptr[i + 1] = ptr[i] + len[i];
+  adj.resize(ptr[nrows]);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < nrows; ++i)
+    std::copy(tmp.begin() + start[i], tmp.begin() + start[i] + len[i], adj.begin() + ptr[i]);
 }
 
 // ------------------------------------------------------------ element data
@@ -394,27 +421,16 @@ int build(const Input& in, Setup& s, std::string* err) {
   const int64_t n1 = (int64_t)x1nodes.size();
   s.n1 = n1;
   s.nfree = n1 + m;
-  std::vector<int64_t> gptr(n1 + 1, 0);
+  std::vector<int64_t> gptr;
   std::vector<int32_t> gadj;
-  {
-    std::vector<int64_t> keys;
-    keys.reserve(s.alpha.size() * 12);
+  pattern_rows(n1, [&](auto f) {
     for (int32_t e : s.alpha) {
       const int32_t* t = in.tets + 4 * e;
       for (int a = 0; a < 4; ++a)
         for (int b = 0; b < 4; ++b)
-          if (a != b && cls[t[a]] == 0 && cls[t[b]] == 0)
-            keys.push_back((int64_t)tid[t[a]] * n1 + tid[t[b]]);
+          if (a != b && cls[t[a]] == 0 && cls[t[b]] == 0) f(tid[t[a]], tid[t[b]]);
     }
-    std::sort(keys.begin(), keys.end());
-    keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
-    gadj.resize(keys.size());
-    for (size_t q = 0; q < keys.size(); ++q) {
-      gptr[keys[q] / n1 + 1]++;
-      gadj[q] = (int32_t)(keys[q] % n1);
-    }
-    for (int64_t i = 0; i < n1; ++i) gptr[i + 1] += gptr[i];
-  }
+  }, gptr, gadj);
   std::vector<int32_t> ndorder;
   {
     std::vector<double> xyz(3 * n1);
@@ -435,29 +451,19 @@ int build(const Input& in, Setup& s, std::string* err) {
   std::vector<int32_t> ridx(n, -1);
   for (int64_t i = 0; i < m; ++i) ridx[in.region[i]] = (int32_t)i;
   auto build_adj = [&](const std::vector<int32_t>& posx1, std::vector<int64_t>& ptr, std::vector<int32_t>& adj) {
-    std::vector<int64_t> keys;
-    keys.reserve(s.alpha.size() * 12);
-    for (int32_t e : s.alpha) {
-      const int32_t* t = in.tets + 4 * e;
-      for (int a = 0; a < 4; ++a) {
-        if (cls[t[a]] != 0) continue;
-        int64_t pa = posx1[tid[t[a]]];
-        for (int b = 0; b < 4; ++b) {
-          if (a == b || cls[t[b]] == 2) continue;
-          int64_t pb = cls[t[b]] == 0 ? posx1[tid[t[b]]] : n1 + ridx[t[b]];
-          keys.push_back(pa * (n1 + m) + pb);
+    pattern_rows(n1, [&](auto f) {
+      for (int32_t e : s.alpha) {
+        const int32_t* t = in.tets + 4 * e;
+        for (int a = 0; a < 4; ++a) {
+          if (cls[t[a]] != 0) continue;
+          const int64_t pa = posx1[tid[t[a]]];
+          for (int b = 0; b < 4; ++b) {
+            if (a == b || cls[t[b]] == 2) continue;
+            f(pa, cls[t[b]] == 0 ? (int64_t)posx1[tid[t[b]]] : n1 + ridx[t[b]]);
+          }
         }
       }
-    }
-    std::sort(keys.begin(), keys.end());
-    keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
-    ptr.assign(n1 + 1, 0);
-    adj.resize(keys.size());
-    for (size_t q = 0; q < keys.size(); ++q) {
-      ptr[keys[q] / (n1 + m) + 1]++;
-      adj[q] = (int32_t)(keys[q] % (n1 + m));
-    }
-    for (int64_t i = 0; i < n1; ++i) ptr[i + 1] += ptr[i];
+    }, ptr, adj);
   };
   // elimination tree (Liu) with all of x_2 contracted to one root
   auto etree = [&](const std::vector<int64_t>& ptr, const std::vector<int32_t>& adj) {
@@ -516,42 +522,59 @@ int build(const Input& in, Setup& s, std::string* err) {
   const int64_t nf = n1 + m;
   LowerCSC& A = s.A;
   {
-    std::vector<std::pair<int64_t, double>> trip;
-    trip.reserve(s.alpha.size() * 10 + n1);
-    for (int32_t e : s.alpha) {
-      const int32_t* t = in.tets + 4 * e;
-      double G[4][3];
-      shape_grad(&s.Dminv[9 * e], G);
-      double w = 2.0 * (in.mu + in.mu_prime + in.kappa) * s.vol[e];
-      for (int a = 0; a < 4; ++a) {
-        int64_t pa = s.pos[t[a]];
-        if (pa < 0) continue;
-        for (int b = 0; b < 4; ++b) {
-          int64_t pb = s.pos[t[b]];
-          if (pb < 0 || pb > pa) continue;
-          double v = w * (G[a][0] * G[b][0] + G[a][1] * G[b][1] + G[a][2] * G[b][2]);
-          trip.push_back({pb * nf + pa, v});   // (row pa >= col pb)
+    // entries (row pa >= column pb) bucketed by column in element order, then
+    // each column sorted by row, stably so that duplicates are summed in
+    // element order, and compacted; columns in parallel
+    auto each = [&](auto f) {
+      for (int32_t e : s.alpha) {
+        const int32_t* t = in.tets + 4 * e;
+        double G[4][3];
+        shape_grad(&s.Dminv[9 * e], G);
+        const double w = 2.0 * (in.mu + in.mu_prime + in.kappa) * s.vol[e];
+        for (int a = 0; a < 4; ++a) {
+          const int64_t pa = s.pos[t[a]];
+          if (pa < 0) continue;
+          for (int b = 0; b < 4; ++b) {
+            const int64_t pb = s.pos[t[b]];
+            if (pb < 0 || pb > pa) continue;
+            f(pb, pa, w * (G[a][0] * G[b][0] + G[a][1] * G[b][1] + G[a][2] * G[b][2]));
+          }
         }
       }
-    }
-    if (in.dt > 0)
-      for (int64_t i = 0; i < n1; ++i) {
-        int64_t p = pos1[i];
-        trip.push_back({p * nf + p, s.mass[x1nodes[i]] / (in.dt * in.dt)});
+      if (in.dt > 0)
+        for (int64_t i = 0; i < n1; ++i) f(pos1[i], pos1[i], s.mass[x1nodes[i]] / (in.dt * in.dt));
+    };
+    std::vector<int64_t> start(nf + 1, 0);
+    each([&](int64_t c, int64_t, double) { ++start[c + 1]; });
+    for (int64_t j = 0; j < nf; ++j) start[j + 1] += start[j];
+    std::vector<std::pair<int32_t, double>> ent(start[nf]);
+    std::vector<int64_t> cur(start.begin(), start.end() - 1);
+    each([&](int64_t c, int64_t r, double v) { ent[cur[c]++] = {(int32_t)r, v}; });
+    std::vector<int64_t> len(nf);
+#pragma omp parallel for schedule(dynamic, 512)
+    for (int64_t j = 0; j < nf; ++j) {
+      const auto b = ent.begin() + start[j], e = ent.begin() + start[j + 1];
+      std::stable_sort(b, e, [](const std::pair<int32_t, double>& x, const std::pair<int32_t, double>& y) {
+        return x.first < y.first;
+      });
+      int64_t k = 0;
+      for (auto q = b; q != e; ++q) {
+        if (k > 0 && b[k - 1].first == q->first) b[k - 1].second += q->second;
+        else b[k++] = *q;
       }
-    std::sort(trip.begin(), trip.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+      len[j] = k;
+    }
     A.n = nf;
     A.colptr.assign(nf + 1, 0);
-    for (size_t q = 0; q < trip.size();) {
-      size_t r = q;
-      double v = 0.0;
-      while (r < trip.size() && trip[r].first == trip[q].first) v += trip[r++].second;
-      A.row.push_back((int32_t)(trip[q].first % nf));
-      A.val.push_back(v);
-      A.colptr[trip[q].first / nf + 1]++;
-      q = r;
-    }
-    for (int64_t j = 0; j < nf; ++j) A.colptr[j + 1] += A.colptr[j];
+    for (int64_t j = 0; j < nf; ++j) A.colptr[j + 1] = A.colptr[j] + len[j];
+    A.row.resize(A.colptr[nf]);
+    A.val.resize(A.colptr[nf]);
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < nf; ++j)
+      for (int64_t k = 0; k < len[j]; ++k) {
+        A.row[A.colptr[j] + k] = ent[start[j] + k].first;
+        A.val[A.colptr[j] + k] = ent[start[j] + k].second;
+      }
   }
   {
     std::vector<std::pair<int64_t, double>> trip;
@@ -591,20 +614,20 @@ int build(const Input& in, Setup& s, std::string* err) {
   for (int64_t j = n1 - 1; j >= 0; --j)
     if (parent[j] >= 0) { cnext[j] = chead[parent[j]]; chead[parent[j]] = (int32_t)j; }
   {
-    std::vector<int32_t> mark(nf, -1);
+    // struct(j) = (rows of A's column j below j) U (struct(c) \ {j} for the
+    // children c of j): sorted lists merged, no sort
+    std::vector<int32_t> buf;
     for (int64_t j = 0; j < n1; ++j) {
       std::vector<int32_t>& st = cstruct[j];
-      for (int64_t q = A.colptr[j]; q < A.colptr[j + 1]; ++q) {
-        int32_t i = A.row[q];
-        if (i > j && mark[i] != j) { mark[i] = (int32_t)j; st.push_back(i); }
-      }
+      for (int64_t q = A.colptr[j]; q < A.colptr[j + 1]; ++q)   // rows ascend within a column
+        if (A.row[q] > j) st.push_back(A.row[q]);
       for (int32_t c = chead[j]; c != -1; c = cnext[c]) {
-        for (int32_t i : cstruct[c])
-          if (i > j && mark[i] != j) { mark[i] = (int32_t)j; st.push_back(i); }
+        const std::vector<int32_t>& cs = cstruct[c];
+        buf.clear();
+        std::set_union(st.begin(), st.end(), std::upper_bound(cs.begin(), cs.end(), (int32_t)j), cs.end(),
+                       std::back_inserter(buf));
+        st.swap(buf);
       }
-      std::sort(st.begin(), st.end());
-      // children structures are no longer needed unless a child ends a supernode;
-      // the last column of each supernode is decided below, so keep sizes only.
     }
   }
   std::vector<int64_t> cnt(n1);
