@@ -1,6 +1,7 @@
 """The in-tree build: every source file under csrc/ is compiled into the
 library, and every local header a source includes is a dependency of every
-object, so that editing a header rebuilds the objects that inline it."""
+object, so that editing a header rebuilds the objects that inline it; and
+the host setup gives the same bits whatever the number of OpenMP threads."""
 import importlib.util
 import os
 import re
@@ -37,3 +38,21 @@ def test_every_local_header_is_a_dependency():
     assert not missing, missing
     # and nothing listed that does not exist
     assert all(os.path.exists(os.path.join(SRC, h)) for h in b.HEADERS)
+
+
+def test_host_setup_is_deterministic_across_thread_counts():
+    # the ordering, assembly and symbolic phases and the host factorisation
+    # run OpenMP loops over rows, columns and fronts; each entry is computed
+    # by one thread in a fixed order, so Sigma_0 must not depend on the count
+    import subprocess
+    import sys
+    code = ("import sys, hashlib; sys.path.insert(0, %r); import scenes, paper_2008_01541_b300 as pd; "
+            "s = scenes.small_elbow(h=1.5); S, _ = pd.host_schur(s.X, s.tets, s.region, s.dirichlet, s.mu, 1000.0, 0.03); "
+            "print(hashlib.sha256(S.tobytes()).hexdigest())") % ROOT
+    digests = set()
+    for nt in ("1", "4"):
+        env = dict(os.environ, OMP_NUM_THREADS=nt)
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+        assert r.returncode == 0, r.stderr[-2000:]
+        digests.add(r.stdout.strip().splitlines()[-1])
+    assert len(digests) == 1
